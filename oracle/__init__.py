@@ -1,0 +1,193 @@
+"""ctypes wrapper around the FP64 CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by __graft_entry__.smoke() and by
+bench.py's CPU-baseline / reference leg.  The product path (the CUDA library
+and its Python binding) never imports this package, and this package never
+imports the product.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liboracle.so")
+SOURCES = [os.path.join(HERE, "oracle.c")]
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (FP64, no fused multiply-add, OpenMP)."""
+    newest = max(os.path.getmtime(p) for p in SOURCES + [os.path.join(HERE, "oracle.h")])
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-o", LIB_PATH] + SOURCES + ["-lm"]
+    subprocess.check_call(cmd)
+    return LIB_PATH
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("n_products", C.c_int),
+        ("m", C.c_int * 2), ("L", C.c_int * 2), ("Q", C.c_int * 2),
+        ("cost", (C.c_double * 5) * 2),
+        ("pmf", C.POINTER(C.c_double) * 2),
+        ("dmax", C.c_int * 2),
+        ("rho", C.c_double),
+        ("gamma", C.c_double),
+        ("issuing", C.c_int),
+    ]
+
+
+class _Step(C.Structure):
+    _fields_ = [
+        ("s_next", C.c_longlong), ("reward", C.c_double), ("demand", C.c_double),
+        ("issued", C.c_double), ("wasted", C.c_double), ("carried", C.c_double),
+        ("arrived", C.c_double), ("shortage", C.c_double), ("unmet1", C.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(LIB_PATH)
+        P = C.POINTER(_Problem)
+        dp = C.POINTER(C.c_double)
+        L.orc_num_states.argtypes = [P]
+        L.orc_num_states.restype = C.c_longlong
+        L.orc_num_actions.argtypes = [P]
+        L.orc_num_actions.restype = C.c_int
+        L.orc_transition.argtypes = [P, C.c_longlong, C.c_int, C.c_int, C.c_int, C.c_int,
+                                     C.POINTER(_Step)]
+        L.orc_qvalues.argtypes = [P, dp, C.c_longlong, dp]
+        L.orc_vi_solve.argtypes = [P, C.c_double, C.c_int, C.c_int, dp, C.c_void_p,
+                                   C.POINTER(C.c_int), dp, dp, dp, C.c_int]
+        L.orc_backup_states.argtypes = [P, dp, C.c_void_p, C.c_longlong, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_int]
+        L.orc_policy_eval.argtypes = [P, C.c_void_p, C.c_double, C.c_int, dp,
+                                      C.POINTER(C.c_int), C.c_int]
+        L.orc_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_simulate.argtypes = [P, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64,
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+class Problem:
+    """An oracle view of a workloads.Instance (keeps its pmf arrays alive)."""
+
+    def __init__(self, inst, gamma: Optional[float] = None):
+        self.inst = inst
+        st = _Problem()
+        prods = inst.products
+        st.n_products = len(prods)
+        self._pmfs = []
+        for k, p in enumerate(prods):
+            st.m[k], st.L[k], st.Q[k] = p.m, p.L, p.Q
+            for j in range(5):
+                st.cost[k][j] = float(p.cost[j])
+            arr = np.ascontiguousarray(p.pmf, dtype=np.float64)
+            self._pmfs.append(arr)
+            st.pmf[k] = arr.ctypes.data_as(C.POINTER(C.c_double))
+            st.dmax[k] = len(arr) - 1
+        st.rho = float(inst.subst_rate)
+        st.gamma = float(inst.gamma if gamma is None else gamma)
+        st.issuing = int(inst.issuing)
+        self.st = st
+        self.n_states = int(lib().orc_num_states(C.byref(st)))
+        self.n_actions = int(lib().orc_num_actions(C.byref(st)))
+
+    @property
+    def ref(self):
+        return C.byref(self.st)
+
+    # -- model -------------------------------------------------------------
+    def transition(self, s: int, a: int, d1: int, d2: int = 0, u: int = 0) -> dict:
+        out = _Step()
+        rc = lib().orc_transition(self.ref, s, a, d1, d2, u, C.byref(out))
+        if rc != 0:
+            raise ValueError("invalid outcome")
+        return {f: getattr(out, f) for f, _ in _Step._fields_}
+
+    def qvalues(self, V: np.ndarray, s: int) -> np.ndarray:
+        V = np.ascontiguousarray(V, np.float64)
+        q = np.empty(self.n_actions, np.float64)
+        lib().orc_qvalues(self.ref, V.ctypes.data_as(C.POINTER(C.c_double)), s,
+                          q.ctypes.data_as(C.POINTER(C.c_double)))
+        return q
+
+    # -- algorithms ----------------------------------------------------------
+    def vi_solve(self, tol: float, max_iters: int, stop_rule: int = 0, V0=None,
+                 nthreads: int = 0) -> dict:
+        V = np.zeros(self.n_states) if V0 is None else np.array(V0, np.float64, copy=True)
+        pol = np.zeros(self.n_states, np.uint8)
+        it = C.c_int(0)
+        crit, dmx, dmn = C.c_double(0), C.c_double(0), C.c_double(0)
+        rc = lib().orc_vi_solve(self.ref, tol, stop_rule, max_iters,
+                                V.ctypes.data_as(C.POINTER(C.c_double)), _ptr(pol),
+                                C.byref(it), C.byref(crit), C.byref(dmx), C.byref(dmn), nthreads)
+        if rc not in (0, 3):
+            raise RuntimeError(f"orc_vi_solve failed rc={rc}")
+        return dict(V=V, policy=pol, iters=it.value, converged=(rc == 0), crit=crit.value,
+                    dmax=dmx.value, dmin=dmn.value)
+
+    def backup_states(self, V: np.ndarray, states, with_q: bool = False, nthreads: int = 0):
+        V = np.ascontiguousarray(V, np.float64)
+        states = np.ascontiguousarray(states, np.int64)
+        n = len(states)
+        v = np.empty(n, np.float64)
+        pol = np.empty(n, np.int32)
+        q = np.empty((n, self.n_actions), np.float64) if with_q else None
+        rc = lib().orc_backup_states(self.ref, V.ctypes.data_as(C.POINTER(C.c_double)),
+                                     _ptr(states), n, _ptr(v), _ptr(pol), _ptr(q), nthreads)
+        if rc != 0:
+            raise RuntimeError("orc_backup_states failed")
+        return (v, pol, q) if with_q else (v, pol)
+
+    def policy_eval(self, policy: np.ndarray, tol: float, max_iters: int, V0=None,
+                    nthreads: int = 0):
+        V = np.zeros(self.n_states) if V0 is None else np.array(V0, np.float64, copy=True)
+        policy = np.ascontiguousarray(policy, np.uint8)
+        it = C.c_int(0)
+        rc = lib().orc_policy_eval(self.ref, _ptr(policy), tol, max_iters,
+                                   V.ctypes.data_as(C.POINTER(C.c_double)), C.byref(it), nthreads)
+        if rc not in (0, 3):
+            raise RuntimeError("orc_policy_eval failed")
+        return V, it.value, rc == 0
+
+    def simulate(self, policy: np.ndarray, n_rollouts: int, horizon: int, seed: int,
+                 warmup: int = 0, with_traj: bool = False):
+        policy = np.ascontiguousarray(policy, np.uint8)
+        ret = np.empty(n_rollouts, np.float64)
+        kpis = np.empty((n_rollouts, 3), np.float64)
+        traj = np.empty((n_rollouts, horizon), np.int32) if with_traj else None
+        dem = np.empty((n_rollouts, horizon), np.int32) if with_traj else None
+        rc = lib().orc_simulate(self.ref, _ptr(policy), n_rollouts, horizon, warmup,
+                                C.c_uint64(seed), _ptr(ret), _ptr(kpis), _ptr(traj), _ptr(dem))
+        if rc != 0:
+            raise RuntimeError("orc_simulate failed")
+        out = dict(returns=ret, kpis=kpis)
+        if with_traj:
+            out["traj"] = traj
+            out["demand"] = dem
+        return out
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    o = np.empty(4, np.uint32)
+    lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(o))
+    return o

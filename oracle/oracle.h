@@ -1,0 +1,99 @@
+/*
+ * oracle.h -- plain FP64 CPU reference for value iteration on the perishable
+ * inventory MDP of Farrington et al., "Going faster to see further" (2023).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or constant with the CUDA library under
+ * paper_2303_10672_b300/ and neither includes the other.
+ *
+ * Model (single product; the paper's Scenario A equations, observed at the
+ * decision epoch): a state holds the on-hand stock X_1..X_{m-1} by remaining
+ * useful life (X_1 expires at the end of this period) and the pipeline
+ * P_1..P_{L-1} (P_1 arrives before this period's demand).  The arrival
+ * u = P_1 (L >= 2) or u = the action itself (L = 1) joins as the freshest slot
+ * Y_m; demand is issued FIFO or LIFO (Eqs. demoor:fifo / demoor:lifo); the
+ * oldest remainder is wasted; the rest ages by one period.  Reward per
+ * Eq. demoor:reward plus revenue per unit issued (Scenario B reward).
+ * Two products: product 1's shortfall accepts product 2 with probability rho
+ * per unit (binomial, Scenario B appendix).
+ *
+ * State index: digit k has weight (Q+1)^k; digits 0..m-2 are X_1..X_{m-1},
+ * digits m-1..m+L-3 are P_1..P_{L-1}.  Two products: s = s_1 + |S_1| * s_2.
+ * Joint action a = a_1 * (Q_2 + 1) + a_2.
+ */
+#ifndef VI_ORACLE_H
+#define VI_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int n_products;          /* 1 or 2 */
+    int m[2], L[2], Q[2];    /* useful life, lead time, order cap per product */
+    double cost[2][5];       /* c_o (order), c_h (holding), c_s (shortage), c_w (waste), c_r (revenue) */
+    const double *pmf[2];    /* demand pmf on 0..dmax[k] */
+    int dmax[2];
+    double rho;              /* substitution acceptance probability (two products) */
+    double gamma;            /* discount factor, 0 <= gamma <= 1 */
+    int issuing;             /* 0 = FIFO, 1 = LIFO */
+} orc_problem;
+
+typedef struct {
+    long long s_next;
+    double reward;
+    double demand;    /* total demand (both products) */
+    double issued;    /* units issued (both products) */
+    double wasted;    /* units expired at end of period */
+    double carried;   /* units carried to the next period (on hand, not pipeline) */
+    double arrived;   /* units received this period */
+    double shortage;  /* demand lost after substitution */
+    int unmet1;       /* product-1 shortfall before substitution (two products) */
+} orc_step;
+
+long long orc_num_states(const orc_problem *P);
+int orc_num_actions(const orc_problem *P);
+
+/* One deterministic transition T(s, a, omega): omega = (d1) or (d1, d2, u). */
+int orc_transition(const orc_problem *P, long long s, int a, int d1, int d2, int u, orc_step *out);
+
+/* Q(s, a) for every action of state s from the value function V (FP64). */
+int orc_qvalues(const orc_problem *P, const double *V, long long s, double *q);
+
+/* Synchronous value iteration from V (in: V_0, out: V_i).  stop_rule 0 = span,
+ * 1 = sup-norm; stops at the first i with criterion < tol or at max_iters.
+ * policy (optional) gets the one-step look-ahead argmax from the returned V.
+ * Returns 0 if converged, 3 if max_iters was reached, 1 on bad input. */
+int orc_vi_solve(const orc_problem *P, double tol, int stop_rule, int max_iters,
+                 double *V, uint8_t *policy, int *iters, double *crit_out,
+                 double *dmax_out, double *dmin_out, int nthreads);
+
+/* One Bellman update at the listed states: v_out[i] = max_a Q(states[i], a),
+ * pol_out[i] = smallest argmax, q_out (optional) = n x |A| Q-values. */
+int orc_backup_states(const orc_problem *P, const double *V, const long long *states,
+                      long long n, double *v_out, int *pol_out, double *q_out, int nthreads);
+
+/* Evaluate a fixed policy: V <- r_pi + gamma P_pi V from the given V until the
+ * sup-norm change is < tol or max_iters.  Returns 0 / 3 like orc_vi_solve. */
+int orc_policy_eval(const orc_problem *P, const uint8_t *policy, double tol, int max_iters,
+                    double *V, int *iters, int nthreads);
+
+/* Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Rollouts of a fixed policy from the all-zero state.  Period t of rollout r
+ * draws Philox4x32-10(ctr = (t, r, 0, 0), key = (seed lo, seed hi)); word 0 gives
+ * product-1 demand, word 1 product-2 demand, word 2 the substitution bits
+ * (rho must be 1/2 for two products).  returns[r] = sum over the horizon of
+ * gamma^t * reward; kpis[3r..3r+2] = service %, wastage %, mean units carried.
+ * traj (optional) = n_rollouts x horizon states observed before each decision. */
+int orc_simulate(const orc_problem *P, const uint8_t *policy, int n_rollouts, int horizon,
+                 int warmup, uint64_t seed, double *returns, double *kpis, int32_t *traj,
+                 int32_t *demand_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

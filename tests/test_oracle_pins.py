@@ -1,0 +1,377 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these compares the oracle with itself: each check uses a worked example
+written by hand from the paper's equations, a published known-answer vector, a
+closed form derived independently, an exhaustive enumeration built on a second
+(unit-by-unit) formulation of the dynamics, or an invariant of the MDP.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+import workloads
+from workloads import FIFO, LIFO
+import unit_model
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10 known-answer vectors
+# ---------------------------------------------------------------------------
+
+def load_kat():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        lhs, rhs = line.split("->")
+        ins = [int(x, 16) for x in lhs.split()]
+        outs = [int(x, 16) for x in rhs.split()]
+        rows.append((ins[:4], ins[4:], outs))
+    return rows
+
+
+def test_philox_known_answers():
+    rows = load_kat()
+    assert len(rows) == 3
+    for ctr, key, want in rows:
+        assert oracle.philox4x32_10(ctr, key).tolist() == want
+
+
+# ---------------------------------------------------------------------------
+# transitions: hand-worked examples of Eq. demoor:fifo / demoor:lifo / reward
+# ---------------------------------------------------------------------------
+
+def _inst_from_case(c):
+    pmf = np.full(c["d"] + 1, 1.0 / (c["d"] + 1))
+    return workloads.single_product(c["m"], c["L"], c["Q"], c["cost"], pmf, 0.9, c["issuing"])
+
+
+def test_golden_transitions_single():
+    data = json.load(open(os.path.join(GOLDEN, "transitions.json")))
+    for c in data["cases"]:
+        inst = _inst_from_case(c)
+        P = oracle.Problem(inst)
+        s = unit_model.encode(c["digits"], c["Q"])
+        st = P.transition(s, c["a"], c["d"])
+        assert st["s_next"] == unit_model.encode(c["s_next_digits"], c["Q"]), c["name"]
+        assert st["reward"] == c["reward"], c["name"]
+        for k in ("wasted", "carried", "shortage", "issued"):
+            assert st[k] == c[k], (c["name"], k)
+
+
+def test_golden_transitions_two_products():
+    data = json.load(open(os.path.join(GOLDEN, "transitions.json")))
+    for c in data["two_product_cases"]:
+        prods = []
+        for k in range(2):
+            pmf = np.full(6, 1.0 / 6)
+            prods.append(workloads.Product(c["m"][k], 1, c["Q"][k], c["cost"][k], pmf))
+        inst = workloads.Instance("g2", prods, gamma=0.9, issuing=c["issuing"], subst_rate=0.5)
+        P = oracle.Problem(inst)
+        s1 = unit_model.encode(c["digits1"], c["Q"][0])
+        s2 = unit_model.encode(c["digits2"], c["Q"][1])
+        S1 = prods[0].n_states
+        a = c["a1"] * (c["Q"][1] + 1) + c["a2"]
+        st = P.transition(s1 + S1 * s2, a, c["d1"], c["d2"], c["u"])
+        want = (unit_model.encode(c["s_next1_digits"], c["Q"][0])
+                + S1 * unit_model.encode(c["s_next2_digits"], c["Q"][1]))
+        assert st["s_next"] == want
+        assert st["reward"] == c["reward"]
+        for k in ("wasted", "carried", "shortage", "issued"):
+            assert st[k] == c[k], k
+
+
+# ---------------------------------------------------------------------------
+# transitions agree with the unit-by-unit issuing model everywhere
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m,L,Q,issuing", [(1, 1, 4, 0), (2, 1, 4, 1), (3, 1, 3, 0), (3, 1, 3, 1),
+                                           (4, 2, 2, 0), (4, 2, 2, 1), (2, 3, 3, 0), (1, 3, 3, 1),
+                                           (5, 1, 2, 1), (3, 2, 3, 0)])
+def test_transition_matches_unit_issuing(m, L, Q, issuing):
+    rng = np.random.default_rng(m * 100 + L * 10 + Q + issuing)
+    cost = rng.uniform(0, 10, 5)
+    inst = workloads.single_product(m, L, Q, cost, workloads.poisson_pmf(2.5, 3 * Q + 2), 0.9, issuing)
+    P = oracle.Problem(inst)
+    for s in range(inst.n_states):
+        for a in range(Q + 1):
+            for d in range(inst.products[0].dmax + 1):
+                st = P.transition(s, a, d)
+                sn, iss, w, car, sh, arr, tot = unit_model.product_period(m, L, Q, issuing, s, a, d)
+                assert st["s_next"] == sn
+                assert (st["issued"], st["wasted"], st["carried"], st["shortage"]) == (iss, w, car, sh)
+                r = -cost[0] * a - cost[1] * car - cost[2] * sh - cost[3] * w + cost[4] * iss
+                assert abs(st["reward"] - r) <= 1e-12 * (1 + abs(r))
+                # conservation: stock on hand + arrival = issued + wasted + carried
+                assert tot == iss + w + car
+                assert sh == max(d - tot, 0)
+
+
+def test_two_product_transitions_match_unit_model():
+    rng = np.random.default_rng(7)
+    prods = [workloads.Product(2, 1, 2, tuple(rng.uniform(0, 5, 5)), workloads.poisson_pmf(1.5, 5)),
+             workloads.Product(3, 1, 1, tuple(rng.uniform(0, 5, 5)), workloads.poisson_pmf(1.0, 4))]
+    for issuing in (FIFO, LIFO):
+        inst = workloads.Instance("t2", prods, gamma=0.9, issuing=issuing, subst_rate=0.3)
+        P = oracle.Problem(inst)
+        for s in range(inst.n_states):
+            for a in range(inst.n_actions):
+                got = {}
+                for d1 in range(6):
+                    for d2 in range(5):
+                        n = P.transition(s, a, d1, d2, 0)["unmet1"]
+                        for u in range(n + 1):
+                            st = P.transition(s, a, d1, d2, u)
+                            got[(d1, d2, u)] = (st["s_next"], st["reward"])
+                want = []
+                for pr, sn, r in unit_model.outcomes(inst, s, a):
+                    want.append((sn, r))
+                assert len(want) == len(got)
+                for (snw, rw), (sng, rg) in zip(want, [got[k] for k in sorted(got)]):
+                    assert snw == sng
+                    assert abs(rw - rg) <= 1e-12 * (1 + abs(rw))
+
+
+def test_outcome_probabilities_sum_to_one():
+    inst = workloads.config3(Q=2)
+    S, A = inst.n_states, inst.n_actions
+    for s in (0, 3, S - 1):
+        for a in (0, A // 2, A - 1):
+            tot = sum(pr for pr, _, _ in unit_model.outcomes(inst, s, a))
+            assert abs(tot - 1.0) < 1e-14
+    for cfg in (workloads.config1(), workloads.config2(), workloads.config4()):
+        assert abs(cfg.products[0].pmf.sum() - 1.0) < 1e-14
+        assert (cfg.products[0].pmf >= 0).all()
+
+
+def test_state_counts_match_configs():
+    assert workloads.config1().n_states == 441
+    assert workloads.config2().n_states == 4_084_101
+    assert workloads.config3().n_states == 50_625
+    assert workloads.config3().n_actions == 225
+    assert workloads.config4().n_states == 19_487_171
+    for cfg in (workloads.config1(), workloads.config3(Q=2)):
+        assert oracle.Problem(cfg).n_states == cfg.n_states
+
+
+# ---------------------------------------------------------------------------
+# P1: newsvendor closed forms (m = 1)
+# ---------------------------------------------------------------------------
+
+def poisson_loss(mu, a):
+    """E[(D-a)^+], E[(a-D)^+] for D ~ Poisson(mu) via the standard loss-function identity."""
+    F = stats.poisson.cdf(a, mu)
+    p = stats.poisson.pmf(a, mu)
+    over = (mu - a) * (1 - F) + mu * p
+    under = a - mu + over
+    return over, under
+
+
+@pytest.mark.parametrize("cost,issuing", [((3, 1, 5, 7, 0), FIFO), ((3, 1, 5, 7, 0), LIFO),
+                                          ((1, 0, 6, 2, 1.5), FIFO)])
+def test_newsvendor_single_state(cost, issuing):
+    mu, Q, gamma = 5.0, 20, 0.99
+    inst = workloads.single_product(1, 1, Q, cost, workloads.poisson_pmf(mu, 40), gamma, issuing)
+    c_o, c_h, c_s, c_w, c_r = cost
+    ratio = (c_s + c_r - c_o) / (c_s + c_r + c_w)
+    a_star = min(a for a in range(Q + 1) if stats.poisson.cdf(a, mu) >= ratio or a == Q)
+    if cost == (3, 1, 5, 7, 0):
+        assert a_star == 3            # F(2)=0.125 < 1/6 <= F(3)=0.265
+    over, under = poisson_loss(mu, a_star)
+    rbar = -c_o * a_star - c_s * over - c_w * under + c_r * (mu - over)
+    P = oracle.Problem(inst)
+    res = P.vi_solve(tol=1e-10, max_iters=20000, stop_rule=1)
+    assert res["converged"]
+    assert res["policy"][0] == a_star
+    assert abs(res["V"][0] - rbar / (1 - gamma)) <= 1e-8 * abs(rbar / (1 - gamma))
+
+
+def test_newsvendor_lead_time_two():
+    """m = 1, L = 2: state = the arriving order x; V(x) = g(x) + M with
+    M = (gamma g(a*) - c_o a*)/(1-gamma) and F(a*) >= (gamma (c_s+c_r) - c_o)/(gamma (c_s+c_r+c_w))."""
+    mu, Q, gamma = 4.0, 12, 0.9
+    cost = (2.0, 0.0, 6.0, 3.0, 0.5)
+    c_o, _, c_s, c_w, c_r = cost
+    inst = workloads.single_product(1, 2, Q, cost, workloads.poisson_pmf(mu, 40), gamma, FIFO)
+    ratio = (gamma * (c_s + c_r) - c_o) / (gamma * (c_s + c_r + c_w))
+    a_star = min(a for a in range(Q + 1) if stats.poisson.cdf(a, mu) >= ratio or a == Q)
+
+    def g(x):
+        over, under = poisson_loss(mu, x)
+        return -c_s * over - c_w * under + c_r * (mu - over)
+
+    M = (gamma * g(a_star) - c_o * a_star) / (1 - gamma)
+    P = oracle.Problem(inst)
+    res = P.vi_solve(tol=1e-11, max_iters=20000, stop_rule=1)
+    assert (res["policy"] == a_star).all()
+    want = np.array([g(x) + M for x in range(Q + 1)])
+    np.testing.assert_allclose(res["V"], want, rtol=1e-9, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# P2: brute force over all deterministic policies (unit-by-unit model)
+# ---------------------------------------------------------------------------
+
+BRUTE = [
+    dict(m=2, L=1, Q=2, issuing=FIFO, mu=1.2, dmax=4),
+    dict(m=3, L=1, Q=2, issuing=LIFO, mu=1.5, dmax=5),
+    dict(m=3, L=1, Q=2, issuing=FIFO, mu=2.0, dmax=6),
+    dict(m=2, L=2, Q=2, issuing=FIFO, mu=1.0, dmax=4),
+    dict(m=1, L=3, Q=2, issuing=LIFO, mu=1.4, dmax=5),
+]
+
+
+@pytest.mark.parametrize("case", BRUTE)
+def test_bruteforce_optimal_policy(case):
+    rng = np.random.default_rng(case["m"] * 7 + case["L"] + case["issuing"])
+    cost = tuple(rng.uniform(0.5, 8.0, 4)) + (float(rng.uniform(0, 3)),)
+    gamma = 0.9
+    inst = workloads.single_product(case["m"], case["L"], case["Q"], cost,
+                                    workloads.poisson_pmf(case["mu"], case["dmax"]), gamma,
+                                    case["issuing"])
+    S, A = inst.n_states, inst.n_actions
+    Pm, R = unit_model.dense_model(inst)
+    pols = unit_model.all_policies(S, A)
+    Vall = unit_model.policy_values(Pm, R, gamma, pols)
+    Vstar = Vall.max(axis=0)
+    # an optimal policy attains V* in every state at once
+    assert np.abs(Vall - Vstar).max(axis=1).min() < 1e-9
+
+    P = oracle.Problem(inst)
+    res = P.vi_solve(tol=1e-12, max_iters=5000, stop_rule=1)
+    np.testing.assert_allclose(res["V"], Vstar, rtol=1e-9, atol=1e-9)
+    Vpi = unit_model.policy_values(Pm, R, gamma, res["policy"].astype(np.int64)[None])[0]
+    np.testing.assert_allclose(Vpi, Vstar, rtol=1e-9, atol=1e-9)
+
+    # MacQueen bounds after a few sweeps (span-rule intermediate iterate)
+    for k in (1, 3, 6):
+        r = P.vi_solve(tol=0.0, max_iters=k, stop_rule=0)
+        lo = r["V"] + gamma / (1 - gamma) * r["dmin"]
+        hi = r["V"] + gamma / (1 - gamma) * r["dmax"]
+        assert (Vstar >= lo - 1e-9).all() and (Vstar <= hi + 1e-9).all()
+
+
+def test_bruteforce_two_products():
+    c1 = (0.5, 0.2, 1.0, 0.7, 1.0)
+    c2 = (0.4, 0.1, 0.5, 0.9, 1.2)
+    prods = [workloads.Product(2, 1, 1, c1, workloads.poisson_pmf(0.8, 3)),
+             workloads.Product(2, 1, 1, c2, workloads.poisson_pmf(1.1, 3))]
+    inst = workloads.Instance("b2", prods, gamma=0.85, issuing=FIFO, subst_rate=0.5)
+    S, A = inst.n_states, inst.n_actions
+    assert (S, A) == (4, 4)
+    Pm, R = unit_model.dense_model(inst)
+    np.testing.assert_allclose(Pm.sum(axis=2), 1.0, atol=1e-14)
+    pols = unit_model.all_policies(S, A)
+    Vall = unit_model.policy_values(Pm, R, inst.gamma, pols)
+    Vstar = Vall.max(axis=0)
+    res = oracle.Problem(inst).vi_solve(tol=1e-12, max_iters=5000, stop_rule=1)
+    np.testing.assert_allclose(res["V"], Vstar, rtol=1e-9, atol=1e-9)
+    Vpi = unit_model.policy_values(Pm, R, inst.gamma, res["policy"].astype(np.int64)[None])[0]
+    np.testing.assert_allclose(Vpi, Vstar, rtol=1e-9, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# P3: invariants
+# ---------------------------------------------------------------------------
+
+def test_values_non_increasing_in_iterations_for_cost_only():
+    inst = workloads.single_product(3, 2, 4, (3, 1, 5, 7, 0), workloads.poisson_pmf(2.0, 10), 0.95, FIFO)
+    P = oracle.Problem(inst)
+    prev = np.zeros(inst.n_states)
+    for k in range(1, 8):
+        V = P.vi_solve(tol=0.0, max_iters=k)["V"]
+        assert (V <= prev).all()
+        prev = V
+
+
+@pytest.mark.parametrize("issuing", [FIFO, LIFO])
+def test_value_monotone_in_stock(issuing):
+    pmf = workloads.poisson_pmf(2.0, 9)
+    base = dict(m=3, L=2, Q=3)
+    K = (base["m"] - 1) + (base["L"] - 1)
+    free = workloads.single_product(**base, cost=(2, 0, 6, 0, 0), pmf=pmf, gamma=0.9, issuing=issuing)
+    costly = workloads.single_product(**base, cost=(2, 1, 0, 3, 0), pmf=pmf, gamma=0.9, issuing=issuing)
+    Vf = oracle.Problem(free).vi_solve(tol=1e-12, max_iters=4000, stop_rule=1)["V"]
+    Vc = oracle.Problem(costly).vi_solve(tol=1e-12, max_iters=4000, stop_rule=1)["V"]
+    Q = base["Q"]
+    for s in range(free.n_states):
+        dig = unit_model.decode(s, Q, K)
+        for k in range(base["m"] - 1):         # stock digits only
+            if dig[k] < Q:
+                up = list(dig)
+                up[k] += 1
+                t = unit_model.encode(up, Q)
+                assert Vf[t] >= Vf[s] - 1e-9        # free holding/waste: more stock never hurts
+                assert Vc[t] <= Vc[s] + 1e-9        # no shortage cost: more stock never helps
+
+
+def test_encode_decode_roundtrip():
+    for Q, K in [(20, 5), (10, 7), (3, 4)]:
+        for s in np.random.default_rng(Q).integers(0, (Q + 1) ** K, 200):
+            dig = unit_model.decode(int(s), Q, K)
+            assert all(0 <= x <= Q for x in dig)
+            assert unit_model.encode(dig, Q) == s
+
+
+# ---------------------------------------------------------------------------
+# P4: gamma = 0 -> V_1 = max_a rbar(s, a)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("issuing", [FIFO, LIFO])
+def test_gamma_zero_is_myopic(issuing):
+    inst = workloads.single_product(3, 2, 3, (2.0, 1.5, 4.0, 3.0, 1.0), workloads.poisson_pmf(2.5, 8),
+                                    0.0, issuing)
+    Pm, R = unit_model.dense_model(inst)
+    res = oracle.Problem(inst).vi_solve(tol=0.0, max_iters=1)
+    np.testing.assert_allclose(res["V"], R.max(axis=0), rtol=1e-12, atol=1e-12)
+    assert (res["policy"] == R.argmax(axis=0)).all()
+
+
+# ---------------------------------------------------------------------------
+# P5: rollouts
+# ---------------------------------------------------------------------------
+
+def test_rollout_newsvendor_mean_and_first_step():
+    mu, Q = 5.0, 20
+    cost = (3.0, 1.0, 5.0, 7.0, 0.0)
+    inst = workloads.single_product(1, 1, Q, cost, workloads.poisson_pmf(mu, 25), 1.0, FIFO)
+    a_star = 3
+    policy = np.array([a_star], np.uint8)
+    n, H = 512, 365
+    out = oracle.Problem(inst).simulate(policy, n, H, seed=0, with_traj=True)
+    over, under = poisson_loss(mu, a_star)
+    rbar = -3 * a_star - 5 * over - 7 * under
+    per_period = out["returns"] / H
+    se = per_period.std(ddof=1) / math.sqrt(n)
+    assert abs(per_period.mean() - rbar) < 4 * se + 1e-3
+    # first period of rollout 0 with seed 0: Philox(0,0,0,0 ; 0,0) word 0 = 0x6627e8d5,
+    # i.e. u = 0.39905..; Poisson(5): F(3)=0.265 < u <= F(4)=0.440 -> demand 4.
+    assert out["demand"][0, 0] == 4
+    assert out["traj"][0, 0] == 0
+    # with demand 4 and order 3: issued 3, shortage 1, nothing left -> r = -9 - 5 = -14
+    single = oracle.Problem(inst).simulate(policy, 1, 1, seed=0)
+    assert single["returns"][0] == -14.0
+    k = single["kpis"][0]
+    assert k[0] == 75.0 and k[1] == 0.0 and k[2] == 0.0
+
+
+def test_ties_resolve_to_smallest_action():
+    """Free ordering and free waste with Q > Dmax: every a >= Dmax covers all demand,
+    so these actions tie exactly and the first argmax (a = Dmax) must be chosen."""
+    dmax = 6
+    inst = workloads.single_product(1, 1, 10, (0.0, 0.0, 4.0, 0.0, 0.0),
+                                    workloads.poisson_pmf(3.0, dmax), 0.9, FIFO)
+    res = oracle.Problem(inst).vi_solve(tol=1e-12, max_iters=3000, stop_rule=1)
+    assert res["policy"][0] == dmax
+    assert res["V"][0] == 0.0
+    zero = workloads.single_product(2, 2, 3, (0, 0, 0, 0, 0), workloads.poisson_pmf(1.0, 4), 0.9, LIFO)
+    r = oracle.Problem(zero).vi_solve(tol=1e-12, max_iters=10)
+    assert (r["policy"] == 0).all() and (r["V"] == 0).all()

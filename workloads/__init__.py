@@ -1,0 +1,232 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+This module only *generates inputs*: demand pmfs (truncated, tail mass folded
+into the last support point), cost vectors drawn from a seeded generator, and
+the request stream of the serving mix.  It holds none of the value-iteration
+arithmetic, so both the CUDA path and the CPU oracle may take inputs from it
+without sharing any of the method's code.
+
+Demand distributions follow the paper's discretise-and-fold rule (Scenario A,
+appendix "Scenario description": the mass above the truncation point is put
+on D_max) applied to Poisson and negative-binomial demand.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional, Sequence
+
+import numpy as np
+from scipy import stats
+
+FIFO, LIFO = 0, 1
+
+# cost vector layout everywhere: (order c_o, holding c_h, shortage c_s, waste c_w, revenue c_r)
+COST_FIELDS = ("order", "holding", "shortage", "waste", "revenue")
+
+
+def folded_pmf(dist, dmax: int) -> np.ndarray:
+    """pmf on {0..dmax}: P(D=d) for d < dmax and P(D >= dmax) on dmax."""
+    d = np.arange(dmax, dtype=np.float64)
+    p = np.empty(dmax + 1, dtype=np.float64)
+    p[:dmax] = dist.pmf(d)
+    p[dmax] = dist.sf(dmax - 1)  # P(D >= dmax)
+    # renormalise the last few ulps so sum == 1 up to rounding of the sum itself
+    p[dmax] += 1.0 - p.sum()
+    if p[dmax] < 0.0:
+        p[dmax] = 0.0
+    return p
+
+
+def poisson_pmf(mean: float, dmax: int) -> np.ndarray:
+    return folded_pmf(stats.poisson(mean), dmax)
+
+
+def negbin_pmf(mean: float, var: float, dmax: int) -> np.ndarray:
+    """Negative binomial with the given mean and variance (var > mean):
+    n = mean^2/(var-mean) successes, success probability p = mean/var."""
+    n = mean * mean / (var - mean)
+    p = mean / var
+    return folded_pmf(stats.nbinom(n, p), dmax)
+
+
+@dataclasses.dataclass
+class Product:
+    m: int                      # maximum useful life (periods)
+    L: int                      # lead time (periods)
+    Q: int                      # order cap, actions 0..Q, each age slot 0..Q
+    cost: Sequence[float]       # (c_o, c_h, c_s, c_w, c_r)
+    pmf: np.ndarray             # demand pmf on {0..dmax}
+
+    @property
+    def dmax(self) -> int:
+        return len(self.pmf) - 1
+
+    @property
+    def n_digits(self) -> int:
+        return (self.m - 1) + (self.L - 1)
+
+    @property
+    def n_states(self) -> int:
+        return (self.Q + 1) ** self.n_digits
+
+
+@dataclasses.dataclass
+class Instance:
+    """One value-iteration problem instance (one or two products)."""
+    name: str
+    products: List[Product]
+    gamma: float
+    issuing: int = FIFO
+    subst_rate: float = 0.0      # share of product-1 shortfall willing to take product 2
+    tol: float = 1e-4
+    max_iters: int = 100_000
+    precision: str = "fp32"      # "fp64" | "fp32" | "fp32_kahan"
+
+    @property
+    def n_states(self) -> int:
+        n = 1
+        for p in self.products:
+            n *= p.n_states
+        return n
+
+    @property
+    def n_actions(self) -> int:
+        n = 1
+        for p in self.products:
+            n *= p.Q + 1
+        return n
+
+    @property
+    def n_outcomes(self) -> int:
+        n = 1
+        for p in self.products:
+            n *= p.dmax + 1
+        return n
+
+    @property
+    def updates_per_sweep(self) -> int:
+        """Nominal |S|*|A|*|Omega| (state-action-demand updates of one sweep)."""
+        return self.n_states * self.n_actions * self.n_outcomes
+
+
+# ---------------------------------------------------------------------------
+# the five workloads
+# ---------------------------------------------------------------------------
+
+PAPER_A_COSTS = (3.0, 1.0, 5.0, 7.0, 0.0)   # C_v=3, C_h=1, C_s=5, C_w=7 (Scenario A settings)
+
+
+def single_product(m, L, Q, cost, pmf, gamma, issuing=FIFO, name="custom", **kw) -> Instance:
+    return Instance(name=name, products=[Product(m, L, Q, tuple(float(c) for c in cost),
+                                                 np.asarray(pmf, np.float64))],
+                    gamma=gamma, issuing=issuing, **kw)
+
+
+def config1() -> Instance:
+    """m=3, L=1, Q=20 (441 states), Poisson(5) folded at 25, FIFO, costs (3,1,5,7), gamma .99."""
+    return single_product(3, 1, 20, PAPER_A_COSTS, poisson_pmf(5.0, 25), 0.99, FIFO,
+                          name="cfg1_m3L1Q20_fifo", precision="fp64")
+
+
+def uniform_costs(rng: np.random.Generator) -> tuple:
+    c = rng.uniform(1.0, 10.0, size=4)
+    return (float(c[0]), float(c[1]), float(c[2]), float(c[3]), 0.0)
+
+
+def config2(seed: int = 2) -> Instance:
+    """m=5, L=2, Q=20 (21^5 = 4,084,101 states), NB(mean 8, var 20) folded at 40, FIFO,
+    costs U[1,10] from a PCG64 stream seeded with `seed`, gamma .99, plain FP32."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return single_product(5, 2, 20, uniform_costs(rng), negbin_pmf(8.0, 20.0, 40), 0.99, FIFO,
+                          name="cfg2_m5L2Q20_nb_fifo", precision="fp32")
+
+
+def config3(Q: int = 14) -> Instance:
+    """Two substitutable products, each m=3, L=1, Q=14 (15^4 = 50,625 states, 225 joint
+    actions), Poisson(4) and Poisson(6) folded at 20, half of product-1 shortfall accepts
+    product 2, order cost 0.5 and revenue 1.0 per unit, gamma .99, FP32 with Kahan sums."""
+    c = (0.5, 0.0, 0.0, 0.0, 1.0)
+    p1 = Product(3, 1, Q, c, poisson_pmf(4.0, 20))
+    p2 = Product(3, 1, Q, c, poisson_pmf(6.0, 20))
+    return Instance(name=f"cfg3_2prod_m3L1Q{Q}_subst", products=[p1, p2], gamma=0.99,
+                    issuing=FIFO, subst_rate=0.5, precision="fp32_kahan")
+
+
+def config4() -> Instance:
+    """m=8, L=1, Q=10 (11^7 = 19,487,171 states), Poisson(4) folded at 15, LIFO,
+    costs (3,1,5,7), gamma .95, FP32."""
+    return single_product(8, 1, 10, PAPER_A_COSTS, poisson_pmf(4.0, 15), 0.95, LIFO,
+                          name="cfg4_m8L1Q10_lifo", precision="fp32")
+
+
+CONFIG4_ROLLOUTS = dict(n_rollouts=4096, horizon=365, seed=4)
+
+
+@dataclasses.dataclass
+class Request:
+    arrival_s: float
+    instance: Instance
+
+
+def serving_mix(n_requests: int = 512, seed: int = 5, rate_per_s: float = 200.0,
+                max_states: int = 21 ** 5) -> List[Request]:
+    """Serving workload: independent single-product instances arriving as a Poisson stream.
+
+    m ~ U{2..6}, L ~ U{1,2,3}, Q ~ U{8..20}, redrawn until (Q+1)^(m+L-2) <= max_states;
+    demand Poisson(mu), mu ~ U[2,10], folded at floor(3 mu + 5); four costs U[1,10];
+    gamma ~ U{0.9, 0.95, 0.99}; FIFO.  Exponential inter-arrival gaps of mean 1/rate.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for i in range(n_requests):
+        while True:
+            m = int(rng.integers(2, 7))
+            L = int(rng.integers(1, 4))
+            Q = int(rng.integers(8, 21))
+            if (Q + 1) ** (m + L - 2) <= max_states:
+                break
+        mu = float(rng.uniform(2.0, 10.0))
+        dmax = int(np.floor(3.0 * mu + 5.0))
+        cost = uniform_costs(rng)
+        gamma = float(rng.choice([0.9, 0.95, 0.99]))
+        t += float(rng.exponential(1.0 / rate_per_s))
+        inst = single_product(m, L, Q, cost, poisson_pmf(mu, dmax), gamma, FIFO,
+                              name=f"req{i}_m{m}L{L}Q{Q}", precision="fp32")
+        out.append(Request(arrival_s=t, instance=inst))
+    return out
+
+
+def random_small_instance(rng: np.random.Generator, max_states: int = 400,
+                          two_product: bool = False) -> Instance:
+    """A random tiny instance (for exhaustive parity sweeps)."""
+    if two_product:
+        while True:
+            Q1, Q2 = int(rng.integers(1, 4)), int(rng.integers(1, 4))
+            m1, m2 = int(rng.integers(1, 4)), int(rng.integers(1, 4))
+            n = (Q1 + 1) ** (m1 - 1) * (Q2 + 1) ** (m2 - 1)
+            if n <= max_states:
+                break
+        mus = rng.uniform(0.5, 4.0, size=2)
+        c1 = (float(rng.uniform(0, 2)), float(rng.uniform(0, 1)), float(rng.uniform(0, 3)),
+              float(rng.uniform(0, 3)), float(rng.uniform(0, 3)))
+        c2 = (float(rng.uniform(0, 2)), float(rng.uniform(0, 1)), float(rng.uniform(0, 3)),
+              float(rng.uniform(0, 3)), float(rng.uniform(0, 3)))
+        p1 = Product(m1, 1, Q1, c1, poisson_pmf(mus[0], int(rng.integers(1, 9))))
+        p2 = Product(m2, 1, Q2, c2, poisson_pmf(mus[1], int(rng.integers(1, 9))))
+        return Instance(name="rand2", products=[p1, p2], gamma=float(rng.uniform(0.5, 0.95)),
+                        issuing=int(rng.integers(0, 2)), subst_rate=float(rng.uniform(0, 1)))
+    while True:
+        m = int(rng.integers(1, 5))
+        L = int(rng.integers(1, 4))
+        Q = int(rng.integers(0, 7))
+        if (Q + 1) ** (m + L - 2) <= max_states:
+            break
+    mu = float(rng.uniform(0.3, 6.0))
+    dmax = int(rng.integers(0, 14))
+    cost = tuple(float(c) for c in rng.uniform(0.0, 10.0, size=5))
+    return single_product(m, L, Q, cost, poisson_pmf(mu, dmax), float(rng.uniform(0.3, 0.99)),
+                          int(rng.integers(0, 2)), name="rand1")
+
+
+CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4}
