@@ -1,0 +1,351 @@
+"""Benchmark of the value-iteration hot path on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload cfg2|cfg4|cfg1|cfg3] [--impl reference]
+
+A step is one complete solve of the workload through the C ABI: synchronous
+FP32 Bellman sweeps (decode, FIFO/LIFO issue, gathers, max/argmax, FP64 span
+reduction and device-side stopping test inside a CUDA-graph while loop) until
+the span of V_i - V_{i-1} is below 1e-4, then the extraction sweep writing the
+policy.  The metric is nominal Bellman state-action-demand updates per second:
+|S| |A| |Omega| x sweeps / solve time.  Default workload: m=5, L=2, Q=20
+(21^5 = 4,084,101 states), negative-binomial demand (mean 8, var 20) folded at
+40, FIFO, costs U[1,10] seeded, gamma 0.99.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (one Bellman update of a sample of states per
+step) and reports the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "bellman_state_action_demand_updates_per_s"
+UNIT = "updates/s"
+WORKLOADS = {
+    "cfg1": workloads.config1,
+    "cfg2": workloads.config2,
+    "cfg3": workloads.config3,
+    "cfg4": workloads.config4,
+}
+TOL = 1e-4
+MAX_ITERS = 100_000
+L2_BYTES = 126 * 1024 * 1024
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return dict(hbm_gbs=d["hbm_gbs"], sm_max_mhz=d.get("sm_max_mhz", 2032.0), source="measured")
+    return dict(hbm_gbs=6400.0, sm_max_mhz=2032.0, source="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sms)) if sms else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    import torch.distributed as dist
+    rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return rank, world, local
+
+
+def barrier_sync(world):
+    import torch
+    import torch.distributed as dist
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# the oracle on host cores (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_rate(inst, seconds_target: float, seed: int = 0):
+    """Updates/s of the FP64 oracle: one Bellman update of a random sample of states
+    (OpenMP over all host cores), sized to take about `seconds_target`."""
+    import oracle
+    P = oracle.Problem(inst)
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    V = rng.uniform(-100.0, 0.0, inst.n_states) if inst.n_states <= 50_000_000 else None
+    per_state = inst.n_actions * inst.n_outcomes
+    n = 64
+    while True:
+        states = rng.integers(0, inst.n_states, n)
+        t0 = time.perf_counter()
+        P.backup_states(V, states, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if dt >= seconds_target or n >= inst.n_states:
+            break
+        n = int(min(inst.n_states, max(n * 2, n * seconds_target / max(dt, 1e-6) * 1.1)))
+    return dict(value=n * per_state / dt, unit=UNIT, cores=cores, kind="oracle",
+                sample=f"one FP64 Bellman update of {n} random states of {inst.name} "
+                       f"({n * per_state:.3g} nominal updates, {dt:.1f} s, {cores} OpenMP threads)",
+                seconds=dt)
+
+
+def run_reference(args):
+    import torch  # noqa: F401  (rank/world plumbing only)
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    inst = WORKLOADS[args.workload]()
+    vals, secs = [], []
+    per_step = max(1.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample_rate(inst, per_step, seed=i)
+        if i >= args.warmup:
+            vals.append(r["value"])
+            secs.append(r["seconds"])
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * float(np.mean(secs)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": inst.name, "states": inst.n_states, "actions": inst.n_actions,
+                   "outcomes": inst.n_outcomes, "parallelism": "host OpenMP"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                         "sample": r["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# the CUDA path
+# ---------------------------------------------------------------------------
+
+def kernel_flops_per_launch(inst, kernel_kind: str) -> dict:
+    """Algorithmic work of one sweep launch of the factorised kernel."""
+    p = inst.products[0]
+    G = p.Q + 1
+    nR = inst.n_states // G
+    A = p.Q + 1
+    D = p.dmax + 1
+    if inst.issuing == workloads.FIFO:
+        nch = (p.dmax + G) // G
+        fma = nR * A * (nch * G * G + G)
+    else:
+        fma = nR * A * (D + G)
+    return {"fma": fma, "flops": 2 * fma, "bytes": inst.n_states * 8}
+
+
+def run_native(args):
+    import torch
+    import paper_2303_10672_b300 as vi
+
+    rank, world, local = dist_setup(args.gpus)
+    inst = WORKLOADS[args.workload]()
+    p = inst.products[0]
+    prec = {"fp32": vi.VI_PREC_FP32, "fp32_kahan": vi.VI_PREC_FP32_KAHAN, "fp64": vi.VI_PREC_FP64}[inst.precision]
+    prods = [dict(m=q.m, L=q.L, Q=q.Q, cost=q.cost, pmf=q.pmf) for q in inst.products]
+    desc, keep = vi.make_desc(prods, inst.gamma, inst.issuing, prec, vi.VI_STOP_SPAN, inst.subst_rate)
+    h = vi.vi_problem_create_desc(desc)
+    sizes = vi.vi_problem_sizes(h)
+    n = sizes["n_states"]
+    vdtype = torch.float64 if sizes["value_bytes"] == 8 else torch.float32
+    V = torch.empty(n, dtype=vdtype, device="cuda")
+    pol = torch.empty(n, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    nominal = float(n) * sizes["n_actions"] * sizes["n_outcomes"]
+
+    for _ in range(args.warmup):
+        vi.vi_solve(h, TOL, MAX_ITERS, V, pol)
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier_sync(world)
+    step_ms, iters = [], []
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)   # evict L2 between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = vi.vi_solve(h, TOL, MAX_ITERS, V, pol, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        iters.append(info["iters"])
+    barrier_sync(world)
+    wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    dev_s = sum(step_ms) / 1000.0
+    dev_s_max = max_over_ranks(dev_s, world)
+    updates = nominal * sum(iters)
+    value = updates * world / dev_s_max
+
+    # dominant kernel: one sweep launch (same kernel, same grid) timed with events
+    V2 = torch.empty_like(V)
+    reps = 20
+    vi.vi_backup(h, V, V2, None, stream=stream, stats=False)
+    flush.fill_(1.0)
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for i in range(reps):
+        if i % 2 == 0:
+            vi.vi_backup(h, V, V2, None, stream=stream, stats=False)
+        else:
+            vi.vi_backup(h, V2, V, None, stream=stream, stats=False)
+    k1.record(stream)
+    k1.synchronize()
+    k_ms = k0.elapsed_time(k1) / reps
+    work = kernel_flops_per_launch(inst, "group")
+    pk = peaks()
+    sm_mhz = clocks.get("sm_mhz") or pk["sm_max_mhz"]
+    fp32_peak_tflops = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved_tflops = work["flops"] / (k_ms * 1e-3) / 1e12
+    roofline = {
+        "bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+        "frac": achieved_tflops / fp32_peak_tflops, "traffic": None,
+        "kernel": "sweep_group_kernel", "kernel_ms": k_ms,
+        "peak_basis": f"148 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock sampled)",
+        "hbm_compulsory_GBs": work["bytes"] / (k_ms * 1e-3) / 1e9, "hbm_peak_GBs": pk["hbm_gbs"],
+    }
+
+    # end to end through the public API with host buffers: create (tables H2D),
+    # solve, V + policy D2H, destroy
+    e2e_steps = max(1, min(args.steps, 5))
+    Vh = torch.empty(n, dtype=vdtype).pin_memory().numpy()
+    ph = torch.empty(n, dtype=torch.uint8).pin_memory().numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(e2e_steps):
+        h2 = vi.vi_problem_create_desc(desc)
+        inf2 = vi.vi_solve_host(h2, TOL, MAX_ITERS, Vh, ph)
+        vi.vi_problem_destroy(h2)
+        e2e_iters += inf2["iters"]
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = nominal * e2e_iters * world / e2e_s
+    h2d = sum(len(q.pmf) * 8 + 5 * 8 for q in inst.products)
+    d2h = n * sizes["value_bytes"] + n
+
+    out = None
+    if rank == 0:
+        cpu = oracle_sample_rate(inst, args.cpu_seconds) if args.cpu_seconds > 0 else None
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * dev_s_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 span/offset)", "data": "synthetic",
+            "config": {"workload": inst.name, "states": n, "actions": sizes["n_actions"],
+                       "outcomes": sizes["n_outcomes"], "sweeps_per_solve": iters[-1], "tol": TOL,
+                       "stop_rule": "span", "l2": "flushed between steps (2x L2 write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "gpu_launches": int(sum(iters) + 2 * args.steps),
+            "clocks": clocks,
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps, "includes": "vi_problem_create + vi_solve_host + vi_problem_destroy"},
+            "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind",
+                                                                           "sample")},
+            "wall_s": wall,
+        }
+        print(json.dumps(out))
+    vi.vi_problem_destroy(h)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle sample length (0 = skip)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * vi.h -- C ABI of the B300 value-iteration library for perishable-inventory
+ * MDPs (Farrington, Li, Wong, Utley, "Going faster to see further:
+ * GPU-accelerated value iteration and simulation for perishable inventory
+ * control using JAX", 2023).
+ *
+ * Model.  A single-product instance (m, L, Q, costs, demand pmf, gamma,
+ * issuing rule) has states made of the on-hand stock X_1..X_{m-1} split by
+ * remaining useful life (X_1 expires at the end of the current period) and
+ * the orders in transit P_1..P_{L-1} (P_1 arrives before this period's
+ * demand; P_{L-1} is the order placed one period ago).  This is the state of
+ * the paper's Scenario A (Appendix A, "Scenario description") observed at the
+ * decision epoch, before the arriving units join the stock.  The order a in
+ * 0..Q is placed; the arrival u (= P_1 if L >= 2, else a itself) joins as the
+ * freshest slot; demand d is issued FIFO (Eq. demoor:fifo) or LIFO
+ * (Eq. demoor:lifo); what is left of the oldest slot expires; the rest ages
+ * by one period.  Reward (Eq. demoor:reward plus the revenue term of the
+ * Scenario B reward):
+ *   r = -c_o a - c_h carried - c_s short - c_w wasted + c_r issued.
+ * Two products (Scenario B): a shortfall of product 1 is offered product 2,
+ * each short unit accepting with probability subst_rate (binomial); product 2
+ * serves its own demand first.
+ *
+ * State index: digit k has weight (Q+1)^k; digits 0..m-2 hold X_1..X_{m-1},
+ * digits m-1..m+L-3 hold P_1..P_{L-1}; |S| = (Q+1)^((m-1)+(L-1)).  Two
+ * products: s = s_1 + |S_1| s_2 and joint action a = a_1 (Q_2+1) + a_2.
+ *
+ * Conventions.
+ *  - Every function returns vi_status and never aborts the process.
+ *  - Pointers documented "device" are CUDA device pointers owned by the
+ *    caller; "host" pointers are ordinary host memory owned by the caller.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - All scratch (ping-pong value buffer, tables, reduction slots, graphs)
+ *    belongs to the handle and is released by vi_problem_destroy.
+ *  - A handle is not thread-safe; use one handle per host thread.  The solve
+ *    server is thread-safe.
+ *  - vi_last_error() describes the most recent failure on the calling thread.
+ */
+#ifndef VI_B300_VI_H
+#define VI_B300_VI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vi_problem *vi_handle;
+typedef struct vi_server_s *vi_server;
+
+typedef enum {
+    VI_OK = 0,
+    VI_EINVAL = 1,          /* an argument is out of range (nothing was changed) */
+    VI_ENOMEM = 2,          /* device or host allocation failed */
+    VI_ENOTCONVERGED = 3,   /* max_iters reached; V and policy hold the last iterate */
+    VI_ETIMEOUT = 4,        /* a bounded device-side wait ran out */
+    VI_EBUSY = 5,           /* server: request does not fit the memory budget yet */
+    VI_ECUDA = 6,           /* a CUDA runtime call failed (see vi_last_error) */
+    VI_ECANCELLED = 7       /* work cancelled from the host */
+} vi_status;
+
+enum { VI_FIFO = 0, VI_LIFO = 1 };
+/* stopping tests: span of V_i - V_{i-1} (Scenario B convergence test) or its
+ * sup-norm (Scenario A convergence test); both strict "< tol". */
+enum { VI_STOP_SPAN = 0, VI_STOP_SUPNORM = 1 };
+/* value arithmetic: FP32 values relative to an FP64 offset, FP32 with
+ * compensated (Kahan) summation over outcomes, or FP64 throughout. */
+enum { VI_PREC_FP32 = 0, VI_PREC_FP32_KAHAN = 1, VI_PREC_FP64 = 2 };
+
+/* vi_solve flags */
+enum {
+    VI_FLAG_WARM_START = 1,    /* V holds the starting iterate (offset in info->offset) */
+    VI_FLAG_NO_GRAPH = 2,      /* host-driven sweep loop instead of the CUDA-graph loop */
+    VI_FLAG_POLICY_EVAL = 4    /* after extraction, evaluate the policy in FP64 (see info) */
+};
+
+/* Full problem description.  cost[k] = {c_o order, c_h holding, c_s shortage,
+ * c_w waste, c_r revenue} per unit for product k (all >= 0).  pmf[k] = host
+ * array of dmax[k]+1 probabilities summing to 1 (tail mass already folded into
+ * the last entry, as in the paper's truncated demand).  L[k] must be 1 for two
+ * products. */
+typedef struct {
+    int n_products;          /* 1 or 2 */
+    int m[2], L[2], Q[2];
+    double cost[2][5];
+    const double *pmf[2];    /* host */
+    int dmax[2];
+    double subst_rate;       /* product-1 shortfall accepting product 2, in [0,1] */
+    double gamma;            /* discount, 0 < gamma <= 1 */
+    int issuing;             /* VI_FIFO or VI_LIFO */
+    int precision;           /* VI_PREC_* */
+    int stop_rule;           /* VI_STOP_* */
+} vi_problem_desc;
+
+typedef struct {
+    int iters;               /* Bellman sweeps applied (V_iters is returned) */
+    int status;              /* VI_OK or VI_ENOTCONVERGED */
+    double crit;             /* stopping criterion of the last sweep */
+    double dmax, dmin;       /* max / min over s of V_iters(s) - V_{iters-1}(s) (absolute) */
+    double offset;           /* FP64 offset b: V_abs(s) = offset + V[s] (FP32 paths; 0 for FP64) */
+    double wall_ms;          /* device time of the solve (CUDA events), sweeps + extraction */
+    double updates_per_s;    /* nominal |S||A||Omega| x iters / wall time */
+    int pe_iters;            /* FP64 policy-evaluation sweeps (VI_FLAG_POLICY_EVAL) */
+    double pe_delta;         /* last sup-norm change of the policy evaluation */
+    double pe_gap;           /* max_s |V_pe(s) - V_abs(s)| after evaluation */
+} vi_solve_info;
+
+/* Create a single-product problem (FP32 values, span stopping test).
+ * Defines: state space and transition of Scenario A (Appendix A, state
+ * definition, Eq. demoor:fifo / demoor:lifo, Eq. demoor:reward).
+ * cost: host double[5]; pmf: host double[dmax+1].  Copies everything it needs
+ * to the current CUDA device.  Errors: VI_EINVAL for m < 1, L < 1, Q < 0,
+ * Q+1 > 256 (policy is uint8), |S| >= 2^32, dmax < 0 or > 4095, pmf entries
+ * < 0 or not summing to 1 within 1e-9, gamma outside (0, 1], a negative cost
+ * or issuing not FIFO/LIFO; VI_ENOMEM / VI_ECUDA on allocation failure. */
+vi_status vi_problem_create(int m, int L, int Q, const double cost[5], const double *pmf,
+                            int dmax, double gamma, int issuing, vi_handle *out);
+
+/* Create a problem from a full description (one or two products, precision,
+ * stopping rule).  Same errors as vi_problem_create; two products also need
+ * L = 1, |A| = (Q_1+1)(Q_2+1) <= 256 and subst_rate in [0,1]. */
+vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_handle *out);
+
+/* Release every device and host resource of the handle.  NULL is accepted. */
+vi_status vi_problem_destroy(vi_handle h);
+
+/* Sizes: |S|, |A|, nominal |Omega| and bytes per stored value (4 or 8). */
+vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
+                           int *n_outcomes, int *value_bytes);
+
+/* Per-handle options (no counterpart in the paper; tuning and test hooks).
+ * VI_OPT_KERNEL: which sweep kernel runs -- VI_KERNEL_AUTO (factorised kernel
+ * whenever the instance allows it), VI_KERNEL_GENERIC (one thread per state)
+ * or VI_KERNEL_GROUP (factorised; VI_EINVAL if the instance does not allow it:
+ * it needs one FP32 product with 2 <= Q+1 <= 24 and at least one state digit).
+ * VI_OPT_PE_MAX_ITERS: sweep cap of the FP64 policy evaluation in vi_solve. */
+enum { VI_OPT_KERNEL = 1, VI_OPT_PE_MAX_ITERS = 2 };
+enum { VI_KERNEL_AUTO = 0, VI_KERNEL_GENERIC = 1, VI_KERNEL_GROUP = 2 };
+vi_status vi_problem_set_option(vi_handle h, int option, int value);
+
+/* Synchronous value iteration (Eq. valueiterationdetupdate, Algorithm 1) from
+ * V_0 = 0 (or the warm start), stopping at the first i with the stopping
+ * criterion < tol, or at max_iters; then one extraction sweep writes the
+ * first argmax policy from V_i (Eq. valueiterationdetpolicy, Algorithm 1).
+ * V: device float[|S|] (FP32 paths; the FP64 offset is info->offset) or
+ * double[|S|] (VI_PREC_FP64), in/out.  policy: device uint8[|S|] or NULL.
+ * info: host, out (and in: offset when VI_FLAG_WARM_START).  Blocks until the
+ * solve is done.  Returns VI_OK, VI_ENOTCONVERGED (V/policy hold the last
+ * iterate), VI_EINVAL (max_iters < 0, tol < 0, V NULL) or VI_ECUDA. */
+vi_status vi_solve(vi_handle h, double tol, int max_iters, void *V, uint8_t *policy,
+                   void *stream, int flags, vi_solve_info *info);
+
+/* vi_solve on host buffers: copies the warm start (if any) host->device,
+ * solves, and copies V and policy device->host.  V_host: host float[|S|] or
+ * double[|S|]; policy_host: host uint8[|S|] or NULL.  Device staging buffers
+ * are owned by the handle (allocated on first use). */
+vi_status vi_solve_host(vi_handle h, double tol, int max_iters, void *V_host,
+                        uint8_t *policy_host, int flags, vi_solve_info *info);
+
+/* One Bellman sweep without renormalisation: V_out(s) = max_a [rbar(s,a) +
+ * gamma sum_omega P(omega) V_in(s'_omega)] and policy(s) = first argmax
+ * (Eq. valueiterationdetupdate).  If V_in holds V_abs - b then V_out holds
+ * V_abs' - gamma b.  V_in/V_out: device float or double [|S|] (must differ);
+ * policy: device uint8[|S|] or NULL; dstats: host double[2] or NULL, receives
+ * max and min of V_out - V_in.  Synchronises the stream when dstats != NULL. */
+vi_status vi_backup(vi_handle h, const void *V_in, void *V_out, uint8_t *policy,
+                    void *stream, double *dstats);
+
+/* Evaluate a fixed policy in FP64 (the paper's double-precision arithmetic,
+ * Methods "Value iteration"): V <- r_pi + gamma P_pi V until the sup-norm
+ * change is < tol or max_iters sweeps.  V: device double[|S|], in (start) /
+ * out.  policy: device uint8[|S|].  iters / delta: host out (may be NULL).
+ * Returns VI_OK or VI_ENOTCONVERGED. */
+vi_status vi_policy_eval(vi_handle h, const uint8_t *policy, double *V, double tol,
+                         int max_iters, void *stream, int *iters, double *delta);
+
+/* Next-state indices T(s, a, omega) of the listed states, computed with the
+ * same incremental index arithmetic as the sweep kernels (Eq. demoor:fifo /
+ * demoor:lifo).  states: device uint32[n].  out: device uint32, single product
+ * n x |A| x (dmax+1) laid out [i][a][d]; two products n x |A| x (dmax1+1) x
+ * (dmax1+dmax2+1) laid out [i][a][d1][z] where z = units of demand facing
+ * product 2 (own demand plus accepted substitutes). */
+vi_status vi_next_states(vi_handle h, const uint32_t *states, int n, uint32_t *out, void *stream);
+
+/* Policy rollouts (the paper's simulators, Methods "Simulation of the Markov
+ * decision processes"): n_rollouts independent runs from the all-zero state;
+ * period t of rollout r draws Philox4x32-10 with counter (t, r, 0, 0) and key
+ * (seed low 32 bits, seed high 32 bits); word 0 is turned into product-1
+ * demand by the integer inverse CDF (smallest d with word < floor(2^32 CDF(d)),
+ * CDF summed in ascending order in FP64), word 1 into product-2 demand, and
+ * the popcount of the low `shortfall` bits of word 2 gives the accepted
+ * substitutions (two products need subst_rate = 1/2).  The first `warmup`
+ * periods are simulated but not scored.  policy: device uint8[|S|];
+ * returns: device double[n] = sum_t gamma^t r_t (FP64, in period order);
+ * kpis: device double[3n] or NULL = {service %, wastage %, mean units carried};
+ * traj: device int32[n x horizon] or NULL = state before each scored decision. */
+vi_status vi_simulate(vi_handle h, const uint8_t *policy, int n_rollouts, int horizon,
+                      int warmup, uint64_t seed, double *returns, double *kpis,
+                      int32_t *traj, void *stream);
+
+const char *vi_status_string(vi_status s);
+const char *vi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VI_B300_VI_H */

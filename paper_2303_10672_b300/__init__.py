@@ -1,0 +1,272 @@
+"""Python binding of libvi_b300.so (the C ABI in include/vi.h).
+
+Argument marshalling only: every step of value iteration, policy evaluation and
+simulation runs in the library's CUDA kernels.  Device buffers are passed as
+torch tensors (or raw integer addresses), streams as torch.cuda.Stream (or raw
+cudaStream_t integers).  If the shared library is missing or cannot be loaded
+the import of the binding fails -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvi_b300.so")
+
+VI_OK, VI_EINVAL, VI_ENOMEM, VI_ENOTCONVERGED, VI_ETIMEOUT, VI_EBUSY, VI_ECUDA, VI_ECANCELLED = range(8)
+VI_FIFO, VI_LIFO = 0, 1
+VI_STOP_SPAN, VI_STOP_SUPNORM = 0, 1
+VI_PREC_FP32, VI_PREC_FP32_KAHAN, VI_PREC_FP64 = 0, 1, 2
+VI_FLAG_WARM_START, VI_FLAG_NO_GRAPH, VI_FLAG_POLICY_EVAL = 1, 2, 4
+VI_OPT_KERNEL, VI_OPT_PE_MAX_ITERS = 1, 2
+VI_KERNEL_AUTO, VI_KERNEL_GENERIC, VI_KERNEL_GROUP = 0, 1, 2
+
+PRECISIONS = {"fp32": VI_PREC_FP32, "fp32_kahan": VI_PREC_FP32_KAHAN, "fp64": VI_PREC_FP64}
+
+
+class ViError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {status_name(status)} ({message})")
+        self.status = status
+
+
+class vi_problem_desc(C.Structure):
+    _fields_ = [
+        ("n_products", C.c_int),
+        ("m", C.c_int * 2), ("L", C.c_int * 2), ("Q", C.c_int * 2),
+        ("cost", (C.c_double * 5) * 2),
+        ("pmf", C.POINTER(C.c_double) * 2),
+        ("dmax", C.c_int * 2),
+        ("subst_rate", C.c_double),
+        ("gamma", C.c_double),
+        ("issuing", C.c_int),
+        ("precision", C.c_int),
+        ("stop_rule", C.c_int),
+    ]
+
+
+class vi_solve_info(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int), ("status", C.c_int), ("crit", C.c_double),
+        ("dmax", C.c_double), ("dmin", C.c_double), ("offset", C.c_double),
+        ("wall_ms", C.c_double), ("updates_per_s", C.c_double),
+        ("pe_iters", C.c_int), ("pe_delta", C.c_double), ("pe_gap", C.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libvi_b300.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing; build it with `python -m paper_2303_10672_b300.build`")
+    L = C.CDLL(LIB_PATH)
+    vp, u8p = C.c_void_p, C.c_void_p
+    H = C.c_void_p
+    sigs = {
+        "vi_problem_create": ([C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                               C.c_int, C.c_double, C.c_int, C.POINTER(H)], C.c_int),
+        "vi_problem_create_desc": ([C.POINTER(vi_problem_desc), C.POINTER(H)], C.c_int),
+        "vi_problem_destroy": ([H], C.c_int),
+        "vi_problem_sizes": ([H, C.POINTER(C.c_uint64), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                              C.POINTER(C.c_int)], C.c_int),
+        "vi_problem_set_option": ([H, C.c_int, C.c_int], C.c_int),
+        "vi_solve": ([H, C.c_double, C.c_int, vp, u8p, vp, C.c_int, C.POINTER(vi_solve_info)], C.c_int),
+        "vi_solve_host": ([H, C.c_double, C.c_int, vp, u8p, C.c_int, C.POINTER(vi_solve_info)], C.c_int),
+        "vi_backup": ([H, vp, vp, u8p, vp, C.POINTER(C.c_double)], C.c_int),
+        "vi_policy_eval": ([H, u8p, vp, C.c_double, C.c_int, vp, C.POINTER(C.c_int),
+                            C.POINTER(C.c_double)], C.c_int),
+        "vi_next_states": ([H, vp, C.c_int, vp, vp], C.c_int),
+        "vi_simulate": ([H, u8p, C.c_int, C.c_int, C.c_int, C.c_uint64, vp, vp, vp, vp], C.c_int),
+        "vi_server_create": ([C.c_size_t, C.c_int, vp, C.POINTER(C.c_void_p)], C.c_int),
+        "vi_server_submit": ([C.c_void_p, C.POINTER(vi_problem_desc), C.c_double, C.c_int,
+                              C.POINTER(C.c_uint64)], C.c_int),
+        "vi_server_poll": ([C.c_void_p, C.c_uint64, C.POINTER(C.c_int), vp, vp, C.POINTER(vi_solve_info)],
+                           C.c_int),
+        "vi_server_destroy": ([C.c_void_p], C.c_int),
+        "vi_status_string": ([C.c_int], C.c_char_p),
+        "vi_last_error": ([], C.c_char_p),
+    }
+    for name, (args, res) in sigs.items():
+        if name.startswith("vi_server_") and not hasattr(L, name):
+            continue
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def status_name(s: int) -> str:
+    try:
+        return lib().vi_status_string(s).decode()
+    except Exception:  # pragma: no cover - only used while formatting an error
+        return str(s)
+
+
+def _check(status: int, where: str, allow=(VI_OK,)) -> int:
+    if status not in allow:
+        raise ViError(status, where, lib().vi_last_error().decode())
+    return status
+
+
+def _addr(x) -> Optional[int]:
+    """Device/host address of a tensor, numpy array, integer or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ---------------------------------------------------------------------------
+# thin wrappers, same names as the C ABI
+# ---------------------------------------------------------------------------
+
+def vi_problem_create(m: int, L: int, Q: int, cost: Sequence[float], pmf: np.ndarray, gamma: float,
+                      issuing: int) -> int:
+    c = np.ascontiguousarray(cost, np.float64)
+    p = np.ascontiguousarray(pmf, np.float64)
+    h = C.c_void_p()
+    _check(lib().vi_problem_create(m, L, Q, c.ctypes.data_as(C.POINTER(C.c_double)),
+                                   p.ctypes.data_as(C.POINTER(C.c_double)), len(p) - 1, gamma, issuing,
+                                   C.byref(h)), "vi_problem_create")
+    return h.value
+
+
+def make_desc(products: Sequence[dict], gamma: float, issuing: int = VI_FIFO, precision: int = VI_PREC_FP32,
+              stop_rule: int = VI_STOP_SPAN, subst_rate: float = 0.0):
+    """products: dicts with m, L, Q, cost (5), pmf (array).  Returns (desc, keepalive)."""
+    d = vi_problem_desc()
+    d.n_products = len(products)
+    keep = []
+    for k, p in enumerate(products):
+        d.m[k], d.L[k], d.Q[k] = int(p["m"]), int(p["L"]), int(p["Q"])
+        for j in range(5):
+            d.cost[k][j] = float(p["cost"][j])
+        arr = np.ascontiguousarray(p["pmf"], np.float64)
+        keep.append(arr)
+        d.pmf[k] = arr.ctypes.data_as(C.POINTER(C.c_double))
+        d.dmax[k] = len(arr) - 1
+    d.subst_rate = float(subst_rate)
+    d.gamma = float(gamma)
+    d.issuing = int(issuing)
+    d.precision = int(precision)
+    d.stop_rule = int(stop_rule)
+    return d, keep
+
+
+def vi_problem_create_desc(desc: vi_problem_desc) -> int:
+    h = C.c_void_p()
+    _check(lib().vi_problem_create_desc(C.byref(desc), C.byref(h)), "vi_problem_create_desc")
+    return h.value
+
+
+def vi_problem_destroy(h: int) -> None:
+    _check(lib().vi_problem_destroy(h), "vi_problem_destroy")
+
+
+def vi_problem_sizes(h: int) -> dict:
+    n = C.c_uint64()
+    a, o, vb = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().vi_problem_sizes(h, C.byref(n), C.byref(a), C.byref(o), C.byref(vb)), "vi_problem_sizes")
+    return dict(n_states=n.value, n_actions=a.value, n_outcomes=o.value, value_bytes=vb.value)
+
+
+def vi_problem_set_option(h: int, option: int, value: int) -> None:
+    _check(lib().vi_problem_set_option(h, option, value), "vi_problem_set_option")
+
+
+def vi_solve(h: int, tol: float, max_iters: int, V, policy=None, stream=None, flags: int = 0,
+             offset: float = 0.0) -> dict:
+    info = vi_solve_info()
+    info.offset = offset
+    st = lib().vi_solve(h, tol, max_iters, _addr(V), _addr(policy), _stream(stream), flags, C.byref(info))
+    _check(st, "vi_solve", allow=(VI_OK, VI_ENOTCONVERGED))
+    return info.as_dict()
+
+
+def vi_solve_host(h: int, tol: float, max_iters: int, V_host: np.ndarray, policy_host: Optional[np.ndarray],
+                  flags: int = 0, offset: float = 0.0) -> dict:
+    info = vi_solve_info()
+    info.offset = offset
+    st = lib().vi_solve_host(h, tol, max_iters, _addr(V_host), _addr(policy_host), flags, C.byref(info))
+    _check(st, "vi_solve_host", allow=(VI_OK, VI_ENOTCONVERGED))
+    return info.as_dict()
+
+
+def vi_backup(h: int, V_in, V_out, policy=None, stream=None, stats: bool = True):
+    ds = (C.c_double * 2)()
+    _check(lib().vi_backup(h, _addr(V_in), _addr(V_out), _addr(policy), _stream(stream),
+                           ds if stats else None), "vi_backup")
+    return (ds[0], ds[1]) if stats else None
+
+
+def vi_policy_eval(h: int, policy, V, tol: float, max_iters: int, stream=None):
+    it, dl = C.c_int(), C.c_double()
+    st = lib().vi_policy_eval(h, _addr(policy), _addr(V), tol, max_iters, _stream(stream), C.byref(it),
+                              C.byref(dl))
+    _check(st, "vi_policy_eval", allow=(VI_OK, VI_ENOTCONVERGED))
+    return dict(iters=it.value, delta=dl.value, converged=(st == VI_OK))
+
+
+def vi_next_states(h: int, states, n: int, out, stream=None) -> None:
+    _check(lib().vi_next_states(h, _addr(states), n, _addr(out), _stream(stream)), "vi_next_states")
+
+
+def vi_simulate(h: int, policy, n_rollouts: int, horizon: int, warmup: int, seed: int, returns, kpis=None,
+                traj=None, stream=None) -> None:
+    _check(lib().vi_simulate(h, _addr(policy), n_rollouts, horizon, warmup, C.c_uint64(seed), _addr(returns),
+                             _addr(kpis), _addr(traj), _stream(stream)), "vi_simulate")
+
+
+def vi_server_create(mem_budget_bytes: int, max_slots: int, stream=None) -> int:
+    srv = C.c_void_p()
+    _check(lib().vi_server_create(mem_budget_bytes, max_slots, _stream(stream), C.byref(srv)), "vi_server_create")
+    return srv.value
+
+
+def vi_server_submit(srv: int, desc: vi_problem_desc, tol: float, max_iters: int) -> int:
+    rid = C.c_uint64()
+    _check(lib().vi_server_submit(srv, C.byref(desc), tol, max_iters, C.byref(rid)), "vi_server_submit")
+    return rid.value
+
+
+def vi_server_poll(srv: int, request_id: int, V_host: Optional[np.ndarray] = None,
+                   policy_host: Optional[np.ndarray] = None):
+    done = C.c_int()
+    info = vi_solve_info()
+    _check(lib().vi_server_poll(srv, request_id, C.byref(done), _addr(V_host), _addr(policy_host),
+                                C.byref(info)), "vi_server_poll")
+    return bool(done.value), info.as_dict()
+
+
+def vi_server_destroy(srv: int) -> None:
+    _check(lib().vi_server_destroy(srv), "vi_server_destroy")

@@ -1,0 +1,781 @@
+// vi_api.cu -- host side of the C ABI declared in include/vi.h.
+//
+// A handle owns: the FP64-built expectation tables (uploaded as float and as
+// double blobs), the device SolveState, the scratch half of the value ping-pong,
+// and a CUDA graph of the solve loop: init -> while(keep_going) { sweep } ->
+// extraction.  The sweep kernel's last block evaluates the stopping test on the
+// device and sets the while-node's condition, so a solve costs one graph launch
+// and one small read-back.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/vi.h"
+#include "vi_api_internal.h"
+#include "vi_common.cuh"
+#include "vi_kernels.h"
+
+using namespace vib;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+vi_status vi_fail(vi_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define CUDA_TRY(call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return vi_fail(e_ == cudaErrorMemoryAllocation ? VI_ENOMEM : VI_ECUDA, "%s: %s (%s:%d)", \
+                           #call, cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+    } while (0)
+
+extern "C" const char *vi_status_string(vi_status s) {
+    switch (s) {
+        case VI_OK: return "ok";
+        case VI_EINVAL: return "invalid argument";
+        case VI_ENOMEM: return "out of memory";
+        case VI_ENOTCONVERGED: return "not converged within max_iters";
+        case VI_ETIMEOUT: return "device wait timed out";
+        case VI_EBUSY: return "busy / over memory budget";
+        case VI_ECUDA: return "CUDA error";
+        case VI_ECANCELLED: return "cancelled";
+    }
+    return "unknown status";
+}
+
+extern "C" const char *vi_last_error(void) { return g_err; }
+
+// ---------------------------------------------------------------------------
+// table construction (FP64 on the host)
+// ---------------------------------------------------------------------------
+static int ceil_log2(int g) {
+    int b = 0;
+    while ((1 << b) < g) ++b;
+    return b;
+}
+
+struct HostTables {
+    std::vector<double> blob;
+};
+
+// expected leftover E[(y - D)^+]
+static std::vector<double> expected_leftover(const std::vector<double> &pmf, int ymax) {
+    std::vector<double> g(ymax + 1, 0.0);
+    for (int y = 0; y <= ymax; ++y) {
+        double s = 0.0;
+        for (int d = 0; d < (int)pmf.size() && d < y; ++d) s += pmf[d] * (double)(y - d);
+        g[y] = s;
+    }
+    return g;
+}
+
+static void fill_product_tables(ProdParams &P, const std::vector<double> &pmf, int issuing, const double *cost,
+                                bool with_reward, std::vector<double> &blob) {
+    const int dmax = P.dmax;
+    P.pn = dmax + 1 + P.tmax + 2 * P.G + 2;
+    P.off_p = (int)blob.size();
+    for (int k = 0; k < P.pn; ++k) blob.push_back(k <= dmax ? pmf[k] : 0.0);
+    P.off_F = (int)blob.size();
+    double c = 0.0;
+    for (int k = 0; k < P.pn; ++k) {
+        if (k <= dmax) c += pmf[k];
+        blob.push_back(c);
+    }
+    P.off_tail = (int)blob.size();
+    std::vector<double> tail(P.pn, 0.0);
+    double t = 0.0;
+    for (int k = dmax; k >= 0; --k) {
+        t += pmf[k];
+        tail[k] = t;
+    }
+    for (int k = 0; k < P.pn; ++k) blob.push_back(tail[k]);
+    P.off_TA = P.off_TB = 0;
+    if (!with_reward) return;
+    const double c_h = cost[1], c_s = cost[2], c_w = cost[3], c_r = cost[4];
+    double mu = 0.0;
+    for (int d = 0; d <= dmax; ++d) mu += (double)d * pmf[d];
+    std::vector<double> G = expected_leftover(pmf, P.tmax);
+    P.off_TA = (int)blob.size();
+    for (int T = 0; T <= P.tmax; ++T) {
+        double A = (c_s + c_r) * T - c_s * mu - (c_h + c_s + c_r) * G[T];
+        if (issuing == VI_LIFO) A += (c_h - c_w) * G[T];
+        blob.push_back(A);
+    }
+    P.off_TB = (int)blob.size();
+    for (int y = 0; y <= P.tmax; ++y) blob.push_back(issuing == VI_LIFO ? -(c_h - c_w) * G[y] : (c_h - c_w) * G[y]);
+}
+
+static double binom(int n, int k, double rho) {
+    double c = 1.0;
+    for (int i = 1; i <= k; ++i) c = c * (double)(n - k + i) / (double)i;
+    return c * pow(rho, (double)k) * pow(1.0 - rho, (double)(n - k));
+}
+
+// two-product extras: substitution mixture rows M and the expected-reward tables H1, H2
+static void fill_two_product_tables(KernelParams &kp, const vi_problem_desc &d, const std::vector<double> &pm1,
+                                    const std::vector<double> &pm2, std::vector<double> &blob) {
+    ProdParams &P1 = kp.p[0], &P2 = kp.p[1];
+    const int D1 = P1.dmax, D2 = P2.dmax;
+    const int zl = D1 + D2 + 1;
+    kp.zlen = zl;
+    const double rho = d.subst_rate;
+    // conv[n][z] = P(d2 + Bin(n, rho) = z)
+    std::vector<double> conv((size_t)(D1 + 1) * zl, 0.0);
+    for (int n = 0; n <= D1; ++n)
+        for (int u = 0; u <= n; ++u) {
+            double b = binom(n, u, rho);
+            for (int d2 = 0; d2 <= D2; ++d2) conv[(size_t)n * zl + d2 + u] += pm2[d2] * b;
+        }
+    const int nT1 = P1.tmax + 1;
+    std::vector<double> M((size_t)nT1 * zl, 0.0);
+    for (int T1 = 0; T1 < nT1; ++T1)
+        for (int d1 = T1; d1 <= D1; ++d1)
+            for (int z = 0; z < zl; ++z) M[(size_t)T1 * zl + z] += pm1[d1] * conv[(size_t)(d1 - T1) * zl + z];
+    kp.off_M = (int)blob.size();
+    blob.insert(blob.end(), M.begin(), M.end());
+    kp.off_Mc = (int)blob.size();
+    for (int T1 = 0; T1 < nT1; ++T1) {
+        double c = 0.0;
+        for (int z = 0; z < zl; ++z) {
+            c += M[(size_t)T1 * zl + z];
+            blob.push_back(c);
+        }
+    }
+    kp.off_Mt = (int)blob.size();
+    for (int T1 = 0; T1 < nT1; ++T1) {
+        std::vector<double> t(zl, 0.0);
+        double c = 0.0;
+        for (int z = zl - 1; z >= 0; --z) {
+            c += M[(size_t)T1 * zl + z];
+            t[z] = c;
+        }
+        blob.insert(blob.end(), t.begin(), t.end());
+    }
+    const double *c1 = d.cost[0], *c2 = d.cost[1];
+    const int lifo = d.issuing == VI_LIFO;
+    // H1[ys1][T1]: product-1 holding, waste and revenue (ys1 = Y_1 for FIFO, R for LIFO)
+    kp.off_H1 = (int)blob.size();
+    for (int ys = 0; ys < nT1; ++ys)
+        for (int T1 = 0; T1 < nT1; ++T1) {
+            double h = 0.0;
+            int y1 = lifo ? T1 - ys : ys;
+            if (y1 >= 0 && y1 <= T1) {
+                int R = T1 - y1;
+                for (int d1 = 0; d1 <= D1; ++d1) {
+                    int iss = std::min(d1, T1);
+                    int W = lifo ? y1 - std::min(y1, std::max(d1 - R, 0)) : std::max(y1 - d1, 0);
+                    int car = T1 - iss - W;
+                    h += pm1[d1] * (-c1[1] * car - c1[3] * W + c1[4] * iss);
+                }
+            }
+            blob.push_back(h);
+        }
+    // H2[T1][ys2][T2]: product-2 terms with substitution + product-1 shortage
+    kp.off_H2 = (int)blob.size();
+    const int nT2 = P2.tmax + 1;
+    const int ny2 = lifo ? nT2 : P2.G;
+    std::vector<double> Pz((size_t)nT1 * zl, 0.0);
+    std::vector<double> En1(nT1, 0.0);
+    for (int T1 = 0; T1 < nT1; ++T1) {
+        double below = 0.0;
+        for (int d1 = 0; d1 <= D1 && d1 < T1; ++d1) below += pm1[d1];
+        for (int z = 0; z < zl; ++z) {
+            double own = (z <= D2) ? pm2[z] : 0.0;
+            Pz[(size_t)T1 * zl + z] = below * own + M[(size_t)T1 * zl + z];
+        }
+        for (int d1 = T1; d1 <= D1; ++d1) En1[T1] += pm1[d1] * (double)(d1 - T1);
+    }
+    for (int T1 = 0; T1 < nT1; ++T1)
+        for (int ys = 0; ys < ny2; ++ys)
+            for (int T2 = 0; T2 < nT2; ++T2) {
+                int y2 = lifo ? T2 - ys : ys;
+                double h = 0.0;
+                if (y2 >= 0 && y2 <= T2) {
+                    int R2 = T2 - y2;
+                    double eshort2 = 0.0, emin2 = 0.0;
+                    for (int d2 = 0; d2 <= D2; ++d2) {
+                        eshort2 += pm2[d2] * (double)std::max(d2 - T2, 0);
+                        emin2 += pm2[d2] * (double)std::min(d2, T2);
+                    }
+                    for (int z = 0; z < zl; ++z) {
+                        double pz = Pz[(size_t)T1 * zl + z];
+                        if (pz == 0.0) continue;
+                        int iss = std::min(z, T2);
+                        int W = lifo ? y2 - std::min(y2, std::max(z - R2, 0)) : std::max(y2 - z, 0);
+                        int car = T2 - iss - W;
+                        h += pz * (-c2[1] * car - c2[3] * W + (c2[4] + c1[2]) * iss);
+                    }
+                    h += -c2[2] * eshort2 - c1[2] * (En1[T1] - emin2);
+                }
+                blob.push_back(h);
+            }
+}
+
+// ---------------------------------------------------------------------------
+// problem creation
+// ---------------------------------------------------------------------------
+static vi_status validate_product(int m, int L, int Q, const double *cost, const double *pmf, int dmax) {
+    if (m < 1 || L < 1 || Q < 0) return vi_fail(VI_EINVAL, "need m >= 1, L >= 1, Q >= 0 (got %d, %d, %d)", m, L, Q);
+    if (Q + 1 > 256) return vi_fail(VI_EINVAL, "Q+1 = %d actions exceeds the uint8 policy", Q + 1);
+    if (dmax < 0 || dmax > kMaxDmax) return vi_fail(VI_EINVAL, "dmax %d outside 0..%d", dmax, kMaxDmax);
+    if (!cost || !pmf) return vi_fail(VI_EINVAL, "null cost or pmf");
+    for (int j = 0; j < 5; ++j)
+        if (!(cost[j] >= 0.0) || !isfinite(cost[j])) return vi_fail(VI_EINVAL, "cost[%d] must be finite and >= 0", j);
+    double s = 0.0;
+    for (int d = 0; d <= dmax; ++d) {
+        if (!(pmf[d] >= 0.0) || !isfinite(pmf[d])) return vi_fail(VI_EINVAL, "pmf[%d] must be >= 0", d);
+        s += pmf[d];
+    }
+    if (fabs(s - 1.0) > 1e-9) return vi_fail(VI_EINVAL, "pmf sums to %.17g, not 1", s);
+    int K = (m - 1) + (L - 1);
+    double ns = pow((double)(Q + 1), (double)K);
+    if (ns >= 4294967296.0 || K > kMaxDigits) return vi_fail(VI_EINVAL, "|S| = (Q+1)^%d does not fit 32 bits", K);
+    return VI_OK;
+}
+
+static void fill_prod_params(ProdParams &P, int m, int L, int Q, int dmax, double c_o) {
+    memset(&P, 0, sizeof(P));
+    P.m = m;
+    P.L = L;
+    P.Q = Q;
+    P.G = Q + 1;
+    P.K = (m - 1) + (L - 1);
+    P.dmax = dmax;
+    P.tmax = m * Q;
+    P.cb = ceil_log2(P.G);
+    uint64_t n = 1;
+    for (int k = 0; k < P.K; ++k) n *= (uint64_t)P.G;
+    P.nS = (uint32_t)n;
+    uint64_t wt = 1;
+    for (int k = 0; k + 1 < P.K; ++k) wt *= (uint64_t)P.G;
+    P.w_top = P.K >= 1 ? (uint32_t)wt : 0u;
+    P.n_rest_slots = (L >= 2) ? (m - 1) : std::max(m - 2, 0);
+    uint64_t wz = 1;
+    for (int k = 0; k + 2 <= m - 1; ++k) wz *= (uint64_t)P.G;   // G^(m-2)
+    P.w_zt = (uint32_t)wz;
+    P.c_o = c_o;
+}
+
+static void destroy_internal(vi_problem *h);
+
+extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_handle *out) {
+    if (!desc || !out) return vi_fail(VI_EINVAL, "null desc or out");
+    *out = nullptr;
+    const vi_problem_desc &d = *desc;
+    if (d.n_products != 1 && d.n_products != 2) return vi_fail(VI_EINVAL, "n_products must be 1 or 2");
+    for (int k = 0; k < d.n_products; ++k) {
+        vi_status s = validate_product(d.m[k], d.L[k], d.Q[k], d.cost[k], d.pmf[k], d.dmax[k]);
+        if (s != VI_OK) return s;
+    }
+    if (!(d.gamma > 0.0 && d.gamma <= 1.0)) return vi_fail(VI_EINVAL, "gamma must be in (0, 1]");
+    if (d.issuing != VI_FIFO && d.issuing != VI_LIFO) return vi_fail(VI_EINVAL, "issuing must be FIFO or LIFO");
+    if (d.precision < VI_PREC_FP32 || d.precision > VI_PREC_FP64) return vi_fail(VI_EINVAL, "bad precision");
+    if (d.stop_rule != VI_STOP_SPAN && d.stop_rule != VI_STOP_SUPNORM) return vi_fail(VI_EINVAL, "bad stop_rule");
+    if (d.n_products == 2) {
+        if (d.L[0] != 1 || d.L[1] != 1) return vi_fail(VI_EINVAL, "two products need L = 1");
+        if ((d.Q[0] + 1) * (d.Q[1] + 1) > 256) return vi_fail(VI_EINVAL, "joint actions exceed 256");
+        if (!(d.subst_rate >= 0.0 && d.subst_rate <= 1.0)) return vi_fail(VI_EINVAL, "subst_rate in [0,1]");
+        double ns = 1.0;
+        for (int k = 0; k < 2; ++k) ns *= pow((double)(d.Q[k] + 1), (double)(d.m[k] - 1));
+        if (ns >= 4294967296.0) return vi_fail(VI_EINVAL, "|S| does not fit 32 bits");
+        if (d.dmax[0] > 255 || d.dmax[1] > 255) return vi_fail(VI_EINVAL, "two products need dmax <= 255");
+    }
+
+    vi_problem *h = new (std::nothrow) vi_problem();
+    if (!h) return vi_fail(VI_ENOMEM, "host allocation failed");
+    h->desc = d;
+    for (int k = 0; k < d.n_products; ++k) {
+        h->pmf[k].assign(d.pmf[k], d.pmf[k] + d.dmax[k] + 1);
+        h->desc.pmf[k] = h->pmf[k].data();
+    }
+    KernelParams &kp = h->kp;
+    memset(&kp, 0, sizeof(kp));
+    kp.n_products = d.n_products;
+    kp.issuing = d.issuing;
+    kp.gamma = d.gamma;
+    std::vector<double> blob;
+    for (int k = 0; k < d.n_products; ++k) {
+        fill_prod_params(kp.p[k], d.m[k], d.L[k], d.Q[k], d.dmax[k], d.cost[k][0]);
+        fill_product_tables(kp.p[k], h->pmf[k], d.issuing, d.cost[k], d.n_products == 1, blob);
+    }
+    if (d.n_products == 1) {
+        kp.nS = kp.p[0].nS;
+        kp.nA = kp.p[0].G;
+        h->n_outcomes = d.dmax[0] + 1;
+    } else {
+        fill_two_product_tables(kp, d, h->pmf[0], h->pmf[1], blob);
+        kp.nS = kp.p[0].nS * kp.p[1].nS;
+        kp.nA = kp.p[0].G * kp.p[1].G;
+        h->n_outcomes = (d.dmax[0] + 1) * (d.dmax[1] + 1);
+    }
+    kp.n_tables = (int)blob.size();
+    // the shared-memory part of the tables must fit one block
+    const int n_smem = (d.n_products == 2) ? kp.off_H1 : kp.n_tables;
+    if ((size_t)n_smem * 8 > 200 * 1024) {
+        delete h;
+        return vi_fail(VI_EINVAL, "expectation tables (%d entries) exceed shared memory", n_smem);
+    }
+    h->value_bytes = d.precision == VI_PREC_FP64 ? 8 : 4;
+    h->use_group = (d.precision == VI_PREC_FP32) && group_supported(kp);
+    std::vector<float> fblob(blob.size());
+    for (size_t i = 0; i < blob.size(); ++i) fblob[i] = (float)blob[i];
+
+    cudaError_t e;
+    if ((e = cudaMalloc(&h->d_tab_f, fblob.size() * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_tab_d, blob.size() * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_state, sizeof(SolveState))) != cudaSuccess ||
+        (e = cudaMallocHost(&h->h_state, sizeof(SolveState))) != cudaSuccess ||
+        (e = cudaMemcpy(h->d_tab_f, fblob.data(), fblob.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMemcpy(h->d_tab_d, blob.data(), blob.size() * sizeof(double), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaEventCreate(&h->ev0)) != cudaSuccess || (e = cudaEventCreate(&h->ev1)) != cudaSuccess) {
+        destroy_internal(h);
+        return vi_fail(e == cudaErrorMemoryAllocation ? VI_ENOMEM : VI_ECUDA, "problem setup: %s",
+                       cudaGetErrorString(e));
+    }
+    memset(h->h_state, 0, sizeof(SolveState));
+    h->h_state->key_min = ~0ull;
+    if ((e = cudaMemcpy(h->d_state, h->h_state, sizeof(SolveState), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        destroy_internal(h);
+        return vi_fail(VI_ECUDA, "state upload: %s", cudaGetErrorString(e));
+    }
+    kp.st = h->d_state;
+    kp.tables = (d.precision == VI_PREC_FP64) ? (const void *)h->d_tab_d : (const void *)h->d_tab_f;
+    *out = h;
+    return VI_OK;
+}
+
+extern "C" vi_status vi_problem_create(int m, int L, int Q, const double cost[5], const double *pmf, int dmax,
+                                       double gamma, int issuing, vi_handle *out) {
+    vi_problem_desc d;
+    memset(&d, 0, sizeof(d));
+    d.n_products = 1;
+    d.m[0] = m;
+    d.L[0] = L;
+    d.Q[0] = Q;
+    if (!cost) return vi_fail(VI_EINVAL, "null cost");
+    for (int j = 0; j < 5; ++j) d.cost[0][j] = cost[j];
+    d.pmf[0] = pmf;
+    d.dmax[0] = dmax;
+    d.gamma = gamma;
+    d.issuing = issuing;
+    d.precision = VI_PREC_FP32;
+    d.stop_rule = VI_STOP_SPAN;
+    return vi_problem_create_desc(&d, out);
+}
+
+static void destroy_internal(vi_problem *h) {
+    if (!h) return;
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->d_tab_f) cudaFree(h->d_tab_f);
+    if (h->d_tab_d) cudaFree(h->d_tab_d);
+    if (h->d_state) cudaFree(h->d_state);
+    if (h->h_state) cudaFreeHost(h->h_state);
+    if (h->d_scratch) cudaFree(h->d_scratch);
+    if (h->d_pe[0]) cudaFree(h->d_pe[0]);
+    if (h->d_pe[1]) cudaFree(h->d_pe[1]);
+    if (h->d_stage_v) cudaFree(h->d_stage_v);
+    if (h->d_stage_p) cudaFree(h->d_stage_p);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+}
+
+extern "C" vi_status vi_problem_destroy(vi_handle h) {
+    if (!h) return VI_OK;
+    cudaDeviceSynchronize();
+    destroy_internal(h);
+    return VI_OK;
+}
+
+extern "C" vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions, int *n_outcomes,
+                                      int *value_bytes) {
+    if (!h) return vi_fail(VI_EINVAL, "null handle");
+    if (n_states) *n_states = h->kp.nS;
+    if (n_actions) *n_actions = h->kp.nA;
+    if (n_outcomes) *n_outcomes = h->n_outcomes;
+    if (value_bytes) *value_bytes = h->value_bytes;
+    return VI_OK;
+}
+
+extern "C" vi_status vi_problem_set_option(vi_handle h, int option, int value) {
+    if (!h) return vi_fail(VI_EINVAL, "null handle");
+    if (option == VI_OPT_KERNEL) {
+        if (value == VI_KERNEL_AUTO) {
+            h->use_group = (h->desc.precision == VI_PREC_FP32) && group_supported(h->kp);
+        } else if (value == VI_KERNEL_GENERIC) {
+            h->use_group = false;
+        } else if (value == VI_KERNEL_GROUP) {
+            if (!(h->desc.precision == VI_PREC_FP32 && group_supported(h->kp)))
+                return vi_fail(VI_EINVAL, "the factorised kernel needs one FP32 product with 2 <= Q+1 <= %d",
+                               kMaxGroupG);
+            h->use_group = true;
+        } else {
+            return vi_fail(VI_EINVAL, "bad kernel choice %d", value);
+        }
+        if (h->graph_exec) {
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+        }
+        if (h->graph) {
+            cudaGraphDestroy(h->graph);
+            h->graph = nullptr;
+        }
+        return VI_OK;
+    }
+    if (option == VI_OPT_PE_MAX_ITERS) {
+        if (value < 0) return vi_fail(VI_EINVAL, "pe max iters must be >= 0");
+        h->pe_max_iters = value;
+        return VI_OK;
+    }
+    return vi_fail(VI_EINVAL, "unknown option %d", option);
+}
+
+// ---------------------------------------------------------------------------
+// solve
+// ---------------------------------------------------------------------------
+static vi_status ensure_scratch(vi_problem *h) {
+    if (h->d_scratch) return VI_OK;
+    CUDA_TRY(cudaMalloc(&h->d_scratch, (size_t)h->kp.nS * h->value_bytes));
+    return VI_OK;
+}
+
+static vi_status launch_desc(const LaunchDesc &ld, void **args, cudaStream_t s) {
+    CUDA_TRY(cudaLaunchKernel(ld.fn, ld.grid, ld.block, args, ld.smem, s));
+    return VI_OK;
+}
+
+static vi_status build_graph(vi_problem *h) {
+    if (h->graph_exec) return VI_OK;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaGraphCreate(&g, 0));
+    h->graph = g;
+    cudaGraphConditionalHandle cond;
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+    h->cond = (unsigned long long)cond;
+
+    LaunchDesc ld_init, ld_sweep;
+    CUDA_TRY(describe_solve_init(h->kp.nS, ld_init));
+    CUDA_TRY(describe_sweep(h->kp, h->desc.precision, h->use_group ? 1 : 0, ld_sweep));
+    h->args_kp = h->kp;
+    h->args_nS = h->kp.nS;
+    h->args_mode_sweep = MODE_SWEEP;
+    h->args_mode_extract = MODE_EXTRACT;
+    h->args_null_v = nullptr;
+    h->args_null_p = nullptr;
+
+    cudaKernelNodeParams kn;
+    memset(&kn, 0, sizeof(kn));
+    void *init_args[] = {&h->kp.st, &h->args_nS};
+    kn.func = (void *)ld_init.fn;
+    kn.gridDim = ld_init.grid;
+    kn.blockDim = ld_init.block;
+    kn.sharedMemBytes = 0;
+    kn.kernelParams = init_args;
+    cudaGraphNode_t n_init;
+    CUDA_TRY(cudaGraphAddKernelNode(&n_init, g, nullptr, 0, &kn));
+
+    // the union inside cudaGraphNodeParams has no default constructor: build it in zeroed storage
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    memset(cp_raw, 0, sizeof(cp_raw));
+    cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t n_loop;
+    CUDA_TRY(cudaGraphAddNode(&n_loop, g, &n_init, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+
+    void *sweep_args[] = {&h->args_kp, &h->args_mode_sweep, &h->args_null_v, &h->args_null_v, &h->args_null_p};
+    memset(&kn, 0, sizeof(kn));
+    kn.func = (void *)ld_sweep.fn;
+    kn.gridDim = ld_sweep.grid;
+    kn.blockDim = ld_sweep.block;
+    kn.sharedMemBytes = (unsigned)ld_sweep.smem;
+    kn.kernelParams = sweep_args;
+    cudaGraphNode_t n_sweep;
+    CUDA_TRY(cudaGraphAddKernelNode(&n_sweep, body, nullptr, 0, &kn));
+
+    void *extract_args[] = {&h->args_kp, &h->args_mode_extract, &h->args_null_v, &h->args_null_v,
+                            &h->args_null_p};
+    kn.kernelParams = extract_args;
+    cudaGraphNode_t n_extract;
+    CUDA_TRY(cudaGraphAddKernelNode(&n_extract, g, &n_loop, 1, &kn));
+
+    CUDA_TRY(cudaGraphInstantiate(&h->graph_exec, g, 0));
+    return VI_OK;
+}
+
+// host-driven loop (VI_FLAG_NO_GRAPH): launches sweeps in batches and polls the flag
+static vi_status run_host_loop(vi_problem *h, cudaStream_t s) {
+    LaunchDesc ld_init, ld_sweep;
+    CUDA_TRY(describe_solve_init(h->kp.nS, ld_init));
+    CUDA_TRY(describe_sweep(h->kp, h->desc.precision, h->use_group ? 1 : 0, ld_sweep));
+    KernelParams kp = h->kp;
+    uint32_t nS = kp.nS;
+    int mode_sweep = MODE_SWEEP, mode_extract = MODE_EXTRACT;
+    void *nv = nullptr;
+    uint8_t *np = nullptr;
+    void *init_args[] = {&kp.st, &nS};
+    vi_status st = launch_desc(ld_init, init_args, s);
+    if (st != VI_OK) return st;
+    void *sweep_args[] = {&kp, &mode_sweep, &nv, &nv, &np};
+    const int batch = 4;
+    int launched = 0;
+    while (launched < h->h_state->max_iters) {
+        for (int k = 0; k < batch && launched < h->h_state->max_iters; ++k, ++launched) {
+            st = launch_desc(ld_sweep, sweep_args, s);
+            if (st != VI_OK) return st;
+        }
+        CUDA_TRY(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (!h->h_state->keep_going) break;
+    }
+    void *extract_args[] = {&kp, &mode_extract, &nv, &nv, &np};
+    return launch_desc(ld_sweep, extract_args, s);
+}
+
+static vi_status policy_eval_impl(vi_problem *h, const uint8_t *policy, double *V, double tol, int max_iters,
+                                  cudaStream_t s, int *iters_out, double *delta_out);
+
+extern "C" vi_status vi_solve(vi_handle h, double tol, int max_iters, void *V, uint8_t *policy, void *stream,
+                              int flags, vi_solve_info *info) {
+    if (!h) return vi_fail(VI_EINVAL, "null handle");
+    if (!V) return vi_fail(VI_EINVAL, "null V");
+    if (!(tol >= 0.0) || max_iters < 0) return vi_fail(VI_EINVAL, "need tol >= 0 and max_iters >= 0");
+    if ((flags & VI_FLAG_WARM_START) && !info) return vi_fail(VI_EINVAL, "warm start needs info->offset");
+    cudaStream_t s = (cudaStream_t)stream;
+    vi_status st = ensure_scratch(h);
+    if (st != VI_OK) return st;
+
+    const bool use_graph = !(flags & VI_FLAG_NO_GRAPH);
+    if (use_graph) {
+        st = build_graph(h);
+        if (st != VI_OK) return st;
+    }
+    SolveState *hs = h->h_state;
+    memset(hs, 0, sizeof(SolveState));
+    hs->buf[0] = V;
+    hs->buf[1] = h->d_scratch;
+    hs->policy = policy;
+    hs->tol = tol;
+    hs->gamma = h->desc.gamma;
+    hs->max_iters = max_iters;
+    hs->stop_rule = h->desc.stop_rule;
+    hs->normalise = h->desc.precision != VI_PREC_FP64;
+    hs->use_cond = use_graph ? 1 : 0;
+    hs->cond = h->cond;
+    hs->warm = (flags & VI_FLAG_WARM_START) ? 1 : 0;
+    hs->value_bytes = h->value_bytes;
+    hs->key_min = ~0ull;
+    hs->offset = (flags & VI_FLAG_WARM_START) ? info->offset : 0.0;
+    CUDA_TRY(cudaMemcpyAsync(h->d_state, hs, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaEventRecord(h->ev0, s));
+    if (use_graph) {
+        CUDA_TRY(cudaGraphLaunch(h->graph_exec, s));
+    } else {
+        st = run_host_loop(h, s);
+        if (st != VI_OK) return st;
+    }
+    CUDA_TRY(cudaEventRecord(h->ev1, s));
+    CUDA_TRY(cudaMemcpyAsync(hs, h->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    vi_status result = hs->converged ? VI_OK : VI_ENOTCONVERGED;
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->iters = hs->iter;
+        info->status = result;
+        info->crit = hs->crit;
+        info->dmax = hs->dmax_abs;
+        info->dmin = hs->dmin_abs;
+        info->offset = hs->normalise ? hs->offset : 0.0;
+        info->wall_ms = ms;
+        double nominal = (double)h->kp.nS * (double)h->kp.nA * (double)h->n_outcomes * (double)hs->iter;
+        info->updates_per_s = ms > 0.f ? nominal / (ms * 1e-3) : 0.0;
+    }
+    if ((flags & VI_FLAG_POLICY_EVAL) && policy && info) {
+        const uint32_t n = h->kp.nS;
+        if (!h->d_pe[0]) {
+            CUDA_TRY(cudaMalloc(&h->d_pe[0], (size_t)n * sizeof(double)));
+            CUDA_TRY(cudaMalloc(&h->d_pe[1], (size_t)n * sizeof(double)));
+        }
+        // start from V_abs of the solve, evaluate the extracted policy in FP64
+        if (h->value_bytes == 4) {
+            CUDA_TRY(launch_to_fp64((const float *)V, info->offset, h->d_pe[0], n, s));
+        } else {
+            CUDA_TRY(cudaMemcpyAsync(h->d_pe[0], V, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+        }
+        CUDA_TRY(cudaMemcpyAsync(h->d_pe[1], h->d_pe[0], (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+        int it = 0;
+        double delta = 0.0;
+        double scale = std::max(fabs(info->offset), 1.0);
+        vi_status ps = policy_eval_impl(h, policy, h->d_pe[0], 1e-9 * scale, h->pe_max_iters, s, &it, &delta);
+        if (ps != VI_OK && ps != VI_ENOTCONVERGED) return ps;
+        CUDA_TRY(launch_absdiff(h->d_pe[0], h->d_pe[1], n, h->d_state, s));
+        CUDA_TRY(cudaMemcpyAsync(hs, h->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        info->pe_iters = it;
+        info->pe_delta = delta;
+        info->pe_gap = hs->dmax_abs;
+    }
+    return result;
+}
+
+extern "C" vi_status vi_solve_host(vi_handle h, double tol, int max_iters, void *V_host, uint8_t *policy_host,
+                                   int flags, vi_solve_info *info) {
+    if (!h) return vi_fail(VI_EINVAL, "null handle");
+    if (!V_host) return vi_fail(VI_EINVAL, "null V_host");
+    if (!h->own_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+    const size_t nb = (size_t)h->kp.nS * h->value_bytes;
+    if (!h->d_stage_v) CUDA_TRY(cudaMalloc(&h->d_stage_v, nb));
+    if (policy_host && !h->d_stage_p) CUDA_TRY(cudaMalloc(&h->d_stage_p, h->kp.nS));
+    cudaStream_t s = h->own_stream;
+    if (flags & VI_FLAG_WARM_START) CUDA_TRY(cudaMemcpyAsync(h->d_stage_v, V_host, nb, cudaMemcpyHostToDevice, s));
+    vi_status st = vi_solve(h, tol, max_iters, h->d_stage_v, policy_host ? h->d_stage_p : nullptr, s, flags, info);
+    if (st != VI_OK && st != VI_ENOTCONVERGED) return st;
+    CUDA_TRY(cudaMemcpyAsync(V_host, h->d_stage_v, nb, cudaMemcpyDeviceToHost, s));
+    if (policy_host) CUDA_TRY(cudaMemcpyAsync(policy_host, h->d_stage_p, h->kp.nS, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// single backup, next states, policy evaluation, rollouts
+// ---------------------------------------------------------------------------
+extern "C" vi_status vi_backup(vi_handle h, const void *V_in, void *V_out, uint8_t *policy, void *stream,
+                               double *dstats) {
+    if (!h) return vi_fail(VI_EINVAL, "null handle");
+    if (!V_in || !V_out || V_in == V_out) return vi_fail(VI_EINVAL, "V_in and V_out must be distinct buffers");
+    cudaStream_t s = (cudaStream_t)stream;
+    LaunchDesc ld;
+    CUDA_TRY(describe_sweep(h->kp, h->desc.precision, h->use_group ? 1 : 0, ld));
+    KernelParams kp = h->kp;
+    int mode = MODE_PLAIN;
+    const void *vin = V_in;
+    void *vout = V_out;
+    void *args[] = {&kp, &mode, &vin, &vout, &policy};
+    vi_status st = launch_desc(ld, args, s);
+    if (st != VI_OK) return st;
+    if (dstats) {
+        CUDA_TRY(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        dstats[0] = h->h_state->dmax_abs;
+        dstats[1] = h->h_state->dmin_abs;
+    }
+    return VI_OK;
+}
+
+extern "C" vi_status vi_next_states(vi_handle h, const uint32_t *states, int n, uint32_t *out, void *stream) {
+    if (!h) return vi_fail(VI_EINVAL, "null handle");
+    if (n < 0 || (n > 0 && (!states || !out))) return vi_fail(VI_EINVAL, "bad states / out");
+    if (n == 0) return VI_OK;
+    if (n > 65535) return vi_fail(VI_EINVAL, "at most 65535 states per call");
+    CUDA_TRY(launch_next_states(h->kp, states, n, out, (cudaStream_t)stream));
+    return VI_OK;
+}
+
+static vi_status policy_eval_impl(vi_problem *h, const uint8_t *policy, double *V, double tol, int max_iters,
+                                  cudaStream_t s, int *iters_out, double *delta_out) {
+    const uint32_t n = h->kp.nS;
+    double *tmp = nullptr;
+    CUDA_TRY(cudaMallocAsync((void **)&tmp, (size_t)n * sizeof(double), s));
+    KernelParams kp = h->kp;
+    kp.tables = h->d_tab_d;
+    double *cur = V, *nxt = tmp;
+    int it = 0;
+    double delta = INFINITY;
+    vi_status result = VI_ENOTCONVERGED;
+    while (it < max_iters) {
+        cudaError_t e = launch_policy_eval(kp, policy, cur, nxt, s);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(tmp, s);
+            return vi_fail(VI_ECUDA, "policy eval launch: %s", cudaGetErrorString(e));
+        }
+        std::swap(cur, nxt);
+        ++it;
+        if (it % 8 == 0 || it == max_iters) {
+            CUDA_TRY(cudaMemcpyAsync(h->h_state, h->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            delta = std::max(fabs(h->h_state->dmax_abs), fabs(h->h_state->dmin_abs));
+            if (delta < tol) {
+                result = VI_OK;
+                break;
+            }
+        }
+    }
+    if (cur != V) CUDA_TRY(cudaMemcpyAsync(V, cur, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaFreeAsync(tmp, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (iters_out) *iters_out = it;
+    if (delta_out) *delta_out = delta;
+    return result;
+}
+
+extern "C" vi_status vi_policy_eval(vi_handle h, const uint8_t *policy, double *V, double tol, int max_iters,
+                                    void *stream, int *iters, double *delta) {
+    if (!h) return vi_fail(VI_EINVAL, "null handle");
+    if (!policy || !V || !(tol >= 0.0) || max_iters < 0) return vi_fail(VI_EINVAL, "bad policy-eval arguments");
+    return policy_eval_impl(h, policy, V, tol, max_iters, (cudaStream_t)stream, iters, delta);
+}
+
+static void make_thresholds(const std::vector<double> &pmf, unsigned long long *thr) {
+    // floor(2^32 * CDF(d)), CDF summed in ascending order; the last entry is 2^32
+    const int dmax = (int)pmf.size() - 1;
+    double c = 0.0;
+    for (int d = 0; d <= dmax; ++d) {
+        c += pmf[d];
+        double t = floor(c * 4294967296.0);
+        if (t > 4294967296.0) t = 4294967296.0;
+        if (t < 0.0) t = 0.0;
+        thr[d] = (unsigned long long)t;
+    }
+    thr[dmax] = 4294967296ull;
+}
+
+extern "C" vi_status vi_simulate(vi_handle h, const uint8_t *policy, int n_rollouts, int horizon, int warmup,
+                                 uint64_t seed, double *returns, double *kpis, int32_t *traj, void *stream) {
+    if (!h) return vi_fail(VI_EINVAL, "null handle");
+    if (!policy || !returns || n_rollouts < 0 || horizon < 0 || warmup < 0)
+        return vi_fail(VI_EINVAL, "bad rollout arguments");
+    if (n_rollouts == 0) return VI_OK;
+    const vi_problem_desc &d = h->desc;
+    for (int k = 0; k < d.n_products; ++k)
+        if (d.dmax[k] > kMaxRollDmax) return vi_fail(VI_EINVAL, "rollouts need dmax <= %d", kMaxRollDmax);
+    if (d.n_products == 2 && d.subst_rate != 0.5)
+        return vi_fail(VI_EINVAL, "two-product rollouts draw substitutions as fair bits (subst_rate 1/2)");
+    RollParams rp;
+    memset(&rp, 0, sizeof(rp));
+    rp.n_rollouts = n_rollouts;
+    rp.horizon = horizon;
+    rp.warmup = warmup;
+    rp.seed = seed;
+    for (int k = 0; k < d.n_products; ++k) {
+        for (int j = 0; j < 5; ++j) rp.cost[k][j] = d.cost[k][j];
+        make_thresholds(h->pmf[k], rp.thr[k]);
+    }
+    CUDA_TRY(launch_rollouts(h->kp, rp, policy, returns, kpis, traj, (cudaStream_t)stream));
+    return VI_OK;
+}

@@ -1,0 +1,41 @@
+// vi_api_internal.h -- the handle behind vi_handle (host side only).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/vi.h"
+#include "vi_common.cuh"
+
+struct vi_problem {
+    vi_problem_desc desc;              // pmf pointers redirected to the copies below
+    std::vector<double> pmf[2];
+    vib::KernelParams kp;              // tables / state pointers filled in
+    int n_outcomes = 0;                // nominal |Omega|
+    int value_bytes = 4;
+    bool use_group = false;            // factorised kernel for this instance
+    int pe_max_iters = 100000;
+    // device resources
+    float *d_tab_f = nullptr;
+    double *d_tab_d = nullptr;
+    vib::SolveState *d_state = nullptr;
+    vib::SolveState *h_state = nullptr;   // pinned mirror
+    void *d_scratch = nullptr;            // second half of the value ping-pong
+    double *d_pe[2] = {nullptr, nullptr};
+    void *d_stage_v = nullptr;            // vi_solve_host staging
+    uint8_t *d_stage_p = nullptr;
+    cudaStream_t own_stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // solve graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    unsigned long long cond = 0;
+    vib::KernelParams args_kp;
+    uint32_t args_nS = 0;
+    int args_mode_sweep = 0, args_mode_extract = 1;
+    void *args_null_v = nullptr;
+    uint8_t *args_null_p = nullptr;
+};
+
+vi_status vi_fail(vi_status s, const char *fmt, ...);

@@ -1,0 +1,207 @@
+// vi_common.cuh -- shared definitions of the B300 value-iteration kernels.
+//
+// State layout (mixed radix, G = Q+1): digit k has weight G^k; digits 0..m-2 are
+// the on-hand stock X_1..X_{m-1} by remaining life, digits m-1..K-1 the orders in
+// transit P_1..P_{L-1}.  Write s = x + G*r with x = digit 0.  Digit 0 is always
+// the oldest unit slot Y_1 (X_1, or the arriving order P_1 when m = 1), and it
+// never survives into the next state: whatever is left of it expires.  The next
+// state only depends on the "rest" r, the action a and the demand reaching the
+// other slots.  With Z_1..Z_{m-1} = (X_2, ..., X_{m-1}, u) (u = arriving units),
+// the next state before any demand is s'_0 = r + a * G^(K-1), and every unit of
+// demand that reaches the rest removes one unit from one Z slot, i.e. subtracts
+// that slot's weight from the index: oldest slot first under FIFO, freshest slot
+// first under LIFO (Eq. demoor:fifo, Eq. demoor:lifo).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vib {
+
+constexpr int kMaxDigits = 31;      // (Q+1)^K < 2^32 with Q >= 1
+constexpr int kMaxDmax = 4095;
+
+// ---------------------------------------------------------------------------
+// per-product parameters (plain data; passed by value inside KernelParams)
+// ---------------------------------------------------------------------------
+struct ProdParams {
+    int m, L, Q, G;       // life, lead time, order cap, radix G = Q+1
+    int K;                // number of state digits (m-1)+(L-1)
+    int dmax;             // demand support 0..dmax
+    int tmax;             // largest stock available in a period, m*Q
+    int cb;               // bits per packed slot count = ceil(log2(G))
+    uint32_t nS;          // G^K
+    uint32_t w_top;       // G^(K-1) (0 if K == 0)
+    int n_rest_slots;     // slots of r that are stock Z digits: m-2 (L=1) or m-1 (L>=2), >= 0
+    uint32_t w_zt;        // G^(m-2): weight of the freshest stock slot Z_{m-1} (1 if m < 2)
+    // offsets (in elements) of this product's tables inside the table blob
+    int off_p;            // p[k]     = P(D = k), zero beyond dmax        (len pn)
+    int off_F;            // F[k]     = P(D <= k), one beyond dmax         (len pn)
+    int off_tail;         // tail[k]  = P(D >= k), zero beyond dmax        (len pn)
+    int off_TA;           // TA[T]    expected reward part depending on T (len tmax+1)
+    int off_TB;           // TB[y]    expected waste part (FIFO: y = Y_1, LIFO: y = R), len tmax+1
+    int pn;               // length of p / F / tail
+    double c_o;           // order cost per unit
+};
+
+struct SolveState;  // device-resident solve bookkeeping (below)
+
+struct KernelParams {
+    ProdParams p[2];
+    int n_products;
+    int issuing;          // 0 FIFO, 1 LIFO
+    uint32_t nS;          // total states
+    int nA;               // total actions
+    double gamma;
+    const void *tables;   // device table blob (float or double, see precision)
+    int n_tables;         // elements in the blob
+    // two-product extras (offsets into the blob)
+    int off_M;            // M[T1][z]: mass of (d1 >= T1, product-2 demand z), row length zlen
+    int off_Mc;           // cumulative of M rows
+    int off_Mt;           // tail of M rows
+    int off_H1;           // H1[y1][T1]  expected product-1 reward terms, row length (tmax1+1)
+    int off_H2;           // H2[T1][y2][T2] expected product-2 + substitution terms
+    int zlen;             // dmax1 + dmax2 + 1
+    SolveState *st;       // solve bookkeeping
+};
+
+// ---------------------------------------------------------------------------
+// device solve bookkeeping.  The sweep kernel reads its input/output buffers and
+// the normalisation constant from here; the last block of every sweep folds the
+// block reductions, updates the FP64 offset and decides whether to continue.
+// ---------------------------------------------------------------------------
+struct SolveState {
+    // configuration (written by the host before a solve)
+    void *buf[2];                 // buf[0] = caller's V, buf[1] = scratch
+    uint8_t *policy;              // caller's policy or null
+    double tol;
+    double gamma;
+    int max_iters;
+    int stop_rule;
+    int normalise;                // FP32 paths subtract c each sweep
+    int use_cond;                 // set the graph conditional from the last block
+    int warm;                     // keep V and the offset given by the caller
+    int value_bytes;              // 4 (float) or 8 (double)
+    unsigned long long cond;      // cudaGraphConditionalHandle
+    // running state
+    unsigned long long key_max;   // order-preserving encoding of max(v_i - v_{i-1})
+    unsigned long long key_min;
+    unsigned int blocks_done;
+    int iter;                     // sweeps done
+    int keep_going;               // 1 while the sweep loop should run
+    int converged;
+    float c_cur;                  // constant subtracted in the current sweep
+    float c_next;                 // unnormalised value of state 0 in the current sweep
+    double offset;                // b: V_abs = b + v
+    double crit, dmax_abs, dmin_abs;
+};
+
+// order-preserving map double -> uint64 so that unsigned max/min give double max/min
+__device__ __forceinline__ unsigned long long dkey(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+    unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+// ---------------------------------------------------------------------------
+// The next-state walker: index of s'(e) after e units of demand reached the rest
+// slots.  Slot counts are packed `cb` bits each in consumption order.
+// ---------------------------------------------------------------------------
+struct Walker {
+    uint32_t idx;        // current next-state index
+    uint32_t w;          // weight of the slot being consumed
+    unsigned long long packed;   // counts of Z_1..Z_{m-1}, Z_1 in the low bits
+    int slot;            // 0-based slot being consumed (weight G^slot)
+    int left;            // units left in it
+};
+
+// FIFO: consume Z_1 first (weight 1) upward.  LIFO: consume Z_{m-1} first.
+__device__ __forceinline__ void walker_init(Walker &wk, uint32_t idx0, unsigned long long packed,
+                                            int nslots, int cb, int lifo, uint32_t G_pow_top) {
+    wk.idx = idx0;
+    wk.packed = packed;
+    unsigned long long mask = (1ull << cb) - 1ull;
+    if (!lifo) {
+        wk.slot = 0;
+        wk.w = 1u;
+        wk.left = (nslots > 0) ? (int)(packed & mask) : 0;
+    } else {
+        wk.slot = nslots - 1;
+        wk.w = G_pow_top;   // G^(nslots-1)
+        wk.left = (nslots > 0) ? (int)((packed >> (cb * (nslots - 1))) & mask) : 0;
+    }
+}
+
+// consume one unit; callers only step while units remain in the slots (e <= R).
+// The slot search is bounded so that a violated precondition cannot spin.
+__device__ __forceinline__ void walker_step(Walker &wk, int cb, int lifo, uint32_t G) {
+    unsigned long long mask = (1ull << cb) - 1ull;
+    for (int guard = 0; wk.left == 0; ++guard) {
+        if (guard >= kMaxDigits) return;
+        if (!lifo) {
+            wk.slot += 1;
+            wk.w *= G;
+        } else {
+            wk.slot -= 1;
+            wk.w /= G;
+        }
+        wk.left = (int)((wk.packed >> (cb * wk.slot)) & mask);
+    }
+    wk.idx -= wk.w;
+    wk.left -= 1;
+}
+
+// ---------------------------------------------------------------------------
+// decode of the rest index r (digits 1..K-1 of s): stock slots + pipeline
+// ---------------------------------------------------------------------------
+struct RestInfo {
+    unsigned long long packed;   // counts of the rest stock slots (without the arrival if L = 1)
+    int R;                       // their sum
+};
+
+__device__ __forceinline__ RestInfo decode_rest(uint32_t r, const ProdParams &P) {
+    RestInfo ri;
+    ri.packed = 0ull;
+    ri.R = 0;
+    uint32_t rem = r;
+    for (int j = 0; j < P.n_rest_slots; ++j) {
+        uint32_t q = rem / (uint32_t)P.G;
+        int dgt = (int)(rem - q * (uint32_t)P.G);
+        rem = q;
+        ri.packed |= (unsigned long long)dgt << (P.cb * j);
+        ri.R += dgt;
+    }
+    return ri;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): rounds multiply words 0 and 2 by
+// 0xD2511F53 / 0xCD9E8D57; key bumped by 0x9E3779B9 / 0xBB67AE85 between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              uint32_t k0, uint32_t k1, uint32_t out[4]) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+}  // namespace vib

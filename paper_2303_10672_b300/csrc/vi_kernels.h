@@ -1,0 +1,56 @@
+// vi_kernels.h -- launchers of the sm_103a kernels (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vi_common.cuh"
+
+namespace vib {
+
+// launch modes of the sweep kernels
+enum {
+    MODE_SWEEP = 0,     // solve sweep: buffers and normalisation from SolveState, span stats, stop test
+    MODE_EXTRACT = 1,   // extraction sweep: policy from V_iters, V_iters copied into the caller's buffer
+    MODE_PLAIN = 2      // one backup between explicit buffers, no normalisation, change stats only
+};
+
+constexpr int kGroupThreads = 128;   // rests per block of the factorised kernel
+constexpr int kGenericThreads = 128;
+constexpr int kMaxGroupG = 24;       // largest Q+1 with a factorised instantiation
+constexpr int kMaxRollDmax = 255;
+
+struct RollParams {
+    int n_rollouts, horizon, warmup;
+    unsigned long long seed;
+    double cost[2][5];
+    unsigned long long thr[2][kMaxRollDmax + 1];   // floor(2^32 CDF(d)), thr[dmax] = 2^32
+};
+
+bool group_supported(const KernelParams &kp);
+cudaError_t launch_sweep_group(const KernelParams &kp, int mode, const float *vin, float *vout,
+                               uint8_t *pol, cudaStream_t stream);
+cudaError_t launch_sweep_generic(const KernelParams &kp, int precision, int mode, const void *vin,
+                                 void *vout, uint8_t *pol, cudaStream_t stream);
+cudaError_t launch_next_states(const KernelParams &kp, const uint32_t *states, int n, uint32_t *out,
+                               cudaStream_t stream);
+cudaError_t launch_policy_eval(const KernelParams &kp, const uint8_t *policy, const double *vin,
+                               double *vout, cudaStream_t stream);
+cudaError_t launch_to_fp64(const float *v, double offset, double *out, uint32_t n, cudaStream_t stream);
+cudaError_t launch_absdiff(const double *a, const double *b, uint32_t n, SolveState *st,
+                           cudaStream_t stream);
+cudaError_t launch_solve_init(SolveState *st, uint32_t n, cudaStream_t stream);
+
+// what a graph kernel node needs (the dynamic shared-memory attribute is set)
+struct LaunchDesc {
+    const void *fn;
+    dim3 grid, block;
+    size_t smem;
+};
+cudaError_t describe_sweep(const KernelParams &kp, int precision, int use_group, LaunchDesc &d);
+cudaError_t describe_solve_init(uint32_t n, LaunchDesc &d);
+cudaError_t launch_state_reset(SolveState *st, cudaStream_t stream);
+cudaError_t launch_rollouts(const KernelParams &kp, const RollParams &rp, const uint8_t *policy,
+                            double *returns, double *kpis, int32_t *traj, cudaStream_t stream);
+
+}  // namespace vib

@@ -1,0 +1,79 @@
+"""Helpers shared by the GPU parity tests: marshal workloads.Instance into the
+C ABI and run solves / backups through it."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import paper_2303_10672_b300 as vi
+
+PREC = {"fp32": vi.VI_PREC_FP32, "fp32_kahan": vi.VI_PREC_FP32_KAHAN, "fp64": vi.VI_PREC_FP64}
+
+# tolerances stated by the benchmark spec: values max|dV|/max|V| <= 1e-5; policy ties within 1e-6 relative
+V_RTOL = 1e-5
+TIE_RTOL = 1e-6
+
+
+def create(inst, precision=None, stop_rule=vi.VI_STOP_SPAN, kernel=vi.VI_KERNEL_AUTO):
+    prods = [dict(m=p.m, L=p.L, Q=p.Q, cost=p.cost, pmf=p.pmf) for p in inst.products]
+    prec = PREC[precision or inst.precision]
+    desc, keep = vi.make_desc(prods, inst.gamma, inst.issuing, prec, stop_rule, inst.subst_rate)
+    h = vi.vi_problem_create_desc(desc)
+    if kernel != vi.VI_KERNEL_AUTO:
+        vi.vi_problem_set_option(h, vi.VI_OPT_KERNEL, kernel)
+    return h
+
+
+class Handle:
+    def __init__(self, inst, precision=None, stop_rule=vi.VI_STOP_SPAN, kernel=vi.VI_KERNEL_AUTO):
+        self.inst = inst
+        self.precision = precision or inst.precision
+        self.h = create(inst, self.precision, stop_rule, kernel)
+        self.sizes = vi.vi_problem_sizes(self.h)
+        self.dtype = torch.float64 if self.sizes["value_bytes"] == 8 else torch.float32
+
+    def close(self):
+        if self.h:
+            vi.vi_problem_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, tol, max_iters, flags=0, V=None, offset=0.0):
+        n = self.sizes["n_states"]
+        if V is None:
+            V = torch.empty(n, dtype=self.dtype, device="cuda")
+        pol = torch.empty(n, dtype=torch.uint8, device="cuda")
+        info = vi.vi_solve(self.h, tol, max_iters, V, pol, flags=flags, offset=offset)
+        torch.cuda.synchronize()
+        return V, pol, info
+
+    def v_abs(self, V, info) -> np.ndarray:
+        return V.double().cpu().numpy() + info["offset"]
+
+
+def compare_values(v_gpu: np.ndarray, v_ref: np.ndarray) -> float:
+    scale = max(np.abs(v_ref).max(), 1e-300)
+    return float(np.abs(v_gpu - v_ref).max() / scale)
+
+
+def policy_mismatches(P_oracle, V_ref: np.ndarray, pol_gpu: np.ndarray, states=None):
+    """States where the GPU policy differs from the oracle's first argmax by more
+    than a tie: Q(s, a_oracle) - Q(s, a_gpu) > TIE_RTOL |Q(s, a_oracle)| (FP64)."""
+    if states is None:
+        states = np.arange(len(pol_gpu))
+    _, pol_o, q = P_oracle.backup_states(V_ref, states, with_q=True)
+    bad = []
+    for i, s in enumerate(states):
+        ag = int(pol_gpu[i])
+        ao = int(pol_o[i])
+        if ag == ao:
+            continue
+        gap = q[i, ao] - q[i, ag]
+        if gap > TIE_RTOL * abs(q[i, ao]):
+            bad.append((int(s), ao, ag, float(gap)))
+    return bad

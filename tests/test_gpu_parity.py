@@ -1,0 +1,337 @@
+"""CUDA path vs FP64 oracle, element by element, through the C ABI.
+
+Values: max|V_gpu - V_oracle| / max|V_oracle| <= 1e-5 at the same iteration.
+Policies: equal except ties whose FP64 Q-gap is <= 1e-6 relative.
+Next-state indices: bit-exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from workloads import FIFO, LIFO
+
+pytestmark = pytest.mark.gpu
+
+vi = pytest.importorskip("paper_2303_10672_b300")
+from gpu_helpers import Handle, compare_values, policy_mismatches, V_RTOL  # noqa: E402
+
+
+def small_instances():
+    out = []
+    rng = np.random.default_rng(123)
+    for i in range(24):
+        out.append(workloads.random_small_instance(rng, max_states=600))
+    # hand-picked shapes: m = 1 (single state / pure pipeline), Q = 0, dmax = 0, long pipelines
+    out.append(workloads.single_product(1, 1, 6, (3, 1, 5, 7, 0), workloads.poisson_pmf(3, 10), 0.9, FIFO))
+    out.append(workloads.single_product(1, 3, 4, (3, 1, 5, 7, 1), workloads.poisson_pmf(2, 8), 0.9, LIFO))
+    out.append(workloads.single_product(3, 1, 0, (3, 1, 5, 7, 0), workloads.poisson_pmf(2, 5), 0.9, FIFO))
+    out.append(workloads.single_product(3, 2, 4, (3, 1, 5, 7, 0), workloads.poisson_pmf(2, 0), 0.9, LIFO))
+    out.append(workloads.single_product(2, 5, 3, (1, 1, 2, 1, 0), workloads.poisson_pmf(1.5, 9), 0.95, FIFO))
+    out.append(workloads.single_product(6, 1, 2, (2, 1, 4, 3, 0), workloads.poisson_pmf(2.5, 12), 0.95, LIFO))
+    out.append(workloads.single_product(4, 2, 5, (2, 1, 4, 3, 0), workloads.poisson_pmf(4.5, 30), 0.9, FIFO))
+    return out
+
+
+SMALL = small_instances()
+
+
+def _ids(insts):
+    return [f"{i}-m{x.products[0].m}L{x.products[0].L}Q{x.products[0].Q}{'L' if x.issuing else 'F'}"
+            for i, x in enumerate(insts)]
+
+
+# ---------------------------------------------------------------------------
+# next-state indices, bit-exact
+# ---------------------------------------------------------------------------
+
+def check_next_states(inst, states):
+    P = oracle.Problem(inst)
+    with Handle(inst, precision="fp32") as H:
+        st = torch.tensor(np.asarray(states, np.uint32).view(np.int32), device="cuda")
+        A = H.sizes["n_actions"]
+        if len(inst.products) == 1:
+            D = inst.products[0].dmax + 1
+            out = torch.empty(len(states) * A * D, dtype=torch.int32, device="cuda")
+            vi.vi_next_states(H.h, st, len(states), out)
+            got = out.cpu().numpy().view(np.uint32).reshape(len(states), A, D)
+            for i, s in enumerate(states):
+                for a in range(A):
+                    for d in range(D):
+                        assert got[i, a, d] == P.transition(int(s), a, d)["s_next"], (s, a, d)
+        else:
+            D1 = inst.products[0].dmax + 1
+            ZL = inst.products[0].dmax + inst.products[1].dmax + 1
+            out = torch.empty(len(states) * A * D1 * ZL, dtype=torch.int32, device="cuda")
+            vi.vi_next_states(H.h, st, len(states), out)
+            got = out.cpu().numpy().view(np.uint32).reshape(len(states), A, D1, ZL)
+            D2 = inst.products[1].dmax
+            for i, s in enumerate(states):
+                for a in range(A):
+                    for d1 in range(D1):
+                        unmet = P.transition(int(s), a, d1, 0, 0)["unmet1"]
+                        for d2 in range(D2 + 1):
+                            for u in range(unmet + 1):
+                                want = P.transition(int(s), a, d1, d2, u)["s_next"]
+                                assert got[i, a, d1, d2 + u] == want, (s, a, d1, d2, u)
+
+
+@pytest.mark.parametrize("inst", SMALL[:12], ids=_ids(SMALL[:12]))
+def test_next_states_small_exhaustive(inst):
+    check_next_states(inst, np.arange(inst.n_states))
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 4])
+def test_next_states_configs_sampled(cfg):
+    inst = workloads.CONFIGS[cfg]()
+    rng = np.random.default_rng(cfg)
+    states = np.unique(np.concatenate([[0, inst.n_states - 1], rng.integers(0, inst.n_states, 40)]))
+    check_next_states(inst, states)
+
+
+def test_next_states_two_products():
+    inst = workloads.config3(Q=3)
+    rng = np.random.default_rng(3)
+    check_next_states(inst, np.unique(np.concatenate([[0, inst.n_states - 1],
+                                                      rng.integers(0, inst.n_states, 12)])))
+
+
+# ---------------------------------------------------------------------------
+# full solves vs the oracle at the oracle's stopping iteration
+# ---------------------------------------------------------------------------
+
+def solve_parity(inst, precision, kernel=vi.VI_KERNEL_AUTO, tol=1e-4, stop_rule=0):
+    P = oracle.Problem(inst)
+    ref = P.vi_solve(tol=tol, max_iters=5000, stop_rule=stop_rule)
+    i_o = ref["iters"]
+    with Handle(inst, precision=precision, stop_rule=stop_rule, kernel=kernel) as H:
+        # same iteration count as the oracle, stop test disabled (tol = 0)
+        V, pol, info = H.solve(0.0, i_o)
+        assert info["iters"] == i_o
+        v = H.v_abs(V, info)
+        err = compare_values(v, ref["V"])
+        assert err <= V_RTOL, f"value error {err:.3e}"
+        bad = policy_mismatches(P, ref["V"], pol.cpu().numpy())
+        assert not bad, bad[:5]
+        # the device stopping test: same rule, own iteration count
+        V2, pol2, info2 = H.solve(tol, 5000)
+        assert info2["status"] == vi.VI_OK
+        assert abs(info2["iters"] - i_o) <= 2, (info2["iters"], i_o)
+    return err
+
+
+@pytest.mark.parametrize("inst", SMALL, ids=_ids(SMALL))
+@pytest.mark.parametrize("precision", ["fp32", "fp32_kahan", "fp64"])
+def test_solve_small(inst, precision):
+    solve_parity(inst, precision)
+
+
+@pytest.mark.parametrize("inst", SMALL, ids=_ids(SMALL))
+def test_solve_small_generic_kernel_fp32(inst):
+    solve_parity(inst, "fp32", kernel=vi.VI_KERNEL_GENERIC)
+
+
+def test_solve_config1_fp64_and_fp32():
+    inst = workloads.config1()
+    for prec in ("fp64", "fp32", "fp32_kahan"):
+        solve_parity(inst, prec)
+
+
+def test_solve_supnorm_rule():
+    inst = workloads.single_product(2, 2, 4, (3, 1, 5, 7, 0), workloads.poisson_pmf(2, 9), 0.8, LIFO)
+    solve_parity(inst, "fp64", tol=1e-6, stop_rule=1)
+    solve_parity(inst, "fp32", tol=1e-3, stop_rule=1)
+
+
+@pytest.mark.parametrize("Q", [2, 4])
+def test_solve_two_products(Q):
+    inst = workloads.config3(Q=Q)
+    for prec in ("fp32_kahan", "fp32", "fp64"):
+        solve_parity(inst, prec)
+
+
+@pytest.mark.parametrize("case", [dict(m=2, Q=2, m2=3, Q2=1, issuing=LIFO, rho=0.3),
+                                  dict(m=3, Q=1, m2=2, Q2=3, issuing=FIFO, rho=0.8),
+                                  dict(m=1, Q=3, m2=2, Q2=2, issuing=FIFO, rho=0.5)])
+def test_solve_two_products_general_costs(case):
+    c1 = (0.7, 0.3, 1.5, 0.9, 1.2)
+    c2 = (0.4, 0.2, 0.8, 1.1, 1.6)
+    prods = [workloads.Product(case["m"], 1, case["Q"], c1, workloads.poisson_pmf(1.3, 6)),
+             workloads.Product(case["m2"], 1, case["Q2"], c2, workloads.poisson_pmf(1.8, 7))]
+    inst = workloads.Instance("g2", prods, gamma=0.9, issuing=case["issuing"], subst_rate=case["rho"])
+    for prec in ("fp64", "fp32_kahan"):
+        solve_parity(inst, prec)
+
+
+# ---------------------------------------------------------------------------
+# full-size instances: one backup in the benchmark's launch configuration,
+# compared on sampled states computed one by one by the oracle
+# ---------------------------------------------------------------------------
+
+def sampled_backup_parity(inst, k_sweeps, n_samples, seed):
+    P = oracle.Problem(inst)
+    with Handle(inst) as H:
+        V, pol, info = H.solve(0.0, k_sweeps)           # V_k (relative) + offset
+        n = H.sizes["n_states"]
+        V_next = torch.empty_like(V)
+        pol_next = torch.empty(n, dtype=torch.uint8, device="cuda")
+        dmx, dmn = vi.vi_backup(H.h, V, V_next, pol_next)
+        torch.cuda.synchronize()
+        b = info["offset"]
+        v_k = V.double().cpu().numpy() + b
+        # V_next holds V_abs' - gamma b
+        v_next = V_next.double().cpu().numpy() + inst.gamma * b
+        rng = np.random.default_rng(seed)
+        states = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, n_samples)]))
+        want, _ = P.backup_states(v_k, states)
+        err = np.abs(v_next[states] - want).max() / np.abs(want).max()
+        assert err <= V_RTOL, err
+        bad = policy_mismatches(P, v_k, pol_next.cpu().numpy()[states], states)
+        assert not bad, bad[:5]
+        # the policy written by the extraction sweep of the solve is the argmax from V_k
+        bad = policy_mismatches(P, v_k, pol.cpu().numpy()[states], states)
+        assert not bad, bad[:5]
+        # change statistics are exact reductions of V_next - V_k (relative values)
+        dv = V_next.double() - V.double()
+        assert dmx == pytest.approx(dv.max().item(), abs=0) and dmn == pytest.approx(dv.min().item(), abs=0)
+
+
+def test_config2_full_size_sampled():
+    sampled_backup_parity(workloads.config2(), 3, 300, 2)
+
+
+def test_config4_full_size_sampled():
+    sampled_backup_parity(workloads.config4(), 3, 300, 4)
+
+
+def test_config3_full_size_sampled():
+    inst = workloads.config3()
+    P = oracle.Problem(inst)
+    with Handle(inst) as H:
+        V, pol, info = H.solve(0.0, 2)
+        n = H.sizes["n_states"]
+        v_k = V.double().cpu().numpy() + info["offset"]
+        V_next = torch.empty_like(V)
+        vi.vi_backup(H.h, V, V_next, None)
+        v_next = V_next.double().cpu().numpy() + inst.gamma * info["offset"]
+        states = np.unique(np.concatenate([[0, n - 1], np.random.default_rng(5).integers(0, n, 24)]))
+        want, _ = P.backup_states(v_k, states)
+        err = np.abs(v_next[states] - want).max() / np.abs(want).max()
+        assert err <= V_RTOL, err
+
+
+# ---------------------------------------------------------------------------
+# FP64 policy evaluation and rollouts
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("inst", [SMALL[3], SMALL[7], workloads.config3(Q=2)], ids=["a", "b", "two"])
+def test_policy_eval_fp64(inst):
+    P = oracle.Problem(inst)
+    ref = P.vi_solve(tol=1e-4, max_iters=5000)
+    pol = ref["policy"]
+    Vpe_ref, _, _ = P.policy_eval(pol, tol=1e-12, max_iters=20000)
+    with Handle(inst) as H:
+        V = torch.zeros(inst.n_states, dtype=torch.float64, device="cuda")
+        pol_t = torch.tensor(pol, device="cuda")
+        r = vi.vi_policy_eval(H.h, pol_t, V, 1e-12, 20000)
+        torch.cuda.synchronize()
+        assert r["converged"]
+        err = compare_values(V.cpu().numpy(), Vpe_ref)
+        assert err < 1e-10, err
+
+
+def rollout_parity(inst, policy, n, horizon, seed, warmup=0):
+    P = oracle.Problem(inst)
+    ref = P.simulate(policy, n, horizon, seed, warmup=warmup, with_traj=True)
+    with Handle(inst) as H:
+        pol_t = torch.tensor(policy, device="cuda")
+        ret = torch.empty(n, dtype=torch.float64, device="cuda")
+        kp = torch.empty(n * 3, dtype=torch.float64, device="cuda")
+        tr = torch.empty(n * horizon, dtype=torch.int32, device="cuda")
+        vi.vi_simulate(H.h, pol_t, n, horizon, warmup, seed, ret, kp, tr)
+        torch.cuda.synchronize()
+        assert (tr.cpu().numpy().reshape(n, horizon) == ref["traj"]).all()
+        np.testing.assert_array_equal(ret.cpu().numpy(), ref["returns"])
+        np.testing.assert_array_equal(kp.cpu().numpy().reshape(n, 3), ref["kpis"])
+
+
+@pytest.mark.parametrize("inst", SMALL[:10] + [workloads.config1()], ids=_ids(SMALL[:10]) + ["cfg1"])
+def test_rollouts_bit_exact(inst):
+    pol = oracle.Problem(inst).vi_solve(tol=1e-4, max_iters=3000)["policy"]
+    rollout_parity(inst, pol, 64, 50, seed=0xDEADBEEF12345, warmup=3)
+
+
+def test_rollouts_two_products_bit_exact():
+    inst = workloads.config3(Q=3)
+    pol = oracle.Problem(inst).vi_solve(tol=1e-4, max_iters=3000)["policy"]
+    rollout_parity(inst, pol, 32, 40, seed=7)
+
+
+def test_rollouts_config4_policy_bit_exact():
+    inst = workloads.config4()
+    with Handle(inst) as H:
+        V, pol, info = H.solve(1e-4, 1000)
+        policy = pol.cpu().numpy()
+    rollout_parity(inst, policy, 256, 365, seed=workloads.CONFIG4_ROLLOUTS["seed"])
+
+
+# ---------------------------------------------------------------------------
+# edge cases and argument checks
+# ---------------------------------------------------------------------------
+
+def test_max_iters_zero_and_not_converged():
+    inst = SMALL[5]
+    with Handle(inst) as H:
+        V, pol, info = H.solve(1e-4, 0)
+        assert info["iters"] == 0 and info["status"] == vi.VI_ENOTCONVERGED
+        assert (V == 0).all()
+        V, pol, info = H.solve(0.0, 2)
+        assert info["iters"] == 2 and info["status"] == vi.VI_ENOTCONVERGED
+
+
+def test_warm_start_resume_is_bit_identical():
+    inst = workloads.single_product(4, 2, 6, (2, 1, 4, 3, 0), workloads.poisson_pmf(3, 14), 0.95, FIFO)
+    with Handle(inst) as H:
+        V_a, _, ia = H.solve(0.0, 7)
+        V_b, _, ib = H.solve(0.0, 4)
+        V_c, _, ic = H.solve(0.0, 3, flags=vi.VI_FLAG_WARM_START, V=V_b, offset=ib["offset"])
+        # the normalisation constant restarts at 0 after a resume, so compare absolute values
+        va = V_a.double().cpu().numpy() + ia["offset"]
+        vc = V_c.double().cpu().numpy() + ic["offset"]
+        assert np.abs(va - vc).max() <= 1e-6 * np.abs(va).max()
+
+
+def test_no_graph_loop_matches_graph():
+    inst = SMALL[8]
+    with Handle(inst) as H:
+        V1, p1, i1 = H.solve(1e-4, 1000)
+        V2, p2, i2 = H.solve(1e-4, 1000, flags=vi.VI_FLAG_NO_GRAPH)
+        assert i1["iters"] == i2["iters"]
+        assert torch.equal(V1, V2) and torch.equal(p1, p2)
+
+
+def test_invalid_arguments():
+    pmf = workloads.poisson_pmf(2, 5)
+    with pytest.raises(vi.ViError):
+        vi.vi_problem_create(0, 1, 3, (1, 1, 1, 1, 0), pmf, 0.9, 0)
+    with pytest.raises(vi.ViError):
+        vi.vi_problem_create(2, 1, 3, (1, -1, 1, 1, 0), pmf, 0.9, 0)
+    with pytest.raises(vi.ViError):
+        vi.vi_problem_create(2, 1, 3, (1, 1, 1, 1, 0), pmf * 0.5, 0.9, 0)
+    with pytest.raises(vi.ViError):
+        vi.vi_problem_create(2, 1, 3, (1, 1, 1, 1, 0), pmf, 1.5, 0)
+    with pytest.raises(vi.ViError):
+        vi.vi_problem_create(2, 1, 300, (1, 1, 1, 1, 0), pmf, 0.9, 0)
+    with pytest.raises(vi.ViError):
+        vi.vi_problem_create(12, 1, 20, (1, 1, 1, 1, 0), pmf, 0.9, 0)   # 21^11 states
+    h = vi.vi_problem_create(2, 1, 3, (1, 1, 1, 1, 0), pmf, 0.9, 0)
+    try:
+        with pytest.raises(vi.ViError):
+            vi.vi_solve(h, -1.0, 10, torch.zeros(4, device="cuda"))
+        with pytest.raises(vi.ViError):
+            vi.vi_solve(h, 1e-4, 10, None)
+        with pytest.raises(vi.ViError):
+            vi.vi_problem_set_option(h, vi.VI_OPT_KERNEL, 99)
+    finally:
+        vi.vi_problem_destroy(h)
