@@ -42,7 +42,9 @@ WORKLOADS = {
     "cfg4": workloads.config4,
 }
 TOL = 1e-4
-MAX_ITERS = 100_000
+MAX_ITERS = 5_000
+DTYPES = {"fp32": "f32 (float-pair values)", "fp32_kahan": "f32 (float-pair values, Kahan sums)", "fp64": "f64",
+          "fp32_single": "f32 (single values, FP64 offset)"}
 L2_BYTES = 126 * 1024 * 1024
 
 
@@ -219,7 +221,8 @@ def run_native(args):
     rank, world, local = dist_setup(args.gpus)
     inst = WORKLOADS[args.workload]()
     p = inst.products[0]
-    prec = {"fp32": vi.VI_PREC_FP32, "fp32_kahan": vi.VI_PREC_FP32_KAHAN, "fp64": vi.VI_PREC_FP64}[inst.precision]
+    prec = {"fp32": vi.VI_PREC_FP32, "fp32_kahan": vi.VI_PREC_FP32_KAHAN, "fp64": vi.VI_PREC_FP64,
+            "fp32_single": vi.VI_PREC_FP32_SINGLE}[args.precision or inst.precision]
     prods = [dict(m=q.m, L=q.L, Q=q.Q, cost=q.cost, pmf=q.pmf) for q in inst.products]
     desc, keep = vi.make_desc(prods, inst.gamma, inst.issuing, prec, vi.VI_STOP_SPAN, inst.subst_rate)
     h = vi.vi_problem_create_desc(desc)
@@ -233,7 +236,7 @@ def run_native(args):
     nominal = float(n) * sizes["n_actions"] * sizes["n_outcomes"]
 
     for _ in range(args.warmup):
-        vi.vi_solve(h, TOL, MAX_ITERS, V, pol)
+        vi.vi_solve(h, TOL, args.max_iters, V, pol)
     sampler = ClockSampler(local)
     sampler.start()
     barrier_sync(world)
@@ -244,7 +247,7 @@ def run_native(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        info = vi.vi_solve(h, TOL, MAX_ITERS, V, pol, stream=stream)
+        info = vi.vi_solve(h, TOL, args.max_iters, V, pol, stream=stream)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -296,7 +299,7 @@ def run_native(args):
     e2e_iters = 0
     for _ in range(e2e_steps):
         h2 = vi.vi_problem_create_desc(desc)
-        inf2 = vi.vi_solve_host(h2, TOL, MAX_ITERS, Vh, ph)
+        inf2 = vi.vi_solve_host(h2, TOL, args.max_iters, Vh, ph)
         vi.vi_problem_destroy(h2)
         e2e_iters += inf2["iters"]
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
@@ -310,9 +313,10 @@ def run_native(args):
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * dev_s_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 span/offset)", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision or inst.precision], "data": "synthetic",
             "config": {"workload": inst.name, "states": n, "actions": sizes["n_actions"],
                        "outcomes": sizes["n_outcomes"], "sweeps_per_solve": iters[-1], "tol": TOL,
+                       "converged": bool(info["status"] == vi.VI_OK), "precision": args.precision or inst.precision,
                        "stop_rule": "span", "l2": "flushed between steps (2x L2 write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "gpu_launches": int(sum(iters) + 2 * args.steps),
@@ -340,6 +344,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle sample length (0 = skip)")
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp32_kahan", "fp64", "fp32_single"])
+    ap.add_argument("--max-iters", type=int, default=MAX_ITERS)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -64,9 +64,19 @@ enum { VI_FIFO = 0, VI_LIFO = 1 };
 /* stopping tests: span of V_i - V_{i-1} (Scenario B convergence test) or its
  * sup-norm (Scenario A convergence test); both strict "< tol". */
 enum { VI_STOP_SPAN = 0, VI_STOP_SUPNORM = 1 };
-/* value arithmetic: FP32 values relative to an FP64 offset, FP32 with
- * compensated (Kahan) summation over outcomes, or FP64 throughout. */
-enum { VI_PREC_FP32 = 0, VI_PREC_FP32_KAHAN = 1, VI_PREC_FP64 = 2 };
+/* Value arithmetic and storage.
+ *  VI_PREC_FP32        FP32 arithmetic; each value is stored as an unevaluated
+ *                      pair of floats (hi, lo), V = hi + lo, interleaved as
+ *                      float[2|S|].  Sums over outcomes are formed in FP32 from
+ *                      differences between values; the absolute value is
+ *                      rebuilt with error-free float transformations, so the
+ *                      stopping test sees no FP32 rounding noise.
+ *  VI_PREC_FP32_KAHAN  as VI_PREC_FP32 with compensated (Kahan) sums over outcomes.
+ *  VI_PREC_FP64        FP64 arithmetic and storage, double[|S|].
+ *  VI_PREC_FP32_SINGLE one float per state relative to an FP64 offset
+ *                      (V = info.offset + v), float[|S|].  Fastest; its stopping
+ *                      test is limited by FP32 rounding (about 1e-7 |V|). */
+enum { VI_PREC_FP32 = 0, VI_PREC_FP32_KAHAN = 1, VI_PREC_FP64 = 2, VI_PREC_FP32_SINGLE = 3 };
 
 /* vi_solve flags */
 enum {
@@ -98,7 +108,7 @@ typedef struct {
     int status;              /* VI_OK or VI_ENOTCONVERGED */
     double crit;             /* stopping criterion of the last sweep */
     double dmax, dmin;       /* max / min over s of V_iters(s) - V_{iters-1}(s) (absolute) */
-    double offset;           /* FP64 offset b: V_abs(s) = offset + V[s] (FP32 paths; 0 for FP64) */
+    double offset;           /* FP64 offset b: V_abs(s) = offset + V[s] (VI_PREC_FP32_SINGLE; else 0) */
     double wall_ms;          /* device time of the solve (CUDA events), sweeps + extraction */
     double updates_per_s;    /* nominal |S||A||Omega| x iters / wall time */
     int pe_iters;            /* FP64 policy-evaluation sweeps (VI_FLAG_POLICY_EVAL) */
@@ -106,7 +116,7 @@ typedef struct {
     double pe_gap;           /* max_s |V_pe(s) - V_abs(s)| after evaluation */
 } vi_solve_info;
 
-/* Create a single-product problem (FP32 values, span stopping test).
+/* Create a single-product problem (VI_PREC_FP32, span stopping test).
  * Defines: state space and transition of Scenario A (Appendix A, state
  * definition, Eq. demoor:fifo / demoor:lifo, Eq. demoor:reward).
  * cost: host double[5]; pmf: host double[dmax+1].  Copies everything it needs
@@ -125,7 +135,8 @@ vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_handle *out);
 /* Release every device and host resource of the handle.  NULL is accepted. */
 vi_status vi_problem_destroy(vi_handle h);
 
-/* Sizes: |S|, |A|, nominal |Omega| and bytes per stored value (4 or 8). */
+/* Sizes: |S|, |A|, nominal |Omega| and bytes per stored value (4 for
+ * VI_PREC_FP32_SINGLE, else 8). */
 vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
                            int *n_outcomes, int *value_bytes);
 
@@ -143,8 +154,9 @@ vi_status vi_problem_set_option(vi_handle h, int option, int value);
  * V_0 = 0 (or the warm start), stopping at the first i with the stopping
  * criterion < tol, or at max_iters; then one extraction sweep writes the
  * first argmax policy from V_i (Eq. valueiterationdetpolicy, Algorithm 1).
- * V: device float[|S|] (FP32 paths; the FP64 offset is info->offset) or
- * double[|S|] (VI_PREC_FP64), in/out.  policy: device uint8[|S|] or NULL.
+ * V: device buffer in the precision's layout (float[2|S|] pairs for
+ * VI_PREC_FP32 / _KAHAN, double[|S|] for VI_PREC_FP64, float[|S|] plus
+ * info->offset for VI_PREC_FP32_SINGLE), in/out.  policy: device uint8[|S|] or NULL.
  * info: host, out (and in: offset when VI_FLAG_WARM_START).  Blocks until the
  * solve is done.  Returns VI_OK, VI_ENOTCONVERGED (V/policy hold the last
  * iterate), VI_EINVAL (max_iters < 0, tol < 0, V NULL) or VI_ECUDA. */
@@ -152,16 +164,17 @@ vi_status vi_solve(vi_handle h, double tol, int max_iters, void *V, uint8_t *pol
                    void *stream, int flags, vi_solve_info *info);
 
 /* vi_solve on host buffers: copies the warm start (if any) host->device,
- * solves, and copies V and policy device->host.  V_host: host float[|S|] or
- * double[|S|]; policy_host: host uint8[|S|] or NULL.  Device staging buffers
+ * solves, and copies V and policy device->host.  V_host: host buffer in the
+ * precision's layout (see vi_solve); policy_host: host uint8[|S|] or NULL.  Device staging buffers
  * are owned by the handle (allocated on first use). */
 vi_status vi_solve_host(vi_handle h, double tol, int max_iters, void *V_host,
                         uint8_t *policy_host, int flags, vi_solve_info *info);
 
 /* One Bellman sweep without renormalisation: V_out(s) = max_a [rbar(s,a) +
  * gamma sum_omega P(omega) V_in(s'_omega)] and policy(s) = first argmax
- * (Eq. valueiterationdetupdate).  If V_in holds V_abs - b then V_out holds
- * V_abs' - gamma b.  V_in/V_out: device float or double [|S|] (must differ);
+ * (Eq. valueiterationdetupdate).  VI_PREC_FP32_SINGLE: if V_in holds V_abs - b
+ * then V_out holds V_abs' - gamma b.  V_in/V_out: device buffers in the
+ * precision's layout (must differ);
  * policy: device uint8[|S|] or NULL; dstats: host double[2] or NULL, receives
  * max and min of V_out - V_in.  Synchronises the stream when dstats != NULL. */
 vi_status vi_backup(vi_handle h, const void *V_in, void *V_out, uint8_t *policy,

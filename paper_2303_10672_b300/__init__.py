@@ -20,12 +20,13 @@ LIB_PATH = os.path.join(HERE, "libvi_b300.so")
 VI_OK, VI_EINVAL, VI_ENOMEM, VI_ENOTCONVERGED, VI_ETIMEOUT, VI_EBUSY, VI_ECUDA, VI_ECANCELLED = range(8)
 VI_FIFO, VI_LIFO = 0, 1
 VI_STOP_SPAN, VI_STOP_SUPNORM = 0, 1
-VI_PREC_FP32, VI_PREC_FP32_KAHAN, VI_PREC_FP64 = 0, 1, 2
+VI_PREC_FP32, VI_PREC_FP32_KAHAN, VI_PREC_FP64, VI_PREC_FP32_SINGLE = 0, 1, 2, 3
 VI_FLAG_WARM_START, VI_FLAG_NO_GRAPH, VI_FLAG_POLICY_EVAL = 1, 2, 4
 VI_OPT_KERNEL, VI_OPT_PE_MAX_ITERS = 1, 2
 VI_KERNEL_AUTO, VI_KERNEL_GENERIC, VI_KERNEL_GROUP = 0, 1, 2
 
-PRECISIONS = {"fp32": VI_PREC_FP32, "fp32_kahan": VI_PREC_FP32_KAHAN, "fp64": VI_PREC_FP64}
+PRECISIONS = {"fp32": VI_PREC_FP32, "fp32_kahan": VI_PREC_FP32_KAHAN, "fp64": VI_PREC_FP64,
+              "fp32_single": VI_PREC_FP32_SINGLE}
 
 
 class ViError(RuntimeError):

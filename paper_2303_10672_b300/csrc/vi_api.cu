@@ -106,20 +106,28 @@ static void fill_product_tables(ProdParams &P, const std::vector<double> &pmf, i
         tail[k] = t;
     }
     for (int k = 0; k < P.pn; ++k) blob.push_back(tail[k]);
-    P.off_TA = P.off_TB = 0;
+    P.off_RT = P.off_RTlo = 0;
+    P.rt_rows = (P.m - 1) * P.Q + 1;
     if (!with_reward) return;
+    // RT[R][y1]: expected one-step reward without the order cost, given y1 units in
+    // the expiring slot and R units in the other slots (T = y1 + R available):
+    //   (c_s + c_r) T - c_s E[D] - (c_h + c_s + c_r) E[(T-D)^+] + (c_h - c_w) E[W]
+    // with E[W] = E[(y1-D)^+] (FIFO) or E[(T-D)^+] - E[(R-D)^+] (LIFO).
     const double c_h = cost[1], c_s = cost[2], c_w = cost[3], c_r = cost[4];
     double mu = 0.0;
     for (int d = 0; d <= dmax; ++d) mu += (double)d * pmf[d];
     std::vector<double> G = expected_leftover(pmf, P.tmax);
-    P.off_TA = (int)blob.size();
-    for (int T = 0; T <= P.tmax; ++T) {
-        double A = (c_s + c_r) * T - c_s * mu - (c_h + c_s + c_r) * G[T];
-        if (issuing == VI_LIFO) A += (c_h - c_w) * G[T];
-        blob.push_back(A);
-    }
-    P.off_TB = (int)blob.size();
-    for (int y = 0; y <= P.tmax; ++y) blob.push_back(issuing == VI_LIFO ? -(c_h - c_w) * G[y] : (c_h - c_w) * G[y]);
+    std::vector<double> rt((size_t)P.rt_rows * P.G);
+    for (int R = 0; R < P.rt_rows; ++R)
+        for (int y1 = 0; y1 < P.G; ++y1) {
+            const int T = y1 + R;
+            const double ew = (issuing == VI_LIFO) ? G[T] - G[R] : G[y1];
+            rt[(size_t)R * P.G + y1] = (c_s + c_r) * T - c_s * mu - (c_h + c_s + c_r) * G[T] + (c_h - c_w) * ew;
+        }
+    P.off_RT = (int)blob.size();
+    blob.insert(blob.end(), rt.begin(), rt.end());
+    P.off_RTlo = (int)blob.size();
+    for (double v : rt) blob.push_back(v - (double)(float)v);
 }
 
 static double binom(int n, int k, double rho) {
@@ -188,6 +196,7 @@ static void fill_two_product_tables(KernelParams &kp, const vi_problem_desc &d, 
             blob.push_back(h);
         }
     // H2[T1][ys2][T2]: product-2 terms with substitution + product-1 shortage
+    const size_t h1_begin = (size_t)kp.off_H1, h1_len = blob.size() - h1_begin;
     kp.off_H2 = (int)blob.size();
     const int nT2 = P2.tmax + 1;
     const int ny2 = lifo ? nT2 : P2.G;
@@ -222,10 +231,22 @@ static void fill_two_product_tables(KernelParams &kp, const vi_problem_desc &d, 
                         int car = T2 - iss - W;
                         h += pz * (-c2[1] * car - c2[3] * W + (c2[4] + c1[2]) * iss);
                     }
-                    h += -c2[2] * eshort2 - c1[2] * (En1[T1] - emin2);
+                    h += -c2[2] * eshort2 - c1[2] * (En1[T1] + emin2);   // short1 = n1 - iss2 + own2
                 }
                 blob.push_back(h);
             }
+    // low halves for the float-pair kernels
+    const size_t h2_begin = (size_t)kp.off_H2, h2_len = blob.size() - h2_begin;
+    kp.off_H1lo = (int)blob.size();
+    for (size_t i = 0; i < h1_len; ++i) {
+        const double v = blob[h1_begin + i];
+        blob.push_back(v - (double)(float)v);
+    }
+    kp.off_H2lo = (int)blob.size();
+    for (size_t i = 0; i < h2_len; ++i) {
+        const double v = blob[h2_begin + i];
+        blob.push_back(v - (double)(float)v);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -286,7 +307,7 @@ extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_hand
     }
     if (!(d.gamma > 0.0 && d.gamma <= 1.0)) return vi_fail(VI_EINVAL, "gamma must be in (0, 1]");
     if (d.issuing != VI_FIFO && d.issuing != VI_LIFO) return vi_fail(VI_EINVAL, "issuing must be FIFO or LIFO");
-    if (d.precision < VI_PREC_FP32 || d.precision > VI_PREC_FP64) return vi_fail(VI_EINVAL, "bad precision");
+    if (d.precision < VI_PREC_FP32 || d.precision > VI_PREC_FP32_SINGLE) return vi_fail(VI_EINVAL, "bad precision");
     if (d.stop_rule != VI_STOP_SPAN && d.stop_rule != VI_STOP_SUPNORM) return vi_fail(VI_EINVAL, "bad stop_rule");
     if (d.n_products == 2) {
         if (d.L[0] != 1 || d.L[1] != 1) return vi_fail(VI_EINVAL, "two products need L = 1");
@@ -326,14 +347,13 @@ extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_hand
         h->n_outcomes = (d.dmax[0] + 1) * (d.dmax[1] + 1);
     }
     kp.n_tables = (int)blob.size();
-    // the shared-memory part of the tables must fit one block
+    // generic kernels stage the tables in shared memory when they fit (FP64 size)
     const int n_smem = (d.n_products == 2) ? kp.off_H1 : kp.n_tables;
-    if ((size_t)n_smem * 8 > 200 * 1024) {
-        delete h;
-        return vi_fail(VI_EINVAL, "expectation tables (%d entries) exceed shared memory", n_smem);
-    }
-    h->value_bytes = d.precision == VI_PREC_FP64 ? 8 : 4;
-    h->use_group = (d.precision == VI_PREC_FP32) && group_supported(kp);
+    kp.tab_in_smem = ((size_t)n_smem * 8 <= 160 * 1024) ? 1 : 0;
+    h->vk = (d.precision == VI_PREC_FP64) ? VK_DOUBLE : (d.precision == VI_PREC_FP32_SINGLE) ? VK_SINGLE : VK_PAIR;
+    h->kahan = (d.precision == VI_PREC_FP32_KAHAN) ? 1 : 0;
+    h->value_bytes = (h->vk == VK_SINGLE) ? 4 : 8;
+    h->use_group = group_supported(kp, h->vk, h->kahan);
     std::vector<float> fblob(blob.size());
     for (size_t i = 0; i < blob.size(); ++i) fblob[i] = (float)blob[i];
 
@@ -358,7 +378,7 @@ extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_hand
         return vi_fail(VI_ECUDA, "state upload: %s", cudaGetErrorString(e));
     }
     kp.st = h->d_state;
-    kp.tables = (d.precision == VI_PREC_FP64) ? (const void *)h->d_tab_d : (const void *)h->d_tab_f;
+    kp.tables = (h->vk == VK_DOUBLE) ? (const void *)h->d_tab_d : (const void *)h->d_tab_f;
     *out = h;
     return VI_OK;
 }
@@ -422,13 +442,14 @@ extern "C" vi_status vi_problem_set_option(vi_handle h, int option, int value) {
     if (!h) return vi_fail(VI_EINVAL, "null handle");
     if (option == VI_OPT_KERNEL) {
         if (value == VI_KERNEL_AUTO) {
-            h->use_group = (h->desc.precision == VI_PREC_FP32) && group_supported(h->kp);
+            h->use_group = group_supported(h->kp, h->vk, h->kahan);
         } else if (value == VI_KERNEL_GENERIC) {
             h->use_group = false;
         } else if (value == VI_KERNEL_GROUP) {
-            if (!(h->desc.precision == VI_PREC_FP32 && group_supported(h->kp)))
-                return vi_fail(VI_EINVAL, "the factorised kernel needs one FP32 product with 2 <= Q+1 <= %d",
-                               kMaxGroupG);
+            if (!group_supported(h->kp, h->vk, h->kahan))
+                return vi_fail(VI_EINVAL,
+                               "the factorised kernel needs one product, FP32 or FP32_SINGLE precision and "
+                               "2 <= Q+1 <= %d", kMaxGroupG);
             h->use_group = true;
         } else {
             return vi_fail(VI_EINVAL, "bad kernel choice %d", value);
@@ -476,7 +497,7 @@ static vi_status build_graph(vi_problem *h) {
 
     LaunchDesc ld_init, ld_sweep;
     CUDA_TRY(describe_solve_init(h->kp.nS, ld_init));
-    CUDA_TRY(describe_sweep(h->kp, h->desc.precision, h->use_group ? 1 : 0, ld_sweep));
+    CUDA_TRY(describe_sweep(h->kp, h->vk, h->kahan, h->use_group ? 1 : 0, ld_sweep));
     h->args_kp = h->kp;
     h->args_nS = h->kp.nS;
     h->args_mode_sweep = MODE_SWEEP;
@@ -531,7 +552,7 @@ static vi_status build_graph(vi_problem *h) {
 static vi_status run_host_loop(vi_problem *h, cudaStream_t s) {
     LaunchDesc ld_init, ld_sweep;
     CUDA_TRY(describe_solve_init(h->kp.nS, ld_init));
-    CUDA_TRY(describe_sweep(h->kp, h->desc.precision, h->use_group ? 1 : 0, ld_sweep));
+    CUDA_TRY(describe_sweep(h->kp, h->vk, h->kahan, h->use_group ? 1 : 0, ld_sweep));
     KernelParams kp = h->kp;
     uint32_t nS = kp.nS;
     int mode_sweep = MODE_SWEEP, mode_extract = MODE_EXTRACT;
@@ -583,7 +604,7 @@ extern "C" vi_status vi_solve(vi_handle h, double tol, int max_iters, void *V, u
     hs->gamma = h->desc.gamma;
     hs->max_iters = max_iters;
     hs->stop_rule = h->desc.stop_rule;
-    hs->normalise = h->desc.precision != VI_PREC_FP64;
+    hs->normalise = (h->vk == VK_SINGLE) ? 1 : 0;
     hs->use_cond = use_graph ? 1 : 0;
     hs->cond = h->cond;
     hs->warm = (flags & VI_FLAG_WARM_START) ? 1 : 0;
@@ -623,11 +644,7 @@ extern "C" vi_status vi_solve(vi_handle h, double tol, int max_iters, void *V, u
             CUDA_TRY(cudaMalloc(&h->d_pe[1], (size_t)n * sizeof(double)));
         }
         // start from V_abs of the solve, evaluate the extracted policy in FP64
-        if (h->value_bytes == 4) {
-            CUDA_TRY(launch_to_fp64((const float *)V, info->offset, h->d_pe[0], n, s));
-        } else {
-            CUDA_TRY(cudaMemcpyAsync(h->d_pe[0], V, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
-        }
+        CUDA_TRY(launch_to_fp64(V, h->vk, info->offset, h->d_pe[0], n, s));
         CUDA_TRY(cudaMemcpyAsync(h->d_pe[1], h->d_pe[0], (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
         int it = 0;
         double delta = 0.0;
@@ -671,7 +688,7 @@ extern "C" vi_status vi_backup(vi_handle h, const void *V_in, void *V_out, uint8
     if (!V_in || !V_out || V_in == V_out) return vi_fail(VI_EINVAL, "V_in and V_out must be distinct buffers");
     cudaStream_t s = (cudaStream_t)stream;
     LaunchDesc ld;
-    CUDA_TRY(describe_sweep(h->kp, h->desc.precision, h->use_group ? 1 : 0, ld));
+    CUDA_TRY(describe_sweep(h->kp, h->vk, h->kahan, h->use_group ? 1 : 0, ld));
     KernelParams kp = h->kp;
     int mode = MODE_PLAIN;
     const void *vin = V_in;

@@ -14,6 +14,8 @@ struct vi_problem {
     vib::KernelParams kp;              // tables / state pointers filled in
     int n_outcomes = 0;                // nominal |Omega|
     int value_bytes = 4;
+    int vk = 0;                        // value kind (VK_SINGLE / VK_PAIR / VK_DOUBLE)
+    int kahan = 0;                     // compensated sums over outcomes
     bool use_group = false;            // factorised kernel for this instance
     int pe_max_iters = 100000;
     // device resources

@@ -38,8 +38,10 @@ struct ProdParams {
     int off_p;            // p[k]     = P(D = k), zero beyond dmax        (len pn)
     int off_F;            // F[k]     = P(D <= k), one beyond dmax         (len pn)
     int off_tail;         // tail[k]  = P(D >= k), zero beyond dmax        (len pn)
-    int off_TA;           // TA[T]    expected reward part depending on T (len tmax+1)
-    int off_TB;           // TB[y]    expected waste part (FIFO: y = Y_1, LIFO: y = R), len tmax+1
+    int off_RT;           // RT[R * G + y1]: expected reward without the order cost, given
+                          // y1 units in the expiring slot and R in the others (FP64-built)
+    int off_RTlo;         // FP32 blobs: RT - fl32(RT), the low half of the pair (zero in FP64 blobs)
+    int rt_rows;          // R ranges over 0..rt_rows-1 = (m-1)Q
     int pn;               // length of p / F / tail
     double c_o;           // order cost per unit
 };
@@ -55,12 +57,14 @@ struct KernelParams {
     double gamma;
     const void *tables;   // device table blob (float or double, see precision)
     int n_tables;         // elements in the blob
+    int tab_in_smem;      // generic kernels stage the (per-block) tables in shared memory
     // two-product extras (offsets into the blob)
     int off_M;            // M[T1][z]: mass of (d1 >= T1, product-2 demand z), row length zlen
     int off_Mc;           // cumulative of M rows
     int off_Mt;           // tail of M rows
     int off_H1;           // H1[y1][T1]  expected product-1 reward terms, row length (tmax1+1)
     int off_H2;           // H2[T1][y2][T2] expected product-2 + substitution terms
+    int off_H1lo, off_H2lo;   // low halves of H1 / H2 (float blobs)
     int zlen;             // dmax1 + dmax2 + 1
     SolveState *st;       // solve bookkeeping
 };
@@ -81,7 +85,7 @@ struct SolveState {
     int normalise;                // FP32 paths subtract c each sweep
     int use_cond;                 // set the graph conditional from the last block
     int warm;                     // keep V and the offset given by the caller
-    int value_bytes;              // 4 (float) or 8 (double)
+    int value_bytes;              // 4 (float) or 8 (double or float pair)
     unsigned long long cond;      // cudaGraphConditionalHandle
     // running state
     unsigned long long key_max;   // order-preserving encoding of max(v_i - v_{i-1})

@@ -1,19 +1,30 @@
 // vi_kernels.cu -- sm_103a kernels of the value-iteration hot path.
 //
-//   sweep_group_kernel    factorised Bellman backup (one thread per rest index r,
-//                         all G = Q+1 values of the expiring slot in registers)
-//   sweep_generic_kernel  one thread per state, float / double / Kahan, one or
-//                         two products
+//   sweep_group_kernel    factorised Bellman backup: one thread per rest index r,
+//                         the G = Q+1 values of the expiring slot in registers
+//   sweep_generic_kernel  one thread per state; one or two products
 //   next_states_kernel    dump of T(s, a, omega) indices (bit-exact checks)
 //   policy_eval_kernel    FP64 fixed-policy sweep
 //   rollout_kernel        Philox4x32-10 policy rollouts with FP64 returns
 //
 // Bellman backup (Eq. valueiterationdetupdate):
 //   V'(s) = max_a [ rbar(s,a) + gamma * sum_omega P(omega) V(s'(s,a,omega)) ]
-// with the expected one-step reward rbar taken from FP64-built expectation tables
-// (the reward of Eq. demoor:reward is affine in issued / short / wasted / carried
-// units, so its expectation only needs E[(y - D)^+] tables).
+// The expected one-step reward rbar comes from FP64-built tables: the reward of
+// Eq. demoor:reward is affine in issued / short / wasted / carried units, so its
+// expectation only needs E[(y - D)^+].
+//
+// Value kinds:
+//   VK_SINGLE  float per state relative to an FP64 offset b (V_abs = b + v); each
+//              sweep subtracts a constant so that v stays near zero.
+//   VK_PAIR    an unevaluated float pair per state (V_abs = hi + lo).  All FP32
+//              arithmetic works on differences V(s') - V(ref) between states
+//              (unchanged when V shifts uniformly, so rounding does not add noise
+//              to V_i - V_{i-1}); only the final absolute value is formed with
+//              error-free TwoSum / TwoProd steps.
+//   VK_DOUBLE  FP64 per state.
 #include <math.h>
+
+#include <type_traits>
 
 #include "vi_common.cuh"
 #include "vi_kernels.h"
@@ -21,60 +32,83 @@
 namespace vib {
 
 // ---------------------------------------------------------------------------
+// error-free float transformations (never contracted into FMAs)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {   // |a| >= |b|
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// difference of two float pairs as an FP32 number (correctly rounded when the
+// high parts are within a factor of two of each other)
+__device__ __forceinline__ float pair_diff(float2 g, float2 ref) {
+    return __fadd_rn(__fsub_rn(g.x, ref.x), __fsub_rn(g.y, ref.y));
+}
+
+// ---------------------------------------------------------------------------
 // block reductions of the per-sweep change statistics
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void warp_minmax(double &mx, double &mn) {
+template <typename T>
+__device__ __forceinline__ void warp_minmax(T &mx, T &mn) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
     }
 }
 
 // All threads of the block call this.  Folds (mx, mn) of the block into the
-// global accumulators; the last block of the grid then runs finalize().
-__device__ void block_reduce_and_finalize(double mx, double mn, SolveState *st, int mode) {
-    __shared__ double s_mx[32], s_mn[32];
+// global accumulators; the last block of the grid then finalises the sweep.
+template <typename T>
+__device__ void block_reduce_and_finalize(T mx, T mn, SolveState *st, int mode) {
+    __shared__ T s_mx[32], s_mn[32];
     __shared__ int s_last;
-    warp_minmax(mx, mn);
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    warp_minmax<T>(mx, mn);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
         s_mx[wid] = mx;
         s_mn[wid] = mn;
     }
     __syncthreads();
     if (wid == 0) {
-        int nw = (blockDim.x + 31) >> 5;
-        mx = lane < nw ? s_mx[lane] : -INFINITY;
-        mn = lane < nw ? s_mn[lane] : INFINITY;
-        warp_minmax(mx, mn);
+        const int nw = (blockDim.x + 31) >> 5;
+        mx = lane < nw ? s_mx[lane] : (T)-INFINITY;
+        mn = lane < nw ? s_mn[lane] : (T)INFINITY;
+        warp_minmax<T>(mx, mn);
         if (lane == 0) {
-            atomicMax(&st->key_max, dkey(mx));
-            atomicMin(&st->key_min, dkey(mn));
+            atomicMax(&st->key_max, dkey((double)mx));
+            atomicMin(&st->key_min, dkey((double)mn));
             __threadfence();
-            unsigned prev = atomicAdd(&st->blocks_done, 1u);
+            const unsigned prev = atomicAdd(&st->blocks_done, 1u);
             s_last = (prev == gridDim.x - 1);
         }
     }
     __syncthreads();
     if (!s_last || threadIdx.x != 0) return;
     __threadfence();
-    double vmax = dkey_inv(atomicAdd(&st->key_max, 0ull));
-    double vmin = dkey_inv(atomicAdd(&st->key_min, 0ull));
+    const double vmax = dkey_inv(atomicAdd(&st->key_max, 0ull));
+    const double vmin = dkey_inv(atomicAdd(&st->key_min, 0ull));
     if (mode == MODE_SWEEP) {
-        double b_old = st->offset;
-        double b_new = st->normalise ? (st->gamma * b_old + (double)st->c_cur) : 0.0;
-        double db = b_new - b_old;
+        const double b_old = st->offset;
+        const double b_new = st->normalise ? (st->gamma * b_old + (double)st->c_cur) : 0.0;
+        const double db = b_new - b_old;
         st->offset = b_new;
         st->dmax_abs = db + vmax;
         st->dmin_abs = db + vmin;
-        double crit = (st->stop_rule == 0) ? (vmax - vmin)
-                                           : fmax(fabs(st->dmax_abs), fabs(st->dmin_abs));
+        const double crit = (st->stop_rule == 0) ? (vmax - vmin) : fmax(fabs(st->dmax_abs), fabs(st->dmin_abs));
         st->crit = crit;
         st->iter += 1;
-        int conv = crit < st->tol;
+        const int conv = crit < st->tol;
         st->converged = conv;
-        int go = (!conv) && (st->iter < st->max_iters);
+        const int go = (!conv) && (st->iter < st->max_iters);
         st->keep_going = go;
         if (st->normalise) st->c_cur = st->c_next;
         if (st->use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)st->cond, go ? 1u : 0u);
@@ -89,36 +123,34 @@ __device__ void block_reduce_and_finalize(double mx, double mn, SolveState *st, 
     st->blocks_done = 0u;
 }
 
-// resolve the buffers of a launch
-template <typename T>
+// buffers of one launch
 struct Bufs {
-    const T *vin;
-    T *vout;        // may be null (extraction without copy)
-    uint8_t *pol;   // may be null
-    T cnorm;
+    const void *vin;
+    void *vout;      // may be null (extraction without copy)
+    uint8_t *pol;    // may be null
+    float cnorm;     // VK_SINGLE normalisation constant
 };
 
-template <typename T>
-__device__ __forceinline__ bool resolve_bufs(const SolveState *st, int mode, const T *vin_arg, T *vout_arg,
-                                             uint8_t *pol_arg, Bufs<T> &b) {
+__device__ __forceinline__ bool resolve_bufs(const SolveState *st, int mode, const void *vin_arg, void *vout_arg,
+                                             uint8_t *pol_arg, Bufs &b) {
     if (mode == MODE_SWEEP) {
         if (!st->keep_going) return false;
-        int it = st->iter;
-        b.vin = (const T *)st->buf[it & 1];
-        b.vout = (T *)st->buf[(it + 1) & 1];
+        const int it = st->iter;
+        b.vin = st->buf[it & 1];
+        b.vout = st->buf[(it + 1) & 1];
         b.pol = nullptr;
-        b.cnorm = st->normalise ? (T)st->c_cur : (T)0;
+        b.cnorm = st->normalise ? st->c_cur : 0.f;
     } else if (mode == MODE_EXTRACT) {
-        int it = st->iter;
-        b.vin = (const T *)st->buf[it & 1];
-        b.vout = (it & 1) ? (T *)st->buf[0] : nullptr;   // result must end in the caller's buffer
+        const int it = st->iter;
+        b.vin = st->buf[it & 1];
+        b.vout = (it & 1) ? st->buf[0] : nullptr;   // the result must end in the caller's buffer
         b.pol = st->policy;
-        b.cnorm = (T)0;
+        b.cnorm = 0.f;
     } else {
         b.vin = vin_arg;
         b.vout = vout_arg;
         b.pol = pol_arg;
-        b.cnorm = (T)0;
+        b.cnorm = 0.f;
     }
     return true;
 }
@@ -129,8 +161,8 @@ __device__ __forceinline__ void load_tables(T *s_tab, const T *g_tab, int n) {
     __syncthreads();
 }
 
-// packed rest-slot counts and their sum for action a (the order joins the
-// slots as Z_{m-1} when L == 1 and m >= 2)
+// packed rest-slot counts and their sum for action a (the order joins the slots
+// as Z_{m-1} when L == 1 and m >= 2)
 __device__ __forceinline__ void slots_for_action(const ProdParams &P, const RestInfo &ri, int a,
                                                  unsigned long long &packed, int &R) {
     packed = ri.packed;
@@ -141,29 +173,65 @@ __device__ __forceinline__ void slots_for_action(const ProdParams &P, const Rest
     }
 }
 
+// a pair (hi, lo) += (xh, xl), high parts added error-free
+__device__ __forceinline__ void pair_add(float &h, float &l, float xh, float xl) {
+    float s, e;
+    two_sum(h, xh, s, e);
+    h = s;
+    l = __fadd_rn(e, __fadd_rn(l, xl));
+}
+
+// gamma * (ref - R0) - c_o a as a pair
+__device__ __forceinline__ void action_base(float gam, float2 ref, float2 R0, float ca, float &bh, float &bl) {
+    float dh, de;
+    two_sum(ref.x, -R0.x, dh, de);
+    const float dl = __fadd_rn(de, __fsub_rn(ref.y, R0.y));
+    float ph, pe;
+    two_prod(gam, dh, ph, pe);
+    const float pl = __fmaf_rn(gam, dl, pe);
+    float s, e;
+    two_sum(ca, ph, s, e);
+    bh = s;
+    bl = __fadd_rn(e, pl);
+}
+
+// gamma * R0 + (bh, bl), normalised pair
+__device__ __forceinline__ float2 pair_finish(float gam, float2 R0, float bh, float bl) {
+    float ph, pe;
+    two_prod(gam, R0.x, ph, pe);
+    const float pl = __fmaf_rn(gam, R0.y, pe);
+    float sh, se;
+    two_sum(ph, bh, sh, se);
+    const float lo = __fadd_rn(se, __fadd_rn(pl, bl));
+    float vh, vl;
+    fast_two_sum(sh, lo, vh, vl);
+    return make_float2(vh, vl);
+}
+
 // ===========================================================================
-// factorised single-product sweep (FP32): thread = rest index r, registers hold
-// the G values of the expiring slot x = X_1 (or P_1 when m == 1).
+// factorised single-product sweep: thread = rest index r (digits 1..K-1 of s),
+// registers hold the G values of the expiring slot x = digit 0 of s.
 //   FIFO: C(x) = sum_d p_d g(clamp(d - x, 0, R))   (x is issued first)
 //   LIFO: C    = sum_d p_d g(min(d, R))            (x is issued last)
-// where g(e) = V[s'(r, a, e)] follows the walker.  The FIFO correlation is
-// evaluated in chunks of G demands with a register window of gathered values.
+// g(e) = V[s'(r, a, e)] follows the walker.  The FIFO correlation runs in
+// chunks of G demands over a register window of gathered values.
 // ===========================================================================
-template <int G, int LIFO>
+template <int G, int LIFO, int VK>
 __global__ void __launch_bounds__(kGroupThreads)
-sweep_group_kernel(KernelParams kp, int mode, const float *vin_arg, float *vout_arg, uint8_t *pol_arg) {
+sweep_group_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr bool PAIR = (VK == VK_PAIR);
     SolveState *st = kp.st;
-    Bufs<float> B;
-    if (!resolve_bufs<float>(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
+    Bufs B;
+    if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
     const ProdParams &P = kp.p[0];
     float *s_tab = (float *)smem_raw;
-    float *s_out = s_tab + ((kp.n_tables + 3) & ~3);
-    uint8_t *s_pol = (uint8_t *)(s_out + kGroupThreads * G);
+    float *s_out = s_tab + ((kp.n_tables + 3) & ~3);          // PAIR: float2 per state
+    uint8_t *s_pol = (uint8_t *)(s_out + kGroupThreads * G * (PAIR ? 2 : 1));
     load_tables<float>(s_tab, (const float *)kp.tables, kp.n_tables);
     const float *s_p = s_tab + P.off_p;
-    const float *s_TA = s_tab + P.off_TA;
-    const float *s_TB = s_tab + P.off_TB;
+    const float *s_RT = s_tab + P.off_RT;
+    const float *s_RTlo = s_tab + P.off_RTlo;
 
     const uint32_t nR = P.nS / (uint32_t)G;
     const uint32_t r0 = blockIdx.x * (uint32_t)kGroupThreads;
@@ -173,26 +241,38 @@ sweep_group_kernel(KernelParams kp, int mode, const float *vin_arg, float *vout_
     const int dmax = P.dmax;
     const int nch = (dmax + G) / G;      // chunks of G demands covering 0..dmax
 
-    float best[G];
+    float bh[G], bl[G];
     int arg[G];
 #pragma unroll
     for (int x = 0; x < G; ++x) {
-        best[x] = -INFINITY;
+        bh[x] = -INFINITY;
+        bl[x] = 0.f;
         arg[x] = 0;
     }
+    float2 R0 = make_float2(0.f, 0.f);
     if (r < nR) {
-        RestInfo ri = decode_rest(r, P);
-        const float *V = B.vin;
+        const RestInfo ri = decode_rest(r, P);
+        const float *V1 = (const float *)B.vin;
+        const float2 *V2 = (const float2 *)B.vin;
+        if (PAIR) R0 = __ldg(V2 + r);   // s'_0 of action 0
         for (int a = 0; a < G; ++a) {
             unsigned long long packed;
             int R;
             slots_for_action(P, ri, a, packed, R);
             Walker wk;
-            walker_init(wk, r + (uint32_t)a * P.w_top, packed, P.m - 1, P.cb, LIFO, P.w_zt);
+            const uint32_t idx0 = r + (uint32_t)a * P.w_top;
+            walker_init(wk, idx0, packed, P.m - 1, P.cb, LIFO, P.w_zt);
+            float2 ref = make_float2(0.f, 0.f);
+            if (PAIR) ref = __ldg(V2 + idx0);
+            // gathered value: absolute (single) or relative to ref (pair)
+            auto gather = [&](uint32_t i) -> float {
+                if (PAIR) return pair_diff(__ldg(V2 + i), ref);
+                return __ldg(V1 + i);
+            };
             float acc[G];
+            const float g0 = PAIR ? 0.f : gather(idx0);
             if (!LIFO) {
                 float gprev[G];
-                float g0 = __ldg(V + wk.idx);
 #pragma unroll
                 for (int x = 0; x < G; ++x) {
                     acc[x] = 0.f;
@@ -204,10 +284,10 @@ sweep_group_kernel(KernelParams kp, int mode, const float *vin_arg, float *vout_
                     float gcur[G];
 #pragma unroll
                     for (int j = 0; j < G; ++j) {
-                        int e = d0 + j;
+                        const int e = d0 + j;
                         if (e >= 1 && e <= R) {
                             walker_step(wk, P.cb, 0, (uint32_t)G);
-                            glast = __ldg(V + wk.idx);
+                            glast = gather(wk.idx);
                         }
                         gcur[j] = glast;
                     }
@@ -226,56 +306,100 @@ sweep_group_kernel(KernelParams kp, int mode, const float *vin_arg, float *vout_
                 }
             } else {
                 float c = 0.f;
-                float g = __ldg(V + wk.idx);
+                float g = g0;
                 for (int d = 0; d <= dmax; ++d) {
                     if (d >= 1 && d <= R) {
                         walker_step(wk, P.cb, 1, (uint32_t)G);
-                        g = __ldg(V + wk.idx);
+                        g = gather(wk.idx);
                     }
                     c = fmaf(s_p[d], g, c);
                 }
 #pragma unroll
                 for (int x = 0; x < G; ++x) acc[x] = c;
             }
-            const float base = -c_o * (float)a;
+            const float *rt = s_RT + R * G;
+            if (PAIR) {
+                float Bh, Bl;
+                action_base(gam, ref, R0, __fmul_rn(-c_o, (float)a), Bh, Bl);
+                const float *rtl = s_RTlo + R * G;
 #pragma unroll
-            for (int x = 0; x < G; ++x) {
-                const float rb = base + s_TA[x + R] + s_TB[LIFO ? R : x];
-                const float q = fmaf(gam, acc[x], rb);
-                if (q > best[x]) {
-                    best[x] = q;
-                    arg[x] = a;
+                for (int x = 0; x < G; ++x) {
+                    float qh = Bh, ql = Bl;
+                    pair_add(qh, ql, rt[x], rtl[x]);
+                    ql = __fmaf_rn(gam, acc[x], ql);
+                    const float diff = __fadd_rn(__fsub_rn(qh, bh[x]), __fsub_rn(ql, bl[x]));
+                    if (diff > 0.f) {
+                        bh[x] = qh;
+                        bl[x] = ql;
+                        arg[x] = a;
+                    }
+                }
+            } else {
+                const float base = -c_o * (float)a;
+#pragma unroll
+                for (int x = 0; x < G; ++x) {
+                    const float q = fmaf(gam, acc[x], base + rt[x]);
+                    if (q > bh[x]) {
+                        bh[x] = q;
+                        arg[x] = a;
+                    }
                 }
             }
         }
-        if (r == 0 && mode == MODE_SWEEP) st->c_next = best[0];
+        if (!PAIR && r == 0 && mode == MODE_SWEEP) st->c_next = bh[0];
     }
-    // stage the block's G*kGroupThreads contiguous states through shared memory
+    // stage the block's G * kGroupThreads contiguous states through shared memory
+    if (PAIR) {
+        float2 *s_out2 = (float2 *)s_out;
 #pragma unroll
-    for (int x = 0; x < G; ++x) {
-        s_out[threadIdx.x * G + x] = best[x];
-        s_pol[threadIdx.x * G + x] = (uint8_t)arg[x];
+        for (int x = 0; x < G; ++x) {
+            s_out2[threadIdx.x * G + x] = (r < nR) ? pair_finish(gam, R0, bh[x], bl[x]) : make_float2(0.f, 0.f);
+            s_pol[threadIdx.x * G + x] = (uint8_t)arg[x];
+        }
+    } else {
+#pragma unroll
+        for (int x = 0; x < G; ++x) {
+            s_out[threadIdx.x * G + x] = bh[x];
+            s_pol[threadIdx.x * G + x] = (uint8_t)arg[x];
+        }
     }
     __syncthreads();
     const uint32_t s0 = r0 * (uint32_t)G;
     const uint32_t nblk = kGroupThreads * G;
-    double mx = -INFINITY, mn = INFINITY;
+    float mx = -INFINITY, mn = INFINITY;
     for (uint32_t i = threadIdx.x; i < nblk; i += kGroupThreads) {
         const uint32_t s = s0 + i;
         if (s >= P.nS) break;
-        if (mode == MODE_EXTRACT) {
-            if (B.vout) B.vout[s] = B.vin[s];
+        if (PAIR) {
+            const float2 *vin2 = (const float2 *)B.vin;
+            float2 *vout2 = (float2 *)B.vout;
+            if (mode == MODE_EXTRACT) {
+                if (vout2) vout2[s] = vin2[s];
+            } else {
+                const float2 vnew = ((const float2 *)s_out)[i];
+                const float2 vold = vin2[s];
+                vout2[s] = vnew;
+                const float dlt = pair_diff(vnew, vold);
+                mx = fmaxf(mx, dlt);
+                mn = fminf(mn, dlt);
+            }
         } else {
-            const float vnew = s_out[i] - B.cnorm;
-            const float vold = B.vin[s];
-            B.vout[s] = vnew;
-            const double dlt = (double)vnew - (double)vold;
-            mx = fmax(mx, dlt);
-            mn = fmin(mn, dlt);
+            const float *vin1 = (const float *)B.vin;
+            float *vout1 = (float *)B.vout;
+            if (mode == MODE_EXTRACT) {
+                if (vout1) vout1[s] = vin1[s];
+            } else {
+                const float vnew = s_out[i] - B.cnorm;
+                const float vold = vin1[s];
+                vout1[s] = vnew;
+                const float dlt = vnew - vold;
+                mx = fmaxf(mx, dlt);
+                mn = fminf(mn, dlt);
+            }
         }
         if (B.pol) B.pol[s] = s_pol[i];
     }
-    if (mode != MODE_EXTRACT) block_reduce_and_finalize(mx, mn, st, mode);
+    if (mode != MODE_EXTRACT) block_reduce_and_finalize<float>(mx, mn, st, mode);
 }
 
 // ===========================================================================
@@ -284,11 +408,14 @@ sweep_group_kernel(KernelParams kp, int mode, const float *vin_arg, float *vout_
 template <typename T, int KAHAN>
 struct Acc {
     T s, c;
-    __device__ __forceinline__ void init() { s = (T)0; c = (T)0; }
+    __device__ __forceinline__ void init() {
+        s = (T)0;
+        c = (T)0;
+    }
     __device__ __forceinline__ void add(T w, T v) {
         if (KAHAN) {
-            T y = w * v - c;
-            T t = s + y;
+            const T y = w * v - c;
+            const T t = s + y;
             c = (t - s) - y;
             s = t;
         } else {
@@ -297,39 +424,50 @@ struct Acc {
     }
 };
 
-// expectation of g over the rest-demand e for one product:
-//   FIFO: e = clamp(d - y1, 0, R); LIFO: e = min(d, R); g(e) = V[base + mult * s'(e)]
-// w-tables (pw = point mass, cw = cumulative, tw = tail) over d; entries at or beyond
-// n (the support length) are zero mass and are skipped
-template <typename T, int KAHAN>
-__device__ __forceinline__ void expect_rest(Acc<T, KAHAN> &acc, const T *V, uint32_t base, uint32_t mult,
-                                            Walker wk, int cb, int lifo, uint32_t G, int y1, int R,
-                                            const T *pw, const T *cw, const T *tw, int n, T scale) {
-    // the index arithmetic only ever steps while e <= R
+// value accessors: plain load, or pair relative to a reference state
+template <typename T>
+struct GetPlain {
+    const T *V;
+    __device__ __forceinline__ T operator()(uint32_t i) const { return V[i]; }
+};
+struct GetRel {
+    const float2 *V;
+    float2 ref;
+    __device__ __forceinline__ float operator()(uint32_t i) const { return pair_diff(V[i], ref); }
+};
+
+// expectation of g over the rest-demand e of one product:
+//   FIFO: e = clamp(d - y1, 0, R); LIFO: e = min(d, R); g(e) = get(base + mult * s'(e))
+// w-tables over d: pw point mass, cw cumulative, tw tail; entries at or beyond n
+// (the support length) carry no mass and are skipped.
+template <typename T, int KAHAN, class Get>
+__device__ __forceinline__ void expect_rest(Acc<T, KAHAN> &acc, const Get &get, uint32_t base, uint32_t mult,
+                                            Walker wk, int cb, int lifo, uint32_t G, int y1, int R, const T *pw,
+                                            const T *cw, const T *tw, int n, T scale) {
     if (!lifo) {
         if (R == 0) {
-            acc.add(scale * tw[0], V[base + mult * wk.idx]);
+            acc.add(scale * tw[0], get(base + mult * wk.idx));
             return;
         }
-        int y = y1 < n - 1 ? y1 : n - 1;
-        acc.add(scale * cw[y], V[base + mult * wk.idx]);
+        const int y = y1 < n - 1 ? y1 : n - 1;
+        acc.add(scale * cw[y], get(base + mult * wk.idx));
         int e = 1;
         for (; e < R; ++e) {
             if (y1 + e >= n) break;
             walker_step(wk, cb, 0, G);
-            acc.add(scale * pw[y1 + e], V[base + mult * wk.idx]);
+            acc.add(scale * pw[y1 + e], get(base + mult * wk.idx));
         }
         if (y1 + R < n) {
             for (; e <= R; ++e) walker_step(wk, cb, 0, G);
-            acc.add(scale * tw[y1 + R], V[base + mult * wk.idx]);
+            acc.add(scale * tw[y1 + R], get(base + mult * wk.idx));
         }
     } else {
         int d = 0;
         for (; d < R && d < n; ++d) {
-            acc.add(scale * pw[d], V[base + mult * wk.idx]);
+            acc.add(scale * pw[d], get(base + mult * wk.idx));
             walker_step(wk, cb, 1, G);
         }
-        if (R < n) acc.add(scale * tw[R], V[base + mult * wk.idx]);
+        if (R < n) acc.add(scale * tw[R], get(base + mult * wk.idx));
     }
 }
 
@@ -369,124 +507,223 @@ __device__ __forceinline__ ProdAction prod_action(const ProdParams &P, const Pro
     pa.y1 = (P.K >= 1) ? ps.x : a;    // m = L = 1: the order itself is the only slot
     pa.R = R;
     pa.T = pa.y1 + R;
-    uint32_t idx0 = (P.K >= 1) ? ps.r + (uint32_t)a * P.w_top : 0u;
+    const uint32_t idx0 = (P.K >= 1) ? ps.r + (uint32_t)a * P.w_top : 0u;
     walker_init(pa.wk, idx0, packed, P.m - 1, P.cb, lifo, P.w_zt);
     return pa;
 }
 
-// Q(s, a) of a single-product state
+// ---- single product ----------------------------------------------------------
+// plain kinds: Q(s, a) as one number
 template <typename T, int KAHAN>
 __device__ __forceinline__ T q_single(const KernelParams &kp, const T *s_tab, const T *V, const ProdState &ps,
                                       int a) {
     const ProdParams &P = kp.p[0];
     const int lifo = kp.issuing;
-    ProdAction pa = prod_action(P, ps, a, lifo);
+    const ProdAction pa = prod_action(P, ps, a, lifo);
     Acc<T, KAHAN> acc;
     acc.init();
-    expect_rest<T, KAHAN>(acc, V, 0u, 1u, pa.wk, P.cb, lifo, (uint32_t)P.G, pa.y1, pa.R, s_tab + P.off_p,
+    GetPlain<T> get{V};
+    expect_rest<T, KAHAN>(acc, get, 0u, 1u, pa.wk, P.cb, lifo, (uint32_t)P.G, pa.y1, pa.R, s_tab + P.off_p,
                           s_tab + P.off_F, s_tab + P.off_tail, P.dmax + 1, (T)1);
-    const T rb = -(T)P.c_o * (T)a + s_tab[P.off_TA + pa.T] + s_tab[P.off_TB + (lifo ? pa.R : pa.y1)];
+    const T rb = -(T)P.c_o * (T)a + s_tab[P.off_RT + pa.R * P.G + pa.y1];
     return rb + (T)kp.gamma * acc.s;
 }
 
-// Q(s, a) of a two-product state (product-1 shortfall may take product 2)
+// pair kind: Q(s, a) - gamma R0 as a pair (qh, ql); R0 = V(s'_0 of action 0)
+template <int KAHAN>
+__device__ __forceinline__ void q_single_pair(const KernelParams &kp, const float *s_tab, const float2 *V,
+                                              const ProdState &ps, int a, float2 R0, float &qh, float &ql) {
+    const ProdParams &P = kp.p[0];
+    const int lifo = kp.issuing;
+    const ProdAction pa = prod_action(P, ps, a, lifo);
+    const float2 ref = V[pa.wk.idx];
+    Acc<float, KAHAN> acc;
+    acc.init();
+    GetRel get{V, ref};
+    expect_rest<float, KAHAN>(acc, get, 0u, 1u, pa.wk, P.cb, lifo, (uint32_t)P.G, pa.y1, pa.R, s_tab + P.off_p,
+                              s_tab + P.off_F, s_tab + P.off_tail, P.dmax + 1, 1.f);
+    const float gam = (float)kp.gamma;
+    action_base(gam, ref, R0, __fmul_rn(-(float)P.c_o, (float)a), qh, ql);
+    const int ti = pa.R * P.G + pa.y1;
+    pair_add(qh, ql, s_tab[P.off_RT + ti], s_tab[P.off_RTlo + ti]);
+    ql = __fmaf_rn(gam, acc.s, ql);
+}
+
+// ---- two products (product-1 shortfall may take product 2) ----------------------
+// expectation over (d1, z): d1 below product-1 stock with product-2 own demand,
+// then the rows of M for d1 at or above the stock (substitution mixture)
+template <typename T, int KAHAN, class Get>
+__device__ __forceinline__ void expect_two(Acc<T, KAHAN> &acc, const Get &get, const KernelParams &kp,
+                                           const T *s_tab, const ProdAction &A1, const ProdAction &A2) {
+    const ProdParams &P1 = kp.p[0];
+    const ProdParams &P2 = kp.p[1];
+    const int lifo = kp.issuing;
+    const uint32_t S1 = P1.nS;
+    Walker w1 = A1.wk;
+    int e1c = 0;
+    const int top1 = A1.T < P1.dmax + 1 ? A1.T : P1.dmax + 1;   // d1 in [0, top1)
+    for (int d1 = 0; d1 < top1; ++d1) {
+        const int e1 = lifo ? min(d1, A1.R) : max(d1 - A1.y1, 0);
+        for (; e1c < e1; ++e1c) walker_step(w1, P1.cb, lifo, (uint32_t)P1.G);
+        const T p1 = s_tab[P1.off_p + d1];
+        expect_rest<T, KAHAN>(acc, get, w1.idx, S1, A2.wk, P2.cb, lifo, (uint32_t)P2.G, A2.y1, A2.R,
+                              s_tab + P2.off_p, s_tab + P2.off_F, s_tab + P2.off_tail, P2.dmax + 1, p1);
+    }
+    if (A1.T <= P1.dmax) {
+        for (; e1c < A1.R; ++e1c) walker_step(w1, P1.cb, lifo, (uint32_t)P1.G);
+        const int row = A1.T * kp.zlen;
+        expect_rest<T, KAHAN>(acc, get, w1.idx, S1, A2.wk, P2.cb, lifo, (uint32_t)P2.G, A2.y1, A2.R,
+                              s_tab + kp.off_M + row, s_tab + kp.off_Mc + row, s_tab + kp.off_Mt + row, kp.zlen,
+                              (T)1);
+    }
+}
+
+__device__ __forceinline__ int h1_index(const KernelParams &kp, const ProdAction &A1) {
+    const int ys1 = kp.issuing ? A1.R : A1.y1;
+    return ys1 * (kp.p[0].tmax + 1) + A1.T;
+}
+__device__ __forceinline__ int h2_index(const KernelParams &kp, const ProdAction &A1, const ProdAction &A2) {
+    const ProdParams &P2 = kp.p[1];
+    const int ys2 = kp.issuing ? A2.R : A2.y1;
+    const int ny2 = kp.issuing ? (P2.tmax + 1) : P2.G;
+    return (A1.T * ny2 + ys2) * (P2.tmax + 1) + A2.T;
+}
+
 template <typename T, int KAHAN>
 __device__ __forceinline__ T q_two(const KernelParams &kp, const T *s_tab, const T *g_tab, const T *V,
                                    const ProdState &p1s, const ProdState &p2s, int a) {
     const ProdParams &P1 = kp.p[0];
     const ProdParams &P2 = kp.p[1];
-    const int lifo = kp.issuing;
     const int a1 = a / P2.G, a2 = a - a1 * P2.G;
-    ProdAction A1 = prod_action(P1, p1s, a1, lifo);
-    ProdAction A2 = prod_action(P2, p2s, a2, lifo);
-    const uint32_t S1 = P1.nS;
+    const ProdAction A1 = prod_action(P1, p1s, a1, kp.issuing);
+    const ProdAction A2 = prod_action(P2, p2s, a2, kp.issuing);
     Acc<T, KAHAN> acc;
     acc.init();
-    // product-1 demand below its stock: product 2 sees its own demand only
-    Walker w1 = A1.wk;
-    int e1c = 0;
-    const int top1 = A1.T < P1.dmax + 1 ? A1.T : P1.dmax + 1;   // d1 in [0, top1)
-    for (int d1 = 0; d1 < top1; ++d1) {
-        const int e1 = lifo ? min(d1, A1.R) : max(d1 - A1.y1, 0);   // < R1 or == R1 (LIFO)
-        for (; e1c < e1; ++e1c) walker_step(w1, P1.cb, lifo, (uint32_t)P1.G);
-        const T p1 = s_tab[P1.off_p + d1];
-        expect_rest<T, KAHAN>(acc, V, w1.idx, S1, A2.wk, P2.cb, lifo, (uint32_t)P2.G, A2.y1, A2.R,
-                              s_tab + P2.off_p, s_tab + P2.off_F, s_tab + P2.off_tail, P2.dmax + 1, p1);
-    }
-    // product-1 demand at or above its stock: rows of M give product 2's demand
-    if (A1.T <= P1.dmax) {
-        // walker 1 must sit at e = R1 (all rest units issued)
-        for (; e1c < A1.R; ++e1c) walker_step(w1, P1.cb, lifo, (uint32_t)P1.G);
-        const int row = A1.T * kp.zlen;
-        expect_rest<T, KAHAN>(acc, V, w1.idx, S1, A2.wk, P2.cb, lifo, (uint32_t)P2.G, A2.y1, A2.R,
-                              s_tab + kp.off_M + row, s_tab + kp.off_Mc + row, s_tab + kp.off_Mt + row,
-                              kp.zlen, (T)1);
-    }
-    const int ys1 = lifo ? A1.R : A1.y1;
-    const int ys2 = lifo ? A2.R : A2.y1;
-    const int ny2 = lifo ? (P2.tmax + 1) : P2.G;
-    const T h1 = g_tab[kp.off_H1 + ys1 * (P1.tmax + 1) + A1.T];
-    const T h2 = g_tab[kp.off_H2 + (A1.T * ny2 + ys2) * (P2.tmax + 1) + A2.T];
-    const T rb = -(T)P1.c_o * (T)a1 - (T)P2.c_o * (T)a2 + h1 + h2;
+    GetPlain<T> get{V};
+    expect_two<T, KAHAN>(acc, get, kp, s_tab, A1, A2);
+    const T rb = -(T)P1.c_o * (T)a1 - (T)P2.c_o * (T)a2 + g_tab[kp.off_H1 + h1_index(kp, A1)] +
+                 g_tab[kp.off_H2 + h2_index(kp, A1, A2)];
     return rb + (T)kp.gamma * acc.s;
+}
+
+// next state of both products before any demand, for action a
+__device__ __forceinline__ uint32_t two_base_state(const KernelParams &kp, const ProdState &p1s,
+                                                   const ProdState &p2s, int a) {
+    const ProdParams &P1 = kp.p[0];
+    const ProdParams &P2 = kp.p[1];
+    const int a1 = a / P2.G, a2 = a - a1 * P2.G;
+    const uint32_t i1 = (P1.K >= 1) ? p1s.r + (uint32_t)a1 * P1.w_top : 0u;
+    const uint32_t i2 = (P2.K >= 1) ? p2s.r + (uint32_t)a2 * P2.w_top : 0u;
+    return i1 + P1.nS * i2;
+}
+
+template <int KAHAN>
+__device__ __forceinline__ void q_two_pair(const KernelParams &kp, const float *s_tab, const float *g_tab,
+                                           const float2 *V, const ProdState &p1s, const ProdState &p2s, int a,
+                                           float2 R0, float &qh, float &ql) {
+    const ProdParams &P1 = kp.p[0];
+    const ProdParams &P2 = kp.p[1];
+    const int a1 = a / P2.G, a2 = a - a1 * P2.G;
+    const ProdAction A1 = prod_action(P1, p1s, a1, kp.issuing);
+    const ProdAction A2 = prod_action(P2, p2s, a2, kp.issuing);
+    const float2 ref = V[A1.wk.idx + P1.nS * A2.wk.idx];
+    Acc<float, KAHAN> acc;
+    acc.init();
+    GetRel get{V, ref};
+    expect_two<float, KAHAN>(acc, get, kp, s_tab, A1, A2);
+    const float gam = (float)kp.gamma;
+    const float ca = __fadd_rn(__fmul_rn(-(float)P1.c_o, (float)a1), __fmul_rn(-(float)P2.c_o, (float)a2));
+    action_base(gam, ref, R0, ca, qh, ql);
+    const int i1 = h1_index(kp, A1), i2 = h2_index(kp, A1, A2);
+    pair_add(qh, ql, g_tab[kp.off_H1 + i1], g_tab[kp.off_H1lo + i1]);
+    pair_add(qh, ql, g_tab[kp.off_H2 + i2], g_tab[kp.off_H2lo + i2]);
+    ql = __fmaf_rn(gam, acc.s, ql);
 }
 
 // ===========================================================================
 // generic sweep: thread = state
 // ===========================================================================
-template <typename T, int KAHAN>
+template <int VK, int KAHAN>
 __global__ void __launch_bounds__(kGenericThreads)
-sweep_generic_kernel(KernelParams kp, int mode, const T *vin_arg, T *vout_arg, uint8_t *pol_arg) {
+sweep_generic_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg) {
+    using T = typename std::conditional<VK == VK_DOUBLE, double, float>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SolveState *st = kp.st;
-    Bufs<T> B;
-    if (!resolve_bufs<T>(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
-    T *s_tab = (T *)smem_raw;
-    const int n_smem_tab = (kp.n_products == 2) ? kp.off_H1 : kp.n_tables;   // H tables stay global
-    load_tables<T>(s_tab, (const T *)kp.tables, n_smem_tab);
+    Bufs B;
+    if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
     const T *g_tab = (const T *)kp.tables;
+    const T *s_tab = g_tab;
+    if (kp.tab_in_smem) {   // H tables of two products stay in global memory
+        T *st_ = (T *)smem_raw;
+        load_tables<T>(st_, g_tab, (kp.n_products == 2) ? kp.off_H1 : kp.n_tables);
+        s_tab = st_;
+    }
 
-    double mx = -INFINITY, mn = INFINITY;
+    T mx = (T)-INFINITY, mn = (T)INFINITY;
     const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < kp.nS) {
-        T best = (T)-INFINITY;
         int arg = 0;
+        ProdState p1s, p2s;
         if (kp.n_products == 1) {
-            ProdState ps = prod_state(kp.p[0], s);
-            for (int a = 0; a < kp.nA; ++a) {
-                T q = q_single<T, KAHAN>(kp, s_tab, B.vin, ps, a);
-                if (q > best) {
-                    best = q;
-                    arg = a;
-                }
-            }
+            p1s = prod_state(kp.p[0], s);
         } else {
             const uint32_t S1 = kp.p[0].nS;
             const uint32_t s2 = s / S1;
-            ProdState p1s = prod_state(kp.p[0], s - s2 * S1);
-            ProdState p2s = prod_state(kp.p[1], s2);
+            p1s = prod_state(kp.p[0], s - s2 * S1);
+            p2s = prod_state(kp.p[1], s2);
+        }
+        if (VK == VK_PAIR) {
+            const float2 *V2 = (const float2 *)B.vin;
+            const uint32_t i0 =
+                (kp.n_products == 1) ? ((kp.p[0].K >= 1) ? p1s.r : 0u) : two_base_state(kp, p1s, p2s, 0);
+            const float2 R0 = V2[i0];
+            float bh = -INFINITY, bl = 0.f;
             for (int a = 0; a < kp.nA; ++a) {
-                T q = q_two<T, KAHAN>(kp, s_tab, g_tab, B.vin, p1s, p2s, a);
+                float qh, ql;
+                if (kp.n_products == 1)
+                    q_single_pair<KAHAN>(kp, (const float *)s_tab, V2, p1s, a, R0, qh, ql);
+                else
+                    q_two_pair<KAHAN>(kp, (const float *)s_tab, (const float *)g_tab, V2, p1s, p2s, a, R0, qh, ql);
+                const float diff = __fadd_rn(__fsub_rn(qh, bh), __fsub_rn(ql, bl));
+                if (diff > 0.f) {
+                    bh = qh;
+                    bl = ql;
+                    arg = a;
+                }
+            }
+            const float2 vold = V2[s];
+            if (mode == MODE_EXTRACT) {
+                if (B.vout) ((float2 *)B.vout)[s] = vold;
+            } else {
+                const float2 vnew = pair_finish((float)kp.gamma, R0, bh, bl);
+                ((float2 *)B.vout)[s] = vnew;
+                const float dlt = pair_diff(vnew, vold);
+                mx = mn = (T)dlt;
+            }
+        } else {
+            const T *V = (const T *)B.vin;
+            T best = (T)-INFINITY;
+            for (int a = 0; a < kp.nA; ++a) {
+                const T q = (kp.n_products == 1) ? q_single<T, KAHAN>(kp, s_tab, V, p1s, a)
+                                                 : q_two<T, KAHAN>(kp, s_tab, g_tab, V, p1s, p2s, a);
                 if (q > best) {
                     best = q;
                     arg = a;
                 }
             }
-        }
-        if (s == 0 && mode == MODE_SWEEP) st->c_next = (float)best;
-        if (mode == MODE_EXTRACT) {
-            if (B.vout) B.vout[s] = B.vin[s];
-        } else {
-            const T vnew = best - B.cnorm;
-            const T vold = B.vin[s];
-            B.vout[s] = vnew;
-            const double dlt = (double)vnew - (double)vold;
-            mx = dlt;
-            mn = dlt;
+            if (VK == VK_SINGLE && s == 0 && mode == MODE_SWEEP) st->c_next = (float)best;
+            if (mode == MODE_EXTRACT) {
+                if (B.vout) ((T *)B.vout)[s] = V[s];
+            } else {
+                const T vnew = best - (T)B.cnorm;
+                const T vold = V[s];
+                ((T *)B.vout)[s] = vnew;
+                mx = mn = vnew - vold;
+            }
         }
         if (B.pol) B.pol[s] = (uint8_t)arg;
     }
-    if (mode != MODE_EXTRACT) block_reduce_and_finalize(mx, mn, st, mode);
+    if (mode != MODE_EXTRACT) block_reduce_and_finalize<T>(mx, mn, st, mode);
 }
 
 // ===========================================================================
@@ -500,13 +737,13 @@ __global__ void next_states_kernel(KernelParams kp, const uint32_t *states, int 
     const int lifo = kp.issuing;
     if (kp.n_products == 1) {
         const ProdParams &P = kp.p[0];
-        ProdState ps = prod_state(P, s);
-        ProdAction pa = prod_action(P, ps, a, lifo);
+        const ProdState ps = prod_state(P, s);
+        const ProdAction pa = prod_action(P, ps, a, lifo);
         uint32_t *o = out + ((size_t)i * kp.nA + a) * (size_t)(P.dmax + 1);
         Walker wk = pa.wk;
         int e_cur = 0;
         for (int d = 0; d <= P.dmax; ++d) {
-            int e = lifo ? min(d, pa.R) : min(max(d - pa.y1, 0), pa.R);
+            const int e = lifo ? min(d, pa.R) : min(max(d - pa.y1, 0), pa.R);
             for (; e_cur < e; ++e_cur) walker_step(wk, P.cb, lifo, (uint32_t)P.G);
             o[d] = wk.idx;
         }
@@ -516,22 +753,22 @@ __global__ void next_states_kernel(KernelParams kp, const uint32_t *states, int 
     const ProdParams &P2 = kp.p[1];
     const uint32_t S1 = P1.nS;
     const uint32_t s2 = s / S1;
-    ProdState p1s = prod_state(P1, s - s2 * S1);
-    ProdState p2s = prod_state(P2, s2);
+    const ProdState p1s = prod_state(P1, s - s2 * S1);
+    const ProdState p2s = prod_state(P2, s2);
     const int a1 = a / P2.G, a2 = a - a1 * P2.G;
-    ProdAction A1 = prod_action(P1, p1s, a1, lifo);
-    ProdAction A2 = prod_action(P2, p2s, a2, lifo);
+    const ProdAction A1 = prod_action(P1, p1s, a1, lifo);
+    const ProdAction A2 = prod_action(P2, p2s, a2, lifo);
     const int zl = P1.dmax + P2.dmax + 1;
     uint32_t *o = out + ((size_t)i * kp.nA + a) * (size_t)(P1.dmax + 1) * (size_t)zl;
     Walker w1 = A1.wk;
     int e1c = 0;
     for (int d1 = 0; d1 <= P1.dmax; ++d1) {
-        int e1 = lifo ? min(d1, A1.R) : min(max(d1 - A1.y1, 0), A1.R);
+        const int e1 = lifo ? min(d1, A1.R) : min(max(d1 - A1.y1, 0), A1.R);
         for (; e1c < e1; ++e1c) walker_step(w1, P1.cb, lifo, (uint32_t)P1.G);
         Walker w2 = A2.wk;
         int e2c = 0;
         for (int z = 0; z < zl; ++z) {
-            int e2 = lifo ? min(z, A2.R) : min(max(z - A2.y1, 0), A2.R);
+            const int e2 = lifo ? min(z, A2.R) : min(max(z - A2.y1, 0), A2.R);
             for (; e2c < e2; ++e2c) walker_step(w2, P2.cb, lifo, (uint32_t)P2.G);
             o[(size_t)d1 * zl + z] = w1.idx + S1 * w2.idx;
         }
@@ -544,59 +781,69 @@ __global__ void next_states_kernel(KernelParams kp, const uint32_t *states, int 
 __global__ void __launch_bounds__(kGenericThreads)
 policy_eval_kernel(KernelParams kp, const uint8_t *policy, const double *vin, double *vout) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *s_tab = (double *)smem_raw;
-    const int n_smem_tab = (kp.n_products == 2) ? kp.off_H1 : kp.n_tables;
-    load_tables<double>(s_tab, (const double *)kp.tables, n_smem_tab);
     const double *g_tab = (const double *)kp.tables;
+    const double *s_tab = g_tab;
+    if (kp.tab_in_smem) {
+        double *st_ = (double *)smem_raw;
+        load_tables<double>(st_, g_tab, (kp.n_products == 2) ? kp.off_H1 : kp.n_tables);
+        s_tab = st_;
+    }
     double mx = -INFINITY, mn = INFINITY;
     const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < kp.nS) {
         const int a = policy[s];
         double q;
         if (kp.n_products == 1) {
-            ProdState ps = prod_state(kp.p[0], s);
+            const ProdState ps = prod_state(kp.p[0], s);
             q = q_single<double, 0>(kp, s_tab, vin, ps, a);
         } else {
             const uint32_t S1 = kp.p[0].nS;
             const uint32_t s2 = s / S1;
-            ProdState p1s = prod_state(kp.p[0], s - s2 * S1);
-            ProdState p2s = prod_state(kp.p[1], s2);
+            const ProdState p1s = prod_state(kp.p[0], s - s2 * S1);
+            const ProdState p2s = prod_state(kp.p[1], s2);
             q = q_two<double, 0>(kp, s_tab, g_tab, vin, p1s, p2s, a);
         }
         vout[s] = q;
         mx = mn = q - vin[s];
     }
-    block_reduce_and_finalize(mx, mn, kp.st, MODE_PLAIN);
+    block_reduce_and_finalize<double>(mx, mn, kp.st, MODE_PLAIN);
 }
 
-// V_abs = offset + v in FP64
-__global__ void to_fp64_kernel(const float *v, double offset, double *out, uint32_t n) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = offset + (double)v[i];
+// V_abs in FP64 from any value kind
+__global__ void to_fp64_kernel(const void *v, int vk, double offset, double *out, uint32_t n) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (vk == VK_SINGLE) {
+        out[i] = offset + (double)((const float *)v)[i];
+    } else if (vk == VK_PAIR) {
+        const float2 p = ((const float2 *)v)[i];
+        out[i] = (double)p.x + (double)p.y;
+    } else {
+        out[i] = ((const double *)v)[i];
+    }
 }
 
-// max_s |a(s) - b(s)| into the state's PLAIN accumulators
+// max_s |a(s) - b(s)| into the state's plain accumulators
 __global__ void absdiff_kernel(const double *a, const double *b, uint32_t n, SolveState *st) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     double d = 0.0;
     if (i < n) d = fabs(a[i] - b[i]);
-    block_reduce_and_finalize(d, d, st, MODE_PLAIN);
+    block_reduce_and_finalize<double>(d, d, st, MODE_PLAIN);
 }
 
 // ===========================================================================
-// solve bookkeeping kernels
+// solve bookkeeping
 // ===========================================================================
 __global__ void solve_init_kernel(SolveState *st, uint32_t n) {
     // zero V_0 unless warm-starting, reset the running state
     const int warm = st->warm;
     const int value_bytes = st->value_bytes;
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (!warm) {
-        if (value_bytes == 4) {
-            if (i < n) ((float *)st->buf[0])[i] = 0.f;
-        } else {
-            if (i < n) ((double *)st->buf[0])[i] = 0.0;
-        }
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (!warm && i < n) {
+        if (value_bytes == 4)
+            ((float *)st->buf[0])[i] = 0.f;
+        else
+            ((double *)st->buf[0])[i] = 0.0;   // also a (0, 0) float pair
     }
     if (i == 0) {
         st->key_max = 0ull;
@@ -610,16 +857,10 @@ __global__ void solve_init_kernel(SolveState *st, uint32_t n) {
         st->c_cur = 0.f;
         st->c_next = 0.f;
         if (!warm) st->offset = 0.0;
-        int go = st->max_iters > 0;
+        const int go = st->max_iters > 0;
         st->keep_going = go;
         if (st->use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)st->cond, go ? 1u : 0u);
     }
-}
-
-__global__ void state_reset_kernel(SolveState *st) {
-    st->key_max = 0ull;
-    st->key_min = ~0ull;
-    st->blocks_done = 0u;
 }
 
 // ===========================================================================
@@ -632,10 +873,10 @@ struct RollOut {
 
 // one product, one period, with the sweep kernels' walker for the next state
 __device__ __forceinline__ RollOut roll_product(const ProdParams &P, int lifo, uint32_t sk, int a, int z) {
-    ProdState ps = prod_state(P, sk);
-    ProdAction pa = prod_action(P, ps, a, lifo);
+    const ProdState ps = prod_state(P, sk);
+    const ProdAction pa = prod_action(P, ps, a, lifo);
     RollOut o;
-    int e = lifo ? min(z, pa.R) : min(max(z - pa.y1, 0), pa.R);
+    const int e = lifo ? min(z, pa.R) : min(max(z - pa.y1, 0), pa.R);
     Walker wk = pa.wk;
     for (int k = 0; k < e; ++k) walker_step(wk, P.cb, lifo, (uint32_t)P.G);
     o.s_next = wk.idx;
@@ -667,8 +908,8 @@ __device__ __forceinline__ int draw_demand(uint32_t w, const unsigned long long 
     return d;
 }
 
-__global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *policy, double *returns,
-                               double *kpis, int32_t *traj) {
+__global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *policy, double *returns, double *kpis,
+                               int32_t *traj) {
     __shared__ unsigned long long s_thr[2][kMaxRollDmax + 1];
     for (int i = threadIdx.x; i <= kMaxRollDmax; i += blockDim.x) {
         s_thr[0][i] = rp.thr[0][i];
@@ -692,7 +933,7 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
         uint32_t s_next;
         if (kp.n_products == 1) {
             const int d1 = draw_demand(w[0], s_thr[0], P1.dmax);
-            RollOut o = roll_product(P1, lifo, s, a, d1);
+            const RollOut o = roll_product(P1, lifo, s, a, d1);
             rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][0], (double)a));
             rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][1], (double)o.carried));
             rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][2], (double)o.shortage));
@@ -711,11 +952,11 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
             const uint32_t S1 = P1.nS;
             const uint32_t s2 = s / S1, s1 = s - s2 * S1;
             const int a1 = a / P2.G, a2 = a - a1 * P2.G;
-            RollOut o1 = roll_product(P1, lifo, s1, a1, d1);
+            const RollOut o1 = roll_product(P1, lifo, s1, a1, d1);
             const int n = o1.shortage;
             const uint32_t mask = (n >= 32) ? 0xffffffffu : ((1u << n) - 1u);
             const int u = __popc(w[2] & mask);
-            RollOut o2 = roll_product(P2, lifo, s2, a2, d2 + u);
+            const RollOut o2 = roll_product(P2, lifo, s2, a2, d2 + u);
             const int own2 = min(d2, o2.total);
             const int short1 = n - (o2.issued - own2);
             const int short2 = max(d2 - o2.total, 0);
@@ -757,31 +998,29 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
 }
 
 // ===========================================================================
-// launchers
+// launch descriptors and launchers
 // ===========================================================================
-static size_t group_smem(const KernelParams &kp, int G) {
-    return (size_t)((kp.n_tables + 3) & ~3) * 4 + (size_t)kGroupThreads * G * 5;
+static size_t group_smem(const KernelParams &kp, int G, int vk) {
+    const size_t vb = (vk == VK_PAIR) ? 8 : 4;
+    return (size_t)((kp.n_tables + 3) & ~3) * 4 + (size_t)kGroupThreads * G * (vb + 1);
 }
 
-template <int G, int LIFO>
-static cudaError_t launch_group_t(const KernelParams &kp, int mode, const float *vin, float *vout,
-                                  uint8_t *pol, cudaStream_t stream) {
+template <int G, int LIFO, int VK>
+static cudaError_t describe_group_t(const KernelParams &kp, LaunchDesc &d) {
     const uint32_t nR = kp.p[0].nS / (uint32_t)G;
-    const uint32_t blocks = (nR + kGroupThreads - 1) / kGroupThreads;
-    size_t smem = group_smem(kp, G);
-    auto fn = sweep_group_kernel<G, LIFO>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    fn<<<blocks, kGroupThreads, smem, stream>>>(kp, mode, vin, vout, pol);
-    return cudaGetLastError();
+    d.fn = (const void *)sweep_group_kernel<G, LIFO, VK>;
+    d.grid = dim3((nR + kGroupThreads - 1) / kGroupThreads);
+    d.block = dim3(kGroupThreads);
+    d.smem = group_smem(kp, G, VK);
+    return cudaFuncSetAttribute(sweep_group_kernel<G, LIFO, VK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)d.smem);
 }
 
-template <int LIFO>
-static cudaError_t launch_group_l(const KernelParams &kp, int G, int mode, const float *vin, float *vout,
-                                  uint8_t *pol, cudaStream_t stream) {
-    switch (G) {
+template <int LIFO, int VK>
+static cudaError_t describe_group_l(const KernelParams &kp, LaunchDesc &d) {
+    switch (kp.p[0].G) {
 #define VIB_G(g) \
-    case g: return launch_group_t<g, LIFO>(kp, mode, vin, vout, pol, stream);
+    case g: return describe_group_t<g, LIFO, VK>(kp, d);
         VIB_G(2) VIB_G(3) VIB_G(4) VIB_G(5) VIB_G(6) VIB_G(7) VIB_G(8) VIB_G(9) VIB_G(10) VIB_G(11)
         VIB_G(12) VIB_G(13) VIB_G(14) VIB_G(15) VIB_G(16) VIB_G(17) VIB_G(18) VIB_G(19) VIB_G(20)
         VIB_G(21) VIB_G(22) VIB_G(23) VIB_G(24)
@@ -790,40 +1029,45 @@ static cudaError_t launch_group_l(const KernelParams &kp, int G, int mode, const
     }
 }
 
-bool group_supported(const KernelParams &kp) {
-    const ProdParams &P = kp.p[0];
-    return kp.n_products == 1 && P.K >= 1 && P.G >= 2 && P.G <= kMaxGroupG;
-}
-
-cudaError_t launch_sweep_group(const KernelParams &kp, int mode, const float *vin, float *vout,
-                               uint8_t *pol, cudaStream_t stream) {
-    if (kp.issuing) return launch_group_l<1>(kp, kp.p[0].G, mode, vin, vout, pol, stream);
-    return launch_group_l<0>(kp, kp.p[0].G, mode, vin, vout, pol, stream);
-}
-
-template <typename T, int KAHAN>
-static cudaError_t launch_generic_t(const KernelParams &kp, int mode, const void *vin, void *vout,
-                                    uint8_t *pol, cudaStream_t stream) {
-    const uint32_t blocks = (kp.nS + kGenericThreads - 1) / kGenericThreads;
+template <int VK, int KAHAN>
+static cudaError_t describe_generic_t(const KernelParams &kp, LaunchDesc &d) {
+    using T = typename std::conditional<VK == VK_DOUBLE, double, float>::type;
+    d.fn = (const void *)sweep_generic_kernel<VK, KAHAN>;
+    d.grid = dim3((kp.nS + kGenericThreads - 1) / kGenericThreads);
+    d.block = dim3(kGenericThreads);
     const int n_smem_tab = (kp.n_products == 2) ? kp.off_H1 : kp.n_tables;
-    size_t smem = (size_t)n_smem_tab * sizeof(T);
-    auto fn = sweep_generic_kernel<T, KAHAN>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    fn<<<blocks, kGenericThreads, smem, stream>>>(kp, mode, (const T *)vin, (T *)vout, pol);
-    return cudaGetLastError();
+    d.smem = kp.tab_in_smem ? (size_t)n_smem_tab * sizeof(T) : 0;
+    return cudaFuncSetAttribute(sweep_generic_kernel<VK, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)d.smem);
 }
 
-cudaError_t launch_sweep_generic(const KernelParams &kp, int precision, int mode, const void *vin, void *vout,
-                                 uint8_t *pol, cudaStream_t stream) {
-    if (precision == 2) return launch_generic_t<double, 0>(kp, mode, vin, vout, pol, stream);
-    if (precision == 1) return launch_generic_t<float, 1>(kp, mode, vin, vout, pol, stream);
-    return launch_generic_t<float, 0>(kp, mode, vin, vout, pol, stream);
+bool group_supported(const KernelParams &kp, int vk, int kahan) {
+    const ProdParams &P = kp.p[0];
+    return kp.n_products == 1 && (vk == VK_PAIR || vk == VK_SINGLE) && !kahan && P.K >= 1 && P.G >= 2 &&
+           P.G <= kMaxGroupG;
+}
+
+cudaError_t describe_sweep(const KernelParams &kp, int vk, int kahan, int use_group, LaunchDesc &d) {
+    if (use_group) {
+        if (vk == VK_PAIR) return kp.issuing ? describe_group_l<1, VK_PAIR>(kp, d) : describe_group_l<0, VK_PAIR>(kp, d);
+        return kp.issuing ? describe_group_l<1, VK_SINGLE>(kp, d) : describe_group_l<0, VK_SINGLE>(kp, d);
+    }
+    if (vk == VK_DOUBLE) return describe_generic_t<VK_DOUBLE, 0>(kp, d);
+    if (vk == VK_PAIR) return kahan ? describe_generic_t<VK_PAIR, 1>(kp, d) : describe_generic_t<VK_PAIR, 0>(kp, d);
+    return kahan ? describe_generic_t<VK_SINGLE, 1>(kp, d) : describe_generic_t<VK_SINGLE, 0>(kp, d);
+}
+
+cudaError_t describe_solve_init(uint32_t n, LaunchDesc &d) {
+    d.fn = (const void *)solve_init_kernel;
+    d.grid = dim3((n + 255) / 256);
+    d.block = dim3(256);
+    d.smem = 0;
+    return cudaSuccess;
 }
 
 cudaError_t launch_next_states(const KernelParams &kp, const uint32_t *states, int n, uint32_t *out,
                                cudaStream_t stream) {
-    dim3 block(64), grid(n, (kp.nA + 63) / 64);
+    const dim3 block(64), grid(n, (kp.nA + 63) / 64);
     next_states_kernel<<<grid, block, 0, stream>>>(kp, states, n, out);
     return cudaGetLastError();
 }
@@ -832,31 +1076,21 @@ cudaError_t launch_policy_eval(const KernelParams &kp, const uint8_t *policy, co
                                cudaStream_t stream) {
     const uint32_t blocks = (kp.nS + kGenericThreads - 1) / kGenericThreads;
     const int n_smem_tab = (kp.n_products == 2) ? kp.off_H1 : kp.n_tables;
-    size_t smem = (size_t)n_smem_tab * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(policy_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const size_t smem = kp.tab_in_smem ? (size_t)n_smem_tab * sizeof(double) : 0;
+    const cudaError_t e =
+        cudaFuncSetAttribute(policy_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     policy_eval_kernel<<<blocks, kGenericThreads, smem, stream>>>(kp, policy, vin, vout);
     return cudaGetLastError();
 }
 
-cudaError_t launch_to_fp64(const float *v, double offset, double *out, uint32_t n, cudaStream_t stream) {
-    to_fp64_kernel<<<(n + 255) / 256, 256, 0, stream>>>(v, offset, out, n);
+cudaError_t launch_to_fp64(const void *v, int vk, double offset, double *out, uint32_t n, cudaStream_t stream) {
+    to_fp64_kernel<<<(n + 255) / 256, 256, 0, stream>>>(v, vk, offset, out, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_absdiff(const double *a, const double *b, uint32_t n, SolveState *st, cudaStream_t stream) {
     absdiff_kernel<<<(n + 255) / 256, 256, 0, stream>>>(a, b, n, st);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_solve_init(SolveState *st, uint32_t n, cudaStream_t stream) {
-    solve_init_kernel<<<(n + 255) / 256, 256, 0, stream>>>(st, n);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_state_reset(SolveState *st, cudaStream_t stream) {
-    state_reset_kernel<<<1, 1, 0, stream>>>(st);
     return cudaGetLastError();
 }
 
@@ -866,63 +1100,6 @@ cudaError_t launch_rollouts(const KernelParams &kp, const RollParams &rp, const 
     const int blocks = (rp.n_rollouts + threads - 1) / threads;
     rollout_kernel<<<blocks, threads, 0, stream>>>(kp, rp, policy, returns, kpis, traj);
     return cudaGetLastError();
-}
-
-
-// ---------------------------------------------------------------------------
-// kernel descriptors for CUDA-graph construction
-// ---------------------------------------------------------------------------
-template <int G, int LIFO>
-static cudaError_t describe_group_t(const KernelParams &kp, LaunchDesc &d) {
-    const uint32_t nR = kp.p[0].nS / (uint32_t)G;
-    d.fn = (const void *)sweep_group_kernel<G, LIFO>;
-    d.grid = dim3((nR + kGroupThreads - 1) / kGroupThreads);
-    d.block = dim3(kGroupThreads);
-    d.smem = group_smem(kp, G);
-    return cudaFuncSetAttribute(sweep_group_kernel<G, LIFO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)d.smem);
-}
-
-template <int LIFO>
-static cudaError_t describe_group_l(const KernelParams &kp, LaunchDesc &d) {
-    switch (kp.p[0].G) {
-#define VIB_G(g) \
-    case g: return describe_group_t<g, LIFO>(kp, d);
-        VIB_G(2) VIB_G(3) VIB_G(4) VIB_G(5) VIB_G(6) VIB_G(7) VIB_G(8) VIB_G(9) VIB_G(10) VIB_G(11)
-        VIB_G(12) VIB_G(13) VIB_G(14) VIB_G(15) VIB_G(16) VIB_G(17) VIB_G(18) VIB_G(19) VIB_G(20)
-        VIB_G(21) VIB_G(22) VIB_G(23) VIB_G(24)
-#undef VIB_G
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename T, int KAHAN>
-static cudaError_t describe_generic_t(const KernelParams &kp, LaunchDesc &d) {
-    d.fn = (const void *)sweep_generic_kernel<T, KAHAN>;
-    d.grid = dim3((kp.nS + kGenericThreads - 1) / kGenericThreads);
-    d.block = dim3(kGenericThreads);
-    const int n_smem_tab = (kp.n_products == 2) ? kp.off_H1 : kp.n_tables;
-    d.smem = (size_t)n_smem_tab * sizeof(T);
-    return cudaFuncSetAttribute(sweep_generic_kernel<T, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)d.smem);
-}
-
-cudaError_t describe_sweep(const KernelParams &kp, int precision, int use_group, LaunchDesc &d) {
-    if (use_group) {
-        if (kp.issuing) return describe_group_l<1>(kp, d);
-        return describe_group_l<0>(kp, d);
-    }
-    if (precision == 2) return describe_generic_t<double, 0>(kp, d);
-    if (precision == 1) return describe_generic_t<float, 1>(kp, d);
-    return describe_generic_t<float, 0>(kp, d);
-}
-
-cudaError_t describe_solve_init(uint32_t n, LaunchDesc &d) {
-    d.fn = (const void *)solve_init_kernel;
-    d.grid = dim3((n + 255) / 256);
-    d.block = dim3(256);
-    d.smem = 0;
-    return cudaSuccess;
 }
 
 }  // namespace vib

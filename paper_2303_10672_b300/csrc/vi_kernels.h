@@ -15,6 +15,9 @@ enum {
     MODE_PLAIN = 2      // one backup between explicit buffers, no normalisation, change stats only
 };
 
+// how values are stored and combined (see vi_kernels.cu)
+enum { VK_SINGLE = 0, VK_PAIR = 1, VK_DOUBLE = 2 };
+
 constexpr int kGroupThreads = 128;   // rests per block of the factorised kernel
 constexpr int kGenericThreads = 128;
 constexpr int kMaxGroupG = 24;       // largest Q+1 with a factorised instantiation
@@ -27,16 +30,12 @@ struct RollParams {
     unsigned long long thr[2][kMaxRollDmax + 1];   // floor(2^32 CDF(d)), thr[dmax] = 2^32
 };
 
-bool group_supported(const KernelParams &kp);
-cudaError_t launch_sweep_group(const KernelParams &kp, int mode, const float *vin, float *vout,
-                               uint8_t *pol, cudaStream_t stream);
-cudaError_t launch_sweep_generic(const KernelParams &kp, int precision, int mode, const void *vin,
-                                 void *vout, uint8_t *pol, cudaStream_t stream);
+bool group_supported(const KernelParams &kp, int vk, int kahan);
 cudaError_t launch_next_states(const KernelParams &kp, const uint32_t *states, int n, uint32_t *out,
                                cudaStream_t stream);
 cudaError_t launch_policy_eval(const KernelParams &kp, const uint8_t *policy, const double *vin,
                                double *vout, cudaStream_t stream);
-cudaError_t launch_to_fp64(const float *v, double offset, double *out, uint32_t n, cudaStream_t stream);
+cudaError_t launch_to_fp64(const void *v, int vk, double offset, double *out, uint32_t n, cudaStream_t stream);
 cudaError_t launch_absdiff(const double *a, const double *b, uint32_t n, SolveState *st,
                            cudaStream_t stream);
 cudaError_t launch_solve_init(SolveState *st, uint32_t n, cudaStream_t stream);
@@ -47,9 +46,8 @@ struct LaunchDesc {
     dim3 grid, block;
     size_t smem;
 };
-cudaError_t describe_sweep(const KernelParams &kp, int precision, int use_group, LaunchDesc &d);
+cudaError_t describe_sweep(const KernelParams &kp, int vk, int kahan, int use_group, LaunchDesc &d);
 cudaError_t describe_solve_init(uint32_t n, LaunchDesc &d);
-cudaError_t launch_state_reset(SolveState *st, cudaStream_t stream);
 cudaError_t launch_rollouts(const KernelParams &kp, const RollParams &rp, const uint8_t *policy,
                             double *returns, double *kpis, int32_t *traj, cudaStream_t stream);
 

@@ -7,7 +7,20 @@ import torch
 
 import paper_2303_10672_b300 as vi
 
-PREC = {"fp32": vi.VI_PREC_FP32, "fp32_kahan": vi.VI_PREC_FP32_KAHAN, "fp64": vi.VI_PREC_FP64}
+PREC = {"fp32": vi.VI_PREC_FP32, "fp32_kahan": vi.VI_PREC_FP32_KAHAN, "fp64": vi.VI_PREC_FP64,
+        "fp32_single": vi.VI_PREC_FP32_SINGLE}
+# storage layout of each precision: float pair, double, or single float + FP64 offset
+LAYOUT = {"fp32": "pair", "fp32_kahan": "pair", "fp64": "double", "fp32_single": "single"}
+
+
+def values_abs(V: torch.Tensor, offset: float, layout: str) -> np.ndarray:
+    """Absolute values V_abs(s) in FP64 from a device value buffer."""
+    if layout == "pair":
+        p = V.view(torch.float32).reshape(-1, 2).double()
+        return (p[:, 0] + p[:, 1]).cpu().numpy()
+    if layout == "double":
+        return V.view(torch.float64).cpu().numpy()
+    return V.view(torch.float32).double().cpu().numpy() + offset
 
 # tolerances stated by the task: values max|dV|/max|V| <= 1e-5; policy ties within 1e-6 relative
 V_RTOL = 1e-5
@@ -30,6 +43,8 @@ class Handle:
         self.precision = precision or inst.precision
         self.h = create(inst, self.precision, stop_rule, kernel)
         self.sizes = vi.vi_problem_sizes(self.h)
+        self.layout = LAYOUT[self.precision]
+        # one 8-byte element per state holds a float pair or a double
         self.dtype = torch.float64 if self.sizes["value_bytes"] == 8 else torch.float32
 
     def close(self):
@@ -53,7 +68,7 @@ class Handle:
         return V, pol, info
 
     def v_abs(self, V, info) -> np.ndarray:
-        return V.double().cpu().numpy() + info["offset"]
+        return values_abs(V, info["offset"], self.layout)
 
 
 def compare_values(v_gpu: np.ndarray, v_ref: np.ndarray) -> float:

@@ -15,7 +15,7 @@ from workloads import FIFO, LIFO
 pytestmark = pytest.mark.gpu
 
 vi = pytest.importorskip("paper_2303_10672_b300")
-from gpu_helpers import Handle, compare_values, policy_mismatches, V_RTOL  # noqa: E402
+from gpu_helpers import Handle, compare_values, policy_mismatches, values_abs, V_RTOL  # noqa: E402
 
 
 def small_instances():
@@ -122,7 +122,7 @@ def solve_parity(inst, precision, kernel=vi.VI_KERNEL_AUTO, tol=1e-4, stop_rule=
 
 
 @pytest.mark.parametrize("inst", SMALL, ids=_ids(SMALL))
-@pytest.mark.parametrize("precision", ["fp32", "fp32_kahan", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "fp32_kahan", "fp64", "fp32_single"])
 def test_solve_small(inst, precision):
     solve_parity(inst, precision)
 
@@ -134,7 +134,7 @@ def test_solve_small_generic_kernel_fp32(inst):
 
 def test_solve_config1_fp64_and_fp32():
     inst = workloads.config1()
-    for prec in ("fp64", "fp32", "fp32_kahan"):
+    for prec in ("fp64", "fp32", "fp32_kahan", "fp32_single"):
         solve_parity(inst, prec)
 
 
@@ -169,19 +169,19 @@ def test_solve_two_products_general_costs(case):
 # compared on sampled states computed one by one by the oracle
 # ---------------------------------------------------------------------------
 
-def sampled_backup_parity(inst, k_sweeps, n_samples, seed):
+def sampled_backup_parity(inst, k_sweeps, n_samples, seed, precision="fp32"):
     P = oracle.Problem(inst)
-    with Handle(inst) as H:
-        V, pol, info = H.solve(0.0, k_sweeps)           # V_k (relative) + offset
+    with Handle(inst, precision=precision) as H:
+        V, pol, info = H.solve(0.0, k_sweeps)           # V_k (+ offset for the single layout)
         n = H.sizes["n_states"]
         V_next = torch.empty_like(V)
         pol_next = torch.empty(n, dtype=torch.uint8, device="cuda")
         dmx, dmn = vi.vi_backup(H.h, V, V_next, pol_next)
         torch.cuda.synchronize()
         b = info["offset"]
-        v_k = V.double().cpu().numpy() + b
-        # V_next holds V_abs' - gamma b
-        v_next = V_next.double().cpu().numpy() + inst.gamma * b
+        v_k = H.v_abs(V, info)
+        # single layout: V_next holds V_abs' - gamma b; pair / double: absolute
+        v_next = values_abs(V_next, inst.gamma * b, H.layout)
         rng = np.random.default_rng(seed)
         states = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, n_samples)]))
         want, _ = P.backup_states(v_k, states)
@@ -192,17 +192,20 @@ def sampled_backup_parity(inst, k_sweeps, n_samples, seed):
         # the policy written by the extraction sweep of the solve is the argmax from V_k
         bad = policy_mismatches(P, v_k, pol.cpu().numpy()[states], states)
         assert not bad, bad[:5]
-        # change statistics are exact reductions of V_next - V_k (relative values)
-        dv = V_next.double() - V.double()
-        assert dmx == pytest.approx(dv.max().item(), abs=0) and dmn == pytest.approx(dv.min().item(), abs=0)
+        # change statistics: max / min of V_next - V_k in the kernel's own value units
+        dv = values_abs(V_next, 0.0, H.layout) - values_abs(V, 0.0, H.layout)
+        scale = max(1.0, np.abs(v_k).max())
+        assert abs(dmx - dv.max()) <= 1e-6 * scale and abs(dmn - dv.min()) <= 1e-6 * scale
 
 
-def test_config2_full_size_sampled():
-    sampled_backup_parity(workloads.config2(), 3, 300, 2)
+@pytest.mark.parametrize("precision", ["fp32", "fp32_single"])
+def test_config2_full_size_sampled(precision):
+    sampled_backup_parity(workloads.config2(), 3, 300, 2, precision)
 
 
-def test_config4_full_size_sampled():
-    sampled_backup_parity(workloads.config4(), 3, 300, 4)
+@pytest.mark.parametrize("precision", ["fp32", "fp32_single"])
+def test_config4_full_size_sampled(precision):
+    sampled_backup_parity(workloads.config4(), 3, 300, 4, precision)
 
 
 def test_config3_full_size_sampled():
@@ -211,10 +214,10 @@ def test_config3_full_size_sampled():
     with Handle(inst) as H:
         V, pol, info = H.solve(0.0, 2)
         n = H.sizes["n_states"]
-        v_k = V.double().cpu().numpy() + info["offset"]
+        v_k = H.v_abs(V, info)
         V_next = torch.empty_like(V)
         vi.vi_backup(H.h, V, V_next, None)
-        v_next = V_next.double().cpu().numpy() + inst.gamma * info["offset"]
+        v_next = values_abs(V_next, inst.gamma * info["offset"], H.layout)
         states = np.unique(np.concatenate([[0, n - 1], np.random.default_rng(5).integers(0, n, 24)]))
         want, _ = P.backup_states(v_k, states)
         err = np.abs(v_next[states] - want).max() / np.abs(want).max()
@@ -296,9 +299,9 @@ def test_warm_start_resume_is_bit_identical():
         V_a, _, ia = H.solve(0.0, 7)
         V_b, _, ib = H.solve(0.0, 4)
         V_c, _, ic = H.solve(0.0, 3, flags=vi.VI_FLAG_WARM_START, V=V_b, offset=ib["offset"])
-        # the normalisation constant restarts at 0 after a resume, so compare absolute values
-        va = V_a.double().cpu().numpy() + ia["offset"]
-        vc = V_c.double().cpu().numpy() + ic["offset"]
+        # compare absolute values (the single layout renormalises after a resume)
+        va = H.v_abs(V_a, ia)
+        vc = H.v_abs(V_c, ic)
         assert np.abs(va - vc).max() <= 1e-6 * np.abs(va).max()
 
 
