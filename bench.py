@@ -308,6 +308,7 @@ def run_native(args):
     d2h = n * sizes["value_bytes"] + n
 
     out = None
+    serving = run_serving(args.serving) if (args.serving > 0 and rank == 0) else None
     if rank == 0:
         cpu = oracle_sample_rate(inst, args.cpu_seconds) if args.cpu_seconds > 0 else None
         out = {
@@ -326,6 +327,7 @@ def run_native(args):
                     "steps": e2e_steps, "includes": "vi_problem_create + vi_solve_host + vi_problem_destroy"},
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind",
                                                                            "sample")},
+            "serving": serving,
             "wall_s": wall,
         }
         print(json.dumps(out))
@@ -334,6 +336,103 @@ def run_native(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return out
+
+
+def run_serving(n_requests: int = 512, seed: int = 5, slots: int = 64, budget_gb: float = 64.0) -> dict:
+    """Serving mix: requests arriving as a Poisson stream, served by the
+    continuous-batching server vs sequential plain solves of the same mix (each:
+    create, solve with host buffers, destroy).  Latency = arrival to result."""
+    import paper_2303_10672_b300 as vi
+    reqs = workloads.serving_mix(n_requests, seed=seed)
+    descs = []
+    for r in reqs:
+        p = r.instance.products[0]
+        descs.append(vi.make_desc([dict(m=p.m, L=p.L, Q=p.Q, cost=p.cost, pmf=p.pmf)], r.instance.gamma,
+                                  r.instance.issuing))
+    nominal = [r.instance.updates_per_sweep for r in reqs]
+
+    # warm up both paths (module load, autotuning of each shape class, graph builds)
+    srv = vi.vi_server_create(int(budget_gb * (1 << 30)), slots)
+    wid = vi.vi_server_submit(srv, descs[0][0], TOL, MAX_ITERS)
+    while not vi.vi_server_poll(srv, wid)[0]:
+        time.sleep(0.001)
+
+    # -- server: submit at the arrival times, poll for completions
+    t0 = time.perf_counter()
+    ids, lat, upd = [], {}, 0.0
+    pending = {}
+    i = 0
+    while i < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i].arrival_s <= now:
+            rid = vi.vi_server_submit(srv, descs[i][0], TOL, MAX_ITERS)
+            pending[rid] = i
+            i += 1
+        for rid in list(pending):
+            done, info = vi.vi_server_poll(srv, rid)
+            if done:
+                k = pending.pop(rid)
+                lat[k] = info["wall_ms"]
+                upd += nominal[k] * info["iters"]
+        time.sleep(0.0002)
+    span_srv = time.perf_counter() - t0
+    vi.vi_server_destroy(srv)
+    lat_srv = np.array([lat[k] for k in range(len(reqs))])
+
+    # -- sequential plain solves in arrival order
+    for d in descs[:3]:
+        h = vi.vi_problem_create_desc(d[0])
+        n = vi.vi_problem_sizes(h)["n_states"]
+        vi.vi_solve_host(h, TOL, MAX_ITERS, np.empty(n, np.float64), np.empty(n, np.uint8))
+        vi.vi_problem_destroy(h)
+    t0 = time.perf_counter()
+    lat_seq, upd_seq = [], 0.0
+    for k, (r, d) in enumerate(zip(reqs, descs)):
+        now = time.perf_counter() - t0
+        if now < r.arrival_s:
+            time.sleep(r.arrival_s - now)
+        h = vi.vi_problem_create_desc(d[0])
+        n = vi.vi_problem_sizes(h)["n_states"]
+        info = vi.vi_solve_host(h, TOL, MAX_ITERS, np.empty(n, np.float64), np.empty(n, np.uint8))
+        vi.vi_problem_destroy(h)
+        lat_seq.append(1e3 * (time.perf_counter() - t0 - r.arrival_s))
+        upd_seq += nominal[k] * info["iters"]
+    span_seq = time.perf_counter() - t0
+    lat_seq = np.array(lat_seq)
+
+    # -- capacity: the whole mix submitted at once, server vs sequential
+    srv = vi.vi_server_create(int(budget_gb * (1 << 30)), slots)
+    t0 = time.perf_counter()
+    ids = [vi.vi_server_submit(srv, d[0], TOL, MAX_ITERS) for d in descs]
+    left = dict(zip(ids, range(len(ids))))
+    upd_b = 0.0
+    while left:
+        for rid in list(left):
+            done, info = vi.vi_server_poll(srv, rid)
+            if done:
+                upd_b += nominal[left.pop(rid)] * info["iters"]
+        time.sleep(0.0002)
+    span_b = time.perf_counter() - t0
+    vi.vi_server_destroy(srv)
+    t0 = time.perf_counter()
+    upd_bs = 0.0
+    for k, d in enumerate(descs):
+        h = vi.vi_problem_create_desc(d[0])
+        n = vi.vi_problem_sizes(h)["n_states"]
+        info = vi.vi_solve_host(h, TOL, MAX_ITERS, np.empty(n, np.float64), np.empty(n, np.uint8))
+        vi.vi_problem_destroy(h)
+        upd_bs += nominal[k] * info["iters"]
+    span_bs = time.perf_counter() - t0
+    return {
+        "workload": f"{n_requests} single-product requests, Poisson arrivals 200/s, m 2..6, L 1..3, Q 8..20, seed {seed}",
+        "server": {"updates_per_s": upd / span_srv, "p50_ms": float(np.percentile(lat_srv, 50)),
+                   "p99_ms": float(np.percentile(lat_srv, 99)), "makespan_s": span_srv, "slots": slots},
+        "sequential": {"updates_per_s": upd_seq / span_seq, "p50_ms": float(np.percentile(lat_seq, 50)),
+                       "p99_ms": float(np.percentile(lat_seq, 99)), "makespan_s": span_seq},
+        "arrivals_span_s": reqs[-1].arrival_s,
+        "burst": {"server_updates_per_s": upd_b / span_b, "server_makespan_s": span_b,
+                  "sequential_updates_per_s": upd_bs / span_bs, "sequential_makespan_s": span_bs},
+    }
 
 
 def main():
@@ -346,6 +445,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle sample length (0 = skip)")
     ap.add_argument("--precision", default=None, choices=["fp32", "fp32_kahan", "fp64", "fp32_single"])
     ap.add_argument("--max-iters", type=int, default=MAX_ITERS)
+    ap.add_argument("--serving", type=int, default=512, help="requests in the serving mix (0 = skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -144,9 +144,15 @@ vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
  * VI_OPT_KERNEL: which sweep kernel runs -- VI_KERNEL_AUTO (factorised kernel
  * whenever the instance allows it), VI_KERNEL_GENERIC (one thread per state)
  * or VI_KERNEL_GROUP (factorised; VI_EINVAL if the instance does not allow it:
- * it needs one FP32 product with 2 <= Q+1 <= 24 and at least one state digit).
- * VI_OPT_PE_MAX_ITERS: sweep cap of the FP64 policy evaluation in vi_solve. */
-enum { VI_OPT_KERNEL = 1, VI_OPT_PE_MAX_ITERS = 2 };
+ * it needs one product, VI_PREC_FP32 or VI_PREC_FP32_SINGLE, 2 <= Q+1 <= 64 and
+ * at least one state digit).
+ * VI_OPT_PE_MAX_ITERS: sweep cap of the FP64 policy evaluation in vi_solve.
+ * VI_OPT_GROUP_WIDTH: run the factorised kernel with this many expiring-slot
+ * values per lane (1..12, 16, 21 or 24; Q+1 is split over ceil((Q+1)/width)
+ * lanes).  Without it the width is autotuned on the first solve (one timed
+ * sweep per candidate width, cached per instance shape; the environment
+ * variable VI_AUTOTUNE=0 selects a fixed rule instead). */
+enum { VI_OPT_KERNEL = 1, VI_OPT_PE_MAX_ITERS = 2, VI_OPT_GROUP_WIDTH = 3 };
 enum { VI_KERNEL_AUTO = 0, VI_KERNEL_GENERIC = 1, VI_KERNEL_GROUP = 2 };
 vi_status vi_problem_set_option(vi_handle h, int option, int value);
 
@@ -211,6 +217,34 @@ vi_status vi_next_states(vi_handle h, const uint32_t *states, int n, uint32_t *o
 vi_status vi_simulate(vi_handle h, const uint8_t *policy, int n_rollouts, int horizon,
                       int warmup, uint64_t seed, double *returns, double *kpis,
                       int32_t *traj, void *stream);
+
+/* Continuous-batching solve server (no counterpart in the paper; it serves the
+ * paper's value iteration to many callers).  Requests -- single-product
+ * instances with 2 <= Q+1 <= 24 and at least one state digit, solved in
+ * VI_PREC_FP32 with the span stopping test -- wait in arrival order and are
+ * admitted while a slot is free and their device memory (about 17 bytes per
+ * state) fits mem_budget_bytes.  A host worker thread with its own stream runs
+ * one batched sweep launch over all admitted instances per iteration, so
+ * instances of different sizes advance together; an instance whose stopping
+ * test passed gets its extraction sweep in the next launch and is then
+ * retired, freeing memory for queued requests.  `stream` is unused (the worker
+ * owns a stream); max_slots in 1..1024. */
+vi_status vi_server_create(size_t mem_budget_bytes, int max_slots, void *stream, vi_server *out);
+/* Queue a request; returns at once with its id.  The description is copied.
+ * VI_EINVAL for a bad description, VI_EBUSY if it can never fit the budget. */
+vi_status vi_server_submit(vi_server srv, const vi_problem_desc *desc, double tol, int max_iters,
+                           uint64_t *request_id);
+/* Poll a request.  done = 1 once finished; then V_host (host double[|S|],
+ * absolute values, or NULL) and policy_host (host uint8[|S|] or NULL) receive
+ * the result and info the solve record (wall_ms = submit-to-result latency,
+ * updates_per_s over the time the request held a slot).  Returns the request's
+ * status (VI_OK, VI_ENOTCONVERGED, VI_ECANCELLED, ...) once done, VI_OK while
+ * pending, VI_EINVAL for an unknown id.  A finished request is forgotten after
+ * it has been polled as done. */
+vi_status vi_server_poll(vi_server srv, uint64_t request_id, int *done, double *V_host,
+                         uint8_t *policy_host, vi_solve_info *info);
+/* Stop the worker and release everything.  Pending requests are cancelled. */
+vi_status vi_server_destroy(vi_server srv);
 
 const char *vi_status_string(vi_status s);
 const char *vi_last_error(void);

@@ -22,7 +22,7 @@ VI_FIFO, VI_LIFO = 0, 1
 VI_STOP_SPAN, VI_STOP_SUPNORM = 0, 1
 VI_PREC_FP32, VI_PREC_FP32_KAHAN, VI_PREC_FP64, VI_PREC_FP32_SINGLE = 0, 1, 2, 3
 VI_FLAG_WARM_START, VI_FLAG_NO_GRAPH, VI_FLAG_POLICY_EVAL = 1, 2, 4
-VI_OPT_KERNEL, VI_OPT_PE_MAX_ITERS = 1, 2
+VI_OPT_KERNEL, VI_OPT_PE_MAX_ITERS, VI_OPT_GROUP_WIDTH = 1, 2, 3
 VI_KERNEL_AUTO, VI_KERNEL_GENERIC, VI_KERNEL_GROUP = 0, 1, 2
 
 PRECISIONS = {"fp32": VI_PREC_FP32, "fp32_kahan": VI_PREC_FP32_KAHAN, "fp64": VI_PREC_FP64,
@@ -100,8 +100,6 @@ def lib() -> C.CDLL:
         "vi_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sigs.items():
-        if name.startswith("vi_server_") and not hasattr(L, name):
-            continue
         fn = getattr(L, name)
         fn.argtypes = args
         fn.restype = res
@@ -262,10 +260,12 @@ def vi_server_submit(srv: int, desc: vi_problem_desc, tol: float, max_iters: int
 
 def vi_server_poll(srv: int, request_id: int, V_host: Optional[np.ndarray] = None,
                    policy_host: Optional[np.ndarray] = None):
+    """Returns (done, info); info["status"] is the request's status once done."""
     done = C.c_int()
     info = vi_solve_info()
-    _check(lib().vi_server_poll(srv, request_id, C.byref(done), _addr(V_host), _addr(policy_host),
-                                C.byref(info)), "vi_server_poll")
+    st = lib().vi_server_poll(srv, request_id, C.byref(done), _addr(V_host), _addr(policy_host), C.byref(info))
+    if st not in (VI_OK, VI_ENOTCONVERGED, VI_ECANCELLED) or (not done.value and st != VI_OK):
+        _check(st, "vi_server_poll")
     return bool(done.value), info.as_dict()
 
 

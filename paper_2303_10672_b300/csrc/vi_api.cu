@@ -14,7 +14,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -353,7 +355,8 @@ extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_hand
     h->vk = (d.precision == VI_PREC_FP64) ? VK_DOUBLE : (d.precision == VI_PREC_FP32_SINGLE) ? VK_SINGLE : VK_PAIR;
     h->kahan = (d.precision == VI_PREC_FP32_KAHAN) ? 1 : 0;
     h->value_bytes = (h->vk == VK_SINGLE) ? 4 : 8;
-    h->use_group = group_supported(kp, h->vk, h->kahan);
+    h->group_ok = group_supported(kp, h->vk, h->kahan);
+    h->group_xw = 0;   // chosen by the autotuner on the first solve (or set explicitly)
     std::vector<float> fblob(blob.size());
     for (size_t i = 0; i < blob.size(); ++i) fblob[i] = (float)blob[i];
 
@@ -442,18 +445,34 @@ extern "C" vi_status vi_problem_set_option(vi_handle h, int option, int value) {
     if (!h) return vi_fail(VI_EINVAL, "null handle");
     if (option == VI_OPT_KERNEL) {
         if (value == VI_KERNEL_AUTO) {
-            h->use_group = group_supported(h->kp, h->vk, h->kahan);
+            h->kernel_choice = VI_KERNEL_AUTO;
         } else if (value == VI_KERNEL_GENERIC) {
-            h->use_group = false;
+            h->kernel_choice = VI_KERNEL_GENERIC;
         } else if (value == VI_KERNEL_GROUP) {
-            if (!group_supported(h->kp, h->vk, h->kahan))
+            if (!h->group_ok)
                 return vi_fail(VI_EINVAL,
                                "the factorised kernel needs one product, FP32 or FP32_SINGLE precision and "
                                "2 <= Q+1 <= %d", kMaxGroupG);
-            h->use_group = true;
+            h->kernel_choice = VI_KERNEL_GROUP;
         } else {
             return vi_fail(VI_EINVAL, "bad kernel choice %d", value);
         }
+        h->group_xw = 0;
+        if (h->graph_exec) {
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+        }
+        if (h->graph) {
+            cudaGraphDestroy(h->graph);
+            h->graph = nullptr;
+        }
+        return VI_OK;
+    }
+    if (option == VI_OPT_GROUP_WIDTH) {
+        if (!h->group_ok || !group_width_supported(value) || value > h->kp.p[0].G)
+            return vi_fail(VI_EINVAL, "lane width %d not available for this instance", value);
+        h->kernel_choice = VI_KERNEL_GROUP;
+        h->group_xw = value;
         if (h->graph_exec) {
             cudaGraphExecDestroy(h->graph_exec);
             h->graph_exec = nullptr;
@@ -473,6 +492,107 @@ extern "C" vi_status vi_problem_set_option(vi_handle h, int option, int value) {
 }
 
 // ---------------------------------------------------------------------------
+// kernel choice and autotuning of the factorised kernel's lane width
+// ---------------------------------------------------------------------------
+struct TuneKey {
+    int vk, issuing, m, L, Q, dmax;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(vk, issuing, m, L, Q, dmax) < std::tie(o.vk, o.issuing, o.m, o.L, o.Q, o.dmax);
+    }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, int> g_tune_cache;
+
+static int heuristic_width(int G, int lifo) {
+    // keep the per-lane register arrays small: at most 8 (FIFO) / 12 (LIFO) values per lane
+    const int cap = lifo ? 12 : 8;
+    int lanes = (G + cap - 1) / cap;
+    int w = (G + lanes - 1) / lanes;
+    while (!group_width_supported(w)) ++w;
+    return w;
+}
+
+static vi_status launch_desc(const LaunchDesc &ld, void **args, cudaStream_t s);
+
+// time one plain sweep per candidate width on scratch buffers, keep the fastest
+static vi_status autotune(vi_problem *h, cudaStream_t s) {
+    const ProdParams &P = h->kp.p[0];
+    const TuneKey key{h->vk, h->kp.issuing, P.m, P.L, P.Q, P.dmax};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            h->group_xw = it->second;
+            return VI_OK;
+        }
+    }
+    const char *env = getenv("VI_AUTOTUNE");
+    if (env && env[0] == '0') {
+        h->group_xw = heuristic_width(P.G, h->kp.issuing);
+        return VI_OK;
+    }
+    int cand[16];
+    const int nc = group_width_candidates(P.G, cand, 16);
+    const size_t nb = (size_t)h->kp.nS * h->value_bytes;
+    void *a = nullptr, *b = nullptr;
+    CUDA_TRY(cudaMallocAsync(&a, nb, s));
+    CUDA_TRY(cudaMallocAsync(&b, nb, s));
+    CUDA_TRY(cudaMemsetAsync(a, 0, nb, s));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = INFINITY;
+    int best = heuristic_width(P.G, h->kp.issuing);
+    KernelParams kp = h->kp;
+    int mode = MODE_PLAIN;
+    uint8_t *np = nullptr;
+    for (int i = 0; i < nc; ++i) {
+        LaunchDesc ld;
+        if (describe_sweep(kp, h->vk, h->kahan, cand[i], ld) != cudaSuccess) continue;
+        int lpr = ld.lpr;
+        void *args[] = {&kp, &mode, &a, &b, &np, &lpr};
+        float ms_min = INFINITY;
+        for (int rep = 0; rep < 3; ++rep) {
+            CUDA_TRY(cudaEventRecord(e0, s));
+            vi_status st = launch_desc(ld, args, s);
+            if (st != VI_OK) return st;
+            CUDA_TRY(cudaEventRecord(e1, s));
+            CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) ms_min = std::min(ms_min, ms);   // first launch warms caches and code
+        }
+        if (ms_min < best_ms) {
+            best_ms = ms_min;
+            best = cand[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CUDA_TRY(cudaFreeAsync(a, s));
+    CUDA_TRY(cudaFreeAsync(b, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    h->group_xw = best;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+    return VI_OK;
+}
+
+// resolve which sweep kernel runs: 0 = generic, > 0 = factorised with that lane width
+static vi_status choose_kernel(vi_problem *h, cudaStream_t s) {
+    if (h->kernel_choice == VI_KERNEL_GENERIC || !h->group_ok) {
+        h->sweep_xw = 0;
+        return VI_OK;
+    }
+    if (h->group_xw == 0) {
+        vi_status st = autotune(h, s);
+        if (st != VI_OK) return st;
+    }
+    h->sweep_xw = h->group_xw;
+    return VI_OK;
+}
+
+// ---------------------------------------------------------------------------
 // solve
 // ---------------------------------------------------------------------------
 static vi_status ensure_scratch(vi_problem *h) {
@@ -487,7 +607,16 @@ static vi_status launch_desc(const LaunchDesc &ld, void **args, cudaStream_t s) 
 }
 
 static vi_status build_graph(vi_problem *h) {
-    if (h->graph_exec) return VI_OK;
+    if (h->graph_exec && h->graph_xw == h->sweep_xw) return VI_OK;
+    if (h->graph_exec) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+    }
+    if (h->graph) {
+        cudaGraphDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->graph_xw = h->sweep_xw;
     cudaGraph_t g = nullptr;
     CUDA_TRY(cudaGraphCreate(&g, 0));
     h->graph = g;
@@ -497,13 +626,14 @@ static vi_status build_graph(vi_problem *h) {
 
     LaunchDesc ld_init, ld_sweep;
     CUDA_TRY(describe_solve_init(h->kp.nS, ld_init));
-    CUDA_TRY(describe_sweep(h->kp, h->vk, h->kahan, h->use_group ? 1 : 0, ld_sweep));
+    CUDA_TRY(describe_sweep(h->kp, h->vk, h->kahan, h->sweep_xw, ld_sweep));
     h->args_kp = h->kp;
     h->args_nS = h->kp.nS;
     h->args_mode_sweep = MODE_SWEEP;
     h->args_mode_extract = MODE_EXTRACT;
     h->args_null_v = nullptr;
     h->args_null_p = nullptr;
+    h->args_lpr = ld_sweep.lpr;
 
     cudaKernelNodeParams kn;
     memset(&kn, 0, sizeof(kn));
@@ -528,7 +658,8 @@ static vi_status build_graph(vi_problem *h) {
     CUDA_TRY(cudaGraphAddNode(&n_loop, g, &n_init, nullptr, 1, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
 
-    void *sweep_args[] = {&h->args_kp, &h->args_mode_sweep, &h->args_null_v, &h->args_null_v, &h->args_null_p};
+    void *sweep_args[] = {&h->args_kp, &h->args_mode_sweep, &h->args_null_v, &h->args_null_v, &h->args_null_p,
+                          &h->args_lpr};
     memset(&kn, 0, sizeof(kn));
     kn.func = (void *)ld_sweep.fn;
     kn.gridDim = ld_sweep.grid;
@@ -539,7 +670,7 @@ static vi_status build_graph(vi_problem *h) {
     CUDA_TRY(cudaGraphAddKernelNode(&n_sweep, body, nullptr, 0, &kn));
 
     void *extract_args[] = {&h->args_kp, &h->args_mode_extract, &h->args_null_v, &h->args_null_v,
-                            &h->args_null_p};
+                            &h->args_null_p, &h->args_lpr};
     kn.kernelParams = extract_args;
     cudaGraphNode_t n_extract;
     CUDA_TRY(cudaGraphAddKernelNode(&n_extract, g, &n_loop, 1, &kn));
@@ -552,7 +683,7 @@ static vi_status build_graph(vi_problem *h) {
 static vi_status run_host_loop(vi_problem *h, cudaStream_t s) {
     LaunchDesc ld_init, ld_sweep;
     CUDA_TRY(describe_solve_init(h->kp.nS, ld_init));
-    CUDA_TRY(describe_sweep(h->kp, h->vk, h->kahan, h->use_group ? 1 : 0, ld_sweep));
+    CUDA_TRY(describe_sweep(h->kp, h->vk, h->kahan, h->sweep_xw, ld_sweep));
     KernelParams kp = h->kp;
     uint32_t nS = kp.nS;
     int mode_sweep = MODE_SWEEP, mode_extract = MODE_EXTRACT;
@@ -561,7 +692,8 @@ static vi_status run_host_loop(vi_problem *h, cudaStream_t s) {
     void *init_args[] = {&kp.st, &nS};
     vi_status st = launch_desc(ld_init, init_args, s);
     if (st != VI_OK) return st;
-    void *sweep_args[] = {&kp, &mode_sweep, &nv, &nv, &np};
+    int lpr = ld_sweep.lpr;
+    void *sweep_args[] = {&kp, &mode_sweep, &nv, &nv, &np, &lpr};
     const int batch = 4;
     int launched = 0;
     while (launched < h->h_state->max_iters) {
@@ -573,7 +705,7 @@ static vi_status run_host_loop(vi_problem *h, cudaStream_t s) {
         CUDA_TRY(cudaStreamSynchronize(s));
         if (!h->h_state->keep_going) break;
     }
-    void *extract_args[] = {&kp, &mode_extract, &nv, &nv, &np};
+    void *extract_args[] = {&kp, &mode_extract, &nv, &nv, &np, &lpr};
     return launch_desc(ld_sweep, extract_args, s);
 }
 
@@ -588,6 +720,8 @@ extern "C" vi_status vi_solve(vi_handle h, double tol, int max_iters, void *V, u
     if ((flags & VI_FLAG_WARM_START) && !info) return vi_fail(VI_EINVAL, "warm start needs info->offset");
     cudaStream_t s = (cudaStream_t)stream;
     vi_status st = ensure_scratch(h);
+    if (st != VI_OK) return st;
+    st = choose_kernel(h, s);
     if (st != VI_OK) return st;
 
     const bool use_graph = !(flags & VI_FLAG_NO_GRAPH);
@@ -687,13 +821,16 @@ extern "C" vi_status vi_backup(vi_handle h, const void *V_in, void *V_out, uint8
     if (!h) return vi_fail(VI_EINVAL, "null handle");
     if (!V_in || !V_out || V_in == V_out) return vi_fail(VI_EINVAL, "V_in and V_out must be distinct buffers");
     cudaStream_t s = (cudaStream_t)stream;
+    vi_status cs = choose_kernel(h, s);
+    if (cs != VI_OK) return cs;
     LaunchDesc ld;
-    CUDA_TRY(describe_sweep(h->kp, h->vk, h->kahan, h->use_group ? 1 : 0, ld));
+    CUDA_TRY(describe_sweep(h->kp, h->vk, h->kahan, h->sweep_xw, ld));
     KernelParams kp = h->kp;
     int mode = MODE_PLAIN;
     const void *vin = V_in;
     void *vout = V_out;
-    void *args[] = {&kp, &mode, &vin, &vout, &policy};
+    int lpr = ld.lpr;
+    void *args[] = {&kp, &mode, &vin, &vout, &policy, &lpr};
     vi_status st = launch_desc(ld, args, s);
     if (st != VI_OK) return st;
     if (dstats) {

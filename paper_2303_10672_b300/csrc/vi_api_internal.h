@@ -16,7 +16,11 @@ struct vi_problem {
     int value_bytes = 4;
     int vk = 0;                        // value kind (VK_SINGLE / VK_PAIR / VK_DOUBLE)
     int kahan = 0;                     // compensated sums over outcomes
-    bool use_group = false;            // factorised kernel for this instance
+    bool group_ok = false;             // the factorised kernel can run this instance
+    int kernel_choice = 0;             // VI_KERNEL_AUTO / _GENERIC / _GROUP
+    int group_xw = 0;                  // lane width of the factorised kernel (0 = not chosen yet)
+    int sweep_xw = 0;                  // kernel of the next launches: 0 generic, else lane width
+    int graph_xw = -1;                 // kernel captured in the graph
     int pe_max_iters = 100000;
     // device resources
     float *d_tab_f = nullptr;
@@ -36,6 +40,7 @@ struct vi_problem {
     vib::KernelParams args_kp;
     uint32_t args_nS = 0;
     int args_mode_sweep = 0, args_mode_extract = 1;
+    int args_lpr = 0;
     void *args_null_v = nullptr;
     uint8_t *args_null_p = nullptr;
 };

@@ -68,7 +68,7 @@ __device__ __forceinline__ void warp_minmax(T &mx, T &mn) {
 // All threads of the block call this.  Folds (mx, mn) of the block into the
 // global accumulators; the last block of the grid then finalises the sweep.
 template <typename T>
-__device__ void block_reduce_and_finalize(T mx, T mn, SolveState *st, int mode) {
+__device__ void block_reduce_and_finalize(T mx, T mn, SolveState *st, int mode, unsigned n_blocks) {
     __shared__ T s_mx[32], s_mn[32];
     __shared__ int s_last;
     warp_minmax<T>(mx, mn);
@@ -88,7 +88,7 @@ __device__ void block_reduce_and_finalize(T mx, T mn, SolveState *st, int mode) 
             atomicMin(&st->key_min, dkey((double)mn));
             __threadfence();
             const unsigned prev = atomicAdd(&st->blocks_done, 1u);
-            s_last = (prev == gridDim.x - 1);
+            s_last = (prev == n_blocks - 1);
         }
     }
     __syncthreads();
@@ -209,48 +209,58 @@ __device__ __forceinline__ float2 pair_finish(float gam, float2 R0, float bh, fl
 }
 
 // ===========================================================================
-// factorised single-product sweep: thread = rest index r (digits 1..K-1 of s),
-// registers hold the G values of the expiring slot x = digit 0 of s.
+// factorised single-product sweep.  A rest index r (digits 1..K-1 of s) is
+// handled by `lpr` consecutive lanes; lane `part` owns the XW values
+// x = part*XW .. part*XW+XW-1 of the expiring slot (digit 0 of s), kept in
+// registers.  For a given order a the next states only depend on r, a and the
+// demand e that reaches the other slots, g(e) = V[s'(r, a, e)]:
 //   FIFO: C(x) = sum_d p_d g(clamp(d - x, 0, R))   (x is issued first)
 //   LIFO: C    = sum_d p_d g(min(d, R))            (x is issued last)
-// g(e) = V[s'(r, a, e)] follows the walker.  The FIFO correlation runs in
-// chunks of G demands over a register window of gathered values.
+// The FIFO correlation runs in chunks of XW demands over a register window of
+// gathered values; each chunk first walks the next-state indices, then issues
+// all of its loads, then consumes them, so the loads overlap.
 // ===========================================================================
-template <int G, int LIFO, int VK>
-__global__ void __launch_bounds__(kGroupThreads)
-sweep_group_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+template <int XW, int LIFO, int VK>
+__device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid, unsigned n_blocks, int mode,
+                                           const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int lpr,
+                                           unsigned char *smem_raw) {
     constexpr bool PAIR = (VK == VK_PAIR);
+    constexpr int LCH = 8;   // LIFO load batch
     SolveState *st = kp.st;
     Bufs B;
     if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
     const ProdParams &P = kp.p[0];
+    const int G = P.G;
+    const int RB = kGroupThreads / lpr;                    // rests per block
     float *s_tab = (float *)smem_raw;
-    float *s_out = s_tab + ((kp.n_tables + 3) & ~3);          // PAIR: float2 per state
-    uint8_t *s_pol = (uint8_t *)(s_out + kGroupThreads * G * (PAIR ? 2 : 1));
+    float *s_out = s_tab + ((kp.n_tables + 3) & ~3);       // PAIR: float2 per state
+    uint8_t *s_pol = (uint8_t *)(s_out + RB * G * (PAIR ? 2 : 1));
     load_tables<float>(s_tab, (const float *)kp.tables, kp.n_tables);
     const float *s_p = s_tab + P.off_p;
     const float *s_RT = s_tab + P.off_RT;
     const float *s_RTlo = s_tab + P.off_RTlo;
 
     const uint32_t nR = P.nS / (uint32_t)G;
-    const uint32_t r0 = blockIdx.x * (uint32_t)kGroupThreads;
-    const uint32_t r = r0 + threadIdx.x;
+    const int rl = threadIdx.x / lpr;
+    const int part = threadIdx.x - rl * lpr;
+    const uint32_t r = bid * (uint32_t)RB + (uint32_t)rl;
+    const bool active = (rl < RB) && (r < nR);
+    const int x0 = part * XW;
+    const int nx = min(XW, G - x0);                        // >= 1 because lpr = ceil(G / XW)
     const float gam = (float)kp.gamma;
     const float c_o = (float)P.c_o;
     const int dmax = P.dmax;
-    const int nch = (dmax + G) / G;      // chunks of G demands covering 0..dmax
 
-    float bh[G], bl[G];
-    int arg[G];
+    float bh[XW], bl[XW];
+    int arg[XW];
 #pragma unroll
-    for (int x = 0; x < G; ++x) {
-        bh[x] = -INFINITY;
-        bl[x] = 0.f;
-        arg[x] = 0;
+    for (int xi = 0; xi < XW; ++xi) {
+        bh[xi] = -INFINITY;
+        bl[xi] = 0.f;
+        arg[xi] = 0;
     }
     float2 R0 = make_float2(0.f, 0.f);
-    if (r < nR) {
+    if (active) {
         const RestInfo ri = decode_rest(r, P);
         const float *V1 = (const float *)B.vin;
         const float2 *V2 = (const float2 *)B.vin;
@@ -263,109 +273,135 @@ sweep_group_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
             const uint32_t idx0 = r + (uint32_t)a * P.w_top;
             walker_init(wk, idx0, packed, P.m - 1, P.cb, LIFO, P.w_zt);
             float2 ref = make_float2(0.f, 0.f);
-            if (PAIR) ref = __ldg(V2 + idx0);
-            // gathered value: absolute (single) or relative to ref (pair)
-            auto gather = [&](uint32_t i) -> float {
-                if (PAIR) return pair_diff(__ldg(V2 + i), ref);
-                return __ldg(V1 + i);
-            };
-            float acc[G];
-            const float g0 = PAIR ? 0.f : gather(idx0);
+            float g0 = 0.f;
+            if (PAIR)
+                ref = __ldg(V2 + idx0);
+            else
+                g0 = __ldg(V1 + idx0);
+            float acc[XW];
             if (!LIFO) {
-                float gprev[G];
+                // lane-local demand axis dd = d - x0: C(x0+xi) = sum_dd p[dd+x0] g(clamp(dd-xi, 0, R))
+                float gprev[XW];
 #pragma unroll
-                for (int x = 0; x < G; ++x) {
-                    acc[x] = 0.f;
-                    gprev[x] = g0;
+                for (int xi = 0; xi < XW; ++xi) {
+                    acc[xi] = 0.f;
+                    gprev[xi] = g0;
                 }
-                float glast = g0;
+                int ecur = 0;
+                const int nch = (dmax + XW) / XW;
                 for (int c = 0; c < nch; ++c) {
-                    const int d0 = c * G;
-                    float gcur[G];
+                    const int d0 = c * XW - x0;
+                    uint32_t idx[XW];
 #pragma unroll
-                    for (int j = 0; j < G; ++j) {
-                        const int e = d0 + j;
-                        if (e >= 1 && e <= R) {
-                            walker_step(wk, P.cb, 0, (uint32_t)G);
-                            glast = gather(wk.idx);
-                        }
-                        gcur[j] = glast;
+                    for (int j = 0; j < XW; ++j) {
+                        const int e = min(max(d0 + j, 0), R);
+                        for (; ecur < e; ++ecur) walker_step(wk, P.cb, 0, (uint32_t)G);
+                        idx[j] = wk.idx;
+                    }
+                    float gcur[XW];
+                    if (PAIR) {
+                        float2 raw[XW];
+#pragma unroll
+                        for (int j = 0; j < XW; ++j) raw[j] = __ldg(V2 + idx[j]);
+#pragma unroll
+                        for (int j = 0; j < XW; ++j) gcur[j] = pair_diff(raw[j], ref);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < XW; ++j) gcur[j] = __ldg(V1 + idx[j]);
                     }
 #pragma unroll
-                    for (int j = 0; j < G; ++j) {
-                        const float pd = s_p[d0 + j];
+                    for (int j = 0; j < XW; ++j) {
+                        const float pd = s_p[d0 + x0 + j];
 #pragma unroll
-                        for (int x = 0; x < G; ++x) {
-                            const int e = j - x;
-                            const float gv = (e >= 0) ? gcur[e] : gprev[G + e];
-                            acc[x] = fmaf(pd, gv, acc[x]);
+                        for (int xi = 0; xi < XW; ++xi) {
+                            const int k = j - xi;
+                            const float gv = (k >= 0) ? gcur[k] : gprev[XW + k];
+                            acc[xi] = fmaf(pd, gv, acc[xi]);
                         }
                     }
 #pragma unroll
-                    for (int j = 0; j < G; ++j) gprev[j] = gcur[j];
+                    for (int j = 0; j < XW; ++j) gprev[j] = gcur[j];
                 }
             } else {
                 float c = 0.f;
-                float g = g0;
-                for (int d = 0; d <= dmax; ++d) {
-                    if (d >= 1 && d <= R) {
-                        walker_step(wk, P.cb, 1, (uint32_t)G);
-                        g = gather(wk.idx);
+                int ecur = 0;
+                for (int d0 = 0; d0 <= dmax; d0 += LCH) {
+                    uint32_t idx[LCH];
+#pragma unroll
+                    for (int j = 0; j < LCH; ++j) {
+                        const int e = min(d0 + j, R);
+                        for (; ecur < e; ++ecur) walker_step(wk, P.cb, 1, (uint32_t)G);
+                        idx[j] = wk.idx;
                     }
-                    c = fmaf(s_p[d], g, c);
+                    float gv[LCH];
+                    if (PAIR) {
+                        float2 raw[LCH];
+#pragma unroll
+                        for (int j = 0; j < LCH; ++j) raw[j] = __ldg(V2 + idx[j]);
+#pragma unroll
+                        for (int j = 0; j < LCH; ++j) gv[j] = pair_diff(raw[j], ref);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < LCH; ++j) gv[j] = __ldg(V1 + idx[j]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < LCH; ++j) c = fmaf(s_p[d0 + j], gv[j], c);   // zero mass beyond dmax
                 }
 #pragma unroll
-                for (int x = 0; x < G; ++x) acc[x] = c;
+                for (int xi = 0; xi < XW; ++xi) acc[xi] = c;
             }
-            const float *rt = s_RT + R * G;
+            const float *rt = s_RT + R * G + x0;
             if (PAIR) {
                 float Bh, Bl;
                 action_base(gam, ref, R0, __fmul_rn(-c_o, (float)a), Bh, Bl);
-                const float *rtl = s_RTlo + R * G;
+                const float *rtl = s_RTlo + R * G + x0;
 #pragma unroll
-                for (int x = 0; x < G; ++x) {
-                    float qh = Bh, ql = Bl;
-                    pair_add(qh, ql, rt[x], rtl[x]);
-                    ql = __fmaf_rn(gam, acc[x], ql);
-                    const float diff = __fadd_rn(__fsub_rn(qh, bh[x]), __fsub_rn(ql, bl[x]));
-                    if (diff > 0.f) {
-                        bh[x] = qh;
-                        bl[x] = ql;
-                        arg[x] = a;
+                for (int xi = 0; xi < XW; ++xi) {
+                    if (xi < nx) {
+                        float qh = Bh, ql = Bl;
+                        pair_add(qh, ql, rt[xi], rtl[xi]);
+                        ql = __fmaf_rn(gam, acc[xi], ql);
+                        const float diff = __fadd_rn(__fsub_rn(qh, bh[xi]), __fsub_rn(ql, bl[xi]));
+                        if (diff > 0.f) {
+                            bh[xi] = qh;
+                            bl[xi] = ql;
+                            arg[xi] = a;
+                        }
                     }
                 }
             } else {
                 const float base = -c_o * (float)a;
 #pragma unroll
-                for (int x = 0; x < G; ++x) {
-                    const float q = fmaf(gam, acc[x], base + rt[x]);
-                    if (q > bh[x]) {
-                        bh[x] = q;
-                        arg[x] = a;
+                for (int xi = 0; xi < XW; ++xi) {
+                    if (xi < nx) {
+                        const float q = fmaf(gam, acc[xi], base + rt[xi]);
+                        if (q > bh[xi]) {
+                            bh[xi] = q;
+                            arg[xi] = a;
+                        }
                     }
                 }
             }
         }
-        if (!PAIR && r == 0 && mode == MODE_SWEEP) st->c_next = bh[0];
+        if (!PAIR && r == 0 && part == 0 && mode == MODE_SWEEP) st->c_next = bh[0];
     }
-    // stage the block's G * kGroupThreads contiguous states through shared memory
-    if (PAIR) {
-        float2 *s_out2 = (float2 *)s_out;
+    // stage the block's G * RB contiguous states through shared memory
+    if (rl < RB) {
 #pragma unroll
-        for (int x = 0; x < G; ++x) {
-            s_out2[threadIdx.x * G + x] = (r < nR) ? pair_finish(gam, R0, bh[x], bl[x]) : make_float2(0.f, 0.f);
-            s_pol[threadIdx.x * G + x] = (uint8_t)arg[x];
-        }
-    } else {
-#pragma unroll
-        for (int x = 0; x < G; ++x) {
-            s_out[threadIdx.x * G + x] = bh[x];
-            s_pol[threadIdx.x * G + x] = (uint8_t)arg[x];
+        for (int xi = 0; xi < XW; ++xi) {
+            if (xi < nx) {
+                const int o = rl * G + x0 + xi;
+                if (PAIR)
+                    ((float2 *)s_out)[o] = active ? pair_finish(gam, R0, bh[xi], bl[xi]) : make_float2(0.f, 0.f);
+                else
+                    s_out[o] = bh[xi];
+                s_pol[o] = (uint8_t)arg[xi];
+            }
         }
     }
     __syncthreads();
-    const uint32_t s0 = r0 * (uint32_t)G;
-    const uint32_t nblk = kGroupThreads * G;
+    const uint32_t s0 = bid * (uint32_t)(RB * G);
+    const uint32_t nblk = (uint32_t)(RB * G);
     float mx = -INFINITY, mn = INFINITY;
     for (uint32_t i = threadIdx.x; i < nblk; i += kGroupThreads) {
         const uint32_t s = s0 + i;
@@ -399,7 +435,46 @@ sweep_group_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
         }
         if (B.pol) B.pol[s] = s_pol[i];
     }
-    if (mode != MODE_EXTRACT) block_reduce_and_finalize<float>(mx, mn, st, mode);
+    if (mode != MODE_EXTRACT) block_reduce_and_finalize<float>(mx, mn, st, mode, n_blocks);
+}
+
+template <int XW, int LIFO, int VK>
+__global__ void __launch_bounds__(kGroupThreads)
+sweep_group_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int lpr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    group_body<XW, LIFO, VK>(kp, blockIdx.x, gridDim.x, mode, vin_arg, vout_arg, pol_arg, lpr, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// batched sweep for the solve server: one launch covers every active instance.
+// Block b belongs to the slot s with block_start[s] <= b < block_start[s+1];
+// each slot has its own tables, value buffers and SolveState.
+// ---------------------------------------------------------------------------
+template <int XW>
+__global__ void __launch_bounds__(kGroupThreads)
+sweep_batch_kernel(const KernelParams *kps, const int *modes, const int *lprs, const uint32_t *block_start,
+                   int n_slots) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ KernelParams s_kp;
+    __shared__ int s_slot;
+    const uint32_t b = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_slots - 1;   // last slot with block_start <= b
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (block_start[mid] <= b) lo = mid; else hi = mid - 1;
+        }
+        s_slot = lo;
+        s_kp = kps[lo];
+    }
+    __syncthreads();
+    const int s = s_slot;
+    const unsigned nb = block_start[s + 1] - block_start[s];
+    const uint32_t local = b - block_start[s];
+    if (s_kp.issuing)
+        group_body<XW, 1, VK_PAIR>(s_kp, local, nb, modes[s], nullptr, nullptr, nullptr, lprs[s], smem_raw);
+    else
+        group_body<XW, 0, VK_PAIR>(s_kp, local, nb, modes[s], nullptr, nullptr, nullptr, lprs[s], smem_raw);
 }
 
 // ===========================================================================
@@ -645,7 +720,7 @@ __device__ __forceinline__ void q_two_pair(const KernelParams &kp, const float *
 // ===========================================================================
 template <int VK, int KAHAN>
 __global__ void __launch_bounds__(kGenericThreads)
-sweep_generic_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg) {
+sweep_generic_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int) {
     using T = typename std::conditional<VK == VK_DOUBLE, double, float>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SolveState *st = kp.st;
@@ -723,7 +798,7 @@ sweep_generic_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_
         }
         if (B.pol) B.pol[s] = (uint8_t)arg;
     }
-    if (mode != MODE_EXTRACT) block_reduce_and_finalize<T>(mx, mn, st, mode);
+    if (mode != MODE_EXTRACT) block_reduce_and_finalize<T>(mx, mn, st, mode, gridDim.x);
 }
 
 // ===========================================================================
@@ -806,7 +881,7 @@ policy_eval_kernel(KernelParams kp, const uint8_t *policy, const double *vin, do
         vout[s] = q;
         mx = mn = q - vin[s];
     }
-    block_reduce_and_finalize<double>(mx, mn, kp.st, MODE_PLAIN);
+    block_reduce_and_finalize<double>(mx, mn, kp.st, MODE_PLAIN, gridDim.x);
 }
 
 // V_abs in FP64 from any value kind
@@ -828,7 +903,7 @@ __global__ void absdiff_kernel(const double *a, const double *b, uint32_t n, Sol
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     double d = 0.0;
     if (i < n) d = fabs(a[i] - b[i]);
-    block_reduce_and_finalize<double>(d, d, st, MODE_PLAIN);
+    block_reduce_and_finalize<double>(d, d, st, MODE_PLAIN, gridDim.x);
 }
 
 // ===========================================================================
@@ -1000,32 +1075,44 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
 // ===========================================================================
 // launch descriptors and launchers
 // ===========================================================================
-static size_t group_smem(const KernelParams &kp, int G, int vk) {
+static size_t group_smem(const KernelParams &kp, int rb, int vk) {
+    const int G = kp.p[0].G;
     const size_t vb = (vk == VK_PAIR) ? 8 : 4;
-    return (size_t)((kp.n_tables + 3) & ~3) * 4 + (size_t)kGroupThreads * G * (vb + 1);
+    return (size_t)((kp.n_tables + 3) & ~3) * 4 + (size_t)rb * G * (vb + 1);
 }
 
-template <int G, int LIFO, int VK>
+template <int XW, int LIFO, int VK>
 static cudaError_t describe_group_t(const KernelParams &kp, LaunchDesc &d) {
+    const int G = kp.p[0].G;
+    const int lpr = (G + XW - 1) / XW;
+    const int rb = kGroupThreads / lpr;
     const uint32_t nR = kp.p[0].nS / (uint32_t)G;
-    d.fn = (const void *)sweep_group_kernel<G, LIFO, VK>;
-    d.grid = dim3((nR + kGroupThreads - 1) / kGroupThreads);
+    d.fn = (const void *)sweep_group_kernel<XW, LIFO, VK>;
+    d.grid = dim3((nR + rb - 1) / rb);
     d.block = dim3(kGroupThreads);
-    d.smem = group_smem(kp, G, VK);
-    return cudaFuncSetAttribute(sweep_group_kernel<G, LIFO, VK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    d.smem = group_smem(kp, rb, VK);
+    d.lpr = lpr;
+    return cudaFuncSetAttribute(sweep_group_kernel<XW, LIFO, VK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)d.smem);
 }
 
 template <int LIFO, int VK>
-static cudaError_t describe_group_l(const KernelParams &kp, LaunchDesc &d) {
-    switch (kp.p[0].G) {
-#define VIB_G(g) \
-    case g: return describe_group_t<g, LIFO, VK>(kp, d);
-        VIB_G(2) VIB_G(3) VIB_G(4) VIB_G(5) VIB_G(6) VIB_G(7) VIB_G(8) VIB_G(9) VIB_G(10) VIB_G(11)
-        VIB_G(12) VIB_G(13) VIB_G(14) VIB_G(15) VIB_G(16) VIB_G(17) VIB_G(18) VIB_G(19) VIB_G(20)
-        VIB_G(21) VIB_G(22) VIB_G(23) VIB_G(24)
-#undef VIB_G
+static cudaError_t describe_group_l(const KernelParams &kp, int xw, LaunchDesc &d) {
+    switch (xw) {
+#define VIB_XW(w) \
+    case w: return describe_group_t<w, LIFO, VK>(kp, d);
+        VIB_XW(1) VIB_XW(2) VIB_XW(3) VIB_XW(4) VIB_XW(5) VIB_XW(6) VIB_XW(7) VIB_XW(8) VIB_XW(9) VIB_XW(10)
+        VIB_XW(11) VIB_XW(12) VIB_XW(16) VIB_XW(21) VIB_XW(24)
+#undef VIB_XW
         default: return cudaErrorInvalidValue;
+    }
+}
+
+bool group_width_supported(int xw) {
+    switch (xw) {
+        case 1: case 2: case 3: case 4: case 5: case 6: case 7: case 8: case 9: case 10: case 11: case 12:
+        case 16: case 21: case 24: return true;
+        default: return false;
     }
 }
 
@@ -1047,14 +1134,103 @@ bool group_supported(const KernelParams &kp, int vk, int kahan) {
            P.G <= kMaxGroupG;
 }
 
+// lane widths worth trying for an instance: G itself and G split over 2..4 lanes,
+// rounded up to an instantiated width, plus a few small widths
+int group_width_candidates(int G, int *out, int max_out) {
+    const int base[] = {G, (G + 1) / 2, (G + 2) / 3, (G + 3) / 4, 8, 6, 4};
+    int n = 0;
+    for (int w : base) {
+        while (w <= 24 && !group_width_supported(w)) ++w;
+        if (w > 24 || w < 1 || w > G) continue;
+        if ((G + w - 1) / w > kGroupThreads) continue;
+        bool seen = false;
+        for (int i = 0; i < n; ++i) seen |= (out[i] == w);
+        if (!seen && n < max_out) out[n++] = w;
+    }
+    return n;
+}
+
 cudaError_t describe_sweep(const KernelParams &kp, int vk, int kahan, int use_group, LaunchDesc &d) {
+    d.lpr = 0;
     if (use_group) {
-        if (vk == VK_PAIR) return kp.issuing ? describe_group_l<1, VK_PAIR>(kp, d) : describe_group_l<0, VK_PAIR>(kp, d);
-        return kp.issuing ? describe_group_l<1, VK_SINGLE>(kp, d) : describe_group_l<0, VK_SINGLE>(kp, d);
+        const int xw = use_group;   // lane width of the factorised kernel
+        if (vk == VK_PAIR)
+            return kp.issuing ? describe_group_l<1, VK_PAIR>(kp, xw, d) : describe_group_l<0, VK_PAIR>(kp, xw, d);
+        return kp.issuing ? describe_group_l<1, VK_SINGLE>(kp, xw, d) : describe_group_l<0, VK_SINGLE>(kp, xw, d);
     }
     if (vk == VK_DOUBLE) return describe_generic_t<VK_DOUBLE, 0>(kp, d);
     if (vk == VK_PAIR) return kahan ? describe_generic_t<VK_PAIR, 1>(kp, d) : describe_generic_t<VK_PAIR, 0>(kp, d);
     return kahan ? describe_generic_t<VK_SINGLE, 1>(kp, d) : describe_generic_t<VK_SINGLE, 0>(kp, d);
+}
+
+// lane-width class of the batched server kernel for an instance: one lane per
+// rest with the smallest instantiated width >= Q+1 (two lanes above 24)
+int batch_width(int G) {
+    if (G <= 8) return 8;
+    if (G <= 12) return 12;
+    if (G <= 16) return 16;
+    if (G <= 21) return 21;
+    return 24;
+}
+
+// blocks and shared memory the batched kernel needs for one slot
+void batch_geometry(const KernelParams &kp, int *lpr, uint32_t *blocks, size_t *smem) {
+    const int G = kp.p[0].G;
+    const int xw = batch_width(G);
+    const int l = (G + xw - 1) / xw;
+    const int rb = kGroupThreads / l;
+    *lpr = l;
+    *blocks = (kp.p[0].nS / (uint32_t)G + rb - 1) / rb;
+    *smem = group_smem(kp, rb, VK_PAIR);
+}
+
+template <int XW>
+static cudaError_t launch_batch_t(const KernelParams *kps, const int *modes, const int *lprs,
+                                  const uint32_t *block_start, int n_slots, uint32_t total_blocks, size_t smem,
+                                  cudaStream_t stream) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_batch_kernel<XW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    sweep_batch_kernel<XW><<<total_blocks, kGroupThreads, smem, stream>>>(kps, modes, lprs, block_start, n_slots);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_batch(int xw, const KernelParams *kps, const int *modes, const int *lprs,
+                               const uint32_t *block_start, int n_slots, uint32_t total_blocks, size_t smem,
+                               cudaStream_t stream) {
+    switch (xw) {
+        case 8: return launch_batch_t<8>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
+        case 12: return launch_batch_t<12>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
+        case 16: return launch_batch_t<16>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
+        case 21: return launch_batch_t<21>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
+        case 24: return launch_batch_t<24>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// compact per-slot status for the server's host loop
+__global__ void gather_status_kernel(SolveState *const *sts, int n, SlotStatus *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const SolveState *st = sts[i];
+    out[i].iter = st->iter;
+    out[i].keep_going = st->keep_going;
+    out[i].converged = st->converged;
+    out[i].crit = st->crit;
+}
+
+cudaError_t launch_gather_status(SolveState *const *sts, int n, SlotStatus *out, cudaStream_t stream) {
+    gather_status_kernel<<<(n + 63) / 64, 64, 0, stream>>>(sts, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_init(SolveState *st, uint32_t n, cudaStream_t stream) {
+    solve_init_kernel<<<(n + 255) / 256, 256, 0, stream>>>(st, n);
+    return cudaGetLastError();
 }
 
 cudaError_t describe_solve_init(uint32_t n, LaunchDesc &d) {

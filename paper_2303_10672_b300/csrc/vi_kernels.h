@@ -20,7 +20,7 @@ enum { VK_SINGLE = 0, VK_PAIR = 1, VK_DOUBLE = 2 };
 
 constexpr int kGroupThreads = 128;   // rests per block of the factorised kernel
 constexpr int kGenericThreads = 128;
-constexpr int kMaxGroupG = 24;       // largest Q+1 with a factorised instantiation
+constexpr int kMaxGroupG = 64;       // largest Q+1 run by the factorised kernel (lane width <= 24)
 constexpr int kMaxRollDmax = 255;
 
 struct RollParams {
@@ -45,8 +45,22 @@ struct LaunchDesc {
     const void *fn;
     dim3 grid, block;
     size_t smem;
+    int lpr;    // lanes per rest of the factorised kernel (0 for the generic kernel)
 };
+// use_group = 0: generic kernel; > 0: factorised kernel with that lane width XW
 cudaError_t describe_sweep(const KernelParams &kp, int vk, int kahan, int use_group, LaunchDesc &d);
+bool group_width_supported(int xw);
+int batch_width(int G);
+void batch_geometry(const KernelParams &kp, int *lpr, uint32_t *blocks, size_t *smem);
+cudaError_t launch_sweep_batch(int xw, const KernelParams *kps, const int *modes, const int *lprs,
+                               const uint32_t *block_start, int n_slots, uint32_t total_blocks, size_t smem,
+                               cudaStream_t stream);
+struct SlotStatus {
+    int iter, keep_going, converged, pad;
+    double crit;
+};
+cudaError_t launch_gather_status(SolveState *const *sts, int n, SlotStatus *out, cudaStream_t stream);
+int group_width_candidates(int G, int *out, int max_out);
 cudaError_t describe_solve_init(uint32_t n, LaunchDesc &d);
 cudaError_t launch_rollouts(const KernelParams &kp, const RollParams &rp, const uint8_t *policy,
                             double *returns, double *kpis, int32_t *traj, cudaStream_t stream);

@@ -338,3 +338,35 @@ def test_invalid_arguments():
             vi.vi_problem_set_option(h, vi.VI_OPT_KERNEL, 99)
     finally:
         vi.vi_problem_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# lane widths of the factorised kernel: the demand sums keep their order, so
+# every width gives bit-identical values and policies
+# ---------------------------------------------------------------------------
+
+WIDTH_CASES = [
+    workloads.single_product(3, 2, 9, (2, 1, 4, 3, 0), workloads.poisson_pmf(3.0, 13), 0.95, FIFO),
+    workloads.single_product(4, 1, 7, (2, 1, 4, 3, 0), workloads.poisson_pmf(2.5, 11), 0.95, LIFO),
+    workloads.single_product(2, 3, 12, (3, 1, 5, 7, 1), workloads.poisson_pmf(5.0, 20), 0.9, FIFO),
+    workloads.single_product(3, 1, 20, (3, 1, 5, 7, 0), workloads.poisson_pmf(5.0, 25), 0.99, LIFO),
+]
+
+
+@pytest.mark.parametrize("inst", WIDTH_CASES, ids=_ids(WIDTH_CASES))
+@pytest.mark.parametrize("precision", ["fp32", "fp32_single"])
+def test_group_widths_bit_identical(inst, precision):
+    G = inst.products[0].Q + 1
+    widths = [w for w in (1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 16, 21, 24) if w <= G]
+    ref = None
+    for w in widths:
+        with Handle(inst, precision=precision) as H:
+            vi.vi_problem_set_option(H.h, vi.VI_OPT_GROUP_WIDTH, w)
+            V, pol, info = H.solve(0.0, 12)
+            got = (V.cpu().numpy().tobytes(), pol.cpu().numpy().tobytes(), info["offset"])
+        if ref is None:
+            ref = got
+        else:
+            assert got == ref, f"width {w} differs"
+    # and the autotuned choice matches the oracle
+    solve_parity(inst, precision)

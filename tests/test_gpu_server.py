@@ -1,0 +1,124 @@
+"""Continuous-batching solve server: every result equals the same instance solved
+alone, admission respects the memory budget, and shutdown cancels pending work."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+vi = pytest.importorskip("paper_2303_10672_b300")
+from gpu_helpers import Handle, compare_values, policy_mismatches, V_RTOL  # noqa: E402
+
+
+def desc_of(inst):
+    p = inst.products[0]
+    return vi.make_desc([dict(m=p.m, L=p.L, Q=p.Q, cost=p.cost, pmf=p.pmf)], inst.gamma, inst.issuing)
+
+
+def wait_all(srv, ids, n_states, timeout_s=120.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(ids):
+        for rid in ids:
+            if rid in out:
+                continue
+            n = n_states[rid]
+            V = np.empty(n, np.float64)
+            pol = np.empty(n, np.uint8)
+            done, info = vi.vi_server_poll(srv, rid, V, pol)
+            if done:
+                out[rid] = (V, pol, info)
+        assert time.time() - t0 < timeout_s, "server did not finish"
+        time.sleep(0.002)
+    return out
+
+
+def mix(n, seed, max_states=60_000):
+    reqs = workloads.serving_mix(n, seed=seed, max_states=max_states)
+    return [r.instance for r in reqs]
+
+
+def test_results_equal_alone_and_in_the_mix():
+    insts = mix(24, seed=11)
+    srv = vi.vi_server_create(4 << 30, 16)
+    try:
+        keep, ids, sizes = [], [], {}
+        for inst in insts:
+            d, k = desc_of(inst)
+            keep.append(k)
+            rid = vi.vi_server_submit(srv, d, 1e-4, 5000)
+            ids.append(rid)
+            sizes[rid] = inst.n_states
+        res = wait_all(srv, ids, sizes)
+    finally:
+        vi.vi_server_destroy(srv)
+    for inst, rid in zip(insts, ids):
+        V, pol, info = res[rid]
+        assert info["status"] == vi.VI_OK
+        with Handle(inst, precision="fp32") as H:
+            Va, pola, ia = H.solve(1e-4, 5000)
+            va = H.v_abs(Va, ia)
+        assert info["iters"] == ia["iters"]
+        # same kernel arithmetic alone and in the batch: identical values and policy
+        np.testing.assert_array_equal(V, va)
+        np.testing.assert_array_equal(pol, pola.cpu().numpy())
+
+
+def test_server_result_matches_oracle():
+    inst = mix(1, seed=3, max_states=5000)[0]
+    ref = oracle.Problem(inst).vi_solve(tol=1e-4, max_iters=5000)
+    srv = vi.vi_server_create(1 << 30, 4)
+    try:
+        d, k = desc_of(inst)
+        rid = vi.vi_server_submit(srv, d, 0.0, ref["iters"])   # oracle's sweep count, stop test off
+        V, pol, info = wait_all(srv, [rid], {rid: inst.n_states})[rid]
+    finally:
+        vi.vi_server_destroy(srv)
+    assert info["iters"] == ref["iters"] and info["status"] == vi.VI_ENOTCONVERGED
+    assert compare_values(V, ref["V"]) <= V_RTOL
+    assert not policy_mismatches(oracle.Problem(inst), ref["V"], pol)
+
+
+def test_admission_respects_budget():
+    insts = mix(6, seed=5, max_states=30_000)
+    biggest = max(i.n_states for i in insts)
+    budget = biggest * 17 + (1 << 16) + (1 << 20)      # room for about one request at a time
+    srv = vi.vi_server_create(budget, 8)
+    try:
+        ids, sizes, keep = [], {}, []
+        for inst in insts:
+            d, k = desc_of(inst)
+            keep.append(k)
+            rid = vi.vi_server_submit(srv, d, 1e-4, 5000)
+            ids.append(rid)
+            sizes[rid] = inst.n_states
+        res = wait_all(srv, ids, sizes)
+        assert all(r[2]["status"] == vi.VI_OK for r in res.values())
+        # a request that can never fit is refused at once
+        big = workloads.single_product(6, 1, 20, (1, 1, 1, 1, 0), workloads.poisson_pmf(3, 14), 0.9)
+        d, k = desc_of(big)
+        with pytest.raises(vi.ViError) as e:
+            vi.vi_server_submit(srv, d, 1e-4, 100)
+        assert e.value.status == vi.VI_EBUSY
+    finally:
+        vi.vi_server_destroy(srv)
+
+
+def test_invalid_requests_and_shutdown_cancels():
+    srv = vi.vi_server_create(1 << 30, 2)
+    two = workloads.config3(Q=2)
+    prods = [dict(m=p.m, L=p.L, Q=p.Q, cost=p.cost, pmf=p.pmf) for p in two.products]
+    d2, k2 = vi.make_desc(prods, two.gamma, two.issuing, subst_rate=0.5)
+    with pytest.raises(vi.ViError):
+        vi.vi_server_submit(srv, d2, 1e-4, 10)
+    inst = workloads.config2()
+    d, k = desc_of(inst)
+    rid = vi.vi_server_submit(srv, d, 0.0, 100000)     # never stops on its own
+    t0 = time.time()
+    vi.vi_server_destroy(srv)                          # cancels it
+    assert time.time() - t0 < 60
