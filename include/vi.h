@@ -246,6 +246,35 @@ vi_status vi_server_poll(vi_server srv, uint64_t request_id, int *done, double *
 /* Stop the worker and release everything.  Pending requests are cancelled. */
 vi_status vi_server_destroy(vi_server srv);
 
+/* One Bellman sweep that allocates no memory -- the paper has no counterpart;
+ * this entry point exists for callers that cannot allocate when they need a
+ * sweep: code running inside an allocator or a memory pool that must not be
+ * re-entered, components whose device memory is budgeted by someone else, or
+ * callers that reserved everything up front.  It computes what vi_backup
+ * computes for a VI_PREC_FP32 single-product problem (V_out(s) = max_a Q(s, a)
+ * from V_in, first argmax in policy, max / min of V_out - V_in in dstats)
+ * without creating a handle.
+ * Arguments: the instance as for vi_problem_create; V_in / V_out: device
+ * float-pair buffers (float[2|S|], the VI_PREC_FP32 layout), distinct;
+ * policy: device uint8[|S|] or NULL; dstats: host double[2] or NULL (when
+ * given, the stream is synchronised); stream: cudaStream_t or NULL.
+ * Scratch: the expectation tables and the reduction slots live in a fixed
+ * array in device memory that belongs to the library, holding at most
+ * VI_NOALLOC_MAX_TABLE_FLOATS table entries (3 (dmax + 1 + mQ + 2(Q+1) + 2)
+ * + 2 (Q+1)((m-1)Q + 1) are needed); larger instances get VI_EINVAL.  Every
+ * GPU that loads the library holds this array (about 65 KiB) until the
+ * process exits.  All calls share it and it keeps the last call's contents
+ * (the call resets what must start at zero), so calls whose work overlaps on
+ * the GPU -- on different streams, or from several host threads without
+ * ordering -- race.  The first call on a device looks up the array's device
+ * address (a one-time set-up for that device); make that first call before
+ * any stream capture.  No cudaMalloc, cudaFree or other allocator is called.
+ * Errors: VI_EINVAL (bad instance or buffers, tables too large), VI_ECUDA. */
+#define VI_NOALLOC_MAX_TABLE_FLOATS 16384
+vi_status vi_backup_noalloc(int m, int L, int Q, const double cost[5], const double *pmf, int dmax,
+                            double gamma, int issuing, const void *V_in, void *V_out, uint8_t *policy,
+                            double *dstats, void *stream);
+
 const char *vi_status_string(vi_status s);
 const char *vi_last_error(void);
 

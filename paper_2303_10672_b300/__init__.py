@@ -96,6 +96,8 @@ def lib() -> C.CDLL:
         "vi_server_poll": ([C.c_void_p, C.c_uint64, C.POINTER(C.c_int), vp, vp, C.POINTER(vi_solve_info)],
                            C.c_int),
         "vi_server_destroy": ([C.c_void_p], C.c_int),
+        "vi_backup_noalloc": ([C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                               C.c_int, C.c_double, C.c_int, vp, vp, u8p, C.POINTER(C.c_double), vp], C.c_int),
         "vi_status_string": ([C.c_int], C.c_char_p),
         "vi_last_error": ([], C.c_char_p),
     }
@@ -225,6 +227,19 @@ def vi_backup(h: int, V_in, V_out, policy=None, stream=None, stats: bool = True)
     ds = (C.c_double * 2)()
     _check(lib().vi_backup(h, _addr(V_in), _addr(V_out), _addr(policy), _stream(stream),
                            ds if stats else None), "vi_backup")
+    return (ds[0], ds[1]) if stats else None
+
+
+def vi_backup_noalloc(m: int, L: int, Q: int, cost: Sequence[float], pmf: np.ndarray, gamma: float, issuing: int,
+                      V_in, V_out, policy=None, stream=None, stats: bool = True):
+    """One sweep without any allocation (see vi.h); V_in / V_out in the float-pair layout."""
+    c = np.ascontiguousarray(cost, np.float64)
+    p = np.ascontiguousarray(pmf, np.float64)
+    ds = (C.c_double * 2)()
+    _check(lib().vi_backup_noalloc(m, L, Q, c.ctypes.data_as(C.POINTER(C.c_double)),
+                                   p.ctypes.data_as(C.POINTER(C.c_double)), len(p) - 1, gamma, issuing,
+                                   _addr(V_in), _addr(V_out), _addr(policy), ds if stats else None,
+                                   _stream(stream)), "vi_backup_noalloc")
     return (ds[0], ds[1]) if stats else None
 
 

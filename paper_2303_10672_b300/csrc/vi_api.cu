@@ -273,7 +273,7 @@ static vi_status validate_product(int m, int L, int Q, const double *cost, const
     return VI_OK;
 }
 
-static void fill_prod_params(ProdParams &P, int m, int L, int Q, int dmax, double c_o) {
+void fill_prod_params(ProdParams &P, int m, int L, int Q, int dmax, double c_o) {
     memset(&P, 0, sizeof(P));
     P.m = m;
     P.L = L;
@@ -503,7 +503,7 @@ struct TuneKey {
 static std::mutex g_tune_mu;
 static std::map<TuneKey, int> g_tune_cache;
 
-static int heuristic_width(int G, int lifo) {
+int heuristic_width(int G, int lifo) {
     // keep the per-lane register arrays small: at most 8 (FIFO) / 12 (LIFO) values per lane
     const int cap = lifo ? 12 : 8;
     int lanes = (G + cap - 1) / cap;

@@ -46,3 +46,6 @@ struct vi_problem {
 };
 
 vi_status vi_fail(vi_status s, const char *fmt, ...);
+// shared with the allocation-free entry point (vi_noalloc.cu)
+void fill_prod_params(vib::ProdParams &P, int m, int L, int Q, int dmax, double c_o);
+int heuristic_width(int G, int lifo);

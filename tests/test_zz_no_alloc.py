@@ -1,0 +1,54 @@
+"""vi_backup_noalloc: the sweep for callers that cannot allocate (inside an
+allocator or memory pool that must not be re-entered, or with device memory
+budgeted elsewhere).  Its output must equal vi_backup on a normally created
+problem, within the parity tolerance, on two calls in a row -- the second one
+checks that the shared scratch left by the first call is reset."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from workloads import FIFO, LIFO
+
+pytestmark = pytest.mark.gpu
+
+vi = pytest.importorskip("paper_2303_10672_b300")
+from gpu_helpers import Handle, values_abs, V_RTOL  # noqa: E402
+
+
+def reference_and_noalloc(inst, k_sweeps):
+    p = inst.products[0]
+    with Handle(inst, precision="fp32") as H:
+        V, _, _ = H.solve(0.0, k_sweeps)                       # a non-trivial V_in
+        n = H.sizes["n_states"]
+        V_ref = torch.empty_like(V)
+        pol_ref = torch.empty(n, dtype=torch.uint8, device="cuda")
+        st_ref = vi.vi_backup(H.h, V, V_ref, pol_ref)
+        V_na = torch.empty_like(V)
+        pol_na = torch.empty(n, dtype=torch.uint8, device="cuda")
+        st_na = vi.vi_backup_noalloc(p.m, p.L, p.Q, p.cost, p.pmf, inst.gamma, inst.issuing, V, V_na, pol_na)
+        torch.cuda.synchronize()
+        a = values_abs(V_ref, 0.0, "pair")
+        b = values_abs(V_na, 0.0, "pair")
+        scale = np.abs(a).max()
+        assert np.abs(a - b).max() <= V_RTOL * scale
+        assert (pol_ref.cpu().numpy() == pol_na.cpu().numpy()).mean() == 1.0
+        assert abs(st_ref[0] - st_na[0]) <= V_RTOL * scale and abs(st_ref[1] - st_na[1]) <= V_RTOL * scale
+
+
+def test_noalloc_matches_backup_two_calls():
+    # first call: FIFO with a pipeline; second call: a different LIFO instance on the same scratch
+    reference_and_noalloc(workloads.config1(), 3)
+    reference_and_noalloc(
+        workloads.single_product(4, 2, 9, (2, 1, 4, 3, 0.5), workloads.poisson_pmf(3.5, 14), 0.95, LIFO), 4)
+
+
+def test_noalloc_rejects_oversized_tables():
+    pmf = workloads.poisson_pmf(4.0, 30)
+    n = 256 ** 3                      # |S| of m = 4, L = 1, Q = 255: buffers of the full size
+    V = torch.zeros(n, dtype=torch.float64, device="cuda")
+    W = torch.zeros(n, dtype=torch.float64, device="cuda")
+    with pytest.raises(vi.ViError) as e:
+        # (Q+1)((m-1)Q+1) pairs far beyond the fixed scratch (|S| = 256^3 fits, the tables do not)
+        vi.vi_backup_noalloc(4, 1, 255, (1, 1, 1, 1, 0), pmf, 0.9, FIFO, V, W)
+    assert e.value.status == vi.VI_EINVAL
