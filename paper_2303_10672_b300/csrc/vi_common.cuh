@@ -100,6 +100,19 @@ struct SolveState {
     double crit, dmax_abs, dmin_abs;
 };
 
+// LIFO with L = 1 (m >= 2): the factorised kernel gathers the two shared
+// sequences of an action-independent layout once per rest, if their per-thread
+// columns fit in 64 KiB of shared memory for a block of 128 threads
+__host__ __device__ inline bool lifo_shared_ok(const ProdParams &P) {
+    return P.L == 1 && P.m >= 2 && (P.G + P.dmax + 1) * 128 * 4 <= 64 * 1024;
+}
+
+// FIFO: the rest path is kept per thread if a column of dmax+1 indices fits in
+// 64 KiB of shared memory for a block of 128 threads
+__host__ __device__ inline bool fifo_shared_ok(const ProdParams &P) {
+    return P.m >= 2 && (P.dmax + 1) * 128 * 4 <= 64 * 1024;
+}
+
 // order-preserving map double -> uint64 so that unsigned max/min give double max/min
 __device__ __forceinline__ unsigned long long dkey(double x) {
     unsigned long long b = (unsigned long long)__double_as_longlong(x);

@@ -250,6 +250,13 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
     const float gam = (float)kp.gamma;
     const float c_o = (float)P.c_o;
     const int dmax = P.dmax;
+    const bool shared_lifo = LIFO && lifo_shared_ok(P);
+    const bool shared_fifo = !LIFO && fifo_shared_ok(P);
+    // per-thread columns (stride kGroupThreads) of the shared LIFO sequences / FIFO path
+    float *colT = (float *)(((uintptr_t)(s_pol + RB * G) + 15) & ~(uintptr_t)15) + threadIdx.x;
+    float *colH = colT + G * kGroupThreads;
+    uint32_t *colP = (uint32_t *)colT;
+    int Rrest = 0;   // units in the rest slots (without the order when L = 1)
 
     float bh[XW], bl[XW];
     int arg[XW];
@@ -262,9 +269,59 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
     float2 R0 = make_float2(0.f, 0.f);
     if (active) {
         const RestInfo ri = decode_rest(r, P);
+        Rrest = ri.R;
         const float *V1 = (const float *)B.vin;
         const float2 *V2 = (const float2 *)B.vin;
         if (PAIR) R0 = __ldg(V2 + r);   // s'_0 of action 0
+        if (shared_fifo) {
+            // FIFO: the demand reaching the rest slots empties them oldest first; that path
+            // (relative to the rest index r) is the same for every order
+            Walker wp;
+            walker_init(wp, r, ri.packed, P.n_rest_slots, P.cb, 0, 1u);
+            const int nP = min(ri.R, dmax) + 1;
+            uint32_t *cp = colP;
+            cp[0] = r;
+            for (int e = 1; e < nP; ++e) {
+                walker_step(wp, P.cb, 0, (uint32_t)G);
+                cp[e * kGroupThreads] = wp.idx;
+            }
+        }
+        if (shared_lifo) {
+            // LIFO with L = 1 issues the new order first, so every action's next states
+            // come from two shared sequences: T[j] = V[r + j G^(K-1)] (part of the order
+            // left) and H[k] = V[state r after k units issued LIFO from X_{m-1}..X_2]
+            const int nH = min(ri.R, dmax) + 1;
+            auto value = [&](uint32_t i) -> float {
+                if (PAIR) return pair_diff(__ldg(V2 + i), R0);
+                return __ldg(V1 + i);
+            };
+            for (int j0 = 0; j0 < G; j0 += LCH) {
+                float v[LCH];
+#pragma unroll
+                for (int j = 0; j < LCH; ++j) v[j] = (j0 + j < G) ? value(r + (uint32_t)(j0 + j) * P.w_top) : 0.f;
+#pragma unroll
+                for (int j = 0; j < LCH; ++j)
+                    if (j0 + j < G) colT[(j0 + j) * kGroupThreads] = v[j];
+            }
+            Walker wh;
+            walker_init(wh, r, ri.packed, P.m - 2, P.cb, 1, P.m >= 3 ? P.w_zt / (uint32_t)G : 1u);
+            int kc = 0;
+            for (int k0 = 0; k0 < nH; k0 += LCH) {
+                uint32_t idx[LCH];
+#pragma unroll
+                for (int j = 0; j < LCH; ++j) {
+                    const int kk = min(k0 + j, nH - 1);
+                    for (; kc < kk; ++kc) walker_step(wh, P.cb, 1, (uint32_t)G);
+                    idx[j] = wh.idx;
+                }
+                float v[LCH];
+#pragma unroll
+                for (int j = 0; j < LCH; ++j) v[j] = value(idx[j]);
+#pragma unroll
+                for (int j = 0; j < LCH; ++j)
+                    if (k0 + j < nH) colH[(k0 + j) * kGroupThreads] = v[j];
+            }
+        }
         for (int a = 0; a < G; ++a) {
             unsigned long long packed;
             int R;
@@ -274,7 +331,9 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
             walker_init(wk, idx0, packed, P.m - 1, P.cb, LIFO, P.w_zt);
             float2 ref = make_float2(0.f, 0.f);
             float g0 = 0.f;
-            if (PAIR)
+            if (shared_lifo)
+                ref = R0;   // all shared values are measured from R0
+            else if (PAIR)
                 ref = __ldg(V2 + idx0);
             else
                 g0 = __ldg(V1 + idx0);
@@ -289,14 +348,31 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                 }
                 int ecur = 0;
                 const int nch = (dmax + XW) / XW;
-                for (int c = 0; c < nch; ++c) {
+                // one chunk of XW demands; in the first chunk of a float-pair sweep the window
+                // before it holds g(0) - ref = 0 exactly, so those products are skipped
+                const uint32_t atop = (uint32_t)a * P.w_top;
+                auto chunk = [&](int c, auto first) {
+                    constexpr bool FIRST = decltype(first)::value;
                     const int d0 = c * XW - x0;
                     uint32_t idx[XW];
+                    if (shared_fifo) {
+                        // rest path shared by all orders; with L = 1 the order is issued last
+                        // demands beyond dmax carry no mass: clamping e there keeps every index inside
+                        // the column (0..min(Rrest, dmax)) and inside the value array
+                        const int ecap = min(R, dmax);
 #pragma unroll
-                    for (int j = 0; j < XW; ++j) {
-                        const int e = min(max(d0 + j, 0), R);
-                        for (; ecur < e; ++ecur) walker_step(wk, P.cb, 0, (uint32_t)G);
-                        idx[j] = wk.idx;
+                        for (int j = 0; j < XW; ++j) {
+                            const int e = min(max(d0 + j, 0), ecap);
+                            idx[j] = (e <= Rrest) ? colP[e * kGroupThreads] + atop
+                                                  : (uint32_t)(a - (e - Rrest)) * P.w_top;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < XW; ++j) {
+                            const int e = min(max(d0 + j, 0), R);
+                            for (; ecur < e; ++ecur) walker_step(wk, P.cb, 0, (uint32_t)G);
+                            idx[j] = wk.idx;
+                        }
                     }
                     float gcur[XW];
                     if (PAIR) {
@@ -314,14 +390,27 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                         const float pd = s_p[d0 + x0 + j];
 #pragma unroll
                         for (int xi = 0; xi < XW; ++xi) {
-                            const int k = j - xi;
-                            const float gv = (k >= 0) ? gcur[k] : gprev[XW + k];
+                            const int kk = j - xi;
+                            if (PAIR && FIRST && kk < 0) continue;
+                            const float gv = (kk >= 0) ? gcur[kk] : gprev[XW + kk];
                             acc[xi] = fmaf(pd, gv, acc[xi]);
                         }
                     }
 #pragma unroll
                     for (int j = 0; j < XW; ++j) gprev[j] = gcur[j];
+                };
+                chunk(0, std::true_type{});
+                for (int c = 1; c < nch; ++c) chunk(c, std::false_type{});
+            } else if (shared_lifo) {
+                // C_a = sum_d p_d g_a(min(d, R)), g_a(e) = T[a-e] (e <= a) or H[e-a] (e > a)
+                float c = 0.f;
+                for (int d = 0; d <= dmax; ++d) {
+                    const int e = min(d, R);
+                    const float v = (e <= a) ? colT[(a - e) * kGroupThreads] : colH[(e - a) * kGroupThreads];
+                    c = fmaf(s_p[d], v, c);
                 }
+#pragma unroll
+                for (int xi = 0; xi < XW; ++xi) acc[xi] = c;
             } else {
                 float c = 0.f;
                 int ecur = 0;
@@ -1076,9 +1165,12 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
 // launch descriptors and launchers
 // ===========================================================================
 static size_t group_smem(const KernelParams &kp, int rb, int vk) {
-    const int G = kp.p[0].G;
+    const ProdParams &P = kp.p[0];
     const size_t vb = (vk == VK_PAIR) ? 8 : 4;
-    return (size_t)((kp.n_tables + 3) & ~3) * 4 + (size_t)rb * G * (vb + 1);
+    size_t bytes = (size_t)((kp.n_tables + 3) & ~3) * 4 + (size_t)rb * P.G * (vb + 1) + 16;
+    if (kp.issuing && lifo_shared_ok(P)) bytes += (size_t)(P.G + P.dmax + 1) * kGroupThreads * 4;
+    if (!kp.issuing && fifo_shared_ok(P)) bytes += (size_t)(P.dmax + 1) * kGroupThreads * 4;
+    return bytes;
 }
 
 template <int XW, int LIFO, int VK>
