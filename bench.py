@@ -226,6 +226,8 @@ def run_native(args):
     prods = [dict(m=q.m, L=q.L, Q=q.Q, cost=q.cost, pmf=q.pmf) for q in inst.products]
     desc, keep = vi.make_desc(prods, inst.gamma, inst.issuing, prec, vi.VI_STOP_SPAN, inst.subst_rate)
     h = vi.vi_problem_create_desc(desc)
+    if args.group_width:
+        vi.vi_problem_set_option(h, vi.VI_OPT_GROUP_WIDTH, args.group_width)
     sizes = vi.vi_problem_sizes(h)
     n = sizes["n_states"]
     vdtype = torch.float64 if sizes["value_bytes"] == 8 else torch.float32
@@ -446,6 +448,8 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp32", "fp32_kahan", "fp64", "fp32_single"])
     ap.add_argument("--max-iters", type=int, default=MAX_ITERS)
     ap.add_argument("--serving", type=int, default=512, help="requests in the serving mix (0 = skip)")
+    ap.add_argument("--group-width", type=int, default=0,
+                    help="lane width of the factorised kernel (0 = autotuned)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -1,0 +1,404 @@
+// vi_group.cuh -- the factorised single-product sweep (template), included by
+// the per-variant translation units vi_group_*.cu and by vi_batch.cu.
+#pragma once
+
+#include "vi_device.cuh"
+
+namespace vib {
+
+// ===========================================================================
+// factorised single-product sweep.  A rest index r (digits 1..K-1 of s) is
+// handled by `lpr` consecutive lanes; lane `part` owns the XW values
+// x = part*XW .. part*XW+XW-1 of the expiring slot (digit 0 of s), kept in
+// registers.  For a given order a the next states only depend on r, a and the
+// demand e that reaches the other slots, g(e) = V[s'(r, a, e)]:
+//   FIFO: C(x) = sum_d p_d g(clamp(d - x, 0, R))   (x is issued first)
+//   LIFO: C    = sum_d p_d g(min(d, R))            (x is issued last)
+// The FIFO correlation runs in chunks of XW demands over a register window of
+// gathered values; each chunk first walks the next-state indices, then issues
+// all of its loads, then consumes them, so the loads overlap.
+// ===========================================================================
+template <int XW, int LIFO, int VK, int LPIPE>
+__device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid, unsigned n_blocks, int mode,
+                                           const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int lpr,
+                                           unsigned char *smem_raw) {
+    constexpr bool PAIR = (VK == VK_PAIR);
+    constexpr int LCH = 8;   // LIFO load batch
+    SolveState *st = kp.st;
+    Bufs B;
+    if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
+    const ProdParams &P = kp.p[0];
+    const int G = P.G;
+    const int RB = kGroupThreads / lpr;                    // rests per block
+    float *s_tab = (float *)smem_raw;
+    float *s_out = s_tab + ((kp.n_tables + 3) & ~3);       // PAIR: float2 per state
+    uint8_t *s_pol = (uint8_t *)(s_out + RB * G * (PAIR ? 2 : 1));
+    load_tables<float>(s_tab, (const float *)kp.tables, kp.n_tables);
+    const float *s_p = s_tab + P.off_p;
+    const float *s_RT = s_tab + P.off_RT;
+    const float *s_RTlo = s_tab + P.off_RTlo;
+
+    const uint32_t nR = P.nS / (uint32_t)G;
+    const int rl = threadIdx.x / lpr;
+    const int part = threadIdx.x - rl * lpr;
+    const uint32_t r = bid * (uint32_t)RB + (uint32_t)rl;
+    const bool active = (rl < RB) && (r < nR);
+    const int x0 = part * XW;
+    const int nx = min(XW, G - x0);                        // >= 1 because lpr = ceil(G / XW)
+    const float gam = (float)kp.gamma;
+    const float c_o = (float)P.c_o;
+    const int dmax = P.dmax;
+    const bool shared_lifo = LIFO && !LPIPE && lifo_shared_ok(P);
+    const bool shared_fifo = !LIFO && fifo_shared_ok(P);
+    constexpr bool rt_common = LPIPE;   // L >= 2: the remaining stock R does not depend on the order
+    // per-thread columns (stride kGroupThreads) of the shared LIFO sequences / FIFO path
+    float *colT = (float *)(((uintptr_t)(s_pol + RB * G) + 15) & ~(uintptr_t)15) + threadIdx.x;
+    float *colH = colT + G * kGroupThreads;
+    uint32_t *colP = (uint32_t *)colT;
+    int Rrest = 0;   // units in the rest slots (without the order when L = 1)
+
+    float bh[XW], bl[XW];
+    int arg[XW];
+#pragma unroll
+    for (int xi = 0; xi < XW; ++xi) {
+        bh[xi] = -INFINITY;
+        bl[xi] = 0.f;
+        arg[xi] = 0;
+    }
+    float2 R0 = make_float2(0.f, 0.f);
+    if (active) {
+        const RestInfo ri = decode_rest(r, P);
+        Rrest = ri.R;
+        const float *V1 = (const float *)B.vin;
+        const float2 *V2 = (const float2 *)B.vin;
+        if (PAIR) R0 = __ldg(V2 + r);   // s'_0 of action 0
+        if (shared_fifo) {
+            // FIFO: the demand reaching the rest slots empties them oldest first; that path
+            // (relative to the rest index r) is the same for every order
+            Walker wp;
+            walker_init(wp, r, ri.packed, P.n_rest_slots, P.cb, 0, 1u);
+            const int nP = min(ri.R, dmax) + 1;
+            uint32_t *cp = colP;
+            cp[0] = r;
+            for (int e = 1; e < nP; ++e) {
+                walker_step(wp, P.cb, 0, (uint32_t)G);
+                cp[e * kGroupThreads] = wp.idx;
+            }
+        }
+        if (shared_lifo) {
+            // LIFO with L = 1 issues the new order first, so every action's next states
+            // come from two shared sequences: T[j] = V[r + j G^(K-1)] (part of the order
+            // left) and H[k] = V[state r after k units issued LIFO from X_{m-1}..X_2]
+            const int nH = min(ri.R, dmax) + 1;
+            auto value = [&](uint32_t i) -> float {
+                if (PAIR) return pair_diff(__ldg(V2 + i), R0);
+                return __ldg(V1 + i);
+            };
+            for (int j0 = 0; j0 < G; j0 += LCH) {
+                float v[LCH];
+#pragma unroll
+                for (int j = 0; j < LCH; ++j) v[j] = (j0 + j < G) ? value(r + (uint32_t)(j0 + j) * P.w_top) : 0.f;
+#pragma unroll
+                for (int j = 0; j < LCH; ++j)
+                    if (j0 + j < G) colT[(j0 + j) * kGroupThreads] = v[j];
+            }
+            Walker wh;
+            walker_init(wh, r, ri.packed, P.m - 2, P.cb, 1, P.m >= 3 ? P.w_zt / (uint32_t)G : 1u);
+            int kc = 0;
+            for (int k0 = 0; k0 < nH; k0 += LCH) {
+                uint32_t idx[LCH];
+#pragma unroll
+                for (int j = 0; j < LCH; ++j) {
+                    const int kk = min(k0 + j, nH - 1);
+                    for (; kc < kk; ++kc) walker_step(wh, P.cb, 1, (uint32_t)G);
+                    idx[j] = wh.idx;
+                }
+                float v[LCH];
+#pragma unroll
+                for (int j = 0; j < LCH; ++j) v[j] = value(idx[j]);
+#pragma unroll
+                for (int j = 0; j < LCH; ++j)
+                    if (k0 + j < nH) colH[(k0 + j) * kGroupThreads] = v[j];
+            }
+        }
+        for (int a = 0; a < G; ++a) {
+            unsigned long long packed;
+            int R;
+            slots_for_action(P, ri, a, packed, R);
+            Walker wk;
+            const uint32_t idx0 = r + (uint32_t)a * P.w_top;
+            walker_init(wk, idx0, packed, P.m - 1, P.cb, LIFO, P.w_zt);
+            float2 ref = make_float2(0.f, 0.f);
+            float g0 = 0.f;
+            if (shared_lifo)
+                ref = R0;   // all shared values are measured from R0
+            else if (PAIR)
+                ref = __ldg(V2 + idx0);
+            else
+                g0 = __ldg(V1 + idx0);
+            float acc[XW];
+            if (!LIFO) {
+                // lane-local demand axis dd = d - x0: C(x0+xi) = sum_dd p[dd+x0] g(clamp(dd-xi, 0, R))
+                float gprev[XW];
+#pragma unroll
+                for (int xi = 0; xi < XW; ++xi) {
+                    acc[xi] = 0.f;
+                    gprev[xi] = g0;
+                }
+                int ecur = 0;
+                const int nch = (dmax + XW) / XW;
+                // one chunk of XW demands; in the first chunk of a float-pair sweep the window
+                // before it holds g(0) - ref = 0 exactly, so those products are skipped
+                const uint32_t atop = (uint32_t)a * P.w_top;
+                auto chunk = [&](int c, auto first) {
+                    constexpr bool FIRST = decltype(first)::value;
+                    const int d0 = c * XW - x0;
+                    uint32_t idx[XW];
+                    if (shared_fifo) {
+                        // rest path shared by all orders; with L = 1 the order is issued last
+                        // demands beyond dmax carry no mass: clamping e there keeps every index inside
+                        // the column (0..min(Rrest, dmax)) and inside the value array
+                        const int ecap = min(R, dmax);
+#pragma unroll
+                        for (int j = 0; j < XW; ++j) {
+                            const int e = min(max(d0 + j, 0), ecap);
+                            idx[j] = (e <= Rrest) ? colP[e * kGroupThreads] + atop
+                                                  : (uint32_t)(a - (e - Rrest)) * P.w_top;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < XW; ++j) {
+                            const int e = min(max(d0 + j, 0), R);
+                            for (; ecur < e; ++ecur) walker_step(wk, P.cb, 0, (uint32_t)G);
+                            idx[j] = wk.idx;
+                        }
+                    }
+                    float gcur[XW];
+                    if (PAIR) {
+                        float2 raw[XW];
+#pragma unroll
+                        for (int j = 0; j < XW; ++j) raw[j] = __ldg(V2 + idx[j]);
+#pragma unroll
+                        for (int j = 0; j < XW; ++j) gcur[j] = pair_diff(raw[j], ref);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < XW; ++j) gcur[j] = __ldg(V1 + idx[j]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < XW; ++j) {
+                        const float pd = s_p[d0 + x0 + j];
+#pragma unroll
+                        for (int xi = 0; xi < XW; ++xi) {
+                            const int kk = j - xi;
+                            if (PAIR && FIRST && kk < 0) continue;
+                            const float gv = (kk >= 0) ? gcur[kk] : gprev[XW + kk];
+                            acc[xi] = fmaf(pd, gv, acc[xi]);
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < XW; ++j) gprev[j] = gcur[j];
+                };
+                // the peeled first chunk pays off without a pipeline (L = 1); with one, the
+                // smaller kernel body wins (measured)
+                if (PAIR && !LPIPE) {
+                    chunk(0, std::true_type{});
+                    for (int c = 1; c < nch; ++c) chunk(c, std::false_type{});
+                } else {
+                    for (int c = 0; c < nch; ++c) chunk(c, std::false_type{});
+                }
+            } else if (shared_lifo) {
+                // C_a = sum_d p_d g_a(min(d, R)), g_a(e) = T[a-e] (e <= a) or H[e-a] (e > a)
+                float c = 0.f;
+                for (int d = 0; d <= dmax; ++d) {
+                    const int e = min(d, R);
+                    const float v = (e <= a) ? colT[(a - e) * kGroupThreads] : colH[(e - a) * kGroupThreads];
+                    c = fmaf(s_p[d], v, c);
+                }
+#pragma unroll
+                for (int xi = 0; xi < XW; ++xi) acc[xi] = c;
+            } else {
+                float c = 0.f;
+                int ecur = 0;
+                for (int d0 = 0; d0 <= dmax; d0 += LCH) {
+                    uint32_t idx[LCH];
+#pragma unroll
+                    for (int j = 0; j < LCH; ++j) {
+                        const int e = min(d0 + j, R);
+                        for (; ecur < e; ++ecur) walker_step(wk, P.cb, 1, (uint32_t)G);
+                        idx[j] = wk.idx;
+                    }
+                    float gv[LCH];
+                    if (PAIR) {
+                        float2 raw[LCH];
+#pragma unroll
+                        for (int j = 0; j < LCH; ++j) raw[j] = __ldg(V2 + idx[j]);
+#pragma unroll
+                        for (int j = 0; j < LCH; ++j) gv[j] = pair_diff(raw[j], ref);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < LCH; ++j) gv[j] = __ldg(V1 + idx[j]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < LCH; ++j) c = fmaf(s_p[d0 + j], gv[j], c);   // zero mass beyond dmax
+                }
+#pragma unroll
+                for (int xi = 0; xi < XW; ++xi) acc[xi] = c;
+            }
+            const float *rt = s_RT + R * G + x0;
+            if (PAIR && rt_common) {
+                // L >= 2: R does not depend on the order, so RT(x, R) is common to all
+                // orders and is added once per x after the max
+                float Bh, Bl;
+                action_base(gam, ref, R0, __fmul_rn(-c_o, (float)a), Bh, Bl);
+#pragma unroll
+                for (int xi = 0; xi < XW; ++xi) {
+                    if (xi < nx) {
+                        const float ql = __fmaf_rn(gam, acc[xi], Bl);
+                        const float diff = __fadd_rn(__fsub_rn(Bh, bh[xi]), __fsub_rn(ql, bl[xi]));
+                        if (diff > 0.f) {
+                            bh[xi] = Bh;
+                            bl[xi] = ql;
+                            arg[xi] = a;
+                        }
+                    }
+                }
+            } else if (PAIR) {
+                float Bh, Bl;
+                action_base(gam, ref, R0, __fmul_rn(-c_o, (float)a), Bh, Bl);
+                const float *rtl = s_RTlo + R * G + x0;
+#pragma unroll
+                for (int xi = 0; xi < XW; ++xi) {
+                    if (xi < nx) {
+                        float qh = Bh, ql = Bl;
+                        pair_add(qh, ql, rt[xi], rtl[xi]);
+                        ql = __fmaf_rn(gam, acc[xi], ql);
+                        const float diff = __fadd_rn(__fsub_rn(qh, bh[xi]), __fsub_rn(ql, bl[xi]));
+                        if (diff > 0.f) {
+                            bh[xi] = qh;
+                            bl[xi] = ql;
+                            arg[xi] = a;
+                        }
+                    }
+                }
+            } else {
+                const float base = -c_o * (float)a;
+#pragma unroll
+                for (int xi = 0; xi < XW; ++xi) {
+                    if (xi < nx) {
+                        const float q = fmaf(gam, acc[xi], base + rt[xi]);
+                        if (q > bh[xi]) {
+                            bh[xi] = q;
+                            arg[xi] = a;
+                        }
+                    }
+                }
+            }
+        }
+        if (!PAIR && r == 0 && part == 0 && mode == MODE_SWEEP) st->c_next = bh[0];
+    }
+    if (PAIR && rt_common && active) {
+        const float *rt = s_RT + Rrest * G + x0;
+        const float *rtl = s_RTlo + Rrest * G + x0;
+#pragma unroll
+        for (int xi = 0; xi < XW; ++xi)
+            if (xi < nx) pair_add(bh[xi], bl[xi], rt[xi], rtl[xi]);
+    }
+    // stage the block's G * RB contiguous states through shared memory
+    if (rl < RB) {
+#pragma unroll
+        for (int xi = 0; xi < XW; ++xi) {
+            if (xi < nx) {
+                const int o = rl * G + x0 + xi;
+                if (PAIR)
+                    ((float2 *)s_out)[o] = active ? pair_finish(gam, R0, bh[xi], bl[xi]) : make_float2(0.f, 0.f);
+                else
+                    s_out[o] = bh[xi];
+                s_pol[o] = (uint8_t)arg[xi];
+            }
+        }
+    }
+    __syncthreads();
+    const uint32_t s0 = bid * (uint32_t)(RB * G);
+    const uint32_t nblk = (uint32_t)(RB * G);
+    float mx = -INFINITY, mn = INFINITY;
+    for (uint32_t i = threadIdx.x; i < nblk; i += kGroupThreads) {
+        const uint32_t s = s0 + i;
+        if (s >= P.nS) break;
+        if (PAIR) {
+            const float2 *vin2 = (const float2 *)B.vin;
+            float2 *vout2 = (float2 *)B.vout;
+            if (mode == MODE_EXTRACT) {
+                if (vout2) vout2[s] = vin2[s];
+            } else {
+                const float2 vnew = ((const float2 *)s_out)[i];
+                const float2 vold = vin2[s];
+                vout2[s] = vnew;
+                const float dlt = pair_diff(vnew, vold);
+                mx = fmaxf(mx, dlt);
+                mn = fminf(mn, dlt);
+            }
+        } else {
+            const float *vin1 = (const float *)B.vin;
+            float *vout1 = (float *)B.vout;
+            if (mode == MODE_EXTRACT) {
+                if (vout1) vout1[s] = vin1[s];
+            } else {
+                const float vnew = s_out[i] - B.cnorm;
+                const float vold = vin1[s];
+                vout1[s] = vnew;
+                const float dlt = vnew - vold;
+                mx = fmaxf(mx, dlt);
+                mn = fminf(mn, dlt);
+            }
+        }
+        if (B.pol) B.pol[s] = s_pol[i];
+    }
+    if (mode != MODE_EXTRACT) block_reduce_and_finalize<float>(mx, mn, st, mode, n_blocks);
+}
+
+template <int XW, int LIFO, int VK, int LPIPE>
+__global__ void __launch_bounds__(kGroupThreads)
+sweep_group_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int lpr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    group_body<XW, LIFO, VK, LPIPE>(kp, blockIdx.x, gridDim.x, mode, vin_arg, vout_arg, pol_arg, lpr, smem_raw);
+}
+
+
+inline size_t group_smem(const KernelParams &kp, int rb, int vk) {
+    const ProdParams &P = kp.p[0];
+    const size_t vb = (vk == VK_PAIR) ? 8 : 4;
+    size_t bytes = (size_t)((kp.n_tables + 3) & ~3) * 4 + (size_t)rb * P.G * (vb + 1) + 16;
+    if (kp.issuing && lifo_shared_ok(P)) bytes += (size_t)(P.G + P.dmax + 1) * kGroupThreads * 4;
+    if (!kp.issuing && fifo_shared_ok(P)) bytes += (size_t)(P.dmax + 1) * kGroupThreads * 4;
+    return bytes;
+}
+
+template <int XW, int LIFO, int VK, int LPIPE>
+cudaError_t describe_group_t(const KernelParams &kp, LaunchDesc &d) {
+    const int G = kp.p[0].G;
+    const int lpr = (G + XW - 1) / XW;
+    const int rb = kGroupThreads / lpr;
+    const uint32_t nR = kp.p[0].nS / (uint32_t)G;
+    d.fn = (const void *)sweep_group_kernel<XW, LIFO, VK, LPIPE>;
+    d.grid = dim3((nR + rb - 1) / rb);
+    d.block = dim3(kGroupThreads);
+    d.smem = group_smem(kp, rb, VK);
+    d.lpr = lpr;
+    return cudaFuncSetAttribute(sweep_group_kernel<XW, LIFO, VK, LPIPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)d.smem);
+}
+
+template <int LIFO, int VK, int LPIPE>
+cudaError_t describe_group_l(const KernelParams &kp, int xw, LaunchDesc &d) {
+    switch (xw) {
+#define VIB_XW(w) \
+    case w: return describe_group_t<w, LIFO, VK, LPIPE>(kp, d);
+        VIB_XW(1) VIB_XW(2) VIB_XW(3) VIB_XW(4) VIB_XW(5) VIB_XW(6) VIB_XW(7) VIB_XW(8) VIB_XW(9) VIB_XW(10)
+        VIB_XW(11) VIB_XW(12) VIB_XW(16) VIB_XW(21) VIB_XW(24)
+#undef VIB_XW
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+
+}  // namespace vib

@@ -26,545 +26,10 @@
 
 #include <type_traits>
 
-#include "vi_common.cuh"
-#include "vi_kernels.h"
+#include "vi_device.cuh"
+#include "vi_group_dispatch.h"
 
 namespace vib {
-
-// ---------------------------------------------------------------------------
-// error-free float transformations (never contracted into FMAs)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
-    p = __fmul_rn(a, b);
-    e = __fmaf_rn(a, b, -p);
-}
-__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {   // |a| >= |b|
-    s = __fadd_rn(a, b);
-    e = __fsub_rn(b, __fsub_rn(s, a));
-}
-// difference of two float pairs as an FP32 number (correctly rounded when the
-// high parts are within a factor of two of each other)
-__device__ __forceinline__ float pair_diff(float2 g, float2 ref) {
-    return __fadd_rn(__fsub_rn(g.x, ref.x), __fsub_rn(g.y, ref.y));
-}
-
-// ---------------------------------------------------------------------------
-// block reductions of the per-sweep change statistics
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void warp_minmax(T &mx, T &mn) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    }
-}
-
-// All threads of the block call this.  Folds (mx, mn) of the block into the
-// global accumulators; the last block of the grid then finalises the sweep.
-template <typename T>
-__device__ void block_reduce_and_finalize(T mx, T mn, SolveState *st, int mode, unsigned n_blocks) {
-    __shared__ T s_mx[32], s_mn[32];
-    __shared__ int s_last;
-    warp_minmax<T>(mx, mn);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        s_mx[wid] = mx;
-        s_mn[wid] = mn;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-        mx = lane < nw ? s_mx[lane] : (T)-INFINITY;
-        mn = lane < nw ? s_mn[lane] : (T)INFINITY;
-        warp_minmax<T>(mx, mn);
-        if (lane == 0) {
-            atomicMax(&st->key_max, dkey((double)mx));
-            atomicMin(&st->key_min, dkey((double)mn));
-            __threadfence();
-            const unsigned prev = atomicAdd(&st->blocks_done, 1u);
-            s_last = (prev == n_blocks - 1);
-        }
-    }
-    __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
-    __threadfence();
-    const double vmax = dkey_inv(atomicAdd(&st->key_max, 0ull));
-    const double vmin = dkey_inv(atomicAdd(&st->key_min, 0ull));
-    if (mode == MODE_SWEEP) {
-        const double b_old = st->offset;
-        const double b_new = st->normalise ? (st->gamma * b_old + (double)st->c_cur) : 0.0;
-        const double db = b_new - b_old;
-        st->offset = b_new;
-        st->dmax_abs = db + vmax;
-        st->dmin_abs = db + vmin;
-        const double crit = (st->stop_rule == 0) ? (vmax - vmin) : fmax(fabs(st->dmax_abs), fabs(st->dmin_abs));
-        st->crit = crit;
-        st->iter += 1;
-        const int conv = crit < st->tol;
-        st->converged = conv;
-        const int go = (!conv) && (st->iter < st->max_iters);
-        st->keep_going = go;
-        if (st->normalise) st->c_cur = st->c_next;
-        if (st->use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)st->cond, go ? 1u : 0u);
-    } else {
-        st->dmax_abs = vmax;
-        st->dmin_abs = vmin;
-        st->crit = vmax - vmin;
-    }
-    st->key_max = 0ull;
-    st->key_min = ~0ull;
-    __threadfence();
-    st->blocks_done = 0u;
-}
-
-// buffers of one launch
-struct Bufs {
-    const void *vin;
-    void *vout;      // may be null (extraction without copy)
-    uint8_t *pol;    // may be null
-    float cnorm;     // VK_SINGLE normalisation constant
-};
-
-__device__ __forceinline__ bool resolve_bufs(const SolveState *st, int mode, const void *vin_arg, void *vout_arg,
-                                             uint8_t *pol_arg, Bufs &b) {
-    if (mode == MODE_SWEEP) {
-        if (!st->keep_going) return false;
-        const int it = st->iter;
-        b.vin = st->buf[it & 1];
-        b.vout = st->buf[(it + 1) & 1];
-        b.pol = nullptr;
-        b.cnorm = st->normalise ? st->c_cur : 0.f;
-    } else if (mode == MODE_EXTRACT) {
-        const int it = st->iter;
-        b.vin = st->buf[it & 1];
-        b.vout = (it & 1) ? st->buf[0] : nullptr;   // the result must end in the caller's buffer
-        b.pol = st->policy;
-        b.cnorm = 0.f;
-    } else {
-        b.vin = vin_arg;
-        b.vout = vout_arg;
-        b.pol = pol_arg;
-        b.cnorm = 0.f;
-    }
-    return true;
-}
-
-template <typename T>
-__device__ __forceinline__ void load_tables(T *s_tab, const T *g_tab, int n) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s_tab[i] = g_tab[i];
-    __syncthreads();
-}
-
-// packed rest-slot counts and their sum for action a (the order joins the slots
-// as Z_{m-1} when L == 1 and m >= 2)
-__device__ __forceinline__ void slots_for_action(const ProdParams &P, const RestInfo &ri, int a,
-                                                 unsigned long long &packed, int &R) {
-    packed = ri.packed;
-    R = ri.R;
-    if (P.L == 1 && P.m >= 2) {
-        packed |= (unsigned long long)a << (P.cb * (P.m - 2));
-        R += a;
-    }
-}
-
-// a pair (hi, lo) += (xh, xl), high parts added error-free
-__device__ __forceinline__ void pair_add(float &h, float &l, float xh, float xl) {
-    float s, e;
-    two_sum(h, xh, s, e);
-    h = s;
-    l = __fadd_rn(e, __fadd_rn(l, xl));
-}
-
-// gamma * (ref - R0) - c_o a as a pair
-__device__ __forceinline__ void action_base(float gam, float2 ref, float2 R0, float ca, float &bh, float &bl) {
-    float dh, de;
-    two_sum(ref.x, -R0.x, dh, de);
-    const float dl = __fadd_rn(de, __fsub_rn(ref.y, R0.y));
-    float ph, pe;
-    two_prod(gam, dh, ph, pe);
-    const float pl = __fmaf_rn(gam, dl, pe);
-    float s, e;
-    two_sum(ca, ph, s, e);
-    bh = s;
-    bl = __fadd_rn(e, pl);
-}
-
-// gamma * R0 + (bh, bl), normalised pair
-__device__ __forceinline__ float2 pair_finish(float gam, float2 R0, float bh, float bl) {
-    float ph, pe;
-    two_prod(gam, R0.x, ph, pe);
-    const float pl = __fmaf_rn(gam, R0.y, pe);
-    float sh, se;
-    two_sum(ph, bh, sh, se);
-    const float lo = __fadd_rn(se, __fadd_rn(pl, bl));
-    float vh, vl;
-    fast_two_sum(sh, lo, vh, vl);
-    return make_float2(vh, vl);
-}
-
-// ===========================================================================
-// factorised single-product sweep.  A rest index r (digits 1..K-1 of s) is
-// handled by `lpr` consecutive lanes; lane `part` owns the XW values
-// x = part*XW .. part*XW+XW-1 of the expiring slot (digit 0 of s), kept in
-// registers.  For a given order a the next states only depend on r, a and the
-// demand e that reaches the other slots, g(e) = V[s'(r, a, e)]:
-//   FIFO: C(x) = sum_d p_d g(clamp(d - x, 0, R))   (x is issued first)
-//   LIFO: C    = sum_d p_d g(min(d, R))            (x is issued last)
-// The FIFO correlation runs in chunks of XW demands over a register window of
-// gathered values; each chunk first walks the next-state indices, then issues
-// all of its loads, then consumes them, so the loads overlap.
-// ===========================================================================
-template <int XW, int LIFO, int VK>
-__device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid, unsigned n_blocks, int mode,
-                                           const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int lpr,
-                                           unsigned char *smem_raw) {
-    constexpr bool PAIR = (VK == VK_PAIR);
-    constexpr int LCH = 8;   // LIFO load batch
-    SolveState *st = kp.st;
-    Bufs B;
-    if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
-    const ProdParams &P = kp.p[0];
-    const int G = P.G;
-    const int RB = kGroupThreads / lpr;                    // rests per block
-    float *s_tab = (float *)smem_raw;
-    float *s_out = s_tab + ((kp.n_tables + 3) & ~3);       // PAIR: float2 per state
-    uint8_t *s_pol = (uint8_t *)(s_out + RB * G * (PAIR ? 2 : 1));
-    load_tables<float>(s_tab, (const float *)kp.tables, kp.n_tables);
-    const float *s_p = s_tab + P.off_p;
-    const float *s_RT = s_tab + P.off_RT;
-    const float *s_RTlo = s_tab + P.off_RTlo;
-
-    const uint32_t nR = P.nS / (uint32_t)G;
-    const int rl = threadIdx.x / lpr;
-    const int part = threadIdx.x - rl * lpr;
-    const uint32_t r = bid * (uint32_t)RB + (uint32_t)rl;
-    const bool active = (rl < RB) && (r < nR);
-    const int x0 = part * XW;
-    const int nx = min(XW, G - x0);                        // >= 1 because lpr = ceil(G / XW)
-    const float gam = (float)kp.gamma;
-    const float c_o = (float)P.c_o;
-    const int dmax = P.dmax;
-    const bool shared_lifo = LIFO && lifo_shared_ok(P);
-    const bool shared_fifo = !LIFO && fifo_shared_ok(P);
-    // per-thread columns (stride kGroupThreads) of the shared LIFO sequences / FIFO path
-    float *colT = (float *)(((uintptr_t)(s_pol + RB * G) + 15) & ~(uintptr_t)15) + threadIdx.x;
-    float *colH = colT + G * kGroupThreads;
-    uint32_t *colP = (uint32_t *)colT;
-    int Rrest = 0;   // units in the rest slots (without the order when L = 1)
-
-    float bh[XW], bl[XW];
-    int arg[XW];
-#pragma unroll
-    for (int xi = 0; xi < XW; ++xi) {
-        bh[xi] = -INFINITY;
-        bl[xi] = 0.f;
-        arg[xi] = 0;
-    }
-    float2 R0 = make_float2(0.f, 0.f);
-    if (active) {
-        const RestInfo ri = decode_rest(r, P);
-        Rrest = ri.R;
-        const float *V1 = (const float *)B.vin;
-        const float2 *V2 = (const float2 *)B.vin;
-        if (PAIR) R0 = __ldg(V2 + r);   // s'_0 of action 0
-        if (shared_fifo) {
-            // FIFO: the demand reaching the rest slots empties them oldest first; that path
-            // (relative to the rest index r) is the same for every order
-            Walker wp;
-            walker_init(wp, r, ri.packed, P.n_rest_slots, P.cb, 0, 1u);
-            const int nP = min(ri.R, dmax) + 1;
-            uint32_t *cp = colP;
-            cp[0] = r;
-            for (int e = 1; e < nP; ++e) {
-                walker_step(wp, P.cb, 0, (uint32_t)G);
-                cp[e * kGroupThreads] = wp.idx;
-            }
-        }
-        if (shared_lifo) {
-            // LIFO with L = 1 issues the new order first, so every action's next states
-            // come from two shared sequences: T[j] = V[r + j G^(K-1)] (part of the order
-            // left) and H[k] = V[state r after k units issued LIFO from X_{m-1}..X_2]
-            const int nH = min(ri.R, dmax) + 1;
-            auto value = [&](uint32_t i) -> float {
-                if (PAIR) return pair_diff(__ldg(V2 + i), R0);
-                return __ldg(V1 + i);
-            };
-            for (int j0 = 0; j0 < G; j0 += LCH) {
-                float v[LCH];
-#pragma unroll
-                for (int j = 0; j < LCH; ++j) v[j] = (j0 + j < G) ? value(r + (uint32_t)(j0 + j) * P.w_top) : 0.f;
-#pragma unroll
-                for (int j = 0; j < LCH; ++j)
-                    if (j0 + j < G) colT[(j0 + j) * kGroupThreads] = v[j];
-            }
-            Walker wh;
-            walker_init(wh, r, ri.packed, P.m - 2, P.cb, 1, P.m >= 3 ? P.w_zt / (uint32_t)G : 1u);
-            int kc = 0;
-            for (int k0 = 0; k0 < nH; k0 += LCH) {
-                uint32_t idx[LCH];
-#pragma unroll
-                for (int j = 0; j < LCH; ++j) {
-                    const int kk = min(k0 + j, nH - 1);
-                    for (; kc < kk; ++kc) walker_step(wh, P.cb, 1, (uint32_t)G);
-                    idx[j] = wh.idx;
-                }
-                float v[LCH];
-#pragma unroll
-                for (int j = 0; j < LCH; ++j) v[j] = value(idx[j]);
-#pragma unroll
-                for (int j = 0; j < LCH; ++j)
-                    if (k0 + j < nH) colH[(k0 + j) * kGroupThreads] = v[j];
-            }
-        }
-        for (int a = 0; a < G; ++a) {
-            unsigned long long packed;
-            int R;
-            slots_for_action(P, ri, a, packed, R);
-            Walker wk;
-            const uint32_t idx0 = r + (uint32_t)a * P.w_top;
-            walker_init(wk, idx0, packed, P.m - 1, P.cb, LIFO, P.w_zt);
-            float2 ref = make_float2(0.f, 0.f);
-            float g0 = 0.f;
-            if (shared_lifo)
-                ref = R0;   // all shared values are measured from R0
-            else if (PAIR)
-                ref = __ldg(V2 + idx0);
-            else
-                g0 = __ldg(V1 + idx0);
-            float acc[XW];
-            if (!LIFO) {
-                // lane-local demand axis dd = d - x0: C(x0+xi) = sum_dd p[dd+x0] g(clamp(dd-xi, 0, R))
-                float gprev[XW];
-#pragma unroll
-                for (int xi = 0; xi < XW; ++xi) {
-                    acc[xi] = 0.f;
-                    gprev[xi] = g0;
-                }
-                int ecur = 0;
-                const int nch = (dmax + XW) / XW;
-                // one chunk of XW demands; in the first chunk of a float-pair sweep the window
-                // before it holds g(0) - ref = 0 exactly, so those products are skipped
-                const uint32_t atop = (uint32_t)a * P.w_top;
-                auto chunk = [&](int c, auto first) {
-                    constexpr bool FIRST = decltype(first)::value;
-                    const int d0 = c * XW - x0;
-                    uint32_t idx[XW];
-                    if (shared_fifo) {
-                        // rest path shared by all orders; with L = 1 the order is issued last
-                        // demands beyond dmax carry no mass: clamping e there keeps every index inside
-                        // the column (0..min(Rrest, dmax)) and inside the value array
-                        const int ecap = min(R, dmax);
-#pragma unroll
-                        for (int j = 0; j < XW; ++j) {
-                            const int e = min(max(d0 + j, 0), ecap);
-                            idx[j] = (e <= Rrest) ? colP[e * kGroupThreads] + atop
-                                                  : (uint32_t)(a - (e - Rrest)) * P.w_top;
-                        }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < XW; ++j) {
-                            const int e = min(max(d0 + j, 0), R);
-                            for (; ecur < e; ++ecur) walker_step(wk, P.cb, 0, (uint32_t)G);
-                            idx[j] = wk.idx;
-                        }
-                    }
-                    float gcur[XW];
-                    if (PAIR) {
-                        float2 raw[XW];
-#pragma unroll
-                        for (int j = 0; j < XW; ++j) raw[j] = __ldg(V2 + idx[j]);
-#pragma unroll
-                        for (int j = 0; j < XW; ++j) gcur[j] = pair_diff(raw[j], ref);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < XW; ++j) gcur[j] = __ldg(V1 + idx[j]);
-                    }
-#pragma unroll
-                    for (int j = 0; j < XW; ++j) {
-                        const float pd = s_p[d0 + x0 + j];
-#pragma unroll
-                        for (int xi = 0; xi < XW; ++xi) {
-                            const int kk = j - xi;
-                            if (PAIR && FIRST && kk < 0) continue;
-                            const float gv = (kk >= 0) ? gcur[kk] : gprev[XW + kk];
-                            acc[xi] = fmaf(pd, gv, acc[xi]);
-                        }
-                    }
-#pragma unroll
-                    for (int j = 0; j < XW; ++j) gprev[j] = gcur[j];
-                };
-                chunk(0, std::true_type{});
-                for (int c = 1; c < nch; ++c) chunk(c, std::false_type{});
-            } else if (shared_lifo) {
-                // C_a = sum_d p_d g_a(min(d, R)), g_a(e) = T[a-e] (e <= a) or H[e-a] (e > a)
-                float c = 0.f;
-                for (int d = 0; d <= dmax; ++d) {
-                    const int e = min(d, R);
-                    const float v = (e <= a) ? colT[(a - e) * kGroupThreads] : colH[(e - a) * kGroupThreads];
-                    c = fmaf(s_p[d], v, c);
-                }
-#pragma unroll
-                for (int xi = 0; xi < XW; ++xi) acc[xi] = c;
-            } else {
-                float c = 0.f;
-                int ecur = 0;
-                for (int d0 = 0; d0 <= dmax; d0 += LCH) {
-                    uint32_t idx[LCH];
-#pragma unroll
-                    for (int j = 0; j < LCH; ++j) {
-                        const int e = min(d0 + j, R);
-                        for (; ecur < e; ++ecur) walker_step(wk, P.cb, 1, (uint32_t)G);
-                        idx[j] = wk.idx;
-                    }
-                    float gv[LCH];
-                    if (PAIR) {
-                        float2 raw[LCH];
-#pragma unroll
-                        for (int j = 0; j < LCH; ++j) raw[j] = __ldg(V2 + idx[j]);
-#pragma unroll
-                        for (int j = 0; j < LCH; ++j) gv[j] = pair_diff(raw[j], ref);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < LCH; ++j) gv[j] = __ldg(V1 + idx[j]);
-                    }
-#pragma unroll
-                    for (int j = 0; j < LCH; ++j) c = fmaf(s_p[d0 + j], gv[j], c);   // zero mass beyond dmax
-                }
-#pragma unroll
-                for (int xi = 0; xi < XW; ++xi) acc[xi] = c;
-            }
-            const float *rt = s_RT + R * G + x0;
-            if (PAIR) {
-                float Bh, Bl;
-                action_base(gam, ref, R0, __fmul_rn(-c_o, (float)a), Bh, Bl);
-                const float *rtl = s_RTlo + R * G + x0;
-#pragma unroll
-                for (int xi = 0; xi < XW; ++xi) {
-                    if (xi < nx) {
-                        float qh = Bh, ql = Bl;
-                        pair_add(qh, ql, rt[xi], rtl[xi]);
-                        ql = __fmaf_rn(gam, acc[xi], ql);
-                        const float diff = __fadd_rn(__fsub_rn(qh, bh[xi]), __fsub_rn(ql, bl[xi]));
-                        if (diff > 0.f) {
-                            bh[xi] = qh;
-                            bl[xi] = ql;
-                            arg[xi] = a;
-                        }
-                    }
-                }
-            } else {
-                const float base = -c_o * (float)a;
-#pragma unroll
-                for (int xi = 0; xi < XW; ++xi) {
-                    if (xi < nx) {
-                        const float q = fmaf(gam, acc[xi], base + rt[xi]);
-                        if (q > bh[xi]) {
-                            bh[xi] = q;
-                            arg[xi] = a;
-                        }
-                    }
-                }
-            }
-        }
-        if (!PAIR && r == 0 && part == 0 && mode == MODE_SWEEP) st->c_next = bh[0];
-    }
-    // stage the block's G * RB contiguous states through shared memory
-    if (rl < RB) {
-#pragma unroll
-        for (int xi = 0; xi < XW; ++xi) {
-            if (xi < nx) {
-                const int o = rl * G + x0 + xi;
-                if (PAIR)
-                    ((float2 *)s_out)[o] = active ? pair_finish(gam, R0, bh[xi], bl[xi]) : make_float2(0.f, 0.f);
-                else
-                    s_out[o] = bh[xi];
-                s_pol[o] = (uint8_t)arg[xi];
-            }
-        }
-    }
-    __syncthreads();
-    const uint32_t s0 = bid * (uint32_t)(RB * G);
-    const uint32_t nblk = (uint32_t)(RB * G);
-    float mx = -INFINITY, mn = INFINITY;
-    for (uint32_t i = threadIdx.x; i < nblk; i += kGroupThreads) {
-        const uint32_t s = s0 + i;
-        if (s >= P.nS) break;
-        if (PAIR) {
-            const float2 *vin2 = (const float2 *)B.vin;
-            float2 *vout2 = (float2 *)B.vout;
-            if (mode == MODE_EXTRACT) {
-                if (vout2) vout2[s] = vin2[s];
-            } else {
-                const float2 vnew = ((const float2 *)s_out)[i];
-                const float2 vold = vin2[s];
-                vout2[s] = vnew;
-                const float dlt = pair_diff(vnew, vold);
-                mx = fmaxf(mx, dlt);
-                mn = fminf(mn, dlt);
-            }
-        } else {
-            const float *vin1 = (const float *)B.vin;
-            float *vout1 = (float *)B.vout;
-            if (mode == MODE_EXTRACT) {
-                if (vout1) vout1[s] = vin1[s];
-            } else {
-                const float vnew = s_out[i] - B.cnorm;
-                const float vold = vin1[s];
-                vout1[s] = vnew;
-                const float dlt = vnew - vold;
-                mx = fmaxf(mx, dlt);
-                mn = fminf(mn, dlt);
-            }
-        }
-        if (B.pol) B.pol[s] = s_pol[i];
-    }
-    if (mode != MODE_EXTRACT) block_reduce_and_finalize<float>(mx, mn, st, mode, n_blocks);
-}
-
-template <int XW, int LIFO, int VK>
-__global__ void __launch_bounds__(kGroupThreads)
-sweep_group_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int lpr) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    group_body<XW, LIFO, VK>(kp, blockIdx.x, gridDim.x, mode, vin_arg, vout_arg, pol_arg, lpr, smem_raw);
-}
-
-// ---------------------------------------------------------------------------
-// batched sweep for the solve server: one launch covers every active instance.
-// Block b belongs to the slot s with block_start[s] <= b < block_start[s+1];
-// each slot has its own tables, value buffers and SolveState.
-// ---------------------------------------------------------------------------
-template <int XW>
-__global__ void __launch_bounds__(kGroupThreads)
-sweep_batch_kernel(const KernelParams *kps, const int *modes, const int *lprs, const uint32_t *block_start,
-                   int n_slots) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ KernelParams s_kp;
-    __shared__ int s_slot;
-    const uint32_t b = blockIdx.x;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = n_slots - 1;   // last slot with block_start <= b
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (block_start[mid] <= b) lo = mid; else hi = mid - 1;
-        }
-        s_slot = lo;
-        s_kp = kps[lo];
-    }
-    __syncthreads();
-    const int s = s_slot;
-    const unsigned nb = block_start[s + 1] - block_start[s];
-    const uint32_t local = b - block_start[s];
-    if (s_kp.issuing)
-        group_body<XW, 1, VK_PAIR>(s_kp, local, nb, modes[s], nullptr, nullptr, nullptr, lprs[s], smem_raw);
-    else
-        group_body<XW, 0, VK_PAIR>(s_kp, local, nb, modes[s], nullptr, nullptr, nullptr, lprs[s], smem_raw);
-}
 
 // ===========================================================================
 // per-state expectation helpers (generic kernels, policy evaluation)
@@ -1164,42 +629,6 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
 // ===========================================================================
 // launch descriptors and launchers
 // ===========================================================================
-static size_t group_smem(const KernelParams &kp, int rb, int vk) {
-    const ProdParams &P = kp.p[0];
-    const size_t vb = (vk == VK_PAIR) ? 8 : 4;
-    size_t bytes = (size_t)((kp.n_tables + 3) & ~3) * 4 + (size_t)rb * P.G * (vb + 1) + 16;
-    if (kp.issuing && lifo_shared_ok(P)) bytes += (size_t)(P.G + P.dmax + 1) * kGroupThreads * 4;
-    if (!kp.issuing && fifo_shared_ok(P)) bytes += (size_t)(P.dmax + 1) * kGroupThreads * 4;
-    return bytes;
-}
-
-template <int XW, int LIFO, int VK>
-static cudaError_t describe_group_t(const KernelParams &kp, LaunchDesc &d) {
-    const int G = kp.p[0].G;
-    const int lpr = (G + XW - 1) / XW;
-    const int rb = kGroupThreads / lpr;
-    const uint32_t nR = kp.p[0].nS / (uint32_t)G;
-    d.fn = (const void *)sweep_group_kernel<XW, LIFO, VK>;
-    d.grid = dim3((nR + rb - 1) / rb);
-    d.block = dim3(kGroupThreads);
-    d.smem = group_smem(kp, rb, VK);
-    d.lpr = lpr;
-    return cudaFuncSetAttribute(sweep_group_kernel<XW, LIFO, VK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)d.smem);
-}
-
-template <int LIFO, int VK>
-static cudaError_t describe_group_l(const KernelParams &kp, int xw, LaunchDesc &d) {
-    switch (xw) {
-#define VIB_XW(w) \
-    case w: return describe_group_t<w, LIFO, VK>(kp, d);
-        VIB_XW(1) VIB_XW(2) VIB_XW(3) VIB_XW(4) VIB_XW(5) VIB_XW(6) VIB_XW(7) VIB_XW(8) VIB_XW(9) VIB_XW(10)
-        VIB_XW(11) VIB_XW(12) VIB_XW(16) VIB_XW(21) VIB_XW(24)
-#undef VIB_XW
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 bool group_width_supported(int xw) {
     switch (xw) {
         case 1: case 2: case 3: case 4: case 5: case 6: case 7: case 8: case 9: case 10: case 11: case 12:
@@ -1246,62 +675,16 @@ cudaError_t describe_sweep(const KernelParams &kp, int vk, int kahan, int use_gr
     d.lpr = 0;
     if (use_group) {
         const int xw = use_group;   // lane width of the factorised kernel
-        if (vk == VK_PAIR)
-            return kp.issuing ? describe_group_l<1, VK_PAIR>(kp, xw, d) : describe_group_l<0, VK_PAIR>(kp, xw, d);
-        return kp.issuing ? describe_group_l<1, VK_SINGLE>(kp, xw, d) : describe_group_l<0, VK_SINGLE>(kp, xw, d);
+        const bool pipe = kp.p[0].L >= 2;
+        if (vk == VK_PAIR) {
+            if (kp.issuing) return pipe ? describe_group_lifo_pipe(kp, xw, d) : describe_group_lifo(kp, xw, d);
+            return pipe ? describe_group_fifo_pipe(kp, xw, d) : describe_group_fifo(kp, xw, d);
+        }
+        return kp.issuing ? describe_group_lifo_single(kp, xw, d) : describe_group_fifo_single(kp, xw, d);
     }
     if (vk == VK_DOUBLE) return describe_generic_t<VK_DOUBLE, 0>(kp, d);
     if (vk == VK_PAIR) return kahan ? describe_generic_t<VK_PAIR, 1>(kp, d) : describe_generic_t<VK_PAIR, 0>(kp, d);
     return kahan ? describe_generic_t<VK_SINGLE, 1>(kp, d) : describe_generic_t<VK_SINGLE, 0>(kp, d);
-}
-
-// lane-width class of the batched server kernel for an instance: one lane per
-// rest with the smallest instantiated width >= Q+1 (two lanes above 24)
-int batch_width(int G) {
-    if (G <= 8) return 8;
-    if (G <= 12) return 12;
-    if (G <= 16) return 16;
-    if (G <= 21) return 21;
-    return 24;
-}
-
-// blocks and shared memory the batched kernel needs for one slot
-void batch_geometry(const KernelParams &kp, int *lpr, uint32_t *blocks, size_t *smem) {
-    const int G = kp.p[0].G;
-    const int xw = batch_width(G);
-    const int l = (G + xw - 1) / xw;
-    const int rb = kGroupThreads / l;
-    *lpr = l;
-    *blocks = (kp.p[0].nS / (uint32_t)G + rb - 1) / rb;
-    *smem = group_smem(kp, rb, VK_PAIR);
-}
-
-template <int XW>
-static cudaError_t launch_batch_t(const KernelParams *kps, const int *modes, const int *lprs,
-                                  const uint32_t *block_start, int n_slots, uint32_t total_blocks, size_t smem,
-                                  cudaStream_t stream) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_batch_kernel<XW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    sweep_batch_kernel<XW><<<total_blocks, kGroupThreads, smem, stream>>>(kps, modes, lprs, block_start, n_slots);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sweep_batch(int xw, const KernelParams *kps, const int *modes, const int *lprs,
-                               const uint32_t *block_start, int n_slots, uint32_t total_blocks, size_t smem,
-                               cudaStream_t stream) {
-    switch (xw) {
-        case 8: return launch_batch_t<8>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
-        case 12: return launch_batch_t<12>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
-        case 16: return launch_batch_t<16>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
-        case 21: return launch_batch_t<21>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
-        case 24: return launch_batch_t<24>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
-        default: return cudaErrorInvalidValue;
-    }
 }
 
 // compact per-slot status for the server's host loop
