@@ -260,7 +260,7 @@ vi_status vi_server_destroy(vi_server srv);
  * given, the stream is synchronised); stream: cudaStream_t or NULL.
  * Scratch: the expectation tables and the reduction slots live in a fixed
  * array in device memory that belongs to the library, holding at most
- * VI_NOALLOC_MAX_TABLE_FLOATS table entries (3 (dmax + 1 + mQ + 2(Q+1) + 2)
+ * VI_NOALLOC_MAX_TABLE_FLOATS table entries (3 (dmax + 1 + mQ + 2(Q+1) + 34)
  * + 2 (Q+1)((m-1)Q + 1) are needed); larger instances get VI_EINVAL.  Every
  * GPU that loads the library holds this array (about 65 KiB) until the
  * process exits.  All calls share it and it keeps the last call's contents

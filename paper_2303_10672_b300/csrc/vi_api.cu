@@ -91,7 +91,7 @@ static std::vector<double> expected_leftover(const std::vector<double> &pmf, int
 static void fill_product_tables(ProdParams &P, const std::vector<double> &pmf, int issuing, const double *cost,
                                 bool with_reward, std::vector<double> &blob) {
     const int dmax = P.dmax;
-    P.pn = dmax + 1 + P.tmax + 2 * P.G + 2;
+    P.pn = p_table_len(dmax, P.tmax, P.G);
     P.off_p = (int)blob.size();
     for (int k = 0; k < P.pn; ++k) blob.push_back(k <= dmax ? pmf[k] : 0.0);
     P.off_F = (int)blob.size();
@@ -535,43 +535,46 @@ static vi_status autotune(vi_problem *h, cudaStream_t s) {
     const int nc = group_width_candidates(P.G, cand, 16);
     const size_t nb = (size_t)h->kp.nS * h->value_bytes;
     void *a = nullptr, *b = nullptr;
-    CUDA_TRY(cudaMallocAsync(&a, nb, s));
-    CUDA_TRY(cudaMallocAsync(&b, nb, s));
-    CUDA_TRY(cudaMemsetAsync(a, 0, nb, s));
-    cudaEvent_t e0, e1;
-    CUDA_TRY(cudaEventCreate(&e0));
-    CUDA_TRY(cudaEventCreate(&e1));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     float best_ms = INFINITY;
     int best = heuristic_width(P.G, h->kp.issuing);
     KernelParams kp = h->kp;
     int mode = MODE_PLAIN;
     uint8_t *np = nullptr;
-    for (int i = 0; i < nc; ++i) {
+    // every failure below falls through to the release of the scratch and events
+    cudaError_t ce = cudaMallocAsync(&a, nb, s);
+    if (ce == cudaSuccess) ce = cudaMallocAsync(&b, nb, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(a, 0, nb, s);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    for (int i = 0; i < nc && ce == cudaSuccess; ++i) {
         LaunchDesc ld;
         if (describe_sweep(kp, h->vk, h->kahan, cand[i], ld) != cudaSuccess) continue;
         int lpr = ld.lpr;
         void *args[] = {&kp, &mode, &a, &b, &np, &lpr};
         float ms_min = INFINITY;
-        for (int rep = 0; rep < 3; ++rep) {
-            CUDA_TRY(cudaEventRecord(e0, s));
-            vi_status st = launch_desc(ld, args, s);
-            if (st != VI_OK) return st;
-            CUDA_TRY(cudaEventRecord(e1, s));
-            CUDA_TRY(cudaEventSynchronize(e1));
+        for (int rep = 0; rep < 3 && ce == cudaSuccess; ++rep) {
             float ms = 0.f;
-            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep > 0) ms_min = std::min(ms_min, ms);   // first launch warms caches and code
+            ce = cudaEventRecord(e0, s);
+            if (ce == cudaSuccess) ce = cudaLaunchKernel(ld.fn, ld.grid, ld.block, args, ld.smem, s);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+            if (ce == cudaSuccess && rep > 0) ms_min = std::min(ms_min, ms);   // first launch warms caches and code
         }
-        if (ms_min < best_ms) {
+        if (ce == cudaSuccess && ms_min < best_ms) {
             best_ms = ms_min;
             best = cand[i];
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    CUDA_TRY(cudaFreeAsync(a, s));
-    CUDA_TRY(cudaFreeAsync(b, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (a) cudaFreeAsync(a, s);
+    if (b) cudaFreeAsync(b, s);
+    cudaError_t se = cudaStreamSynchronize(s);
+    if (ce == cudaSuccess) ce = se;
+    if (ce != cudaSuccess)
+        return vi_fail(ce == cudaErrorMemoryAllocation ? VI_ENOMEM : VI_ECUDA, "autotune: %s", cudaGetErrorString(ce));
     h->group_xw = best;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best;

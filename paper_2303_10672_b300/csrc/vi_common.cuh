@@ -100,6 +100,10 @@ struct SolveState {
     double crit, dmax_abs, dmin_abs;
 };
 
+// length of the p / F / tail tables: zero (p, tail) or one (F) beyond dmax, long
+// enough for every index a sweep kernel forms (x + k + chunk padding, x + R)
+__host__ __device__ inline int p_table_len(int dmax, int tmax, int G) { return dmax + 1 + tmax + 2 * G + 34; }
+
 // LIFO with L = 1 (m >= 2): the factorised kernel gathers the two shared
 // sequences of an action-independent layout once per rest, if their per-thread
 // columns fit in 64 KiB of shared memory for a block of 128 threads

@@ -2,6 +2,8 @@
 // the per-variant translation units vi_group_*.cu and by vi_batch.cu.
 #pragma once
 
+#include <algorithm>
+
 #include "vi_device.cuh"
 
 namespace vib {
@@ -51,20 +53,27 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
     const bool shared_lifo = LIFO && !LPIPE && lifo_shared_ok(P);
     const bool shared_fifo = !LIFO && fifo_shared_ok(P);
     constexpr bool rt_common = LPIPE;   // L >= 2: the remaining stock R does not depend on the order
-    // per-thread columns (stride kGroupThreads) of the shared LIFO sequences / FIFO path
-    float *colT = (float *)(((uintptr_t)(s_pol + RB * G) + 15) & ~(uintptr_t)15) + threadIdx.x;
+    // per-thread columns (stride kGroupThreads) of the shared LIFO sequences / FIFO path;
+    // they share their space with the output staging, which is written after a barrier
+    float *colT = s_out + threadIdx.x;
     float *colH = colT + G * kGroupThreads;
     uint32_t *colP = (uint32_t *)colT;
     int Rrest = 0;   // units in the rest slots (without the order when L = 1)
 
     float bh[XW], bl[XW];
-    int arg[XW];
+    uint32_t argp[(XW + 3) / 4];   // best order per x, one byte each (G <= 256)
 #pragma unroll
     for (int xi = 0; xi < XW; ++xi) {
         bh[xi] = -INFINITY;
         bl[xi] = 0.f;
-        arg[xi] = 0;
     }
+#pragma unroll
+    for (int i = 0; i < (XW + 3) / 4; ++i) argp[i] = 0u;
+    // replace byte xi & 3 of argp[xi >> 2] by the order a
+    auto set_arg = [&](int xi, int a) {
+        constexpr unsigned sel[4] = {0x3214u, 0x3240u, 0x3410u, 0x4210u};
+        argp[xi >> 2] = __byte_perm(argp[xi >> 2], (unsigned)a, sel[xi & 3]);
+    };
     float2 R0 = make_float2(0.f, 0.f);
     if (active) {
         const RestInfo ri = decode_rest(r, P);
@@ -138,73 +147,75 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                 g0 = __ldg(V1 + idx0);
             float acc[XW];
             if (!LIFO) {
-                // lane-local demand axis dd = d - x0: C(x0+xi) = sum_dd p[dd+x0] g(clamp(dd-xi, 0, R))
-                float gprev[XW];
+                // demand k = d - x reaching the other slots; d <= x leaves them untouched:
+                //   C(x) = F(x) g(0) + sum_{k=1}^{R-1} p[x+k] g(k) + tail[x+R] g(R)      (R >= 1)
+                // A float-pair sweep measures g from ref = g(0), so the first term vanishes.
+                // k runs in chunks of KW over a register window of gathered values; the
+                // probabilities p[x+k] come from shared memory, and groups of x whose whole
+                // chunk lies beyond dmax (zero mass) are skipped.
+                constexpr int KW = 8;
+                constexpr int NG = XW >= 12 ? 3 : (XW >= 6 ? 2 : 1);
+                constexpr int GS = (XW + NG - 1) / NG;
+                if (PAIR) {
 #pragma unroll
-                for (int xi = 0; xi < XW; ++xi) {
-                    acc[xi] = 0.f;
-                    gprev[xi] = g0;
-                }
-                int ecur = 0;
-                const int nch = (dmax + XW) / XW;
-                // one chunk of XW demands; in the first chunk of a float-pair sweep the window
-                // before it holds g(0) - ref = 0 exactly, so those products are skipped
-                const uint32_t atop = (uint32_t)a * P.w_top;
-                auto chunk = [&](int c, auto first) {
-                    constexpr bool FIRST = decltype(first)::value;
-                    const int d0 = c * XW - x0;
-                    uint32_t idx[XW];
-                    if (shared_fifo) {
-                        // rest path shared by all orders; with L = 1 the order is issued last
-                        // demands beyond dmax carry no mass: clamping e there keeps every index inside
-                        // the column (0..min(Rrest, dmax)) and inside the value array
-                        const int ecap = min(R, dmax);
-#pragma unroll
-                        for (int j = 0; j < XW; ++j) {
-                            const int e = min(max(d0 + j, 0), ecap);
-                            idx[j] = (e <= Rrest) ? colP[e * kGroupThreads] + atop
-                                                  : (uint32_t)(a - (e - Rrest)) * P.w_top;
-                        }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < XW; ++j) {
-                            const int e = min(max(d0 + j, 0), R);
-                            for (; ecur < e; ++ecur) walker_step(wk, P.cb, 0, (uint32_t)G);
-                            idx[j] = wk.idx;
-                        }
-                    }
-                    float gcur[XW];
-                    if (PAIR) {
-                        float2 raw[XW];
-#pragma unroll
-                        for (int j = 0; j < XW; ++j) raw[j] = __ldg(V2 + idx[j]);
-#pragma unroll
-                        for (int j = 0; j < XW; ++j) gcur[j] = pair_diff(raw[j], ref);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < XW; ++j) gcur[j] = __ldg(V1 + idx[j]);
-                    }
-#pragma unroll
-                    for (int j = 0; j < XW; ++j) {
-                        const float pd = s_p[d0 + x0 + j];
-#pragma unroll
-                        for (int xi = 0; xi < XW; ++xi) {
-                            const int kk = j - xi;
-                            if (PAIR && FIRST && kk < 0) continue;
-                            const float gv = (kk >= 0) ? gcur[kk] : gprev[XW + kk];
-                            acc[xi] = fmaf(pd, gv, acc[xi]);
-                        }
-                    }
-#pragma unroll
-                    for (int j = 0; j < XW; ++j) gprev[j] = gcur[j];
-                };
-                // the peeled first chunk pays off without a pipeline (L = 1); with one, the
-                // smaller kernel body wins (measured)
-                if (PAIR && !LPIPE) {
-                    chunk(0, std::true_type{});
-                    for (int c = 1; c < nch; ++c) chunk(c, std::false_type{});
+                    for (int xi = 0; xi < XW; ++xi) acc[xi] = 0.f;
                 } else {
-                    for (int c = 0; c < nch; ++c) chunk(c, std::false_type{});
+                    const float *s_F = s_tab + P.off_F + x0;
+#pragma unroll
+                    for (int xi = 0; xi < XW; ++xi) acc[xi] = (R == 0) ? g0 : s_F[xi] * g0;
+                }
+                const uint32_t atop = (uint32_t)a * P.w_top;
+                int ecur = 0;
+                // index of g(e); e never decreases between calls (the walker moves forward)
+                auto index_of = [&](int e) -> uint32_t {
+                    if (shared_fifo) {
+                        // the rest path is shared by all orders; with L = 1 the order is issued last
+                        if (LPIPE || e <= Rrest) return colP[e * kGroupThreads] + atop;
+                        return (uint32_t)(a - (e - Rrest)) * P.w_top;
+                    }
+                    for (; ecur < e; ++ecur) walker_step(wk, P.cb, 0, (uint32_t)G);
+                    return wk.idx;
+                };
+                auto value_of = [&](uint32_t i) -> float {
+                    if (PAIR) return pair_diff(__ldg(V2 + i), ref);
+                    return __ldg(V1 + i);
+                };
+                const int kend = min(R - 1, dmax - x0);   // last k carrying mass for some x of this lane
+                const float *s_px = s_p + x0;
+                for (int k0 = 1; k0 <= kend; k0 += KW) {
+                    uint32_t idx[KW];
+#pragma unroll
+                    for (int j = 0; j < KW; ++j) idx[j] = index_of(min(k0 + j, kend));
+                    float g[KW];
+                    if (PAIR) {
+                        float2 raw[KW];
+#pragma unroll
+                        for (int j = 0; j < KW; ++j) raw[j] = __ldg(V2 + idx[j]);
+#pragma unroll
+                        for (int j = 0; j < KW; ++j) g[j] = (k0 + j <= kend) ? pair_diff(raw[j], ref) : 0.f;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < KW; ++j) g[j] = (k0 + j <= kend) ? __ldg(V1 + idx[j]) : 0.f;
+                    }
+                    float pw[XW + KW - 1];
+#pragma unroll
+                    for (int i = 0; i < XW + KW - 1; ++i) pw[i] = s_px[k0 + i];
+#pragma unroll
+                    for (int q = 0; q < NG; ++q) {
+                        if (q == 0 || x0 + q * GS + k0 <= dmax) {
+#pragma unroll
+                            for (int j = 0; j < KW; ++j)
+#pragma unroll
+                                for (int xi = q * GS; xi < min(XW, (q + 1) * GS); ++xi)
+                                    acc[xi] = fmaf(pw[xi + j], g[j], acc[xi]);
+                        }
+                    }
+                }
+                if (R >= 1 && x0 + R <= dmax) {
+                    const float gR = value_of(index_of(R));
+                    const float *s_tx = s_tab + P.off_tail + x0 + R;
+#pragma unroll
+                    for (int xi = 0; xi < XW; ++xi) acc[xi] = fmaf(s_tx[xi], gR, acc[xi]);
                 }
             } else if (shared_lifo) {
                 // C_a = sum_d p_d g_a(min(d, R)), g_a(e) = T[a-e] (e <= a) or H[e-a] (e > a)
@@ -258,7 +269,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                         if (diff > 0.f) {
                             bh[xi] = Bh;
                             bl[xi] = ql;
-                            arg[xi] = a;
+                            set_arg(xi, a);
                         }
                     }
                 }
@@ -276,7 +287,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                         if (diff > 0.f) {
                             bh[xi] = qh;
                             bl[xi] = ql;
-                            arg[xi] = a;
+                            set_arg(xi, a);
                         }
                     }
                 }
@@ -288,7 +299,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                         const float q = fmaf(gam, acc[xi], base + rt[xi]);
                         if (q > bh[xi]) {
                             bh[xi] = q;
-                            arg[xi] = a;
+                            set_arg(xi, a);
                         }
                     }
                 }
@@ -304,6 +315,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
             if (xi < nx) pair_add(bh[xi], bl[xi], rt[xi], rtl[xi]);
     }
     // stage the block's G * RB contiguous states through shared memory
+    if (shared_fifo || shared_lifo) __syncthreads();   // every column is consumed
     if (rl < RB) {
 #pragma unroll
         for (int xi = 0; xi < XW; ++xi) {
@@ -313,7 +325,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                     ((float2 *)s_out)[o] = active ? pair_finish(gam, R0, bh[xi], bl[xi]) : make_float2(0.f, 0.f);
                 else
                     s_out[o] = bh[xi];
-                s_pol[o] = (uint8_t)arg[xi];
+                s_pol[o] = (uint8_t)(argp[xi >> 2] >> (8 * (xi & 3)));
             }
         }
     }
@@ -367,10 +379,10 @@ sweep_group_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
 inline size_t group_smem(const KernelParams &kp, int rb, int vk) {
     const ProdParams &P = kp.p[0];
     const size_t vb = (vk == VK_PAIR) ? 8 : 4;
-    size_t bytes = (size_t)((kp.n_tables + 3) & ~3) * 4 + (size_t)rb * P.G * (vb + 1) + 16;
-    if (kp.issuing && lifo_shared_ok(P)) bytes += (size_t)(P.G + P.dmax + 1) * kGroupThreads * 4;
-    if (!kp.issuing && fifo_shared_ok(P)) bytes += (size_t)(P.dmax + 1) * kGroupThreads * 4;
-    return bytes;
+    size_t work = (size_t)rb * P.G * (vb + 1);   // output staging, shared with the columns
+    if (kp.issuing && lifo_shared_ok(P)) work = std::max(work, (size_t)(P.G + P.dmax + 1) * kGroupThreads * 4);
+    if (!kp.issuing && fifo_shared_ok(P)) work = std::max(work, (size_t)(P.dmax + 1) * kGroupThreads * 4);
+    return (size_t)((kp.n_tables + 3) & ~3) * 4 + work + 16;
 }
 
 template <int XW, int LIFO, int VK, int LPIPE>

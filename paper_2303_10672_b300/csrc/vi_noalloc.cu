@@ -42,7 +42,7 @@ static double g_leftover[kTabFloats];              // E[(y - D)^+], y = 0..m Q
 // the same tables vi_problem_create builds for one product, into static storage
 static int build_tables_static(ProdParams &P, const double *pmf, int issuing, const double *cost) {
     const int dmax = P.dmax;
-    P.pn = dmax + 1 + P.tmax + 2 * P.G + 2;
+    P.pn = p_table_len(dmax, P.tmax, P.G);
     P.rt_rows = (P.m - 1) * P.Q + 1;
     const long need = 3L * P.pn + 2L * P.G * P.rt_rows;
     if (need > kTabFloats || P.tmax + 1 > kTabFloats) return -1;
