@@ -199,19 +199,26 @@ def run_reference(args):
 # the CUDA path
 # ---------------------------------------------------------------------------
 
-def kernel_flops_per_launch(inst, kernel_kind: str) -> dict:
-    """Algorithmic work of one sweep launch of the factorised kernel."""
-    p = inst.products[0]
-    G = p.Q + 1
-    nR = inst.n_states // G
-    A = p.Q + 1
-    D = p.dmax + 1
-    if inst.issuing == workloads.FIFO:
-        nch = (p.dmax + G) // G
-        fma = nR * A * (nch * G * G + G)
-    else:
-        fma = nR * A * (D + G)
-    return {"fma": fma, "flops": 2 * fma, "bytes": inst.n_states * 8}
+def algorithmic_work(inst) -> dict:
+    """Algorithmic work of one Bellman sweep: one multiply-add of p(d) and the
+    next-state value per (state, order, demand outcome), and the compulsory HBM
+    bytes (old and new value of every state, 8 B float pair each)."""
+    updates = inst.updates_per_sweep
+    return {"updates": updates, "flops": 2 * updates, "bytes": inst.n_states * 16}
+
+
+# DRAM bytes (read + write) of one sweep launch, from `ncu --section MemoryWorkloadAnalysis`
+# captures of the dominant kernel (summaries under profiles/); None once the kernel changed
+NCU_TRAFFIC = {}
+
+
+def l2_read_peak_gbs(vi, torch) -> float:
+    """Best of three L1-bypassing streaming reads of a 32 MiB L2-resident buffer."""
+    nbytes = 32 << 20
+    buf = torch.ones(nbytes // 4, dtype=torch.float32, device="cuda")
+    reps = 64
+    best = min(vi.vi_probe_l2_read(buf, nbytes, reps) for _ in range(3))
+    return nbytes * reps / (best * 1e-3) / 1e9
 
 
 def run_native(args):
@@ -279,16 +286,22 @@ def run_native(args):
     k1.record(stream)
     k1.synchronize()
     k_ms = k0.elapsed_time(k1) / reps
-    work = kernel_flops_per_launch(inst, "group")
+    work = algorithmic_work(inst)
     pk = peaks()
     sm_mhz = clocks.get("sm_mhz") or pk["sm_max_mhz"]
     fp32_peak_tflops = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved_tflops = work["flops"] / (k_ms * 1e-3) / 1e12
+    l2_gbs = l2_read_peak_gbs(vi, torch)
+    gather_gbs = work["updates"] * 4 / (k_ms * 1e-3) / 1e9
     roofline = {
         "bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-        "frac": achieved_tflops / fp32_peak_tflops, "traffic": None,
+        "frac": achieved_tflops / fp32_peak_tflops, "traffic": NCU_TRAFFIC.get(inst.name),
         "kernel": "sweep_group_kernel", "kernel_ms": k_ms,
+        "work": "2 flop (one multiply-add) per state x order x demand outcome",
         "peak_basis": f"148 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock sampled)",
+        "gather": {"logical_GBs": gather_gbs, "l2_read_peak_GBs": l2_gbs, "frac": gather_gbs / l2_gbs,
+                   "basis": "4 B of next-state value per update vs an L1-bypassing read of a 32 MiB "
+                            "L2-resident buffer (measured here)"},
         "hbm_compulsory_GBs": work["bytes"] / (k_ms * 1e-3) / 1e9, "hbm_peak_GBs": pk["hbm_gbs"],
     }
 

@@ -275,6 +275,16 @@ vi_status vi_backup_noalloc(int m, int L, int Q, const double cost[5], const dou
                             double gamma, int issuing, const void *V_in, void *V_out, uint8_t *policy,
                             double *dstats, void *stream);
 
+/* Measurement helper (the paper has no counterpart): read bandwidth of the L2
+ * cache, the denominator of the gather roofline.  Streams the caller's device
+ * buffer `reps` times with 16-byte loads that bypass L1, after one untimed pass
+ * that brings it into L2, and returns the timed pass's duration in *ms (CUDA
+ * events on `stream`; the call synchronises the stream).  Choose `bytes` well
+ * below the L2 size (e.g. 32 MiB of 126 MB) so that the passes hit L2; the read
+ * rate is bytes * reps / ms.  The buffer is only read.
+ * Errors: VI_EINVAL (NULL, unaligned or too small buffer, reps < 1), VI_ECUDA. */
+vi_status vi_probe_l2_read(const void *buf, size_t bytes, int reps, void *stream, float *ms);
+
 const char *vi_status_string(vi_status s);
 const char *vi_last_error(void);
 

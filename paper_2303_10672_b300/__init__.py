@@ -98,6 +98,7 @@ def lib() -> C.CDLL:
         "vi_server_destroy": ([C.c_void_p], C.c_int),
         "vi_backup_noalloc": ([C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                C.c_int, C.c_double, C.c_int, vp, vp, u8p, C.POINTER(C.c_double), vp], C.c_int),
+        "vi_probe_l2_read": ([vp, C.c_size_t, C.c_int, vp, C.POINTER(C.c_float)], C.c_int),
         "vi_status_string": ([C.c_int], C.c_char_p),
         "vi_last_error": ([], C.c_char_p),
     }
@@ -259,6 +260,13 @@ def vi_simulate(h: int, policy, n_rollouts: int, horizon: int, warmup: int, seed
                 traj=None, stream=None) -> None:
     _check(lib().vi_simulate(h, _addr(policy), n_rollouts, horizon, warmup, C.c_uint64(seed), _addr(returns),
                              _addr(kpis), _addr(traj), _stream(stream)), "vi_simulate")
+
+
+def vi_probe_l2_read(buf, nbytes: int, reps: int, stream=None) -> float:
+    """Duration in ms of `reps` L1-bypassing reads of an L2-resident device buffer."""
+    ms = C.c_float()
+    _check(lib().vi_probe_l2_read(_addr(buf), nbytes, reps, _stream(stream), C.byref(ms)), "vi_probe_l2_read")
+    return ms.value
 
 
 def vi_server_create(mem_budget_bytes: int, max_slots: int, stream=None) -> int:

@@ -69,10 +69,14 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
     }
 #pragma unroll
     for (int i = 0; i < (XW + 3) / 4; ++i) argp[i] = 0u;
-    // replace byte xi & 3 of argp[xi >> 2] by the order a
-    auto set_arg = [&](int xi, int a) {
+    // keep (h, l, a) as the best of x if `up`: selects, no branch.  Byte xi & 3 of
+    // argp[xi >> 2] holds the order.
+    auto take = [&](int xi, bool up, float h, float l, int a) {
         constexpr unsigned sel[4] = {0x3214u, 0x3240u, 0x3410u, 0x4210u};
-        argp[xi >> 2] = __byte_perm(argp[xi >> 2], (unsigned)a, sel[xi & 3]);
+        bh[xi] = up ? h : bh[xi];
+        if (PAIR) bl[xi] = up ? l : bl[xi];
+        const unsigned na = __byte_perm(argp[xi >> 2], (unsigned)a, sel[xi & 3]);
+        argp[xi >> 2] = up ? na : argp[xi >> 2];
     };
     float2 R0 = make_float2(0.f, 0.f);
     if (active) {
@@ -218,12 +222,18 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                     for (int xi = 0; xi < XW; ++xi) acc[xi] = fmaf(s_tx[xi], gR, acc[xi]);
                 }
             } else if (shared_lifo) {
-                // C_a = sum_d p_d g_a(min(d, R)), g_a(e) = T[a-e] (e <= a) or H[e-a] (e > a)
+                // C_a = sum_{d < R} p_d g_a(d) + tail[R] g_a(R), g_a(e) = T[a-e] while the
+                // demand stays within the order (e <= a), H[e-a] beyond it
                 float c = 0.f;
-                for (int d = 0; d <= dmax; ++d) {
-                    const int e = min(d, R);
-                    const float v = (e <= a) ? colT[(a - e) * kGroupThreads] : colH[(e - a) * kGroupThreads];
-                    c = fmaf(s_p[d], v, c);
+                const int dlast = min(R - 1, dmax);
+                const int d1 = min(a, dlast);
+                const float *pT = colT + a * kGroupThreads;
+                for (int d = 0; d <= d1; ++d) c = fmaf(s_p[d], pT[-d * kGroupThreads], c);
+                const float *pH = colH - a * kGroupThreads;
+                for (int d = a + 1; d <= dlast; ++d) c = fmaf(s_p[d], pH[d * kGroupThreads], c);
+                if (R <= dmax) {
+                    const float *pR = (R <= a) ? colT + (a - R) * kGroupThreads : colH + (R - a) * kGroupThreads;
+                    c = fmaf(s_tab[P.off_tail + R], *pR, c);
                 }
 #pragma unroll
                 for (int xi = 0; xi < XW; ++xi) acc[xi] = c;
@@ -255,6 +265,8 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
 #pragma unroll
                 for (int xi = 0; xi < XW; ++xi) acc[xi] = c;
             }
+            // lanes past the last x (x0 + xi >= G) compute values that are never stored;
+            // their table reads stay inside the shared memory that follows the tables
             const float *rt = s_RT + R * G + x0;
             if (PAIR && rt_common) {
                 // L >= 2: R does not depend on the order, so RT(x, R) is common to all
@@ -263,45 +275,29 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                 action_base(gam, ref, R0, __fmul_rn(-c_o, (float)a), Bh, Bl);
 #pragma unroll
                 for (int xi = 0; xi < XW; ++xi) {
-                    if (xi < nx) {
-                        const float ql = __fmaf_rn(gam, acc[xi], Bl);
-                        const float diff = __fadd_rn(__fsub_rn(Bh, bh[xi]), __fsub_rn(ql, bl[xi]));
-                        if (diff > 0.f) {
-                            bh[xi] = Bh;
-                            bl[xi] = ql;
-                            set_arg(xi, a);
-                        }
-                    }
+                    const float ql = __fmaf_rn(gam, acc[xi], Bl);
+                    const float diff = __fadd_rn(__fsub_rn(Bh, bh[xi]), __fsub_rn(ql, bl[xi]));
+                    take(xi, diff > 0.f, Bh, ql, a);
                 }
             } else if (PAIR) {
                 float Bh, Bl;
                 action_base(gam, ref, R0, __fmul_rn(-c_o, (float)a), Bh, Bl);
+                if (LIFO) Bl = __fmaf_rn(gam, acc[0], Bl);   // the expectation does not depend on x
                 const float *rtl = s_RTlo + R * G + x0;
 #pragma unroll
                 for (int xi = 0; xi < XW; ++xi) {
-                    if (xi < nx) {
-                        float qh = Bh, ql = Bl;
-                        pair_add(qh, ql, rt[xi], rtl[xi]);
-                        ql = __fmaf_rn(gam, acc[xi], ql);
-                        const float diff = __fadd_rn(__fsub_rn(qh, bh[xi]), __fsub_rn(ql, bl[xi]));
-                        if (diff > 0.f) {
-                            bh[xi] = qh;
-                            bl[xi] = ql;
-                            set_arg(xi, a);
-                        }
-                    }
+                    float qh = Bh, ql = Bl;
+                    pair_add(qh, ql, rt[xi], rtl[xi]);
+                    if (!LIFO) ql = __fmaf_rn(gam, acc[xi], ql);
+                    const float diff = __fadd_rn(__fsub_rn(qh, bh[xi]), __fsub_rn(ql, bl[xi]));
+                    take(xi, diff > 0.f, qh, ql, a);
                 }
             } else {
                 const float base = -c_o * (float)a;
 #pragma unroll
                 for (int xi = 0; xi < XW; ++xi) {
-                    if (xi < nx) {
-                        const float q = fmaf(gam, acc[xi], base + rt[xi]);
-                        if (q > bh[xi]) {
-                            bh[xi] = q;
-                            set_arg(xi, a);
-                        }
-                    }
+                    const float q = fmaf(gam, acc[xi], base + rt[xi]);
+                    take(xi, q > bh[xi], q, 0.f, a);
                 }
             }
         }

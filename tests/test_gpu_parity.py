@@ -370,3 +370,18 @@ def test_group_widths_bit_identical(inst, precision):
             assert got == ref, f"width {w} differs"
     # and the autotuned choice matches the oracle
     solve_parity(inst, precision)
+
+
+def test_l2_read_probe():
+    """The L2 read probe returns a plausible rate and rejects bad buffers."""
+    import torch
+    nbytes = 8 << 20
+    buf = torch.ones(nbytes // 4, dtype=torch.float32, device="cuda")
+    ms = vi.vi_probe_l2_read(buf, nbytes, 16)
+    gbs = nbytes * 16 / (ms * 1e-3) / 1e9
+    assert 100.0 < gbs < 1e6
+    assert torch.all(buf == 1.0)   # only read
+    with pytest.raises(vi.ViError):
+        vi.vi_probe_l2_read(buf, 15, 1)
+    with pytest.raises(vi.ViError):
+        vi.vi_probe_l2_read(buf, nbytes, 0)
