@@ -207,9 +207,12 @@ def algorithmic_work(inst) -> dict:
     return {"updates": updates, "flops": 2 * updates, "bytes": inst.n_states * 16}
 
 
-# DRAM bytes (read + write) of one sweep launch, from `ncu --section MemoryWorkloadAnalysis`
-# captures of the dominant kernel (summaries under profiles/); None once the kernel changed
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu captures
+# summarised in profiles/sweep_group_*.md; an entry is dropped when that kernel changes
+NCU_TRAFFIC = {
+    "cfg2_m5L2Q20_nb_fifo": 34_302_208,    # sweep_group_kernel<21, FIFO, pair, L>=2>
+    "cfg4_m8L1Q10_lifo": 394_315_520,      # sweep_group_kernel<11, LIFO, pair, L=1>
+}
 
 
 def l2_read_peak_gbs(vi, torch) -> float:
