@@ -210,8 +210,8 @@ def algorithmic_work(inst) -> dict:
 # DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu captures
 # summarised in profiles/sweep_group_*.md; an entry is dropped when that kernel changes
 NCU_TRAFFIC = {
-    "cfg2_m5L2Q20_nb_fifo": 34_302_208,    # sweep_group_kernel<21, FIFO, pair, L>=2>
-    "cfg4_m8L1Q10_lifo": 394_315_520,      # sweep_group_kernel<11, LIFO, pair, L=1>
+    ("cfg2_m5L2Q20_nb_fifo", "sweep_group_kernel (lane width 21)"): 34_302_208,
+    ("cfg4_m8L1Q10_lifo", "sweep_group_kernel (lane width 11)"): 394_315_520,
 }
 
 
@@ -235,9 +235,17 @@ def run_native(args):
             "fp32_single": vi.VI_PREC_FP32_SINGLE}[args.precision or inst.precision]
     prods = [dict(m=q.m, L=q.L, Q=q.Q, cost=q.cost, pmf=q.pmf) for q in inst.products]
     desc, keep = vi.make_desc(prods, inst.gamma, inst.issuing, prec, vi.VI_STOP_SPAN, inst.subst_rate)
+    kernel = {"auto": vi.VI_KERNEL_AUTO, "group": vi.VI_KERNEL_GROUP, "tensor": vi.VI_KERNEL_TENSOR,
+              "generic": vi.VI_KERNEL_GENERIC}[args.kernel]
+
+    def configure(hh):
+        if kernel != vi.VI_KERNEL_AUTO:
+            vi.vi_problem_set_option(hh, vi.VI_OPT_KERNEL, kernel)
+        if args.group_width:
+            vi.vi_problem_set_option(hh, vi.VI_OPT_GROUP_WIDTH, args.group_width)
+
     h = vi.vi_problem_create_desc(desc)
-    if args.group_width:
-        vi.vi_problem_set_option(h, vi.VI_OPT_GROUP_WIDTH, args.group_width)
+    configure(h)
     sizes = vi.vi_problem_sizes(h)
     n = sizes["n_states"]
     vdtype = torch.float64 if sizes["value_bytes"] == 8 else torch.float32
@@ -289,6 +297,9 @@ def run_native(args):
     k1.record(stream)
     k1.synchronize()
     k_ms = k0.elapsed_time(k1) / reps
+    kch, kw = vi.vi_problem_kernel(h)
+    kernel_name = {vi.VI_KERNEL_GENERIC: "sweep_generic_kernel", vi.VI_KERNEL_TENSOR: "sweep_tc_kernel"}.get(
+        kch, f"sweep_group_kernel (lane width {kw})")
     work = algorithmic_work(inst)
     pk = peaks()
     sm_mhz = clocks.get("sm_mhz") or pk["sm_max_mhz"]
@@ -298,8 +309,8 @@ def run_native(args):
     gather_gbs = work["updates"] * 4 / (k_ms * 1e-3) / 1e9
     roofline = {
         "bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-        "frac": achieved_tflops / fp32_peak_tflops, "traffic": NCU_TRAFFIC.get(inst.name),
-        "kernel": "sweep_group_kernel", "kernel_ms": k_ms,
+        "frac": achieved_tflops / fp32_peak_tflops, "traffic": NCU_TRAFFIC.get((inst.name, kernel_name)),
+        "kernel": kernel_name, "kernel_ms": k_ms,
         "work": "2 flop (one multiply-add) per state x order x demand outcome",
         "peak_basis": f"148 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock sampled)",
         "gather": {"logical_GBs": gather_gbs, "l2_read_peak_GBs": l2_gbs, "frac": gather_gbs / l2_gbs,
@@ -315,8 +326,7 @@ def run_native(args):
     ph = torch.empty(n, dtype=torch.uint8).pin_memory().numpy()
     def e2e_step():
         h2 = vi.vi_problem_create_desc(desc)
-        if args.group_width:
-            vi.vi_problem_set_option(h2, vi.VI_OPT_GROUP_WIDTH, args.group_width)
+        configure(h2)
         inf2 = vi.vi_solve_host(h2, TOL, args.max_iters, Vh, ph, flags=sflags)
         vi.vi_problem_destroy(h2)
         return inf2["iters"]
@@ -473,6 +483,8 @@ def main():
     ap.add_argument("--serving", type=int, default=512, help="requests in the serving mix (0 = skip)")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven sweep loop instead of the CUDA graph (same kernels; lets a profiler see each launch)")
+    ap.add_argument("--kernel", choices=["auto", "group", "tensor", "generic"], default="auto",
+                    help="sweep kernel (auto: the autotuner picks among the factorised variants)")
     ap.add_argument("--group-width", type=int, default=0,
                     help="lane width of the factorised kernel (0 = autotuned)")
     args = ap.parse_args()

@@ -142,10 +142,14 @@ vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
 
 /* Per-handle options (no counterpart in the paper; tuning and test hooks).
  * VI_OPT_KERNEL: which sweep kernel runs -- VI_KERNEL_AUTO (factorised kernel
- * whenever the instance allows it), VI_KERNEL_GENERIC (one thread per state)
- * or VI_KERNEL_GROUP (factorised; VI_EINVAL if the instance does not allow it:
+ * whenever the instance allows it; the tensor-core variant is one of the
+ * autotuned candidates), VI_KERNEL_GENERIC (one thread per state),
+ * VI_KERNEL_GROUP (factorised; VI_EINVAL if the instance does not allow it:
  * it needs one product, VI_PREC_FP32 or VI_PREC_FP32_SINGLE, 2 <= Q+1 <= 64 and
- * at least one state digit).
+ * at least one state digit) or VI_KERNEL_TENSOR (factorised, with the FIFO
+ * expectation of a tile of rests and orders computed as one product on the
+ * tensor cores; VI_EINVAL unless one product, FIFO, VI_PREC_FP32, L >= 2,
+ * 2 <= Q+1 <= 32 and Dmax <= 127).
  * VI_OPT_PE_MAX_ITERS: sweep cap of the FP64 policy evaluation in vi_solve.
  * VI_OPT_GROUP_WIDTH: run the factorised kernel with this many expiring-slot
  * values per lane (1..12, 16, 21 or 24; Q+1 is split over ceil((Q+1)/width)
@@ -153,8 +157,15 @@ vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
  * sweep per candidate width, cached per instance shape; the environment
  * variable VI_AUTOTUNE=0 selects a fixed rule instead). */
 enum { VI_OPT_KERNEL = 1, VI_OPT_PE_MAX_ITERS = 2, VI_OPT_GROUP_WIDTH = 3 };
-enum { VI_KERNEL_AUTO = 0, VI_KERNEL_GENERIC = 1, VI_KERNEL_GROUP = 2 };
+enum { VI_KERNEL_AUTO = 0, VI_KERNEL_GENERIC = 1, VI_KERNEL_GROUP = 2, VI_KERNEL_TENSOR = 3 };
 vi_status vi_problem_set_option(vi_handle h, int option, int value);
+
+/* Which sweep kernel the handle runs (no counterpart in the paper): *kernel =
+ * VI_KERNEL_GENERIC, VI_KERNEL_GROUP or VI_KERNEL_TENSOR, *width = the lane
+ * width of VI_KERNEL_GROUP (0 otherwise).  Resolves the choice (and runs the
+ * autotuner, on the handle's default stream) if no solve has done so yet.
+ * Either pointer may be NULL.  Errors: VI_EINVAL (null handle), VI_ECUDA. */
+vi_status vi_problem_kernel(vi_handle h, int *kernel, int *width);
 
 /* Synchronous value iteration (Eq. valueiterationdetupdate, Algorithm 1) from
  * V_0 = 0 (or the warm start), stopping at the first i with the stopping

@@ -23,7 +23,7 @@ VI_STOP_SPAN, VI_STOP_SUPNORM = 0, 1
 VI_PREC_FP32, VI_PREC_FP32_KAHAN, VI_PREC_FP64, VI_PREC_FP32_SINGLE = 0, 1, 2, 3
 VI_FLAG_WARM_START, VI_FLAG_NO_GRAPH, VI_FLAG_POLICY_EVAL = 1, 2, 4
 VI_OPT_KERNEL, VI_OPT_PE_MAX_ITERS, VI_OPT_GROUP_WIDTH = 1, 2, 3
-VI_KERNEL_AUTO, VI_KERNEL_GENERIC, VI_KERNEL_GROUP = 0, 1, 2
+VI_KERNEL_AUTO, VI_KERNEL_GENERIC, VI_KERNEL_GROUP, VI_KERNEL_TENSOR = 0, 1, 2, 3
 
 PRECISIONS = {"fp32": VI_PREC_FP32, "fp32_kahan": VI_PREC_FP32_KAHAN, "fp64": VI_PREC_FP64,
               "fp32_single": VI_PREC_FP32_SINGLE}
@@ -99,6 +99,7 @@ def lib() -> C.CDLL:
         "vi_backup_noalloc": ([C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                C.c_int, C.c_double, C.c_int, vp, vp, u8p, C.POINTER(C.c_double), vp], C.c_int),
         "vi_probe_l2_read": ([vp, C.c_size_t, C.c_int, vp, C.POINTER(C.c_float)], C.c_int),
+        "vi_problem_kernel": ([H, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
         "vi_status_string": ([C.c_int], C.c_char_p),
         "vi_last_error": ([], C.c_char_p),
     }
@@ -260,6 +261,13 @@ def vi_simulate(h: int, policy, n_rollouts: int, horizon: int, warmup: int, seed
                 traj=None, stream=None) -> None:
     _check(lib().vi_simulate(h, _addr(policy), n_rollouts, horizon, warmup, C.c_uint64(seed), _addr(returns),
                              _addr(kpis), _addr(traj), _stream(stream)), "vi_simulate")
+
+
+def vi_problem_kernel(h: int) -> tuple:
+    """(kernel, lane width) of the sweep the handle runs; resolves the choice if needed."""
+    k, w = C.c_int(), C.c_int()
+    _check(lib().vi_problem_kernel(h, C.byref(k), C.byref(w)), "vi_problem_kernel")
+    return k.value, w.value
 
 
 def vi_probe_l2_read(buf, nbytes: int, reps: int, stream=None) -> float:

@@ -454,10 +454,16 @@ extern "C" vi_status vi_problem_set_option(vi_handle h, int option, int value) {
                                "the factorised kernel needs one product, FP32 or FP32_SINGLE precision and "
                                "2 <= Q+1 <= %d", kMaxGroupG);
             h->kernel_choice = VI_KERNEL_GROUP;
+        } else if (value == VI_KERNEL_TENSOR) {
+            if (!h->group_ok || !tc_supported(h->kp, h->vk, h->kahan))
+                return vi_fail(VI_EINVAL,
+                               "the tensor-core kernel needs one product, FIFO, FP32 precision, L >= 2, "
+                               "2 <= Q+1 <= 32 and Dmax <= 127");
+            h->kernel_choice = VI_KERNEL_TENSOR;
         } else {
             return vi_fail(VI_EINVAL, "bad kernel choice %d", value);
         }
-        h->group_xw = 0;
+        h->group_xw = (value == VI_KERNEL_TENSOR) ? kTcWidth : 0;
         if (h->graph_exec) {
             cudaGraphExecDestroy(h->graph_exec);
             h->graph_exec = nullptr;
@@ -495,9 +501,9 @@ extern "C" vi_status vi_problem_set_option(vi_handle h, int option, int value) {
 // kernel choice and autotuning of the factorised kernel's lane width
 // ---------------------------------------------------------------------------
 struct TuneKey {
-    int vk, issuing, m, L, Q, dmax;
+    int vk, issuing, m, L, Q, dmax, tc;
     bool operator<(const TuneKey &o) const {
-        return std::tie(vk, issuing, m, L, Q, dmax) < std::tie(o.vk, o.issuing, o.m, o.L, o.Q, o.dmax);
+        return std::tie(vk, issuing, m, L, Q, dmax, tc) < std::tie(o.vk, o.issuing, o.m, o.L, o.Q, o.dmax, o.tc);
     }
 };
 static std::mutex g_tune_mu;
@@ -517,7 +523,9 @@ static vi_status launch_desc(const LaunchDesc &ld, void **args, cudaStream_t s);
 // time one plain sweep per candidate width on scratch buffers, keep the fastest
 static vi_status autotune(vi_problem *h, cudaStream_t s) {
     const ProdParams &P = h->kp.p[0];
-    const TuneKey key{h->vk, h->kp.issuing, P.m, P.L, P.Q, P.dmax};
+    // the tensor-core kernel competes only when the caller left the choice open
+    const int tc = (h->kernel_choice == VI_KERNEL_AUTO && tc_supported(h->kp, h->vk, h->kahan)) ? 1 : 0;
+    const TuneKey key{h->vk, h->kp.issuing, P.m, P.L, P.Q, P.dmax, tc};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -531,8 +539,9 @@ static vi_status autotune(vi_problem *h, cudaStream_t s) {
         h->group_xw = heuristic_width(P.G, h->kp.issuing);
         return VI_OK;
     }
-    int cand[16];
-    const int nc = group_width_candidates(P.G, cand, 16);
+    int cand[17];
+    int nc = group_width_candidates(P.G, cand, 16);
+    if (tc) cand[nc++] = kTcWidth;
     const size_t nb = (size_t)h->kp.nS * h->value_bytes;
     void *a = nullptr, *b = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -592,6 +601,16 @@ static vi_status choose_kernel(vi_problem *h, cudaStream_t s) {
         if (st != VI_OK) return st;
     }
     h->sweep_xw = h->group_xw;
+    return VI_OK;
+}
+
+extern "C" vi_status vi_problem_kernel(vi_handle h, int *kernel, int *width) {
+    if (!h) return vi_fail(VI_EINVAL, "null handle");
+    vi_status st = choose_kernel(h, nullptr);
+    if (st != VI_OK) return st;
+    const int xw = h->sweep_xw;
+    if (kernel) *kernel = (xw == 0) ? VI_KERNEL_GENERIC : (xw == kTcWidth) ? VI_KERNEL_TENSOR : VI_KERNEL_GROUP;
+    if (width) *width = (xw == 0 || xw == kTcWidth) ? 0 : xw;
     return VI_OK;
 }
 
@@ -761,6 +780,7 @@ extern "C" vi_status vi_solve(vi_handle h, double tol, int max_iters, void *V, u
     CUDA_TRY(cudaStreamSynchronize(s));
     float ms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    if (hs->fault) return vi_fail(VI_ECUDA, "a sweep's bounded wait on the tensor cores gave up; V is not valid");
     vi_status result = hs->converged ? VI_OK : VI_ENOTCONVERGED;
     if (info) {
         memset(info, 0, sizeof(*info));
@@ -841,6 +861,7 @@ extern "C" vi_status vi_backup(vi_handle h, const void *V_in, void *V_out, uint8
         CUDA_TRY(cudaStreamSynchronize(s));
         dstats[0] = h->h_state->dmax_abs;
         dstats[1] = h->h_state->dmin_abs;
+        if (h->h_state->fault) return vi_fail(VI_ECUDA, "the sweep's bounded wait on the tensor cores gave up");
     }
     return VI_OK;
 }

@@ -98,6 +98,7 @@ struct SolveState {
     float c_next;                 // unnormalised value of state 0 in the current sweep
     double offset;                // b: V_abs = b + v
     double crit, dmax_abs, dmin_abs;
+    int fault;                    // set by a kernel whose bounded wait on the tensor cores gave up
 };
 
 // length of the p / F / tail tables: zero (p, tail) or one (F) beyond dmax, long

@@ -478,6 +478,7 @@ __global__ void solve_init_kernel(SolveState *st, uint32_t n) {
         st->key_max = 0ull;
         st->key_min = ~0ull;
         st->blocks_done = 0u;
+        st->fault = 0;
         st->iter = 0;
         st->converged = 0;
         st->crit = INFINITY;
@@ -673,6 +674,7 @@ int group_width_candidates(int G, int *out, int max_out) {
 
 cudaError_t describe_sweep(const KernelParams &kp, int vk, int kahan, int use_group, LaunchDesc &d) {
     d.lpr = 0;
+    if (use_group == kTcWidth) return describe_tc(kp, d);
     if (use_group) {
         const int xw = use_group;   // lane width of the factorised kernel
         const bool pipe = kp.p[0].L >= 2;

@@ -47,9 +47,14 @@ struct LaunchDesc {
     size_t smem;
     int lpr;    // lanes per rest of the factorised kernel (0 for the generic kernel)
 };
-// use_group = 0: generic kernel; > 0: factorised kernel with that lane width XW
+// use_group = 0: generic kernel; kTcWidth: tensor-core FIFO kernel; otherwise the
+// factorised kernel with that lane width XW
 cudaError_t describe_sweep(const KernelParams &kp, int vk, int kahan, int use_group, LaunchDesc &d);
 bool group_width_supported(int xw);
+// lane-width token that selects the tensor-core FIFO sweep (vi_tc.cu)
+constexpr int kTcWidth = 100;
+bool tc_supported(const KernelParams &kp, int vk, int kahan);
+cudaError_t describe_tc(const KernelParams &kp, LaunchDesc &d);
 int batch_width(int G);
 void batch_geometry(const KernelParams &kp, int *lpr, uint32_t *blocks, size_t *smem);
 cudaError_t launch_sweep_batch(int xw, const KernelParams *kps, const int *modes, const int *lprs,

@@ -169,9 +169,9 @@ def test_solve_two_products_general_costs(case):
 # compared on sampled states computed one by one by the oracle
 # ---------------------------------------------------------------------------
 
-def sampled_backup_parity(inst, k_sweeps, n_samples, seed, precision="fp32"):
+def sampled_backup_parity(inst, k_sweeps, n_samples, seed, precision="fp32", kernel=vi.VI_KERNEL_AUTO):
     P = oracle.Problem(inst)
-    with Handle(inst, precision=precision) as H:
+    with Handle(inst, precision=precision, kernel=kernel) as H:
         V, pol, info = H.solve(0.0, k_sweeps)           # V_k (+ offset for the single layout)
         n = H.sizes["n_states"]
         V_next = torch.empty_like(V)

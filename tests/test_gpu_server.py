@@ -60,7 +60,8 @@ def test_results_equal_alone_and_in_the_mix():
     for inst, rid in zip(insts, ids):
         V, pol, info = res[rid]
         assert info["status"] == vi.VI_OK
-        with Handle(inst, precision="fp32") as H:
+        # the server runs the factorised CUDA-core kernel (bit-identical across lane widths)
+        with Handle(inst, precision="fp32", kernel=vi.VI_KERNEL_GROUP) as H:
             Va, pola, ia = H.solve(1e-4, 5000)
             va = H.v_abs(Va, ia)
         assert info["iters"] == ia["iters"]
