@@ -112,6 +112,11 @@ __host__ __device__ inline bool lifo_shared_ok(const ProdParams &P) {
     return P.L == 1 && P.m >= 2 && (P.G + P.dmax + 1) * 128 * 4 <= 64 * 1024;
 }
 
+// LIFO with L = 1 and the shared sequences: the running max compares one float
+// per (x, order) and keeps each order's expectation term in a per-thread column
+// of G floats
+__host__ __device__ inline bool lifo_key_ok(const ProdParams &P) { return P.L == 1 && P.G <= 32; }
+
 // FIFO: the rest path is kept per thread if a column of dmax+1 indices fits in
 // 64 KiB of shared memory for a block of 128 threads
 __host__ __device__ inline bool fifo_shared_ok(const ProdParams &P) {

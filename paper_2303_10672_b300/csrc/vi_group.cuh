@@ -33,7 +33,10 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
     const int G = P.G;
     const int RB = kGroupThreads / lpr;                    // rests per block
     float *s_tab = (float *)smem_raw;
-    float *s_out = s_tab + ((kp.n_tables + 3) & ~3);       // PAIR: float2 per state
+    // LIFO, L = 1, shared sequences: per-thread column of gamma * C_a, one float per order
+    const bool key_lifo = PAIR && LIFO && !LPIPE && lifo_key_ok(P) && lifo_shared_ok(P);
+    float *s_kc = s_tab + ((kp.n_tables + 3) & ~3) + threadIdx.x;
+    float *s_out = s_tab + ((kp.n_tables + 3) & ~3) + (key_lifo ? G * kGroupThreads : 0);   // PAIR: float2 per state
     uint8_t *s_pol = (uint8_t *)(s_out + RB * G * (PAIR ? 2 : 1));
     load_tables<float>(s_tab, (const float *)kp.tables, kp.n_tables);
     const float *s_p = s_tab + P.off_p;
@@ -268,7 +271,15 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
             // lanes past the last x (x0 + xi >= G) compute values that are never stored;
             // their table reads stay inside the shared memory that follows the tables
             const float *rt = s_RT + R * G + x0;
-            if (PAIR && rt_common) {
+            if (PAIR && rt_common && LIFO) {
+                // L >= 2 and LIFO: neither the reward (added after the max) nor the
+                // expectation depends on x, so one comparison serves every x
+                float Bh, Bl;
+                action_base(gam, ref, R0, __fmul_rn(-c_o, (float)a), Bh, Bl);
+                const float ql = __fmaf_rn(gam, acc[0], Bl);
+                const float diff = __fadd_rn(__fsub_rn(Bh, bh[0]), __fsub_rn(ql, bl[0]));
+                take(0, diff > 0.f, Bh, ql, a);
+            } else if (PAIR && rt_common) {
                 // L >= 2: R does not depend on the order, so RT(x, R) is common to all
                 // orders and is added once per x after the max
                 float Bh, Bl;
@@ -278,6 +289,19 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                     const float ql = __fmaf_rn(gam, acc[xi], Bl);
                     const float diff = __fadd_rn(__fsub_rn(Bh, bh[xi]), __fsub_rn(ql, bl[xi]));
                     take(xi, diff > 0.f, Bh, ql, a);
+                }
+            } else if (PAIR && LIFO && key_lifo) {
+                // L = 1, LIFO, values measured from R0: the base of order a is exactly
+                // (-c_o a, gamma C_a).  Compare the single float -c_o a + gamma C_a + RT(x, R);
+                // the exact pair of the chosen order is rebuilt after the last order.
+                const float Bh = __fmul_rn(-c_o, (float)a);
+                const float Bl = __fmaf_rn(gam, acc[0], 0.f);
+                s_kc[a * kGroupThreads] = Bl;
+                const float ks = __fadd_rn(Bh, Bl);
+#pragma unroll
+                for (int xi = 0; xi < XW; ++xi) {
+                    const float key = __fadd_rn(ks, rt[xi]);
+                    take(xi, key > bh[xi], key, 0.f, a);
                 }
             } else if (PAIR) {
                 float Bh, Bl;
@@ -302,6 +326,27 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
             }
         }
         if (!PAIR && r == 0 && part == 0 && mode == MODE_SWEEP) st->c_next = bh[0];
+    }
+    if (PAIR && rt_common && LIFO && active) {
+#pragma unroll
+        for (int xi = 1; xi < XW; ++xi) {
+            bh[xi] = bh[0];
+            bl[xi] = bl[0];
+        }
+#pragma unroll
+        for (int i = 0; i < (XW + 3) / 4; ++i) argp[i] = (argp[0] & 0xFFu) * 0x01010101u;
+    }
+    if (key_lifo && active) {
+        // the exact pair of each x's chosen order: its base plus RT(x, Rrest + a)
+#pragma unroll
+        for (int xi = 0; xi < XW; ++xi) {
+            const int a = (int)((argp[xi >> 2] >> (8 * (xi & 3))) & 0xFFu);
+            float qh = __fmul_rn(-c_o, (float)a), ql = s_kc[a * kGroupThreads];
+            const int R = Rrest + a;
+            pair_add(qh, ql, s_RT[R * G + x0 + xi], s_RTlo[R * G + x0 + xi]);
+            bh[xi] = qh;
+            bl[xi] = ql;
+        }
     }
     if (PAIR && rt_common && active) {
         const float *rt = s_RT + Rrest * G + x0;
@@ -376,9 +421,11 @@ inline size_t group_smem(const KernelParams &kp, int rb, int vk) {
     const ProdParams &P = kp.p[0];
     const size_t vb = (vk == VK_PAIR) ? 8 : 4;
     size_t work = (size_t)rb * P.G * (vb + 1);   // output staging, shared with the columns
+    const size_t keyc =
+        (vk == VK_PAIR && kp.issuing && lifo_key_ok(P) && lifo_shared_ok(P)) ? (size_t)P.G * kGroupThreads * 4 : 0;
     if (kp.issuing && lifo_shared_ok(P)) work = std::max(work, (size_t)(P.G + P.dmax + 1) * kGroupThreads * 4);
     if (!kp.issuing && fifo_shared_ok(P)) work = std::max(work, (size_t)(P.dmax + 1) * kGroupThreads * 4);
-    return (size_t)((kp.n_tables + 3) & ~3) * 4 + work + 16;
+    return (size_t)((kp.n_tables + 3) & ~3) * 4 + keyc + work + 16;
 }
 
 template <int XW, int LIFO, int VK, int LPIPE>
