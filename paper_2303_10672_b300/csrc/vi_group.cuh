@@ -137,7 +137,52 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                     if (k0 + j < nH) colH[(k0 + j) * kGroupThreads] = v[j];
             }
         }
-        for (int a = 0; a < G; ++a) {
+        // LIFO, L = 1, shared sequences, one lane covering every x: the expectations of
+        // all orders at once, C[a] = sum_{d<=a} p_d T[a-d] + sum_{e>=1} p_{a+e} H[e]
+        // + tail[R] g_a(R), summed per order in the same order as the scalar loop
+        // below (terms past dmax carry zero mass), so the two agree bit for bit
+        const bool vec_lifo = key_lifo && lpr == 1 && Rrest >= 1;
+        if (vec_lifo) {
+            float T[XW], C[XW];
+#pragma unroll
+            for (int j = 0; j < XW; ++j) {
+                T[j] = (j < G) ? colT[j * kGroupThreads] : 0.f;
+                C[j] = 0.f;
+            }
+#pragma unroll
+            for (int d = 0; d < XW; ++d) {
+                const float pd = s_p[d];
+#pragma unroll
+                for (int a = d; a < XW; ++a) C[a] = fmaf(pd, T[a - d], C[a]);
+            }
+            const int elast = min(Rrest - 1, dmax);
+            for (int e = 1; e <= elast; ++e) {
+                const float h = colH[e * kGroupThreads];
+#pragma unroll
+                for (int a = 0; a < XW; ++a) C[a] = fmaf(s_p[a + e], h, C[a]);
+            }
+            const float hR = (Rrest <= dmax) ? colH[Rrest * kGroupThreads] : 0.f;
+            const float *s_tail = s_tab + P.off_tail + Rrest;
+#pragma unroll
+            for (int a = 0; a < XW; ++a)
+                if (Rrest + a <= dmax) C[a] = fmaf(s_tail[a], hR, C[a]);
+#pragma unroll
+            for (int a = 0; a < XW; ++a) {
+                if (a < G) {
+                    const float Bh = __fmul_rn(-c_o, (float)a);
+                    const float Bl = __fmaf_rn(gam, C[a], 0.f);
+                    s_kc[a * kGroupThreads] = Bl;
+                    const float ks = __fadd_rn(Bh, Bl);
+                    const float *rt = s_RT + (Rrest + a) * G;
+#pragma unroll
+                    for (int xi = 0; xi < XW; ++xi) {
+                        const float key = __fadd_rn(ks, rt[xi]);
+                        take(xi, key > bh[xi], key, 0.f, a);
+                    }
+                }
+            }
+        }
+        for (int a = 0; a < (vec_lifo ? 0 : G); ++a) {
             unsigned long long packed;
             int R;
             slots_for_action(P, ri, a, packed, R);
