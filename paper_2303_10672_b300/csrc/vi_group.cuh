@@ -454,8 +454,18 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
     if (mode != MODE_EXTRACT) block_reduce_and_finalize<float>(mx, mn, st, mode, n_blocks);
 }
 
+// Resident blocks per SM that the register allocation aims for: the register
+// estimate grows with the lane width (accumulators, best pair and order per x).
+// Measured on B300 for the 21-wide FIFO (L >= 2) and 11-wide LIFO (L = 1)
+// kernels: 4 and 8 blocks beat both the compiler's own choice and one block.
+__host__ __device__ constexpr int group_min_blocks(int xw, int lifo) {
+    const int regs = lifo ? 3 * xw + 31 : 4 * xw + 44;
+    const int b = 512 / regs;
+    return b < 1 ? 1 : (b > 8 ? 8 : b);
+}
+
 template <int XW, int LIFO, int VK, int LPIPE>
-__global__ void __launch_bounds__(kGroupThreads)
+__global__ void __launch_bounds__(kGroupThreads, group_min_blocks(XW, LIFO))
 sweep_group_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int lpr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     group_body<XW, LIFO, VK, LPIPE>(kp, blockIdx.x, gridDim.x, mode, vin_arg, vout_arg, pol_arg, lpr, smem_raw);
