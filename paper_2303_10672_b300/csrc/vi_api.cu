@@ -296,6 +296,30 @@ void fill_prod_params(ProdParams &P, int m, int L, int Q, int dmax, double c_o) 
     P.c_o = c_o;
 }
 
+vi_status build_single_product(const vi_problem_desc &d, KernelParams &kp, std::vector<float> &ftab,
+                               int &n_outcomes) {
+    vi_status s = validate_product(d.m[0], d.L[0], d.Q[0], d.cost[0], d.pmf[0], d.dmax[0]);
+    if (s != VI_OK) return s;
+    if (!(d.gamma > 0.0 && d.gamma <= 1.0)) return vi_fail(VI_EINVAL, "gamma must be in (0, 1]");
+    if (d.issuing != VI_FIFO && d.issuing != VI_LIFO) return vi_fail(VI_EINVAL, "issuing must be FIFO or LIFO");
+    memset(&kp, 0, sizeof(kp));
+    kp.n_products = 1;
+    kp.issuing = d.issuing;
+    kp.gamma = d.gamma;
+    std::vector<double> pm(d.pmf[0], d.pmf[0] + d.dmax[0] + 1);
+    std::vector<double> blob;
+    fill_prod_params(kp.p[0], d.m[0], d.L[0], d.Q[0], d.dmax[0], d.cost[0][0]);
+    fill_product_tables(kp.p[0], pm, d.issuing, d.cost[0], true, blob);
+    kp.nS = kp.p[0].nS;
+    kp.nA = kp.p[0].G;
+    kp.n_tables = (int)blob.size();
+    kp.tab_in_smem = ((size_t)kp.n_tables * 8 <= 160 * 1024) ? 1 : 0;
+    n_outcomes = d.dmax[0] + 1;
+    ftab.resize(blob.size());
+    for (size_t i = 0; i < blob.size(); ++i) ftab[i] = (float)blob[i];
+    return VI_OK;
+}
+
 static void destroy_internal(vi_problem *h);
 
 extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_handle *out) {

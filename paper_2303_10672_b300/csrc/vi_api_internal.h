@@ -49,3 +49,7 @@ vi_status vi_fail(vi_status s, const char *fmt, ...);
 // shared with the allocation-free entry point (vi_noalloc.cu)
 void fill_prod_params(vib::ProdParams &P, int m, int L, int Q, int dmax, double c_o);
 int heuristic_width(int G, int lifo);
+// the solve server's table builder: validates one product of d and fills the
+// kernel parameters (no device pointers) and the FP32 table blob
+vi_status build_single_product(const vi_problem_desc &d, vib::KernelParams &kp, std::vector<float> &ftab,
+                               int &n_outcomes);

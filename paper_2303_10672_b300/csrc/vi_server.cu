@@ -2,13 +2,19 @@
 //
 // A host worker thread owns one CUDA stream.  Requests wait in a FIFO queue and
 // are admitted, in order, while a slot is free and their device memory (value
-// ping-pong, policy, tables) fits the budget.  Every iteration of the worker runs
-// one batched sweep over all admitted instances -- one launch per lane-width
-// class, each block finding its instance from a prefix sum of block counts -- so
-// instances of different sizes advance together.  An instance whose stopping
-// test passed gets an extraction sweep in the next launch and is then retired:
-// its values (FP64) and policy are copied to host memory, its device memory is
-// released and queued requests can take its place.
+// ping-pong and policy) fits the budget.  Each iteration of the worker runs a few
+// batched sweeps over all admitted instances -- one launch per lane-width class
+// and sweep, each block finding its instance from a prefix sum of block counts --
+// so instances of different sizes advance together, then reads every slot's
+// status once.  An instance whose stopping test passed gets an extraction sweep
+// in the next iteration; its values are converted to FP64 on the device and a
+// retirement thread copies them (and the policy) to host memory on a second
+// stream and releases the buffers, while the worker carries on.
+//
+// Slots own their expectation tables, solve state and pinned upload staging for
+// the server's lifetime; value and policy buffers come from the stream-ordered
+// allocator, so admitting and retiring a request never synchronises the device.
+// Tables are built on the submitting thread.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,6 +40,9 @@ using namespace vib;
 
 namespace {
 
+constexpr int kSlotTabFloats = 16384;   // expectation-table capacity of a slot (64 KiB)
+constexpr int kSweepsPerCheck = 4;      // batched sweeps between two status reads
+
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -41,7 +50,9 @@ double now_s() {
 struct Request {
     uint64_t id = 0;
     vi_problem_desc desc;
-    std::vector<double> pmf;
+    KernelParams kp;               // built at submission (device pointers set at admission)
+    std::vector<float> ftab;       // FP32 expectation tables
+    int n_outcomes = 0;
     double tol = 1e-4;
     int max_iters = 0;
     size_t bytes = 0;              // device memory while admitted
@@ -58,14 +69,28 @@ struct Request {
 
 struct Slot {
     std::shared_ptr<Request> req;
-    vi_handle h = nullptr;
+    KernelParams kp;
     void *V = nullptr;             // float pairs
+    void *scratch = nullptr;       // ping-pong partner, then the FP64 result
     uint8_t *policy = nullptr;
     int mode = MODE_SWEEP;
     int xw = 0, lpr = 0;
     uint32_t blocks = 0;
     size_t smem = 0;
-    double updates = 0.0;          // nominal updates per sweep
+    // owned for the server's lifetime
+    SolveState *d_state = nullptr;
+    SolveState *h_state = nullptr;   // pinned
+    float *d_tab = nullptr;
+    float *h_tab = nullptr;          // pinned
+};
+
+struct RetireJob {
+    std::shared_ptr<Request> req;
+    void *V = nullptr, *scratch = nullptr;
+    uint8_t *policy = nullptr;
+    cudaEvent_t ready = nullptr;
+    uint32_t n = 0;
+    SlotStatus ss;
 };
 
 }  // namespace
@@ -73,20 +98,24 @@ struct Slot {
 struct vi_server_s {
     size_t budget = 0, used = 0;
     int max_slots = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;    // batched sweeps
+    cudaStream_t rstream = nullptr;   // retirement copies
     std::mutex mu;
     std::condition_variable cv;
     std::deque<std::shared_ptr<Request>> queue;
     std::map<uint64_t, std::shared_ptr<Request>> all;
     std::vector<Slot> slots;
-    std::thread worker;
-    bool stop = false;
+    std::thread worker, retirer;
+    std::deque<RetireJob> retire_q;
+    std::condition_variable retire_cv;
+    bool stop = false, retire_stop = false;
     uint64_t next_id = 1;
     vi_status fatal = VI_OK;
     char fatal_msg[256] = "";
     // batch descriptors (device) and their pinned host mirrors
     KernelParams *d_kps = nullptr, *h_kps = nullptr;
     int *d_modes = nullptr, *h_modes = nullptr;
+    int *d_modes_sweep = nullptr;     // MODE_SWEEP for every slot: the later sweeps of an iteration
     int *d_lprs = nullptr, *h_lprs = nullptr;
     uint32_t *d_bstart = nullptr, *h_bstart = nullptr;
     SolveState **d_sts = nullptr, **h_sts = nullptr;
@@ -101,78 +130,149 @@ static bool server_shape_ok(const vi_problem_desc &d) {
     return K >= 1 && d.Q[0] + 1 >= 2 && d.Q[0] + 1 <= 24;
 }
 
-// create the slot's problem, buffers and initial solve state (worker thread)
+static void set_fatal(vi_server_s *srv, const char *what, cudaError_t e) {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (srv->fatal == VI_OK) {
+        srv->fatal = VI_ECUDA;
+        snprintf(srv->fatal_msg, sizeof(srv->fatal_msg), "%s: %s", what, cudaGetErrorString(e));
+    }
+    srv->stop = true;
+    srv->cv.notify_all();
+}
+
+// admit a request into a free slot (worker thread; nothing here waits for the device)
 static vi_status slot_open(vi_server_s *srv, Slot &sl, std::shared_ptr<Request> req) {
     sl.req = req;
-    vi_problem_desc d = req->desc;
-    d.pmf[0] = req->pmf.data();
-    d.precision = VI_PREC_FP32;
-    d.stop_rule = VI_STOP_SPAN;
-    vi_status st = vi_problem_create_desc(&d, &sl.h);
-    if (st != VI_OK) return st;
-    const uint32_t n = sl.h->kp.nS;
+    sl.kp = req->kp;
+    const uint32_t n = sl.kp.nS;
+    memcpy(sl.h_tab, req->ftab.data(), req->ftab.size() * sizeof(float));
+    sl.kp.tables = sl.d_tab;
+    sl.kp.st = sl.d_state;
     cudaError_t e;
     if ((e = cudaMallocAsync(&sl.V, (size_t)n * 8, srv->stream)) != cudaSuccess ||
-        (e = cudaMallocAsync(&sl.h->d_scratch, (size_t)n * 8, srv->stream)) != cudaSuccess ||
+        (e = cudaMallocAsync(&sl.scratch, (size_t)n * 8, srv->stream)) != cudaSuccess ||
         (e = cudaMallocAsync((void **)&sl.policy, n, srv->stream)) != cudaSuccess)
         return vi_fail(VI_ENOMEM, "server slot allocation: %s", cudaGetErrorString(e));
-    SolveState *hs = sl.h->h_state;
+    SolveState *hs = sl.h_state;
     memset(hs, 0, sizeof(SolveState));
     hs->buf[0] = sl.V;
-    hs->buf[1] = sl.h->d_scratch;
+    hs->buf[1] = sl.scratch;
     hs->policy = sl.policy;
     hs->tol = req->tol;
-    hs->gamma = d.gamma;
+    hs->gamma = req->desc.gamma;
     hs->max_iters = req->max_iters;
     hs->stop_rule = VI_STOP_SPAN;
     hs->value_bytes = 8;
     hs->key_min = ~0ull;
-    if ((e = cudaMemcpyAsync(sl.h->d_state, hs, sizeof(SolveState), cudaMemcpyHostToDevice, srv->stream)) !=
-        cudaSuccess)
-        return vi_fail(VI_ECUDA, "server slot state: %s", cudaGetErrorString(e));
-    if ((e = launch_solve_init(sl.h->d_state, n, srv->stream)) != cudaSuccess)
-        return vi_fail(VI_ECUDA, "server slot init: %s", cudaGetErrorString(e));
-    // pinned host mirror is reused for the next state upload; wait until the copy is done
-    if ((e = cudaStreamSynchronize(srv->stream)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(sl.d_tab, sl.h_tab, req->ftab.size() * sizeof(float), cudaMemcpyHostToDevice,
+                             srv->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(sl.d_state, hs, sizeof(SolveState), cudaMemcpyHostToDevice, srv->stream)) !=
+            cudaSuccess ||
+        (e = launch_solve_init(sl.d_state, n, srv->stream)) != cudaSuccess)
         return vi_fail(VI_ECUDA, "server slot init: %s", cudaGetErrorString(e));
     sl.mode = req->max_iters > 0 ? MODE_SWEEP : MODE_EXTRACT;
-    sl.xw = batch_width(sl.h->kp.p[0].G);
-    batch_geometry(sl.h->kp, &sl.lpr, &sl.blocks, &sl.smem);
-    sl.updates = (double)n * (double)sl.h->kp.nA * (double)sl.h->n_outcomes;
+    sl.xw = batch_width(sl.kp.p[0].G);
+    batch_geometry(sl.kp, &sl.lpr, &sl.blocks, &sl.smem);
     return VI_OK;
 }
 
-static void slot_close(vi_server_s *srv, Slot &sl) {
+// give the slot's buffers back (stream ordered) and free the slot
+static void slot_release(vi_server_s *srv, Slot &sl) {
     if (sl.V) cudaFreeAsync(sl.V, srv->stream);
+    if (sl.scratch) cudaFreeAsync(sl.scratch, srv->stream);
     if (sl.policy) cudaFreeAsync(sl.policy, srv->stream);
-    if (sl.h) {
-        if (sl.h->d_scratch) {
-            cudaFreeAsync(sl.h->d_scratch, srv->stream);
-            sl.h->d_scratch = nullptr;
-        }
-        cudaStreamSynchronize(srv->stream);
-        vi_problem_destroy(sl.h);
-    }
-    sl = Slot();
+    sl.V = sl.scratch = nullptr;
+    sl.policy = nullptr;
+    sl.req.reset();
 }
 
-// copy the finished instance to host memory (FP64 values in the scratch buffer)
-static vi_status slot_retire(vi_server_s *srv, Slot &sl, const SlotStatus &ss) {
-    Request &rq = *sl.req;
-    const uint32_t n = sl.h->kp.nS;
-    rq.V.resize(n);
-    rq.policy.resize(n);
-    cudaError_t e;
-    if ((e = launch_to_fp64(sl.V, VK_PAIR, 0.0, (double *)sl.h->d_scratch, n, srv->stream)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(rq.V.data(), sl.h->d_scratch, (size_t)n * 8, cudaMemcpyDeviceToHost, srv->stream)) !=
-            cudaSuccess ||
-        (e = cudaMemcpyAsync(rq.policy.data(), sl.policy, n, cudaMemcpyDeviceToHost, srv->stream)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(srv->stream)) != cudaSuccess)
-        return vi_fail(VI_ECUDA, "server retire: %s", cudaGetErrorString(e));
-    rq.iters = ss.iter;
-    rq.crit = ss.crit;
-    rq.status = ss.converged ? VI_OK : VI_ENOTCONVERGED;
-    return VI_OK;
+static void finish(vi_server_s *srv, Request &rq, vi_status st) {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (st != VI_OK) rq.status = st;
+    rq.done = true;
+    rq.t_done = now_s();
+    srv->used -= rq.bytes;
+    srv->cv.notify_all();
+}
+
+// retirement thread: wait for a finished instance's FP64 conversion, copy the
+// values and the policy to host memory, release the buffers
+static void retire_loop(vi_server_s *srv) {
+    while (true) {
+        RetireJob job;
+        {
+            std::unique_lock<std::mutex> lk(srv->mu);
+            srv->retire_cv.wait(lk, [srv] { return srv->retire_stop || !srv->retire_q.empty(); });
+            if (srv->retire_q.empty()) break;   // stop requested and nothing left
+            job = srv->retire_q.front();
+            srv->retire_q.pop_front();
+        }
+        Request &rq = *job.req;
+        vi_status st = VI_OK;
+        rq.V.resize(job.n);
+        rq.policy.resize(job.n);
+        cudaError_t e;
+        if ((e = cudaStreamWaitEvent(srv->rstream, job.ready, 0)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(rq.V.data(), job.scratch, (size_t)job.n * 8, cudaMemcpyDeviceToHost,
+                                 srv->rstream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(rq.policy.data(), job.policy, job.n, cudaMemcpyDeviceToHost, srv->rstream)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(srv->rstream)) != cudaSuccess)
+            st = vi_fail(VI_ECUDA, "server retire: %s", cudaGetErrorString(e));
+        cudaFreeAsync(job.V, srv->rstream);
+        cudaFreeAsync(job.scratch, srv->rstream);
+        cudaFreeAsync(job.policy, srv->rstream);
+        cudaEventDestroy(job.ready);
+        rq.iters = job.ss.iter;
+        rq.crit = job.ss.crit;
+        rq.status = job.ss.converged ? VI_OK : VI_ENOTCONVERGED;
+        finish(srv, rq, st);
+    }
+}
+
+// one launch per lane-width class over the active slots; modes from the slots
+// (first sweep of an iteration) or MODE_SWEEP for all (the later ones)
+static cudaError_t launch_round(vi_server_s *srv, const std::vector<int> &act, bool first) {
+    int koff = 0, boff = 0;
+    for (int xw : {8, 12, 16, 21, 24}) {
+        const int kbase = koff, bbase = boff;
+        uint32_t total = 0;
+        size_t smem = 0;
+        for (int i : act) {
+            Slot &sl = srv->slots[i];
+            if (sl.xw != xw) continue;
+            if (first) {
+                srv->h_kps[koff] = sl.kp;
+                srv->h_modes[koff] = sl.mode;
+                srv->h_lprs[koff] = sl.lpr;
+                srv->h_bstart[boff] = total;
+            }
+            ++boff;
+            total += sl.blocks;
+            smem = std::max(smem, sl.smem);
+            ++koff;
+        }
+        const int n_cls = koff - kbase;
+        if (n_cls == 0) continue;
+        if (first) srv->h_bstart[boff] = total;
+        ++boff;
+        cudaError_t e;
+        if (first) {
+            if ((e = cudaMemcpyAsync(srv->d_kps + kbase, srv->h_kps + kbase, sizeof(KernelParams) * n_cls,
+                                     cudaMemcpyHostToDevice, srv->stream)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(srv->d_modes + kbase, srv->h_modes + kbase, sizeof(int) * n_cls,
+                                     cudaMemcpyHostToDevice, srv->stream)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(srv->d_lprs + kbase, srv->h_lprs + kbase, sizeof(int) * n_cls,
+                                     cudaMemcpyHostToDevice, srv->stream)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(srv->d_bstart + bbase, srv->h_bstart + bbase, sizeof(uint32_t) * (n_cls + 1),
+                                     cudaMemcpyHostToDevice, srv->stream)) != cudaSuccess)
+                return e;
+        }
+        e = launch_sweep_batch(xw, srv->d_kps + kbase, (first ? srv->d_modes : srv->d_modes_sweep) + kbase,
+                               srv->d_lprs + kbase, srv->d_bstart + bbase, n_cls, total, smem, srv->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 static void worker_loop(vi_server_s *srv) {
@@ -201,105 +301,79 @@ static void worker_loop(vi_server_s *srv) {
             auto it = std::find_if(srv->slots.begin(), srv->slots.end(), [](const Slot &s) { return !s.req; });
             vi_status st = slot_open(srv, *it, rq);
             if (st != VI_OK) {
-                std::lock_guard<std::mutex> lk(srv->mu);
-                rq->status = st;
-                rq->done = true;
-                rq->t_done = now_s();
-                srv->used -= rq->bytes;
-                slot_close(srv, *it);
-                srv->cv.notify_all();
+                slot_release(srv, *it);
+                finish(srv, *rq, st);
             }
         }
-        // one batched sweep (or extraction) for every active slot, per width class
         std::vector<int> act;
+        bool sweeping = false;
         for (int i = 0; i < cap; ++i)
-            if (srv->slots[i].req) act.push_back(i);
+            if (srv->slots[i].req) {
+                act.push_back(i);
+                sweeping |= (srv->slots[i].mode == MODE_SWEEP);
+            }
         if (act.empty()) continue;
-        int koff = 0, boff = 0;
-        bool failed = false;
-        for (int xw : {8, 12, 16, 21, 24}) {
-            const int kbase = koff, bbase = boff;
-            uint32_t total = 0;
-            size_t smem = 0;
-            for (int i : act) {
-                Slot &sl = srv->slots[i];
-                if (sl.xw != xw) continue;
-                srv->h_kps[koff] = sl.h->kp;
-                srv->h_modes[koff] = sl.mode;
-                srv->h_lprs[koff] = sl.lpr;
-                srv->h_bstart[boff++] = total;
-                total += sl.blocks;
-                smem = std::max(smem, sl.smem);
-                ++koff;
-            }
-            const int n_cls = koff - kbase;
-            if (n_cls == 0) continue;
-            srv->h_bstart[boff++] = total;
-            cudaMemcpyAsync(srv->d_kps + kbase, srv->h_kps + kbase, sizeof(KernelParams) * n_cls,
-                            cudaMemcpyHostToDevice, srv->stream);
-            cudaMemcpyAsync(srv->d_modes + kbase, srv->h_modes + kbase, sizeof(int) * n_cls,
-                            cudaMemcpyHostToDevice, srv->stream);
-            cudaMemcpyAsync(srv->d_lprs + kbase, srv->h_lprs + kbase, sizeof(int) * n_cls, cudaMemcpyHostToDevice,
-                            srv->stream);
-            cudaMemcpyAsync(srv->d_bstart + bbase, srv->h_bstart + bbase, sizeof(uint32_t) * (n_cls + 1),
-                            cudaMemcpyHostToDevice, srv->stream);
-            cudaError_t e = launch_sweep_batch(xw, srv->d_kps + kbase, srv->d_modes + kbase, srv->d_lprs + kbase,
-                                               srv->d_bstart + bbase, n_cls, total, smem, srv->stream);
-            if (e != cudaSuccess) {
-                std::lock_guard<std::mutex> lk(srv->mu);
-                srv->fatal = VI_ECUDA;
-                snprintf(srv->fatal_msg, sizeof(srv->fatal_msg), "batched sweep: %s", cudaGetErrorString(e));
-                srv->stop = true;
-                failed = true;
-                break;
-            }
-        }
-        if (failed) break;
-        // statuses of every active slot
-        for (size_t j = 0; j < act.size(); ++j) srv->h_sts[j] = srv->slots[act[j]].h->d_state;
-        cudaMemcpyAsync(srv->d_sts, srv->h_sts, sizeof(SolveState *) * act.size(), cudaMemcpyHostToDevice,
-                        srv->stream);
-        launch_gather_status(srv->d_sts, (int)act.size(), srv->d_status, srv->stream);
-        cudaMemcpyAsync(srv->h_status, srv->d_status, sizeof(SlotStatus) * act.size(), cudaMemcpyDeviceToHost,
-                        srv->stream);
-        cudaError_t e = cudaStreamSynchronize(srv->stream);
+        // a few sweeps back to back: an instance that stopped turns the later ones into no-ops
+        const int rounds = sweeping ? kSweepsPerCheck : 1;
+        cudaError_t e = cudaSuccess;
+        for (int rd = 0; rd < rounds && e == cudaSuccess; ++rd) e = launch_round(srv, act, rd == 0);
         if (e != cudaSuccess) {
-            std::lock_guard<std::mutex> lk(srv->mu);
-            srv->fatal = VI_ECUDA;
-            snprintf(srv->fatal_msg, sizeof(srv->fatal_msg), "server stream: %s", cudaGetErrorString(e));
-            srv->stop = true;
-            srv->cv.notify_all();
+            set_fatal(srv, "batched sweep", e);
+            break;
+        }
+        for (size_t j = 0; j < act.size(); ++j) srv->h_sts[j] = srv->slots[act[j]].d_state;
+        if ((e = cudaMemcpyAsync(srv->d_sts, srv->h_sts, sizeof(SolveState *) * act.size(), cudaMemcpyHostToDevice,
+                                 srv->stream)) != cudaSuccess ||
+            (e = launch_gather_status(srv->d_sts, (int)act.size(), srv->d_status, srv->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(srv->h_status, srv->d_status, sizeof(SlotStatus) * act.size(),
+                                 cudaMemcpyDeviceToHost, srv->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(srv->stream)) != cudaSuccess) {
+            set_fatal(srv, "server stream", e);
             break;
         }
         for (size_t j = 0; j < act.size(); ++j) {
             Slot &sl = srv->slots[act[j]];
             const SlotStatus ss = srv->h_status[j];
             if (sl.mode == MODE_EXTRACT) {
-                vi_status st = slot_retire(srv, sl, ss);
-                auto rq = sl.req;
-                slot_close(srv, sl);
+                // extraction done: FP64 values into the scratch buffer, then hand over
+                RetireJob job;
+                job.req = sl.req;
+                job.V = sl.V;
+                job.scratch = sl.scratch;
+                job.policy = sl.policy;
+                job.n = sl.kp.nS;
+                job.ss = ss;
+                if ((e = launch_to_fp64(sl.V, VK_PAIR, 0.0, (double *)sl.scratch, job.n, srv->stream)) !=
+                        cudaSuccess ||
+                    (e = cudaEventCreateWithFlags(&job.ready, cudaEventDisableTiming)) != cudaSuccess ||
+                    (e = cudaEventRecord(job.ready, srv->stream)) != cudaSuccess) {
+                    set_fatal(srv, "server retire", e);
+                    break;
+                }
+                sl.V = sl.scratch = nullptr;
+                sl.policy = nullptr;
+                sl.req.reset();
                 std::lock_guard<std::mutex> lk(srv->mu);
-                if (st != VI_OK) rq->status = st;
-                rq->done = true;
-                rq->t_done = now_s();
-                srv->used -= rq->bytes;
-                srv->cv.notify_all();
+                srv->retire_q.push_back(job);
+                srv->retire_cv.notify_one();
             } else if (!ss.keep_going) {
                 sl.mode = MODE_EXTRACT;
             }
         }
+        if (e != cudaSuccess) break;
     }
     // cancel whatever is left
-    std::lock_guard<std::mutex> lk(srv->mu);
     for (auto &sl : srv->slots)
         if (sl.req) {
-            sl.req->status = VI_ECANCELLED;
-            sl.req->done = true;
-            slot_close(srv, sl);
+            auto rq = sl.req;
+            slot_release(srv, sl);
+            finish(srv, *rq, VI_ECANCELLED);
         }
-    for (auto &q : srv->queue) {
-        q->status = VI_ECANCELLED;
-        q->done = true;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    for (auto &rq : srv->queue) {
+        rq->status = VI_ECANCELLED;
+        rq->done = true;
+        rq->t_done = now_s();
     }
     srv->queue.clear();
     srv->cv.notify_all();
@@ -318,9 +392,11 @@ extern "C" vi_status vi_server_create(size_t mem_budget_bytes, int max_slots, vo
     const int n = max_slots + 8;   // one extra block_start entry per width class
     cudaError_t e;
     if ((e = cudaStreamCreateWithFlags(&srv->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&srv->rstream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaMalloc(&srv->d_kps, sizeof(KernelParams) * n)) != cudaSuccess ||
         (e = cudaMallocHost(&srv->h_kps, sizeof(KernelParams) * n)) != cudaSuccess ||
         (e = cudaMalloc(&srv->d_modes, sizeof(int) * n)) != cudaSuccess ||
+        (e = cudaMalloc(&srv->d_modes_sweep, sizeof(int) * n)) != cudaSuccess ||
         (e = cudaMallocHost(&srv->h_modes, sizeof(int) * n)) != cudaSuccess ||
         (e = cudaMalloc(&srv->d_lprs, sizeof(int) * n)) != cudaSuccess ||
         (e = cudaMallocHost(&srv->h_lprs, sizeof(int) * n)) != cudaSuccess ||
@@ -334,12 +410,33 @@ extern "C" vi_status vi_server_create(size_t mem_budget_bytes, int max_slots, vo
         return vi_fail(e == cudaErrorMemoryAllocation ? VI_ENOMEM : VI_ECUDA, "server setup: %s",
                        cudaGetErrorString(e));
     }
-    (void)stream;   // the server keeps its own stream so that its host loop never blocks the caller's
+    for (auto &sl : srv->slots)
+        if ((e = cudaMalloc(&sl.d_state, sizeof(SolveState))) != cudaSuccess ||
+            (e = cudaMallocHost(&sl.h_state, sizeof(SolveState))) != cudaSuccess ||
+            (e = cudaMalloc(&sl.d_tab, sizeof(float) * kSlotTabFloats)) != cudaSuccess ||
+            (e = cudaMallocHost(&sl.h_tab, sizeof(float) * kSlotTabFloats)) != cudaSuccess) {
+            vi_server_destroy(srv);
+            return vi_fail(e == cudaErrorMemoryAllocation ? VI_ENOMEM : VI_ECUDA, "server slots: %s",
+                           cudaGetErrorString(e));
+        }
+    {
+        std::vector<int> sweep(n, MODE_SWEEP);
+        if ((e = cudaMemcpy(srv->d_modes_sweep, sweep.data(), sizeof(int) * n, cudaMemcpyHostToDevice)) !=
+            cudaSuccess) {
+            vi_server_destroy(srv);
+            return vi_fail(VI_ECUDA, "server setup: %s", cudaGetErrorString(e));
+        }
+    }
+    (void)stream;   // the server keeps its own streams so that its host loops never block the caller's
     int dev = 0;
     cudaGetDevice(&dev);
     srv->worker = std::thread([srv, dev]() {
         cudaSetDevice(dev);
         worker_loop(srv);
+    });
+    srv->retirer = std::thread([srv, dev]() {
+        cudaSetDevice(dev);
+        retire_loop(srv);
     });
     *out = srv;
     return VI_OK;
@@ -352,43 +449,29 @@ extern "C" vi_status vi_server_submit(vi_server srv, const vi_problem_desc *desc
         return vi_fail(VI_EINVAL, "the server takes single-product instances with at least one state digit "
                                   "and 2 <= Q+1 <= 24");
     if (!(tol >= 0.0) || max_iters < 0) return vi_fail(VI_EINVAL, "need tol >= 0 and max_iters >= 0");
-    // validate everything vi_problem_create_desc would check, on the host, now
-    vi_problem_desc d = *desc;
-    d.precision = VI_PREC_FP32;
-    d.stop_rule = VI_STOP_SPAN;
-    {
-        const int K = (d.m[0] - 1) + (d.L[0] - 1);
-        double ns = 1.0;
-        for (int k = 0; k < K; ++k) ns *= (double)(d.Q[0] + 1);
-        if (ns >= 4294967296.0) return vi_fail(VI_EINVAL, "|S| does not fit 32 bits");
-        if (!d.pmf[0] || d.dmax[0] < 0 || d.dmax[0] > kMaxDmax) return vi_fail(VI_EINVAL, "bad pmf");
-        double s = 0.0;
-        for (int i = 0; i <= d.dmax[0]; ++i) {
-            if (!(d.pmf[0][i] >= 0.0)) return vi_fail(VI_EINVAL, "pmf entries must be >= 0");
-            s += d.pmf[0][i];
-        }
-        if (fabs(s - 1.0) > 1e-9) return vi_fail(VI_EINVAL, "pmf does not sum to 1");
-        for (int j = 0; j < 5; ++j)
-            if (!(d.cost[0][j] >= 0.0)) return vi_fail(VI_EINVAL, "costs must be >= 0");
-        if (!(d.gamma > 0.0 && d.gamma <= 1.0)) return vi_fail(VI_EINVAL, "gamma must be in (0, 1]");
-        if (d.issuing != VI_FIFO && d.issuing != VI_LIFO) return vi_fail(VI_EINVAL, "bad issuing rule");
-        auto rq = std::make_shared<Request>();
-        rq->desc = d;
-        rq->pmf.assign(d.pmf[0], d.pmf[0] + d.dmax[0] + 1);
-        rq->tol = tol;
-        rq->max_iters = max_iters;
-        rq->n_states = (uint64_t)ns;
-        rq->bytes = request_bytes(rq->n_states);
-        rq->t_submit = now_s();
-        std::lock_guard<std::mutex> lk(srv->mu);
-        if (srv->fatal != VI_OK) return vi_fail(srv->fatal, "server stopped: %s", srv->fatal_msg);
-        if (rq->bytes > srv->budget) return vi_fail(VI_EBUSY, "request needs %zu bytes, budget %zu", rq->bytes, srv->budget);
-        rq->id = srv->next_id++;
-        srv->all[rq->id] = rq;
-        srv->queue.push_back(rq);
-        *request_id = rq->id;
-        srv->cv.notify_all();
-    }
+    auto rq = std::make_shared<Request>();
+    rq->desc = *desc;
+    rq->desc.precision = VI_PREC_FP32;
+    rq->desc.stop_rule = VI_STOP_SPAN;
+    vi_status st = build_single_product(rq->desc, rq->kp, rq->ftab, rq->n_outcomes);
+    if (st != VI_OK) return st;
+    if ((int)rq->ftab.size() > kSlotTabFloats)
+        return vi_fail(VI_EINVAL, "expectation tables of %zu entries exceed a slot's %d", rq->ftab.size(),
+                       kSlotTabFloats);
+    rq->desc.pmf[0] = nullptr;   // the caller's pmf is not kept
+    rq->tol = tol;
+    rq->max_iters = max_iters;
+    rq->n_states = rq->kp.nS;
+    rq->bytes = request_bytes(rq->n_states);
+    rq->t_submit = now_s();
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (srv->fatal != VI_OK) return vi_fail(srv->fatal, "server stopped: %s", srv->fatal_msg);
+    if (rq->bytes > srv->budget) return vi_fail(VI_EBUSY, "request needs %zu bytes, budget %zu", rq->bytes, srv->budget);
+    rq->id = srv->next_id++;
+    srv->all[rq->id] = rq;
+    srv->queue.push_back(rq);
+    *request_id = rq->id;
+    srv->cv.notify_all();
     return VI_OK;
 }
 
@@ -428,10 +511,24 @@ extern "C" vi_status vi_server_destroy(vi_server srv) {
         srv->cv.notify_all();
     }
     if (srv->worker.joinable()) srv->worker.join();
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->retire_stop = true;
+        srv->retire_cv.notify_all();
+    }
+    if (srv->retirer.joinable()) srv->retirer.join();
     if (srv->stream) cudaStreamSynchronize(srv->stream);
+    if (srv->rstream) cudaStreamSynchronize(srv->rstream);
+    for (auto &sl : srv->slots) {
+        if (sl.d_state) cudaFree(sl.d_state);
+        if (sl.h_state) cudaFreeHost(sl.h_state);
+        if (sl.d_tab) cudaFree(sl.d_tab);
+        if (sl.h_tab) cudaFreeHost(sl.h_tab);
+    }
     cudaFree(srv->d_kps);
     cudaFreeHost(srv->h_kps);
     cudaFree(srv->d_modes);
+    cudaFree(srv->d_modes_sweep);
     cudaFreeHost(srv->h_modes);
     cudaFree(srv->d_lprs);
     cudaFreeHost(srv->h_lprs);
@@ -442,6 +539,7 @@ extern "C" vi_status vi_server_destroy(vi_server srv) {
     cudaFree(srv->d_status);
     cudaFreeHost(srv->h_status);
     if (srv->stream) cudaStreamDestroy(srv->stream);
+    if (srv->rstream) cudaStreamDestroy(srv->rstream);
     delete srv;
     return VI_OK;
 }
