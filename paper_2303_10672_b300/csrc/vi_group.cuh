@@ -35,11 +35,22 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
     float *s_tab = (float *)smem_raw;
     // LIFO, L = 1, shared sequences: per-thread column of gamma * C_a, one float per order
     const bool key_lifo = PAIR && LIFO && !LPIPE && lifo_key_ok(P) && lifo_shared_ok(P);
-    float *s_kc = s_tab + ((kp.n_tables + 3) & ~3) + threadIdx.x;
-    float *s_out = s_tab + ((kp.n_tables + 3) & ~3) + (key_lifo ? G * kGroupThreads : 0);   // PAIR: float2 per state
+    // FIFO: four copies of the pmf shifted by 0..3, so that every probability window
+    // starts on a 16-byte boundary in one of them
+    const int pn4 = (P.pn + 3) & ~3;
+    float *s_pc = s_tab + ((kp.n_tables + 3) & ~3);
+    float *s_kc = s_pc + (LIFO ? 0 : 4 * pn4) + threadIdx.x;
+    float *s_out = s_pc + (LIFO ? 0 : 4 * pn4) + (key_lifo ? G * kGroupThreads : 0);   // PAIR: float2 per state
     uint8_t *s_pol = (uint8_t *)(s_out + RB * G * (PAIR ? 2 : 1));
     load_tables<float>(s_tab, (const float *)kp.tables, kp.n_tables);
     const float *s_p = s_tab + P.off_p;
+    if (!LIFO) {
+        for (int i = threadIdx.x; i < 4 * pn4; i += kGroupThreads) {
+            const int o = i / pn4, j = i - o * pn4;
+            s_pc[i] = (j + o < P.pn) ? s_p[j + o] : 0.f;
+        }
+        __syncthreads();
+    }
     const float *s_RT = s_tab + P.off_RT;
     const float *s_RTlo = s_tab + P.off_RTlo;
 
@@ -233,7 +244,9 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                     return __ldg(V1 + i);
                 };
                 const int kend = min(R - 1, dmax - x0);   // last k carrying mass for some x of this lane
-                const float *s_px = s_p + x0;
+                // window of chunk k0 (k0 = 1 mod 4): p[x0 + k0 + i] = copy_o[x0 + k0 - o + i]
+                const int po = (x0 + 1) & 3;
+                const float *s_px = s_pc + po * pn4 + (x0 + 1 - po);   // + (k0 - 1) is a multiple of 4
                 for (int k0 = 1; k0 <= kend; k0 += KW) {
                     uint32_t idx[KW];
 #pragma unroll
@@ -249,9 +262,17 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
 #pragma unroll
                         for (int j = 0; j < KW; ++j) g[j] = (k0 + j <= kend) ? __ldg(V1 + idx[j]) : 0.f;
                     }
-                    float pw[XW + KW - 1];
+                    constexpr int NW4 = (XW + KW - 1 + 3) / 4;
+                    float pw[4 * NW4];
+                    const float4 *pw4 = (const float4 *)(s_px + (k0 - 1));
 #pragma unroll
-                    for (int i = 0; i < XW + KW - 1; ++i) pw[i] = s_px[k0 + i];
+                    for (int t = 0; t < NW4; ++t) {
+                        const float4 v = pw4[t];
+                        pw[4 * t] = v.x;
+                        pw[4 * t + 1] = v.y;
+                        pw[4 * t + 2] = v.z;
+                        pw[4 * t + 3] = v.w;
+                    }
 #pragma unroll
                     for (int q = 0; q < NG; ++q) {
                         if (q == 0 || x0 + q * GS + k0 <= dmax) {
@@ -480,7 +501,8 @@ inline size_t group_smem(const KernelParams &kp, int rb, int vk) {
         (vk == VK_PAIR && kp.issuing && lifo_key_ok(P) && lifo_shared_ok(P)) ? (size_t)P.G * kGroupThreads * 4 : 0;
     if (kp.issuing && lifo_shared_ok(P)) work = std::max(work, (size_t)(P.G + P.dmax + 1) * kGroupThreads * 4);
     if (!kp.issuing && fifo_shared_ok(P)) work = std::max(work, (size_t)(P.dmax + 1) * kGroupThreads * 4);
-    return (size_t)((kp.n_tables + 3) & ~3) * 4 + keyc + work + 16;
+    const size_t pcopies = kp.issuing ? 0 : (size_t)4 * ((P.pn + 3) & ~3) * 4;
+    return (size_t)((kp.n_tables + 3) & ~3) * 4 + pcopies + keyc + work + 16;
 }
 
 template <int XW, int LIFO, int VK, int LPIPE>
