@@ -111,7 +111,8 @@ __device__ __forceinline__ uint32_t umma_off(int row, int col, int nkc) {
 struct TcLayout {
     int kpad, nkc, rpt, rows, pn_pad;
     uint32_t planeA, planeB;
-    uint32_t offB, offP, offPath, offQ, offBh, offRef, offR0, offR, offDig, offMbar, offTmem, total;
+    int nag, nkd, n_items;
+    uint32_t offB, offP, offPath, offQ, offBh, offRef, offR0, offR, offDig, offItems, offMbar, offTmem, total;
 };
 
 __host__ __device__ inline TcLayout tc_layout(const ProdParams &P) {
@@ -143,6 +144,11 @@ __host__ __device__ inline TcLayout tc_layout(const ProdParams &P) {
     o += (uint32_t)L.rpt * 4;
     L.offDig = o;
     o += (uint32_t)L.rpt * kMaxDigits * 4;
+    L.nag = (P.G + kTcAG - 1) / kTcAG;
+    L.nkd = (P.dmax + 7) / 8;
+    L.n_items = L.rpt * L.nag * L.nkd;
+    L.offItems = o;
+    o += (uint32_t)L.n_items * 4;
     o = (o + 7) & ~7u;
     L.offMbar = o;
     o += 8;
@@ -222,12 +228,26 @@ __global__ void __launch_bounds__(kTcThreads) sweep_tc_kernel(KernelParams kp, i
     const uint32_t idesc = umma_idesc_bf16(kTcRows, kTcCols);
     const uint32_t sbo = (uint32_t)nkc * 128u;
 
+    // staging work items (rest, group of kTcAG orders, chunk of 8 demands), packed once
+    uint32_t *s_items = (uint32_t *)(smem + Lo.offItems);
+    for (int it = tid; it < Lo.n_items; it += kTcThreads) {
+        const int jj = it % rpt, rest = it / rpt;
+        const int ag = rest % Lo.nag, kc = rest / Lo.nag;
+        const int a0 = ag * kTcAG, a1 = min(G, a0 + kTcAG);
+        s_items[it] = (uint32_t)jj | ((uint32_t)a0 << 8) | ((uint32_t)a1 << 16) | ((uint32_t)kc << 24);
+    }
+    __syncthreads();
+    // fixed roles of this thread: accumulator row (order ra, rest rj) and output state (rest oj, slot ox)
+    const int ra = tid / rpt, rj = tid - ra * rpt;
+    const int oj = tid / G, ox = tid - oj * G;
+    const bool row_ok = tid < rows;
+
     float mx = -INFINITY, mn = INFINITY;
     uint32_t parity = 0;
     bool fault = false;
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const uint32_t r0 = tile * (uint32_t)rpt;
-        // ---- rest digits and stock
+        // ---- rest digits and stock (-1: past the last rest)
         if (tid < rpt) {
             const uint32_t r = r0 + tid;
             int R = 0;
@@ -242,69 +262,70 @@ __global__ void __launch_bounds__(kTcThreads) sweep_tc_kernel(KernelParams kp, i
             s_R[tid] = (r < nR) ? R : -1;
         }
         __syncthreads();
-        // ---- FIFO demand path of each rest: next-state index after e units (the order on top excluded)
-        for (int i = tid; i < rpt * plen; i += kTcThreads) {
-            const int j = i / plen, e = i - j * plen;
+        // ---- FIFO demand path of each rest: next-state index after e units (the order on top
+        // excluded); a rest past the end gets index 0 so that its (unused) row reads valid memory
+        for (int j = 0; j < rpt; ++j) {
             const int R = s_R[j];
-            if (R < 0 || e > min(R, dmax)) continue;
-            uint32_t idx = r0 + (uint32_t)j, w = 1u;
-            int left = e;
-            for (int s = 0; s < P.n_rest_slots && left > 0; ++s) {
-                const int c = min(left, s_dig[j * kMaxDigits + s]);
-                idx -= (uint32_t)c * w;
-                left -= c;
-                w *= (uint32_t)G;
-            }
-            s_path[i] = idx;
-        }
-        __syncthreads();
-        // ---- references g_a(0) of every row (order a, rest j): row t = a * rpt + j
-        const int a = tid / rpt, j = tid - a * rpt;
-        const bool row_on = tid < rows && s_R[j] >= 0;
-        if (tid < rows) {
-            const float2 ref = row_on ? __ldg(V2 + s_path[j * plen] + (uint32_t)a * P.w_top) : make_float2(0.f, 0.f);
-            s_ref[tid] = ref;
-            if (a == 0) s_r0[j] = ref;
-        }
-        __syncthreads();
-        // ---- staging: item = (rest j, 8 demands k, group of kTcAG orders); the path indices of the
-        // chunk are shared by the orders, whose next states differ by a * w_top
-        {
-            const int nkd = (dmax + 7) / 8;        // chunks holding some k <= dmax
-            const int nag = (G + kTcAG - 1) / kTcAG;
-            const int n_items = rpt * nag * nkd;
-            for (int it = tid; it < n_items; it += kTcThreads) {
-                const int jj = it % rpt;
-                const int rest_i = it / rpt;
-                const int ag = rest_i % nag, kc = rest_i / nag;
-                const int R = s_R[jj];
-                const int ecap = min(max(R, 0), dmax);
-                uint32_t idx[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) idx[i] = s_path[jj * plen + min(kc * 8 + i + 1, ecap)];
-                const int a_end = min(G, (ag + 1) * kTcAG);
-                for (int aa = ag * kTcAG; aa < a_end; ++aa) {
-                    const int row = aa * rpt + jj;
-                    const float2 ref = s_ref[row];
-                    const float2 *Va = V2 + (size_t)aa * P.w_top;
-                    float2 raw[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) raw[i] = (R >= 0 && kc * 8 + i + 1 <= dmax) ? __ldg(Va + idx[i]) : ref;
-                    uint32_t p1[4], p2[4], p3[4];
-#pragma unroll
-                    for (int i = 0; i < 8; i += 2) {
-                        uint32_t a1, a2, a3, b1, b2, b3;
-                        split3(pair_diff(raw[i], ref), a1, a2, a3);
-                        split3(pair_diff(raw[i + 1], ref), b1, b2, b3);
-                        p1[i / 2] = __byte_perm(a1, b1, 0x7632);
-                        p2[i / 2] = __byte_perm(a2, b2, 0x7632);
-                        p3[i / 2] = __byte_perm(a3, b3, 0x7632);
-                    }
-                    const uint32_t off = umma_off(row, kc * 8, nkc);
-                    *(uint4 *)(sA + off) = make_uint4(p1[0], p1[1], p1[2], p1[3]);
-                    *(uint4 *)(sA + Lo.planeA + off) = make_uint4(p2[0], p2[1], p2[2], p2[3]);
-                    *(uint4 *)(sA + 2 * Lo.planeA + off) = make_uint4(p3[0], p3[1], p3[2], p3[3]);
+            const int ecap = min(max(R, 0), dmax);
+            for (int e = tid; e <= ecap; e += kTcThreads) {
+                uint32_t idx = (R < 0) ? 0u : r0 + (uint32_t)j, w = 1u;
+                int left = (R < 0) ? 0 : e;
+                for (int sl = 0; sl < P.n_rest_slots && left > 0; ++sl) {
+                    const int c = min(left, s_dig[j * kMaxDigits + sl]);
+                    idx -= (uint32_t)c * w;
+                    left -= c;
+                    w *= (uint32_t)G;
                 }
+                s_path[j * plen + e] = idx;
+            }
+        }
+        __syncthreads();
+        // ---- staging: differences g_a(min(k, R)) - g_a(0), split into three bf16 planes.
+        // Columns past dmax meet zero probabilities: any finite value will do there.
+        for (int it = tid; it < Lo.n_items; it += kTcThreads) {
+            const uint32_t code = s_items[it];
+            const int jj = (int)(code & 0xFFu), a0 = (int)((code >> 8) & 0xFFu), a1 = (int)((code >> 16) & 0xFFu);
+            const int kc = (int)(code >> 24);
+            const int ecap = min(max(s_R[jj], 0), dmax);
+            const uint32_t *path = s_path + jj * plen;
+            uint32_t idx[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) idx[i] = path[min(kc * 8 + i + 1, ecap)];
+            const bool on = s_R[jj] >= 0;
+            // every gather of the item first (kTcAG orders x 8 demands and the references),
+            // so that their latencies overlap; orders past a1 repeat the last one
+            float2 ref[kTcAG], raw[kTcAG][8];
+#pragma unroll
+            for (int u = 0; u < kTcAG; ++u) {
+                const int aa = min(a0 + u, a1 - 1);
+                const float2 *Va = V2 + (size_t)aa * P.w_top;
+                ref[u] = on ? __ldg(Va + path[0]) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) raw[u][i] = __ldg(Va + idx[i]);
+            }
+#pragma unroll
+            for (int u = 0; u < kTcAG; ++u) {
+                const int aa = a0 + u;
+                if (aa >= a1) break;
+                const int row = aa * rpt + jj;
+                if (kc == 0) {
+                    s_ref[row] = ref[u];
+                    if (aa == 0) s_r0[jj] = ref[u];
+                }
+                uint32_t p1[4], p2[4], p3[4];
+#pragma unroll
+                for (int i = 0; i < 8; i += 2) {
+                    uint32_t a1b, a2b, a3b, b1b, b2b, b3b;
+                    split3(pair_diff(raw[u][i], ref[u]), a1b, a2b, a3b);
+                    split3(pair_diff(raw[u][i + 1], ref[u]), b1b, b2b, b3b);
+                    p1[i / 2] = __byte_perm(a1b, b1b, 0x7632);
+                    p2[i / 2] = __byte_perm(a2b, b2b, 0x7632);
+                    p3[i / 2] = __byte_perm(a3b, b3b, 0x7632);
+                }
+                const uint32_t off = umma_off(row, kc * 8, nkc);
+                *(uint4 *)(sA + off) = make_uint4(p1[0], p1[1], p1[2], p1[3]);
+                *(uint4 *)(sA + Lo.planeA + off) = make_uint4(p2[0], p2[1], p2[2], p2[3]);
+                *(uint4 *)(sA + 2 * Lo.planeA + off) = make_uint4(p3[0], p3[1], p3[2], p3[3]);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -336,27 +357,26 @@ __global__ void __launch_bounds__(kTcThreads) sweep_tc_kernel(KernelParams kp, i
             break;
         }
         tc_fence_after();
-        // ---- accumulator row -> gamma * C + base, transposed into (rest, x, order)
+        // ---- accumulator row (ra, rj) -> gamma * C + base, transposed into (rest, x, order)
         float c[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), c);
-        if (row_on) {
+        if (row_ok && s_R[rj] >= 0) {
             float Bh, Bl;
-            action_base(gam, s_ref[tid], s_r0[j], __fmul_rn(-c_o, (float)a), Bh, Bl);
-            s_bh[j * G + a] = Bh;
-            float *q = s_q + (j * G) * G + a;
+            action_base(gam, s_ref[tid], s_r0[rj], __fmul_rn(-c_o, (float)ra), Bh, Bl);
+            s_bh[rj * G + ra] = Bh;
+            float *q = s_q + (rj * G) * G + ra;
 #pragma unroll
             for (int x = 0; x < kTcCols; ++x)
                 if (x < G) q[x * G] = __fmaf_rn(gam, c[x], Bl);
         }
         tc_fence_before();
         __syncthreads();
-        // ---- first argmax over orders per state (j, x); the reward does not depend on the order (L >= 2)
-        if (tid < rows) {
-            const int jj = tid / G, x = tid - jj * G;
-            const int R = s_R[jj];
+        // ---- first argmax over orders per state (oj, ox); the reward does not depend on the order (L >= 2)
+        if (row_ok) {
+            const int R = s_R[oj];
             if (R >= 0) {
-                const float *q = s_q + (jj * G + x) * G;
-                const float *bhv = s_bh + jj * G;
+                const float *q = s_q + (oj * G + ox) * G;
+                const float *bhv = s_bh + oj * G;
                 float bh = -INFINITY, bl = 0.f;
                 int arg = 0;
                 for (int aa = 0; aa < G; ++aa) {
@@ -367,14 +387,14 @@ __global__ void __launch_bounds__(kTcThreads) sweep_tc_kernel(KernelParams kp, i
                     bl = up ? l : bl;
                     arg = up ? aa : arg;
                 }
-                pair_add(bh, bl, __ldg(tab + P.off_RT + R * G + x), __ldg(tab + P.off_RTlo + R * G + x));
-                const uint32_t s = (r0 + (uint32_t)jj) * (uint32_t)G + (uint32_t)x;
+                pair_add(bh, bl, __ldg(tab + P.off_RT + R * G + ox), __ldg(tab + P.off_RTlo + R * G + ox));
+                const uint32_t s = (r0 + (uint32_t)oj) * (uint32_t)G + (uint32_t)ox;
                 const float2 *vin2 = (const float2 *)B.vin;
                 float2 *vout2 = (float2 *)B.vout;
                 if (mode == MODE_EXTRACT) {
                     if (vout2) vout2[s] = vin2[s];
                 } else {
-                    const float2 vnew = pair_finish(gam, s_r0[jj], bh, bl);
+                    const float2 vnew = pair_finish(gam, s_r0[oj], bh, bl);
                     const float2 vold = vin2[s];
                     vout2[s] = vnew;
                     const float dlt = pair_diff(vnew, vold);
