@@ -210,8 +210,9 @@ def algorithmic_work(inst) -> dict:
 # DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu captures
 # summarised in profiles/sweep_group_*.md; an entry is dropped when that kernel changes
 NCU_TRAFFIC = {
-    ("cfg2_m5L2Q20_nb_fifo", "sweep_group_kernel (lane width 21)"): 34_302_208,
-    ("cfg4_m8L1Q10_lifo", "sweep_group_kernel (lane width 11)"): 394_315_520,
+    ("cfg2_m5L2Q20_nb_fifo", "sweep_group_kernel (lane width 21)"): 34_021_632,
+    ("cfg4_m8L1Q10_lifo", "sweep_group_kernel (lane width 11)"): 392_604_160,
+    ("cfg2_m5L2Q20_nb_fifo", "sweep_tc_kernel"): 34_120_448,
 }
 
 
@@ -319,6 +320,25 @@ def run_native(args):
         "hbm_compulsory_GBs": work["bytes"] / (k_ms * 1e-3) / 1e9, "hbm_peak_GBs": pk["hbm_gbs"],
     }
 
+    # policy rollouts (row a12): 4096 rollouts x 365 periods of the extracted policy
+    rollouts = None
+    if len(inst.products) == 1:
+        ro = workloads.CONFIG4_ROLLOUTS
+        rets = torch.empty(ro["n_rollouts"], dtype=torch.float64, device="cuda")
+        kpis = torch.empty(3 * ro["n_rollouts"], dtype=torch.float64, device="cuda")
+        vi.vi_simulate(h, pol, ro["n_rollouts"], ro["horizon"], 0, ro["seed"], rets, kpis, stream=stream)
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        for _ in range(5):
+            vi.vi_simulate(h, pol, ro["n_rollouts"], ro["horizon"], 0, ro["seed"], rets, kpis, stream=stream)
+        r1.record(stream)
+        r1.synchronize()
+        r_ms = r0.elapsed_time(r1) / 5
+        rollouts = {"n_rollouts": ro["n_rollouts"], "horizon": ro["horizon"], "ms": r_ms,
+                    "periods_per_s": ro["n_rollouts"] * ro["horizon"] / (r_ms * 1e-3),
+                    "mean_return": float(rets.mean().item())}
+
     # end to end through the public API with host buffers: create (tables H2D),
     # solve, V + policy D2H, destroy
     e2e_steps = max(1, min(args.steps, 5))
@@ -363,6 +383,7 @@ def run_native(args):
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind",
                                                                            "sample")},
             "serving": serving,
+            "rollouts": rollouts,
             "wall_s": wall,
         }
         print(json.dumps(out))
