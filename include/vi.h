@@ -155,8 +155,12 @@ vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
  * values per lane (1..12, 16, 21 or 24; Q+1 is split over ceil((Q+1)/width)
  * lanes).  Without it the width is autotuned on the first solve (one timed
  * sweep per candidate width, cached per instance shape; the environment
- * variable VI_AUTOTUNE=0 selects a fixed rule instead). */
-enum { VI_OPT_KERNEL = 1, VI_OPT_PE_MAX_ITERS = 2, VI_OPT_GROUP_WIDTH = 3 };
+ * variable VI_AUTOTUNE=0 selects a fixed rule instead).
+ * VI_OPT_TEST_STALL (test hook): 1 makes the tensor-core kernel withhold its
+ * MMAs, so that its bounded wait for them runs out after a short limit; the
+ * sweep then reports VI_ECUDA ("bounded wait ... gave up") and the CUDA
+ * context stays usable.  0 restores normal operation. */
+enum { VI_OPT_KERNEL = 1, VI_OPT_PE_MAX_ITERS = 2, VI_OPT_GROUP_WIDTH = 3, VI_OPT_TEST_STALL = 4 };
 enum { VI_KERNEL_AUTO = 0, VI_KERNEL_GENERIC = 1, VI_KERNEL_GROUP = 2, VI_KERNEL_TENSOR = 3 };
 vi_status vi_problem_set_option(vi_handle h, int option, int value);
 

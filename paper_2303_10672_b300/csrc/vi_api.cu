@@ -513,6 +513,19 @@ extern "C" vi_status vi_problem_set_option(vi_handle h, int option, int value) {
         }
         return VI_OK;
     }
+    if (option == VI_OPT_TEST_STALL) {
+        if (value != 0 && value != 1) return vi_fail(VI_EINVAL, "test stall must be 0 or 1");
+        h->kp.tc_stall = value;
+        if (h->graph_exec) {   // the graph holds a copy of the kernel parameters
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+        }
+        if (h->graph) {
+            cudaGraphDestroy(h->graph);
+            h->graph = nullptr;
+        }
+        return VI_OK;
+    }
     if (option == VI_OPT_PE_MAX_ITERS) {
         if (value < 0) return vi_fail(VI_EINVAL, "pe max iters must be >= 0");
         h->pe_max_iters = value;
@@ -885,7 +898,10 @@ extern "C" vi_status vi_backup(vi_handle h, const void *V_in, void *V_out, uint8
         CUDA_TRY(cudaStreamSynchronize(s));
         dstats[0] = h->h_state->dmax_abs;
         dstats[1] = h->h_state->dmin_abs;
-        if (h->h_state->fault) return vi_fail(VI_ECUDA, "the sweep's bounded wait on the tensor cores gave up");
+        if (h->h_state->fault) {
+            cudaMemsetAsync(&h->d_state->fault, 0, sizeof(int), s);   // reported once
+            return vi_fail(VI_ECUDA, "the sweep's bounded wait on the tensor cores gave up");
+        }
     }
     return VI_OK;
 }

@@ -67,6 +67,7 @@ struct KernelParams {
     int off_H1lo, off_H2lo;   // low halves of H1 / H2 (float blobs)
     int zlen;             // dmax1 + dmax2 + 1
     SolveState *st;       // solve bookkeeping
+    int tc_stall;         // test hook: the tensor-core kernel withholds its MMAs, so its bounded wait runs out
 };
 
 // ---------------------------------------------------------------------------

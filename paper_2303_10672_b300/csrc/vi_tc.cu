@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(kTcThreads) sweep_tc_kernel(KernelParams kp, i
         __syncthreads();
         tc_fence_after();
         // ---- six split products, smallest first, K in steps of 16
-        if (tid == 0) {
+        if (tid == 0 && !kp.tc_stall) {
             const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
             const int pa[6] = {2, 1, 0, 1, 0, 0};
             const int pb[6] = {0, 1, 2, 0, 1, 0};
@@ -350,7 +350,8 @@ __global__ void __launch_bounds__(kTcThreads) sweep_tc_kernel(KernelParams kp, i
             umma_commit(smem_u32(s_mbar));
         }
         bool done = false;
-        for (long it = 0; it < kTcMaxPolls && !done; ++it) done = mbar_try_wait(smem_u32(s_mbar), parity);
+        const long polls = kp.tc_stall ? 4096 : kTcMaxPolls;
+        for (long it = 0; it < polls && !done; ++it) done = mbar_try_wait(smem_u32(s_mbar), parity);
         parity ^= 1u;
         if (__syncthreads_or(!done)) {
             fault = true;

@@ -91,3 +91,27 @@ def test_tensor_extraction_and_backup_modes():
         torch.cuda.synchronize()
         assert torch.equal(out, V6)
         assert torch.equal(pb, pol)   # extraction of the 5-sweep solve = argmax from V_5
+
+
+def test_bounded_wait_reports_and_context_survives():
+    """The tensor-core kernel's wait for its MMAs is bounded: with the test hook
+    that withholds the MMAs, the sweep reports VI_ECUDA instead of hanging, and
+    the handle works normally afterwards."""
+    inst = TC[2]
+    with Handle(inst, precision="fp32", kernel=vi.VI_KERNEL_TENSOR) as H:
+        V, pol, info = H.solve(0.0, 2)
+        out = torch.empty_like(V)
+        vi.vi_problem_set_option(H.h, vi.VI_OPT_TEST_STALL, 1)
+        with pytest.raises(vi.ViError) as e:
+            vi.vi_backup(H.h, V, out, None)
+        assert e.value.status == vi.VI_ECUDA
+        with pytest.raises(vi.ViError) as e:
+            H.solve(1e-4, 20)
+        assert e.value.status == vi.VI_ECUDA
+        vi.vi_problem_set_option(H.h, vi.VI_OPT_TEST_STALL, 0)
+        V3, pol3, info3 = H.solve(0.0, 3)
+        vi.vi_backup(H.h, V3, out, None)
+        torch.cuda.synchronize()
+    with Handle(inst, precision="fp32", kernel=vi.VI_KERNEL_TENSOR) as F:
+        V4, pol4, info4 = F.solve(0.0, 3)
+    assert torch.equal(V3, V4) and torch.equal(pol3, pol4)
