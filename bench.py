@@ -301,6 +301,8 @@ def run_native(args):
     kch, kw = vi.vi_problem_kernel(h)
     kernel_name = {vi.VI_KERNEL_GENERIC: "sweep_generic_kernel", vi.VI_KERNEL_TENSOR: "sweep_tc_kernel"}.get(
         kch, f"sweep_group_kernel (lane width {kw})")
+    if len(inst.products) == 2 and kch == vi.VI_KERNEL_GROUP:
+        kernel_name = "two_e2_kernel + two_mix_kernel + sweep_two_kernel"
     work = algorithmic_work(inst)
     pk = peaks()
     sm_mhz = clocks.get("sm_mhz") or pk["sm_max_mhz"]

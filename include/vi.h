@@ -71,7 +71,13 @@ enum { VI_STOP_SPAN = 0, VI_STOP_SUPNORM = 1 };
  *                      differences between values; the absolute value is
  *                      rebuilt with error-free float transformations, so the
  *                      stopping test sees no FP32 rounding noise.
- *  VI_PREC_FP32_KAHAN  as VI_PREC_FP32 with compensated (Kahan) sums over outcomes.
+ *  VI_PREC_FP32_KAHAN  as VI_PREC_FP32 with compensated (Kahan) sums over outcomes
+ *                      in the one-thread-per-state kernel (VI_KERNEL_GENERIC).
+ *                      Two-product instances otherwise run the factorised
+ *                      two-product sweep, whose sums are short (at most Dmax1+1
+ *                      terms of product-2 expectations, each over at most
+ *                      Dmax2+1 outcomes, all measured from nearby values) and
+ *                      uncompensated in both FP32 modes.
  *  VI_PREC_FP64        FP64 arithmetic and storage, double[|S|].
  *  VI_PREC_FP32_SINGLE one float per state relative to an FP64 offset
  *                      (V = info.offset + v), float[|S|].  Fastest; its stopping
@@ -143,7 +149,9 @@ vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
 /* Per-handle options (no counterpart in the paper; tuning and test hooks).
  * VI_OPT_KERNEL: which sweep kernel runs -- VI_KERNEL_AUTO (factorised kernel
  * whenever the instance allows it; the tensor-core variant is one of the
- * autotuned candidates), VI_KERNEL_GENERIC (one thread per state),
+ * autotuned candidates; two products in FP32 run the factorised two-product
+ * sweep, which vi_problem_kernel reports as VI_KERNEL_GROUP with width 0),
+ * VI_KERNEL_GENERIC (one thread per state),
  * VI_KERNEL_GROUP (factorised; VI_EINVAL if the instance does not allow it:
  * it needs one product, VI_PREC_FP32 or VI_PREC_FP32_SINGLE, 2 <= Q+1 <= 64 and
  * at least one state digit) or VI_KERNEL_TENSOR (factorised, with the FIFO

@@ -380,6 +380,7 @@ extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_hand
     h->kahan = (d.precision == VI_PREC_FP32_KAHAN) ? 1 : 0;
     h->value_bytes = (h->vk == VK_SINGLE) ? 4 : 8;
     h->group_ok = group_supported(kp, h->vk, h->kahan);
+    h->two_ok = two_supported(kp, h->vk);
     h->group_xw = 0;   // chosen by the autotuner on the first solve (or set explicitly)
     std::vector<float> fblob(blob.size());
     for (size_t i = 0; i < blob.size(); ++i) fblob[i] = (float)blob[i];
@@ -403,6 +404,19 @@ extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_hand
     if ((e = cudaMemcpy(h->d_state, h->h_state, sizeof(SolveState), cudaMemcpyHostToDevice)) != cudaSuccess) {
         destroy_internal(h);
         return vi_fail(VI_ECUDA, "state upload: %s", cudaGetErrorString(e));
+    }
+    if (h->two_ok) {
+        size_t n_mix = 0;
+        const size_t n_e2 = two_table_floats(kp, &n_mix);
+        if ((e = cudaMalloc(&h->d_two_e2, n_e2 * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc(&h->d_two_mix, n_mix * sizeof(float))) != cudaSuccess) {
+            destroy_internal(h);
+            return vi_fail(e == cudaErrorMemoryAllocation ? VI_ENOMEM : VI_ECUDA, "two-product tables: %s",
+                           cudaGetErrorString(e));
+        }
+        kp.two_e2 = h->d_two_e2;
+        kp.two_mix = h->d_two_mix;
+        kp.two_nt1 = kp.p[0].dmax + 1;
     }
     kp.st = h->d_state;
     kp.tables = (h->vk == VK_DOUBLE) ? (const void *)h->d_tab_d : (const void *)h->d_tab_f;
@@ -438,6 +452,8 @@ static void destroy_internal(vi_problem *h) {
     if (h->d_state) cudaFree(h->d_state);
     if (h->h_state) cudaFreeHost(h->h_state);
     if (h->d_scratch) cudaFree(h->d_scratch);
+    if (h->d_two_e2) cudaFree(h->d_two_e2);
+    if (h->d_two_mix) cudaFree(h->d_two_mix);
     if (h->d_pe[0]) cudaFree(h->d_pe[0]);
     if (h->d_pe[1]) cudaFree(h->d_pe[1]);
     if (h->d_stage_v) cudaFree(h->d_stage_v);
@@ -629,6 +645,10 @@ static vi_status autotune(vi_problem *h, cudaStream_t s) {
 
 // resolve which sweep kernel runs: 0 = generic, > 0 = factorised with that lane width
 static vi_status choose_kernel(vi_problem *h, cudaStream_t s) {
+    if (h->two_ok && h->kernel_choice != VI_KERNEL_GENERIC) {
+        h->sweep_xw = kTwoWidth;
+        return VI_OK;
+    }
     if (h->kernel_choice == VI_KERNEL_GENERIC || !h->group_ok) {
         h->sweep_xw = 0;
         return VI_OK;
@@ -647,7 +667,7 @@ extern "C" vi_status vi_problem_kernel(vi_handle h, int *kernel, int *width) {
     if (st != VI_OK) return st;
     const int xw = h->sweep_xw;
     if (kernel) *kernel = (xw == 0) ? VI_KERNEL_GENERIC : (xw == kTcWidth) ? VI_KERNEL_TENSOR : VI_KERNEL_GROUP;
-    if (width) *width = (xw == 0 || xw == kTcWidth) ? 0 : xw;
+    if (width) *width = (xw == 0 || xw == kTcWidth || xw == kTwoWidth) ? 0 : xw;
     return VI_OK;
 }
 
@@ -661,7 +681,29 @@ static vi_status ensure_scratch(vi_problem *h) {
 }
 
 static vi_status launch_desc(const LaunchDesc &ld, void **args, cudaStream_t s) {
+    for (int i = 0; i < ld.n_pre; ++i) CUDA_TRY(cudaLaunchKernel(ld.pre_fn[i], ld.pre_grid[i], ld.pre_block[i], args, 0, s));
     CUDA_TRY(cudaLaunchKernel(ld.fn, ld.grid, ld.block, args, ld.smem, s));
+    return VI_OK;
+}
+
+// kernel nodes of one sweep (pre-kernels, then the sweep) after `dep`; returns the last node
+static vi_status add_sweep_nodes(cudaGraph_t g, const LaunchDesc &ld, void **args, cudaGraphNode_t dep,
+                                 cudaGraphNode_t *last) {
+    cudaKernelNodeParams kn;
+    cudaGraphNode_t prev = dep;
+    for (int i = 0; i <= ld.n_pre; ++i) {
+        memset(&kn, 0, sizeof(kn));
+        const bool pre = i < ld.n_pre;
+        kn.func = (void *)(pre ? ld.pre_fn[i] : ld.fn);
+        kn.gridDim = pre ? ld.pre_grid[i] : ld.grid;
+        kn.blockDim = pre ? ld.pre_block[i] : ld.block;
+        kn.sharedMemBytes = pre ? 0u : (unsigned)ld.smem;
+        kn.kernelParams = args;
+        cudaGraphNode_t node;
+        CUDA_TRY(cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kn));
+        prev = node;
+    }
+    *last = prev;
     return VI_OK;
 }
 
@@ -719,20 +761,15 @@ static vi_status build_graph(vi_problem *h) {
 
     void *sweep_args[] = {&h->args_kp, &h->args_mode_sweep, &h->args_null_v, &h->args_null_v, &h->args_null_p,
                           &h->args_lpr};
-    memset(&kn, 0, sizeof(kn));
-    kn.func = (void *)ld_sweep.fn;
-    kn.gridDim = ld_sweep.grid;
-    kn.blockDim = ld_sweep.block;
-    kn.sharedMemBytes = (unsigned)ld_sweep.smem;
-    kn.kernelParams = sweep_args;
     cudaGraphNode_t n_sweep;
-    CUDA_TRY(cudaGraphAddKernelNode(&n_sweep, body, nullptr, 0, &kn));
+    vi_status vs = add_sweep_nodes(body, ld_sweep, sweep_args, nullptr, &n_sweep);
+    if (vs != VI_OK) return vs;
 
     void *extract_args[] = {&h->args_kp, &h->args_mode_extract, &h->args_null_v, &h->args_null_v,
                             &h->args_null_p, &h->args_lpr};
-    kn.kernelParams = extract_args;
     cudaGraphNode_t n_extract;
-    CUDA_TRY(cudaGraphAddKernelNode(&n_extract, g, &n_loop, 1, &kn));
+    vs = add_sweep_nodes(g, ld_sweep, extract_args, n_loop, &n_extract);
+    if (vs != VI_OK) return vs;
 
     CUDA_TRY(cudaGraphInstantiate(&h->graph_exec, g, 0));
     return VI_OK;

@@ -17,6 +17,7 @@ struct vi_problem {
     int vk = 0;                        // value kind (VK_SINGLE / VK_PAIR / VK_DOUBLE)
     int kahan = 0;                     // compensated sums over outcomes
     bool group_ok = false;             // the factorised kernel can run this instance
+    bool two_ok = false;               // the factorised two-product sweep can run this instance
     int kernel_choice = 0;             // VI_KERNEL_AUTO / _GENERIC / _GROUP
     int group_xw = 0;                  // lane width of the factorised kernel (0 = not chosen yet)
     int sweep_xw = 0;                  // kernel of the next launches: 0 generic, else lane width
@@ -28,6 +29,8 @@ struct vi_problem {
     vib::SolveState *d_state = nullptr;
     vib::SolveState *h_state = nullptr;   // pinned mirror
     void *d_scratch = nullptr;            // second half of the value ping-pong
+    float *d_two_e2 = nullptr;            // two-product expectation tables (factorised sweep)
+    float *d_two_mix = nullptr;
     double *d_pe[2] = {nullptr, nullptr};
     void *d_stage_v = nullptr;            // vi_solve_host staging
     uint8_t *d_stage_p = nullptr;

@@ -68,6 +68,10 @@ struct KernelParams {
     int zlen;             // dmax1 + dmax2 + 1
     SolveState *st;       // solve bookkeeping
     int tc_stall;         // test hook: the tensor-core kernel withholds its MMAs, so its bounded wait runs out
+    // factorised two-product sweep: per-sweep tables of product-2 expectations
+    float *two_e2;        // [s2][a2][i1]  sum_z w(z) (V(i1, s2'(z)) - V(i1, s2'(0)))
+    float *two_mix;       // [s2][a2][T1]  the substitution mixture of d1 >= T1, same frame with i1 = 0
+    int two_nt1;          // T1 values kept: 0..dmax1
 };
 
 // ---------------------------------------------------------------------------

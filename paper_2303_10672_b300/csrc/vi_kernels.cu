@@ -672,9 +672,183 @@ int group_width_candidates(int G, int *out, int max_out) {
     return n;
 }
 
+// ===========================================================================
+// factorised two-product sweep.  Product 1's next state depends on (s1, a1, d1)
+// only and product 2's on (s2, a2, z), z = d2 (d1 below product-1 stock) or the
+// substitution mixture of d1 >= T1, which leaves product 1 empty (index 0 with
+// L = 1).  So, with ref the no-demand next state of (s, a) and i2_0 that of
+// product 2,
+//   E[V(s') - ref] = sum_{d1 < T1} p1(d1) [E2(i1(d1), s2, a2) + V(i1(d1), i2_0) - ref]
+//                  + Mix(s2, a2, T1) + tail1(T1) [V(0, i2_0) - ref],
+// with E2 and Mix product-2 expectations measured from V(i1, i2_0), built once
+// per sweep by two small kernels ahead of the sweep.
+// ===========================================================================
+__global__ void __launch_bounds__(kGenericThreads)
+two_e2_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int) {
+    SolveState *st = kp.st;
+    Bufs B;
+    if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
+    const ProdParams &P1 = kp.p[0];
+    const ProdParams &P2 = kp.p[1];
+    const uint32_t S1 = P1.nS;
+    const uint64_t n = (uint64_t)S1 * P2.nS * (uint32_t)P2.G;
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const uint32_t i1 = (uint32_t)(t % S1);
+    const uint32_t rest = (uint32_t)(t / S1);
+    const int a2 = (int)(rest % (uint32_t)P2.G);
+    const uint32_t s2 = rest / (uint32_t)P2.G;
+    const float *tab = (const float *)kp.tables;
+    const ProdState p2s = prod_state(P2, s2);
+    const ProdAction A2 = prod_action(P2, p2s, a2, kp.issuing);
+    const float2 *V2 = (const float2 *)B.vin;
+    Acc<float, 0> acc;
+    acc.init();
+    GetRel get{V2, V2[i1 + S1 * A2.wk.idx]};
+    expect_rest<float, 0>(acc, get, i1, S1, A2.wk, P2.cb, kp.issuing, (uint32_t)P2.G, A2.y1, A2.R,
+                          tab + P2.off_p, tab + P2.off_F, tab + P2.off_tail, P2.dmax + 1, 1.f);
+    kp.two_e2[t] = acc.s;
+}
+
+__global__ void __launch_bounds__(kGenericThreads)
+two_mix_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int) {
+    SolveState *st = kp.st;
+    Bufs B;
+    if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
+    const ProdParams &P1 = kp.p[0];
+    const ProdParams &P2 = kp.p[1];
+    const uint32_t S1 = P1.nS;
+    const uint32_t nt = (uint32_t)kp.two_nt1;
+    const uint32_t n = P2.nS * (uint32_t)P2.G * nt;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int T1 = (int)(t % nt);
+    const uint32_t rest = t / nt;
+    const int a2 = (int)(rest % (uint32_t)P2.G);
+    const uint32_t s2 = rest / (uint32_t)P2.G;
+    const float *tab = (const float *)kp.tables;
+    const ProdState p2s = prod_state(P2, s2);
+    const ProdAction A2 = prod_action(P2, p2s, a2, kp.issuing);
+    const float2 *V2 = (const float2 *)B.vin;
+    Acc<float, 0> acc;
+    acc.init();
+    GetRel get{V2, V2[S1 * A2.wk.idx]};
+    const int row = T1 * kp.zlen;
+    expect_rest<float, 0>(acc, get, 0u, S1, A2.wk, P2.cb, kp.issuing, (uint32_t)P2.G, A2.y1, A2.R,
+                          tab + kp.off_M + row, tab + kp.off_Mc + row, tab + kp.off_Mt + row, kp.zlen, 1.f);
+    kp.two_mix[t] = acc.s;
+}
+
+__global__ void __launch_bounds__(kGenericThreads)
+sweep_two_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int) {
+    SolveState *st = kp.st;
+    Bufs B;
+    if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
+    const ProdParams &P1 = kp.p[0];
+    const ProdParams &P2 = kp.p[1];
+    const uint32_t S1 = P1.nS;
+    const float *tab = (const float *)kp.tables;
+    const float2 *V2 = (const float2 *)B.vin;
+    const float gam = (float)kp.gamma;
+    const int lifo = kp.issuing;
+    float mx = -INFINITY, mn = INFINITY;
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < kp.nS) {
+        const uint32_t s2 = s / S1;
+        const ProdState p1s = prod_state(P1, s - s2 * S1);
+        const ProdState p2s = prod_state(P2, s2);
+        const float2 R0 = V2[two_base_state(kp, p1s, p2s, 0)];
+        float bh = -INFINITY, bl = 0.f;
+        int arg = 0;
+        for (int a1 = 0; a1 < P1.G; ++a1) {
+            const ProdAction A1 = prod_action(P1, p1s, a1, lifo);
+            const int top1 = min(A1.T, P1.dmax + 1);   // d1 in [0, top1)
+            for (int a2 = 0; a2 < P2.G; ++a2) {
+                const ProdAction A2 = prod_action(P2, p2s, a2, lifo);
+                const uint32_t i20 = S1 * A2.wk.idx;
+                const float2 ref = V2[A1.wk.idx + i20];
+                const float *e2 = kp.two_e2 + ((uint64_t)s2 * P2.G + a2) * S1;
+                float acc = 0.f;
+                Walker w1 = A1.wk;
+                int e1c = 0;
+                for (int d1 = 0; d1 < top1; ++d1) {
+                    const int e1 = lifo ? min(d1, A1.R) : max(d1 - A1.y1, 0);
+                    for (; e1c < e1; ++e1c) walker_step(w1, P1.cb, lifo, (uint32_t)P1.G);
+                    const float t = e2[w1.idx] + pair_diff(V2[w1.idx + i20], ref);
+                    acc = fmaf(tab[P1.off_p + d1], t, acc);
+                }
+                if (A1.T <= P1.dmax) {
+                    const float t = kp.two_mix[((uint32_t)s2 * P2.G + a2) * kp.two_nt1 + A1.T];
+                    acc += t + tab[P1.off_tail + A1.T] * pair_diff(V2[i20], ref);
+                }
+                float qh, ql;
+                const float ca =
+                    __fadd_rn(__fmul_rn(-(float)P1.c_o, (float)a1), __fmul_rn(-(float)P2.c_o, (float)a2));
+                action_base(gam, ref, R0, ca, qh, ql);
+                const int i1 = h1_index(kp, A1), i2 = h2_index(kp, A1, A2);
+                pair_add(qh, ql, tab[kp.off_H1 + i1], tab[kp.off_H1lo + i1]);
+                pair_add(qh, ql, tab[kp.off_H2 + i2], tab[kp.off_H2lo + i2]);
+                ql = __fmaf_rn(gam, acc, ql);
+                const float diff = __fadd_rn(__fsub_rn(qh, bh), __fsub_rn(ql, bl));
+                const bool up = diff > 0.f;
+                bh = up ? qh : bh;
+                bl = up ? ql : bl;
+                arg = up ? a1 * P2.G + a2 : arg;
+            }
+        }
+        const float2 vold = V2[s];
+        if (mode == MODE_EXTRACT) {
+            if (B.vout) ((float2 *)B.vout)[s] = vold;
+        } else {
+            const float2 vnew = pair_finish(gam, R0, bh, bl);
+            ((float2 *)B.vout)[s] = vnew;
+            const float dlt = pair_diff(vnew, vold);
+            mx = mn = dlt;
+        }
+        if (B.pol) B.pol[s] = (uint8_t)arg;
+    }
+    if (mode != MODE_EXTRACT) block_reduce_and_finalize<float>(mx, mn, st, mode, gridDim.x);
+}
+
+bool two_supported(const KernelParams &kp, int vk) {
+    if (kp.n_products != 2 || vk != VK_PAIR) return false;
+    const ProdParams &P1 = kp.p[0];
+    const ProdParams &P2 = kp.p[1];
+    if (P1.L != 1 || P2.L != 1) return false;
+    size_t mix = 0;
+    return two_table_floats(kp, &mix) <= ((size_t)1 << 27) && mix <= ((size_t)1 << 27);
+}
+
+size_t two_table_floats(const KernelParams &kp, size_t *mix_floats) {
+    const ProdParams &P1 = kp.p[0];
+    const ProdParams &P2 = kp.p[1];
+    if (mix_floats) *mix_floats = (size_t)P2.nS * P2.G * (size_t)(P1.dmax + 1);
+    return (size_t)P1.nS * P2.nS * (size_t)P2.G;
+}
+
+static cudaError_t describe_two(const KernelParams &kp, LaunchDesc &d) {
+    const uint64_t n_e2 = (uint64_t)kp.p[0].nS * kp.p[1].nS * (uint32_t)kp.p[1].G;
+    const uint64_t n_mix = (uint64_t)kp.p[1].nS * (uint32_t)kp.p[1].G * (uint32_t)kp.two_nt1;
+    d.fn = (const void *)sweep_two_kernel;
+    d.grid = dim3((kp.nS + kGenericThreads - 1) / kGenericThreads);
+    d.block = dim3(kGenericThreads);
+    d.smem = 0;
+    d.lpr = 0;
+    d.n_pre = 2;
+    d.pre_fn[0] = (const void *)two_e2_kernel;
+    d.pre_grid[0] = dim3((unsigned)((n_e2 + kGenericThreads - 1) / kGenericThreads));
+    d.pre_block[0] = dim3(kGenericThreads);
+    d.pre_fn[1] = (const void *)two_mix_kernel;
+    d.pre_grid[1] = dim3((unsigned)((n_mix + kGenericThreads - 1) / kGenericThreads));
+    d.pre_block[1] = dim3(kGenericThreads);
+    return cudaSuccess;
+}
+
 cudaError_t describe_sweep(const KernelParams &kp, int vk, int kahan, int use_group, LaunchDesc &d) {
     d.lpr = 0;
+    d.n_pre = 0;
     if (use_group == kTcWidth) return describe_tc(kp, d);
+    if (use_group == kTwoWidth) return describe_two(kp, d);
     if (use_group) {
         const int xw = use_group;   // lane width of the factorised kernel
         const bool pipe = kp.p[0].L >= 2;

@@ -46,6 +46,10 @@ struct LaunchDesc {
     dim3 grid, block;
     size_t smem;
     int lpr;    // lanes per rest of the factorised kernel (0 for the generic kernel)
+    // kernels that run before fn in every sweep and extraction, with the same arguments
+    int n_pre = 0;
+    const void *pre_fn[2] = {nullptr, nullptr};
+    dim3 pre_grid[2], pre_block[2];
 };
 // use_group = 0: generic kernel; kTcWidth: tensor-core FIFO kernel; otherwise the
 // factorised kernel with that lane width XW
@@ -53,6 +57,10 @@ cudaError_t describe_sweep(const KernelParams &kp, int vk, int kahan, int use_gr
 bool group_width_supported(int xw);
 // lane-width token that selects the tensor-core FIFO sweep (vi_tc.cu)
 constexpr int kTcWidth = 100;
+// lane-width token of the factorised two-product sweep
+constexpr int kTwoWidth = 200;
+bool two_supported(const KernelParams &kp, int vk);
+size_t two_table_floats(const KernelParams &kp, size_t *mix_floats);
 bool tc_supported(const KernelParams &kp, int vk, int kahan);
 cudaError_t describe_tc(const KernelParams &kp, LaunchDesc &d);
 int batch_width(int G);

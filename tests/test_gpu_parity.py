@@ -385,3 +385,17 @@ def test_l2_read_probe():
         vi.vi_probe_l2_read(buf, 15, 1)
     with pytest.raises(vi.ViError):
         vi.vi_probe_l2_read(buf, nbytes, 0)
+
+
+def test_two_product_factorised_matches_generic():
+    """The factorised two-product sweep (expectation tables of product 2 built
+    per sweep) and the generic one agree after the same number of sweeps."""
+    inst = workloads.config3(Q=4)
+    with Handle(inst, precision="fp32") as F, Handle(inst, precision="fp32", kernel=vi.VI_KERNEL_GENERIC) as G:
+        assert vi.vi_problem_kernel(F.h)[0] == vi.VI_KERNEL_GROUP
+        assert vi.vi_problem_kernel(G.h)[0] == vi.VI_KERNEL_GENERIC
+        Vf, pf, inf_ = F.solve(0.0, 8)
+        Vg, pg, ing = G.solve(0.0, 8)
+        err = compare_values(F.v_abs(Vf, inf_), G.v_abs(Vg, ing))
+        assert err <= 1e-6, err
+        assert (pf != pg).sum().item() <= 1e-3 * pf.numel()
