@@ -123,10 +123,12 @@ def dist_setup(n_gpus):
 def barrier_sync(world):
     import torch
     import torch.distributed as dist
-    torch.cuda.synchronize()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
 
 
 def max_over_ranks(x: float, world: int) -> float:
@@ -134,9 +136,16 @@ def max_over_ranks(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_value(units_per_rank: float, seconds_max: float, world: int) -> float:
+    """Whole-job rate of N independent replicas: every rank does the same work,
+    the job takes as long as the slowest rank."""
+    return units_per_rank * world / seconds_max
 
 
 # ---------------------------------------------------------------------------
@@ -280,7 +289,7 @@ def run_native(args):
     dev_s = sum(step_ms) / 1000.0
     dev_s_max = max_over_ranks(dev_s, world)
     updates = nominal * sum(iters)
-    value = updates * world / dev_s_max
+    value = replica_value(updates, dev_s_max, world)
 
     # dominant kernel: one sweep launch (same kernel, same grid) timed with events
     V2 = torch.empty_like(V)
