@@ -250,8 +250,10 @@ vi_status vi_simulate(vi_handle h, const uint8_t *policy, int n_rollouts, int ho
  * one batched sweep launch over all admitted instances per iteration, so
  * instances of different sizes advance together; an instance whose stopping
  * test passed gets its extraction sweep in the next launch and is then
- * retired, freeing memory for queued requests.  `stream` is unused (the worker
- * owns a stream); max_slots in 1..1024. */
+ * retired, freeing memory for queued requests.  Value buffers come from a
+ * memory pool of the server's own that keeps freed memory reserved up to the
+ * budget (min(budget, 1 GiB) is reserved at creation).  `stream` is unused (the
+ * worker owns a stream); max_slots in 1..1024. */
 vi_status vi_server_create(size_t mem_budget_bytes, int max_slots, void *stream, vi_server *out);
 /* Queue a request; returns at once with its id.  The description is copied.
  * VI_EINVAL for a bad description, VI_EBUSY if it can never fit the budget. */

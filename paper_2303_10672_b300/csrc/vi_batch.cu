@@ -9,8 +9,8 @@ namespace vib {
 // Block b belongs to the slot s with block_start[s] <= b < block_start[s+1];
 // each slot has its own tables, value buffers and SolveState.
 // ---------------------------------------------------------------------------
-template <int XW>
-__global__ void __launch_bounds__(kGroupThreads)
+template <int XW, int LIFO, int LPIPE>
+__global__ void __launch_bounds__(kGroupThreads, group_min_blocks(XW, LIFO))
 sweep_batch_kernel(const KernelParams *kps, const int *modes, const int *lprs, const uint32_t *block_start,
                    int n_slots) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -30,18 +30,7 @@ sweep_batch_kernel(const KernelParams *kps, const int *modes, const int *lprs, c
     const int s = s_slot;
     const unsigned nb = block_start[s + 1] - block_start[s];
     const uint32_t local = b - block_start[s];
-    const bool pipe = s_kp.p[0].L >= 2;
-    if (s_kp.issuing) {
-        if (pipe)
-            group_body<XW, 1, VK_PAIR, 1>(s_kp, local, nb, modes[s], nullptr, nullptr, nullptr, lprs[s], smem_raw);
-        else
-            group_body<XW, 1, VK_PAIR, 0>(s_kp, local, nb, modes[s], nullptr, nullptr, nullptr, lprs[s], smem_raw);
-    } else {
-        if (pipe)
-            group_body<XW, 0, VK_PAIR, 1>(s_kp, local, nb, modes[s], nullptr, nullptr, nullptr, lprs[s], smem_raw);
-        else
-            group_body<XW, 0, VK_PAIR, 0>(s_kp, local, nb, modes[s], nullptr, nullptr, nullptr, lprs[s], smem_raw);
-    }
+    group_body<XW, LIFO, VK_PAIR, LPIPE>(s_kp, local, nb, modes[s], nullptr, nullptr, nullptr, lprs[s], smem_raw);
 }
 
 // lane-width class of the batched server kernel for an instance: one lane per
@@ -65,30 +54,65 @@ void batch_geometry(const KernelParams &kp, int *lpr, uint32_t *blocks, size_t *
     *smem = group_smem(kp, rb, VK_PAIR);
 }
 
+template <int XW, int LIFO, int LPIPE>
+static cudaError_t prepare_batch_t() {
+    return cudaFuncSetAttribute(sweep_batch_kernel<XW, LIFO, LPIPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024);
+}
+
 template <int XW>
+static cudaError_t prepare_batch_w() {
+    cudaError_t e;
+    if ((e = prepare_batch_t<XW, 0, 0>()) != cudaSuccess || (e = prepare_batch_t<XW, 0, 1>()) != cudaSuccess ||
+        (e = prepare_batch_t<XW, 1, 0>()) != cudaSuccess || (e = prepare_batch_t<XW, 1, 1>()) != cudaSuccess)
+        return e;
+    return cudaSuccess;
+}
+
+// set the shared-memory attribute of every batched variant; this also loads them,
+// so that no first launch pays for loading its code (the server calls it at creation)
+cudaError_t prepare_sweep_batch() {
+    cudaError_t e;
+    if ((e = prepare_batch_w<8>()) != cudaSuccess || (e = prepare_batch_w<12>()) != cudaSuccess ||
+        (e = prepare_batch_w<16>()) != cudaSuccess || (e = prepare_batch_w<21>()) != cudaSuccess ||
+        (e = prepare_batch_w<24>()) != cudaSuccess)
+        return e;
+    return cudaSuccess;
+}
+
+template <int XW, int LIFO, int LPIPE>
 static cudaError_t launch_batch_t(const KernelParams *kps, const int *modes, const int *lprs,
                                   const uint32_t *block_start, int n_slots, uint32_t total_blocks, size_t smem,
                                   cudaStream_t stream) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_batch_kernel<XW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    sweep_batch_kernel<XW><<<total_blocks, kGroupThreads, smem, stream>>>(kps, modes, lprs, block_start, n_slots);
+    sweep_batch_kernel<XW, LIFO, LPIPE><<<total_blocks, kGroupThreads, smem, stream>>>(kps, modes, lprs, block_start,
+                                                                                       n_slots);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_batch(int xw, const KernelParams *kps, const int *modes, const int *lprs,
+template <int XW>
+static cudaError_t launch_batch_w(int variant, const KernelParams *kps, const int *modes, const int *lprs,
+                                  const uint32_t *block_start, int n_slots, uint32_t total_blocks, size_t smem,
+                                  cudaStream_t stream) {
+    switch (variant) {
+        case 0: return launch_batch_t<XW, 0, 0>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
+        case 1: return launch_batch_t<XW, 0, 1>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
+        case 2: return launch_batch_t<XW, 1, 0>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
+        case 3: return launch_batch_t<XW, 1, 1>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int batch_variant(const KernelParams &kp) { return (kp.issuing ? 2 : 0) + (kp.p[0].L >= 2 ? 1 : 0); }
+
+cudaError_t launch_sweep_batch(int xw, int variant, const KernelParams *kps, const int *modes, const int *lprs,
                                const uint32_t *block_start, int n_slots, uint32_t total_blocks, size_t smem,
                                cudaStream_t stream) {
     switch (xw) {
-        case 8: return launch_batch_t<8>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
-        case 12: return launch_batch_t<12>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
-        case 16: return launch_batch_t<16>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
-        case 21: return launch_batch_t<21>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
-        case 24: return launch_batch_t<24>(kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
+        case 8: return launch_batch_w<8>(variant, kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
+        case 12: return launch_batch_w<12>(variant, kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
+        case 16: return launch_batch_w<16>(variant, kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
+        case 21: return launch_batch_w<21>(variant, kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
+        case 24: return launch_batch_w<24>(variant, kps, modes, lprs, block_start, n_slots, total_blocks, smem, stream);
         default: return cudaErrorInvalidValue;
     }
 }

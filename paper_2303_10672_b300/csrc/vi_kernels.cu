@@ -874,6 +874,16 @@ __global__ void gather_status_kernel(SolveState *const *sts, int n, SlotStatus *
     out[i].crit = st->crit;
 }
 
+cudaError_t prepare_server_helpers() {
+    cudaFuncAttributes fa;
+    cudaError_t e;
+    if ((e = cudaFuncGetAttributes(&fa, gather_status_kernel)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa, to_fp64_kernel)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa, solve_init_kernel)) != cudaSuccess)
+        return e;
+    return cudaSuccess;
+}
+
 cudaError_t launch_gather_status(SolveState *const *sts, int n, SlotStatus *out, cudaStream_t stream) {
     gather_status_kernel<<<(n + 63) / 64, 64, 0, stream>>>(sts, n, out);
     return cudaGetLastError();

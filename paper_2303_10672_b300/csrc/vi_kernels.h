@@ -65,7 +65,13 @@ bool tc_supported(const KernelParams &kp, int vk, int kahan);
 cudaError_t describe_tc(const KernelParams &kp, LaunchDesc &d);
 int batch_width(int G);
 void batch_geometry(const KernelParams &kp, int *lpr, uint32_t *blocks, size_t *smem);
-cudaError_t launch_sweep_batch(int xw, const KernelParams *kps, const int *modes, const int *lprs,
+// loads every batched variant and sets its shared-memory limit (before the first launch)
+cudaError_t prepare_sweep_batch();
+// loads the server's helper kernels (status gather, FP64 conversion, solve init)
+cudaError_t prepare_server_helpers();
+// variant of the batched kernel: 2 * LIFO + (L >= 2); one launch per (lane width, variant)
+int batch_variant(const KernelParams &kp);
+cudaError_t launch_sweep_batch(int xw, int variant, const KernelParams *kps, const int *modes, const int *lprs,
                                const uint32_t *block_start, int n_slots, uint32_t total_blocks, size_t smem,
                                cudaStream_t stream);
 struct SlotStatus {

@@ -41,7 +41,10 @@ using namespace vib;
 namespace {
 
 constexpr int kSlotTabFloats = 16384;   // expectation-table capacity of a slot (64 KiB)
-constexpr int kSweepsPerCheck = 4;      // batched sweeps between two status reads
+constexpr int kSweepsPerCheck = 4;      // batched sweeps between two status reads (small batches)
+// Above this many active states a batched sweep outlasts the status round trip,
+// and further sweeps would only delay the extraction of instances that stopped.
+constexpr double kOneSweepStates = 1 << 20;
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -74,7 +77,7 @@ struct Slot {
     void *scratch = nullptr;       // ping-pong partner, then the FP64 result
     uint8_t *policy = nullptr;
     int mode = MODE_SWEEP;
-    int xw = 0, lpr = 0;
+    int xw = 0, variant = 0, lpr = 0;
     uint32_t blocks = 0;
     size_t smem = 0;
     // owned for the server's lifetime
@@ -100,6 +103,7 @@ struct vi_server_s {
     int max_slots = 0;
     cudaStream_t stream = nullptr;    // batched sweeps
     cudaStream_t rstream = nullptr;   // retirement copies
+    cudaMemPool_t pool = nullptr;     // value and policy buffers; keeps up to the budget between requests
     std::mutex mu;
     std::condition_variable cv;
     std::deque<std::shared_ptr<Request>> queue;
@@ -149,9 +153,9 @@ static vi_status slot_open(vi_server_s *srv, Slot &sl, std::shared_ptr<Request> 
     sl.kp.tables = sl.d_tab;
     sl.kp.st = sl.d_state;
     cudaError_t e;
-    if ((e = cudaMallocAsync(&sl.V, (size_t)n * 8, srv->stream)) != cudaSuccess ||
-        (e = cudaMallocAsync(&sl.scratch, (size_t)n * 8, srv->stream)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&sl.policy, n, srv->stream)) != cudaSuccess)
+    if ((e = cudaMallocFromPoolAsync(&sl.V, (size_t)n * 8, srv->pool, srv->stream)) != cudaSuccess ||
+        (e = cudaMallocFromPoolAsync(&sl.scratch, (size_t)n * 8, srv->pool, srv->stream)) != cudaSuccess ||
+        (e = cudaMallocFromPoolAsync((void **)&sl.policy, n, srv->pool, srv->stream)) != cudaSuccess)
         return vi_fail(VI_ENOMEM, "server slot allocation: %s", cudaGetErrorString(e));
     SolveState *hs = sl.h_state;
     memset(hs, 0, sizeof(SolveState));
@@ -172,6 +176,7 @@ static vi_status slot_open(vi_server_s *srv, Slot &sl, std::shared_ptr<Request> 
         return vi_fail(VI_ECUDA, "server slot init: %s", cudaGetErrorString(e));
     sl.mode = req->max_iters > 0 ? MODE_SWEEP : MODE_EXTRACT;
     sl.xw = batch_width(sl.kp.p[0].G);
+    sl.variant = batch_variant(sl.kp);
     batch_geometry(sl.kp, &sl.lpr, &sl.blocks, &sl.smem);
     return VI_OK;
 }
@@ -230,17 +235,19 @@ static void retire_loop(vi_server_s *srv) {
     }
 }
 
-// one launch per lane-width class over the active slots; modes from the slots
-// (first sweep of an iteration) or MODE_SWEEP for all (the later ones)
+// one launch per (lane width, variant) class over the active slots; modes from the
+// slots (first sweep of an iteration) or MODE_SWEEP for all (the later ones)
 static cudaError_t launch_round(vi_server_s *srv, const std::vector<int> &act, bool first) {
     int koff = 0, boff = 0;
-    for (int xw : {8, 12, 16, 21, 24}) {
+    for (int cls = 0; cls < 5 * 4; ++cls) {
+        static const int widths[5] = {8, 12, 16, 21, 24};
+        const int xw = widths[cls / 4], variant = cls % 4;
         const int kbase = koff, bbase = boff;
         uint32_t total = 0;
         size_t smem = 0;
         for (int i : act) {
             Slot &sl = srv->slots[i];
-            if (sl.xw != xw) continue;
+            if (sl.xw != xw || sl.variant != variant) continue;
             if (first) {
                 srv->h_kps[koff] = sl.kp;
                 srv->h_modes[koff] = sl.mode;
@@ -268,7 +275,7 @@ static cudaError_t launch_round(vi_server_s *srv, const std::vector<int> &act, b
                                      cudaMemcpyHostToDevice, srv->stream)) != cudaSuccess)
                 return e;
         }
-        e = launch_sweep_batch(xw, srv->d_kps + kbase, (first ? srv->d_modes : srv->d_modes_sweep) + kbase,
+        e = launch_sweep_batch(xw, variant, srv->d_kps + kbase, (first ? srv->d_modes : srv->d_modes_sweep) + kbase,
                                srv->d_lprs + kbase, srv->d_bstart + bbase, n_cls, total, smem, srv->stream);
         if (e != cudaSuccess) return e;
     }
@@ -307,14 +314,17 @@ static void worker_loop(vi_server_s *srv) {
         }
         std::vector<int> act;
         bool sweeping = false;
+        double states = 0.0;
         for (int i = 0; i < cap; ++i)
             if (srv->slots[i].req) {
                 act.push_back(i);
                 sweeping |= (srv->slots[i].mode == MODE_SWEEP);
+                states += (double)srv->slots[i].kp.nS;
             }
         if (act.empty()) continue;
-        // a few sweeps back to back: an instance that stopped turns the later ones into no-ops
-        const int rounds = sweeping ? kSweepsPerCheck : 1;
+        // a few sweeps back to back while the batch is small: an instance that stopped
+        // turns the later ones into no-ops
+        const int rounds = (sweeping && states < kOneSweepStates) ? kSweepsPerCheck : 1;
         cudaError_t e = cudaSuccess;
         for (int rd = 0; rd < rounds && e == cudaSuccess; ++rd) e = launch_round(srv, act, rd == 0);
         if (e != cudaSuccess) {
@@ -389,8 +399,36 @@ extern "C" vi_status vi_server_create(size_t mem_budget_bytes, int max_slots, vo
     srv->budget = mem_budget_bytes;
     srv->max_slots = max_slots;
     srv->slots.resize(max_slots);
-    const int n = max_slots + 8;   // one extra block_start entry per width class
+    const int n = max_slots + 24;   // one extra block_start entry per (width, variant) class
+    int dev = 0;
+    cudaGetDevice(&dev);
     cudaError_t e;
+    {
+        // a pool of its own whose freed memory stays reserved up to the budget: the default
+        // pool would hand it back at every synchronisation and the next admission would
+        // map fresh memory
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        uint64_t keep = (uint64_t)mem_budget_bytes;
+        if ((e = cudaMemPoolCreate(&srv->pool, &props)) != cudaSuccess ||
+            (e = cudaMemPoolSetAttribute(srv->pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+            vi_server_destroy(srv);
+            return vi_fail(VI_ECUDA, "server memory pool: %s", cudaGetErrorString(e));
+        }
+        // map part of the budget now, so that the first large admissions do not pay for it
+        void *warm = nullptr;
+        const size_t warm_bytes = std::min(mem_budget_bytes, (size_t)1 << 30);
+        if (cudaMallocFromPoolAsync(&warm, warm_bytes, srv->pool, nullptr) == cudaSuccess) {
+            cudaFreeAsync(warm, nullptr);
+            cudaStreamSynchronize(nullptr);
+        } else {
+            cudaGetLastError();   // not enough free memory to reserve now: grow on demand instead
+        }
+    }
     if ((e = cudaStreamCreateWithFlags(&srv->stream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&srv->rstream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaMalloc(&srv->d_kps, sizeof(KernelParams) * n)) != cudaSuccess ||
@@ -419,6 +457,10 @@ extern "C" vi_status vi_server_create(size_t mem_budget_bytes, int max_slots, vo
             return vi_fail(e == cudaErrorMemoryAllocation ? VI_ENOMEM : VI_ECUDA, "server slots: %s",
                            cudaGetErrorString(e));
         }
+    if ((e = prepare_sweep_batch()) != cudaSuccess || (e = prepare_server_helpers()) != cudaSuccess) {
+        vi_server_destroy(srv);
+        return vi_fail(VI_ECUDA, "server kernels: %s", cudaGetErrorString(e));
+    }
     {
         std::vector<int> sweep(n, MODE_SWEEP);
         if ((e = cudaMemcpy(srv->d_modes_sweep, sweep.data(), sizeof(int) * n, cudaMemcpyHostToDevice)) !=
@@ -428,8 +470,6 @@ extern "C" vi_status vi_server_create(size_t mem_budget_bytes, int max_slots, vo
         }
     }
     (void)stream;   // the server keeps its own streams so that its host loops never block the caller's
-    int dev = 0;
-    cudaGetDevice(&dev);
     srv->worker = std::thread([srv, dev]() {
         cudaSetDevice(dev);
         worker_loop(srv);
@@ -540,6 +580,7 @@ extern "C" vi_status vi_server_destroy(vi_server srv) {
     cudaFreeHost(srv->h_status);
     if (srv->stream) cudaStreamDestroy(srv->stream);
     if (srv->rstream) cudaStreamDestroy(srv->rstream);
+    if (srv->pool) cudaMemPoolDestroy(srv->pool);
     delete srv;
     return VI_OK;
 }
