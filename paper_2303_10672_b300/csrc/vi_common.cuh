@@ -125,7 +125,7 @@ __host__ __device__ inline bool lifo_key_ok(const ProdParams &P) { return P.L ==
 // FIFO: the rest path is kept per thread if a column of dmax+1 indices fits in
 // 64 KiB of shared memory for a block of 128 threads
 __host__ __device__ inline bool fifo_shared_ok(const ProdParams &P) {
-    return P.m >= 2 && (P.dmax + 1) * 128 * 4 <= 64 * 1024;
+    return P.m >= 2 && (P.dmax + 9) * 128 * 4 <= 64 * 1024;   // + 8 entries past the last k of a chunk
 }
 
 // order-preserving map double -> uint64 so that unsigned max/min give double max/min

@@ -73,6 +73,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
     float *colH = colT + G * kGroupThreads;
     uint32_t *colP = (uint32_t *)colT;
     int Rrest = 0;   // units in the rest slots (without the order when L = 1)
+    uint32_t tail_rel = 0;   // L >= 2, shared FIFO path: next-state index after all R units (without the order)
 
     float bh[XW], bl[XW];
     uint32_t argp[(XW + 3) / 4];   // best order per x, one byte each (G <= 256)
@@ -110,6 +111,14 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
             for (int e = 1; e < nP; ++e) {
                 walker_step(wp, P.cb, 0, (uint32_t)G);
                 cp[e * kGroupThreads] = wp.idx;
+            }
+            if (PAIR && LPIPE) {
+                // R does not depend on the order, so neither does the k range of this lane: past
+                // its last k the column points at the no-demand state, whose difference is
+                // exactly zero, and the chunk loop needs no clamp or mask
+                const int kend0 = min(ri.R - 1, dmax - x0);
+                if (ri.R <= dmax) tail_rel = cp[ri.R * kGroupThreads];
+                for (int k = max(kend0, 0) + 1; k <= max(kend0, 0) + 8; ++k) cp[k * kGroupThreads] = r;
             }
         }
         if (shared_lifo) {
@@ -247,17 +256,28 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                 // window of chunk k0 (k0 = 1 mod 4): p[x0 + k0 + i] = copy_o[x0 + k0 - o + i]
                 const int po = (x0 + 1) & 3;
                 const float *s_px = s_pc + po * pn4 + (x0 + 1 - po);   // + (k0 - 1) is a multiple of 4
+                constexpr bool preclamped = PAIR && LPIPE;   // with shared_fifo: see the column set-up
                 for (int k0 = 1; k0 <= kend; k0 += KW) {
                     uint32_t idx[KW];
+                    if (preclamped && shared_fifo) {
 #pragma unroll
-                    for (int j = 0; j < KW; ++j) idx[j] = index_of(min(k0 + j, kend));
+                        for (int j = 0; j < KW; ++j) idx[j] = colP[(k0 + j) * kGroupThreads] + atop;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < KW; ++j) idx[j] = index_of(min(k0 + j, kend));
+                    }
                     float g[KW];
                     if (PAIR) {
                         float2 raw[KW];
 #pragma unroll
                         for (int j = 0; j < KW; ++j) raw[j] = __ldg(V2 + idx[j]);
+                        if (preclamped && shared_fifo) {
 #pragma unroll
-                        for (int j = 0; j < KW; ++j) g[j] = (k0 + j <= kend) ? pair_diff(raw[j], ref) : 0.f;
+                            for (int j = 0; j < KW; ++j) g[j] = pair_diff(raw[j], ref);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < KW; ++j) g[j] = (k0 + j <= kend) ? pair_diff(raw[j], ref) : 0.f;
+                        }
                     } else {
 #pragma unroll
                         for (int j = 0; j < KW; ++j) g[j] = (k0 + j <= kend) ? __ldg(V1 + idx[j]) : 0.f;
@@ -285,7 +305,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                     }
                 }
                 if (R >= 1 && x0 + R <= dmax) {
-                    const float gR = value_of(index_of(R));
+                    const float gR = value_of((preclamped && shared_fifo) ? tail_rel + atop : index_of(R));
                     const float *s_tx = s_tab + P.off_tail + x0 + R;
 #pragma unroll
                     for (int xi = 0; xi < XW; ++xi) acc[xi] = fmaf(s_tx[xi], gR, acc[xi]);
@@ -500,7 +520,7 @@ inline size_t group_smem(const KernelParams &kp, int rb, int vk) {
     const size_t keyc =
         (vk == VK_PAIR && kp.issuing && lifo_key_ok(P) && lifo_shared_ok(P)) ? (size_t)P.G * kGroupThreads * 4 : 0;
     if (kp.issuing && lifo_shared_ok(P)) work = std::max(work, (size_t)(P.G + P.dmax + 1) * kGroupThreads * 4);
-    if (!kp.issuing && fifo_shared_ok(P)) work = std::max(work, (size_t)(P.dmax + 1) * kGroupThreads * 4);
+    if (!kp.issuing && fifo_shared_ok(P)) work = std::max(work, (size_t)(P.dmax + 9) * kGroupThreads * 4);
     const size_t pcopies = kp.issuing ? 0 : (size_t)4 * ((P.pn + 3) & ~3) * 4;
     return (size_t)((kp.n_tables + 3) & ~3) * 4 + pcopies + keyc + work + 16;
 }
