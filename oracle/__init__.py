@@ -77,6 +77,7 @@ def lib():
         L.orc_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_simulate.argtypes = [P, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_basestock_policy.argtypes = [P, C.c_int, C.c_void_p]
         _lib = L
     return _lib
 
@@ -183,6 +184,14 @@ class Problem:
             out["traj"] = traj
             out["demand"] = dem
         return out
+
+
+    def basestock_policy(self, S: int) -> np.ndarray:
+        """A = [S - I]^+ (I: stock on hand and in transit), capped at Q, for every state."""
+        pol = np.empty(self.n_states, np.uint8)
+        if lib().orc_basestock_policy(self.ref, int(S), _ptr(pol)) != 0:
+            raise RuntimeError("orc_basestock_policy failed")
+        return pol
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

@@ -467,3 +467,25 @@ int orc_simulate(const orc_problem *P, const uint8_t *policy, int n_rollouts, in
     }
     return 0;
 }
+
+/* Base-stock heuristic (Methods, Scenario A): A = [S - I]^+ with I the total
+ * stock on hand and in transit, i.e. the sum of all digits of the state. */
+int orc_basestock_policy(const orc_problem *P, int S, uint8_t *policy) {
+    if (!valid(P) || P->n_products != 1 || !policy || S < 0) return 1;
+    const long long n = orc_num_states(P);
+    const int G = P->Q[0] + 1;
+    const int K = (P->m[0] - 1) + (P->L[0] - 1);
+    for (long long s = 0; s < n; ++s) {
+        long long rem = s;
+        int stock = 0;
+        for (int k = 0; k < K; ++k) {
+            stock += (int)(rem % G);
+            rem /= G;
+        }
+        int a = S - stock;
+        if (a < 0) a = 0;
+        if (a > P->Q[0]) a = P->Q[0];
+        policy[s] = (uint8_t)a;
+    }
+    return 0;
+}

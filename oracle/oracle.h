@@ -83,6 +83,11 @@ int orc_policy_eval(const orc_problem *P, const uint8_t *policy, double tol, int
 /* Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
+/* Base-stock heuristic (Methods, Scenario A "Heuristic policies"): order up to
+ * S counting every unit on hand and in transit, A = [S - I]^+, capped at the
+ * largest order Q.  Single product; writes the action of every state. */
+int orc_basestock_policy(const orc_problem *P, int S, uint8_t *policy);
+
 /* Rollouts of a fixed policy from the all-zero state.  Period t of rollout r
  * draws Philox4x32-10(ctr = (t, r, 0, 0), key = (seed lo, seed hi)); word 0 gives
  * product-1 demand, word 1 product-2 demand, word 2 the substitution bits

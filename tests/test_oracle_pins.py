@@ -375,3 +375,42 @@ def test_ties_resolve_to_smallest_action():
     zero = workloads.single_product(2, 2, 3, (0, 0, 0, 0, 0), workloads.poisson_pmf(1.0, 4), 0.9, LIFO)
     r = oracle.Problem(zero).vi_solve(tol=1e-12, max_iters=10)
     assert (r["policy"] == 0).all() and (r["V"] == 0).all()
+
+
+# ---------------------------------------------------------------------------
+# base-stock heuristic (Methods, Scenario A: A = [S - I]^+, I on hand + in transit)
+# ---------------------------------------------------------------------------
+
+def test_basestock_policy_hand_worked_states():
+    """m = 3, L = 2, Q = 6 (G = 7): digits (X_1, X_2, P_1).  State (2, 1, 3) holds
+    6 units, so S = 10 orders 4, S = 5 orders 0; (0, 0, 0) with S = 9 orders the
+    cap Q = 6; (6, 6, 6) holds 18 units and never orders."""
+    inst = workloads.single_product(3, 2, 6, (1, 1, 1, 1, 0), workloads.poisson_pmf(2.0, 8), 0.9)
+    P = oracle.Problem(inst)
+    idx = lambda x1, x2, p1: x1 + 7 * x2 + 49 * p1
+    assert P.basestock_policy(10)[idx(2, 1, 3)] == 4
+    assert P.basestock_policy(5)[idx(2, 1, 3)] == 0
+    assert P.basestock_policy(9)[idx(0, 0, 0)] == 6
+    assert P.basestock_policy(6)[idx(6, 6, 6)] == 0
+
+
+def test_basestock_search_on_the_newsvendor_matches_value_iteration():
+    """m = L = 1 (one state, no stock carried): base-stock S orders S every day, so
+    the discounted return of H days has mean rbar(S) (1 - gamma^H) / (1 - gamma)
+    with rbar(S) = Q(0, S) - gamma V*(0).  Simulated means (common random
+    numbers) lie within 4 standard errors of it, and the best S is value
+    iteration's optimal order."""
+    inst = workloads.single_product(1, 1, 12, (3.0, 1.0, 5.0, 7.0, 0.0), workloads.poisson_pmf(5.0, 25), 0.9)
+    P = oracle.Problem(inst)
+    ref = P.vi_solve(tol=1e-10, max_iters=100000, stop_rule=1)
+    a_star = int(ref["policy"][0])
+    q = P.qvalues(ref["V"], 0)
+    g, H, n = inst.gamma, 60, 4000
+    means = []
+    for S in range(13):
+        out = P.simulate(P.basestock_policy(S), n, H, seed=11)
+        r = out["returns"]
+        expect = (q[S] - g * ref["V"][0]) * (1.0 - g ** H) / (1.0 - g)
+        assert abs(r.mean() - expect) <= 4.0 * r.std(ddof=1) / np.sqrt(n) + 1e-9, (S, r.mean(), expect)
+        means.append(r.mean())
+    assert int(np.argmax(means)) == a_star == 3
