@@ -350,6 +350,29 @@ def run_native(args):
                     "periods_per_s": ro["n_rollouts"] * ro["horizon"] / (r_ms * 1e-3),
                     "mean_return": float(rets.mean().item())}
 
+    # base-stock policy search (the paper's heuristic benchmark): every S in 0..Q,
+    # 4000 rollouts x 365 scored days after 100 warm-up days, shared random numbers;
+    # the value-iteration policy is scored on the same rollouts
+    policy_search = None
+    if len(inst.products) == 1:
+        n_r, H_s, W_s, seed_s = 4000, 365, 100, 4
+        Qp = inst.products[0].Q
+        ret_s = torch.empty((Qp + 1) * n_r, dtype=torch.float64, device="cuda")
+        vi.vi_basestock_search(h, 0, Qp, n_r, H_s, W_s, seed_s, ret_s, stream=stream)
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        means_s, best_s = vi.vi_basestock_search(h, 0, Qp, n_r, H_s, W_s, seed_s, ret_s, stream=stream)
+        b1.record(stream)
+        b1.synchronize()
+        bs_ms = b0.elapsed_time(b1)
+        rets_vi = torch.empty(n_r, dtype=torch.float64, device="cuda")
+        vi.vi_simulate(h, pol, n_r, H_s, W_s, seed_s, rets_vi, stream=stream)
+        policy_search = {"S_range": [0, Qp], "n_rollouts": n_r, "horizon": H_s, "warmup": W_s, "ms": bs_ms,
+                         "rollout_periods_per_s": (Qp + 1) * n_r * (H_s + W_s) / (bs_ms * 1e-3),
+                         "best_S": int(best_s), "best_mean_return": float(means_s[best_s]),
+                         "vi_policy_mean_return": float(rets_vi.mean().item())}
+
     # end to end through the public API with host buffers: create (tables H2D),
     # solve, V + policy D2H, destroy
     e2e_steps = max(1, min(args.steps, 5))
@@ -395,6 +418,7 @@ def run_native(args):
                                                                            "sample")},
             "serving": serving,
             "rollouts": rollouts,
+            "policy_search": policy_search,
             "wall_s": wall,
         }
         print(json.dumps(out))

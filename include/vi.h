@@ -241,6 +241,22 @@ vi_status vi_simulate(vi_handle h, const uint8_t *policy, int n_rollouts, int ho
                       int warmup, uint64_t seed, double *returns, double *kpis,
                       int32_t *traj, void *stream);
 
+/* Base-stock policy search by simulation (Methods, Scenario A heuristic policy:
+ * A = [S - I]^+ with I the total stock on hand and in transit; the paper scores
+ * every S in 0..A_max by its mean simulated return).  Single product.  For each
+ * S in s_lo..s_hi, n_rollouts rollouts from the all-zero state with `warmup`
+ * unscored periods then `horizon` scored ones, exactly as vi_simulate does with
+ * the policy A(s) = min([S - I(s)]^+, Q); every S uses the same random numbers
+ * (Philox counters (t, r)).
+ * returns: device double[(s_hi - s_lo + 1) * n_rollouts], row S - s_lo, column r
+ * (the caller's buffer).  mean_returns: host double[s_hi - s_lo + 1] or NULL;
+ * best_S: host int or NULL (the first S with the largest mean); when either is
+ * given the stream is synchronised and the means are summed in FP64 in rollout
+ * order.  Errors: VI_EINVAL (two products, bad sizes, dmax above the rollout
+ * limit), VI_ECUDA. */
+vi_status vi_basestock_search(vi_handle h, int s_lo, int s_hi, int n_rollouts, int horizon, int warmup,
+                              uint64_t seed, double *returns, double *mean_returns, int *best_S, void *stream);
+
 /* Continuous-batching solve server (no counterpart in the paper; it serves the
  * paper's value iteration to many callers).  Requests -- single-product
  * instances with 2 <= Q+1 <= 24 and at least one state digit, solved in

@@ -99,6 +99,8 @@ def lib() -> C.CDLL:
         "vi_backup_noalloc": ([C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                C.c_int, C.c_double, C.c_int, vp, vp, u8p, C.POINTER(C.c_double), vp], C.c_int),
         "vi_probe_l2_read": ([vp, C.c_size_t, C.c_int, vp, C.POINTER(C.c_float)], C.c_int),
+        "vi_basestock_search": ([H, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, vp,
+                                 C.POINTER(C.c_double), C.POINTER(C.c_int), vp], C.c_int),
         "vi_problem_kernel": ([H, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
         "vi_status_string": ([C.c_int], C.c_char_p),
         "vi_last_error": ([], C.c_char_p),
@@ -268,6 +270,18 @@ def vi_problem_kernel(h: int) -> tuple:
     k, w = C.c_int(), C.c_int()
     _check(lib().vi_problem_kernel(h, C.byref(k), C.byref(w)), "vi_problem_kernel")
     return k.value, w.value
+
+
+def vi_basestock_search(h: int, s_lo: int, s_hi: int, n_rollouts: int, horizon: int, warmup: int, seed: int,
+                        returns, stream=None):
+    """Mean return per order-up-to level S in s_lo..s_hi and the best S; per-rollout
+    returns land in the device buffer `returns` (row S - s_lo)."""
+    n_S = s_hi - s_lo + 1
+    means = (C.c_double * n_S)()
+    best = C.c_int()
+    _check(lib().vi_basestock_search(h, s_lo, s_hi, n_rollouts, horizon, warmup, C.c_uint64(seed), _addr(returns),
+                                     means, C.byref(best), _stream(stream)), "vi_basestock_search")
+    return np.array(list(means)), best.value
 
 
 def vi_probe_l2_read(buf, nbytes: int, reps: int, stream=None) -> float:

@@ -1034,3 +1034,44 @@ extern "C" vi_status vi_simulate(vi_handle h, const uint8_t *policy, int n_rollo
     CUDA_TRY(launch_rollouts(h->kp, rp, policy, returns, kpis, traj, (cudaStream_t)stream));
     return VI_OK;
 }
+
+extern "C" vi_status vi_basestock_search(vi_handle h, int s_lo, int s_hi, int n_rollouts, int horizon, int warmup,
+                                         uint64_t seed, double *returns, double *mean_returns, int *best_S,
+                                         void *stream) {
+    if (!h) return vi_fail(VI_EINVAL, "null handle");
+    const vi_problem_desc &d = h->desc;
+    if (d.n_products != 1) return vi_fail(VI_EINVAL, "the base-stock search takes single-product instances");
+    if (!returns || s_lo < 0 || s_hi < s_lo || n_rollouts < 1 || horizon < 0 || warmup < 0)
+        return vi_fail(VI_EINVAL, "bad search arguments");
+    if (d.dmax[0] > kMaxRollDmax) return vi_fail(VI_EINVAL, "rollouts need dmax <= %d", kMaxRollDmax);
+    const int n_S = s_hi - s_lo + 1;
+    if ((long long)n_S * n_rollouts > (1ll << 31)) return vi_fail(VI_EINVAL, "too many (S, rollout) pairs");
+    RollParams rp;
+    memset(&rp, 0, sizeof(rp));
+    rp.n_rollouts = n_rollouts;
+    rp.horizon = horizon;
+    rp.warmup = warmup;
+    rp.seed = seed;
+    for (int j = 0; j < 5; ++j) rp.cost[0][j] = d.cost[0][j];
+    make_thresholds(h->pmf[0], rp.thr[0]);
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(launch_basestock(h->kp, rp, s_lo, n_S, returns, s));
+    if (!mean_returns && !best_S) return VI_OK;
+    std::vector<double> host((size_t)n_S * n_rollouts);
+    CUDA_TRY(cudaMemcpyAsync(host.data(), returns, host.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    int best = s_lo;
+    double best_mean = -INFINITY;
+    for (int i = 0; i < n_S; ++i) {
+        double sum = 0.0;   // rollout order, FP64
+        for (int r = 0; r < n_rollouts; ++r) sum += host[(size_t)i * n_rollouts + r];
+        const double mean = sum / (double)n_rollouts;
+        if (mean_returns) mean_returns[i] = mean;
+        if (mean > best_mean) {
+            best_mean = mean;
+            best = s_lo + i;
+        }
+    }
+    if (best_S) *best_S = best;
+    return VI_OK;
+}

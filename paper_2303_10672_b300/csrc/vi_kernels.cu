@@ -538,6 +538,19 @@ __device__ __forceinline__ int draw_demand(uint32_t w, const unsigned long long 
     return d;
 }
 
+// one period of a single product: reward (FP64, unfused, in the oracle's order) and outcome
+__device__ __forceinline__ double single_period(const ProdParams &P1, int lifo, const RollParams &rp, uint32_t s, int a,
+                                                int d1, RollOut &o) {
+    o = roll_product(P1, lifo, s, a, d1);
+    double rew = 0.0;
+    rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][0], (double)a));
+    rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][1], (double)o.carried));
+    rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][2], (double)o.shortage));
+    rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][3], (double)o.wasted));
+    rew = __dadd_rn(rew, __dmul_rn(rp.cost[0][4], (double)o.issued));
+    return rew;
+}
+
 __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *policy, double *returns, double *kpis,
                                int32_t *traj) {
     __shared__ unsigned long long s_thr[2][kMaxRollDmax + 1];
@@ -563,12 +576,8 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
         uint32_t s_next;
         if (kp.n_products == 1) {
             const int d1 = draw_demand(w[0], s_thr[0], P1.dmax);
-            const RollOut o = roll_product(P1, lifo, s, a, d1);
-            rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][0], (double)a));
-            rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][1], (double)o.carried));
-            rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][2], (double)o.shortage));
-            rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][3], (double)o.wasted));
-            rew = __dadd_rn(rew, __dmul_rn(rp.cost[0][4], (double)o.issued));
+            RollOut o;
+            rew = single_period(P1, lifo, rp, s, a, d1, o);
             s_next = o.s_next;
             t_dem = d1;
             t_iss = o.issued;
@@ -625,6 +634,55 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
         kpis[3 * r + 1] = arr > 0.0 ? __ddiv_rn(__dmul_rn(100.0, was), arr) : 0.0;
         kpis[3 * r + 2] = rp.horizon > 0 ? __ddiv_rn(car, (double)rp.horizon) : 0.0;
     }
+}
+
+// ===========================================================================
+// base-stock policy search (Methods, Scenario A heuristic): thread = (S, rollout);
+// A = min([S - I]^+, Q) with I the units on hand and in transit (the sum of the
+// state's digits).  Every S sees the same demands (Philox counters (t, r)).
+// ===========================================================================
+__global__ void basestock_kernel(KernelParams kp, RollParams rp, int s_lo, int n_S, double *returns) {
+    __shared__ unsigned long long s_thr[kMaxRollDmax + 1];
+    for (int i = threadIdx.x; i <= kMaxRollDmax; i += blockDim.x) s_thr[i] = rp.thr[0][i];
+    __syncthreads();
+    const long long t_id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t_id >= (long long)n_S * rp.n_rollouts) return;
+    const int S = s_lo + (int)(t_id / rp.n_rollouts);
+    const int r = (int)(t_id % rp.n_rollouts);
+    const ProdParams &P1 = kp.p[0];
+    const int lifo = kp.issuing;
+    const uint32_t k0 = (uint32_t)(rp.seed & 0xffffffffull), k1 = (uint32_t)(rp.seed >> 32);
+    uint32_t s = 0;
+    double ret = 0.0, disc = 1.0;
+    for (int t = 0; t < rp.warmup + rp.horizon; ++t) {
+        uint32_t w[4];
+        philox4x32_10((uint32_t)t, (uint32_t)r, 0u, 0u, k0, k1, w);
+        int stock = 0;
+        uint32_t rem = s;
+        for (int k = 0; k < P1.K; ++k) {
+            const uint32_t q = rem / (uint32_t)P1.G;
+            stock += (int)(rem - q * (uint32_t)P1.G);
+            rem = q;
+        }
+        const int a = min(max(S - stock, 0), P1.Q);
+        const int d1 = draw_demand(w[0], s_thr, P1.dmax);
+        RollOut o;
+        const double rew = single_period(P1, lifo, rp, s, a, d1, o);
+        if (t >= rp.warmup) {
+            ret = __dadd_rn(ret, __dmul_rn(disc, rew));
+            disc = __dmul_rn(disc, kp.gamma);
+        }
+        s = o.s_next;
+    }
+    returns[t_id] = ret;
+}
+
+cudaError_t launch_basestock(const KernelParams &kp, const RollParams &rp, int s_lo, int n_S, double *returns,
+                             cudaStream_t stream) {
+    const long long n = (long long)n_S * rp.n_rollouts;
+    const int threads = 128;
+    basestock_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, stream>>>(kp, rp, s_lo, n_S, returns);
+    return cudaGetLastError();
 }
 
 // ===========================================================================

@@ -81,6 +81,8 @@ struct SlotStatus {
 cudaError_t launch_gather_status(SolveState *const *sts, int n, SlotStatus *out, cudaStream_t stream);
 int group_width_candidates(int G, int *out, int max_out);
 cudaError_t describe_solve_init(uint32_t n, LaunchDesc &d);
+cudaError_t launch_basestock(const KernelParams &kp, const RollParams &rp, int s_lo, int n_S, double *returns,
+                             cudaStream_t stream);
 cudaError_t launch_rollouts(const KernelParams &kp, const RollParams &rp, const uint8_t *policy,
                             double *returns, double *kpis, int32_t *traj, cudaStream_t stream);
 
