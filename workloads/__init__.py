@@ -49,6 +49,19 @@ def negbin_pmf(mean: float, var: float, dmax: int) -> np.ndarray:
     return folded_pmf(stats.nbinom(n, p), dmax)
 
 
+def gamma_discretised_pmf(mean: float, sd: float, dmax: int) -> np.ndarray:
+    """Gamma demand rounded to the nearest integer (Scenario A appendix): P(D = d) =
+    F(d + 1/2) - F(d - 1/2) for d < dmax and 1 - F(dmax - 1/2) on dmax, F = 0 below 0;
+    shape (mean/sd)^2, scale sd^2/mean."""
+    dist = stats.gamma(a=(mean / sd) ** 2, scale=sd * sd / mean)
+    F = lambda x: np.where(x <= 0.0, 0.0, dist.cdf(np.maximum(x, 0.0)))
+    d = np.arange(dmax, dtype=np.float64)
+    p = np.empty(dmax + 1, dtype=np.float64)
+    p[:dmax] = F(d + 0.5) - F(d - 0.5)
+    p[dmax] = 1.0 - F(dmax - 0.5)
+    return p
+
+
 @dataclasses.dataclass
 class Product:
     m: int                      # maximum useful life (periods)
@@ -160,6 +173,24 @@ def config4() -> Instance:
 
 
 CONFIG4_ROLLOUTS = dict(n_rollouts=4096, horizon=365, seed=4)
+
+
+# The paper's Scenario A (de Moor et al. settings, Scenario A appendix): the state
+# holds X_1..X_m (X_m arrived at the start of the day) and L-1 orders in transit,
+# m + L - 1 digits in all.  X_m is available before the day's demand, exactly as
+# the arrival slot P_1 of this library's state with lead time L + 1, and the
+# reward has no revenue term.  Dmax 100, Amax 10, Cv 3, Ch 1, Cs 5, mean demand 4
+# with coefficient of variation sigma/mu = 0.5, gamma 0.99, sup-norm test 1e-4.
+SCENARIO_A = dict(dmax=100, q=10, c_v=3.0, c_h=1.0, c_s=5.0, mean=4.0, cv=0.5, gamma=0.99, eps=1e-4)
+SCENARIO_A_ROLLOUTS = dict(n_rollouts=10_000, horizon=365, warmup=100)
+
+
+def scenario_a(m: int, L: int, c_w: float, issuing: int) -> Instance:
+    """Scenario A experiment (m, L, C_w, issuing) in this library's state convention."""
+    a = SCENARIO_A
+    pmf = gamma_discretised_pmf(a["mean"], a["cv"] * a["mean"], a["dmax"])
+    return single_product(m, L + 1, a["q"], (a["c_v"], a["c_h"], a["c_s"], c_w, 0.0), pmf, a["gamma"], issuing,
+                          name=f"scenA_m{m}L{L}Cw{int(c_w)}{'LIFO' if issuing else 'FIFO'}", precision="fp32")
 
 
 @dataclasses.dataclass
