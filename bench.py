@@ -397,6 +397,7 @@ def run_native(args):
     d2h = n * sizes["value_bytes"] + n
 
     out = None
+    paper_a = run_paper_scenario_a(vi, torch, stream) if rank == 0 else None
     serving = run_serving(args.serving) if (args.serving > 0 and rank == 0) else None
     if rank == 0:
         cpu = oracle_sample_rate(inst, args.cpu_seconds) if args.cpu_seconds > 0 else None
@@ -419,6 +420,7 @@ def run_native(args):
             "serving": serving,
             "rollouts": rollouts,
             "policy_search": policy_search,
+            "paper_scenario_a": paper_a,
             "wall_s": wall,
         }
         print(json.dumps(out))
@@ -427,6 +429,37 @@ def run_native(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return out
+
+
+def run_paper_scenario_a(vi, torch, stream) -> dict:
+    """The paper's largest Scenario A experiment (m = 5, L = 2, FIFO, C_w = 7; Table 3
+    row 5/6): value iteration with the paper's sup-norm test, then its 10,000-rollout
+    evaluation, against the printed return and value-iteration wall time."""
+    inst = workloads.scenario_a(5, 2, 7.0, workloads.FIFO)
+    A, RO = workloads.SCENARIO_A, workloads.SCENARIO_A_ROLLOUTS
+    p = inst.products[0]
+    desc, keep = vi.make_desc([dict(m=p.m, L=p.L, Q=p.Q, cost=p.cost, pmf=p.pmf)], inst.gamma, inst.issuing,
+                              vi.VI_PREC_FP32, vi.VI_STOP_SUPNORM)
+    h = vi.vi_problem_create_desc(desc)
+    n = vi.vi_problem_sizes(h)["n_states"]
+    V = torch.empty(n, dtype=torch.float64, device="cuda")
+    pol = torch.empty(n, dtype=torch.uint8, device="cuda")
+    vi.vi_solve(h, A["eps"], 100000, V, pol, stream=stream)          # warm-up (autotune, graph)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    info = vi.vi_solve(h, A["eps"], 100000, V, pol, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    solve_ms = e0.elapsed_time(e1)
+    ret = torch.empty(RO["n_rollouts"], dtype=torch.float64, device="cuda")
+    vi.vi_simulate(h, pol, RO["n_rollouts"], RO["horizon"], RO["warmup"], 2023, ret, stream=stream)
+    r = ret.cpu().numpy()
+    vi.vi_problem_destroy(h)
+    return {"experiment": "Scenario A, m=5, L=2, FIFO, C_w=7 (Table 3)", "states": n, "iterations": info["iters"],
+            "vi_solve_ms": solve_ms, "paper_vi_wall_s": 1185.0,
+            "return_mean": float(r.mean()), "return_sd": float(r.std(ddof=1)),
+            "paper_return_mean": -1432.0, "paper_return_sd": 55.0}
 
 
 def run_serving(n_requests: int = 512, seed: int = 5, slots: int = 64, budget_gb: float = 64.0) -> dict:
