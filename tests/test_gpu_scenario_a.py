@@ -35,3 +35,41 @@ def test_scenario_a_returns_match_table3(row):
     se = np.hypot(r.std(ddof=1), row["vi_return_sd"]) / np.sqrt(RO["n_rollouts"])
     assert abs(r.mean() - row["vi_return_mean"]) <= 4.0 * se + 0.5, (r.mean(), row["vi_return_mean"])
     assert abs(r.std(ddof=1) - row["vi_return_sd"]) <= 3.0
+
+
+def _kpi_close(got, printed, n):
+    mean, sd = printed
+    se = np.hypot(got.std(ddof=1), sd) / np.sqrt(n)
+    return abs(got.mean() - mean) <= 4.0 * se + 0.05
+
+
+@pytest.mark.parametrize("row", ROWS, ids=[f"m{r['m']}e{r['exp']}" for r in ROWS])
+def test_scenario_a_kpis_and_base_stock_match_the_paper(row):
+    """GPU rollouts: the value-iteration policy's KPIs (appendix KPI table); the GPU
+    base-stock search over S = 0..A_max (4,000 rollouts x 365 days after 100
+    warm-up days) finds a level whose mean return is within noise of the paper's
+    S_best, and S_best's own return matches Table 3's simulation-optimisation one."""
+    inst = workloads.scenario_a(row["m"], row["L"], row["c_w"],
+                                workloads.LIFO if row["issuing"] == "LIFO" else workloads.FIFO)
+    A, RO = workloads.SCENARIO_A, workloads.SCENARIO_A_ROLLOUTS
+    n = RO["n_rollouts"]
+    with Handle(inst, precision="fp32", stop_rule=vi.VI_STOP_SUPNORM) as H:
+        V, pol, info = H.solve(A["eps"], 100000)
+        ret = torch.empty(n, dtype=torch.float64, device="cuda")
+        kpis = torch.empty(3 * n, dtype=torch.float64, device="cuda")
+        vi.vi_simulate(H.h, pol, n, RO["horizon"], RO["warmup"], 2023, ret, kpis)
+        k = kpis.cpu().numpy().reshape(n, 3)
+        assert _kpi_close(k[:, 0], row["service_vi"], n)
+        assert _kpi_close(k[:, 1], row["wastage_vi"], n)
+        assert _kpi_close(k[:, 2], row["holding_vi"], n)
+        ns = 4000
+        grid = torch.empty(11 * ns, dtype=torch.float64, device="cuda")
+        means, best = vi.vi_basestock_search(H.h, 0, 10, ns, 365, 100, 7, grid)
+        g = grid.cpu().numpy().reshape(11, ns)
+        d = g[best] - g[row["s_best"]]          # shared random numbers: the paired difference
+        assert best == row["s_best"] or abs(d.mean()) <= 4.0 * d.std(ddof=1) / np.sqrt(ns)
+        so = torch.empty(n, dtype=torch.float64, device="cuda")
+        vi.vi_basestock_search(H.h, row["s_best"], row["s_best"], n, RO["horizon"], RO["warmup"], 2023, so)
+        r = so.cpu().numpy()
+    se = np.hypot(r.std(ddof=1), row["so_return_sd"]) / np.sqrt(n)
+    assert abs(r.mean() - row["so_return_mean"]) <= 4.0 * se + 0.5, (r.mean(), row["so_return_mean"])

@@ -453,3 +453,36 @@ def test_scenario_a_m2_returns_match_table3(row):
     se = np.hypot(ret.std(ddof=1), row["vi_return_sd"]) / np.sqrt(RO["n_rollouts"])
     assert abs(ret.mean() - row["vi_return_mean"]) <= 4.0 * se + 0.5, (ret.mean(), row["vi_return_mean"])
     assert abs(ret.std(ddof=1) - row["vi_return_sd"]) <= 3.0
+
+
+def _kpi_close(got: np.ndarray, printed, n: int) -> bool:
+    """Printed mean +- sd (1 decimal): agreement within 4 standard errors of the
+    difference plus the printed rounding."""
+    mean, sd = printed
+    se = np.hypot(got.std(ddof=1), sd) / np.sqrt(n)
+    return abs(got.mean() - mean) <= 4.0 * se + 0.05
+
+
+@pytest.mark.parametrize("row", [r for r in _TABLE3 if r["m"] == 2],
+                         ids=[f"m2e{r['exp']}" for r in _TABLE3 if r["m"] == 2])
+def test_scenario_a_m2_kpis_and_base_stock_match_the_paper(row):
+    """The value-iteration policy's service level, wastage and holding (appendix KPI
+    table), the best order-up-to level found by simulating every S = 0..A_max
+    (4,000 rollouts x 365 days after 100 warm-up days, shared random numbers), and
+    that level's evaluated return (Table 3, simulation optimisation)."""
+    inst = _scen_a(row)
+    P = oracle.Problem(inst)
+    A, RO = workloads.SCENARIO_A, workloads.SCENARIO_A_ROLLOUTS
+    n = RO["n_rollouts"]
+    ref = P.vi_solve(tol=A["eps"], max_iters=100000, stop_rule=1)
+    k = P.simulate(ref["policy"], n, RO["horizon"], seed=2023, warmup=RO["warmup"])["kpis"]
+    assert _kpi_close(k[:, 0], row["service_vi"], n)
+    assert _kpi_close(k[:, 1], row["wastage_vi"], n)
+    assert _kpi_close(k[:, 2], row["holding_vi"], n)
+    means = [P.simulate(P.basestock_policy(S), 4000, 365, seed=7, warmup=100)["returns"].mean() for S in range(11)]
+    assert int(np.argmax(means)) == row["s_best"]
+    so = P.simulate(P.basestock_policy(row["s_best"]), n, RO["horizon"], seed=2023, warmup=RO["warmup"])
+    r = so["returns"]
+    se = np.hypot(r.std(ddof=1), row["so_return_sd"]) / np.sqrt(n)
+    assert abs(r.mean() - row["so_return_mean"]) <= 4.0 * se + 0.5
+    assert _kpi_close(so["kpis"][:, 0], row["service_so"], n)
