@@ -231,8 +231,9 @@ vi_status vi_next_states(vi_handle h, const uint32_t *states, int n, uint32_t *o
  * (seed low 32 bits, seed high 32 bits); word 0 is turned into product-1
  * demand by the integer inverse CDF (smallest d with word < floor(2^32 CDF(d)),
  * CDF summed in ascending order in FP64), word 1 into product-2 demand, and
- * the popcount of the low `shortfall` bits of word 2 gives the accepted
- * substitutions (two products need subst_rate = 1/2).  The first `warmup`
+ * the popcount of the low `shortfall` bits of the 64-bit word (word 3, word 2)
+ * gives the accepted substitutions (two products need subst_rate = 1/2; a
+ * shortfall above 64 uses all 64 bits).  The first `warmup`
  * periods are simulated but not scored.  policy: device uint8[|S|];
  * returns: device double[n] = sum_t gamma^t r_t (FP64, in period order);
  * kpis: device double[3n] or NULL = {service %, wastage %, mean units carried};

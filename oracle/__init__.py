@@ -48,6 +48,8 @@ class _Step(C.Structure):
         ("s_next", C.c_longlong), ("reward", C.c_double), ("demand", C.c_double),
         ("issued", C.c_double), ("wasted", C.c_double), ("carried", C.c_double),
         ("arrived", C.c_double), ("shortage", C.c_double), ("unmet1", C.c_int),
+        ("demand_k", C.c_double * 2), ("issued_k", C.c_double * 2), ("wasted_k", C.c_double * 2),
+        ("carried_k", C.c_double * 2), ("arrived_k", C.c_double * 2), ("sub_served", C.c_int),
     ]
 
 
@@ -77,7 +79,12 @@ def lib():
         L.orc_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_simulate.argtypes = [P, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_simulate_ex.argtypes = [P, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_basestock_policy.argtypes = [P, C.c_int, C.c_void_p]
+        L.orc_issued_pmf.argtypes = [P, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p]
+        L.orc_mbs_simulate.argtypes = [P, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                       C.c_uint64, C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
 
@@ -120,7 +127,21 @@ class Problem:
         rc = lib().orc_transition(self.ref, s, a, d1, d2, u, C.byref(out))
         if rc != 0:
             raise ValueError("invalid outcome")
-        return {f: getattr(out, f) for f, _ in _Step._fields_}
+        res = {}
+        for f, _ in _Step._fields_:
+            v = getattr(out, f)
+            res[f] = list(v) if f.endswith("_k") else v
+        return res
+
+    def issued_pmf(self, s: int, a: int) -> np.ndarray:
+        """P(h1, h2 | s, a) from the Scenario B five-case formula; (T1+1) x (T2+1)."""
+        T = np.zeros(2, np.int32)
+        p1, p2 = self.inst.products
+        buf = np.zeros((p1.m * p1.Q + 1) * (p2.m * p2.Q + 1), np.float64)
+        if lib().orc_issued_pmf(self.ref, s, a, _ptr(buf), _ptr(T)) != 0:
+            raise RuntimeError("orc_issued_pmf failed")
+        n1, n2 = int(T[0]) + 1, int(T[1]) + 1
+        return buf[: n1 * n2].reshape(n1, n2).copy()
 
     def qvalues(self, V: np.ndarray, s: int) -> np.ndarray:
         V = np.ascontiguousarray(V, np.float64)
@@ -173,18 +194,33 @@ class Problem:
         policy = np.ascontiguousarray(policy, np.uint8)
         ret = np.empty(n_rollouts, np.float64)
         kpis = np.empty((n_rollouts, 3), np.float64)
+        kprod = np.empty((n_rollouts, 2, 3), np.float64)
         traj = np.empty((n_rollouts, horizon), np.int32) if with_traj else None
         dem = np.empty((n_rollouts, horizon), np.int32) if with_traj else None
-        rc = lib().orc_simulate(self.ref, _ptr(policy), n_rollouts, horizon, warmup,
-                                C.c_uint64(seed), _ptr(ret), _ptr(kpis), _ptr(traj), _ptr(dem))
+        rc = lib().orc_simulate_ex(self.ref, _ptr(policy), n_rollouts, horizon, warmup,
+                                   C.c_uint64(seed), _ptr(ret), _ptr(kpis), _ptr(kprod), _ptr(traj),
+                                   _ptr(dem))
         if rc != 0:
             raise RuntimeError("orc_simulate failed")
-        out = dict(returns=ret, kpis=kpis)
+        out = dict(returns=ret, kpis=kpis, kpis_prod=kprod)
         if with_traj:
             out["traj"] = traj
             out["demand"] = dem
         return out
 
+
+    def mbs_simulate(self, S, mu, n_rollouts: int, horizon: int, seed: int, warmup: int = 0,
+                     cap: bool = False) -> dict:
+        """Modified base-stock rollouts: order [S_k - I_k + [X_1k - mu_k]^+]^+ per product."""
+        Sv = np.ascontiguousarray(list(S) + [0] * (2 - len(S)), np.int32)
+        mv = np.ascontiguousarray(list(mu) + [0] * (2 - len(mu)), np.int32)
+        ret = np.empty(n_rollouts, np.float64)
+        kprod = np.empty((n_rollouts, 2, 3), np.float64)
+        rc = lib().orc_mbs_simulate(self.ref, _ptr(Sv), _ptr(mv), int(bool(cap)), n_rollouts, horizon,
+                                    warmup, C.c_uint64(seed), _ptr(ret), _ptr(kprod))
+        if rc != 0:
+            raise RuntimeError("orc_mbs_simulate failed")
+        return dict(returns=ret, kpis_prod=kprod)
 
     def basestock_policy(self, S: int) -> np.ndarray:
         """A = [S - I]^+ (I: stock on hand and in transit), capped at Q, for every state."""

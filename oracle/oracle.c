@@ -30,6 +30,7 @@
 
 #define MAXDIG 48
 
+static int valid(const orc_problem *P);
 static int ipos(int x) { return x > 0 ? x : 0; }
 static int imin(int a, int b) { return a < b ? a : b; }
 
@@ -163,6 +164,14 @@ int orc_transition(const orc_problem *P, long long s, int a, int d1, int d2, int
         out->arrived = o.arrived;
         out->shortage = o.shortage;
         out->unmet1 = o.shortage;
+        out->demand_k[0] = d1;
+        out->issued_k[0] = o.issued;
+        out->wasted_k[0] = o.wasted;
+        out->carried_k[0] = o.carried;
+        out->arrived_k[0] = o.arrived;
+        out->demand_k[1] = out->issued_k[1] = out->wasted_k[1] = 0.0;
+        out->carried_k[1] = out->arrived_k[1] = 0.0;
+        out->sub_served = 0;
         return 0;
     }
     long long S1 = product_states(P, 0);
@@ -200,6 +209,95 @@ int orc_transition(const orc_problem *P, long long s, int a, int d1, int d2, int
     out->arrived = o1.arrived + o2.arrived;
     out->shortage = short1 + short2;
     out->unmet1 = unmet1;
+    out->demand_k[0] = d1;
+    out->demand_k[1] = d2;
+    out->issued_k[0] = o1.issued;
+    out->issued_k[1] = o2.issued;
+    out->wasted_k[0] = o1.wasted;
+    out->wasted_k[1] = o2.wasted;
+    out->carried_k[0] = o1.carried;
+    out->carried_k[1] = o2.carried;
+    out->arrived_k[0] = o1.arrived;
+    out->arrived_k[1] = o2.arrived;
+    out->sub_served = sub_served;
+    return 0;
+}
+
+/* Units available to product k this period for action a_k: the stock slots plus
+ * the arrival (P_1 when L >= 2, else the order itself). */
+static int units_available(const orc_problem *P, int k, long long sk, int ak) {
+    prod_out o;
+    product_step(P->m[k], P->L[k], P->Q[k], P->issuing, sk, ak, 0, &o);
+    return o.total;
+}
+
+/* Scenario B appendix, issued-units outcome set.  Read with product 1 = B and
+ * product 2 = A:
+ *   P(h1, h2) = 0                                   h1 > I1 or h2 > I2
+ *             = P(D1 = h1) P(D2 = h2)               h1 < I1, h2 < I2
+ *             = P(D1 = h1) P(D2 >= I2)              h1 < I1, h2 = I2
+ *             = P(Dz = h2) P(D1 >= I1)              h1 = I1, h2 < I2
+ *             = (1 - sum_{d < I2} P(Dz = d)) P(D1 >= I1)   h1 = I1, h2 = I2
+ * with Dz = D2 + Du the product-2 demand including substitutes, and Du the
+ * substituting part of the product-1 shortfall c = D1 - I1 given D1 >= I1:
+ *   P(Du = x) = sum_{c >= x} P(D1 = c + I1) Bin(x; c, rho) / P(D1 >= I1).
+ * The printed series for Du omits the division by P(D1 >= I1); without it the
+ * five cases would not sum to one, so it is read as the conditional law. */
+int orc_issued_pmf(const orc_problem *P, long long s, int a, double *out, int T_out[2]) {
+    if (!valid(P) || P->n_products != 2) return 1;
+    ensure_binom(P);
+    long long S1 = product_states(P, 0);
+    long long s1 = s % S1, s2 = s / S1;
+    int A2 = P->Q[1] + 1;
+    int a1 = a / A2, a2 = a % A2;
+    const int I1 = units_available(P, 0, s1, a1);
+    const int I2 = units_available(P, 1, s2, a2);
+    const double *p1 = P->pmf[0], *p2 = P->pmf[1];
+    const int D1 = P->dmax[0], D2 = P->dmax[1];
+#define PD1(d) (((d) >= 0 && (d) <= D1) ? p1[(d)] : 0.0)
+#define PD2(d) (((d) >= 0 && (d) <= D2) ? p2[(d)] : 0.0)
+    double ge1 = 0.0, ge2 = 0.0;   /* P(D1 >= I1), P(D2 >= I2) */
+    for (int d = I1; d <= D1; ++d) ge1 += PD1(d);
+    for (int d = I2; d <= D2; ++d) ge2 += PD2(d);
+    /* P(Du = x | D1 >= I1) for x = 0..D1 - I1, then P(Dz = z) for z < I2 */
+    int nu = D1 - I1 + 1;
+    if (nu < 1) nu = 1;
+    double *du = (double *)calloc((size_t)nu, sizeof(double));
+    double *dz = (double *)calloc((size_t)(I2 + 1), sizeof(double));
+    if (!du || !dz) { free(du); free(dz); return 2; }
+    if (ge1 > 0.0) {
+        for (int x = 0; x < nu; ++x) {
+            double acc = 0.0;
+            for (int c = x; c + I1 <= D1; ++c) acc += PD1(c + I1) * binom_pmf(c, x, P->rho);
+            du[x] = acc / ge1;
+        }
+    }
+    for (int z = 0; z <= I2; ++z) {
+        double acc = 0.0;
+        for (int k = 0; k <= z; ++k) acc += PD2(k) * ((z - k) < nu ? du[z - k] : 0.0);
+        dz[z] = acc;
+    }
+    for (int h1 = 0; h1 <= I1; ++h1)
+        for (int h2 = 0; h2 <= I2; ++h2) {
+            double v;
+            if (h1 < I1 && h2 < I2) {
+                v = PD1(h1) * PD2(h2);
+            } else if (h1 < I1) {
+                v = PD1(h1) * ge2;
+            } else if (h2 < I2) {
+                v = dz[h2] * ge1;
+            } else {
+                double below = 0.0;
+                for (int d = 0; d < I2; ++d) below += dz[d];
+                v = (1.0 - below) * ge1;
+            }
+            out[(long long)h1 * (I2 + 1) + h2] = v;
+        }
+#undef PD1
+#undef PD2
+    free(du);
+    free(dz);
+    if (T_out) { T_out[0] = I1; T_out[1] = I2; }
     return 0;
 }
 
@@ -415,9 +513,39 @@ static int popcount32(uint32_t x) {
     return c;
 }
 
+/* per-product KPI sums of one rollout */
+typedef struct {
+    double dem[2], served[2], was[2], arr[2], car[2];
+} kpi_sums;
+
+static void kpi_sums_finish(const kpi_sums *k, int horizon, double *out6) {
+    for (int j = 0; j < 2; ++j) {
+        out6[3 * j + 0] = k->dem[j] > 0.0 ? 100.0 * k->served[j] / k->dem[j] : 100.0;
+        out6[3 * j + 1] = k->arr[j] > 0.0 ? 100.0 * k->was[j] / k->arr[j] : 0.0;
+        out6[3 * j + 2] = horizon > 0 ? k->car[j] / (double)horizon : 0.0;
+    }
+}
+
+/* the substituting customers among n: popcount of the low n bits of the 64-bit
+ * word (word 3, word 2) -- bits 0..31 from word 2, bits 32..63 from word 3 */
+static int substitutes(uint32_t w2, uint32_t w3, int n) {
+    const int lo = n < 32 ? n : 32;
+    const int hi = n > 64 ? 32 : (n > 32 ? n - 32 : 0);
+    const uint32_t mlo = (lo >= 32) ? 0xffffffffu : ((1u << lo) - 1u);
+    const uint32_t mhi = (hi >= 32) ? 0xffffffffu : ((1u << hi) - 1u);
+    return popcount32(w2 & mlo) + popcount32(w3 & mhi);
+}
+
 int orc_simulate(const orc_problem *P, const uint8_t *policy, int n_rollouts, int horizon,
                  int warmup, uint64_t seed, double *returns, double *kpis, int32_t *traj,
                  int32_t *demand_out) {
+    return orc_simulate_ex(P, policy, n_rollouts, horizon, warmup, seed, returns, kpis, NULL, traj,
+                           demand_out);
+}
+
+int orc_simulate_ex(const orc_problem *P, const uint8_t *policy, int n_rollouts, int horizon,
+                    int warmup, uint64_t seed, double *returns, double *kpis, double *kpis_prod,
+                    int32_t *traj, int32_t *demand_out) {
     if (!valid(P)) return 1;
     if (P->n_products == 2 && P->rho != 0.5) return 1;
     uint64_t thr0[512], thr1[512];
@@ -429,6 +557,8 @@ int orc_simulate(const orc_problem *P, const uint8_t *policy, int n_rollouts, in
         long long s = 0;
         double ret = 0.0, disc = 1.0;
         double dem = 0.0, iss = 0.0, was = 0.0, arr = 0.0, car = 0.0;
+        kpi_sums ks;
+        memset(&ks, 0, sizeof(ks));
         for (int t = 0; t < warmup + horizon; ++t) {
             uint32_t ctr[4] = {(uint32_t)t, (uint32_t)r, 0u, 0u}, w[4];
             orc_philox4x32_10(ctr, key, w);
@@ -439,9 +569,7 @@ int orc_simulate(const orc_problem *P, const uint8_t *policy, int n_rollouts, in
             if (P->n_products == 2) {
                 d2 = draw_demand(w[1], thr1, P->dmax[1]);
                 orc_transition(P, s, a, d1, d2, 0, &st);
-                int n = st.unmet1;
-                uint32_t mask = (n >= 32) ? 0xffffffffu : ((1u << n) - 1u);
-                u = popcount32(w[2] & mask);
+                u = substitutes(w[2], w[3], st.unmet1);
             }
             orc_transition(P, s, a, d1, d2, u, &st);
             if (t >= warmup) {
@@ -455,6 +583,15 @@ int orc_simulate(const orc_problem *P, const uint8_t *policy, int n_rollouts, in
                 was += st.wasted;
                 arr += st.arrived;
                 car += st.carried;
+                ks.dem[0] += st.demand_k[0];
+                ks.dem[1] += st.demand_k[1];
+                ks.served[0] += st.issued_k[0] + (double)st.sub_served;
+                ks.served[1] += st.issued_k[1] - (double)st.sub_served;
+                for (int j = 0; j < 2; ++j) {
+                    ks.was[j] += st.wasted_k[j];
+                    ks.arr[j] += st.arrived_k[j];
+                    ks.car[j] += st.carried_k[j];
+                }
             }
             s = st.s_next;
         }
@@ -464,6 +601,140 @@ int orc_simulate(const orc_problem *P, const uint8_t *policy, int n_rollouts, in
             kpis[3 * r + 1] = arr > 0.0 ? 100.0 * was / arr : 0.0;
             kpis[3 * r + 2] = horizon > 0 ? car / (double)horizon : 0.0;
         }
+        if (kpis_prod) kpi_sums_finish(&ks, horizon, kpis_prod + 6 * (long long)r);
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Modified base-stock heuristic on plain stock vectors.  One product, one
+ * period: Y_1..Y_{m-1} = X_1..X_{m-1} (Y_1 expires), Y_m = the arrival; z units
+ * are issued FIFO (oldest first) or LIFO (freshest first), the rest of Y_1 is
+ * wasted and the others age by one period (the issuing equations of Scenario A
+ * and Scenario B, applied slot by slot).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int X[MAXDIG + 2];      /* X[1..m-1] */
+    int Pp[MAXDIG + 2];     /* P[1..L-1] */
+} stock_vec;
+
+static void vec_period(const orc_problem *P, int k, stock_vec *v, int order, int z, prod_out *o) {
+    const int m = P->m[k], L = P->L[k];
+    int Y[MAXDIG + 2];
+    for (int j = 1; j <= m - 1; ++j) Y[j] = v->X[j];
+    Y[m] = (L >= 2) ? v->Pp[1] : order;
+    int T = 0;
+    for (int j = 1; j <= m; ++j) T += Y[j];
+    int left = z;   /* demand not yet met */
+    int rem[MAXDIG + 2] = {0};
+    for (int j = 1; j <= m; ++j) rem[j] = Y[j];
+    if (P->issuing == 0) {
+        for (int j = 1; j <= m && left > 0; ++j) {
+            int take = imin(rem[j], left);
+            rem[j] -= take;
+            left -= take;
+        }
+    } else {
+        for (int j = m; j >= 1 && left > 0; --j) {
+            int take = imin(rem[j], left);
+            rem[j] -= take;
+            left -= take;
+        }
+    }
+    o->total = T;
+    o->issued = imin(z, T);
+    o->wasted = rem[1];
+    o->shortage = ipos(z - T);
+    o->arrived = Y[m];
+    int car = 0;
+    for (int j = 1; j <= m - 1; ++j) {
+        v->X[j] = rem[j + 1];
+        car += rem[j + 1];
+    }
+    o->carried = car;
+    for (int j = 1; j <= L - 2; ++j) v->Pp[j] = v->Pp[j + 1];
+    if (L >= 2) v->Pp[L - 1] = order;
+    o->s_next = 0;
+}
+
+int orc_mbs_simulate(const orc_problem *P, const int S[2], const int mu[2], int cap, int n_rollouts,
+                     int horizon, int warmup, uint64_t seed, double *returns, double *kpis_prod) {
+    if (!valid(P) || !S || !mu) return 1;
+    if (P->n_products == 2 && P->rho != 0.5) return 1;
+    const int np = P->n_products;
+    uint64_t thr[2][512];
+    for (int k = 0; k < np; ++k) {
+        if (P->dmax[k] >= 512) return 1;
+        make_thresholds(P->pmf[k], P->dmax[k], thr[k]);
+    }
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    for (int r = 0; r < n_rollouts; ++r) {
+        stock_vec v[2];
+        memset(v, 0, sizeof(v));
+        double ret = 0.0, disc = 1.0;
+        kpi_sums ks;
+        memset(&ks, 0, sizeof(ks));
+        for (int t = 0; t < warmup + horizon; ++t) {
+            uint32_t ctr[4] = {(uint32_t)t, (uint32_t)r, 0u, 0u}, w[4];
+            orc_philox4x32_10(ctr, key, w);
+            int order[2] = {0, 0};
+            for (int k = 0; k < np; ++k) {
+                int onhand = 0;
+                for (int j = 1; j <= P->m[k] - 1; ++j) onhand += v[k].X[j];
+                if (P->L[k] >= 2) onhand += v[k].Pp[1];
+                int expiring = (P->m[k] >= 2) ? v[k].X[1] : ((P->L[k] >= 2) ? v[k].Pp[1] : 0);
+                int q = S[k] - onhand + ipos(expiring - mu[k]);
+                q = ipos(q);
+                if (cap && q > P->Q[k]) q = P->Q[k];
+                order[k] = q;
+            }
+            const int d1 = draw_demand(w[0], thr[0], P->dmax[0]);
+            const int d2 = (np == 2) ? draw_demand(w[1], thr[1], P->dmax[1]) : 0;
+            prod_out o1, o2;
+            vec_period(P, 0, &v[0], order[0], d1, &o1);
+            double rew = 0.0;
+            int sub = 0, short1 = o1.shortage, short2 = 0;
+            if (np == 2) {
+                const int u = substitutes(w[2], w[3], o1.shortage);
+                vec_period(P, 1, &v[1], order[1], d2 + u, &o2);
+                const int own2 = imin(d2, o2.total);
+                sub = o2.issued - own2;
+                short1 = o1.shortage - sub;
+                short2 = ipos(d2 - o2.total);
+            }
+            const double *c1 = P->cost[0];
+            rew -= c1[0] * (double)order[0];
+            rew -= c1[1] * (double)o1.carried;
+            rew -= c1[2] * (double)short1;
+            rew -= c1[3] * (double)o1.wasted;
+            rew += c1[4] * (double)o1.issued;
+            if (np == 2) {
+                const double *c2 = P->cost[1];
+                rew -= c2[0] * (double)order[1];
+                rew -= c2[1] * (double)o2.carried;
+                rew -= c2[2] * (double)short2;
+                rew -= c2[3] * (double)o2.wasted;
+                rew += c2[4] * (double)o2.issued;
+            }
+            if (t >= warmup) {
+                ret += disc * rew;
+                disc *= P->gamma;
+                ks.dem[0] += d1;
+                ks.served[0] += o1.issued + sub;
+                ks.was[0] += o1.wasted;
+                ks.arr[0] += o1.arrived;
+                ks.car[0] += o1.carried;
+                if (np == 2) {
+                    ks.dem[1] += d2;
+                    ks.served[1] += o2.issued - sub;
+                    ks.was[1] += o2.wasted;
+                    ks.arr[1] += o2.arrived;
+                    ks.car[1] += o2.carried;
+                }
+            }
+        }
+        returns[r] = ret;
+        if (kpis_prod) kpi_sums_finish(&ks, horizon, kpis_prod + 6 * (long long)r);
     }
     return 0;
 }

@@ -51,6 +51,11 @@ typedef struct {
     double arrived;   /* units received this period */
     double shortage;  /* demand lost after substitution */
     int unmet1;       /* product-1 shortfall before substitution (two products) */
+    /* per product k (index 1 is zero for one product) */
+    double demand_k[2];   /* own demand d_k */
+    double issued_k[2];   /* units leaving product k's stock (product 2: own + substitutes) */
+    double wasted_k[2], carried_k[2], arrived_k[2];
+    int sub_served;       /* product-1 shortfall met by product 2 */
 } orc_step;
 
 long long orc_num_states(const orc_problem *P);
@@ -80,6 +85,14 @@ int orc_backup_states(const orc_problem *P, const double *V, const long long *st
 int orc_policy_eval(const orc_problem *P, const uint8_t *policy, double tol, int max_iters,
                     double *V, int *iters, int nthreads);
 
+/* Distribution of the units issued, P(h1, h2 | s, a), from the Scenario B
+ * appendix's five cases (issued-units outcome set, with the substitution
+ * demand D^u and the total product-2 demand D^z).  Product 1 here is the
+ * paper's product B (its shortfall may take product 2), product 2 the paper's
+ * product A.  out: (T1 + 1) x (T2 + 1) row-major (row h1), T_k = units of
+ * product k available this period (written to T_out).  Two products only. */
+int orc_issued_pmf(const orc_problem *P, long long s, int a, double *out, int T_out[2]);
+
 /* Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
@@ -90,13 +103,30 @@ int orc_basestock_policy(const orc_problem *P, int S, uint8_t *policy);
 
 /* Rollouts of a fixed policy from the all-zero state.  Period t of rollout r
  * draws Philox4x32-10(ctr = (t, r, 0, 0), key = (seed lo, seed hi)); word 0 gives
- * product-1 demand, word 1 product-2 demand, word 2 the substitution bits
- * (rho must be 1/2 for two products).  returns[r] = sum over the horizon of
+ * product-1 demand, word 1 product-2 demand, words 2 and 3 the substitution bits
+ * (the popcount of the low `shortfall` bits of the 64-bit word (word 3, word 2);
+ * rho must be 1/2 for two products; a shortfall above 64 uses 64 bits).  returns[r] = sum over the horizon of
  * gamma^t * reward; kpis[3r..3r+2] = service %, wastage %, mean units carried.
  * traj (optional) = n_rollouts x horizon states observed before each decision. */
 int orc_simulate(const orc_problem *P, const uint8_t *policy, int n_rollouts, int horizon,
                  int warmup, uint64_t seed, double *returns, double *kpis, int32_t *traj,
                  int32_t *demand_out);
+
+/* orc_simulate plus per-product KPIs: kpis_prod[6r + 3k + j] = product k's
+ * service % (product 1 counts its shortfall met by substitution as served),
+ * wastage % of the units received, mean units carried.  NULL skips them. */
+int orc_simulate_ex(const orc_problem *P, const uint8_t *policy, int n_rollouts, int horizon,
+                    int warmup, uint64_t seed, double *returns, double *kpis, double *kpis_prod,
+                    int32_t *traj, int32_t *demand_out);
+
+/* Modified base-stock heuristic (Scenario B "Heuristic policies"): product k
+ * orders [S_k - I_k + [X_{1,k} - mu_k]^+]^+ looking at its own stock only, with
+ * I_k the units on hand (X_1..X_{m-1} and, when L >= 2, the arrival P_1) and
+ * X_{1,k} the units that expire this period; cap != 0 clips the order at Q_k,
+ * cap == 0 lets it exceed Q_k (stock is kept as plain vectors, not as a state
+ * index).  Same random numbers, reward and KPIs as orc_simulate_ex. */
+int orc_mbs_simulate(const orc_problem *P, const int S[2], const int mu[2], int cap, int n_rollouts,
+                     int horizon, int warmup, uint64_t seed, double *returns, double *kpis_prod);
 
 #ifdef __cplusplus
 }

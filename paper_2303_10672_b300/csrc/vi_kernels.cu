@@ -531,6 +531,16 @@ __device__ __forceinline__ RollOut roll_product(const ProdParams &P, int lifo, u
     return o;
 }
 
+// accepted substitutions among n short units: popcount of the low n bits of the
+// 64-bit word (w3, w2); a shortfall above 64 uses all 64 bits
+__device__ __forceinline__ int substitutes(uint32_t w2, uint32_t w3, int n) {
+    const int lo = min(n, 32);
+    const int hi = min(max(n - 32, 0), 32);
+    const uint32_t mlo = (lo >= 32) ? 0xffffffffu : ((1u << lo) - 1u);
+    const uint32_t mhi = (hi >= 32) ? 0xffffffffu : ((1u << hi) - 1u);
+    return __popc(w2 & mlo) + __popc(w3 & mhi);
+}
+
 // smallest d with w < thr[d], thr[d] = floor(2^32 CDF(d)) (thr[dmax] = 2^32)
 __device__ __forceinline__ int draw_demand(uint32_t w, const unsigned long long *thr, int dmax) {
     int d = 0;
@@ -592,12 +602,10 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
             const uint32_t s2 = s / S1, s1 = s - s2 * S1;
             const int a1 = a / P2.G, a2 = a - a1 * P2.G;
             const RollOut o1 = roll_product(P1, lifo, s1, a1, d1);
-            const int n = o1.shortage;
-            const uint32_t mask = (n >= 32) ? 0xffffffffu : ((1u << n) - 1u);
-            const int u = __popc(w[2] & mask);
+            const int u = substitutes(w[2], w[3], o1.shortage);
             const RollOut o2 = roll_product(P2, lifo, s2, a2, d2 + u);
             const int own2 = min(d2, o2.total);
-            const int short1 = n - (o2.issued - own2);
+            const int short1 = o1.shortage - (o2.issued - own2);
             const int short2 = max(d2 - o2.total, 0);
             rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][0], (double)a1));
             rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][1], (double)o1.carried));

@@ -193,6 +193,53 @@ def scenario_a(m: int, L: int, c_w: float, issuing: int) -> Instance:
                           name=f"scenA_m{m}L{L}Cw{int(c_w)}{'LIFO' if issuing else 'FIFO'}", precision="fp32")
 
 
+# The paper's Scenario B (Hendrix et al. and Ortega et al. settings, Scenario B
+# appendix): two perishable products with the same useful life m.  The paper's
+# product B, half of whose unmet demand accepts product A, is product 1 here and
+# product A is product 2; a joint action is a1 * (Amax_A + 1) + a2.  The paper's
+# lead time L = 1 (an order arrives before the next day and sits in the state as
+# X_m) is lead time 2 in this library's convention (the arrival slot P_1).
+# Poisson demand, C_v = 0.5 and C_r = 1 per unit for both products, no holding,
+# shortage or waste cost, rho = 0.5, gamma = 1, span test 1e-4.  Demand is
+# folded at the smallest d with P(D > d) < 1e-12.
+SCENARIO_B = dict(c_v=0.5, c_r=1.0, rho=0.5, gamma=1.0, eps=1e-4, tail=1e-12)
+SCENARIO_B_ROLLOUTS = dict(n_rollouts=10_000, horizon=365, warmup=100)
+# name: (m, mu_A, mu_B, Amax_A, Amax_B, fixed VI iterations or None); Table 4
+# (Hendrix et al., run to convergence) and Table 5 (Ortega et al., 100 iterations)
+SCENARIO_B_EXPERIMENTS = {
+    "m2_exp1": (2, 5, 5, 10, 10, None),
+    "m2_exp2": (2, 7, 3, 14, 6, None),
+    "m3_exp1": (3, 5, 5, 15, 15, None),
+    "m3_exp2": (3, 7, 3, 21, 9, None),
+    "m3_exp3": (3, 5, 5, 13, 13, None),
+    "m3_exp4": (3, 7, 3, 20, 4, None),
+    "P1": (2, 5, 5, 10, 10, 100),
+    "P2": (2, 5, 6, 10, 12, 100),
+    "P3": (2, 6, 6, 12, 12, 100),
+    "P4": (2, 7, 7, 13, 13, 100),
+}
+
+
+def poisson_dmax(mean: float, tail: float) -> int:
+    """Smallest d with P(D > d) < tail for D ~ Poisson(mean)."""
+    dist = stats.poisson(mean)
+    d = 0
+    while dist.sf(d) >= tail:
+        d += 1
+    return d
+
+
+def scenario_b(name: str, precision: str = "fp32") -> Instance:
+    """Scenario B experiment `name` in this library's convention (product 1 = paper's B)."""
+    m, mu_a, mu_b, q_a, q_b, _ = SCENARIO_B_EXPERIMENTS[name]
+    b = SCENARIO_B
+    c = (b["c_v"], 0.0, 0.0, 0.0, b["c_r"])
+    pB = Product(m, 2, q_b, c, poisson_pmf(mu_b, poisson_dmax(mu_b, b["tail"])))
+    pA = Product(m, 2, q_a, c, poisson_pmf(mu_a, poisson_dmax(mu_a, b["tail"])))
+    return Instance(name=f"scenB_{name}", products=[pB, pA], gamma=b["gamma"], issuing=FIFO,
+                    subst_rate=b["rho"], tol=b["eps"], precision=precision)
+
+
 @dataclasses.dataclass
 class Request:
     arrival_s: float
