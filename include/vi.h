@@ -94,8 +94,9 @@ enum {
 /* Full problem description.  cost[k] = {c_o order, c_h holding, c_s shortage,
  * c_w waste, c_r revenue} per unit for product k (all >= 0).  pmf[k] = host
  * array of dmax[k]+1 probabilities summing to 1 (tail mass already folded into
- * the last entry, as in the paper's truncated demand).  L[k] must be 1 for two
- * products. */
+ * the last entry, as in the paper's truncated demand).  Two products may have
+ * any lead times (the paper's Scenario B, where an order arrives before the next
+ * day, is L = 2 for both in this convention: the arrival slot P_1). */
 typedef struct {
     int n_products;          /* 1 or 2 */
     int m[2], L[2], Q[2];
@@ -135,7 +136,7 @@ vi_status vi_problem_create(int m, int L, int Q, const double cost[5], const dou
 
 /* Create a problem from a full description (one or two products, precision,
  * stopping rule).  Same errors as vi_problem_create; two products also need
- * L = 1, |A| = (Q_1+1)(Q_2+1) <= 256 and subst_rate in [0,1]. */
+ * |A| = (Q_1+1)(Q_2+1) <= 256, dmax <= 255 and subst_rate in [0,1]. */
 vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_handle *out);
 
 /* Release every device and host resource of the handle.  NULL is accepted. */
@@ -149,8 +150,10 @@ vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
 /* Per-handle options (no counterpart in the paper; tuning and test hooks).
  * VI_OPT_KERNEL: which sweep kernel runs -- VI_KERNEL_AUTO (factorised kernel
  * whenever the instance allows it; the tensor-core variant is one of the
- * autotuned candidates; two products in FP32 run the factorised two-product
- * sweep, which vi_problem_kernel reports as VI_KERNEL_GROUP with width 0),
+ * autotuned candidates; two products in VI_PREC_FP32 run the factorised
+ * two-product sweep -- with lead times >= 2 on both products its pipeline form
+ * (m >= 2, Q+1 <= 32) -- which vi_problem_kernel reports as VI_KERNEL_GROUP with
+ * width 0),
  * VI_KERNEL_GENERIC (one thread per state),
  * VI_KERNEL_GROUP (factorised; VI_EINVAL if the instance does not allow it:
  * it needs one product, VI_PREC_FP32 or VI_PREC_FP32_SINGLE, 2 <= Q+1 <= 64 and
@@ -241,6 +244,35 @@ vi_status vi_next_states(vi_handle h, const uint32_t *states, int n, uint32_t *o
 vi_status vi_simulate(vi_handle h, const uint8_t *policy, int n_rollouts, int horizon,
                       int warmup, uint64_t seed, double *returns, double *kpis,
                       int32_t *traj, void *stream);
+
+/* vi_simulate plus per-product KPIs (Scenario B appendix, KPI tables):
+ * kpis_prod: device double[6n] or NULL; entry 6r + 3k + j is, for product k
+ * of rollout r, j = 0 the service level % (product 1's shortfall met by
+ * substitution counts as served), j = 1 wastage % of the units received, j = 2
+ * mean units carried to the next period.  Product index 1 is {100, 0, 0} for
+ * one product.  Other arguments and errors as vi_simulate. */
+vi_status vi_simulate_ex(vi_handle h, const uint8_t *policy, int n_rollouts, int horizon, int warmup,
+                         uint64_t seed, double *returns, double *kpis, double *kpis_prod, int32_t *traj,
+                         void *stream);
+
+/* Modified base-stock search by simulation (Scenario B "Heuristic policies",
+ * after Haijema et al.): product k orders [S_k - I_k + [X_{1,k} - mu_k]^+]^+,
+ * I_k = its units on hand (X_1..X_{m-1} and the arrival P_1 when L >= 2),
+ * X_{1,k} = its units expiring this period; cap != 0 clips each order at Q_k,
+ * cap == 0 lets it exceed Q_k (the simulation keeps plain slot counts).  Every
+ * pair (S_1, S_2) in [S_lo, S_hi] (S_lo[1], S_hi[1], mu[1] ignored for one
+ * product) runs n_rollouts rollouts from empty stock with `warmup` unscored
+ * periods and `horizon` scored ones, on the random numbers of vi_simulate.
+ * returns: device double[n_pairs * n_rollouts], row pair = (S_1 - S_lo[0]) *
+ * n_2 + (S_2 - S_lo[1]); kpis_prod: device double[6 n_pairs n_rollouts] or
+ * NULL (layout of vi_simulate_ex); mean_returns: host double[n_pairs] or NULL;
+ * best_S: host int[2] or NULL (the first pair with the largest mean, FP64
+ * sums in rollout order; the stream is synchronised when either is given).
+ * Errors: VI_EINVAL (bad ranges, m > 8 or L > 4, dmax above the rollout limit,
+ * subst_rate other than 1/2 for two products), VI_ECUDA. */
+vi_status vi_mbs_search(vi_handle h, const int S_lo[2], const int S_hi[2], const int mu[2], int cap,
+                        int n_rollouts, int horizon, int warmup, uint64_t seed, double *returns,
+                        double *kpis_prod, double *mean_returns, int best_S[2], void *stream);
 
 /* Base-stock policy search by simulation (Methods, Scenario A heuristic policy:
  * A = [S - I]^+ with I the total stock on hand and in transit; the paper scores

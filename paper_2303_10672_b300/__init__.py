@@ -90,6 +90,10 @@ def lib() -> C.CDLL:
                             C.POINTER(C.c_double)], C.c_int),
         "vi_next_states": ([H, vp, C.c_int, vp, vp], C.c_int),
         "vi_simulate": ([H, u8p, C.c_int, C.c_int, C.c_int, C.c_uint64, vp, vp, vp, vp], C.c_int),
+        "vi_simulate_ex": ([H, u8p, C.c_int, C.c_int, C.c_int, C.c_uint64, vp, vp, vp, vp, vp], C.c_int),
+        "vi_mbs_search": ([H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int, C.c_int,
+                           C.c_int, C.c_int, C.c_uint64, vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_int), vp],
+                          C.c_int),
         "vi_server_create": ([C.c_size_t, C.c_int, vp, C.POINTER(C.c_void_p)], C.c_int),
         "vi_server_submit": ([C.c_void_p, C.POINTER(vi_problem_desc), C.c_double, C.c_int,
                               C.POINTER(C.c_uint64)], C.c_int),
@@ -263,6 +267,28 @@ def vi_simulate(h: int, policy, n_rollouts: int, horizon: int, warmup: int, seed
                 traj=None, stream=None) -> None:
     _check(lib().vi_simulate(h, _addr(policy), n_rollouts, horizon, warmup, C.c_uint64(seed), _addr(returns),
                              _addr(kpis), _addr(traj), _stream(stream)), "vi_simulate")
+
+
+def vi_simulate_ex(h: int, policy, n_rollouts: int, horizon: int, warmup: int, seed: int, returns, kpis=None,
+                   kpis_prod=None, traj=None, stream=None) -> None:
+    _check(lib().vi_simulate_ex(h, _addr(policy), n_rollouts, horizon, warmup, C.c_uint64(seed), _addr(returns),
+                                _addr(kpis), _addr(kpis_prod), _addr(traj), _stream(stream)), "vi_simulate_ex")
+
+
+def vi_mbs_search(h: int, S_lo, S_hi, mu, cap: bool, n_rollouts: int, horizon: int, warmup: int, seed: int,
+                  returns, kpis_prod=None, stream=None):
+    """Modified base-stock search over the (S_1, S_2) grid: per-pair mean returns
+    (row-major, product 1 outer) and the best pair; per-rollout returns (and
+    per-product KPIs if given) land in the device buffers."""
+    lo = (C.c_int * 2)(*(list(S_lo) + [0] * (2 - len(S_lo))))
+    hi = (C.c_int * 2)(*(list(S_hi) + [0] * (2 - len(S_hi))))
+    mv = (C.c_int * 2)(*(list(mu) + [0] * (2 - len(mu))))
+    n_pairs = (hi[0] - lo[0] + 1) * ((hi[1] - lo[1] + 1) if len(S_lo) == 2 else 1)
+    means = (C.c_double * n_pairs)()
+    best = (C.c_int * 2)()
+    _check(lib().vi_mbs_search(h, lo, hi, mv, int(bool(cap)), n_rollouts, horizon, warmup, C.c_uint64(seed),
+                               _addr(returns), _addr(kpis_prod), means, best, _stream(stream)), "vi_mbs_search")
+    return np.array(list(means)), (best[0], best[1])
 
 
 def vi_problem_kernel(h: int) -> tuple:

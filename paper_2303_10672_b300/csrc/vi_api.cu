@@ -336,7 +336,6 @@ extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_hand
     if (d.precision < VI_PREC_FP32 || d.precision > VI_PREC_FP32_SINGLE) return vi_fail(VI_EINVAL, "bad precision");
     if (d.stop_rule != VI_STOP_SPAN && d.stop_rule != VI_STOP_SUPNORM) return vi_fail(VI_EINVAL, "bad stop_rule");
     if (d.n_products == 2) {
-        if (d.L[0] != 1 || d.L[1] != 1) return vi_fail(VI_EINVAL, "two products need L = 1");
         if ((d.Q[0] + 1) * (d.Q[1] + 1) > 256) return vi_fail(VI_EINVAL, "joint actions exceed 256");
         if (!(d.subst_rate >= 0.0 && d.subst_rate <= 1.0)) return vi_fail(VI_EINVAL, "subst_rate in [0,1]");
         double ns = 1.0;
@@ -416,7 +415,9 @@ extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_hand
         }
         kp.two_e2 = h->d_two_e2;
         kp.two_mix = h->d_two_mix;
-        kp.two_nt1 = kp.p[0].dmax + 1;
+        kp.two_nt1 = two_mix_rows(kp.p[0]);
+        kp.two_npipe1 = 1;
+        for (int k = 1; k < kp.p[0].L; ++k) kp.two_npipe1 *= kp.p[0].G;
     }
     kp.st = h->d_state;
     kp.tables = (h->vk == VK_DOUBLE) ? (const void *)h->d_tab_d : (const void *)h->d_tab_f;
@@ -1010,18 +1011,14 @@ static void make_thresholds(const std::vector<double> &pmf, unsigned long long *
     thr[dmax] = 4294967296ull;
 }
 
-extern "C" vi_status vi_simulate(vi_handle h, const uint8_t *policy, int n_rollouts, int horizon, int warmup,
-                                 uint64_t seed, double *returns, double *kpis, int32_t *traj, void *stream) {
-    if (!h) return vi_fail(VI_EINVAL, "null handle");
-    if (!policy || !returns || n_rollouts < 0 || horizon < 0 || warmup < 0)
-        return vi_fail(VI_EINVAL, "bad rollout arguments");
-    if (n_rollouts == 0) return VI_OK;
+// the rollout parameters shared by vi_simulate_ex and vi_mbs_search
+static vi_status roll_params(const vi_problem *h, int n_rollouts, int horizon, int warmup, uint64_t seed,
+                             RollParams &rp) {
     const vi_problem_desc &d = h->desc;
     for (int k = 0; k < d.n_products; ++k)
         if (d.dmax[k] > kMaxRollDmax) return vi_fail(VI_EINVAL, "rollouts need dmax <= %d", kMaxRollDmax);
     if (d.n_products == 2 && d.subst_rate != 0.5)
         return vi_fail(VI_EINVAL, "two-product rollouts draw substitutions as fair bits (subst_rate 1/2)");
-    RollParams rp;
     memset(&rp, 0, sizeof(rp));
     rp.n_rollouts = n_rollouts;
     rp.horizon = horizon;
@@ -1031,7 +1028,77 @@ extern "C" vi_status vi_simulate(vi_handle h, const uint8_t *policy, int n_rollo
         for (int j = 0; j < 5; ++j) rp.cost[k][j] = d.cost[k][j];
         make_thresholds(h->pmf[k], rp.thr[k]);
     }
-    CUDA_TRY(launch_rollouts(h->kp, rp, policy, returns, kpis, traj, (cudaStream_t)stream));
+    return VI_OK;
+}
+
+extern "C" vi_status vi_simulate_ex(vi_handle h, const uint8_t *policy, int n_rollouts, int horizon, int warmup,
+                                    uint64_t seed, double *returns, double *kpis, double *kpis_prod, int32_t *traj,
+                                    void *stream) {
+    if (!h) return vi_fail(VI_EINVAL, "null handle");
+    if (!policy || !returns || n_rollouts < 0 || horizon < 0 || warmup < 0)
+        return vi_fail(VI_EINVAL, "bad rollout arguments");
+    if (n_rollouts == 0) return VI_OK;
+    RollParams rp;
+    vi_status st = roll_params(h, n_rollouts, horizon, warmup, seed, rp);
+    if (st != VI_OK) return st;
+    CUDA_TRY(launch_rollouts(h->kp, rp, policy, returns, kpis, kpis_prod, traj, (cudaStream_t)stream));
+    return VI_OK;
+}
+
+extern "C" vi_status vi_simulate(vi_handle h, const uint8_t *policy, int n_rollouts, int horizon, int warmup,
+                                 uint64_t seed, double *returns, double *kpis, int32_t *traj, void *stream) {
+    return vi_simulate_ex(h, policy, n_rollouts, horizon, warmup, seed, returns, kpis, nullptr, traj, stream);
+}
+
+extern "C" vi_status vi_mbs_search(vi_handle h, const int S_lo[2], const int S_hi[2], const int mu[2], int cap,
+                                   int n_rollouts, int horizon, int warmup, uint64_t seed, double *returns,
+                                   double *kpis_prod, double *mean_returns, int best_S[2], void *stream) {
+    if (!h) return vi_fail(VI_EINVAL, "null handle");
+    const vi_problem_desc &d = h->desc;
+    const int np = d.n_products;
+    if (!S_lo || !S_hi || !mu || !returns || n_rollouts < 1 || horizon < 0 || warmup < 0)
+        return vi_fail(VI_EINVAL, "bad search arguments");
+    for (int k = 0; k < np; ++k) {
+        if (S_lo[k] < 0 || S_hi[k] < S_lo[k] || mu[k] < 0) return vi_fail(VI_EINVAL, "bad order-up-to range");
+        if (d.m[k] > kMbsMaxM || d.L[k] > kMbsMaxL)
+            return vi_fail(VI_EINVAL, "the heuristic keeps m <= %d and L <= %d slots", kMbsMaxM, kMbsMaxL);
+    }
+    MbsParams mp;
+    memset(&mp, 0, sizeof(mp));
+    mp.s_lo[0] = S_lo[0];
+    mp.s_lo[1] = (np == 2) ? S_lo[1] : 0;
+    const int n1 = S_hi[0] - S_lo[0] + 1;
+    mp.n2 = (np == 2) ? S_hi[1] - S_lo[1] + 1 : 1;
+    mp.n_pairs = n1 * mp.n2;
+    mp.mu[0] = mu[0];
+    mp.mu[1] = (np == 2) ? mu[1] : 0;
+    mp.cap = cap ? 1 : 0;
+    if ((long long)mp.n_pairs * n_rollouts > (1ll << 31)) return vi_fail(VI_EINVAL, "too many (pair, rollout) runs");
+    RollParams rp;
+    vi_status st = roll_params(h, n_rollouts, horizon, warmup, seed, rp);
+    if (st != VI_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(launch_mbs(h->kp, rp, mp, returns, kpis_prod, s));
+    if (!mean_returns && !best_S) return VI_OK;
+    std::vector<double> host((size_t)mp.n_pairs * n_rollouts);
+    CUDA_TRY(cudaMemcpyAsync(host.data(), returns, host.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    int best = 0;
+    double best_mean = -INFINITY;
+    for (int i = 0; i < mp.n_pairs; ++i) {
+        double sum = 0.0;   // rollout order, FP64
+        for (int r = 0; r < n_rollouts; ++r) sum += host[(size_t)i * n_rollouts + r];
+        const double mean = sum / (double)n_rollouts;
+        if (mean_returns) mean_returns[i] = mean;
+        if (mean > best_mean) {
+            best_mean = mean;
+            best = i;
+        }
+    }
+    if (best_S) {
+        best_S[0] = mp.s_lo[0] + best / mp.n2;
+        best_S[1] = mp.s_lo[1] + best % mp.n2;
+    }
     return VI_OK;
 }
 

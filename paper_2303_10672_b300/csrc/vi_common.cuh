@@ -71,7 +71,9 @@ struct KernelParams {
     // factorised two-product sweep: per-sweep tables of product-2 expectations
     float *two_e2;        // [s2][a2][i1]  sum_z w(z) (V(i1, s2'(z)) - V(i1, s2'(0)))
     float *two_mix;       // [s2][a2][T1]  the substitution mixture of d1 >= T1, same frame with i1 = 0
-    int two_nt1;          // T1 values kept: 0..dmax1
+                          // (lead times >= 2: [s2][a2][pipe1][T1], pipe1 = product-1 pipeline of s')
+    int two_nt1;          // T1 values kept: 0..min(dmax1, m1 Q1)
+    int two_npipe1;       // product-1 pipeline classes of an emptied next state: G1^(L1-1)
 };
 
 // ---------------------------------------------------------------------------

@@ -561,8 +561,25 @@ __device__ __forceinline__ double single_period(const ProdParams &P1, int lifo, 
     return rew;
 }
 
+// per-product KPI sums of one rollout (integers, so FP64 sums are exact)
+struct KpiSums {
+    double dem[2], served[2], was[2], arr[2], car[2];
+    __device__ __forceinline__ void init() {
+        for (int j = 0; j < 2; ++j) dem[j] = served[j] = was[j] = arr[j] = car[j] = 0.0;
+    }
+    // service % (product 1 counts its shortfall met by substitution as served),
+    // wastage % of the units received, mean units carried
+    __device__ __forceinline__ void finish(int horizon, double *out6) const {
+        for (int j = 0; j < 2; ++j) {
+            out6[3 * j + 0] = dem[j] > 0.0 ? __ddiv_rn(__dmul_rn(100.0, served[j]), dem[j]) : 100.0;
+            out6[3 * j + 1] = arr[j] > 0.0 ? __ddiv_rn(__dmul_rn(100.0, was[j]), arr[j]) : 0.0;
+            out6[3 * j + 2] = horizon > 0 ? __ddiv_rn(car[j], (double)horizon) : 0.0;
+        }
+    }
+};
+
 __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *policy, double *returns, double *kpis,
-                               int32_t *traj) {
+                               double *kpis_prod, int32_t *traj) {
     __shared__ unsigned long long s_thr[2][kMaxRollDmax + 1];
     for (int i = threadIdx.x; i <= kMaxRollDmax; i += blockDim.x) {
         s_thr[0][i] = rp.thr[0][i];
@@ -576,6 +593,8 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
     uint32_t s = 0;
     double ret = 0.0, disc = 1.0;
     double dem = 0.0, iss = 0.0, was = 0.0, arr = 0.0, car = 0.0;
+    KpiSums ks;
+    ks.init();
     const ProdParams &P1 = kp.p[0];
     for (int t = 0; t < rp.warmup + rp.horizon; ++t) {
         uint32_t w[4];
@@ -583,6 +602,7 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
         const int a = policy[s];
         double rew = 0.0;
         double t_dem, t_iss, t_was, t_arr, t_car;
+        int p_dem[2] = {0, 0}, p_srv[2] = {0, 0}, p_was[2] = {0, 0}, p_arr[2] = {0, 0}, p_car[2] = {0, 0};
         uint32_t s_next;
         if (kp.n_products == 1) {
             const int d1 = draw_demand(w[0], s_thr[0], P1.dmax);
@@ -594,6 +614,11 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
             t_was = o.wasted;
             t_arr = o.arrived;
             t_car = o.carried;
+            p_dem[0] = d1;
+            p_srv[0] = o.issued;
+            p_was[0] = o.wasted;
+            p_arr[0] = o.arrived;
+            p_car[0] = o.carried;
         } else {
             const ProdParams &P2 = kp.p[1];
             const int d1 = draw_demand(w[0], s_thr[0], P1.dmax);
@@ -623,6 +648,17 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
             t_was = o1.wasted + o2.wasted;
             t_arr = o1.arrived + o2.arrived;
             t_car = o1.carried + o2.carried;
+            const int sub = o2.issued - own2;
+            p_dem[0] = d1;
+            p_dem[1] = d2;
+            p_srv[0] = o1.issued + sub;
+            p_srv[1] = own2;
+            p_was[0] = o1.wasted;
+            p_was[1] = o2.wasted;
+            p_arr[0] = o1.arrived;
+            p_arr[1] = o2.arrived;
+            p_car[0] = o1.carried;
+            p_car[1] = o2.carried;
         }
         if (t >= rp.warmup) {
             if (traj) traj[(size_t)r * rp.horizon + (t - rp.warmup)] = (int32_t)s;
@@ -633,6 +669,13 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
             was = __dadd_rn(was, t_was);
             arr = __dadd_rn(arr, t_arr);
             car = __dadd_rn(car, t_car);
+            for (int j = 0; j < 2; ++j) {
+                ks.dem[j] += (double)p_dem[j];
+                ks.served[j] += (double)p_srv[j];
+                ks.was[j] += (double)p_was[j];
+                ks.arr[j] += (double)p_arr[j];
+                ks.car[j] += (double)p_car[j];
+            }
         }
         s = s_next;
     }
@@ -642,6 +685,7 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
         kpis[3 * r + 1] = arr > 0.0 ? __ddiv_rn(__dmul_rn(100.0, was), arr) : 0.0;
         kpis[3 * r + 2] = rp.horizon > 0 ? __ddiv_rn(car, (double)rp.horizon) : 0.0;
     }
+    if (kpis_prod) ks.finish(rp.horizon, kpis_prod + 6 * (size_t)r);
 }
 
 // ===========================================================================
@@ -690,6 +734,170 @@ cudaError_t launch_basestock(const KernelParams &kp, const RollParams &rp, int s
     const long long n = (long long)n_S * rp.n_rollouts;
     const int threads = 128;
     basestock_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, stream>>>(kp, rp, s_lo, n_S, returns);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// modified base-stock search (Scenario B heuristic): thread = ((S_1, S_2), rollout).
+// Product k orders [S_k - I_k + [X_{1,k} - mu_k]^+]^+ from its own stock (I_k:
+// units on hand, X_1..X_{m-1} and the arrival P_1 when L >= 2), optionally
+// capped at Q_k.  The stock is kept as plain slot counts, not as a state index,
+// so an uncapped order may exceed Q_k.  Same random numbers as the rollouts.
+// ===========================================================================
+struct StockVec {
+    int X[kMbsMaxM];       // X_1..X_{m-1}
+    int P[kMbsMaxL];       // P_1..P_{L-1}
+};
+
+struct VecOut {
+    int issued, wasted, carried, shortage, arrived, total;
+};
+
+__device__ __forceinline__ void vec_period(const ProdParams &P, int lifo, StockVec &v, int order, int z, VecOut &o) {
+    int Y[kMbsMaxM];
+#pragma unroll
+    for (int j = 0; j < kMbsMaxM; ++j) Y[j] = (j < P.m - 1) ? v.X[j] : 0;
+    const int arrival = (P.L >= 2) ? v.P[0] : order;
+#pragma unroll
+    for (int j = 0; j < kMbsMaxM; ++j)
+        if (j == P.m - 1) Y[j] = arrival;
+    int T = 0;
+#pragma unroll
+    for (int j = 0; j < kMbsMaxM; ++j) T += (j < P.m) ? Y[j] : 0;
+    int left = z;
+    if (!lifo) {
+#pragma unroll
+        for (int j = 0; j < kMbsMaxM; ++j) {
+            if (j < P.m) {
+                const int take = min(Y[j], left);
+                Y[j] -= take;
+                left -= take;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = kMbsMaxM - 1; j >= 0; --j) {
+            if (j < P.m) {
+                const int take = min(Y[j], left);
+                Y[j] -= take;
+                left -= take;
+            }
+        }
+    }
+    o.total = T;
+    o.issued = min(z, T);
+    o.wasted = Y[0];
+    o.shortage = max(z - T, 0);
+    o.arrived = arrival;
+    int car = 0;
+#pragma unroll
+    for (int j = 0; j < kMbsMaxM - 1; ++j) {
+        const int nx = (j < P.m - 1) ? Y[j + 1] : 0;
+        v.X[j] = nx;
+        car += nx;
+    }
+    o.carried = car;
+#pragma unroll
+    for (int j = 0; j < kMbsMaxL - 1; ++j)
+        if (j < P.L - 2) v.P[j] = v.P[j + 1];
+#pragma unroll
+    for (int j = 0; j < kMbsMaxL; ++j)
+        if (j == P.L - 2) v.P[j] = order;
+}
+
+__device__ __forceinline__ int mbs_order(const ProdParams &P, const StockVec &v, int S, int mu, int cap) {
+    int onhand = 0;
+#pragma unroll
+    for (int j = 0; j < kMbsMaxM; ++j) onhand += (j < P.m - 1) ? v.X[j] : 0;
+    if (P.L >= 2) onhand += v.P[0];
+    const int expiring = (P.m >= 2) ? v.X[0] : ((P.L >= 2) ? v.P[0] : 0);
+    int q = max(S - onhand + max(expiring - mu, 0), 0);
+    if (cap) q = min(q, P.Q);
+    return q;
+}
+
+__global__ void mbs_kernel(KernelParams kp, RollParams rp, MbsParams mp, double *returns, double *kpis_prod) {
+    __shared__ unsigned long long s_thr[2][kMaxRollDmax + 1];
+    for (int i = threadIdx.x; i <= kMaxRollDmax; i += blockDim.x) {
+        s_thr[0][i] = rp.thr[0][i];
+        s_thr[1][i] = rp.thr[1][i];
+    }
+    __syncthreads();
+    const long long t_id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t_id >= (long long)mp.n_pairs * rp.n_rollouts) return;
+    const int pair = (int)(t_id / rp.n_rollouts);
+    const int r = (int)(t_id % rp.n_rollouts);
+    const int S1 = mp.s_lo[0] + pair / mp.n2, S2 = mp.s_lo[1] + pair % mp.n2;
+    const int np = kp.n_products;
+    const int lifo = kp.issuing;
+    const ProdParams &P1 = kp.p[0];
+    const ProdParams &P2 = kp.p[1];
+    const uint32_t k0 = (uint32_t)(rp.seed & 0xffffffffull), k1 = (uint32_t)(rp.seed >> 32);
+    StockVec v1, v2;
+#pragma unroll
+    for (int j = 0; j < kMbsMaxM; ++j) v1.X[j] = v2.X[j] = 0;
+#pragma unroll
+    for (int j = 0; j < kMbsMaxL; ++j) v1.P[j] = v2.P[j] = 0;
+    double ret = 0.0, disc = 1.0;
+    KpiSums ks;
+    ks.init();
+    for (int t = 0; t < rp.warmup + rp.horizon; ++t) {
+        uint32_t w[4];
+        philox4x32_10((uint32_t)t, (uint32_t)r, 0u, 0u, k0, k1, w);
+        const int q1 = mbs_order(P1, v1, S1, mp.mu[0], mp.cap);
+        const int q2 = (np == 2) ? mbs_order(P2, v2, S2, mp.mu[1], mp.cap) : 0;
+        const int d1 = draw_demand(w[0], s_thr[0], P1.dmax);
+        const int d2 = (np == 2) ? draw_demand(w[1], s_thr[1], P2.dmax) : 0;
+        VecOut o1, o2;
+        vec_period(P1, lifo, v1, q1, d1, o1);
+        int sub = 0, short1 = o1.shortage, short2 = 0;
+        if (np == 2) {
+            const int u = substitutes(w[2], w[3], o1.shortage);
+            vec_period(P2, lifo, v2, q2, d2 + u, o2);
+            const int own2 = min(d2, o2.total);
+            sub = o2.issued - own2;
+            short1 = o1.shortage - sub;
+            short2 = max(d2 - o2.total, 0);
+        }
+        double rew = 0.0;
+        rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][0], (double)q1));
+        rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][1], (double)o1.carried));
+        rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][2], (double)short1));
+        rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][3], (double)o1.wasted));
+        rew = __dadd_rn(rew, __dmul_rn(rp.cost[0][4], (double)o1.issued));
+        if (np == 2) {
+            rew = __dsub_rn(rew, __dmul_rn(rp.cost[1][0], (double)q2));
+            rew = __dsub_rn(rew, __dmul_rn(rp.cost[1][1], (double)o2.carried));
+            rew = __dsub_rn(rew, __dmul_rn(rp.cost[1][2], (double)short2));
+            rew = __dsub_rn(rew, __dmul_rn(rp.cost[1][3], (double)o2.wasted));
+            rew = __dadd_rn(rew, __dmul_rn(rp.cost[1][4], (double)o2.issued));
+        }
+        if (t >= rp.warmup) {
+            ret = __dadd_rn(ret, __dmul_rn(disc, rew));
+            disc = __dmul_rn(disc, kp.gamma);
+            ks.dem[0] += (double)d1;
+            ks.served[0] += (double)(o1.issued + sub);
+            ks.was[0] += (double)o1.wasted;
+            ks.arr[0] += (double)o1.arrived;
+            ks.car[0] += (double)o1.carried;
+            if (np == 2) {
+                ks.dem[1] += (double)d2;
+                ks.served[1] += (double)(o2.issued - sub);
+                ks.was[1] += (double)o2.wasted;
+                ks.arr[1] += (double)o2.arrived;
+                ks.car[1] += (double)o2.carried;
+            }
+        }
+    }
+    returns[t_id] = ret;
+    if (kpis_prod) ks.finish(rp.horizon, kpis_prod + 6 * t_id);
+}
+
+cudaError_t launch_mbs(const KernelParams &kp, const RollParams &rp, const MbsParams &mp, double *returns,
+                       double *kpis_prod, cudaStream_t stream) {
+    const long long n = (long long)mp.n_pairs * rp.n_rollouts;
+    const int threads = 128;
+    mbs_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, stream>>>(kp, rp, mp, returns, kpis_prod);
     return cudaGetLastError();
 }
 
@@ -876,19 +1084,358 @@ sweep_two_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg,
     if (mode != MODE_EXTRACT) block_reduce_and_finalize<float>(mx, mn, st, mode, gridDim.x);
 }
 
+// ===========================================================================
+// factorised two-product sweep with lead times >= 2 (the paper's Scenario B:
+// an order arrives before the next period, so this library's state holds it in
+// the arrival slot P_1).  The order of this period then only fills the top
+// pipeline digit: issuing, the expected reward and the next stock slots do not
+// depend on the action, and V(s') is read at s'(no order) + a1 w1 + S1 a2 w2.
+// Per sweep, with c(s2, a2) = V(0, i2_0 + a2 w2) the reference of a row,
+//   E2(i1, s2, a2)  = sum_d2 p2(d2) [V(i1, i2(s2, d2) + a2 w2) - c]
+//   Mix(s2, a2, pipe1, T1) = sum_z M(T1, z) [V(pipe1 W1, i2(s2, z) + a2 w2) - c]
+// (M = the product-2 demand z = d2 + substitutes when d1 >= T1), and the sweep
+//   Q(s, a) = H(s) - c_o a + gamma [c + sum_{d1 < T1} p1(d1) E2(i1(d1) + a1 w1, s2, a2)
+//                                      + Mix(s2, a2, pipe1(a1), T1)].
+// States sharing the rest r1 of product 1 (all X_1 = x) share every gathered
+// E2 value: FIFO takes k = d1 - x units from the rest, LIFO min(d1, R1), so one
+// thread computes all x of a rest as a correlation over k.  The E2 and Mix
+// kernels use the same correlation over product 2's expiring slot.
+// ===========================================================================
+
+// pmf-like coefficients of a correlation row: point mass, cumulative, tail,
+// with the values a table of length n takes beyond its end
+struct CoefRow {
+    const float *p, *c, *t;
+    int n;
+    __device__ __forceinline__ float pm(int i) const { return i < n ? p[i] : 0.f; }
+    __device__ __forceinline__ float cum(int i) const { return i < n ? c[i] : c[n - 1]; }
+    __device__ __forceinline__ float tl(int i) const { return i < n ? t[i] : 0.f; }
+};
+
+// expectation over product 2's issuing for every expiring-slot value x2 < XW of
+// the rest r2: out[x2] = sum_e w(x2, e) g(e), g(e) = value after e units taken
+// from the rest (FIFO: e = clamp(z - x2, 0, R2); LIFO: e = min(z, R2))
+template <int XW, class Gather>
+__device__ __forceinline__ void corr_product2(float (&out)[XW], const Gather &g, Walker wk, const ProdParams &P,
+                                              int lifo, int R, const CoefRow &w) {
+    if (!lifo) {
+        const float g0 = g(wk.idx);
+        if (R == 0) {
+#pragma unroll
+            for (int x = 0; x < XW; ++x) out[x] = w.cum(w.n - 1) * g0;
+            return;
+        }
+#pragma unroll
+        for (int x = 0; x < XW; ++x) out[x] = w.cum(x) * g0;
+        int e = 1;
+        for (; e < R && e < w.n; ++e) {
+            walker_step(wk, P.cb, 0, (uint32_t)P.G);
+            const float ge = g(wk.idx);
+#pragma unroll
+            for (int x = 0; x < XW; ++x) out[x] = fmaf(w.pm(x + e), ge, out[x]);
+        }
+        if (R < w.n) {
+            for (; e <= R; ++e) walker_step(wk, P.cb, 0, (uint32_t)P.G);
+            const float gR = g(wk.idx);
+#pragma unroll
+            for (int x = 0; x < XW; ++x) out[x] = fmaf(w.tl(x + R), gR, out[x]);
+        }
+    } else {
+        float acc = 0.f;
+        int e = 0;
+        for (; e < R && e < w.n; ++e) {
+            acc = fmaf(w.pm(e), g(wk.idx), acc);
+            walker_step(wk, P.cb, 1, (uint32_t)P.G);
+        }
+        if (R < w.n) acc = fmaf(w.tl(R), g(wk.idx), acc);
+#pragma unroll
+        for (int x = 0; x < XW; ++x) out[x] = acc;
+    }
+}
+
+struct GetRow {
+    const float2 *V;
+    uint32_t base, mult;
+    float2 ref;
+    __device__ __forceinline__ float operator()(uint32_t i2) const { return pair_diff(V[base + mult * i2], ref); }
+};
+
+// thread = (i1, r2, a2), i1 fastest: writes E2 for every x2 of the rest r2
+template <int XW>
+__global__ void __launch_bounds__(kGenericThreads)
+twop_e2_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int) {
+    SolveState *st = kp.st;
+    Bufs B;
+    if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
+    const ProdParams &P1 = kp.p[0];
+    const ProdParams &P2 = kp.p[1];
+    const uint32_t S1 = P1.nS;
+    const uint32_t G2 = (uint32_t)P2.G;
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (uint64_t)S1 * P2.nS) return;
+    const uint32_t i1 = (uint32_t)(t % S1);
+    const uint32_t rest = (uint32_t)(t / S1);
+    const int a2 = (int)(rest % G2);
+    const uint32_t r2 = rest / G2;
+    const ProdState ps = prod_state(P2, r2 * G2);
+    const ProdAction A = prod_action(P2, ps, a2, kp.issuing);
+    const float2 *V2 = (const float2 *)B.vin;
+    const float *tab = (const float *)kp.tables;
+    const GetRow g{V2, i1, S1, V2[(uint64_t)S1 * A.wk.idx]};
+    const CoefRow w{tab + P2.off_p, tab + P2.off_F, tab + P2.off_tail, P2.pn};
+    float out[XW];
+    corr_product2<XW>(out, g, A.wk, P2, kp.issuing, A.R, w);
+#pragma unroll
+    for (int x = 0; x < XW; ++x)
+        if (x < P2.G) kp.two_e2[((uint64_t)(r2 * G2 + (uint32_t)x) * G2 + (uint32_t)a2) * S1 + i1] = out[x];
+}
+
+// thread = (pipe1, T1, a2, r2): the substitution mixture for every x2 of r2
+template <int XW>
+__global__ void __launch_bounds__(kGenericThreads)
+twop_mix_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int) {
+    SolveState *st = kp.st;
+    Bufs B;
+    if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
+    const ProdParams &P1 = kp.p[0];
+    const ProdParams &P2 = kp.p[1];
+    const uint32_t S1 = P1.nS;
+    const uint32_t G2 = (uint32_t)P2.G;
+    const uint32_t np1 = (uint32_t)kp.two_npipe1, nt = (uint32_t)kp.two_nt1;
+    const uint64_t n = (uint64_t)np1 * nt * P2.nS;
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const uint32_t pipe1 = (uint32_t)(t % np1);
+    uint64_t rest = t / np1;
+    const int T1 = (int)(rest % nt);
+    rest /= nt;
+    const int a2 = (int)(rest % G2);
+    const uint32_t r2 = (uint32_t)(rest / G2);
+    const ProdState ps = prod_state(P2, r2 * G2);
+    const ProdAction A = prod_action(P2, ps, a2, kp.issuing);
+    const float2 *V2 = (const float2 *)B.vin;
+    const float *tab = (const float *)kp.tables;
+    const uint32_t w1s = P1.nS / (uint32_t)np1;   // G1^(m1-1): weight of the first pipeline digit
+    const GetRow g{V2, pipe1 * w1s, S1, V2[(uint64_t)S1 * A.wk.idx]};
+    const int row = T1 * kp.zlen;
+    const CoefRow w{tab + kp.off_M + row, tab + kp.off_Mc + row, tab + kp.off_Mt + row, kp.zlen};
+    float out[XW];
+    corr_product2<XW>(out, g, A.wk, P2, kp.issuing, A.R, w);
+#pragma unroll
+    for (int x = 0; x < XW; ++x)
+        if (x < P2.G)
+            kp.two_mix[(((uint64_t)(r2 * G2 + (uint32_t)x) * G2 + (uint32_t)a2) * np1 + pipe1) * nt + (uint32_t)T1] =
+                out[x];
+}
+
+// thread = (r1, s2), r1 fastest: the G1 states x + G1 r1 of product 1 with
+// product-2 state s2, all joint orders
+template <int XW>
+__global__ void __launch_bounds__(kGenericThreads)
+twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SolveState *st = kp.st;
+    Bufs B;
+    if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
+    const ProdParams &P1 = kp.p[0];
+    const ProdParams &P2 = kp.p[1];
+    const float *tab = (const float *)kp.tables;
+    // shared: p1, F1 (pn each), then the per-thread column of rest-path indices
+    float *s_p = (float *)smem_raw;
+    float *s_F = s_p + P1.pn;
+    uint32_t *s_col = (uint32_t *)(s_F + P1.pn);
+    for (int i = threadIdx.x; i < P1.pn; i += blockDim.x) {
+        s_p[i] = tab[P1.off_p + i];
+        s_F[i] = tab[P1.off_F + i];
+    }
+    __syncthreads();
+    const uint32_t S1 = P1.nS;
+    const uint32_t G1 = (uint32_t)P1.G, G2 = (uint32_t)P2.G;
+    const uint32_t NR1 = S1 / G1;
+    const int lifo = kp.issuing;
+    const int dmax1 = P1.dmax;
+    const float gam = (float)kp.gamma;
+    const float2 *V2 = (const float2 *)B.vin;
+    float mx = -INFINITY, mn = INFINITY;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < NR1 * P2.nS) {
+        const uint32_t r1 = t % NR1;
+        const uint32_t s2 = t / NR1;
+        const ProdState ps1 = prod_state(P1, r1 * G1);
+        const ProdAction A1 = prod_action(P1, ps1, 0, lifo);
+        const int R1 = A1.R;
+        // rest path of product 1: s'(e) with no order, e = 0..E1
+        const int E1 = lifo ? min(R1, dmax1 + 1) : min(max(R1 - 1, 0), dmax1);
+        {
+            Walker wk = A1.wk;
+            s_col[threadIdx.x] = wk.idx;
+            for (int e = 1; e <= E1; ++e) {
+                walker_step(wk, P1.cb, lifo, G1);
+                s_col[e * blockDim.x + threadIdx.x] = wk.idx;
+            }
+        }
+        const ProdState ps2 = prod_state(P2, s2);
+        const ProdAction A2 = prod_action(P2, ps2, 0, lifo);
+        const float2 R0 = V2[r1 + S1 * A2.wk.idx];
+        const uint32_t np1 = (uint32_t)kp.two_npipe1, nt = (uint32_t)kp.two_nt1;
+        const uint32_t w1s = S1 / np1;
+        const uint32_t pipe_base = r1 / w1s;                        // P_2..P_{L-1} of product 1
+        const uint32_t pipe_step = np1 / G1;                        // G1^(L1-2): weight of the order
+        float bh[XW], bl[XW];
+        int arg[XW];
+#pragma unroll
+        for (int x = 0; x < XW; ++x) {
+            bh[x] = -INFINITY;
+            bl[x] = 0.f;
+            arg[x] = 0;
+        }
+        for (int a2 = 0; a2 < P2.G; ++a2) {
+            const uint32_t i2n = A2.wk.idx + (uint32_t)a2 * P2.w_top;
+            const float2 c = V2[(uint64_t)S1 * i2n];
+            const float *row = kp.two_e2 + ((uint64_t)s2 * G2 + (uint32_t)a2) * S1;
+            const float *mixb = kp.two_mix + ((uint64_t)s2 * G2 + (uint32_t)a2) * np1 * nt;
+            for (int a1 = 0; a1 < P1.G; ++a1) {
+                const uint32_t off = (uint32_t)a1 * P1.w_top;
+                float acc[XW];
+                if (!lifo) {
+                    const float g0 = row[s_col[threadIdx.x] + off];
+                    if (R1 >= 1) {
+#pragma unroll
+                        for (int x = 0; x < XW; ++x) acc[x] = s_F[x] * g0;
+                    } else {
+#pragma unroll
+                        for (int x = 0; x < XW; ++x) acc[x] = (x >= 1) ? s_F[x - 1] * g0 : 0.f;
+                    }
+                    for (int e = 1; e <= E1; ++e) {
+                        const float ge = row[s_col[e * blockDim.x + threadIdx.x] + off];
+#pragma unroll
+                        for (int x = 0; x < XW; ++x) acc[x] = fmaf(s_p[x + e], ge, acc[x]);
+                    }
+                } else {
+                    float sum = 0.f;
+                    const int ne = min(R1, dmax1 + 1);
+                    for (int e = 0; e < ne; ++e) sum = fmaf(s_p[e], row[s_col[e * blockDim.x + threadIdx.x] + off], sum);
+                    if (R1 <= dmax1) {
+                        // d1 in [R1, T1): all of the rest taken, the expiring slot partly
+                        const float gR = row[s_col[R1 * blockDim.x + threadIdx.x] + off];
+                        float cw = 0.f;
+#pragma unroll
+                        for (int x = 0; x < XW; ++x) {
+                            acc[x] = fmaf(cw, gR, sum);
+                            cw += s_p[R1 + x];
+                        }
+                    } else {
+#pragma unroll
+                        for (int x = 0; x < XW; ++x) acc[x] = sum;
+                    }
+                }
+                const float *mixr = mixb + (pipe_base + (uint32_t)a1 * pipe_step) * nt;
+#pragma unroll
+                for (int x = 0; x < XW; ++x) {
+                    const int T1 = x + R1;   // rows exist for T1 <= min(dmax1, m1 Q1)
+                    if (T1 < (int)nt) acc[x] += mixr[T1];
+                }
+                float qh, ql;
+                const float ca =
+                    __fadd_rn(__fmul_rn(-(float)P1.c_o, (float)a1), __fmul_rn(-(float)P2.c_o, (float)a2));
+                action_base(gam, c, R0, ca, qh, ql);
+                const int code = a1 * P2.G + a2;
+#pragma unroll
+                for (int x = 0; x < XW; ++x) {
+                    const float l = __fmaf_rn(gam, acc[x], ql);
+                    const float diff = __fadd_rn(__fsub_rn(qh, bh[x]), __fsub_rn(l, bl[x]));
+                    const bool up = diff > 0.f;
+                    bh[x] = up ? qh : bh[x];
+                    bl[x] = up ? l : bl[x];
+                    arg[x] = up ? code : arg[x];
+                }
+            }
+        }
+        // the expected reward depends on the state only: added after the max
+        const int ys2 = lifo ? A2.R : A2.y1;
+        const int ny2 = lifo ? (P2.tmax + 1) : P2.G;
+#pragma unroll
+        for (int x = 0; x < XW; ++x) {
+            if (x < P1.G) {
+                const uint32_t s = (uint32_t)x + G1 * r1 + S1 * s2;
+                const int T1 = x + R1;
+                const int i1 = (lifo ? R1 : x) * (P1.tmax + 1) + T1;
+                const int i2 = (T1 * ny2 + ys2) * (P2.tmax + 1) + A2.T;
+                float h = bh[x], l = bl[x];
+                pair_add(h, l, tab[kp.off_H1 + i1], tab[kp.off_H1lo + i1]);
+                pair_add(h, l, tab[kp.off_H2 + i2], tab[kp.off_H2lo + i2]);
+                const float2 vold = V2[s];
+                if (mode == MODE_EXTRACT) {
+                    if (B.vout) ((float2 *)B.vout)[s] = vold;
+                } else {
+                    const float2 vnew = pair_finish(gam, R0, h, l);
+                    ((float2 *)B.vout)[s] = vnew;
+                    const float dlt = pair_diff(vnew, vold);
+                    mx = fmaxf(mx, dlt);
+                    mn = fminf(mn, dlt);
+                }
+                if (B.pol) B.pol[s] = (uint8_t)arg[x];
+            }
+        }
+    }
+    if (mode != MODE_EXTRACT) block_reduce_and_finalize<float>(mx, mn, st, mode, gridDim.x);
+}
+
+static int twop_width(int G) { return G <= 8 ? 8 : (G <= 16 ? 16 : 32); }
+
+static cudaError_t describe_twop(const KernelParams &kp, LaunchDesc &d) {
+    const ProdParams &P1 = kp.p[0];
+    const ProdParams &P2 = kp.p[1];
+    const int w1 = twop_width(P1.G), w2 = twop_width(P2.G);
+    const uint64_t n_e2 = (uint64_t)P1.nS * P2.nS;
+    const uint64_t n_mix = (uint64_t)kp.two_npipe1 * (uint32_t)kp.two_nt1 * P2.nS;
+    const uint64_t n_sw = (uint64_t)(P1.nS / (uint32_t)P1.G) * P2.nS;
+    d.fn = (w1 == 8) ? (const void *)twop_sweep_kernel<8>
+                     : (w1 == 16) ? (const void *)twop_sweep_kernel<16> : (const void *)twop_sweep_kernel<32>;
+    d.grid = dim3((unsigned)((n_sw + kGenericThreads - 1) / kGenericThreads));
+    d.block = dim3(kGenericThreads);
+    d.smem = (size_t)2 * P1.pn * sizeof(float) + (size_t)(P1.dmax + 2) * kGenericThreads * sizeof(uint32_t);
+    d.lpr = 0;
+    d.n_pre = 2;
+    d.pre_fn[0] = (w2 == 8) ? (const void *)twop_e2_kernel<8>
+                            : (w2 == 16) ? (const void *)twop_e2_kernel<16> : (const void *)twop_e2_kernel<32>;
+    d.pre_grid[0] = dim3((unsigned)((n_e2 + kGenericThreads - 1) / kGenericThreads));
+    d.pre_block[0] = dim3(kGenericThreads);
+    d.pre_fn[1] = (w2 == 8) ? (const void *)twop_mix_kernel<8>
+                            : (w2 == 16) ? (const void *)twop_mix_kernel<16> : (const void *)twop_mix_kernel<32>;
+    d.pre_grid[1] = dim3((unsigned)((n_mix + kGenericThreads - 1) / kGenericThreads));
+    d.pre_block[1] = dim3(kGenericThreads);
+    return cudaSuccess;
+}
+
+// pipeline classes of product 1's emptied next state: G1^(L1-1) (1 with L1 = 1)
+static size_t two_npipe1(const ProdParams &P1) {
+    size_t n = 1;
+    for (int k = 1; k < P1.L; ++k) n *= (size_t)P1.G;
+    return n;
+}
+
 bool two_supported(const KernelParams &kp, int vk) {
     if (kp.n_products != 2 || vk != VK_PAIR) return false;
     const ProdParams &P1 = kp.p[0];
     const ProdParams &P2 = kp.p[1];
-    if (P1.L != 1 || P2.L != 1) return false;
     size_t mix = 0;
-    return two_table_floats(kp, &mix) <= ((size_t)1 << 27) && mix <= ((size_t)1 << 27);
+    const size_t e2 = two_table_floats(kp, &mix);
+    if (P1.L == 1 && P2.L == 1) return e2 <= ((size_t)1 << 27) && mix <= ((size_t)1 << 27);
+    // lead times >= 2 on both products: the pipeline form; the correlation keeps
+    // up to 32 expiring-slot values per thread and the rest path in shared memory
+    if (P1.L < 2 || P2.L < 2 || P1.m < 2 || P2.m < 2) return false;
+    if (P1.G > 32 || P2.G > 32) return false;
+    if ((size_t)(P1.dmax + 2) * kGenericThreads * 4 + (size_t)2 * P1.pn * 4 > 48 * 1024) return false;
+    return e2 <= ((size_t)1 << 30) && mix <= ((size_t)1 << 30);
 }
+
+int two_mix_rows(const ProdParams &P1) { return (P1.dmax < P1.tmax ? P1.dmax : P1.tmax) + 1; }
 
 size_t two_table_floats(const KernelParams &kp, size_t *mix_floats) {
     const ProdParams &P1 = kp.p[0];
     const ProdParams &P2 = kp.p[1];
-    if (mix_floats) *mix_floats = (size_t)P2.nS * P2.G * (size_t)(P1.dmax + 1);
+    if (mix_floats) *mix_floats = (size_t)P2.nS * P2.G * two_npipe1(P1) * (size_t)two_mix_rows(P1);
     return (size_t)P1.nS * P2.nS * (size_t)P2.G;
 }
 
@@ -914,7 +1461,7 @@ cudaError_t describe_sweep(const KernelParams &kp, int vk, int kahan, int use_gr
     d.lpr = 0;
     d.n_pre = 0;
     if (use_group == kTcWidth) return describe_tc(kp, d);
-    if (use_group == kTwoWidth) return describe_two(kp, d);
+    if (use_group == kTwoWidth) return (kp.p[0].L >= 2) ? describe_twop(kp, d) : describe_two(kp, d);
     if (use_group) {
         const int xw = use_group;   // lane width of the factorised kernel
         const bool pipe = kp.p[0].L >= 2;
@@ -998,10 +1545,10 @@ cudaError_t launch_absdiff(const double *a, const double *b, uint32_t n, SolveSt
 }
 
 cudaError_t launch_rollouts(const KernelParams &kp, const RollParams &rp, const uint8_t *policy, double *returns,
-                            double *kpis, int32_t *traj, cudaStream_t stream) {
+                            double *kpis, double *kpis_prod, int32_t *traj, cudaStream_t stream) {
     const int threads = 128;
     const int blocks = (rp.n_rollouts + threads - 1) / threads;
-    rollout_kernel<<<blocks, threads, 0, stream>>>(kp, rp, policy, returns, kpis, traj);
+    rollout_kernel<<<blocks, threads, 0, stream>>>(kp, rp, policy, returns, kpis, kpis_prod, traj);
     return cudaGetLastError();
 }
 

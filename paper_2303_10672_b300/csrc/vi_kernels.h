@@ -30,6 +30,17 @@ struct RollParams {
     unsigned long long thr[2][kMaxRollDmax + 1];   // floor(2^32 CDF(d)), thr[dmax] = 2^32
 };
 
+// modified base-stock search: slot bounds of the plain stock vectors, and the
+// grid of order-up-to pairs (pair = (S_1 - s_lo[0]) * n2 + (S_2 - s_lo[1]))
+constexpr int kMbsMaxM = 8;   // m <= 8
+constexpr int kMbsMaxL = 4;   // L <= 4
+struct MbsParams {
+    int s_lo[2];
+    int n2, n_pairs;
+    int mu[2];
+    int cap;
+};
+
 bool group_supported(const KernelParams &kp, int vk, int kahan);
 cudaError_t launch_next_states(const KernelParams &kp, const uint32_t *states, int n, uint32_t *out,
                                cudaStream_t stream);
@@ -61,6 +72,8 @@ constexpr int kTcWidth = 100;
 constexpr int kTwoWidth = 200;
 bool two_supported(const KernelParams &kp, int vk);
 size_t two_table_floats(const KernelParams &kp, size_t *mix_floats);
+// rows of the substitution mixture table: product-1 stock T1 = 0..min(dmax1, m1 Q1)
+int two_mix_rows(const ProdParams &P1);
 bool tc_supported(const KernelParams &kp, int vk, int kahan);
 cudaError_t describe_tc(const KernelParams &kp, LaunchDesc &d);
 int batch_width(int G);
@@ -84,6 +97,8 @@ cudaError_t describe_solve_init(uint32_t n, LaunchDesc &d);
 cudaError_t launch_basestock(const KernelParams &kp, const RollParams &rp, int s_lo, int n_S, double *returns,
                              cudaStream_t stream);
 cudaError_t launch_rollouts(const KernelParams &kp, const RollParams &rp, const uint8_t *policy,
-                            double *returns, double *kpis, int32_t *traj, cudaStream_t stream);
+                            double *returns, double *kpis, double *kpis_prod, int32_t *traj, cudaStream_t stream);
+cudaError_t launch_mbs(const KernelParams &kp, const RollParams &rp, const MbsParams &mp, double *returns,
+                       double *kpis_prod, cudaStream_t stream);
 
 }  // namespace vib
