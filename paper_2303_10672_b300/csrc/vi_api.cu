@@ -415,6 +415,31 @@ extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_hand
         }
         kp.two_e2 = h->d_two_e2;
         kp.two_mix = h->d_two_mix;
+        if (kp.p[0].L >= 2) {
+            // rests r1 of product 1 ordered by the units they hold (digits of the
+            // n_rest_slots stock slots), so that a warp's lanes share one path length
+            const ProdParams &P1 = kp.p[0];
+            const uint32_t nr = P1.nS / (uint32_t)P1.G;
+            std::vector<uint32_t> perm(nr), tot(nr);
+            for (uint32_t r = 0; r < nr; ++r) {
+                uint32_t rem = r, sum = 0;
+                for (int j = 0; j < P1.n_rest_slots; ++j) {
+                    sum += rem % (uint32_t)P1.G;
+                    rem /= (uint32_t)P1.G;
+                }
+                tot[r] = sum;
+                perm[r] = r;
+            }
+            std::stable_sort(perm.begin(), perm.end(), [&](uint32_t a, uint32_t b) { return tot[a] < tot[b]; });
+            if ((e = cudaMalloc(&h->d_two_rperm, nr * sizeof(uint32_t))) != cudaSuccess ||
+                (e = cudaMemcpy(h->d_two_rperm, perm.data(), nr * sizeof(uint32_t), cudaMemcpyHostToDevice)) !=
+                    cudaSuccess) {
+                destroy_internal(h);
+                return vi_fail(e == cudaErrorMemoryAllocation ? VI_ENOMEM : VI_ECUDA, "two-product tables: %s",
+                               cudaGetErrorString(e));
+            }
+            kp.two_rperm = h->d_two_rperm;
+        }
         kp.two_nt1 = two_mix_rows(kp.p[0]);
         kp.two_npipe1 = 1;
         for (int k = 1; k < kp.p[0].L; ++k) kp.two_npipe1 *= kp.p[0].G;
@@ -455,6 +480,7 @@ static void destroy_internal(vi_problem *h) {
     if (h->d_scratch) cudaFree(h->d_scratch);
     if (h->d_two_e2) cudaFree(h->d_two_e2);
     if (h->d_two_mix) cudaFree(h->d_two_mix);
+    if (h->d_two_rperm) cudaFree(h->d_two_rperm);
     if (h->d_pe[0]) cudaFree(h->d_pe[0]);
     if (h->d_pe[1]) cudaFree(h->d_pe[1]);
     if (h->d_stage_v) cudaFree(h->d_stage_v);

@@ -31,6 +31,7 @@ struct vi_problem {
     void *d_scratch = nullptr;            // second half of the value ping-pong
     float *d_two_e2 = nullptr;            // two-product expectation tables (factorised sweep)
     float *d_two_mix = nullptr;
+    uint32_t *d_two_rperm = nullptr;      // rests of product 1 ordered by unit total (pipeline form)
     double *d_pe[2] = {nullptr, nullptr};
     void *d_stage_v = nullptr;            // vi_solve_host staging
     uint8_t *d_stage_p = nullptr;

@@ -74,6 +74,7 @@ struct KernelParams {
                           // (lead times >= 2: [s2][a2][pipe1][T1], pipe1 = product-1 pipeline of s')
     int two_nt1;          // T1 values kept: 0..min(dmax1, m1 Q1)
     int two_npipe1;       // product-1 pipeline classes of an emptied next state: G1^(L1-1)
+    const uint32_t *two_rperm;   // lead times >= 2: product-1 rests ordered by their unit total
 };
 
 // ---------------------------------------------------------------------------

@@ -1228,11 +1228,31 @@ twop_mix_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, 
                 out[x];
 }
 
-// thread = (r1, s2), r1 fastest: the G1 states x + G1 r1 of product 1 with
-// product-2 state s2, all joint orders
+// shared-memory layout of the pipeline sweep: four copies of p1 shifted by
+// 0..3 (so that the window p1[e..e+XW) is an aligned float4 run of copy e & 3),
+// F1[x] and F1[x-1] for x < 32, then the per-thread column of rest-path indices
+__host__ __device__ inline int twop_pn4(const ProdParams &P1) { return ((P1.dmax + 36) + 3) & ~3; }
+__host__ __device__ inline size_t twop_smem(const ProdParams &P1, int threads) {
+    return (size_t)(4 * twop_pn4(P1) + 64) * sizeof(float) + (size_t)(P1.dmax + 2) * threads * sizeof(uint32_t);
+}
+
+// orders handled together: their gathers share one probability-window load
 template <int XW>
-__global__ void __launch_bounds__(kGenericThreads)
+struct TwopBlock {
+    static constexpr int AB = (XW <= 8) ? 4 : ((XW <= 16) ? 2 : 1);
+    static constexpr int MINB = (XW <= 16) ? 4 : 3;
+};
+
+// thread = (rank, s2), rank fastest; rank -> r1 through a permutation that
+// orders the rests of product 1 by their unit total R1, so that the lanes of a
+// warp walk rest paths of one length.  The thread computes the G1 states
+// x + G1 r1 of product 1 with product-2 state s2 for every joint order, keeps
+// a float key of Q - gamma R0 - H per state, and forms the exact float pair of
+// the best order once at the end.
+template <int XW>
+__global__ void __launch_bounds__(kGenericThreads, TwopBlock<XW>::MINB)
 twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int) {
+    constexpr int AB = TwopBlock<XW>::AB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SolveState *st = kp.st;
     Bufs B;
@@ -1240,13 +1260,18 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
     const ProdParams &P1 = kp.p[0];
     const ProdParams &P2 = kp.p[1];
     const float *tab = (const float *)kp.tables;
-    // shared: p1, F1 (pn each), then the per-thread column of rest-path indices
-    float *s_p = (float *)smem_raw;
-    float *s_F = s_p + P1.pn;
-    uint32_t *s_col = (uint32_t *)(s_F + P1.pn);
-    for (int i = threadIdx.x; i < P1.pn; i += blockDim.x) {
-        s_p[i] = tab[P1.off_p + i];
-        s_F[i] = tab[P1.off_F + i];
+    const int pn4 = twop_pn4(P1);
+    float *s_pc = (float *)smem_raw;
+    float *s_F0 = s_pc + 4 * pn4;
+    float *s_Fm = s_F0 + 32;
+    uint32_t *s_col = (uint32_t *)(s_Fm + 32);
+    for (int i = threadIdx.x; i < 4 * pn4; i += blockDim.x) {
+        const int j = i / pn4, k = i - j * pn4 + j;
+        s_pc[i] = (k < P1.pn) ? tab[P1.off_p + k] : 0.f;
+    }
+    for (int i = threadIdx.x; i < 32; i += blockDim.x) {
+        s_F0[i] = tab[P1.off_F + i];                      // pn > 32 always
+        s_Fm[i] = (i == 0) ? 0.f : tab[P1.off_F + i - 1];
     }
     __syncthreads();
     const uint32_t S1 = P1.nS;
@@ -1256,10 +1281,11 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
     const int dmax1 = P1.dmax;
     const float gam = (float)kp.gamma;
     const float2 *V2 = (const float2 *)B.vin;
+    const uint32_t bd = blockDim.x, tid = threadIdx.x;
     float mx = -INFINITY, mn = INFINITY;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < NR1 * P2.nS) {
-        const uint32_t r1 = t % NR1;
+        const uint32_t r1 = kp.two_rperm[t % NR1];
         const uint32_t s2 = t / NR1;
         const ProdState ps1 = prod_state(P1, r1 * G1);
         const ProdAction A1 = prod_action(P1, ps1, 0, lifo);
@@ -1268,10 +1294,10 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
         const int E1 = lifo ? min(R1, dmax1 + 1) : min(max(R1 - 1, 0), dmax1);
         {
             Walker wk = A1.wk;
-            s_col[threadIdx.x] = wk.idx;
+            s_col[tid] = wk.idx;
             for (int e = 1; e <= E1; ++e) {
                 walker_step(wk, P1.cb, lifo, G1);
-                s_col[e * blockDim.x + threadIdx.x] = wk.idx;
+                s_col[e * bd + tid] = wk.idx;
             }
         }
         const ProdState ps2 = prod_state(P2, s2);
@@ -1281,12 +1307,12 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
         const uint32_t w1s = S1 / np1;
         const uint32_t pipe_base = r1 / w1s;                        // P_2..P_{L-1} of product 1
         const uint32_t pipe_step = np1 / G1;                        // G1^(L1-2): weight of the order
-        float bh[XW], bl[XW];
+        const float *cf0 = (R1 >= 1) ? s_F0 : s_Fm;                 // weight of the rest-free path
+        float key[XW];
         int arg[XW];
 #pragma unroll
         for (int x = 0; x < XW; ++x) {
-            bh[x] = -INFINITY;
-            bl[x] = 0.f;
+            key[x] = -INFINITY;
             arg[x] = 0;
         }
         for (int a2 = 0; a2 < P2.G; ++a2) {
@@ -1294,74 +1320,130 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
             const float2 c = V2[(uint64_t)S1 * i2n];
             const float *row = kp.two_e2 + ((uint64_t)s2 * G2 + (uint32_t)a2) * S1;
             const float *mixb = kp.two_mix + ((uint64_t)s2 * G2 + (uint32_t)a2) * np1 * nt;
-            for (int a1 = 0; a1 < P1.G; ++a1) {
-                const uint32_t off = (uint32_t)a1 * P1.w_top;
-                float acc[XW];
+            for (int a1b = 0; a1b < P1.G; a1b += AB) {
+                uint32_t off[AB];
+#pragma unroll
+                for (int j = 0; j < AB; ++j) off[j] = (uint32_t)min(a1b + j, P1.G - 1) * P1.w_top;
+                float acc[AB][XW];
                 if (!lifo) {
-                    const float g0 = row[s_col[threadIdx.x] + off];
-                    if (R1 >= 1) {
+                    const uint32_t i0 = s_col[tid];
 #pragma unroll
-                        for (int x = 0; x < XW; ++x) acc[x] = s_F[x] * g0;
-                    } else {
+                    for (int j = 0; j < AB; ++j) {
+                        const float g = row[i0 + off[j]];
 #pragma unroll
-                        for (int x = 0; x < XW; ++x) acc[x] = (x >= 1) ? s_F[x - 1] * g0 : 0.f;
+                        for (int q = 0; q < XW / 4; ++q) {
+                            const float4 f = ((const float4 *)cf0)[q];
+                            acc[j][4 * q + 0] = __fmul_rn(f.x, g);
+                            acc[j][4 * q + 1] = __fmul_rn(f.y, g);
+                            acc[j][4 * q + 2] = __fmul_rn(f.z, g);
+                            acc[j][4 * q + 3] = __fmul_rn(f.w, g);
+                        }
                     }
                     for (int e = 1; e <= E1; ++e) {
-                        const float ge = row[s_col[e * blockDim.x + threadIdx.x] + off];
+                        const uint32_t ie = s_col[e * bd + tid];
+                        float g[AB];
 #pragma unroll
-                        for (int x = 0; x < XW; ++x) acc[x] = fmaf(s_p[x + e], ge, acc[x]);
+                        for (int j = 0; j < AB; ++j) g[j] = row[ie + off[j]];
+                        const float4 *pw = (const float4 *)(s_pc + (e & 3) * pn4 + (e & ~3));
+#pragma unroll
+                        for (int q = 0; q < XW / 4; ++q) {
+                            const float4 f = pw[q];
+#pragma unroll
+                            for (int j = 0; j < AB; ++j) {
+                                acc[j][4 * q + 0] = __fmaf_rn(f.x, g[j], acc[j][4 * q + 0]);
+                                acc[j][4 * q + 1] = __fmaf_rn(f.y, g[j], acc[j][4 * q + 1]);
+                                acc[j][4 * q + 2] = __fmaf_rn(f.z, g[j], acc[j][4 * q + 2]);
+                                acc[j][4 * q + 3] = __fmaf_rn(f.w, g[j], acc[j][4 * q + 3]);
+                            }
+                        }
                     }
                 } else {
-                    float sum = 0.f;
                     const int ne = min(R1, dmax1 + 1);
-                    for (int e = 0; e < ne; ++e) sum = fmaf(s_p[e], row[s_col[e * blockDim.x + threadIdx.x] + off], sum);
-                    if (R1 <= dmax1) {
-                        // d1 in [R1, T1): all of the rest taken, the expiring slot partly
-                        const float gR = row[s_col[R1 * blockDim.x + threadIdx.x] + off];
-                        float cw = 0.f;
 #pragma unroll
-                        for (int x = 0; x < XW; ++x) {
-                            acc[x] = fmaf(cw, gR, sum);
-                            cw += s_p[R1 + x];
+                    for (int j = 0; j < AB; ++j) {
+                        float sum = 0.f;
+                        for (int e = 0; e < ne; ++e) sum = __fmaf_rn(s_pc[e], row[s_col[e * bd + tid] + off[j]], sum);
+                        if (R1 <= dmax1) {
+                            // d1 in [R1, T1): all of the rest taken, the expiring slot partly
+                            const float gR = row[s_col[R1 * bd + tid] + off[j]];
+                            float cw = 0.f;
+#pragma unroll
+                            for (int x = 0; x < XW; ++x) {
+                                acc[j][x] = __fmaf_rn(cw, gR, sum);
+                                cw = __fadd_rn(cw, s_pc[R1 + x]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int x = 0; x < XW; ++x) acc[j][x] = sum;
                         }
-                    } else {
-#pragma unroll
-                        for (int x = 0; x < XW; ++x) acc[x] = sum;
                     }
                 }
-                const float *mixr = mixb + (pipe_base + (uint32_t)a1 * pipe_step) * nt;
 #pragma unroll
-                for (int x = 0; x < XW; ++x) {
-                    const int T1 = x + R1;   // rows exist for T1 <= min(dmax1, m1 Q1)
-                    if (T1 < (int)nt) acc[x] += mixr[T1];
-                }
-                float qh, ql;
-                const float ca =
-                    __fadd_rn(__fmul_rn(-(float)P1.c_o, (float)a1), __fmul_rn(-(float)P2.c_o, (float)a2));
-                action_base(gam, c, R0, ca, qh, ql);
-                const int code = a1 * P2.G + a2;
+                for (int j = 0; j < AB; ++j) {
+                    const int a1 = a1b + j;
+                    if (a1 < P1.G) {
+                        const float *mixr = mixb + (pipe_base + (uint32_t)a1 * pipe_step) * nt;
+                        float qh, ql;
+                        const float ca =
+                            __fadd_rn(__fmul_rn(-(float)P1.c_o, (float)a1), __fmul_rn(-(float)P2.c_o, (float)a2));
+                        action_base(gam, c, R0, ca, qh, ql);
+                        const float base = __fadd_rn(qh, ql);
+                        const int code = a1 * P2.G + a2;
 #pragma unroll
-                for (int x = 0; x < XW; ++x) {
-                    const float l = __fmaf_rn(gam, acc[x], ql);
-                    const float diff = __fadd_rn(__fsub_rn(qh, bh[x]), __fsub_rn(l, bl[x]));
-                    const bool up = diff > 0.f;
-                    bh[x] = up ? qh : bh[x];
-                    bl[x] = up ? l : bl[x];
-                    arg[x] = up ? code : arg[x];
+                        for (int x = 0; x < XW; ++x) {
+                            const int T1 = x + R1;   // mixture rows exist for T1 <= min(dmax1, m1 Q1)
+                            const float ax = (T1 < (int)nt) ? __fadd_rn(acc[j][x], mixr[T1]) : acc[j][x];
+                            const float k = __fmaf_rn(gam, ax, base);
+                            const bool up = k > key[x];
+                            key[x] = up ? k : key[x];
+                            arg[x] = up ? code : arg[x];
+                        }
+                    }
                 }
             }
         }
-        // the expected reward depends on the state only: added after the max
+        // exact float pair of the chosen order; the expected reward depends on
+        // the state only and is added after the max
         const int ys2 = lifo ? A2.R : A2.y1;
         const int ny2 = lifo ? (P2.tmax + 1) : P2.G;
 #pragma unroll
         for (int x = 0; x < XW; ++x) {
             if (x < P1.G) {
-                const uint32_t s = (uint32_t)x + G1 * r1 + S1 * s2;
+                const int a1 = arg[x] / P2.G, a2 = arg[x] - a1 * P2.G;
+                const uint32_t i2n = A2.wk.idx + (uint32_t)a2 * P2.w_top;
+                const float2 c = V2[(uint64_t)S1 * i2n];
+                const float *row = kp.two_e2 + ((uint64_t)s2 * G2 + (uint32_t)a2) * S1;
+                const uint32_t off = (uint32_t)a1 * P1.w_top;
+                float ax;
+                if (!lifo) {
+                    ax = __fmul_rn(cf0[x], row[s_col[tid] + off]);
+                    for (int e = 1; e <= E1; ++e) ax = __fmaf_rn(s_pc[x + e], row[s_col[e * bd + tid] + off], ax);
+                } else {
+                    float sum = 0.f;
+                    const int ne = min(R1, dmax1 + 1);
+                    for (int e = 0; e < ne; ++e) sum = __fmaf_rn(s_pc[e], row[s_col[e * bd + tid] + off], sum);
+                    if (R1 <= dmax1) {
+                        float cw = 0.f;
+                        for (int y = 0; y < x; ++y) cw = __fadd_rn(cw, s_pc[R1 + y]);
+                        ax = __fmaf_rn(cw, row[s_col[R1 * bd + tid] + off], sum);
+                    } else {
+                        ax = sum;
+                    }
+                }
                 const int T1 = x + R1;
+                if (T1 < (int)nt) {
+                    const float *mixr = kp.two_mix + (((uint64_t)s2 * G2 + (uint32_t)a2) * np1 + pipe_base +
+                                                      (uint32_t)a1 * pipe_step) * nt;
+                    ax = __fadd_rn(ax, mixr[T1]);
+                }
+                float h, l;
+                const float ca =
+                    __fadd_rn(__fmul_rn(-(float)P1.c_o, (float)a1), __fmul_rn(-(float)P2.c_o, (float)a2));
+                action_base(gam, c, R0, ca, h, l);
+                l = __fmaf_rn(gam, ax, l);
+                const uint32_t s = (uint32_t)x + G1 * r1 + S1 * s2;
                 const int i1 = (lifo ? R1 : x) * (P1.tmax + 1) + T1;
                 const int i2 = (T1 * ny2 + ys2) * (P2.tmax + 1) + A2.T;
-                float h = bh[x], l = bl[x];
                 pair_add(h, l, tab[kp.off_H1 + i1], tab[kp.off_H1lo + i1]);
                 pair_add(h, l, tab[kp.off_H2 + i2], tab[kp.off_H2lo + i2]);
                 const float2 vold = V2[s];
@@ -1394,7 +1476,7 @@ static cudaError_t describe_twop(const KernelParams &kp, LaunchDesc &d) {
                      : (w1 == 16) ? (const void *)twop_sweep_kernel<16> : (const void *)twop_sweep_kernel<32>;
     d.grid = dim3((unsigned)((n_sw + kGenericThreads - 1) / kGenericThreads));
     d.block = dim3(kGenericThreads);
-    d.smem = (size_t)2 * P1.pn * sizeof(float) + (size_t)(P1.dmax + 2) * kGenericThreads * sizeof(uint32_t);
+    d.smem = twop_smem(P1, kGenericThreads);
     d.lpr = 0;
     d.n_pre = 2;
     d.pre_fn[0] = (w2 == 8) ? (const void *)twop_e2_kernel<8>
@@ -1426,7 +1508,7 @@ bool two_supported(const KernelParams &kp, int vk) {
     // up to 32 expiring-slot values per thread and the rest path in shared memory
     if (P1.L < 2 || P2.L < 2 || P1.m < 2 || P2.m < 2) return false;
     if (P1.G > 32 || P2.G > 32) return false;
-    if ((size_t)(P1.dmax + 2) * kGenericThreads * 4 + (size_t)2 * P1.pn * 4 > 48 * 1024) return false;
+    if (twop_smem(P1, kGenericThreads) > 48 * 1024) return false;
     return e2 <= ((size_t)1 << 30) && mix <= ((size_t)1 << 30);
 }
 
