@@ -398,6 +398,7 @@ def run_native(args):
 
     out = None
     paper_a = run_paper_scenario_a(vi, torch, stream) if rank == 0 else None
+    paper_b = run_paper_scenario_b(vi, torch, stream) if rank == 0 else None
     serving = run_serving(args.serving) if (args.serving > 0 and rank == 0) else None
     if rank == 0:
         cpu = oracle_sample_rate(inst, args.cpu_seconds) if args.cpu_seconds > 0 else None
@@ -421,6 +422,7 @@ def run_native(args):
             "rollouts": rollouts,
             "policy_search": policy_search,
             "paper_scenario_a": paper_a,
+            "paper_scenario_b": paper_b,
             "wall_s": wall,
         }
         print(json.dumps(out))
@@ -460,6 +462,87 @@ def run_paper_scenario_a(vi, torch, stream) -> dict:
             "vi_solve_ms": solve_ms, "paper_vi_wall_s": 1185.0,
             "return_mean": float(r.mean()), "return_sd": float(r.std(ddof=1)),
             "paper_return_mean": -1432.0, "paper_return_sd": 55.0}
+
+
+SCEN_B_TABLES = os.path.join(ROOT, "tests", "golden", "scenario_b_tables.json")
+
+
+def run_paper_scenario_b(vi, torch, stream) -> dict:
+    """The paper's Scenario B (two products, half of product B's unmet demand takes
+    product A): the four Ortega et al. settings P1-P4 at exactly 100 iterations
+    (Table 5) and the largest Hendrix et al. setting, m = 3 experiment 1 with
+    16,777,216 states, to the span test (Table 4), each from V_0 = the expected
+    one-day revenue (one sweep from V = 0); the 10,000-rollout return of each
+    value-iteration policy; and the modified base-stock search over the paper's
+    whole (S_A, S_B) grid (4,000 rollouts x 365 days after 100) for P1 and m = 3
+    experiment 1.  Times are CUDA-event device times on the launching stream."""
+    rows = {r["name"]: r for r in json.load(open(SCEN_B_TABLES))["rows"]}
+    RO = workloads.SCENARIO_B_ROLLOUTS
+    out = {"note": "paper times: RTX 3060, FP64 JAX (Tables 4 and 5); updates = |S| |A| |Omega| x iterations "
+                   "with |Omega| = (m A_A + 1)(m A_B + 1), the paper's issued-units outcome count",
+           "experiments": []}
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    for name in ("P1", "P2", "P3", "P4", "m3_exp1"):
+        row = rows[name]
+        inst = workloads.scenario_b(name)
+        prods = [dict(m=p.m, L=p.L, Q=p.Q, cost=p.cost, pmf=p.pmf) for p in inst.products]
+        desc, keep = vi.make_desc(prods, inst.gamma, inst.issuing, vi.VI_PREC_FP32, vi.VI_STOP_SPAN,
+                                  inst.subst_rate)
+        h = vi.vi_problem_create_desc(desc)
+        n = vi.vi_problem_sizes(h)["n_states"]
+        Z = torch.zeros(n, dtype=torch.float64, device="cuda")
+        V = torch.empty(n, dtype=torch.float64, device="cuda")
+        pol = torch.empty(n, dtype=torch.uint8, device="cuda")
+        fixed = row["vi_iterations"]
+        tol, cap = (0.0, fixed) if fixed else (workloads.SCENARIO_B["eps"], 100000)
+
+        def solve():
+            vi.vi_backup(h, Z, V, stream=stream, stats=False)     # V_0 = expected revenue
+            return vi.vi_solve(h, tol, cap, V, pol, stream=stream, flags=vi.VI_FLAG_WARM_START)
+
+        solve()                                                 # warm-up (graph build)
+        info, ms = timed(solve)
+        ret = torch.empty(RO["n_rollouts"], dtype=torch.float64, device="cuda")
+        vi.vi_simulate(h, pol, RO["n_rollouts"], RO["horizon"], RO["warmup"], 2023, ret, stream=stream)
+        r = ret.cpu().numpy()
+        iters = info["iters"]
+        updates = float(n) * row["n_actions"] * row["n_outcomes"] * iters
+        e = {"experiment": name, "table": row["table"], "states": n, "iterations": iters,
+             "converged": bool(info["status"] == vi.VI_OK) if not fixed else None,
+             "vi_ms": ms, "paper_vi_wall_s": row["vi_wall_s"], "speedup_vs_paper": row["vi_wall_s"] * 1e3 / ms,
+             "paper_updates_per_s": updates / (ms / 1e3),
+             "paper_own_updates_per_s": updates / row["vi_wall_s"] if fixed else None,
+             "return_mean": float(r.mean()), "return_sd": float(r.std(ddof=1)),
+             "paper_return_mean": row["vi_return_mean"], "paper_return_sd": row["vi_return_sd"]}
+        if name in ("P1", "m3_exp1"):
+            lo, hi = (0, 0), (2 * row["amax_b"], 2 * row["amax_a"])
+            mu = (row["mu_b"], row["mu_a"])
+            npairs = (hi[0] + 1) * (hi[1] + 1)
+            grid = torch.empty(npairs * 4000, dtype=torch.float64, device="cuda")
+            vi.vi_mbs_search(h, lo, hi, mu, False, 64, 10, 0, 7, grid, stream=stream, means=False)  # warm-up
+            _, sms = timed(lambda: vi.vi_mbs_search(h, lo, hi, mu, False, 4000, 365, 100, 7, grid, stream=stream,
+                                                    means=False))
+            gm = grid.view(npairs, 4000).mean(dim=1)
+            bi = int(torch.argmax(gm).item())
+            best = (bi // (hi[1] + 1), bi % (hi[1] + 1))
+            e["base_stock_search"] = {
+                "pairs": npairs, "rollouts": 4000, "days": 465, "ms": sms, "paper_so_wall_s": row["so_wall_s"],
+                "best_S_A_B": [int(best[1]), int(best[0])],
+                "paper_best_S_A_B": [row["kpis"]["A"]["s_best"], row["kpis"]["B"]["s_best"]],
+                "rollout_periods_per_s": npairs * 4000 * 465 / (sms / 1e3)}
+        out["experiments"].append(e)
+        vi.vi_problem_destroy(h)
+        del Z, V, pol
+    return out
 
 
 def run_serving(n_requests: int = 512, seed: int = 5, slots: int = 64, budget_gb: float = 64.0) -> dict:

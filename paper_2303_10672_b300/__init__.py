@@ -276,19 +276,24 @@ def vi_simulate_ex(h: int, policy, n_rollouts: int, horizon: int, warmup: int, s
 
 
 def vi_mbs_search(h: int, S_lo, S_hi, mu, cap: bool, n_rollouts: int, horizon: int, warmup: int, seed: int,
-                  returns, kpis_prod=None, stream=None):
+                  returns, kpis_prod=None, stream=None, means: bool = True):
     """Modified base-stock search over the (S_1, S_2) grid: per-pair mean returns
     (row-major, product 1 outer) and the best pair; per-rollout returns (and
-    per-product KPIs if given) land in the device buffers."""
+    per-product KPIs if given) land in the device buffers.  means=False only
+    launches (no synchronisation) and returns None."""
     lo = (C.c_int * 2)(*(list(S_lo) + [0] * (2 - len(S_lo))))
     hi = (C.c_int * 2)(*(list(S_hi) + [0] * (2 - len(S_hi))))
     mv = (C.c_int * 2)(*(list(mu) + [0] * (2 - len(mu))))
     n_pairs = (hi[0] - lo[0] + 1) * ((hi[1] - lo[1] + 1) if len(S_lo) == 2 else 1)
-    means = (C.c_double * n_pairs)()
+    if not means:
+        _check(lib().vi_mbs_search(h, lo, hi, mv, int(bool(cap)), n_rollouts, horizon, warmup, C.c_uint64(seed),
+                                   _addr(returns), _addr(kpis_prod), None, None, _stream(stream)), "vi_mbs_search")
+        return None
+    mr = (C.c_double * n_pairs)()
     best = (C.c_int * 2)()
     _check(lib().vi_mbs_search(h, lo, hi, mv, int(bool(cap)), n_rollouts, horizon, warmup, C.c_uint64(seed),
-                               _addr(returns), _addr(kpis_prod), means, best, _stream(stream)), "vi_mbs_search")
-    return np.array(list(means)), (best[0], best[1])
+                               _addr(returns), _addr(kpis_prod), mr, best, _stream(stream)), "vi_mbs_search")
+    return np.array(list(mr)), (best[0], best[1])
 
 
 def vi_problem_kernel(h: int) -> tuple:
