@@ -40,6 +40,10 @@ WORKLOADS = {
     "cfg2": workloads.config2,
     "cfg3": workloads.config3,
     "cfg4": workloads.config4,
+    # the paper's Scenario B settings (for profiling the two-product pipeline sweep)
+    "scenB_P4": lambda: workloads.scenario_b("P4"),
+    "scenB_m3_exp1": lambda: workloads.scenario_b("m3_exp1"),
+    "scenB_m3_exp3": lambda: workloads.scenario_b("m3_exp3"),
 }
 TOL = 1e-4
 MAX_ITERS = 5_000
@@ -208,12 +212,61 @@ def run_reference(args):
 # the CUDA path
 # ---------------------------------------------------------------------------
 
+def _rest_totals(p) -> np.ndarray:
+    """Units held by each rest r (digits 1.. of a product state) in the slots the
+    demand can reach: n_rest_slots = m - 2 (L = 1) or m - 1 (L >= 2) digits."""
+    G, K = p.Q + 1, p.n_digits
+    nslots = (p.m - 2) if p.L == 1 else (p.m - 1)
+    r = np.arange(G ** (K - 1), dtype=np.int64)
+    tot = np.zeros_like(r)
+    for _ in range(max(nslots, 0)):
+        tot += r % G
+        r //= G
+    return tot
+
+
+def two_product_fmas(inst) -> int:
+    """Multiply-adds one sweep of the factorised two-product method performs (the
+    products are not expanded over the joint (d1, d2, u) outcomes): the product-2
+    expectation table E2, the substitution-mixture table and the sweep's sum over
+    d1 below product 1's stock, counted per (state, order) as the kernels loop."""
+    p1, p2 = inst.products
+    G1, G2 = p1.Q + 1, p2.Q + 1
+    S1, S2 = p1.n_states, p2.n_states
+    D1 = p1.dmax
+    R1, R2 = _rest_totals(p1), _rest_totals(p2)
+    nt = min(D1, p1.m * p1.Q) + 1
+    if p1.L >= 2 and p2.L >= 2:
+        e1 = np.minimum(np.maximum(R1 - 1, 0), D1) + 1          # terms per order of a rest of product 1
+        sweep = int(S2) * G1 * G2 * G1 * int(e1.sum())
+        terms2 = int((R2 + 1).sum()) * G2                         # per (i1 or mixture row, a2), all x2
+        npipe1 = G1 ** (p1.L - 1)
+        return sweep + S1 * G2 * terms2 + npipe1 * nt * G2 * terms2
+    # lead time 1: the order joins product 1's rest; d1 runs below T1 = x + R1 + a1
+    x = np.arange(G1)[:, None, None]
+    a = np.arange(G1)[None, None, :]
+    T1 = x + R1[None, :, None] + a
+    sweep = int(np.minimum(T1, D1 + 1).sum()) * G2 * S2
+    a2 = np.arange(G2)[None, :]
+    terms2 = int((R2[:, None] + a2 + 1).sum()) * G2               # per (i1 or mixture row), all (s2, a2)
+    return sweep + S1 * terms2 + nt * terms2
+
+
 def algorithmic_work(inst) -> dict:
-    """Algorithmic work of one Bellman sweep: one multiply-add of p(d) and the
-    next-state value per (state, order, demand outcome), and the compulsory HBM
-    bytes (old and new value of every state, 8 B float pair each)."""
+    """Algorithmic work of one Bellman sweep and the compulsory HBM bytes (old and
+    new value of every state, 8 B float pair each).  One product: one
+    multiply-add of p(d) and the next-state value per (state, order, demand
+    outcome), which the factorised kernel performs exactly.  Two products: the
+    multiply-adds of the factorised method (two_product_fmas); `updates` stays the
+    nominal |S| |A| |Omega|."""
     updates = inst.updates_per_sweep
-    return {"updates": updates, "flops": 2 * updates, "bytes": inst.n_states * 16}
+    if len(inst.products) == 2:
+        fmas = two_product_fmas(inst)
+        return {"updates": updates, "flops": 2 * fmas, "bytes": inst.n_states * 16,
+                "work": "2 flop per multiply-add of the factorised two-product method (E2 table, "
+                        "substitution mixture, sum over d1 below stock)"}
+    return {"updates": updates, "flops": 2 * updates, "bytes": inst.n_states * 16,
+            "work": "2 flop (one multiply-add) per state x order x demand outcome"}
 
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu captures
@@ -311,7 +364,8 @@ def run_native(args):
     kernel_name = {vi.VI_KERNEL_GENERIC: "sweep_generic_kernel", vi.VI_KERNEL_TENSOR: "sweep_tc_kernel"}.get(
         kch, f"sweep_group_kernel (lane width {kw})")
     if len(inst.products) == 2 and kch == vi.VI_KERNEL_GROUP:
-        kernel_name = "two_e2_kernel + two_mix_kernel + sweep_two_kernel"
+        kernel_name = ("twop_e2_kernel + twop_mix_kernel + twop_sweep_kernel" if inst.products[0].L >= 2
+                       else "two_e2_kernel + two_mix_kernel + sweep_two_kernel")
     work = algorithmic_work(inst)
     pk = peaks()
     sm_mhz = clocks.get("sm_mhz") or pk["sm_max_mhz"]
@@ -323,11 +377,14 @@ def run_native(args):
         "bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
         "frac": achieved_tflops / fp32_peak_tflops, "traffic": NCU_TRAFFIC.get((inst.name, kernel_name)),
         "kernel": kernel_name, "kernel_ms": k_ms,
-        "work": "2 flop (one multiply-add) per state x order x demand outcome",
+        "work": work["work"],
         "peak_basis": f"148 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock sampled)",
-        "gather": {"logical_GBs": gather_gbs, "l2_read_peak_GBs": l2_gbs, "frac": gather_gbs / l2_gbs,
-                   "basis": "4 B of next-state value per update vs an L1-bypassing read of a 32 MiB "
-                            "L2-resident buffer (measured here)"},
+        # one product: every nominal update gathers one next-state value; the
+        # two-product method does not expand the joint outcomes, so no such model
+        "gather": None if len(inst.products) == 2 else {
+            "logical_GBs": gather_gbs, "l2_read_peak_GBs": l2_gbs, "frac": gather_gbs / l2_gbs,
+            "basis": "4 B of next-state value per update vs an L1-bypassing read of a 32 MiB "
+                     "L2-resident buffer (measured here)"},
         "hbm_compulsory_GBs": work["bytes"] / (k_ms * 1e-3) / 1e9, "hbm_peak_GBs": pk["hbm_gbs"],
     }
 
@@ -397,8 +454,8 @@ def run_native(args):
     d2h = n * sizes["value_bytes"] + n
 
     out = None
-    paper_a = run_paper_scenario_a(vi, torch, stream) if rank == 0 else None
-    paper_b = run_paper_scenario_b(vi, torch, stream) if rank == 0 else None
+    paper_a = run_paper_scenario_a(vi, torch, stream) if (rank == 0 and args.paper) else None
+    paper_b = run_paper_scenario_b(vi, torch, stream) if (rank == 0 and args.paper) else None
     serving = run_serving(args.serving) if (args.serving > 0 and rank == 0) else None
     if rank == 0:
         cpu = oracle_sample_rate(inst, args.cpu_seconds) if args.cpu_seconds > 0 else None
@@ -479,7 +536,9 @@ def run_paper_scenario_b(vi, torch, stream) -> dict:
     rows = {r["name"]: r for r in json.load(open(SCEN_B_TABLES))["rows"]}
     RO = workloads.SCENARIO_B_ROLLOUTS
     out = {"note": "paper times: RTX 3060, FP64 JAX (Tables 4 and 5); updates = |S| |A| |Omega| x iterations "
-                   "with |Omega| = (m A_A + 1)(m A_B + 1), the paper's issued-units outcome count",
+                   "with |Omega| = (m A_A + 1)(m A_B + 1), the paper's issued-units outcome count; method_tflops = "
+                   "2 x the factorised method's multiply-adds per sweep (bench.two_product_fmas) x sweeps / time, "
+                   "against 148 x 128 x 2 flop x SM clock (77 TFLOP/s at 2032 MHz)",
            "experiments": []}
 
     def timed(fn):
@@ -516,11 +575,13 @@ def run_paper_scenario_b(vi, torch, stream) -> dict:
         r = ret.cpu().numpy()
         iters = info["iters"]
         updates = float(n) * row["n_actions"] * row["n_outcomes"] * iters
+        method_tflops = 2.0 * two_product_fmas(inst) * (iters + 1) / (ms * 1e-3) / 1e12   # + the V_0 sweep
         e = {"experiment": name, "table": row["table"], "states": n, "iterations": iters,
              "converged": bool(info["status"] == vi.VI_OK) if not fixed else None,
              "vi_ms": ms, "paper_vi_wall_s": row["vi_wall_s"], "speedup_vs_paper": row["vi_wall_s"] * 1e3 / ms,
              "paper_updates_per_s": updates / (ms / 1e3),
              "paper_own_updates_per_s": updates / row["vi_wall_s"] if fixed else None,
+             "method_tflops": method_tflops,
              "return_mean": float(r.mean()), "return_sd": float(r.std(ddof=1)),
              "paper_return_mean": row["vi_return_mean"], "paper_return_sd": row["vi_return_sd"]}
         if name in ("P1", "m3_exp1"):
@@ -653,6 +714,7 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp32", "fp32_kahan", "fp64", "fp32_single"])
     ap.add_argument("--max-iters", type=int, default=MAX_ITERS)
     ap.add_argument("--serving", type=int, default=512, help="requests in the serving mix (0 = skip)")
+    ap.add_argument("--paper", type=int, default=1, help="the paper's Scenario A/B results (0 = skip)")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven sweep loop instead of the CUDA graph (same kernels; lets a profiler see each launch)")
     ap.add_argument("--kernel", choices=["auto", "group", "tensor", "generic"], default="auto",
