@@ -16,7 +16,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liboracle.so")
-SOURCES = [os.path.join(HERE, "oracle.c")]
+SOURCES = [os.path.join(HERE, "oracle.c"), os.path.join(HERE, "oracle_pc.c")]
 
 
 def build(force: bool = False) -> str:
@@ -53,6 +53,23 @@ class _Step(C.Structure):
     ]
 
 
+class _Periodic(C.Structure):
+    _fields_ = [
+        ("m", C.c_int), ("Q", C.c_int), ("dmax", C.c_int),
+        ("pmf", C.POINTER(C.c_double)),
+        ("c0", C.c_double * 9), ("c1", C.c_double * 9),
+        ("cost", C.c_double * 4),
+        ("gamma", C.c_double),
+    ]
+
+
+class _PcStep(C.Structure):
+    _fields_ = [
+        ("s_next", C.c_longlong), ("reward", C.c_double), ("demand", C.c_double), ("issued", C.c_double),
+        ("wasted", C.c_double), ("held", C.c_double), ("accepted", C.c_double), ("refused", C.c_double),
+    ]
+
+
 _lib = None
 
 
@@ -82,6 +99,20 @@ def lib():
         L.orc_simulate_ex.argtypes = [P, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_basestock_policy.argtypes = [P, C.c_int, C.c_void_p]
+        PP = C.POINTER(_Periodic)
+        L.orc_pc_num_states.argtypes = [PP]
+        L.orc_pc_num_states.restype = C.c_longlong
+        L.orc_pc_arrival_params.argtypes = [PP, C.c_int, C.c_void_p]
+        L.orc_pc_arrival_prob.argtypes = [PP, C.c_int, C.c_void_p]
+        L.orc_pc_arrival_prob.restype = C.c_double
+        L.orc_pc_next_profile.argtypes = [C.c_int, C.c_int, C.c_void_p]
+        L.orc_pc_transition.argtypes = [PP, C.c_longlong, C.c_int, C.c_int, C.c_void_p, C.POINTER(_PcStep)]
+        L.orc_pc_qvalues.argtypes = [PP, dp, C.c_longlong, dp]
+        L.orc_pc_backup_states.argtypes = [PP, dp, C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p, C.c_int]
+        L.orc_pc_vi_solve.argtypes = [PP, C.c_double, C.c_int, C.c_int, dp, C.c_void_p, C.POINTER(C.c_int), dp,
+                                      dp, dp, C.c_int]
+        L.orc_pc_simulate.argtypes = [PP, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_void_p,
+                                      C.c_void_p, C.c_void_p]
         L.orc_issued_pmf.argtypes = [P, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p]
         L.orc_mbs_simulate.argtypes = [P, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
                                        C.c_uint64, C.c_void_p, C.c_void_p]
@@ -236,3 +267,99 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     o = np.empty(4, np.uint32)
     lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(o))
     return o
+
+
+class PeriodicProblem:
+    """An oracle view of a workloads.PeriodicInstance (Scenario C)."""
+
+    def __init__(self, inst):
+        self.inst = inst
+        st = _Periodic()
+        st.m, st.Q, st.dmax = inst.m, inst.Q, inst.dmax
+        self._pmf = np.ascontiguousarray(inst.pmf, dtype=np.float64).reshape(7, inst.dmax + 1)
+        st.pmf = self._pmf.ctypes.data_as(C.POINTER(C.c_double))
+        for k in range(9):
+            st.c0[k] = float(inst.c0[k]) if k < len(inst.c0) else 0.0
+            st.c1[k] = float(inst.c1[k]) if k < len(inst.c1) else 0.0
+        for j in range(4):
+            st.cost[j] = float(inst.cost[j])
+        st.gamma = float(inst.gamma)
+        self.st = st
+        self.n_states = int(lib().orc_pc_num_states(C.byref(st)))
+        self.n_actions = inst.Q + 1
+
+    @property
+    def ref(self):
+        return C.byref(self.st)
+
+    def arrival_params(self, a: int) -> np.ndarray:
+        p = np.zeros(9, np.float64)
+        lib().orc_pc_arrival_params(self.ref, a, _ptr(p))
+        return p[1:self.inst.m + 1].copy()
+
+    def arrival_prob(self, a: int, y) -> float:
+        v = np.zeros(9, np.int32)
+        v[1:len(y) + 1] = y
+        return float(lib().orc_pc_arrival_prob(self.ref, a, _ptr(v)))
+
+    def profiles(self, a: int):
+        """All y (y[0] = units with 1 day left ... y[m-1] fresh) with sum a, in the oracle's order."""
+        m = self.inst.m
+        y = np.zeros(9, np.int32)
+        y[1] = a
+        out = [y[1:m + 1].copy()]
+        while lib().orc_pc_next_profile(m, a, _ptr(y)):
+            out.append(y[1:m + 1].copy())
+        return out
+
+    def transition(self, s: int, a: int, d: int, y) -> dict:
+        v = np.zeros(9, np.int32)
+        v[1:len(y) + 1] = y
+        out = _PcStep()
+        if lib().orc_pc_transition(self.ref, s, a, d, _ptr(v), C.byref(out)) != 0:
+            raise ValueError("invalid outcome")
+        return {f: getattr(out, f) for f, _ in _PcStep._fields_}
+
+    def qvalues(self, V: np.ndarray, s: int) -> np.ndarray:
+        V = np.ascontiguousarray(V, np.float64)
+        q = np.empty(self.n_actions, np.float64)
+        lib().orc_pc_qvalues(self.ref, V.ctypes.data_as(C.POINTER(C.c_double)), s,
+                             q.ctypes.data_as(C.POINTER(C.c_double)))
+        return q
+
+    def vi_solve(self, eps: float, max_iters: int, stop_rule: int = 2, V0=None, nthreads: int = 0) -> dict:
+        V = np.zeros(self.n_states) if V0 is None else np.array(V0, np.float64, copy=True)
+        pol = np.zeros(self.n_states, np.uint8)
+        it = C.c_int(0)
+        crit, dmx, dmn = C.c_double(0), C.c_double(0), C.c_double(0)
+        rc = lib().orc_pc_vi_solve(self.ref, eps, stop_rule, max_iters, V.ctypes.data_as(C.POINTER(C.c_double)),
+                                   _ptr(pol), C.byref(it), C.byref(crit), C.byref(dmx), C.byref(dmn), nthreads)
+        if rc not in (0, 3):
+            raise RuntimeError(f"orc_pc_vi_solve failed rc={rc}")
+        return dict(V=V, policy=pol, iters=it.value, converged=(rc == 0), crit=crit.value, dmax=dmx.value,
+                    dmin=dmn.value)
+
+    def backup_states(self, V: np.ndarray, states, nthreads: int = 0):
+        V = np.ascontiguousarray(V, np.float64)
+        states = np.ascontiguousarray(states, np.int64)
+        n = len(states)
+        v = np.empty(n, np.float64)
+        pol = np.empty(n, np.int32)
+        if lib().orc_pc_backup_states(self.ref, V.ctypes.data_as(C.POINTER(C.c_double)), _ptr(states), n,
+                                      _ptr(v), _ptr(pol), nthreads) != 0:
+            raise RuntimeError("orc_pc_backup_states failed")
+        return v, pol
+
+    def simulate(self, policy: np.ndarray, n_rollouts: int, horizon: int, seed: int, warmup: int = 0,
+                 with_traj: bool = False) -> dict:
+        policy = np.ascontiguousarray(policy, np.uint8)
+        ret = np.empty(n_rollouts, np.float64)
+        kpis = np.empty((n_rollouts, 3), np.float64)
+        traj = np.empty((n_rollouts, horizon), np.int32) if with_traj else None
+        if lib().orc_pc_simulate(self.ref, _ptr(policy), n_rollouts, horizon, warmup, C.c_uint64(seed),
+                                 _ptr(ret), _ptr(kpis), _ptr(traj)) != 0:
+            raise RuntimeError("orc_pc_simulate failed")
+        out = dict(returns=ret, kpis=kpis)
+        if with_traj:
+            out["traj"] = traj
+        return out

@@ -128,6 +128,56 @@ int orc_simulate_ex(const orc_problem *P, const uint8_t *policy, int n_rollouts,
 int orc_mbs_simulate(const orc_problem *P, const int S[2], const int mu[2], int cap, int n_rollouts,
                      int horizon, int warmup, uint64_t seed, double *returns, double *kpis_prod);
 
+/* ---------------------------------------------------------------------------
+ * Scenario C (periodic demand, uncertain useful life on arrival; oracle_pc.c).
+ * State s = tau (A_max+1)^(m-1) + sum_j X_j (A_max+1)^(j-1): weekday tau
+ * (0 = Monday) and X_1..X_{m-1}, the units with j days of life left (X_1
+ * expires at the end of today), each 0..A_max.  Actions 0..A_max.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int m;                   /* maximum useful life on arrival, 2..8 */
+    int Q;                   /* A_max: largest order and capacity for each age */
+    int dmax;                /* demand support 0..dmax */
+    const double *pmf;       /* 7 x (dmax+1): demand pmf of weekday tau in row tau */
+    double c0[9], c1[9];     /* log(p_k(a) / p_1(a)) = c0[k] + c1[k] a, k = 2..m */
+    double cost[4];          /* C_f (fixed, per order placed), C_h, C_s, C_w per unit */
+    double gamma;            /* 0 < gamma < 1 */
+} orc_periodic;
+
+typedef struct {
+    long long s_next;
+    double reward;
+    double demand, issued;
+    double wasted;           /* units expiring at the end of the day */
+    double held;             /* units left at the end of the day, expiring ones included */
+    double accepted;         /* units received into stock */
+    double refused;          /* units refused at delivery (age capacity) */
+} orc_pc_step;
+
+long long orc_pc_num_states(const orc_periodic *P);
+void orc_pc_arrival_params(const orc_periodic *P, int a, double *p);            /* p[1..m] */
+double orc_pc_arrival_prob(const orc_periodic *P, int a, const int *y);          /* y[1..m] */
+/* next composition y[1..m] of a (start: y_1 = a, others 0); 0 when exhausted */
+int orc_pc_next_profile(int m, int a, int *y);
+int orc_pc_transition(const orc_periodic *P, long long s, int a, int d, const int *y, orc_pc_step *out);
+int orc_pc_qvalues(const orc_periodic *P, const double *V, long long s, double *q);
+int orc_pc_backup_states(const orc_periodic *P, const double *V, const long long *states, long long n,
+                         double *v_out, int *pol_out, int nthreads);
+/* value iteration from V; stop_rule 0 = span, 1 = sup-norm (criterion < eps),
+ * 2 = periodic test (Scenario C appendix, tested from i = 7 on).  Returns 0 if
+ * converged, 3 at max_iters, 1 on bad input.  dmax/dmin: extremes of V_i - V_{i-1}
+ * (rules 0, 1) or of Delta_i (rule 2). */
+int orc_pc_vi_solve(const orc_periodic *P, double eps, int stop_rule, int max_iters, double *V, uint8_t *policy,
+                    int *iters, double *crit_out, double *dmax_out, double *dmin_out, int nthreads);
+/* Rollouts from state 0 (Monday, no stock).  Period t of rollout r: demand from
+ * word 0 of Philox4x32-10(ctr (t, r, 0, 0)) by the weekday's thresholds
+ * floor(2^32 CDF(d)); unit u of the order takes age class k (1..m) from word
+ * u % 4 of Philox4x32-10(ctr (t, r, 1 + u / 4, 0)) by the thresholds
+ * floor(2^32 (p_1(a) + .. + p_k(a))).  kpis[3r..] = service %, wastage % of the
+ * units accepted, mean units held at the end of the day (expiring included). */
+int orc_pc_simulate(const orc_periodic *P, const uint8_t *policy, int n_rollouts, int horizon, int warmup,
+                    uint64_t seed, double *returns, double *kpis, int32_t *traj);
+
 #ifdef __cplusplus
 }
 #endif

@@ -240,6 +240,80 @@ def scenario_b(name: str, precision: str = "fp32") -> Instance:
                     subst_rate=b["rho"], tol=b["eps"], precision=precision)
 
 
+# The paper's Scenario C (Mirjalili's platelet problem, Scenario C appendix):
+# weekday-periodic negative binomial demand (Table 13: n^tau successes, mean
+# delta^tau, p = n / (n + delta)) folded at D_max = 20; remaining useful life on
+# arrival multinomial with log(p_k(a) / p_1(a)) = c0_k + c1_k a (Table 14);
+# A_max = 20 for the order and for the stock of each age; C_f 10 per order
+# placed, C_h 1, C_s 20, C_w 5 per unit, gamma 0.95, periodic test epsilon 1e-4
+# (Table 12).
+SCENARIO_C = dict(dmax=20, q=20, c_f=10.0, c_h=1.0, c_s=20.0, c_w=5.0, gamma=0.95, eps=1e-4)
+SCENARIO_C_ROLLOUTS = dict(n_rollouts=10_000, horizon=365, warmup=100)
+SCENARIO_C_DEMAND = ((3.5, 5.7), (11.0, 6.9), (7.2, 6.5), (11.1, 6.2), (5.9, 5.8), (5.5, 3.3), (2.2, 3.4))
+# (m, experiment): (c0_2..c0_m, c1_2..c1_m); experiment 1 exogenous, 2 endogenous
+SCENARIO_C_LIFE = {
+    (3, 1): ((1.0, 0.5), (0.0, 0.0)),
+    (3, 2): ((1.0, 0.5), (0.40, 0.80)),
+    (5, 1): ((1.6, 2.6, 2.8, 1.6), (0.0, 0.0, 0.0, 0.0)),
+    (5, 2): ((1.9, 3.1, 3.1, 2.5), (-0.03, -0.06, -0.03, -0.09)),
+    (8, 1): ((0.8, 1.4, 1.9, 2.3, 1.7, 1.2, 0.8), (0.0,) * 7),
+    (8, 2): ((0.8, 1.4, 1.9, 2.3, 1.7, 1.2, 0.8), (-0.03, -0.04, -0.05, -0.06, -0.07, -0.08, -0.09)),
+}
+
+
+@dataclasses.dataclass
+class PeriodicInstance:
+    """A Scenario C instance: weekday in the state, multinomial age on arrival."""
+    name: str
+    m: int
+    Q: int                      # A_max
+    pmf: np.ndarray             # 7 x (dmax+1), row tau = weekday demand pmf
+    c0: Sequence[float]         # index k = 0..m (entries 0 and 1 unused, zero)
+    c1: Sequence[float]
+    cost: Sequence[float]       # (C_f, C_h, C_s, C_w)
+    gamma: float
+    tol: float = 1e-4
+
+    @property
+    def dmax(self) -> int:
+        return self.pmf.shape[1] - 1
+
+    @property
+    def n_states(self) -> int:
+        return 7 * (self.Q + 1) ** (self.m - 1)
+
+    @property
+    def n_actions(self) -> int:
+        return self.Q + 1
+
+    @property
+    def n_outcomes(self) -> int:
+        """The paper's |Omega|: demands x arrival age profiles y with sum y <= A_max."""
+        from math import comb
+        return (self.dmax + 1) * comb(self.Q + self.m, self.m)
+
+
+def scenario_c_demand(dmax: int) -> np.ndarray:
+    """Weekday demand pmfs (Eq. mirjalili:demand), folded at dmax."""
+    rows = []
+    for n, delta in SCENARIO_C_DEMAND:
+        rows.append(folded_pmf(stats.nbinom(n, n / (n + delta)), dmax))
+    return np.stack(rows)
+
+
+def periodic_instance(m, Q, dmax, c0, c1, cost, gamma, name="periodic", pmf=None) -> PeriodicInstance:
+    pmf = scenario_c_demand(dmax) if pmf is None else np.asarray(pmf, np.float64)
+    return PeriodicInstance(name=name, m=m, Q=Q, pmf=pmf, c0=[0.0, 0.0] + list(c0), c1=[0.0, 0.0] + list(c1),
+                            cost=tuple(cost), gamma=gamma)
+
+
+def scenario_c(m: int, exp: int) -> PeriodicInstance:
+    c = SCENARIO_C
+    c0, c1 = SCENARIO_C_LIFE[(m, exp)]
+    return periodic_instance(m, c["q"], c["dmax"], c0, c1, (c["c_f"], c["c_h"], c["c_s"], c["c_w"]), c["gamma"],
+                             name=f"scenC_m{m}_exp{exp}")
+
+
 @dataclasses.dataclass
 class Request:
     arrival_s: float
