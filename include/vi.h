@@ -63,7 +63,7 @@ typedef enum {
 enum { VI_FIFO = 0, VI_LIFO = 1 };
 /* stopping tests: span of V_i - V_{i-1} (Scenario B convergence test) or its
  * sup-norm (Scenario A convergence test); both strict "< tol". */
-enum { VI_STOP_SPAN = 0, VI_STOP_SUPNORM = 1 };
+enum { VI_STOP_SPAN = 0, VI_STOP_SUPNORM = 1, VI_STOP_PERIODIC = 2 };
 /* Value arithmetic and storage.
  *  VI_PREC_FP32        FP32 arithmetic; each value is stored as an unevaluated
  *                      pair of floats (hi, lo), V = hi + lo, interleaved as
@@ -138,6 +138,46 @@ vi_status vi_problem_create(int m, int L, int Q, const double cost[5], const dou
  * stopping rule).  Same errors as vi_problem_create; two products also need
  * |A| = (Q_1+1)(Q_2+1) <= 256, dmax <= 255 and subst_rate in [0,1]. */
 vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_handle *out);
+
+/* Scenario C of the paper (Scenario C appendix): weekday-periodic demand and
+ * uncertain useful life on arrival.  State s = tau (Q+1)^(m-1) + sum_j X_j
+ * (Q+1)^(j-1): the weekday tau (0 = Monday) and X_1..X_{m-1}, the units with j
+ * days of life left (X_1 expires at the end of today), each 0..Q; actions
+ * 0..Q.  An order a arrives at once as y_1..y_m units with k days left,
+ * multinomial over the a units with log(p_k(a) / p_1(a)) = c0[k] + c1[k] a
+ * (Eq. mirjalili:ageonarrival); units beyond Q of an age are refused at
+ * delivery; the day's demand (pmf row tau, Eq. mirjalili:demand) is issued
+ * oldest first (Eq. mirjalili:state_transition); reward -C_f 1{a > 0} - C_h
+ * (units left, expiring ones included) - C_s (unmet demand) - C_w (expiring
+ * units left).  Solved in FP64 (V: device double[|S|] in vi_solve), with
+ * stop_rule VI_STOP_PERIODIC the periodic test of the appendix (for i >= 7,
+ * Delta_i(s) = sum_{j=0}^{6} gamma^-(i-j-1) (V_{i-j}(s) - V_{i-j-1}(s)); stop at
+ * max Delta - min Delta <= 2 tol min(|max Delta|, |min Delta|); vi_solve_info
+ * dmax/dmin then report max/min Delta and crit their relative spread).
+ * vi_simulate draws the day's demand from word 0 of Philox4x32-10(ctr (t, r, 0,
+ * 0)) by the weekday's floor(2^32 CDF) thresholds and unit u of the order's age
+ * class from word u % 4 of Philox4x32-10(ctr (t, r, 1 + u / 4, 0)) by the
+ * thresholds floor(2^32 (p_1(a) + .. + p_k(a))); kpis = service %, wastage % of
+ * the units accepted, mean units left at the end of the day (expiring
+ * included).  vi_simulate_ex needs kpis_prod = NULL; vi_policy_eval,
+ * VI_FLAG_POLICY_EVAL, vi_next_states and the base-stock searches return
+ * VI_EINVAL for these problems. */
+typedef struct {
+    int m;                   /* maximum useful life on arrival, 2..8 */
+    int Q;                   /* A_max: largest order and capacity of each age, 0..63 */
+    int dmax;                /* demand support 0..dmax */
+    const double *pmf;       /* host, 7 x (dmax+1), row tau = weekday tau's demand pmf */
+    double c0[9], c1[9];     /* logits of the life on arrival, entries 2..m used */
+    double cost[4];          /* C_f per order placed, C_h, C_s, C_w per unit (>= 0) */
+    double gamma;            /* 0 < gamma < 1 */
+    int stop_rule;           /* VI_STOP_PERIODIC, VI_STOP_SPAN or VI_STOP_SUPNORM */
+} vi_periodic_desc;
+
+/* Create a Scenario C problem.  Copies everything it needs to the current
+ * device.  Errors: VI_EINVAL for m outside 2..8, Q outside 0..63, a pmf row not
+ * summing to 1 within 1e-9, gamma outside (0, 1), a negative cost, a bad stop
+ * rule or 7 (Q+1)^m >= 2^31; VI_ENOMEM / VI_ECUDA. */
+vi_status vi_problem_create_periodic(const vi_periodic_desc *desc, vi_handle *out);
 
 /* Release every device and host resource of the handle.  NULL is accepted. */
 vi_status vi_problem_destroy(vi_handle h);
@@ -237,7 +277,8 @@ vi_status vi_next_states(vi_handle h, const uint32_t *states, int n, uint32_t *o
  * the popcount of the low `shortfall` bits of the 64-bit word (word 3, word 2)
  * gives the accepted substitutions (two products need subst_rate = 1/2; a
  * shortfall above 64 uses all 64 bits).  The first `warmup`
- * periods are simulated but not scored.  policy: device uint8[|S|];
+ * periods are simulated but not scored.  policy: device uint8[|S|], entries
+ * below |A|;
  * returns: device double[n] = sum_t gamma^t r_t (FP64, in period order);
  * kpis: device double[3n] or NULL = {service %, wastage %, mean units carried};
  * traj: device int32[n x horizon] or NULL = state before each scored decision. */

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libvi_b300.so")
 
 VI_OK, VI_EINVAL, VI_ENOMEM, VI_ENOTCONVERGED, VI_ETIMEOUT, VI_EBUSY, VI_ECUDA, VI_ECANCELLED = range(8)
 VI_FIFO, VI_LIFO = 0, 1
-VI_STOP_SPAN, VI_STOP_SUPNORM = 0, 1
+VI_STOP_SPAN, VI_STOP_SUPNORM, VI_STOP_PERIODIC = 0, 1, 2
 VI_PREC_FP32, VI_PREC_FP32_KAHAN, VI_PREC_FP64, VI_PREC_FP32_SINGLE = 0, 1, 2, 3
 VI_FLAG_WARM_START, VI_FLAG_NO_GRAPH, VI_FLAG_POLICY_EVAL = 1, 2, 4
 VI_OPT_KERNEL, VI_OPT_PE_MAX_ITERS, VI_OPT_GROUP_WIDTH, VI_OPT_TEST_STALL = 1, 2, 3, 4
@@ -33,6 +33,17 @@ class ViError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         super().__init__(f"{where}: {status_name(status)} ({message})")
         self.status = status
+
+
+class vi_periodic_desc(C.Structure):
+    _fields_ = [
+        ("m", C.c_int), ("Q", C.c_int), ("dmax", C.c_int),
+        ("pmf", C.POINTER(C.c_double)),
+        ("c0", C.c_double * 9), ("c1", C.c_double * 9),
+        ("cost", C.c_double * 4),
+        ("gamma", C.c_double),
+        ("stop_rule", C.c_int),
+    ]
 
 
 class vi_problem_desc(C.Structure):
@@ -90,6 +101,7 @@ def lib() -> C.CDLL:
                             C.POINTER(C.c_double)], C.c_int),
         "vi_next_states": ([H, vp, C.c_int, vp, vp], C.c_int),
         "vi_simulate": ([H, u8p, C.c_int, C.c_int, C.c_int, C.c_uint64, vp, vp, vp, vp], C.c_int),
+        "vi_problem_create_periodic": ([C.POINTER(vi_periodic_desc), C.POINTER(C.c_void_p)], C.c_int),
         "vi_simulate_ex": ([H, u8p, C.c_int, C.c_int, C.c_int, C.c_uint64, vp, vp, vp, vp, vp], C.c_int),
         "vi_mbs_search": ([H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int, C.c_int,
                            C.c_int, C.c_int, C.c_uint64, vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_int), vp],
@@ -190,6 +202,29 @@ def make_desc(products: Sequence[dict], gamma: float, issuing: int = VI_FIFO, pr
     d.precision = int(precision)
     d.stop_rule = int(stop_rule)
     return d, keep
+
+
+def make_periodic_desc(m: int, Q: int, pmf, c0, c1, cost, gamma: float, stop_rule: int = VI_STOP_PERIODIC):
+    """Scenario C description: pmf 7 x (dmax+1) (row = weekday), c0 / c1 indexed by
+    age class k (entries 2..m used), cost (C_f, C_h, C_s, C_w).  Returns (desc, keepalive)."""
+    arr = np.ascontiguousarray(pmf, dtype=np.float64)
+    d = vi_periodic_desc()
+    d.m, d.Q, d.dmax = m, Q, arr.shape[1] - 1
+    d.pmf = arr.ctypes.data_as(C.POINTER(C.c_double))
+    for k in range(9):
+        d.c0[k] = float(c0[k]) if k < len(c0) else 0.0
+        d.c1[k] = float(c1[k]) if k < len(c1) else 0.0
+    for j in range(4):
+        d.cost[j] = float(cost[j])
+    d.gamma = gamma
+    d.stop_rule = stop_rule
+    return d, arr
+
+
+def vi_problem_create_periodic(desc: vi_periodic_desc) -> int:
+    h = C.c_void_p()
+    _check(lib().vi_problem_create_periodic(C.byref(desc), C.byref(h)), "vi_problem_create_periodic")
+    return h.value
 
 
 def vi_problem_create_desc(desc: vi_problem_desc) -> int:

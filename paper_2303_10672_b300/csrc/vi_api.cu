@@ -450,6 +450,175 @@ extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_hand
     return VI_OK;
 }
 
+// ---------------------------------------------------------------------------
+// periodic problems (Scenario C)
+// ---------------------------------------------------------------------------
+// floor(2^32 CDF) thresholds of a pmf summed in ascending order, last one 2^32
+static void pc_thresholds(const double *pmf, int n, unsigned long long *thr) {
+    double cdf = 0.0;
+    for (int i = 0; i < n; ++i) {
+        cdf += pmf[i];
+        double t = floor(cdf * 4294967296.0);
+        t = t > 4294967296.0 ? 4294967296.0 : (t < 0.0 ? 0.0 : t);
+        thr[i] = (unsigned long long)t;
+    }
+    thr[n - 1] = 4294967296ull;
+}
+
+// p_1(a)..p_m(a) of the multinomial life on arrival: log(p_k / p_1) = c0_k + c1_k a
+static void pc_arrival_params(const vi_periodic_desc &d, int a, double *p) {
+    double e[kPcMaxM + 1];
+    double z = 1.0;
+    e[1] = 1.0;
+    for (int k = 2; k <= d.m; ++k) {
+        e[k] = exp(d.c0[k] + d.c1[k] * (double)a);
+        z += e[k];
+    }
+    for (int k = 1; k <= d.m; ++k) p[k] = e[k] / z;
+}
+
+extern "C" vi_status vi_problem_create_periodic(const vi_periodic_desc *desc, vi_handle *out) {
+    if (!desc || !out) return vi_fail(VI_EINVAL, "null desc or out");
+    *out = nullptr;
+    const vi_periodic_desc &d = *desc;
+    if (d.m < 2 || d.m > kPcMaxM) return vi_fail(VI_EINVAL, "m must be in 2..%d", kPcMaxM);
+    if (d.Q < 0 || d.Q > 63) return vi_fail(VI_EINVAL, "A_max must be in 0..63");
+    if (d.dmax < 0 || d.dmax > 4095 || !d.pmf) return vi_fail(VI_EINVAL, "bad demand pmf");
+    if (!(d.gamma > 0.0 && d.gamma < 1.0)) return vi_fail(VI_EINVAL, "gamma must be in (0, 1)");
+    if (d.stop_rule != VI_STOP_SPAN && d.stop_rule != VI_STOP_SUPNORM && d.stop_rule != VI_STOP_PERIODIC)
+        return vi_fail(VI_EINVAL, "bad stop_rule");
+    for (int j = 0; j < 4; ++j)
+        if (!(d.cost[j] >= 0.0)) return vi_fail(VI_EINVAL, "costs must be >= 0");
+    for (int t = 0; t < 7; ++t) {
+        double sum = 0.0;
+        for (int i = 0; i <= d.dmax; ++i) {
+            const double v = d.pmf[(size_t)t * (d.dmax + 1) + i];
+            if (!(v >= 0.0)) return vi_fail(VI_EINVAL, "negative demand probability");
+            sum += v;
+        }
+        if (fabs(sum - 1.0) > 1e-9) return vi_fail(VI_EINVAL, "weekday %d pmf sums to %.12g", t, sum);
+    }
+    const int G = d.Q + 1;
+    double n_post = 7.0;
+    for (int j = 0; j < d.m; ++j) n_post *= G;
+    if (n_post / G >= 4294967296.0 || n_post > 2147483648.0)
+        return vi_fail(VI_EINVAL, "7 (A_max+1)^m must stay below 2^31");
+
+    vi_problem *h = new (std::nothrow) vi_problem();
+    if (!h) return vi_fail(VI_ENOMEM, "host allocation failed");
+    h->periodic = true;
+    memset(&h->desc, 0, sizeof(h->desc));
+    h->desc.n_products = 1;
+    h->desc.gamma = d.gamma;
+    h->desc.stop_rule = d.stop_rule;
+    h->desc.precision = VI_PREC_FP64;
+    KernelParams &kp = h->kp;
+    memset(&kp, 0, sizeof(kp));
+    fill_prod_params(kp.p[0], d.m, 1, d.Q, d.dmax, 0.0);   // m-1 digits: the stock slots
+    kp.n_products = 1;
+    kp.gamma = d.gamma;
+    kp.nS = 7u * kp.p[0].nS;
+    kp.nA = G;
+    kp.pc = 1;
+    kp.pc_m = d.m;
+    for (int j = 0; j < 4; ++j) kp.pc_cost[j] = d.cost[j];
+    h->vk = VK_DOUBLE;
+    h->value_bytes = 8;
+    h->group_ok = false;
+    h->two_ok = false;
+
+    // arrival profiles by order size (all compositions of a into m classes), their
+    // probabilities, and the rollout thresholds
+    std::vector<unsigned long long> prof;
+    std::vector<double> prob;
+    std::vector<int> off(G + 1, 0);
+    std::vector<unsigned long long> thr_y((size_t)G * d.m);
+    for (int a = 0; a <= d.Q; ++a) {
+        off[a] = (int)prof.size();
+        double p[kPcMaxM + 1];
+        pc_arrival_params(d, a, p);
+        pc_thresholds(p + 1, d.m, thr_y.data() + (size_t)a * d.m);
+        int y[kPcMaxM + 1] = {0};
+        y[1] = a;
+        while (true) {
+            double coef = 1.0;
+            int left = a;
+            for (int k = 1; k <= d.m; ++k) {
+                double c = 1.0;
+                for (int i = 1; i <= y[k]; ++i) c = c * (double)(left - y[k] + i) / (double)i;
+                coef *= c;
+                left -= y[k];
+            }
+            double pr = coef;
+            for (int k = 1; k <= d.m; ++k) pr *= pow(p[k], (double)y[k]);
+            unsigned long long packed = 0;
+            for (int k = 1; k <= d.m; ++k) packed |= (unsigned long long)y[k] << (6 * (k - 1));
+            prof.push_back(packed);
+            prob.push_back(pr);
+            // next composition: raise the lowest class k >= 2 with room, reset the ones below
+            int k = 2;
+            for (; k <= d.m; ++k) {
+                int upper = 0;
+                for (int j = k; j <= d.m; ++j) upper += y[j];
+                if (upper < a) break;
+            }
+            if (k > d.m) break;
+            y[k] += 1;
+            for (int j = 2; j < k; ++j) y[j] = 0;
+            int rest = 0;
+            for (int j = 2; j <= d.m; ++j) rest += y[j];
+            y[1] = a - rest;
+        }
+    }
+    off[G] = (int)prof.size();
+    std::vector<unsigned long long> thr_d((size_t)7 * (d.dmax + 1));
+    for (int t = 0; t < 7; ++t)
+        pc_thresholds(d.pmf + (size_t)t * (d.dmax + 1), d.dmax + 1, thr_d.data() + (size_t)t * (d.dmax + 1));
+    // the paper's |Omega|: demands x profiles with sum y <= A_max
+    h->n_outcomes = (d.dmax + 1) * (int)prof.size();
+
+    const size_t n_pmf = (size_t)7 * (d.dmax + 1);
+    cudaError_t e;
+    if ((e = cudaMalloc(&h->d_pc_pmf, n_pmf * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_pc_prof, prof.size() * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_pc_prob, prob.size() * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_pc_off, off.size() * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_pc_W, (size_t)n_post * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_pc_ring, (size_t)7 * kp.nS * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_pc_thr_d, thr_d.size() * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_pc_thr_y, thr_y.size() * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_state, sizeof(SolveState))) != cudaSuccess ||
+        (e = cudaMallocHost(&h->h_state, sizeof(SolveState))) != cudaSuccess ||
+        (e = cudaMemcpy(h->d_pc_pmf, d.pmf, n_pmf * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(h->d_pc_prof, prof.data(), prof.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(h->d_pc_prob, prob.data(), prob.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(h->d_pc_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMemcpy(h->d_pc_thr_d, thr_d.data(), thr_d.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(h->d_pc_thr_y, thr_y.data(), thr_y.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(h->d_pc_ring, 0, (size_t)7 * kp.nS * sizeof(double))) != cudaSuccess ||
+        (e = cudaEventCreate(&h->ev0)) != cudaSuccess || (e = cudaEventCreate(&h->ev1)) != cudaSuccess) {
+        destroy_internal(h);
+        return vi_fail(e == cudaErrorMemoryAllocation ? VI_ENOMEM : VI_ECUDA, "periodic problem setup: %s",
+                       cudaGetErrorString(e));
+    }
+    kp.pc_pmf = h->d_pc_pmf;
+    kp.pc_prof = h->d_pc_prof;
+    kp.pc_prob = h->d_pc_prob;
+    kp.pc_off = h->d_pc_off;
+    kp.pc_W = h->d_pc_W;
+    kp.pc_ring = h->d_pc_ring;
+    memset(h->h_state, 0, sizeof(SolveState));
+    h->h_state->key_min = ~0ull;
+    if ((e = cudaMemcpy(h->d_state, h->h_state, sizeof(SolveState), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        destroy_internal(h);
+        return vi_fail(VI_ECUDA, "state upload: %s", cudaGetErrorString(e));
+    }
+    kp.st = h->d_state;
+    *out = h;
+    return VI_OK;
+}
+
 extern "C" vi_status vi_problem_create(int m, int L, int Q, const double cost[5], const double *pmf, int dmax,
                                        double gamma, int issuing, vi_handle *out) {
     vi_problem_desc d;
@@ -481,6 +650,10 @@ static void destroy_internal(vi_problem *h) {
     if (h->d_two_e2) cudaFree(h->d_two_e2);
     if (h->d_two_mix) cudaFree(h->d_two_mix);
     if (h->d_two_rperm) cudaFree(h->d_two_rperm);
+    void *pc_bufs[] = {h->d_pc_pmf, h->d_pc_prof, h->d_pc_prob, h->d_pc_off, h->d_pc_W, h->d_pc_ring,
+                       h->d_pc_thr_d, h->d_pc_thr_y};
+    for (void *b : pc_bufs)
+        if (b) cudaFree(b);
     if (h->d_pe[0]) cudaFree(h->d_pe[0]);
     if (h->d_pe[1]) cudaFree(h->d_pe[1]);
     if (h->d_stage_v) cudaFree(h->d_stage_v);
@@ -841,6 +1014,8 @@ extern "C" vi_status vi_solve(vi_handle h, double tol, int max_iters, void *V, u
     if (!V) return vi_fail(VI_EINVAL, "null V");
     if (!(tol >= 0.0) || max_iters < 0) return vi_fail(VI_EINVAL, "need tol >= 0 and max_iters >= 0");
     if ((flags & VI_FLAG_WARM_START) && !info) return vi_fail(VI_EINVAL, "warm start needs info->offset");
+    if (h->periodic && (flags & VI_FLAG_POLICY_EVAL))
+        return vi_fail(VI_EINVAL, "VI_FLAG_POLICY_EVAL is not available for periodic problems");
     cudaStream_t s = (cudaStream_t)stream;
     vi_status st = ensure_scratch(h);
     if (st != VI_OK) return st;
@@ -869,6 +1044,8 @@ extern "C" vi_status vi_solve(vi_handle h, double tol, int max_iters, void *V, u
     hs->key_min = ~0ull;
     hs->offset = (flags & VI_FLAG_WARM_START) ? info->offset : 0.0;
     CUDA_TRY(cudaMemcpyAsync(h->d_state, hs, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+    if (h->periodic && hs->stop_rule == VI_STOP_PERIODIC)   // the periodic test restarts with every solve
+        CUDA_TRY(cudaMemsetAsync(h->d_pc_ring, 0, (size_t)7 * h->kp.nS * sizeof(double), s));
     CUDA_TRY(cudaEventRecord(h->ev0, s));
     if (use_graph) {
         CUDA_TRY(cudaGraphLaunch(h->graph_exec, s));
@@ -972,6 +1149,7 @@ extern "C" vi_status vi_backup(vi_handle h, const void *V_in, void *V_out, uint8
 
 extern "C" vi_status vi_next_states(vi_handle h, const uint32_t *states, int n, uint32_t *out, void *stream) {
     if (!h) return vi_fail(VI_EINVAL, "null handle");
+    if (h->periodic) return vi_fail(VI_EINVAL, "vi_next_states takes problems with demand outcomes only");
     if (n < 0 || (n > 0 && (!states || !out))) return vi_fail(VI_EINVAL, "bad states / out");
     if (n == 0) return VI_OK;
     if (n > 65535) return vi_fail(VI_EINVAL, "at most 65535 states per call");
@@ -1018,6 +1196,7 @@ static vi_status policy_eval_impl(vi_problem *h, const uint8_t *policy, double *
 
 extern "C" vi_status vi_policy_eval(vi_handle h, const uint8_t *policy, double *V, double tol, int max_iters,
                                     void *stream, int *iters, double *delta) {
+    if (h && h->periodic) return vi_fail(VI_EINVAL, "vi_policy_eval is not available for periodic problems");
     if (!h) return vi_fail(VI_EINVAL, "null handle");
     if (!policy || !V || !(tol >= 0.0) || max_iters < 0) return vi_fail(VI_EINVAL, "bad policy-eval arguments");
     return policy_eval_impl(h, policy, V, tol, max_iters, (cudaStream_t)stream, iters, delta);
@@ -1064,6 +1243,18 @@ extern "C" vi_status vi_simulate_ex(vi_handle h, const uint8_t *policy, int n_ro
     if (!policy || !returns || n_rollouts < 0 || horizon < 0 || warmup < 0)
         return vi_fail(VI_EINVAL, "bad rollout arguments");
     if (n_rollouts == 0) return VI_OK;
+    if (h->periodic) {
+        if (kpis_prod) return vi_fail(VI_EINVAL, "periodic problems have one product (kpis_prod must be NULL)");
+        PcRollParams pp;
+        pp.n_rollouts = n_rollouts;
+        pp.horizon = horizon;
+        pp.warmup = warmup;
+        pp.seed = seed;
+        pp.thr_d = h->d_pc_thr_d;
+        pp.thr_y = h->d_pc_thr_y;
+        CUDA_TRY(launch_pc_rollouts(h->kp, pp, policy, returns, kpis, traj, (cudaStream_t)stream));
+        return VI_OK;
+    }
     RollParams rp;
     vi_status st = roll_params(h, n_rollouts, horizon, warmup, seed, rp);
     if (st != VI_OK) return st;
@@ -1080,6 +1271,7 @@ extern "C" vi_status vi_mbs_search(vi_handle h, const int S_lo[2], const int S_h
                                    int n_rollouts, int horizon, int warmup, uint64_t seed, double *returns,
                                    double *kpis_prod, double *mean_returns, int best_S[2], void *stream) {
     if (!h) return vi_fail(VI_EINVAL, "null handle");
+    if (h->periodic) return vi_fail(VI_EINVAL, "the modified base-stock search takes Scenario A/B problems");
     const vi_problem_desc &d = h->desc;
     const int np = d.n_products;
     if (!S_lo || !S_hi || !mu || !returns || n_rollouts < 1 || horizon < 0 || warmup < 0)
@@ -1132,6 +1324,7 @@ extern "C" vi_status vi_basestock_search(vi_handle h, int s_lo, int s_hi, int n_
                                          uint64_t seed, double *returns, double *mean_returns, int *best_S,
                                          void *stream) {
     if (!h) return vi_fail(VI_EINVAL, "null handle");
+    if (h->periodic) return vi_fail(VI_EINVAL, "the base-stock search takes Scenario A problems");
     const vi_problem_desc &d = h->desc;
     if (d.n_products != 1) return vi_fail(VI_EINVAL, "the base-stock search takes single-product instances");
     if (!returns || s_lo < 0 || s_hi < s_lo || n_rollouts < 1 || horizon < 0 || warmup < 0)

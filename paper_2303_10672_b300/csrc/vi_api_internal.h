@@ -32,6 +32,15 @@ struct vi_problem {
     float *d_two_e2 = nullptr;            // two-product expectation tables (factorised sweep)
     float *d_two_mix = nullptr;
     uint32_t *d_two_rperm = nullptr;      // rests of product 1 ordered by unit total (pipeline form)
+    // periodic problems (Scenario C, vi_pc.cu)
+    bool periodic = false;
+    double *d_pc_pmf = nullptr;
+    unsigned long long *d_pc_prof = nullptr;
+    double *d_pc_prob = nullptr;
+    int *d_pc_off = nullptr;
+    double *d_pc_W = nullptr;
+    double *d_pc_ring = nullptr;
+    unsigned long long *d_pc_thr_d = nullptr, *d_pc_thr_y = nullptr;
     double *d_pe[2] = {nullptr, nullptr};
     void *d_stage_v = nullptr;            // vi_solve_host staging
     uint8_t *d_stage_p = nullptr;

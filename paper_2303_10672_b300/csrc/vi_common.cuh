@@ -75,7 +75,21 @@ struct KernelParams {
     int two_nt1;          // T1 values kept: 0..min(dmax1, m1 Q1)
     int two_npipe1;       // product-1 pipeline classes of an emptied next state: G1^(L1-1)
     const uint32_t *two_rperm;   // lead times >= 2: product-1 rests ordered by their unit total
+    // Scenario C (periodic demand, life on arrival; vi_pc.cu): p[0] holds m, Q = A_max,
+    // G, dmax, nS = G^(m-1) states per weekday
+    int pc;                      // 1 for a periodic problem
+    int pc_m;                    // maximum useful life on arrival
+    const double *pc_pmf;        // 7 x (dmax+1): demand pmf of weekday tau in row tau
+    const unsigned long long *pc_prof;   // arrival profiles y_1..y_m, 6 bits each (y_1 lowest), by order
+    const double *pc_prob;       // P(y | a) of each profile
+    const int *pc_off;           // the profiles of order a are [pc_off[a], pc_off[a+1])
+    double *pc_W;                // 7 G^m post-decision values
+    double *pc_ring;             // 7 |S| weighted differences of the periodic stopping test
+    double pc_cost[4];           // C_f per order placed, C_h, C_s, C_w per unit
 };
+
+constexpr int kPcMaxM = 8;       // periodic problems: m <= 8
+constexpr int kStopPeriodic = 2; // the periodic stopping test (VI_STOP_PERIODIC)
 
 // ---------------------------------------------------------------------------
 // device solve bookkeeping.  The sweep kernel reads its input/output buffers and

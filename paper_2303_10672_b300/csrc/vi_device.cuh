@@ -84,10 +84,19 @@ __device__ void block_reduce_and_finalize(T mx, T mn, SolveState *st, int mode, 
         st->offset = b_new;
         st->dmax_abs = db + vmax;
         st->dmin_abs = db + vmin;
-        const double crit = (st->stop_rule == 0) ? (vmax - vmin) : fmax(fabs(st->dmax_abs), fabs(st->dmin_abs));
-        st->crit = crit;
+        double crit;
+        int conv;
         st->iter += 1;
-        const int conv = crit < st->tol;
+        if (st->stop_rule == kStopPeriodic) {
+            // periodic test on Delta_i (Scenario C appendix), from the seventh sweep on
+            const double lo = fmin(fabs(vmax), fabs(vmin));
+            crit = (vmax - vmin) / lo;
+            conv = (st->iter >= 7) && (vmax - vmin <= 2.0 * st->tol * lo);
+        } else {
+            crit = (st->stop_rule == 0) ? (vmax - vmin) : fmax(fabs(st->dmax_abs), fabs(st->dmin_abs));
+            conv = crit < st->tol;
+        }
+        st->crit = crit;
         st->converged = conv;
         const int go = (!conv) && (st->iter < st->max_iters);
         st->keep_going = go;

@@ -1542,6 +1542,7 @@ static cudaError_t describe_two(const KernelParams &kp, LaunchDesc &d) {
 cudaError_t describe_sweep(const KernelParams &kp, int vk, int kahan, int use_group, LaunchDesc &d) {
     d.lpr = 0;
     d.n_pre = 0;
+    if (kp.pc) return describe_pc(kp, d);
     if (use_group == kTcWidth) return describe_tc(kp, d);
     if (use_group == kTwoWidth) return (kp.p[0].L >= 2) ? describe_twop(kp, d) : describe_two(kp, d);
     if (use_group) {

@@ -100,5 +100,15 @@ cudaError_t launch_rollouts(const KernelParams &kp, const RollParams &rp, const 
                             double *returns, double *kpis, double *kpis_prod, int32_t *traj, cudaStream_t stream);
 cudaError_t launch_mbs(const KernelParams &kp, const RollParams &rp, const MbsParams &mp, double *returns,
                        double *kpis_prod, cudaStream_t stream);
+// periodic problems (vi_pc.cu)
+struct PcRollParams {
+    int n_rollouts, horizon, warmup;
+    unsigned long long seed;
+    const unsigned long long *thr_d;   // device, 7 x (dmax+1): floor(2^32 CDF(d)) of each weekday
+    const unsigned long long *thr_y;   // device, (Q+1) x m: floor(2^32 (p_1(a) + .. + p_k(a)))
+};
+cudaError_t describe_pc(const KernelParams &kp, LaunchDesc &d);
+cudaError_t launch_pc_rollouts(const KernelParams &kp, const PcRollParams &rp, const uint8_t *policy,
+                               double *returns, double *kpis, int32_t *traj, cudaStream_t stream);
 
 }  // namespace vib
