@@ -454,8 +454,9 @@ def run_native(args):
     d2h = n * sizes["value_bytes"] + n
 
     out = None
-    paper_a = run_paper_scenario_a(vi, torch, stream) if (rank == 0 and args.paper) else None
-    paper_b = run_paper_scenario_b(vi, torch, stream) if (rank == 0 and args.paper) else None
+    paper_a = run_paper_scenario_a(vi, torch, stream) if (rank == 0 and "a" in args.paper) else None
+    paper_b = run_paper_scenario_b(vi, torch, stream) if (rank == 0 and "b" in args.paper) else None
+    paper_c = run_paper_scenario_c(vi, torch, stream, args.no_graph) if (rank == 0 and "c" in args.paper) else None
     serving = run_serving(args.serving) if (args.serving > 0 and rank == 0) else None
     if rank == 0:
         cpu = oracle_sample_rate(inst, args.cpu_seconds) if args.cpu_seconds > 0 else None
@@ -480,6 +481,7 @@ def run_native(args):
             "policy_search": policy_search,
             "paper_scenario_a": paper_a,
             "paper_scenario_b": paper_b,
+            "paper_scenario_c": paper_c,
             "wall_s": wall,
         }
         print(json.dumps(out))
@@ -606,6 +608,61 @@ def run_paper_scenario_b(vi, torch, stream) -> dict:
     return out
 
 
+SCEN_C_TABLES = os.path.join(ROOT, "tests", "golden", "scenario_c_tables.json")
+
+
+def run_paper_scenario_c(vi, torch, stream, no_graph: bool = False) -> dict:
+    """The paper's Scenario C (weekday demand, uncertain life on arrival, FP64):
+    both m = 3 settings and both m = 5 settings of Table 6 (1,361,367 states,
+    which took 49.5 hours there) to the periodic stopping test from V_0 = 0, then
+    10,000 rollouts of 365 days after 100 of each value-iteration policy.  Times
+    are CUDA-event device times on the launching stream."""
+    rows = json.load(open(SCEN_C_TABLES))["rows"]
+    RO = workloads.SCENARIO_C_ROLLOUTS
+    out = {"note": "paper times: RTX 3060, FP64 JAX (Table 6); work = one FP64 multiply-add per (state, order, "
+                   "arrival profile) in the sweep plus one per (post-decision state, demand) in the post-decision "
+                   "table; fp64_frac = that rate / 0.625e12 multiply-adds/s (B300 nominal FP64, 1.25 TFLOP/s)",
+           "experiments": []}
+    for row in rows:
+        if row["m"] > 5:
+            continue
+        inst = workloads.scenario_c(row["m"], row["exp"])
+        d, keep = vi.make_periodic_desc(inst.m, inst.Q, inst.pmf, inst.c0, inst.c1, inst.cost, inst.gamma)
+        h = vi.vi_problem_create_periodic(d)
+        n = inst.n_states
+        V = torch.zeros(n, dtype=torch.float64, device="cuda")
+        pol = torch.empty(n, dtype=torch.uint8, device="cuda")
+        flags = vi.VI_FLAG_NO_GRAPH if no_graph else 0
+        if row["m"] == 3:
+            vi.vi_solve(h, workloads.SCENARIO_C["eps"], 2000, V, pol, stream=stream, flags=flags)   # warm-up
+            V.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = vi.vi_solve(h, workloads.SCENARIO_C["eps"], 2000, V, pol, stream=stream, flags=flags)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        ret = torch.empty(RO["n_rollouts"], dtype=torch.float64, device="cuda")
+        vi.vi_simulate(h, pol, RO["n_rollouts"], RO["horizon"], RO["warmup"], 2023, ret, stream=stream)
+        r = ret.cpu().numpy()
+        from math import comb
+        G = inst.Q + 1
+        profiles = comb(inst.Q + inst.m, inst.m)
+        fmas = n * profiles + 7 * G ** inst.m * (inst.dmax + 1)
+        out["experiments"].append({
+            "experiment": f"m{row['m']}_exp{row['exp']} ({row['uncertainty']})", "states": n,
+            "iterations": info["iters"], "converged": bool(info["status"] == vi.VI_OK), "vi_ms": ms,
+            "paper_vi_wall_s": row["vi_wall_s"], "speedup_vs_paper": row["vi_wall_s"] * 1e3 / ms,
+            "fp64_fma_per_s": fmas * info["iters"] / (ms * 1e-3),
+            "fp64_frac": fmas * info["iters"] / (ms * 1e-3) / 0.625e12,
+            "return_mean": float(r.mean()), "return_sd": float(r.std(ddof=1)),
+            "paper_return_mean": row["vi_return_mean"], "paper_return_sd": row["vi_return_sd"]})
+        vi.vi_problem_destroy(h)
+        del V, pol
+    return out
+
+
 def run_serving(n_requests: int = 512, seed: int = 5, slots: int = 64, budget_gb: float = 64.0) -> dict:
     """Serving mix: requests arriving as a Poisson stream, served by the
     continuous-batching server vs sequential plain solves of the same mix (each:
@@ -714,7 +771,7 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp32", "fp32_kahan", "fp64", "fp32_single"])
     ap.add_argument("--max-iters", type=int, default=MAX_ITERS)
     ap.add_argument("--serving", type=int, default=512, help="requests in the serving mix (0 = skip)")
-    ap.add_argument("--paper", type=int, default=1, help="the paper's Scenario A/B results (0 = skip)")
+    ap.add_argument("--paper", default="abc", help="which of the paper's Scenario A/B/C results to run ('' or 0 = none)")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven sweep loop instead of the CUDA graph (same kernels; lets a profiler see each launch)")
     ap.add_argument("--kernel", choices=["auto", "group", "tensor", "generic"], default="auto",
