@@ -650,6 +650,7 @@ static void destroy_internal(vi_problem *h) {
     if (h->d_two_e2) cudaFree(h->d_two_e2);
     if (h->d_two_mix) cudaFree(h->d_two_mix);
     if (h->d_two_rperm) cudaFree(h->d_two_rperm);
+    if (h->d_grp_order) cudaFree(h->d_grp_order);
     void *pc_bufs[] = {h->d_pc_pmf, h->d_pc_prof, h->d_pc_prob, h->d_pc_off, h->d_pc_W, h->d_pc_ring,
                        h->d_pc_thr_d, h->d_pc_thr_y};
     for (void *b : pc_bufs)
@@ -801,6 +802,7 @@ static vi_status autotune(vi_problem *h, cudaStream_t s) {
     float best_ms = INFINITY;
     int best = heuristic_width(P.G, h->kp.issuing);
     KernelParams kp = h->kp;
+    kp.grp_order = nullptr;   // the block order belongs to one lane width
     int mode = MODE_PLAIN;
     uint8_t *np = nullptr;
     // every failure below falls through to the release of the scratch and events
@@ -843,6 +845,44 @@ static vi_status autotune(vi_problem *h, cudaStream_t s) {
     return VI_OK;
 }
 
+// Block order of the factorised sweep with lane width xw: blocks sorted by the
+// demand they reach, sum over their rests of min(R, Dmax) + 1 (R = units in the
+// slots the demand consumes after the expiring one), heaviest first.  Blocks are
+// dispatched roughly in index order, so the last wave holds the lightest ones.
+static vi_status ensure_group_order(vi_problem *h, int xw) {
+    if (h->order_xw == xw && h->d_grp_order) {
+        h->kp.grp_order = h->d_grp_order;
+        return VI_OK;
+    }
+    const ProdParams &P = h->kp.p[0];
+    const uint32_t G = (uint32_t)P.G;
+    const int lpr = (P.G + xw - 1) / xw;
+    const uint32_t rb = (uint32_t)(kGroupThreads / lpr);
+    const uint32_t nR = P.nS / G;
+    const uint32_t nb = (nR + rb - 1) / rb;
+    std::vector<double> w(nb, 0.0);
+    for (uint32_t r = 0; r < nR; ++r) {
+        uint32_t rem = r, R = 0;
+        for (int j = 0; j < P.n_rest_slots; ++j) {
+            R += rem % G;
+            rem /= G;
+        }
+        w[r / rb] += (double)std::min<uint32_t>(R, (uint32_t)P.dmax) + 1.0;
+    }
+    std::vector<uint32_t> order(nb);
+    for (uint32_t b = 0; b < nb; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return w[a] > w[b]; });
+    if (h->d_grp_order) {
+        cudaFree(h->d_grp_order);
+        h->d_grp_order = nullptr;
+    }
+    CUDA_TRY(cudaMalloc(&h->d_grp_order, (size_t)nb * sizeof(uint32_t)));
+    CUDA_TRY(cudaMemcpy(h->d_grp_order, order.data(), (size_t)nb * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    h->order_xw = xw;
+    h->kp.grp_order = h->d_grp_order;
+    return VI_OK;
+}
+
 // resolve which sweep kernel runs: 0 = generic, > 0 = factorised with that lane width
 static vi_status choose_kernel(vi_problem *h, cudaStream_t s) {
     if (h->two_ok && h->kernel_choice != VI_KERNEL_GENERIC) {
@@ -858,7 +898,12 @@ static vi_status choose_kernel(vi_problem *h, cudaStream_t s) {
         if (st != VI_OK) return st;
     }
     h->sweep_xw = h->group_xw;
-    return VI_OK;
+    // measured on B300: 2.4% faster for the FIFO 4.08M-state sweep, none for LIFO
+    if (h->sweep_xw == kTcWidth || h->kp.issuing != VI_FIFO) {
+        h->kp.grp_order = nullptr;
+        return VI_OK;
+    }
+    return ensure_group_order(h, h->sweep_xw);
 }
 
 extern "C" vi_status vi_problem_kernel(vi_handle h, int *kernel, int *width) {

@@ -32,6 +32,8 @@ struct vi_problem {
     float *d_two_e2 = nullptr;            // two-product expectation tables (factorised sweep)
     float *d_two_mix = nullptr;
     uint32_t *d_two_rperm = nullptr;      // rests of product 1 ordered by unit total (pipeline form)
+    uint32_t *d_grp_order = nullptr;      // block order of the factorised sweep for lane width order_xw
+    int order_xw = 0;
     // periodic problems (Scenario C, vi_pc.cu)
     bool periodic = false;
     double *d_pc_pmf = nullptr;

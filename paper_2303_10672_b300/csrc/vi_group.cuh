@@ -509,7 +509,10 @@ template <int XW, int LIFO, int VK, int LPIPE>
 __global__ void __launch_bounds__(kGroupThreads, group_min_blocks(XW, LIFO))
 sweep_group_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int lpr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    group_body<XW, LIFO, VK, LPIPE>(kp, blockIdx.x, gridDim.x, mode, vin_arg, vout_arg, pol_arg, lpr, smem_raw);
+    // blocks start in the order of grp_order (most demand-reaching units first), so
+    // that the last wave is made of the lightest blocks
+    const uint32_t bid = kp.grp_order ? kp.grp_order[blockIdx.x] : blockIdx.x;
+    group_body<XW, LIFO, VK, LPIPE>(kp, bid, gridDim.x, mode, vin_arg, vout_arg, pol_arg, lpr, smem_raw);
 }
 
 
