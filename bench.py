@@ -666,7 +666,8 @@ def run_paper_scenario_c(vi, torch, stream, no_graph: bool = False) -> dict:
 def run_serving(n_requests: int = 512, seed: int = 5, slots: int = 64, budget_gb: float = 64.0) -> dict:
     """Serving mix: requests arriving as a Poisson stream, served by the
     continuous-batching server vs sequential plain solves of the same mix (each:
-    create, solve with host buffers, destroy).  Latency = arrival to result."""
+    create, solve with host buffers, destroy).  Both deliver every request's
+    values and policy to host arrays.  Latency = arrival to result."""
     import paper_2303_10672_b300 as vi
     reqs = workloads.serving_mix(n_requests, seed=seed)
     descs = []
@@ -675,12 +676,18 @@ def run_serving(n_requests: int = 512, seed: int = 5, slots: int = 64, budget_gb
         descs.append(vi.make_desc([dict(m=p.m, L=p.L, Q=p.Q, cost=p.cost, pmf=p.pmf)], r.instance.gamma,
                                   r.instance.issuing))
     nominal = [r.instance.updates_per_sweep for r in reqs]
+    n_states = [r.instance.n_states for r in reqs]
+
+    def host_bufs(k):
+        # the values and policy delivered to host memory, as the sequential path does
+        return np.empty(n_states[k], np.float64), np.empty(n_states[k], np.uint8)
 
     # warm up both paths (module load, autotuning of each shape class, graph builds)
     srv = vi.vi_server_create(int(budget_gb * (1 << 30)), slots)
     wid = vi.vi_server_submit(srv, descs[0][0], TOL, MAX_ITERS)
     while not vi.vi_server_poll(srv, wid)[0]:
         time.sleep(0.001)
+    vi.vi_server_wait(srv, 0)   # forget the warm-up request
 
     # -- server: submit at the arrival times, poll for completions
     t0 = time.perf_counter()
@@ -690,16 +697,18 @@ def run_serving(n_requests: int = 512, seed: int = 5, slots: int = 64, budget_gb
     while i < len(reqs) or pending:
         now = time.perf_counter() - t0
         while i < len(reqs) and reqs[i].arrival_s <= now:
-            rid = vi.vi_server_submit(srv, descs[i][0], TOL, MAX_ITERS)
-            pending[rid] = i
+            bufs = host_bufs(i)
+            rid = vi.vi_server_submit_to(srv, descs[i][0], TOL, MAX_ITERS, *bufs)
+            pending[rid] = (i, bufs)
             i += 1
-        for rid in list(pending):
+        wait_ms = 5 if i >= len(reqs) else max(0, min(5, int(1e3 * (reqs[i].arrival_s - now))))
+        for rid in vi.vi_server_wait(srv, wait_ms):
+            if rid not in pending:
+                continue
             done, info = vi.vi_server_poll(srv, rid)
-            if done:
-                k = pending.pop(rid)
-                lat[k] = info["wall_ms"]
-                upd += nominal[k] * info["iters"]
-        time.sleep(0.0002)
+            k = pending.pop(rid)[0]
+            lat[k] = info["wall_ms"]
+            upd += nominal[k] * info["iters"]
     span_srv = time.perf_counter() - t0
     vi.vi_server_destroy(srv)
     lat_srv = np.array([lat[k] for k in range(len(reqs))])
@@ -728,15 +737,14 @@ def run_serving(n_requests: int = 512, seed: int = 5, slots: int = 64, budget_gb
     # -- capacity: the whole mix submitted at once, server vs sequential
     srv = vi.vi_server_create(int(budget_gb * (1 << 30)), slots)
     t0 = time.perf_counter()
-    ids = [vi.vi_server_submit(srv, d[0], TOL, MAX_ITERS) for d in descs]
-    left = dict(zip(ids, range(len(ids))))
+    bufs = [host_bufs(k) for k in range(len(descs))]
+    ids = [vi.vi_server_submit_to(srv, d[0], TOL, MAX_ITERS, *b) for d, b in zip(descs, bufs)]
+    left = {rid: (k, bufs[k]) for k, rid in enumerate(ids)}
     upd_b = 0.0
     while left:
-        for rid in list(left):
+        for rid in vi.vi_server_wait(srv, 5):
             done, info = vi.vi_server_poll(srv, rid)
-            if done:
-                upd_b += nominal[left.pop(rid)] * info["iters"]
-        time.sleep(0.0002)
+            upd_b += nominal[left.pop(rid)[0]] * info["iters"]
     span_b = time.perf_counter() - t0
     vi.vi_server_destroy(srv)
     t0 = time.perf_counter()

@@ -349,6 +349,14 @@ vi_status vi_server_create(size_t mem_budget_bytes, int max_slots, void *stream,
  * VI_EINVAL for a bad description, VI_EBUSY if it can never fit the budget. */
 vi_status vi_server_submit(vi_server srv, const vi_problem_desc *desc, double tol, int max_iters,
                            uint64_t *request_id);
+/* vi_server_submit that delivers the result into the caller's host buffers:
+ * V_host (double[|S|], absolute values) and policy_host (uint8[|S|]) are
+ * written by the server's retirement threads before the request reports done,
+ * so the caller copies nothing; they must stay valid until then.  Either may be
+ * NULL (that part then waits in the server for vi_server_poll).  Errors as
+ * vi_server_submit. */
+vi_status vi_server_submit_to(vi_server srv, const vi_problem_desc *desc, double tol, int max_iters,
+                              double *V_host, uint8_t *policy_host, uint64_t *request_id);
 /* Poll a request.  done = 1 once finished; then V_host (host double[|S|],
  * absolute values, or NULL) and policy_host (host uint8[|S|] or NULL) receive
  * the result and info the solve record (wall_ms = submit-to-result latency,
@@ -358,6 +366,12 @@ vi_status vi_server_submit(vi_server srv, const vi_problem_desc *desc, double to
  * it has been polled as done. */
 vi_status vi_server_poll(vi_server srv, uint64_t request_id, int *done, double *V_host,
                          uint8_t *policy_host, vi_solve_info *info);
+/* Wait up to timeout_ms (0: do not wait) for requests to finish.  Writes into
+ * ids (host uint64[max_ids]) the ids of up to max_ids requests that finished
+ * and were not yet reported by this call, in the order they finished, and
+ * their count into *n_out (0 after a time-out).  A reported request is then
+ * read with vi_server_poll.  VI_EINVAL for bad arguments. */
+vi_status vi_server_wait(vi_server srv, int timeout_ms, uint64_t *ids, int max_ids, int *n_out);
 /* Stop the worker and release everything.  Pending requests are cancelled. */
 vi_status vi_server_destroy(vi_server srv);
 

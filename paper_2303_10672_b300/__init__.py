@@ -112,6 +112,9 @@ def lib() -> C.CDLL:
         "vi_server_poll": ([C.c_void_p, C.c_uint64, C.POINTER(C.c_int), vp, vp, C.POINTER(vi_solve_info)],
                            C.c_int),
         "vi_server_destroy": ([C.c_void_p], C.c_int),
+        "vi_server_wait": ([C.c_void_p, C.c_int, vp, C.c_int, C.POINTER(C.c_int)], C.c_int),
+        "vi_server_submit_to": ([C.c_void_p, C.POINTER(vi_problem_desc), C.c_double, C.c_int, vp, vp,
+                                 C.POINTER(C.c_uint64)], C.c_int),
         "vi_backup_noalloc": ([C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                C.c_int, C.c_double, C.c_int, vp, vp, u8p, C.POINTER(C.c_double), vp], C.c_int),
         "vi_probe_l2_read": ([vp, C.c_size_t, C.c_int, vp, C.POINTER(C.c_float)], C.c_int),
@@ -378,6 +381,23 @@ def vi_server_poll(srv: int, request_id: int, V_host: Optional[np.ndarray] = Non
     if st not in (VI_OK, VI_ENOTCONVERGED, VI_ECANCELLED) or (not done.value and st != VI_OK):
         _check(st, "vi_server_poll")
     return bool(done.value), info.as_dict()
+
+
+def vi_server_submit_to(srv: int, desc, tol: float, max_iters: int, V_host: np.ndarray,
+                        policy_host: np.ndarray) -> int:
+    """Submit with the result delivered into V_host / policy_host (keep them alive until done)."""
+    rid = C.c_uint64()
+    _check(lib().vi_server_submit_to(srv, C.byref(desc), tol, max_iters, _addr(V_host), _addr(policy_host),
+                                     C.byref(rid)), "vi_server_submit_to")
+    return rid.value
+
+
+def vi_server_wait(srv: int, timeout_ms: int = 0, max_ids: int = 1024) -> list:
+    """Ids of requests that finished since the last call (waits up to timeout_ms for one)."""
+    buf = (C.c_uint64 * max_ids)()
+    n = C.c_int()
+    _check(lib().vi_server_wait(srv, timeout_ms, C.cast(buf, C.c_void_p), max_ids, C.byref(n)), "vi_server_wait")
+    return list(buf[:n.value])
 
 
 def vi_server_destroy(srv: int) -> None:

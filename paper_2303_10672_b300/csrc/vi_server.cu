@@ -8,8 +8,11 @@
 // so instances of different sizes advance together, then reads every slot's
 // status once.  An instance whose stopping test passed gets an extraction sweep
 // in the next iteration; its values are converted to FP64 on the device and a
-// retirement thread copies them (and the policy) to host memory on a second
-// stream and releases the buffers, while the worker carries on.
+// retirement thread copies them (and the policy) to pinned host memory on a
+// second stream and releases the buffers, while the worker carries on.  The
+// pinned result buffers come from a free list of the server's (power-of-two
+// sizes) and go back to it when the caller polls the result: fresh pageable
+// memory would cost a zero-fill and a page fault per page of every result.
 //
 // Slots own their expectation tables, solve state and pinned upload staging for
 // the server's lifetime; value and policy buffers come from the stream-ordered
@@ -45,6 +48,9 @@ constexpr int kSweepsPerCheck = 4;      // batched sweeps between two status rea
 // Above this many active states a batched sweep outlasts the status round trip,
 // and further sweeps would only delay the extraction of instances that stopped.
 constexpr double kOneSweepStates = 1 << 20;
+// retirement threads: results written straight into the callers' (pageable) buffers
+// are mostly page faults and copies on the host, which several threads overlap
+constexpr int kRetireThreads = 2;
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -66,8 +72,11 @@ struct Request {
     vi_status status = VI_OK;
     int iters = 0;
     double crit = 0.0;
-    std::vector<double> V;
-    std::vector<uint8_t> policy;
+    double *V = nullptr;           // pinned result buffers (from the server's free list)
+    uint8_t *policy = nullptr;
+    size_t V_cap = 0, policy_cap = 0;
+    double *dst_V = nullptr;       // vi_server_submit_to: the caller's host buffers, written at retirement
+    uint8_t *dst_policy = nullptr;
 };
 
 struct Slot {
@@ -102,18 +111,21 @@ struct vi_server_s {
     size_t budget = 0, used = 0;
     int max_slots = 0;
     cudaStream_t stream = nullptr;    // batched sweeps
-    cudaStream_t rstream = nullptr;   // retirement copies
+    cudaStream_t rstream[kRetireThreads] = {};   // retirement copies, one stream per retirement thread
     cudaMemPool_t pool = nullptr;     // value and policy buffers; keeps up to the budget between requests
     std::mutex mu;
     std::condition_variable cv;
     std::deque<std::shared_ptr<Request>> queue;
     std::map<uint64_t, std::shared_ptr<Request>> all;
     std::vector<Slot> slots;
-    std::thread worker, retirer;
+    std::thread worker, retirer[kRetireThreads];
     std::deque<RetireJob> retire_q;
     std::condition_variable retire_cv;
     bool stop = false, retire_stop = false;
     uint64_t next_id = 1;
+    std::multimap<size_t, void *> pinned_free;   // pinned result buffers by capacity (guarded by mu)
+    std::deque<uint64_t> completed;               // finished, not yet reported by vi_server_wait
+    std::condition_variable done_cv;
     vi_status fatal = VI_OK;
     char fatal_msg[256] = "";
     // batch descriptors (device) and their pinned host mirrors
@@ -127,6 +139,31 @@ struct vi_server_s {
 };
 
 static size_t request_bytes(uint64_t n) { return (size_t)n * (8 + 8 + 1) + (1 << 16); }
+
+// a pinned host buffer of at least `bytes` (power-of-two capacity, 64 KiB or more)
+static void *pinned_get(vi_server_s *srv, size_t bytes, size_t *cap) {
+    size_t c = (size_t)1 << 16;
+    while (c < bytes) c <<= 1;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        auto it = srv->pinned_free.find(c);
+        if (it != srv->pinned_free.end()) {
+            void *p = it->second;
+            srv->pinned_free.erase(it);
+            *cap = c;
+            return p;
+        }
+    }
+    void *p = nullptr;
+    if (cudaMallocHost(&p, c) != cudaSuccess) return nullptr;
+    *cap = c;
+    return p;
+}
+
+// caller holds srv->mu
+static void pinned_put_locked(vi_server_s *srv, void *p, size_t cap) {
+    if (p) srv->pinned_free.emplace(cap, p);
+}
 
 static bool server_shape_ok(const vi_problem_desc &d) {
     if (d.n_products != 1) return false;
@@ -197,12 +234,16 @@ static void finish(vi_server_s *srv, Request &rq, vi_status st) {
     rq.done = true;
     rq.t_done = now_s();
     srv->used -= rq.bytes;
+    srv->completed.push_back(rq.id);
     srv->cv.notify_all();
+    srv->done_cv.notify_all();
 }
 
 // retirement thread: wait for a finished instance's FP64 conversion, copy the
-// values and the policy to host memory, release the buffers
-static void retire_loop(vi_server_s *srv) {
+// values and the policy to host memory (the caller's buffers given at submission,
+// else pinned buffers of the server's), release the device buffers
+static void retire_loop(vi_server_s *srv, int k) {
+    cudaStream_t rs = srv->rstream[k];
     while (true) {
         RetireJob job;
         {
@@ -214,19 +255,37 @@ static void retire_loop(vi_server_s *srv) {
         }
         Request &rq = *job.req;
         vi_status st = VI_OK;
-        rq.V.resize(job.n);
-        rq.policy.resize(job.n);
+        // device -> pinned staging (a pageable destination would make the copy
+        // synchronous in the driver and hold up the worker's launches), then, for
+        // vi_server_submit_to, a host copy into the caller's buffers on this thread
+        rq.V = (double *)pinned_get(srv, (size_t)job.n * 8, &rq.V_cap);
+        rq.policy = (uint8_t *)pinned_get(srv, job.n, &rq.policy_cap);
         cudaError_t e;
-        if ((e = cudaStreamWaitEvent(srv->rstream, job.ready, 0)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(rq.V.data(), job.scratch, (size_t)job.n * 8, cudaMemcpyDeviceToHost,
-                                 srv->rstream)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(rq.policy.data(), job.policy, job.n, cudaMemcpyDeviceToHost, srv->rstream)) !=
-                cudaSuccess ||
-            (e = cudaStreamSynchronize(srv->rstream)) != cudaSuccess)
+        if (!rq.V || !rq.policy) {
+            st = vi_fail(VI_ENOMEM, "server retire: no pinned host memory for the result");
+        } else if ((e = cudaStreamWaitEvent(rs, job.ready, 0)) != cudaSuccess ||
+                   (e = cudaMemcpyAsync(rq.V, job.scratch, (size_t)job.n * 8, cudaMemcpyDeviceToHost, rs)) !=
+                       cudaSuccess ||
+                   (e = cudaMemcpyAsync(rq.policy, job.policy, job.n, cudaMemcpyDeviceToHost, rs)) != cudaSuccess ||
+                   (e = cudaStreamSynchronize(rs)) != cudaSuccess) {
             st = vi_fail(VI_ECUDA, "server retire: %s", cudaGetErrorString(e));
-        cudaFreeAsync(job.V, srv->rstream);
-        cudaFreeAsync(job.scratch, srv->rstream);
-        cudaFreeAsync(job.policy, srv->rstream);
+        }
+        cudaFreeAsync(job.V, rs);
+        cudaFreeAsync(job.scratch, rs);
+        cudaFreeAsync(job.policy, rs);
+        if (st == VI_OK && (rq.dst_V || rq.dst_policy)) {
+            if (rq.dst_V) memcpy(rq.dst_V, rq.V, (size_t)job.n * 8);
+            if (rq.dst_policy) memcpy(rq.dst_policy, rq.policy, job.n);
+            std::lock_guard<std::mutex> lk(srv->mu);
+            if (rq.dst_V) {
+                pinned_put_locked(srv, rq.V, rq.V_cap);
+                rq.V = nullptr;
+            }
+            if (rq.dst_policy) {
+                pinned_put_locked(srv, rq.policy, rq.policy_cap);
+                rq.policy = nullptr;
+            }
+        }
         cudaEventDestroy(job.ready);
         rq.iters = job.ss.iter;
         rq.crit = job.ss.crit;
@@ -430,7 +489,8 @@ extern "C" vi_status vi_server_create(size_t mem_budget_bytes, int max_slots, vo
         }
     }
     if ((e = cudaStreamCreateWithFlags(&srv->stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&srv->rstream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&srv->rstream[0], cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&srv->rstream[1], cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaMalloc(&srv->d_kps, sizeof(KernelParams) * n)) != cudaSuccess ||
         (e = cudaMallocHost(&srv->h_kps, sizeof(KernelParams) * n)) != cudaSuccess ||
         (e = cudaMalloc(&srv->d_modes, sizeof(int) * n)) != cudaSuccess ||
@@ -474,16 +534,22 @@ extern "C" vi_status vi_server_create(size_t mem_budget_bytes, int max_slots, vo
         cudaSetDevice(dev);
         worker_loop(srv);
     });
-    srv->retirer = std::thread([srv, dev]() {
-        cudaSetDevice(dev);
-        retire_loop(srv);
-    });
+    for (int k = 0; k < kRetireThreads; ++k)
+        srv->retirer[k] = std::thread([srv, dev, k]() {
+            cudaSetDevice(dev);
+            retire_loop(srv, k);
+        });
     *out = srv;
     return VI_OK;
 }
 
 extern "C" vi_status vi_server_submit(vi_server srv, const vi_problem_desc *desc, double tol, int max_iters,
                                       uint64_t *request_id) {
+    return vi_server_submit_to(srv, desc, tol, max_iters, nullptr, nullptr, request_id);
+}
+
+extern "C" vi_status vi_server_submit_to(vi_server srv, const vi_problem_desc *desc, double tol, int max_iters,
+                                         double *V_host, uint8_t *policy_host, uint64_t *request_id) {
     if (!srv || !desc || !request_id) return vi_fail(VI_EINVAL, "null argument");
     if (!server_shape_ok(*desc))
         return vi_fail(VI_EINVAL, "the server takes single-product instances with at least one state digit "
@@ -499,6 +565,8 @@ extern "C" vi_status vi_server_submit(vi_server srv, const vi_problem_desc *desc
         return vi_fail(VI_EINVAL, "expectation tables of %zu entries exceed a slot's %d", rq->ftab.size(),
                        kSlotTabFloats);
     rq->desc.pmf[0] = nullptr;   // the caller's pmf is not kept
+    rq->dst_V = V_host;
+    rq->dst_policy = policy_host;
     rq->tol = tol;
     rq->max_iters = max_iters;
     rq->n_states = rq->kp.nS;
@@ -528,8 +596,15 @@ extern "C" vi_status vi_server_poll(vi_server srv, uint64_t request_id, int *don
         if (!rq->done) return VI_OK;
         srv->all.erase(it);
     }
-    if (V_host && !rq->V.empty()) memcpy(V_host, rq->V.data(), rq->V.size() * sizeof(double));
-    if (policy_host && !rq->policy.empty()) memcpy(policy_host, rq->policy.data(), rq->policy.size());
+    if (V_host && rq->V) memcpy(V_host, rq->V, (size_t)rq->n_states * sizeof(double));
+    if (policy_host && rq->policy) memcpy(policy_host, rq->policy, (size_t)rq->n_states);
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        pinned_put_locked(srv, rq->V, rq->V_cap);
+        pinned_put_locked(srv, rq->policy, rq->policy_cap);
+        rq->V = nullptr;
+        rq->policy = nullptr;
+    }
     if (info) {
         memset(info, 0, sizeof(*info));
         info->iters = rq->iters;
@@ -541,6 +616,22 @@ extern "C" vi_status vi_server_poll(vi_server srv, uint64_t request_id, int *don
         info->updates_per_s = run > 0 ? nominal * rq->iters / run : 0.0;
     }
     return rq->status;
+}
+
+extern "C" vi_status vi_server_wait(vi_server srv, int timeout_ms, uint64_t *ids, int max_ids, int *n_out) {
+    if (!srv || !n_out || max_ids < 0 || (max_ids > 0 && !ids)) return vi_fail(VI_EINVAL, "bad arguments");
+    *n_out = 0;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    if (srv->completed.empty() && timeout_ms > 0)
+        srv->done_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms),
+                              [srv] { return !srv->completed.empty() || srv->stop; });
+    int n = 0;
+    while (n < max_ids && !srv->completed.empty()) {
+        ids[n++] = srv->completed.front();
+        srv->completed.pop_front();
+    }
+    *n_out = n;
+    return VI_OK;
 }
 
 extern "C" vi_status vi_server_destroy(vi_server srv) {
@@ -556,9 +647,11 @@ extern "C" vi_status vi_server_destroy(vi_server srv) {
         srv->retire_stop = true;
         srv->retire_cv.notify_all();
     }
-    if (srv->retirer.joinable()) srv->retirer.join();
+    for (auto &t : srv->retirer)
+        if (t.joinable()) t.join();
     if (srv->stream) cudaStreamSynchronize(srv->stream);
-    if (srv->rstream) cudaStreamSynchronize(srv->rstream);
+    for (auto rs : srv->rstream)
+        if (rs) cudaStreamSynchronize(rs);
     for (auto &sl : srv->slots) {
         if (sl.d_state) cudaFree(sl.d_state);
         if (sl.h_state) cudaFreeHost(sl.h_state);
@@ -578,8 +671,14 @@ extern "C" vi_status vi_server_destroy(vi_server srv) {
     cudaFreeHost(srv->h_sts);
     cudaFree(srv->d_status);
     cudaFreeHost(srv->h_status);
+    for (auto &kv : srv->all) {   // results that were never polled
+        if (kv.second->V) cudaFreeHost(kv.second->V);
+        if (kv.second->policy) cudaFreeHost(kv.second->policy);
+    }
+    for (auto &kv : srv->pinned_free) cudaFreeHost(kv.second);
     if (srv->stream) cudaStreamDestroy(srv->stream);
-    if (srv->rstream) cudaStreamDestroy(srv->rstream);
+    for (auto rs : srv->rstream)
+        if (rs) cudaStreamDestroy(rs);
     if (srv->pool) cudaMemPoolDestroy(srv->pool);
     delete srv;
     return VI_OK;

@@ -123,3 +123,53 @@ def test_invalid_requests_and_shutdown_cancels():
     t0 = time.time()
     vi.vi_server_destroy(srv)                          # cancels it
     assert time.time() - t0 < 60
+
+
+def test_wait_reports_each_finished_request_once():
+    rng = np.random.default_rng(8)
+    insts = [workloads.random_small_instance(rng, max_states=3000) for _ in range(24)]
+    insts = [i for i in insts if i.products[0].n_digits >= 1 and 2 <= i.products[0].Q + 1 <= 24]
+    srv = vi.vi_server_create(1 << 30, 8)
+    try:
+        keep = [desc_of(i) for i in insts]
+        ids = [vi.vi_server_submit(srv, d, 1e-4, 2000) for d, _ in keep]
+        seen = []
+        t0 = time.time()
+        while len(seen) < len(ids):
+            got = vi.vi_server_wait(srv, 20, max_ids=5)
+            assert len(got) <= 5
+            seen += got
+            assert time.time() - t0 < 120.0, "server did not finish"
+        assert sorted(seen) == sorted(ids)
+        for rid, inst in zip(ids, insts):
+            n = inst.n_states
+            V, pol = np.empty(n, np.float64), np.empty(n, np.uint8)
+            done, info = vi.vi_server_poll(srv, rid, V, pol)
+            assert done and info["status"] == vi.VI_OK
+        assert vi.vi_server_wait(srv, 0) == []
+    finally:
+        vi.vi_server_destroy(srv)
+
+
+def test_submit_to_writes_the_callers_buffers():
+    rng = np.random.default_rng(9)
+    insts = [workloads.random_small_instance(rng, max_states=2000) for _ in range(16)]
+    insts = [i for i in insts if i.products[0].n_digits >= 1 and 2 <= i.products[0].Q + 1 <= 24]
+    srv = vi.vi_server_create(1 << 30, 8)
+    try:
+        keep = [desc_of(i) for i in insts]
+        bufs = [(np.full(i.n_states, np.nan), np.full(i.n_states, 255, np.uint8)) for i in insts]
+        ids_to = [vi.vi_server_submit_to(srv, d, 1e-4, 2000, *b) for (d, _), b in zip(keep, bufs)]
+        ids = [vi.vi_server_submit(srv, d, 1e-4, 2000) for d, _ in keep]
+        got = wait_all(srv, ids, {rid: i.n_states for rid, i in zip(ids, insts)})
+        for rid, inst, (V, pol) in zip(ids_to, insts, bufs):
+            t0 = time.time()
+            while not vi.vi_server_poll(srv, rid)[0]:
+                assert time.time() - t0 < 120.0
+                time.sleep(0.002)
+        for rid, (V, pol) in zip(ids, bufs):
+            Vp, Pp, info = got[rid]
+            np.testing.assert_array_equal(V, Vp)
+            np.testing.assert_array_equal(pol, Pp)
+    finally:
+        vi.vi_server_destroy(srv)
