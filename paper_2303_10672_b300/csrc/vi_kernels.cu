@@ -1236,23 +1236,26 @@ __host__ __device__ inline size_t twop_smem(const ProdParams &P1, int threads) {
     return (size_t)(4 * twop_pn4(P1) + 64) * sizeof(float) + (size_t)(P1.dmax + 2) * threads * sizeof(uint32_t);
 }
 
-// orders handled together: their gathers share one probability-window load
-template <int XW>
+// orders handled together (their gathers share one probability-window load) and
+// resident blocks per SM: split lanes trade order blocking for occupancy
+template <int XW, int LPR>
 struct TwopBlock {
-    static constexpr int AB = (XW <= 8) ? 4 : ((XW <= 16) ? 2 : 1);
-    static constexpr int MINB = (XW <= 16) ? 4 : 3;
+    static constexpr int AB = (XW <= 8) ? (LPR == 1 ? 4 : 2) : ((XW <= 16) ? 2 : 1);
+    static constexpr int MINB = (XW <= 8) ? (LPR == 1 ? 4 : 5) : ((XW <= 16) ? 4 : 3);
 };
 
-// thread = (rank, s2), rank fastest; rank -> r1 through a permutation that
+// thread = (part, rank, s2), part fastest; rank -> r1 through a permutation that
 // orders the rests of product 1 by their unit total R1, so that the lanes of a
-// warp walk rest paths of one length.  The thread computes the G1 states
-// x + G1 r1 of product 1 with product-2 state s2 for every joint order, keeps
-// a float key of Q - gamma R0 - H per state, and forms the exact float pair of
-// the best order once at the end.
-template <int XW>
-__global__ void __launch_bounds__(kGenericThreads, TwopBlock<XW>::MINB)
+// warp walk rest paths of one length.  The LPR lanes of a rest split the G1
+// states x + G1 r1 of product 1 with product-2 state s2 (lane `part` owns x =
+// part XW .. part XW + XW - 1) and gather the same values, which the warp
+// serves once; splitting keeps fewer accumulators per lane and more warps per
+// SM.  A lane covers every joint order, keeps a float key of Q - gamma R0 - H
+// per state and forms the exact float pair of the best order once at the end.
+template <int XW, int LPR>
+__global__ void __launch_bounds__(kGenericThreads, TwopBlock<XW, LPR>::MINB)
 twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int) {
-    constexpr int AB = TwopBlock<XW>::AB;
+    constexpr int AB = TwopBlock<XW, LPR>::AB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SolveState *st = kp.st;
     Bufs B;
@@ -1284,9 +1287,11 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
     const uint32_t bd = blockDim.x, tid = threadIdx.x;
     float mx = -INFINITY, mn = INFINITY;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < NR1 * P2.nS) {
-        const uint32_t r1 = kp.two_rperm[t % NR1];
-        const uint32_t s2 = t / NR1;
+    const uint32_t u = t / (uint32_t)LPR;
+    const int x0 = (int)(t - u * (uint32_t)LPR) * XW;   // first expiring-slot value of this lane
+    if (u < NR1 * P2.nS) {
+        const uint32_t r1 = kp.two_rperm[u % NR1];
+        const uint32_t s2 = u / NR1;
         const ProdState ps1 = prod_state(P1, r1 * G1);
         const ProdAction A1 = prod_action(P1, ps1, 0, lifo);
         const int R1 = A1.R;
@@ -1307,7 +1312,7 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
         const uint32_t w1s = S1 / np1;
         const uint32_t pipe_base = r1 / w1s;                        // P_2..P_{L-1} of product 1
         const uint32_t pipe_step = np1 / G1;                        // G1^(L1-2): weight of the order
-        const float *cf0 = (R1 >= 1) ? s_F0 : s_Fm;                 // weight of the rest-free path
+        const float *cf0 = ((R1 >= 1) ? s_F0 : s_Fm) + x0;          // weight of the rest-free path
         float key[XW];
         int arg[XW];
 #pragma unroll
@@ -1344,7 +1349,7 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
                         float g[AB];
 #pragma unroll
                         for (int j = 0; j < AB; ++j) g[j] = row[ie + off[j]];
-                        const float4 *pw = (const float4 *)(s_pc + (e & 3) * pn4 + (e & ~3));
+                        const float4 *pw = (const float4 *)(s_pc + (e & 3) * pn4 + (e & ~3) + x0);
 #pragma unroll
                         for (int q = 0; q < XW / 4; ++q) {
                             const float4 f = pw[q];
@@ -1367,10 +1372,11 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
                             // d1 in [R1, T1): all of the rest taken, the expiring slot partly
                             const float gR = row[s_col[R1 * bd + tid] + off[j]];
                             float cw = 0.f;
+                            for (int y = 0; y < x0; ++y) cw = __fadd_rn(cw, s_pc[R1 + y]);
 #pragma unroll
                             for (int x = 0; x < XW; ++x) {
                                 acc[j][x] = __fmaf_rn(cw, gR, sum);
-                                cw = __fadd_rn(cw, s_pc[R1 + x]);
+                                cw = __fadd_rn(cw, s_pc[R1 + x0 + x]);
                             }
                         } else {
 #pragma unroll
@@ -1391,7 +1397,7 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
                         const int code = a1 * P2.G + a2;
 #pragma unroll
                         for (int x = 0; x < XW; ++x) {
-                            const int T1 = x + R1;   // mixture rows exist for T1 <= min(dmax1, m1 Q1)
+                            const int T1 = x0 + x + R1;   // mixture rows exist for T1 <= min(dmax1, m1 Q1)
                             const float ax = (T1 < (int)nt) ? __fadd_rn(acc[j][x], mixr[T1]) : acc[j][x];
                             const float k = __fmaf_rn(gam, ax, base);
                             const bool up = k > key[x];
@@ -1407,16 +1413,17 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
         const int ys2 = lifo ? A2.R : A2.y1;
         const int ny2 = lifo ? (P2.tmax + 1) : P2.G;
 #pragma unroll
-        for (int x = 0; x < XW; ++x) {
+        for (int xl = 0; xl < XW; ++xl) {
+            const int x = x0 + xl;
             if (x < P1.G) {
-                const int a1 = arg[x] / P2.G, a2 = arg[x] - a1 * P2.G;
+                const int a1 = arg[xl] / P2.G, a2 = arg[xl] - a1 * P2.G;
                 const uint32_t i2n = A2.wk.idx + (uint32_t)a2 * P2.w_top;
                 const float2 c = V2[(uint64_t)S1 * i2n];
                 const float *row = kp.two_e2 + ((uint64_t)s2 * G2 + (uint32_t)a2) * S1;
                 const uint32_t off = (uint32_t)a1 * P1.w_top;
                 float ax;
                 if (!lifo) {
-                    ax = __fmul_rn(cf0[x], row[s_col[tid] + off]);
+                    ax = __fmul_rn(cf0[xl], row[s_col[tid] + off]);
                     for (int e = 1; e <= E1; ++e) ax = __fmaf_rn(s_pc[x + e], row[s_col[e * bd + tid] + off], ax);
                 } else {
                     float sum = 0.f;
@@ -1456,7 +1463,7 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
                     mx = fmaxf(mx, dlt);
                     mn = fminf(mn, dlt);
                 }
-                if (B.pol) B.pol[s] = (uint8_t)arg[x];
+                if (B.pol) B.pol[s] = (uint8_t)arg[xl];
             }
         }
     }
@@ -1464,6 +1471,15 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
 }
 
 static int twop_width(int G) { return G <= 8 ? 8 : (G <= 16 ? 16 : 32); }
+// Lanes per rest of the sweep: one lane per rest while that gives the device
+// about four waves of threads (measured best at 10-17M states); below, lanes of
+// 8 values, which doubled the threads of the 15K-38K-state settings and cut
+// their sweep by about a fifth.
+static int twop_lanes(const ProdParams &P1, const ProdParams &P2) {
+    const uint64_t threads = (uint64_t)(P1.nS / (uint32_t)P1.G) * P2.nS;
+    if (P1.G <= 8 || threads >= 4ull * 148 * 512) return 1;
+    return P1.G <= 16 ? 2 : 4;
+}
 
 static cudaError_t describe_twop(const KernelParams &kp, LaunchDesc &d) {
     const ProdParams &P1 = kp.p[0];
@@ -1471,9 +1487,13 @@ static cudaError_t describe_twop(const KernelParams &kp, LaunchDesc &d) {
     const int w1 = twop_width(P1.G), w2 = twop_width(P2.G);
     const uint64_t n_e2 = (uint64_t)P1.nS * P2.nS;
     const uint64_t n_mix = (uint64_t)kp.two_npipe1 * (uint32_t)kp.two_nt1 * P2.nS;
-    const uint64_t n_sw = (uint64_t)(P1.nS / (uint32_t)P1.G) * P2.nS;
-    d.fn = (w1 == 8) ? (const void *)twop_sweep_kernel<8>
-                     : (w1 == 16) ? (const void *)twop_sweep_kernel<16> : (const void *)twop_sweep_kernel<32>;
+    const int lp = twop_lanes(P1, P2);
+    const uint64_t n_sw = (uint64_t)(P1.nS / (uint32_t)P1.G) * P2.nS * (uint64_t)lp;
+    if (lp == 1)
+        d.fn = (w1 == 8) ? (const void *)twop_sweep_kernel<8, 1>
+                         : (w1 == 16) ? (const void *)twop_sweep_kernel<16, 1> : (const void *)twop_sweep_kernel<32, 1>;
+    else
+        d.fn = (lp == 2) ? (const void *)twop_sweep_kernel<8, 2> : (const void *)twop_sweep_kernel<8, 4>;
     d.grid = dim3((unsigned)((n_sw + kGenericThreads - 1) / kGenericThreads));
     d.block = dim3(kGenericThreads);
     d.smem = twop_smem(P1, kGenericThreads);
