@@ -149,10 +149,104 @@ pc_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, 
     if (mode != MODE_EXTRACT) block_reduce_and_finalize<double>(mx, mn, st, mode, gridDim.x);
 }
 
+// Few states (the paper's m = 3 settings: 3,087): one warp per state, the
+// orders spread over the lanes (lane l takes a = l, l + 32, ..), then the first
+// maximum over the warp by shuffles.  One thread per state would give the
+// device a few blocks only.
+__global__ void __launch_bounds__(kGenericThreads)
+pc_sweep_warp_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int) {
+    SolveState *st = kp.st;
+    Bufs B;
+    if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
+    const ProdParams &P = kp.p[0];
+    const uint32_t G = (uint32_t)P.G;
+    const int m = kp.pc_m;
+    const int Q = P.Q;
+    const int lane = threadIdx.x & 31;
+    double mx = -INFINITY, mn = INFINITY;
+    const uint32_t s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s < kp.nS) {
+        const uint32_t tau = s / P.nS;
+        uint32_t rem = s - tau * P.nS;
+        int X[kPcMaxM];
+#pragma unroll
+        for (int j = 0; j < kPcMaxM; ++j) {
+            X[j] = 0;
+            if (j < m - 1) {
+                const uint32_t q = rem / G;
+                X[j] = (int)(rem - q * G);
+                rem = q;
+            }
+        }
+        const double *W = kp.pc_W + (size_t)tau * P.nS * G;
+        double best = -INFINITY;
+        int arg = 0x7fffffff;
+        for (int a = lane; a <= Q; a += 32) {
+            double q = 0.0;
+            const int c1 = kp.pc_off[a + 1];
+            for (int c = kp.pc_off[a]; c < c1; ++c) {
+                const unsigned long long prof = kp.pc_prof[c];
+                uint32_t idx = 0, wgt = 1;
+#pragma unroll
+                for (int j = 0; j < kPcMaxM - 1; ++j) {
+                    if (j < m - 1) {
+                        const int y = (int)((prof >> (6 * j)) & 63ull);
+                        idx += (uint32_t)min(X[j] + y, Q) * wgt;
+                        wgt *= G;
+                    }
+                }
+                idx += (uint32_t)((prof >> (6 * (m - 1))) & 63ull) * wgt;
+                q = __fma_rn(kp.pc_prob[c], W[idx], q);
+            }
+            if (a > 0) q = __dsub_rn(q, kp.pc_cost[0]);
+            if (q > best) {
+                best = q;
+                arg = a;
+            }
+        }
+        // first maximum over the lanes: larger value, or equal value and smaller order
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+            if (ob > best || (ob == best && oa < arg)) {
+                best = ob;
+                arg = oa;
+            }
+        }
+        if (lane == 0) {
+            const double vold = ((const double *)B.vin)[s];
+            if (mode == MODE_EXTRACT) {
+                if (B.vout) ((double *)B.vout)[s] = vold;
+            } else {
+                ((double *)B.vout)[s] = best;
+                const double dlt = best - vold;
+                if (mode == MODE_SWEEP && st->stop_rule == kStopPeriodic) {
+                    const int it = st->iter;
+                    const size_t n = kp.nS;
+                    kp.pc_ring[(size_t)(it % 7) * n + s] = dlt / pow(kp.gamma, (double)it);
+                    double D = 0.0;
+                    for (int k = 0; k < 7; ++k) D += kp.pc_ring[(size_t)k * n + s];
+                    mx = mn = D;
+                } else {
+                    mx = mn = dlt;
+                }
+            }
+            if (B.pol) B.pol[s] = (uint8_t)arg;
+        }
+    }
+    if (mode != MODE_EXTRACT) block_reduce_and_finalize<double>(mx, mn, st, mode, gridDim.x);
+}
+
+// states below which a sweep takes one warp per state
+constexpr uint32_t kPcWarpStates = 1u << 16;
+
 cudaError_t describe_pc(const KernelParams &kp, LaunchDesc &d) {
     const uint64_t n_post = 7ull * kp.p[0].nS * (uint32_t)kp.p[0].G;
-    d.fn = (const void *)pc_sweep_kernel;
-    d.grid = dim3((kp.nS + kGenericThreads - 1) / kGenericThreads);
+    const bool warp = kp.nS <= kPcWarpStates;
+    d.fn = warp ? (const void *)pc_sweep_warp_kernel : (const void *)pc_sweep_kernel;
+    d.grid = warp ? dim3((unsigned)(((uint64_t)kp.nS * 32 + kGenericThreads - 1) / kGenericThreads))
+                  : dim3((kp.nS + kGenericThreads - 1) / kGenericThreads);
     d.block = dim3(kGenericThreads);
     d.smem = 0;
     d.lpr = 0;

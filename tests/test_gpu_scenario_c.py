@@ -204,3 +204,23 @@ def test_scenario_c_matches_the_paper(row):
     for j, key in enumerate(("service_vi", "wastage_vi", "holding_vi")):
         assert _close(k[:, j], row[key], n, 0.05), (key, k[:, j].mean())
     assert _close(rs, (row["so_return_mean"], row["so_return_sd"]), n, 0.5), rs.mean()
+
+
+def test_large_instance_sampled_backup():
+    """The paper's m = 5 setting (1,361,367 states: the thread-per-state sweep;
+    the m <= 4 cases above take the warp-per-state one): a backup from a value
+    function three sweeps in, at sampled states, against the oracle."""
+    inst = w.scenario_c(5, 2)
+    P = oracle.PeriodicProblem(inst)
+    with PHandle(inst) as H:
+        V, _, info = H.solve(0.0, 3)
+        Vd = torch.tensor(V, device="cuda")
+        Vo = torch.empty_like(Vd)
+        po = torch.empty(len(V), dtype=torch.uint8, device="cuda")
+        vi.vi_backup(H.h, Vd, Vo, po)
+        vo, pn = Vo.cpu().numpy(), po.cpu().numpy()
+    rng = np.random.default_rng(12)
+    states = np.unique(np.concatenate([[0, len(V) - 1], rng.choice(len(V), 14, replace=False)]))
+    v_o, p_o = P.backup_states(V, states)
+    assert np.abs(vo[states] - v_o).max() <= 1e-11 * np.abs(v_o).max()
+    assert not _policy_mismatches(P, V, pn, states)
