@@ -849,6 +849,10 @@ static vi_status autotune(vi_problem *h, cudaStream_t s) {
 // demand they reach, sum over their rests of min(R, Dmax) + 1 (R = units in the
 // slots the demand consumes after the expiring one), heaviest first.  Blocks are
 // dispatched roughly in index order, so the last wave holds the lightest ones.
+// orders computed so far, by (G, K, rest slots, Dmax, lane width)
+static std::mutex g_order_mu;
+static std::map<std::tuple<int, int, int, int, int>, std::vector<uint32_t>> g_order_cache;
+
 static vi_status ensure_group_order(vi_problem *h, int xw) {
     if (h->order_xw == xw && h->d_grp_order) {
         h->kp.grp_order = h->d_grp_order;
@@ -860,18 +864,36 @@ static vi_status ensure_group_order(vi_problem *h, int xw) {
     const uint32_t rb = (uint32_t)(kGroupThreads / lpr);
     const uint32_t nR = P.nS / G;
     const uint32_t nb = (nR + rb - 1) / rb;
-    std::vector<double> w(nb, 0.0);
-    for (uint32_t r = 0; r < nR; ++r) {
-        uint32_t rem = r, R = 0;
-        for (int j = 0; j < P.n_rest_slots; ++j) {
-            R += rem % G;
-            rem /= G;
-        }
-        w[r / rb] += (double)std::min<uint32_t>(R, (uint32_t)P.dmax) + 1.0;
+    const auto key = std::make_tuple(P.G, P.K, P.n_rest_slots, P.dmax, xw);
+    std::vector<uint32_t> order;
+    {
+        std::lock_guard<std::mutex> lk(g_order_mu);
+        auto it = g_order_cache.find(key);
+        if (it != g_order_cache.end()) order = it->second;
     }
-    std::vector<uint32_t> order(nb);
-    for (uint32_t b = 0; b < nb; ++b) order[b] = b;
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return w[a] > w[b]; });
+    if (order.empty()) {
+        std::vector<double> w(nb, 0.0);
+        // the rests in index order: an odometer over their digits keeps the total
+        // of the first n_rest_slots digits without divisions
+        std::vector<uint32_t> dig((size_t)std::max(P.K - 1, 1), 0u);
+        uint32_t R = 0;
+        for (uint32_t r = 0; r < nR; ++r) {
+            w[r / rb] += (double)std::min<uint32_t>(R, (uint32_t)P.dmax) + 1.0;
+            for (int j = 0; j < P.K - 1; ++j) {
+                if (++dig[j] < G) {
+                    if (j < P.n_rest_slots) ++R;
+                    break;
+                }
+                if (j < P.n_rest_slots) R -= G - 1;
+                dig[j] = 0;
+            }
+        }
+        order.resize(nb);
+        for (uint32_t b = 0; b < nb; ++b) order[b] = b;
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return w[a] > w[b]; });
+        std::lock_guard<std::mutex> lk(g_order_mu);
+        g_order_cache[key] = order;
+    }
     if (h->d_grp_order) {
         cudaFree(h->d_grp_order);
         h->d_grp_order = nullptr;
