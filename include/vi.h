@@ -31,7 +31,10 @@
  *    caller; "host" pointers are ordinary host memory owned by the caller.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *  - All scratch (ping-pong value buffer, tables, reduction slots, graphs)
- *    belongs to the handle and is released by vi_problem_destroy.
+ *    belongs to the handle and is released by vi_problem_destroy.  Released
+ *    device blocks (up to 8 GiB), pinned host blocks (up to 256 MiB) and
+ *    streams are kept by the library for the next handle of a similar size;
+ *    vi_release_cached_memory returns them to the driver.
  *  - A handle is not thread-safe; use one handle per host thread.  The solve
  *    server is thread-safe.
  *  - vi_last_error() describes the most recent failure on the calling thread.
@@ -179,8 +182,20 @@ typedef struct {
  * rule or 7 (Q+1)^m >= 2^31; VI_ENOMEM / VI_ECUDA. */
 vi_status vi_problem_create_periodic(const vi_periodic_desc *desc, vi_handle *out);
 
-/* Release every device and host resource of the handle.  NULL is accepted. */
+/* Release every device and host resource of the handle.  NULL is accepted.
+ * Synchronises the current device first (as cudaFree does): the handle's
+ * blocks then go to the library's cache of blocks (see Conventions). */
 vi_status vi_problem_destroy(vi_handle h);
+
+/* Free every cached device block, pinned host block and idle stream that
+ * destroyed handles left to the library (no counterpart in the paper; memory
+ * management).  *bytes_released (may be NULL) receives the bytes freed.  Call
+ * it when no handle is being created or destroyed on another thread. */
+vi_status vi_release_cached_memory(size_t *bytes_released);
+
+/* Bytes currently held in that cache (device plus pinned host).
+ * Errors: VI_EINVAL for a NULL pointer. */
+vi_status vi_cached_memory(size_t *bytes);
 
 /* Sizes: |S|, |A|, nominal |Omega| and bytes per stored value (4 for
  * VI_PREC_FP32_SINGLE, else 8). */
@@ -236,9 +251,14 @@ vi_status vi_solve(vi_handle h, double tol, int max_iters, void *V, uint8_t *pol
                    void *stream, int flags, vi_solve_info *info);
 
 /* vi_solve on host buffers: copies the warm start (if any) host->device,
- * solves, and copies V and policy device->host.  V_host: host buffer in the
- * precision's layout (see vi_solve); policy_host: host uint8[|S|] or NULL.  Device staging buffers
- * are owned by the handle (allocated on first use). */
+ * solves, and returns V and the policy in the host buffers.  V_host: host buffer
+ * in the precision's layout (see vi_solve) holding |S| values; policy_host: host
+ * uint8[|S|] or NULL.  When every given host buffer is page-locked
+ * (cudaMallocHost, cudaHostAlloc, cudaHostRegister) and VI_FLAG_POLICY_EVAL is
+ * not set, the extraction sweep writes V and the policy into them directly, so
+ * the transfer overlaps the sweep; otherwise they are copied from device
+ * staging buffers after it.  Staging buffers are owned by the handle
+ * (allocated on first use). */
 vi_status vi_solve_host(vi_handle h, double tol, int max_iters, void *V_host,
                         uint8_t *policy_host, int flags, vi_solve_info *info);
 

@@ -91,6 +91,8 @@ def lib() -> C.CDLL:
                                C.c_int, C.c_double, C.c_int, C.POINTER(H)], C.c_int),
         "vi_problem_create_desc": ([C.POINTER(vi_problem_desc), C.POINTER(H)], C.c_int),
         "vi_problem_destroy": ([H], C.c_int),
+        "vi_release_cached_memory": ([C.POINTER(C.c_size_t)], C.c_int),
+        "vi_cached_memory": ([C.POINTER(C.c_size_t)], C.c_int),
         "vi_problem_sizes": ([H, C.POINTER(C.c_uint64), C.POINTER(C.c_int), C.POINTER(C.c_int),
                               C.POINTER(C.c_int)], C.c_int),
         "vi_problem_set_option": ([H, C.c_int, C.c_int], C.c_int),
@@ -238,6 +240,20 @@ def vi_problem_create_desc(desc: vi_problem_desc) -> int:
 
 def vi_problem_destroy(h: int) -> None:
     _check(lib().vi_problem_destroy(h), "vi_problem_destroy")
+
+
+def vi_release_cached_memory() -> int:
+    """Free the device / pinned blocks and streams cached from destroyed handles; bytes freed."""
+    n = C.c_size_t()
+    _check(lib().vi_release_cached_memory(C.byref(n)), "vi_release_cached_memory")
+    return n.value
+
+
+def vi_cached_memory() -> int:
+    """Bytes held in the library's cache of released blocks."""
+    n = C.c_size_t()
+    _check(lib().vi_cached_memory(C.byref(n)), "vi_cached_memory")
+    return n.value
 
 
 def vi_problem_sizes(h: int) -> dict:

@@ -22,6 +22,7 @@
 
 #include "../../include/vi.h"
 #include "vi_api_internal.h"
+#include "vi_pool.h"
 #include "vi_common.cuh"
 #include "vi_kernels.h"
 
@@ -385,10 +386,10 @@ extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_hand
     for (size_t i = 0; i < blob.size(); ++i) fblob[i] = (float)blob[i];
 
     cudaError_t e;
-    if ((e = cudaMalloc(&h->d_tab_f, fblob.size() * sizeof(float))) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_tab_d, blob.size() * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_state, sizeof(SolveState))) != cudaSuccess ||
-        (e = cudaMallocHost(&h->h_state, sizeof(SolveState))) != cudaSuccess ||
+    if ((e = vip::dev_alloc_t(&h->d_tab_f, fblob.size() * sizeof(float))) != cudaSuccess ||
+        (e = vip::dev_alloc_t(&h->d_tab_d, blob.size() * sizeof(double))) != cudaSuccess ||
+        (e = vip::dev_alloc_t(&h->d_state, sizeof(SolveState))) != cudaSuccess ||
+        (e = vip::host_alloc((void **)&h->h_state, sizeof(SolveState))) != cudaSuccess ||
         (e = cudaMemcpy(h->d_tab_f, fblob.data(), fblob.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
             cudaSuccess ||
         (e = cudaMemcpy(h->d_tab_d, blob.data(), blob.size() * sizeof(double), cudaMemcpyHostToDevice)) !=
@@ -407,8 +408,8 @@ extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_hand
     if (h->two_ok) {
         size_t n_mix = 0;
         const size_t n_e2 = two_table_floats(kp, &n_mix);
-        if ((e = cudaMalloc(&h->d_two_e2, n_e2 * sizeof(float))) != cudaSuccess ||
-            (e = cudaMalloc(&h->d_two_mix, n_mix * sizeof(float))) != cudaSuccess) {
+        if ((e = vip::dev_alloc_t(&h->d_two_e2, n_e2 * sizeof(float))) != cudaSuccess ||
+            (e = vip::dev_alloc_t(&h->d_two_mix, n_mix * sizeof(float))) != cudaSuccess) {
             destroy_internal(h);
             return vi_fail(e == cudaErrorMemoryAllocation ? VI_ENOMEM : VI_ECUDA, "two-product tables: %s",
                            cudaGetErrorString(e));
@@ -431,7 +432,7 @@ extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_hand
                 perm[r] = r;
             }
             std::stable_sort(perm.begin(), perm.end(), [&](uint32_t a, uint32_t b) { return tot[a] < tot[b]; });
-            if ((e = cudaMalloc(&h->d_two_rperm, nr * sizeof(uint32_t))) != cudaSuccess ||
+            if ((e = vip::dev_alloc_t(&h->d_two_rperm, nr * sizeof(uint32_t))) != cudaSuccess ||
                 (e = cudaMemcpy(h->d_two_rperm, perm.data(), nr * sizeof(uint32_t), cudaMemcpyHostToDevice)) !=
                     cudaSuccess) {
                 destroy_internal(h);
@@ -579,16 +580,16 @@ extern "C" vi_status vi_problem_create_periodic(const vi_periodic_desc *desc, vi
 
     const size_t n_pmf = (size_t)7 * (d.dmax + 1);
     cudaError_t e;
-    if ((e = cudaMalloc(&h->d_pc_pmf, n_pmf * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_pc_prof, prof.size() * sizeof(unsigned long long))) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_pc_prob, prob.size() * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_pc_off, off.size() * sizeof(int))) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_pc_W, (size_t)n_post * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_pc_ring, (size_t)7 * kp.nS * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_pc_thr_d, thr_d.size() * sizeof(unsigned long long))) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_pc_thr_y, thr_y.size() * sizeof(unsigned long long))) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_state, sizeof(SolveState))) != cudaSuccess ||
-        (e = cudaMallocHost(&h->h_state, sizeof(SolveState))) != cudaSuccess ||
+    if ((e = vip::dev_alloc_t(&h->d_pc_pmf, n_pmf * sizeof(double))) != cudaSuccess ||
+        (e = vip::dev_alloc_t(&h->d_pc_prof, prof.size() * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = vip::dev_alloc_t(&h->d_pc_prob, prob.size() * sizeof(double))) != cudaSuccess ||
+        (e = vip::dev_alloc_t(&h->d_pc_off, off.size() * sizeof(int))) != cudaSuccess ||
+        (e = vip::dev_alloc_t(&h->d_pc_W, (size_t)n_post * sizeof(double))) != cudaSuccess ||
+        (e = vip::dev_alloc_t(&h->d_pc_ring, (size_t)7 * kp.nS * sizeof(double))) != cudaSuccess ||
+        (e = vip::dev_alloc_t(&h->d_pc_thr_d, thr_d.size() * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = vip::dev_alloc_t(&h->d_pc_thr_y, thr_y.size() * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = vip::dev_alloc_t(&h->d_state, sizeof(SolveState))) != cudaSuccess ||
+        (e = vip::host_alloc((void **)&h->h_state, sizeof(SolveState))) != cudaSuccess ||
         (e = cudaMemcpy(h->d_pc_pmf, d.pmf, n_pmf * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(h->d_pc_prof, prof.data(), prof.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(h->d_pc_prob, prob.data(), prob.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -642,26 +643,26 @@ static void destroy_internal(vi_problem *h) {
     if (!h) return;
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->graph) cudaGraphDestroy(h->graph);
-    if (h->d_tab_f) cudaFree(h->d_tab_f);
-    if (h->d_tab_d) cudaFree(h->d_tab_d);
-    if (h->d_state) cudaFree(h->d_state);
-    if (h->h_state) cudaFreeHost(h->h_state);
-    if (h->d_scratch) cudaFree(h->d_scratch);
-    if (h->d_two_e2) cudaFree(h->d_two_e2);
-    if (h->d_two_mix) cudaFree(h->d_two_mix);
-    if (h->d_two_rperm) cudaFree(h->d_two_rperm);
-    if (h->d_grp_order) cudaFree(h->d_grp_order);
+    if (h->d_tab_f) vip::release(h->d_tab_f);
+    if (h->d_tab_d) vip::release(h->d_tab_d);
+    if (h->d_state) vip::release(h->d_state);
+    if (h->h_state) vip::release(h->h_state);
+    if (h->d_scratch) vip::release(h->d_scratch);
+    if (h->d_two_e2) vip::release(h->d_two_e2);
+    if (h->d_two_mix) vip::release(h->d_two_mix);
+    if (h->d_two_rperm) vip::release(h->d_two_rperm);
+    if (h->d_grp_order) vip::release(h->d_grp_order);
     void *pc_bufs[] = {h->d_pc_pmf, h->d_pc_prof, h->d_pc_prob, h->d_pc_off, h->d_pc_W, h->d_pc_ring,
                        h->d_pc_thr_d, h->d_pc_thr_y};
     for (void *b : pc_bufs)
-        if (b) cudaFree(b);
-    if (h->d_pe[0]) cudaFree(h->d_pe[0]);
-    if (h->d_pe[1]) cudaFree(h->d_pe[1]);
-    if (h->d_stage_v) cudaFree(h->d_stage_v);
-    if (h->d_stage_p) cudaFree(h->d_stage_p);
+        if (b) vip::release(b);
+    if (h->d_pe[0]) vip::release(h->d_pe[0]);
+    if (h->d_pe[1]) vip::release(h->d_pe[1]);
+    if (h->d_stage_v) vip::release(h->d_stage_v);
+    if (h->d_stage_p) vip::release(h->d_stage_p);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
-    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    if (h->own_stream) vip::stream_put(h->own_stream);
     delete h;
 }
 
@@ -895,10 +896,11 @@ static vi_status ensure_group_order(vi_problem *h, int xw) {
         g_order_cache[key] = order;
     }
     if (h->d_grp_order) {
-        cudaFree(h->d_grp_order);
+        cudaDeviceSynchronize();   // queued sweeps may still read the old order
+        vip::release(h->d_grp_order);
         h->d_grp_order = nullptr;
     }
-    CUDA_TRY(cudaMalloc(&h->d_grp_order, (size_t)nb * sizeof(uint32_t)));
+    CUDA_TRY(vip::dev_alloc_t(&h->d_grp_order, (size_t)nb * sizeof(uint32_t)));
     CUDA_TRY(cudaMemcpy(h->d_grp_order, order.data(), (size_t)nb * sizeof(uint32_t), cudaMemcpyHostToDevice));
     h->order_xw = xw;
     h->kp.grp_order = h->d_grp_order;
@@ -943,7 +945,7 @@ extern "C" vi_status vi_problem_kernel(vi_handle h, int *kernel, int *width) {
 // ---------------------------------------------------------------------------
 static vi_status ensure_scratch(vi_problem *h) {
     if (h->d_scratch) return VI_OK;
-    CUDA_TRY(cudaMalloc(&h->d_scratch, (size_t)h->kp.nS * h->value_bytes));
+    CUDA_TRY(vip::dev_alloc_t(&h->d_scratch, (size_t)h->kp.nS * h->value_bytes));
     return VI_OK;
 }
 
@@ -1075,8 +1077,18 @@ static vi_status run_host_loop(vi_problem *h, cudaStream_t s) {
 static vi_status policy_eval_impl(vi_problem *h, const uint8_t *policy, double *V, double tol, int max_iters,
                                   cudaStream_t s, int *iters_out, double *delta_out);
 
+static vi_status solve_impl(vi_problem *h, double tol, int max_iters, void *V, uint8_t *policy, void *stream,
+                            int flags, vi_solve_info *info, void *vhost);
+
 extern "C" vi_status vi_solve(vi_handle h, double tol, int max_iters, void *V, uint8_t *policy, void *stream,
                               int flags, vi_solve_info *info) {
+    return solve_impl(h, tol, max_iters, V, policy, stream, flags, info, nullptr);
+}
+
+// vhost: device view of pinned host memory that the extraction sweep fills with
+// the final V (V itself then need not hold it), or null
+static vi_status solve_impl(vi_problem *h, double tol, int max_iters, void *V, uint8_t *policy, void *stream,
+                            int flags, vi_solve_info *info, void *vhost) {
     if (!h) return vi_fail(VI_EINVAL, "null handle");
     if (!V) return vi_fail(VI_EINVAL, "null V");
     if (!(tol >= 0.0) || max_iters < 0) return vi_fail(VI_EINVAL, "need tol >= 0 and max_iters >= 0");
@@ -1099,6 +1111,7 @@ extern "C" vi_status vi_solve(vi_handle h, double tol, int max_iters, void *V, u
     hs->buf[0] = V;
     hs->buf[1] = h->d_scratch;
     hs->policy = policy;
+    hs->vhost = vhost;
     hs->tol = tol;
     hs->gamma = h->desc.gamma;
     hs->max_iters = max_iters;
@@ -1142,8 +1155,8 @@ extern "C" vi_status vi_solve(vi_handle h, double tol, int max_iters, void *V, u
     if ((flags & VI_FLAG_POLICY_EVAL) && policy && info) {
         const uint32_t n = h->kp.nS;
         if (!h->d_pe[0]) {
-            CUDA_TRY(cudaMalloc(&h->d_pe[0], (size_t)n * sizeof(double)));
-            CUDA_TRY(cudaMalloc(&h->d_pe[1], (size_t)n * sizeof(double)));
+            CUDA_TRY(vip::dev_alloc_t(&h->d_pe[0], (size_t)n * sizeof(double)));
+            CUDA_TRY(vip::dev_alloc_t(&h->d_pe[1], (size_t)n * sizeof(double)));
         }
         // start from V_abs of the solve, evaluate the extracted policy in FP64
         CUDA_TRY(launch_to_fp64(V, h->vk, info->offset, h->d_pe[0], n, s));
@@ -1163,17 +1176,41 @@ extern "C" vi_status vi_solve(vi_handle h, double tol, int max_iters, void *V, u
     return result;
 }
 
+// the device view of page-locked host memory (cudaMallocHost / cudaHostAlloc /
+// cudaHostRegister), or false for pageable memory
+static bool pinned_view(void *p, void **dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+    *dev = a.devicePointer;
+    return true;
+}
+
 extern "C" vi_status vi_solve_host(vi_handle h, double tol, int max_iters, void *V_host, uint8_t *policy_host,
                                    int flags, vi_solve_info *info) {
     if (!h) return vi_fail(VI_EINVAL, "null handle");
     if (!V_host) return vi_fail(VI_EINVAL, "null V_host");
-    if (!h->own_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+    if (!h->own_stream) CUDA_TRY(vip::stream_get(&h->own_stream));
     const size_t nb = (size_t)h->kp.nS * h->value_bytes;
-    if (!h->d_stage_v) CUDA_TRY(cudaMalloc(&h->d_stage_v, nb));
-    if (policy_host && !h->d_stage_p) CUDA_TRY(cudaMalloc(&h->d_stage_p, h->kp.nS));
+    if (!h->d_stage_v) CUDA_TRY(vip::dev_alloc_t(&h->d_stage_v, nb));
+    if (policy_host && !h->d_stage_p) CUDA_TRY(vip::dev_alloc_t(&h->d_stage_p, h->kp.nS));
     cudaStream_t s = h->own_stream;
     if (flags & VI_FLAG_WARM_START) CUDA_TRY(cudaMemcpyAsync(h->d_stage_v, V_host, nb, cudaMemcpyHostToDevice, s));
-    vi_status st = vi_solve(h, tol, max_iters, h->d_stage_v, policy_host ? h->d_stage_p : nullptr, s, flags, info);
+    // pinned host buffers: the extraction sweep writes V and the policy straight into
+    // them, so the transfer overlaps the sweep instead of following it (not with the
+    // FP64 policy evaluation, which reads both on the device afterwards)
+    void *dv = nullptr, *dp = nullptr;
+    const bool direct = !(flags & VI_FLAG_POLICY_EVAL) && pinned_view(V_host, &dv) &&
+                        (!policy_host || pinned_view(policy_host, &dp));
+    vi_status st;
+    if (direct) {
+        st = solve_impl(h, tol, max_iters, h->d_stage_v, (uint8_t *)dp, s, flags, info, dv);
+        return st;   // solve_impl synchronised the stream after the extraction sweep
+    }
+    st = vi_solve(h, tol, max_iters, h->d_stage_v, policy_host ? h->d_stage_p : nullptr, s, flags, info);
     if (st != VI_OK && st != VI_ENOTCONVERGED) return st;
     CUDA_TRY(cudaMemcpyAsync(V_host, h->d_stage_v, nb, cudaMemcpyDeviceToHost, s));
     if (policy_host) CUDA_TRY(cudaMemcpyAsync(policy_host, h->d_stage_p, h->kp.nS, cudaMemcpyDeviceToHost, s));

@@ -101,6 +101,7 @@ struct SolveState {
     // configuration (written by the host before a solve)
     void *buf[2];                 // buf[0] = caller's V, buf[1] = scratch
     uint8_t *policy;              // caller's policy or null
+    void *vhost;                  // extraction writes V here (device view of pinned host memory) or null
     double tol;
     double gamma;
     int max_iters;

@@ -133,7 +133,9 @@ __device__ __forceinline__ bool resolve_bufs(const SolveState *st, int mode, con
     } else if (mode == MODE_EXTRACT) {
         const int it = st->iter;
         b.vin = st->buf[it & 1];
-        b.vout = (it & 1) ? st->buf[0] : nullptr;   // the result must end in the caller's buffer
+        // the result must end in the caller's buffer: pinned host memory written over
+        // the bus while the sweep runs, else buf[0] if the last sweep wrote the scratch
+        b.vout = st->vhost ? st->vhost : ((it & 1) ? st->buf[0] : nullptr);
         b.pol = st->policy;
         b.cnorm = 0.f;
     } else {

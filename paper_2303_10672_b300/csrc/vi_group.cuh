@@ -217,7 +217,12 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                 ref = __ldg(V2 + idx0);
             else
                 g0 = __ldg(V1 + idx0);
-            float acc[XW];
+            // accumulators in pairs of x, so that the widest FIFO correlations run on
+            // packed two-lane FMAs (each lane rounds exactly as fmaf)
+            float2 acc2[(XW + 1) / 2];
+            auto acc = [&](int xi) -> float & { return (xi & 1) ? acc2[xi >> 1].y : acc2[xi >> 1].x; };
+#pragma unroll
+            for (int i = 0; i < (XW + 1) / 2; ++i) acc2[i] = make_float2(0.f, 0.f);
             if (!LIFO) {
                 // demand k = d - x reaching the other slots; d <= x leaves them untouched:
                 //   C(x) = F(x) g(0) + sum_{k=1}^{R-1} p[x+k] g(k) + tail[x+R] g(R)      (R >= 1)
@@ -228,13 +233,20 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                 constexpr int KW = 8;
                 constexpr int NG = XW >= 12 ? 3 : (XW >= 6 ? 2 : 1);
                 constexpr int GS = (XW + NG - 1) / NG;
-                if (PAIR) {
-#pragma unroll
-                    for (int xi = 0; xi < XW; ++xi) acc[xi] = 0.f;
-                } else {
+                // 16 or more x per lane: packed FMAs over pairs of x (measured on B300: 1% faster
+                // at 21; the narrower lanes have too few independent pairs per skip group and
+                // lose).  Pairs per skip group are even, so that each group's probability
+                // window starts on a 16-byte boundary (2 q GP floats past the chunk's start).
+                constexpr bool PACKED = XW >= 16;
+                constexpr int XP = (XW + 1) / 2;
+                constexpr int GP = (((XP + NG - 1) / NG) + 1) & ~1;
+                constexpr int NGE = (XP + GP - 1) / GP;     // non-empty groups
+                constexpr int WQ = (GP + KW / 2) / 2;       // float4 loads per group window
+                static_assert(GP % 2 == 0 && 2 * WQ >= GP + KW / 2 - 1, "window layout");
+                if (!PAIR) {
                     const float *s_F = s_tab + P.off_F + x0;
 #pragma unroll
-                    for (int xi = 0; xi < XW; ++xi) acc[xi] = (R == 0) ? g0 : s_F[xi] * g0;
+                    for (int xi = 0; xi < XW; ++xi) acc(xi) = (R == 0) ? g0 : s_F[xi] * g0;
                 }
                 const uint32_t atop = (uint32_t)a * P.w_top;
                 int ecur = 0;
@@ -256,6 +268,8 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                 // window of chunk k0 (k0 = 1 mod 4): p[x0 + k0 + i] = copy_o[x0 + k0 - o + i]
                 const int po = (x0 + 1) & 3;
                 const float *s_px = s_pc + po * pn4 + (x0 + 1 - po);   // + (k0 - 1) is a multiple of 4
+                const int po1 = (x0 + 2) & 3;                          // the window shifted by one
+                const float *s_px1 = s_pc + po1 * pn4 + (x0 + 2 - po1);
                 constexpr bool preclamped = PAIR && LPIPE;   // with shared_fifo: see the column set-up
                 for (int k0 = 1; k0 <= kend; k0 += KW) {
                     uint32_t idx[KW];
@@ -282,25 +296,56 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
 #pragma unroll
                         for (int j = 0; j < KW; ++j) g[j] = (k0 + j <= kend) ? __ldg(V1 + idx[j]) : 0.f;
                     }
-                    constexpr int NW4 = (XW + KW - 1 + 3) / 4;
-                    float pw[4 * NW4];
-                    const float4 *pw4 = (const float4 *)(s_px + (k0 - 1));
+                    if constexpr (PACKED) {
 #pragma unroll
-                    for (int t = 0; t < NW4; ++t) {
-                        const float4 v = pw4[t];
-                        pw[4 * t] = v.x;
-                        pw[4 * t + 1] = v.y;
-                        pw[4 * t + 2] = v.z;
-                        pw[4 * t + 3] = v.w;
-                    }
+                        for (int q = 0; q < NGE; ++q) {
+                            if (q == 0 || x0 + 2 * q * GP + k0 <= dmax) {
+                                // this group's probability pairs (p[x+k0+2t], p[x+k0+2t+1]) and
+                                // the same shifted by one (x = x0 + 2 q GP), so that every
+                                // (x pair, k) coefficient is one aligned register pair
+                                float2 pe[2 * WQ], pod[2 * WQ];
+                                const float4 *we = (const float4 *)(s_px + (k0 - 1) + 2 * q * GP);
+                                const float4 *wo = (const float4 *)(s_px1 + (k0 - 1) + 2 * q * GP);
 #pragma unroll
-                    for (int q = 0; q < NG; ++q) {
-                        if (q == 0 || x0 + q * GS + k0 <= dmax) {
+                                for (int t = 0; t < WQ; ++t) {
+                                    const float4 v = we[t], u = wo[t];
+                                    pe[2 * t] = make_float2(v.x, v.y);
+                                    pe[2 * t + 1] = make_float2(v.z, v.w);
+                                    pod[2 * t] = make_float2(u.x, u.y);
+                                    pod[2 * t + 1] = make_float2(u.z, u.w);
+                                }
 #pragma unroll
-                            for (int j = 0; j < KW; ++j)
+                                for (int j = 0; j < KW; ++j) {
+                                    const float2 gj = make_float2(g[j], g[j]);
 #pragma unroll
-                                for (int xi = q * GS; xi < min(XW, (q + 1) * GS); ++xi)
-                                    acc[xi] = fmaf(pw[xi + j], g[j], acc[xi]);
+                                    for (int i = q * GP; i < min(XP, (q + 1) * GP); ++i) {
+                                        const int t = i - q * GP + (j >> 1);
+                                        acc2[i] = __ffma2_rn((j & 1) ? pod[t] : pe[t], gj, acc2[i]);
+                                    }
+                                }
+                            }
+                        }
+                    } else {
+                        constexpr int NW4 = (XW + KW - 1 + 3) / 4;
+                        float pw[4 * NW4];
+                        const float4 *pw4 = (const float4 *)(s_px + (k0 - 1));
+#pragma unroll
+                        for (int t = 0; t < NW4; ++t) {
+                            const float4 v = pw4[t];
+                            pw[4 * t] = v.x;
+                            pw[4 * t + 1] = v.y;
+                            pw[4 * t + 2] = v.z;
+                            pw[4 * t + 3] = v.w;
+                        }
+#pragma unroll
+                        for (int q = 0; q < NG; ++q) {
+                            if (q == 0 || x0 + q * GS + k0 <= dmax) {
+#pragma unroll
+                                for (int j = 0; j < KW; ++j)
+#pragma unroll
+                                    for (int xi = q * GS; xi < min(XW, (q + 1) * GS); ++xi)
+                                        acc(xi) = fmaf(pw[xi + j], g[j], acc(xi));
+                            }
                         }
                     }
                 }
@@ -308,7 +353,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                     const float gR = value_of((preclamped && shared_fifo) ? tail_rel + atop : index_of(R));
                     const float *s_tx = s_tab + P.off_tail + x0 + R;
 #pragma unroll
-                    for (int xi = 0; xi < XW; ++xi) acc[xi] = fmaf(s_tx[xi], gR, acc[xi]);
+                    for (int xi = 0; xi < XW; ++xi) acc(xi) = fmaf(s_tx[xi], gR, acc(xi));
                 }
             } else if (shared_lifo) {
                 // C_a = sum_{d < R} p_d g_a(d) + tail[R] g_a(R), g_a(e) = T[a-e] while the
@@ -325,7 +370,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                     c = fmaf(s_tab[P.off_tail + R], *pR, c);
                 }
 #pragma unroll
-                for (int xi = 0; xi < XW; ++xi) acc[xi] = c;
+                for (int xi = 0; xi < XW; ++xi) acc(xi) = c;
             } else {
                 float c = 0.f;
                 int ecur = 0;
@@ -352,7 +397,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                     for (int j = 0; j < LCH; ++j) c = fmaf(s_p[d0 + j], gv[j], c);   // zero mass beyond dmax
                 }
 #pragma unroll
-                for (int xi = 0; xi < XW; ++xi) acc[xi] = c;
+                for (int xi = 0; xi < XW; ++xi) acc(xi) = c;
             }
             // lanes past the last x (x0 + xi >= G) compute values that are never stored;
             // their table reads stay inside the shared memory that follows the tables
@@ -362,7 +407,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                 // expectation depends on x, so one comparison serves every x
                 float Bh, Bl;
                 action_base(gam, ref, R0, __fmul_rn(-c_o, (float)a), Bh, Bl);
-                const float ql = __fmaf_rn(gam, acc[0], Bl);
+                const float ql = __fmaf_rn(gam, acc(0), Bl);
                 const float diff = __fadd_rn(__fsub_rn(Bh, bh[0]), __fsub_rn(ql, bl[0]));
                 take(0, diff > 0.f, Bh, ql, a);
             } else if (PAIR && rt_common) {
@@ -372,7 +417,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                 action_base(gam, ref, R0, __fmul_rn(-c_o, (float)a), Bh, Bl);
 #pragma unroll
                 for (int xi = 0; xi < XW; ++xi) {
-                    const float ql = __fmaf_rn(gam, acc[xi], Bl);
+                    const float ql = __fmaf_rn(gam, acc(xi), Bl);
                     const float diff = __fadd_rn(__fsub_rn(Bh, bh[xi]), __fsub_rn(ql, bl[xi]));
                     take(xi, diff > 0.f, Bh, ql, a);
                 }
@@ -381,7 +426,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                 // (-c_o a, gamma C_a).  Compare the single float -c_o a + gamma C_a + RT(x, R);
                 // the exact pair of the chosen order is rebuilt after the last order.
                 const float Bh = __fmul_rn(-c_o, (float)a);
-                const float Bl = __fmaf_rn(gam, acc[0], 0.f);
+                const float Bl = __fmaf_rn(gam, acc(0), 0.f);
                 s_kc[a * kGroupThreads] = Bl;
                 const float ks = __fadd_rn(Bh, Bl);
 #pragma unroll
@@ -392,13 +437,13 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
             } else if (PAIR) {
                 float Bh, Bl;
                 action_base(gam, ref, R0, __fmul_rn(-c_o, (float)a), Bh, Bl);
-                if (LIFO) Bl = __fmaf_rn(gam, acc[0], Bl);   // the expectation does not depend on x
+                if (LIFO) Bl = __fmaf_rn(gam, acc(0), Bl);   // the expectation does not depend on x
                 const float *rtl = s_RTlo + R * G + x0;
 #pragma unroll
                 for (int xi = 0; xi < XW; ++xi) {
                     float qh = Bh, ql = Bl;
                     pair_add(qh, ql, rt[xi], rtl[xi]);
-                    if (!LIFO) ql = __fmaf_rn(gam, acc[xi], ql);
+                    if (!LIFO) ql = __fmaf_rn(gam, acc(xi), ql);
                     const float diff = __fadd_rn(__fsub_rn(qh, bh[xi]), __fsub_rn(ql, bl[xi]));
                     take(xi, diff > 0.f, qh, ql, a);
                 }
@@ -406,7 +451,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                 const float base = -c_o * (float)a;
 #pragma unroll
                 for (int xi = 0; xi < XW; ++xi) {
-                    const float q = fmaf(gam, acc[xi], base + rt[xi]);
+                    const float q = fmaf(gam, acc(xi), base + rt[xi]);
                     take(xi, q > bh[xi], q, 0.f, a);
                 }
             }
