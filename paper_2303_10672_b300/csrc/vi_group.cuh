@@ -26,6 +26,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                                            unsigned char *smem_raw) {
     constexpr bool PAIR = (VK == VK_PAIR);
     constexpr int LCH = 8;   // LIFO load batch
+    constexpr int LCS = 8;   // load batch of the shared LIFO sequences
     SolveState *st = kp.st;
     Bufs B;
     if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
@@ -130,30 +131,30 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                 if (PAIR) return pair_diff(__ldg(V2 + i), R0);
                 return __ldg(V1 + i);
             };
-            for (int j0 = 0; j0 < G; j0 += LCH) {
-                float v[LCH];
+            for (int j0 = 0; j0 < G; j0 += LCS) {
+                float v[LCS];
 #pragma unroll
-                for (int j = 0; j < LCH; ++j) v[j] = (j0 + j < G) ? value(r + (uint32_t)(j0 + j) * P.w_top) : 0.f;
+                for (int j = 0; j < LCS; ++j) v[j] = (j0 + j < G) ? value(r + (uint32_t)(j0 + j) * P.w_top) : 0.f;
 #pragma unroll
-                for (int j = 0; j < LCH; ++j)
+                for (int j = 0; j < LCS; ++j)
                     if (j0 + j < G) colT[(j0 + j) * kGroupThreads] = v[j];
             }
             Walker wh;
             walker_init(wh, r, ri.packed, P.m - 2, P.cb, 1, P.m >= 3 ? P.w_zt / (uint32_t)G : 1u);
             int kc = 0;
-            for (int k0 = 0; k0 < nH; k0 += LCH) {
-                uint32_t idx[LCH];
+            for (int k0 = 0; k0 < nH; k0 += LCS) {
+                uint32_t idx[LCS];
 #pragma unroll
-                for (int j = 0; j < LCH; ++j) {
+                for (int j = 0; j < LCS; ++j) {
                     const int kk = min(k0 + j, nH - 1);
                     for (; kc < kk; ++kc) walker_step(wh, P.cb, 1, (uint32_t)G);
                     idx[j] = wh.idx;
                 }
-                float v[LCH];
+                float v[LCS];
 #pragma unroll
-                for (int j = 0; j < LCH; ++j) v[j] = value(idx[j]);
+                for (int j = 0; j < LCS; ++j) v[j] = value(idx[j]);
 #pragma unroll
-                for (int j = 0; j < LCH; ++j)
+                for (int j = 0; j < LCS; ++j)
                     if (k0 + j < nH) colH[(k0 + j) * kGroupThreads] = v[j];
             }
         }
@@ -505,22 +506,40 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
     const uint32_t s0 = bid * (uint32_t)(RB * G);
     const uint32_t nblk = (uint32_t)(RB * G);
     float mx = -INFINITY, mn = INFINITY;
-    for (uint32_t i = threadIdx.x; i < nblk; i += kGroupThreads) {
+    if (PAIR && mode != MODE_EXTRACT) {
+        // the previous values of WB states are loaded together, so that one load
+        // latency serves WB states instead of one
+        constexpr int WB = LIFO ? 4 : 1;
+        const float2 *vin2 = (const float2 *)B.vin;
+        float2 *vout2 = (float2 *)B.vout;
+        for (uint32_t i0 = threadIdx.x; i0 < nblk; i0 += WB * kGroupThreads) {
+            float2 vold[WB];
+#pragma unroll
+            for (int u = 0; u < WB; ++u) {
+                const uint32_t i = i0 + (uint32_t)u * kGroupThreads;
+                vold[u] = (i < nblk && s0 + i < P.nS) ? vin2[s0 + i] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < WB; ++u) {
+                const uint32_t i = i0 + (uint32_t)u * kGroupThreads;
+                if (i < nblk && s0 + i < P.nS) {
+                    const float2 vnew = ((const float2 *)s_out)[i];
+                    vout2[s0 + i] = vnew;
+                    const float dlt = pair_diff(vnew, vold[u]);
+                    mx = fmaxf(mx, dlt);
+                    mn = fminf(mn, dlt);
+                    if (B.pol) B.pol[s0 + i] = s_pol[i];
+                }
+            }
+        }
+    }
+    for (uint32_t i = threadIdx.x; i < ((PAIR && mode != MODE_EXTRACT) ? 0u : nblk); i += kGroupThreads) {
         const uint32_t s = s0 + i;
         if (s >= P.nS) break;
         if (PAIR) {
             const float2 *vin2 = (const float2 *)B.vin;
             float2 *vout2 = (float2 *)B.vout;
-            if (mode == MODE_EXTRACT) {
-                if (vout2) vout2[s] = vin2[s];
-            } else {
-                const float2 vnew = ((const float2 *)s_out)[i];
-                const float2 vold = vin2[s];
-                vout2[s] = vnew;
-                const float dlt = pair_diff(vnew, vold);
-                mx = fmaxf(mx, dlt);
-                mn = fminf(mn, dlt);
-            }
+            if (vout2) vout2[s] = vin2[s];   // extraction: only when the result must move
         } else {
             const float *vin1 = (const float *)B.vin;
             float *vout1 = (float *)B.vout;
