@@ -147,9 +147,31 @@ __device__ __forceinline__ bool resolve_bufs(const SolveState *st, int mode, con
     return true;
 }
 
+// Stage a table blob in shared memory: 16-byte loads, eight in flight per thread
+// before any is stored (a plain element loop waits one L2 round trip per element
+// at the start of every block), then the elements past the last full 16 bytes.
 template <typename T>
 __device__ __forceinline__ void load_tables(T *s_tab, const T *g_tab, int n) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s_tab[i] = g_tab[i];
+    const int nb = n * (int)sizeof(T);
+    int done = 0;   // elements copied by the vector part
+    if ((((uintptr_t)g_tab | (uintptr_t)s_tab) & 15) == 0) {
+        constexpr int U = 8;
+        const int n16 = nb >> 4;
+        const uint4 *src = (const uint4 *)g_tab;
+        uint4 *dst = (uint4 *)s_tab;
+        const int step = (int)blockDim.x;
+        int i = (int)threadIdx.x;
+        for (; i + (U - 1) * step < n16; i += U * step) {
+            uint4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = __ldg(src + i + u * step);
+#pragma unroll
+            for (int u = 0; u < U; ++u) dst[i + u * step] = v[u];
+        }
+        for (; i < n16; i += step) dst[i] = __ldg(src + i);
+        done = (n16 << 4) / (int)sizeof(T);
+    }
+    for (int i = done + (int)threadIdx.x; i < n; i += (int)blockDim.x) s_tab[i] = g_tab[i];
     __syncthreads();
 }
 
