@@ -44,6 +44,8 @@ WORKLOADS = {
     "scenB_P4": lambda: workloads.scenario_b("P4"),
     "scenB_m3_exp1": lambda: workloads.scenario_b("m3_exp1"),
     "scenB_m3_exp3": lambda: workloads.scenario_b("m3_exp3"),
+    # the paper's largest Scenario A setting (m = 5, L = 2, FIFO, C_w = 7)
+    "scenA_m5L2": lambda: workloads.scenario_a(5, 2, 7.0, workloads.FIFO),
 }
 TOL = 1e-4
 MAX_ITERS = 5_000

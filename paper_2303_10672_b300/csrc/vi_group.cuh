@@ -250,6 +250,15 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                     for (int xi = 0; xi < XW; ++xi) acc(xi) = (R == 0) ? g0 : s_F[xi] * g0;
                 }
                 const uint32_t atop = (uint32_t)a * P.w_top;
+                // L >= 2 with the shared path: the tail value's index is known now, so its
+                // load is issued before the chunks and is consumed after them (measured on
+                // B300: 2% faster at 11 x per lane, 0.6% slower at 21, which has no
+                // registers to spare)
+                constexpr bool early_tail = PAIR && LPIPE && XW <= 12;
+                float2 rawR = make_float2(0.f, 0.f);
+                if constexpr (early_tail) {
+                    if (shared_fifo && R >= 1 && x0 + R <= dmax) rawR = __ldg(V2 + tail_rel + atop);
+                }
                 int ecur = 0;
                 // index of g(e); e never decreases between calls (the walker moves forward)
                 auto index_of = [&](int e) -> uint32_t {
@@ -351,7 +360,11 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                     }
                 }
                 if (R >= 1 && x0 + R <= dmax) {
-                    const float gR = value_of((preclamped && shared_fifo) ? tail_rel + atop : index_of(R));
+                    float gR;
+                    if constexpr (early_tail)
+                        gR = shared_fifo ? pair_diff(rawR, ref) : value_of(index_of(R));
+                    else
+                        gR = value_of((preclamped && shared_fifo) ? tail_rel + atop : index_of(R));
                     const float *s_tx = s_tab + P.off_tail + x0 + R;
 #pragma unroll
                     for (int xi = 0; xi < XW; ++xi) acc(xi) = fmaf(s_tx[xi], gR, acc(xi));
