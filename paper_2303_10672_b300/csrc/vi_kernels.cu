@@ -548,32 +548,54 @@ __device__ __forceinline__ int draw_demand(uint32_t w, const unsigned long long 
     return d;
 }
 
+// The cost terms c n of a period's reward, n a unit count: the products
+// __dmul_rn(c, n) for n < kCostTab read from a table in shared memory (the same
+// doubles, without an FP64 multiply and conversion per term), computed above it
+constexpr int kCostTab = 256;
+struct CostTab {
+    const double *t;          // [product][cost][n], in shared memory
+    const RollParams *rp;
+    int len;                  // kCostTab, or 0: always multiply
+    __device__ __forceinline__ double operator()(int j, int k, int n) const {
+        return (unsigned)n < (unsigned)len ? t[(j * 5 + k) * kCostTab + n] : __dmul_rn(rp->cost[j][k], (double)n);
+    }
+};
+
+__device__ __forceinline__ void fill_cost_tab(double *t, const RollParams &rp, int n_products) {
+    for (int i = threadIdx.x; i < n_products * 5 * kCostTab; i += blockDim.x) {
+        const int jk = i / kCostTab;
+        t[i] = __dmul_rn(rp.cost[jk / 5][jk % 5], (double)(i - jk * kCostTab));
+    }
+}
+
 // one period of a single product: reward (FP64, unfused, in the oracle's order) and outcome
-__device__ __forceinline__ double single_period(const ProdParams &P1, int lifo, const RollParams &rp, uint32_t s, int a,
+__device__ __forceinline__ double single_period(const ProdParams &P1, int lifo, const CostTab &ct, uint32_t s, int a,
                                                 int d1, RollOut &o) {
     o = roll_product(P1, lifo, s, a, d1);
     double rew = 0.0;
-    rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][0], (double)a));
-    rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][1], (double)o.carried));
-    rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][2], (double)o.shortage));
-    rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][3], (double)o.wasted));
-    rew = __dadd_rn(rew, __dmul_rn(rp.cost[0][4], (double)o.issued));
+    rew = __dsub_rn(rew, ct(0, 0, a));
+    rew = __dsub_rn(rew, ct(0, 1, o.carried));
+    rew = __dsub_rn(rew, ct(0, 2, o.shortage));
+    rew = __dsub_rn(rew, ct(0, 3, o.wasted));
+    rew = __dadd_rn(rew, ct(0, 4, o.issued));
     return rew;
 }
 
-// per-product KPI sums of one rollout (integers, so FP64 sums are exact)
+// per-product KPI sums of one rollout; unit counts summed as integers: exactly the FP64 running sums of the same counts
+// (every partial sum is an integer below 2^53), without an FP64 add per period
 struct KpiSums {
-    double dem[2], served[2], was[2], arr[2], car[2];
+    long long dem[2], served[2], was[2], arr[2], car[2];
     __device__ __forceinline__ void init() {
-        for (int j = 0; j < 2; ++j) dem[j] = served[j] = was[j] = arr[j] = car[j] = 0.0;
+        for (int j = 0; j < 2; ++j) dem[j] = served[j] = was[j] = arr[j] = car[j] = 0;
     }
     // service % (product 1 counts its shortfall met by substitution as served),
     // wastage % of the units received, mean units carried
     __device__ __forceinline__ void finish(int horizon, double *out6) const {
         for (int j = 0; j < 2; ++j) {
-            out6[3 * j + 0] = dem[j] > 0.0 ? __ddiv_rn(__dmul_rn(100.0, served[j]), dem[j]) : 100.0;
-            out6[3 * j + 1] = arr[j] > 0.0 ? __ddiv_rn(__dmul_rn(100.0, was[j]), arr[j]) : 0.0;
-            out6[3 * j + 2] = horizon > 0 ? __ddiv_rn(car[j], (double)horizon) : 0.0;
+            const double d = (double)dem[j], sv = (double)served[j], w = (double)was[j], a = (double)arr[j];
+            out6[3 * j + 0] = d > 0.0 ? __ddiv_rn(__dmul_rn(100.0, sv), d) : 100.0;
+            out6[3 * j + 1] = a > 0.0 ? __ddiv_rn(__dmul_rn(100.0, w), a) : 0.0;
+            out6[3 * j + 2] = horizon > 0 ? __ddiv_rn((double)car[j], (double)horizon) : 0.0;
         }
     }
 };
@@ -581,33 +603,37 @@ struct KpiSums {
 __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *policy, double *returns, double *kpis,
                                double *kpis_prod, int32_t *traj) {
     __shared__ unsigned long long s_thr[2][kMaxRollDmax + 1];
+    __shared__ double s_ct[2 * 5 * kCostTab];
     for (int i = threadIdx.x; i <= kMaxRollDmax; i += blockDim.x) {
         s_thr[0][i] = rp.thr[0][i];
         s_thr[1][i] = rp.thr[1][i];
     }
+    fill_cost_tab(s_ct, rp, kp.n_products);
     __syncthreads();
+    const CostTab ct{s_ct, &rp, kCostTab};
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rp.n_rollouts) return;
     const int lifo = kp.issuing;
     const uint32_t k0 = (uint32_t)(rp.seed & 0xffffffffull), k1 = (uint32_t)(rp.seed >> 32);
     uint32_t s = 0;
     double ret = 0.0, disc = 1.0;
-    double dem = 0.0, iss = 0.0, was = 0.0, arr = 0.0, car = 0.0;
+    long long dem = 0, iss = 0, was = 0, arr = 0, car = 0;
     KpiSums ks;
     ks.init();
     const ProdParams &P1 = kp.p[0];
     for (int t = 0; t < rp.warmup + rp.horizon; ++t) {
+        // the policy load is issued first: the random numbers do not depend on it
+        const int a = __ldg(policy + s);
         uint32_t w[4];
         philox4x32_10((uint32_t)t, (uint32_t)r, 0u, 0u, k0, k1, w);
-        const int a = policy[s];
         double rew = 0.0;
-        double t_dem, t_iss, t_was, t_arr, t_car;
+        int t_dem, t_iss, t_was, t_arr, t_car;
         int p_dem[2] = {0, 0}, p_srv[2] = {0, 0}, p_was[2] = {0, 0}, p_arr[2] = {0, 0}, p_car[2] = {0, 0};
         uint32_t s_next;
         if (kp.n_products == 1) {
             const int d1 = draw_demand(w[0], s_thr[0], P1.dmax);
             RollOut o;
-            rew = single_period(P1, lifo, rp, s, a, d1, o);
+            rew = single_period(P1, lifo, ct, s, a, d1, o);
             s_next = o.s_next;
             t_dem = d1;
             t_iss = o.issued;
@@ -632,16 +658,16 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
             const int own2 = min(d2, o2.total);
             const int short1 = o1.shortage - (o2.issued - own2);
             const int short2 = max(d2 - o2.total, 0);
-            rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][0], (double)a1));
-            rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][1], (double)o1.carried));
-            rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][2], (double)short1));
-            rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][3], (double)o1.wasted));
-            rew = __dadd_rn(rew, __dmul_rn(rp.cost[0][4], (double)o1.issued));
-            rew = __dsub_rn(rew, __dmul_rn(rp.cost[1][0], (double)a2));
-            rew = __dsub_rn(rew, __dmul_rn(rp.cost[1][1], (double)o2.carried));
-            rew = __dsub_rn(rew, __dmul_rn(rp.cost[1][2], (double)short2));
-            rew = __dsub_rn(rew, __dmul_rn(rp.cost[1][3], (double)o2.wasted));
-            rew = __dadd_rn(rew, __dmul_rn(rp.cost[1][4], (double)o2.issued));
+            rew = __dsub_rn(rew, ct(0, 0, a1));
+            rew = __dsub_rn(rew, ct(0, 1, o1.carried));
+            rew = __dsub_rn(rew, ct(0, 2, short1));
+            rew = __dsub_rn(rew, ct(0, 3, o1.wasted));
+            rew = __dadd_rn(rew, ct(0, 4, o1.issued));
+            rew = __dsub_rn(rew, ct(1, 0, a2));
+            rew = __dsub_rn(rew, ct(1, 1, o2.carried));
+            rew = __dsub_rn(rew, ct(1, 2, short2));
+            rew = __dsub_rn(rew, ct(1, 3, o2.wasted));
+            rew = __dadd_rn(rew, ct(1, 4, o2.issued));
             s_next = o1.s_next + S1 * o2.s_next;
             t_dem = d1 + d2;
             t_iss = o1.issued + o2.issued;
@@ -664,26 +690,27 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
             if (traj) traj[(size_t)r * rp.horizon + (t - rp.warmup)] = (int32_t)s;
             ret = __dadd_rn(ret, __dmul_rn(disc, rew));
             disc = __dmul_rn(disc, kp.gamma);
-            dem = __dadd_rn(dem, t_dem);
-            iss = __dadd_rn(iss, t_iss);
-            was = __dadd_rn(was, t_was);
-            arr = __dadd_rn(arr, t_arr);
-            car = __dadd_rn(car, t_car);
+            dem += t_dem;
+            iss += t_iss;
+            was += t_was;
+            arr += t_arr;
+            car += t_car;
             for (int j = 0; j < 2; ++j) {
-                ks.dem[j] += (double)p_dem[j];
-                ks.served[j] += (double)p_srv[j];
-                ks.was[j] += (double)p_was[j];
-                ks.arr[j] += (double)p_arr[j];
-                ks.car[j] += (double)p_car[j];
+                ks.dem[j] += p_dem[j];
+                ks.served[j] += p_srv[j];
+                ks.was[j] += p_was[j];
+                ks.arr[j] += p_arr[j];
+                ks.car[j] += p_car[j];
             }
         }
         s = s_next;
     }
     returns[r] = ret;
     if (kpis) {
-        kpis[3 * r + 0] = dem > 0.0 ? __ddiv_rn(__dmul_rn(100.0, iss), dem) : 100.0;
-        kpis[3 * r + 1] = arr > 0.0 ? __ddiv_rn(__dmul_rn(100.0, was), arr) : 0.0;
-        kpis[3 * r + 2] = rp.horizon > 0 ? __ddiv_rn(car, (double)rp.horizon) : 0.0;
+        const double fd = (double)dem, fi = (double)iss, fw = (double)was, fa = (double)arr;
+        kpis[3 * r + 0] = fd > 0.0 ? __ddiv_rn(__dmul_rn(100.0, fi), fd) : 100.0;
+        kpis[3 * r + 1] = fa > 0.0 ? __ddiv_rn(__dmul_rn(100.0, fw), fa) : 0.0;
+        kpis[3 * r + 2] = rp.horizon > 0 ? __ddiv_rn((double)car, (double)rp.horizon) : 0.0;
     }
     if (kpis_prod) ks.finish(rp.horizon, kpis_prod + 6 * (size_t)r);
 }
@@ -697,6 +724,9 @@ __global__ void basestock_kernel(KernelParams kp, RollParams rp, int s_lo, int n
     __shared__ unsigned long long s_thr[kMaxRollDmax + 1];
     for (int i = threadIdx.x; i <= kMaxRollDmax; i += blockDim.x) s_thr[i] = rp.thr[0][i];
     __syncthreads();
+    // thousands of threads per SM: FP64 multiplies are not the bound here and the
+    // table measured slower (1.4%), so the costs are multiplied
+    const CostTab ct{nullptr, &rp, 0};
     const long long t_id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t_id >= (long long)n_S * rp.n_rollouts) return;
     const int S = s_lo + (int)(t_id / rp.n_rollouts);
@@ -719,7 +749,7 @@ __global__ void basestock_kernel(KernelParams kp, RollParams rp, int s_lo, int n
         const int a = min(max(S - stock, 0), P1.Q);
         const int d1 = draw_demand(w[0], s_thr, P1.dmax);
         RollOut o;
-        const double rew = single_period(P1, lifo, rp, s, a, d1, o);
+        const double rew = single_period(P1, lifo, ct, s, a, d1, o);
         if (t >= rp.warmup) {
             ret = __dadd_rn(ret, __dmul_rn(disc, rew));
             disc = __dmul_rn(disc, kp.gamma);
@@ -818,11 +848,14 @@ __device__ __forceinline__ int mbs_order(const ProdParams &P, const StockVec &v,
 
 __global__ void mbs_kernel(KernelParams kp, RollParams rp, MbsParams mp, double *returns, double *kpis_prod) {
     __shared__ unsigned long long s_thr[2][kMaxRollDmax + 1];
+    __shared__ double s_ct[2 * 5 * kCostTab];
     for (int i = threadIdx.x; i <= kMaxRollDmax; i += blockDim.x) {
         s_thr[0][i] = rp.thr[0][i];
         s_thr[1][i] = rp.thr[1][i];
     }
+    fill_cost_tab(s_ct, rp, 2);
     __syncthreads();
+    const CostTab ct{s_ct, &rp, kCostTab};
     const long long t_id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t_id >= (long long)mp.n_pairs * rp.n_rollouts) return;
     const int pair = (int)(t_id / rp.n_rollouts);
@@ -860,32 +893,32 @@ __global__ void mbs_kernel(KernelParams kp, RollParams rp, MbsParams mp, double 
             short2 = max(d2 - o2.total, 0);
         }
         double rew = 0.0;
-        rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][0], (double)q1));
-        rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][1], (double)o1.carried));
-        rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][2], (double)short1));
-        rew = __dsub_rn(rew, __dmul_rn(rp.cost[0][3], (double)o1.wasted));
-        rew = __dadd_rn(rew, __dmul_rn(rp.cost[0][4], (double)o1.issued));
+        rew = __dsub_rn(rew, ct(0, 0, q1));
+        rew = __dsub_rn(rew, ct(0, 1, o1.carried));
+        rew = __dsub_rn(rew, ct(0, 2, short1));
+        rew = __dsub_rn(rew, ct(0, 3, o1.wasted));
+        rew = __dadd_rn(rew, ct(0, 4, o1.issued));
         if (np == 2) {
-            rew = __dsub_rn(rew, __dmul_rn(rp.cost[1][0], (double)q2));
-            rew = __dsub_rn(rew, __dmul_rn(rp.cost[1][1], (double)o2.carried));
-            rew = __dsub_rn(rew, __dmul_rn(rp.cost[1][2], (double)short2));
-            rew = __dsub_rn(rew, __dmul_rn(rp.cost[1][3], (double)o2.wasted));
-            rew = __dadd_rn(rew, __dmul_rn(rp.cost[1][4], (double)o2.issued));
+            rew = __dsub_rn(rew, ct(1, 0, q2));
+            rew = __dsub_rn(rew, ct(1, 1, o2.carried));
+            rew = __dsub_rn(rew, ct(1, 2, short2));
+            rew = __dsub_rn(rew, ct(1, 3, o2.wasted));
+            rew = __dadd_rn(rew, ct(1, 4, o2.issued));
         }
         if (t >= rp.warmup) {
             ret = __dadd_rn(ret, __dmul_rn(disc, rew));
             disc = __dmul_rn(disc, kp.gamma);
-            ks.dem[0] += (double)d1;
-            ks.served[0] += (double)(o1.issued + sub);
-            ks.was[0] += (double)o1.wasted;
-            ks.arr[0] += (double)o1.arrived;
-            ks.car[0] += (double)o1.carried;
+            ks.dem[0] += d1;
+            ks.served[0] += o1.issued + sub;
+            ks.was[0] += o1.wasted;
+            ks.arr[0] += o1.arrived;
+            ks.car[0] += o1.carried;
             if (np == 2) {
-                ks.dem[1] += (double)d2;
-                ks.served[1] += (double)(o2.issued - sub);
-                ks.was[1] += (double)o2.wasted;
-                ks.arr[1] += (double)o2.arrived;
-                ks.car[1] += (double)o2.carried;
+                ks.dem[1] += d2;
+                ks.served[1] += o2.issued - sub;
+                ks.was[1] += o2.wasted;
+                ks.arr[1] += o2.arrived;
+                ks.car[1] += o2.carried;
             }
         }
     }

@@ -281,7 +281,8 @@ __global__ void pc_rollout_kernel(KernelParams kp, PcRollParams rp, const uint8_
     const uint32_t k0 = (uint32_t)(rp.seed & 0xffffffffull), k1 = (uint32_t)(rp.seed >> 32);
     uint32_t s = 0;
     double ret = 0.0, disc = 1.0;
-    double dem = 0.0, iss = 0.0, was = 0.0, acc = 0.0, held = 0.0;
+    // unit counts summed as integers: exactly the FP64 running sums of the same counts
+    long long dem = 0, iss = 0, was = 0, acc = 0, held = 0;
     for (int t = 0; t < rp.warmup + rp.horizon; ++t) {
         uint32_t w[4];
         philox4x32_10((uint32_t)t, (uint32_t)r, 0u, 0u, k0, k1, w);
@@ -339,19 +340,20 @@ __global__ void pc_rollout_kernel(KernelParams kp, PcRollParams rp, const uint8_
             if (traj) traj[(size_t)r * rp.horizon + (t - rp.warmup)] = (int32_t)s;
             ret = __dadd_rn(ret, __dmul_rn(disc, rew));
             disc = __dmul_rn(disc, kp.gamma);
-            dem += (double)d;
-            iss += (double)min(d, T);
-            was += (double)wasted;
-            acc += (double)accepted;
-            held += (double)left;
+            dem += d;
+            iss += min(d, T);
+            was += wasted;
+            acc += accepted;
+            held += left;
         }
         s = ((tau + 1) % 7) * P.nS + idx;
     }
     returns[r] = ret;
     if (kpis) {
-        kpis[3 * r + 0] = dem > 0.0 ? __ddiv_rn(__dmul_rn(100.0, iss), dem) : 100.0;
-        kpis[3 * r + 1] = acc > 0.0 ? __ddiv_rn(__dmul_rn(100.0, was), acc) : 0.0;
-        kpis[3 * r + 2] = rp.horizon > 0 ? __ddiv_rn(held, (double)rp.horizon) : 0.0;
+        const double fd = (double)dem, fi = (double)iss, fw = (double)was, fa = (double)acc;
+        kpis[3 * r + 0] = fd > 0.0 ? __ddiv_rn(__dmul_rn(100.0, fi), fd) : 100.0;
+        kpis[3 * r + 1] = fa > 0.0 ? __ddiv_rn(__dmul_rn(100.0, fw), fa) : 0.0;
+        kpis[3 * r + 2] = rp.horizon > 0 ? __ddiv_rn((double)held, (double)rp.horizon) : 0.0;
     }
 }
 
