@@ -91,3 +91,50 @@ def test_pinned_host_buffers_receive_the_same_result(case, max_iters):
     np.testing.assert_array_equal(a[1], b[1])
     vals = a[0].view(np.float64) if prec == "fp64" else a[0]   # NaN sentinels left if unwritten
     assert np.isfinite(vals).all() and (a[1] != 255).all()
+
+
+def test_pinned_values_without_a_policy_and_mixed_buffers():
+    """Pinned V with no policy buffer (the sweep writes V only), and pinned V with a
+    pageable policy (copied after the sweep): the same V and policy as pageable."""
+    inst = HOST_CASES[0][1]
+    Vr, pr, ir = _host_solve(inst, "fp32", False, 10_000)
+    h = create(inst, "fp32")
+    n = vi.vi_problem_sizes(h)["n_states"]
+    V = torch.empty(2 * n, dtype=torch.float32).pin_memory().numpy()
+    V[:] = np.nan
+    info = vi.vi_solve_host(h, 1e-4, 10_000, V, None)
+    assert info["iters"] == ir
+    np.testing.assert_array_equal(V.view(np.uint32), Vr.view(np.uint32))
+    V[:] = np.nan
+    pol = np.full(n, 255, np.uint8)
+    vi.vi_solve_host(h, 1e-4, 10_000, V, pol)
+    vi.vi_problem_destroy(h)
+    np.testing.assert_array_equal(V.view(np.uint32), Vr.view(np.uint32))
+    np.testing.assert_array_equal(pol, pr)
+
+
+def test_pinned_host_buffers_periodic_problem():
+    """Scenario C (FP64, periodic test): pinned and pageable host buffers agree."""
+    inst = workloads.scenario_c(3, 1)
+
+    def run(pinned):
+        d, keep = vi.make_periodic_desc(inst.m, inst.Q, inst.pmf, inst.c0, inst.c1, inst.cost, inst.gamma,
+                                        vi.VI_STOP_PERIODIC)
+        h = vi.vi_problem_create_periodic(d)
+        n = vi.vi_problem_sizes(h)["n_states"]
+        if pinned:
+            V = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+            pol = torch.empty(n, dtype=torch.uint8).pin_memory().numpy()
+        else:
+            V = np.empty(n, np.float64)
+            pol = np.empty(n, np.uint8)
+        V[:] = np.nan
+        info = vi.vi_solve_host(h, 1e-4, 2000, V, pol)
+        vi.vi_problem_destroy(h)
+        return V.copy(), pol.copy(), info["iters"]
+
+    a, b = run(True), run(False)
+    assert a[2] == b[2]
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    assert np.isfinite(a[0]).all()
