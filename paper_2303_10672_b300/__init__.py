@@ -160,6 +160,32 @@ def _addr(x) -> Optional[int]:
     raise TypeError(f"cannot take the address of {type(x)}")
 
 
+def _nbytes(x) -> Optional[int]:
+    """Bytes a tensor or numpy array holds (None for raw addresses, which cannot be checked)."""
+    if hasattr(x, "element_size") and hasattr(x, "numel"):
+        return x.element_size() * x.numel()
+    if isinstance(x, np.ndarray):
+        return x.nbytes
+    return None
+
+
+def _check_sizes(h: int, where: str, values=(), policies=()) -> None:
+    """The C ABI takes plain pointers: refuse a value buffer smaller than |S| values of
+    the handle's layout, or a policy buffer smaller than |S| bytes, before any kernel
+    writes past it."""
+    n = C.c_uint64()
+    vb = C.c_int()
+    _check(lib().vi_problem_sizes(h, C.byref(n), None, None, C.byref(vb)), "vi_problem_sizes")
+    for x in values:
+        nb = _nbytes(x) if x is not None else None
+        if nb is not None and nb < n.value * vb.value:
+            raise ValueError(f"{where}: value buffer of {nb} bytes, the problem needs {n.value} x {vb.value}")
+    for x in policies:
+        nb = _nbytes(x) if x is not None else None
+        if nb is not None and nb < n.value:
+            raise ValueError(f"{where}: policy buffer of {nb} bytes, the problem needs {n.value}")
+
+
 def _stream(s) -> Optional[int]:
     if s is None:
         try:
@@ -269,6 +295,7 @@ def vi_problem_set_option(h: int, option: int, value: int) -> None:
 
 def vi_solve(h: int, tol: float, max_iters: int, V, policy=None, stream=None, flags: int = 0,
              offset: float = 0.0) -> dict:
+    _check_sizes(h, "vi_solve", (V,), (policy,))
     info = vi_solve_info()
     info.offset = offset
     st = lib().vi_solve(h, tol, max_iters, _addr(V), _addr(policy), _stream(stream), flags, C.byref(info))
@@ -278,6 +305,7 @@ def vi_solve(h: int, tol: float, max_iters: int, V, policy=None, stream=None, fl
 
 def vi_solve_host(h: int, tol: float, max_iters: int, V_host: np.ndarray, policy_host: Optional[np.ndarray],
                   flags: int = 0, offset: float = 0.0) -> dict:
+    _check_sizes(h, "vi_solve_host", (V_host,), (policy_host,))
     info = vi_solve_info()
     info.offset = offset
     st = lib().vi_solve_host(h, tol, max_iters, _addr(V_host), _addr(policy_host), flags, C.byref(info))
@@ -286,6 +314,7 @@ def vi_solve_host(h: int, tol: float, max_iters: int, V_host: np.ndarray, policy
 
 
 def vi_backup(h: int, V_in, V_out, policy=None, stream=None, stats: bool = True):
+    _check_sizes(h, "vi_backup", (V_in, V_out), (policy,))
     ds = (C.c_double * 2)()
     _check(lib().vi_backup(h, _addr(V_in), _addr(V_out), _addr(policy), _stream(stream),
                            ds if stats else None), "vi_backup")

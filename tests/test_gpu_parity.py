@@ -331,9 +331,18 @@ def test_invalid_arguments():
     h = vi.vi_problem_create(2, 1, 3, (1, 1, 1, 1, 0), pmf, 0.9, 0)
     try:
         with pytest.raises(vi.ViError):
-            vi.vi_solve(h, -1.0, 10, torch.zeros(4, device="cuda"))
+            vi.vi_solve(h, -1.0, 10, torch.zeros(8, device="cuda"))
         with pytest.raises(vi.ViError):
             vi.vi_solve(h, 1e-4, 10, None)
+        # 4 states need 4 float pairs: a buffer of 4 floats is refused before any kernel runs
+        with pytest.raises(ValueError):
+            vi.vi_solve(h, 1e-4, 10, torch.zeros(4, device="cuda"))
+        with pytest.raises(ValueError):
+            vi.vi_solve(h, 1e-4, 10, torch.zeros(8, device="cuda"), torch.zeros(3, dtype=torch.uint8, device="cuda"))
+        with pytest.raises(ValueError):
+            vi.vi_backup(h, torch.zeros(8, device="cuda"), torch.zeros(6, device="cuda"))
+        with pytest.raises(ValueError):
+            vi.vi_solve_host(h, 1e-4, 10, np.zeros(7, np.float32), None)
         with pytest.raises(vi.ViError):
             vi.vi_problem_set_option(h, vi.VI_OPT_KERNEL, 99)
     finally:
