@@ -186,6 +186,13 @@ def _check_sizes(h: int, where: str, values=(), policies=()) -> None:
             raise ValueError(f"{where}: policy buffer of {nb} bytes, the problem needs {n.value}")
 
 
+def _need(x, nbytes: int, where: str, what: str) -> None:
+    """Refuse a buffer that holds fewer than `nbytes` (raw addresses are not checked)."""
+    nb = _nbytes(x) if x is not None else None
+    if nb is not None and nb < nbytes:
+        raise ValueError(f"{where}: {what} buffer of {nb} bytes, the call needs {nbytes}")
+
+
 def _stream(s) -> Optional[int]:
     if s is None:
         try:
@@ -335,6 +342,8 @@ def vi_backup_noalloc(m: int, L: int, Q: int, cost: Sequence[float], pmf: np.nda
 
 
 def vi_policy_eval(h: int, policy, V, tol: float, max_iters: int, stream=None):
+    _check_sizes(h, "vi_policy_eval", (), (policy,))
+    _need(V, 8 * vi_problem_sizes(h)["n_states"], "vi_policy_eval", "FP64 value")
     it, dl = C.c_int(), C.c_double()
     st = lib().vi_policy_eval(h, _addr(policy), _addr(V), tol, max_iters, _stream(stream), C.byref(it),
                               C.byref(dl))
@@ -343,17 +352,29 @@ def vi_policy_eval(h: int, policy, V, tol: float, max_iters: int, stream=None):
 
 
 def vi_next_states(h: int, states, n: int, out, stream=None) -> None:
+    _need(states, 4 * n, "vi_next_states", "state")
+    _need(out, 4 * n, "vi_next_states", "output")
     _check(lib().vi_next_states(h, _addr(states), n, _addr(out), _stream(stream)), "vi_next_states")
+
+
+def _check_rollout_bufs(h, where, policy, n, horizon, returns, kpis, kpis_prod, traj) -> None:
+    _check_sizes(h, where, (), (policy,))
+    _need(returns, 8 * n, where, "returns")
+    _need(kpis, 24 * n, where, "KPI")
+    _need(kpis_prod, 48 * n, where, "per-product KPI")
+    _need(traj, 4 * n * horizon, where, "trajectory")
 
 
 def vi_simulate(h: int, policy, n_rollouts: int, horizon: int, warmup: int, seed: int, returns, kpis=None,
                 traj=None, stream=None) -> None:
+    _check_rollout_bufs(h, "vi_simulate", policy, n_rollouts, horizon, returns, kpis, None, traj)
     _check(lib().vi_simulate(h, _addr(policy), n_rollouts, horizon, warmup, C.c_uint64(seed), _addr(returns),
                              _addr(kpis), _addr(traj), _stream(stream)), "vi_simulate")
 
 
 def vi_simulate_ex(h: int, policy, n_rollouts: int, horizon: int, warmup: int, seed: int, returns, kpis=None,
                    kpis_prod=None, traj=None, stream=None) -> None:
+    _check_rollout_bufs(h, "vi_simulate_ex", policy, n_rollouts, horizon, returns, kpis, kpis_prod, traj)
     _check(lib().vi_simulate_ex(h, _addr(policy), n_rollouts, horizon, warmup, C.c_uint64(seed), _addr(returns),
                                 _addr(kpis), _addr(kpis_prod), _addr(traj), _stream(stream)), "vi_simulate_ex")
 
@@ -368,6 +389,8 @@ def vi_mbs_search(h: int, S_lo, S_hi, mu, cap: bool, n_rollouts: int, horizon: i
     hi = (C.c_int * 2)(*(list(S_hi) + [0] * (2 - len(S_hi))))
     mv = (C.c_int * 2)(*(list(mu) + [0] * (2 - len(mu))))
     n_pairs = (hi[0] - lo[0] + 1) * ((hi[1] - lo[1] + 1) if len(S_lo) == 2 else 1)
+    _need(returns, 8 * max(n_pairs, 0) * n_rollouts, "vi_mbs_search", "returns")
+    _need(kpis_prod, 48 * max(n_pairs, 0) * n_rollouts, "vi_mbs_search", "per-product KPI")
     if not means:
         _check(lib().vi_mbs_search(h, lo, hi, mv, int(bool(cap)), n_rollouts, horizon, warmup, C.c_uint64(seed),
                                    _addr(returns), _addr(kpis_prod), None, None, _stream(stream)), "vi_mbs_search")
@@ -391,6 +414,7 @@ def vi_basestock_search(h: int, s_lo: int, s_hi: int, n_rollouts: int, horizon: 
     """Mean return per order-up-to level S in s_lo..s_hi and the best S; per-rollout
     returns land in the device buffer `returns` (row S - s_lo)."""
     n_S = s_hi - s_lo + 1
+    _need(returns, 8 * max(n_S, 0) * n_rollouts, "vi_basestock_search", "returns")
     means = (C.c_double * n_S)()
     best = C.c_int()
     _check(lib().vi_basestock_search(h, s_lo, s_hi, n_rollouts, horizon, warmup, C.c_uint64(seed), _addr(returns),
