@@ -76,12 +76,15 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
     int Rrest = 0;   // units in the rest slots (without the order when L = 1)
     uint32_t tail_rel = 0;   // L >= 2, shared FIFO path: next-state index after all R units (without the order)
 
-    float bh[XW], bl[XW];
+    // best (hi, lo) per x, in pairs of x like the accumulators (packed arithmetic)
+    float2 bh2[(XW + 1) / 2], bl2[(XW + 1) / 2];
+    auto bhr = [&](int xi) -> float & { return (xi & 1) ? bh2[xi >> 1].y : bh2[xi >> 1].x; };
+    auto blr = [&](int xi) -> float & { return (xi & 1) ? bl2[xi >> 1].y : bl2[xi >> 1].x; };
     uint32_t argp[(XW + 3) / 4];   // best order per x, one byte each (G <= 256)
 #pragma unroll
-    for (int xi = 0; xi < XW; ++xi) {
-        bh[xi] = -INFINITY;
-        bl[xi] = 0.f;
+    for (int i = 0; i < (XW + 1) / 2; ++i) {
+        bh2[i] = make_float2(-INFINITY, -INFINITY);
+        bl2[i] = make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int i = 0; i < (XW + 3) / 4; ++i) argp[i] = 0u;
@@ -89,8 +92,8 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
     // argp[xi >> 2] holds the order.
     auto take = [&](int xi, bool up, float h, float l, int a) {
         constexpr unsigned sel[4] = {0x3214u, 0x3240u, 0x3410u, 0x4210u};
-        bh[xi] = up ? h : bh[xi];
-        if (PAIR) bl[xi] = up ? l : bl[xi];
+        bhr(xi) = up ? h : bhr(xi);
+        if (PAIR) blr(xi) = up ? l : blr(xi);
         const unsigned na = __byte_perm(argp[xi >> 2], (unsigned)a, sel[xi & 3]);
         argp[xi >> 2] = up ? na : argp[xi >> 2];
     };
@@ -198,7 +201,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
 #pragma unroll
                     for (int xi = 0; xi < XW; ++xi) {
                         const float key = __fadd_rn(ks, rt[xi]);
-                        take(xi, key > bh[xi], key, 0.f, a);
+                        take(xi, key > bhr(xi), key, 0.f, a);
                     }
                 }
             }
@@ -295,7 +298,16 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                         float2 raw[KW];
 #pragma unroll
                         for (int j = 0; j < KW; ++j) raw[j] = __ldg(V2 + idx[j]);
-                        if (preclamped && shared_fifo) {
+                        if (PACKED && preclamped && shared_fifo) {
+                            // (raw - ref) per half as one packed fma(ref, -1, raw), then the
+                            // halves added: the same rounding as pair_diff
+                            const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+                            for (int j = 0; j < KW; ++j) {
+                                const float2 d = __ffma2_rn(ref, m1, raw[j]);
+                                g[j] = __fadd_rn(d.x, d.y);
+                            }
+                        } else if (preclamped && shared_fifo) {
 #pragma unroll
                             for (int j = 0; j < KW; ++j) g[j] = pair_diff(raw[j], ref);
                         } else {
@@ -422,18 +434,33 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                 float Bh, Bl;
                 action_base(gam, ref, R0, __fmul_rn(-c_o, (float)a), Bh, Bl);
                 const float ql = __fmaf_rn(gam, acc(0), Bl);
-                const float diff = __fadd_rn(__fsub_rn(Bh, bh[0]), __fsub_rn(ql, bl[0]));
+                const float diff = __fadd_rn(__fsub_rn(Bh, bhr(0)), __fsub_rn(ql, blr(0)));
                 take(0, diff > 0.f, Bh, ql, a);
             } else if (PAIR && rt_common) {
                 // L >= 2: R does not depend on the order, so RT(x, R) is common to all
                 // orders and is added once per x after the max
                 float Bh, Bl;
                 action_base(gam, ref, R0, __fmul_rn(-c_o, (float)a), Bh, Bl);
+                if constexpr (XW >= 16) {
+                    // two x per packed instruction; a - b as fma(b, -1, a), rounded as the
+                    // subtraction
+                    const float2 g2 = make_float2(gam, gam), Bh2 = make_float2(Bh, Bh), Bl2 = make_float2(Bl, Bl);
+                    const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
-                for (int xi = 0; xi < XW; ++xi) {
-                    const float ql = __fmaf_rn(gam, acc(xi), Bl);
-                    const float diff = __fadd_rn(__fsub_rn(Bh, bh[xi]), __fsub_rn(ql, bl[xi]));
-                    take(xi, diff > 0.f, Bh, ql, a);
+                    for (int i = 0; i < (XW + 1) / 2; ++i) {
+                        const float2 ql = __ffma2_rn(g2, acc2[i], Bl2);
+                        const float2 diff =
+                            __fadd2_rn(__ffma2_rn(bh2[i], m1, Bh2), __ffma2_rn(bl2[i], m1, ql));
+                        take(2 * i, diff.x > 0.f, Bh, ql.x, a);
+                        if (2 * i + 1 < XW) take(2 * i + 1, diff.y > 0.f, Bh, ql.y, a);
+                    }
+                } else {
+#pragma unroll
+                    for (int xi = 0; xi < XW; ++xi) {
+                        const float ql = __fmaf_rn(gam, acc(xi), Bl);
+                        const float diff = __fadd_rn(__fsub_rn(Bh, bhr(xi)), __fsub_rn(ql, blr(xi)));
+                        take(xi, diff > 0.f, Bh, ql, a);
+                    }
                 }
             } else if (PAIR && LIFO && key_lifo) {
                 // L = 1, LIFO, values measured from R0: the base of order a is exactly
@@ -446,7 +473,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
 #pragma unroll
                 for (int xi = 0; xi < XW; ++xi) {
                     const float key = __fadd_rn(ks, rt[xi]);
-                    take(xi, key > bh[xi], key, 0.f, a);
+                    take(xi, key > bhr(xi), key, 0.f, a);
                 }
             } else if (PAIR) {
                 float Bh, Bl;
@@ -458,7 +485,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                     float qh = Bh, ql = Bl;
                     pair_add(qh, ql, rt[xi], rtl[xi]);
                     if (!LIFO) ql = __fmaf_rn(gam, acc(xi), ql);
-                    const float diff = __fadd_rn(__fsub_rn(qh, bh[xi]), __fsub_rn(ql, bl[xi]));
+                    const float diff = __fadd_rn(__fsub_rn(qh, bhr(xi)), __fsub_rn(ql, blr(xi)));
                     take(xi, diff > 0.f, qh, ql, a);
                 }
             } else {
@@ -466,17 +493,17 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
 #pragma unroll
                 for (int xi = 0; xi < XW; ++xi) {
                     const float q = fmaf(gam, acc(xi), base + rt[xi]);
-                    take(xi, q > bh[xi], q, 0.f, a);
+                    take(xi, q > bhr(xi), q, 0.f, a);
                 }
             }
         }
-        if (!PAIR && r == 0 && part == 0 && mode == MODE_SWEEP) st->c_next = bh[0];
+        if (!PAIR && r == 0 && part == 0 && mode == MODE_SWEEP) st->c_next = bhr(0);
     }
     if (PAIR && rt_common && LIFO && active) {
 #pragma unroll
         for (int xi = 1; xi < XW; ++xi) {
-            bh[xi] = bh[0];
-            bl[xi] = bl[0];
+            bhr(xi) = bhr(0);
+            blr(xi) = blr(0);
         }
 #pragma unroll
         for (int i = 0; i < (XW + 3) / 4; ++i) argp[i] = (argp[0] & 0xFFu) * 0x01010101u;
@@ -489,8 +516,8 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
             float qh = __fmul_rn(-c_o, (float)a), ql = s_kc[a * kGroupThreads];
             const int R = Rrest + a;
             pair_add(qh, ql, s_RT[R * G + x0 + xi], s_RTlo[R * G + x0 + xi]);
-            bh[xi] = qh;
-            bl[xi] = ql;
+            bhr(xi) = qh;
+            blr(xi) = ql;
         }
     }
     if (PAIR && rt_common && active) {
@@ -498,7 +525,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
         const float *rtl = s_RTlo + Rrest * G + x0;
 #pragma unroll
         for (int xi = 0; xi < XW; ++xi)
-            if (xi < nx) pair_add(bh[xi], bl[xi], rt[xi], rtl[xi]);
+            if (xi < nx) pair_add(bhr(xi), blr(xi), rt[xi], rtl[xi]);
     }
     // stage the block's G * RB contiguous states through shared memory
     if (shared_fifo || shared_lifo) __syncthreads();   // every column is consumed
@@ -508,9 +535,9 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
             if (xi < nx) {
                 const int o = rl * G + x0 + xi;
                 if (PAIR)
-                    ((float2 *)s_out)[o] = active ? pair_finish(gam, R0, bh[xi], bl[xi]) : make_float2(0.f, 0.f);
+                    ((float2 *)s_out)[o] = active ? pair_finish(gam, R0, bhr(xi), blr(xi)) : make_float2(0.f, 0.f);
                 else
-                    s_out[o] = bh[xi];
+                    s_out[o] = bhr(xi);
                 s_pol[o] = (uint8_t)(argp[xi >> 2] >> (8 * (xi & 3)));
             }
         }
