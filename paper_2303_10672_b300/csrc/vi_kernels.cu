@@ -1362,7 +1362,13 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
                 uint32_t off[AB];
 #pragma unroll
                 for (int j = 0; j < AB; ++j) off[j] = (uint32_t)min(a1b + j, P1.G - 1) * P1.w_top;
-                float acc[AB][XW];
+                // accumulators in pairs of x; with 8 x per lane the correlation runs on
+                // packed two-lane FP32 instructions, each lane rounded as the scalar one
+                // (measured on B300: 2.5% faster at 8, 6-12% slower at 16, whose
+                // registers are all taken)
+                constexpr bool PK = XW <= 8;
+                float2 acc2[AB][XW / 2];
+                auto acc = [&](int j, int x) -> float & { return (x & 1) ? acc2[j][x >> 1].y : acc2[j][x >> 1].x; };
                 if (!lifo) {
                     const uint32_t i0 = s_col[tid];
 #pragma unroll
@@ -1371,10 +1377,16 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
 #pragma unroll
                         for (int q = 0; q < XW / 4; ++q) {
                             const float4 f = ((const float4 *)cf0)[q];
-                            acc[j][4 * q + 0] = __fmul_rn(f.x, g);
-                            acc[j][4 * q + 1] = __fmul_rn(f.y, g);
-                            acc[j][4 * q + 2] = __fmul_rn(f.z, g);
-                            acc[j][4 * q + 3] = __fmul_rn(f.w, g);
+                            if constexpr (PK) {
+                                const float2 g2 = make_float2(g, g);
+                                acc2[j][2 * q] = __fmul2_rn(make_float2(f.x, f.y), g2);
+                                acc2[j][2 * q + 1] = __fmul2_rn(make_float2(f.z, f.w), g2);
+                            } else {
+                                acc(j, 4 * q + 0) = __fmul_rn(f.x, g);
+                                acc(j, 4 * q + 1) = __fmul_rn(f.y, g);
+                                acc(j, 4 * q + 2) = __fmul_rn(f.z, g);
+                                acc(j, 4 * q + 3) = __fmul_rn(f.w, g);
+                            }
                         }
                     }
                     for (int e = 1; e <= E1; ++e) {
@@ -1388,10 +1400,16 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
                             const float4 f = pw[q];
 #pragma unroll
                             for (int j = 0; j < AB; ++j) {
-                                acc[j][4 * q + 0] = __fmaf_rn(f.x, g[j], acc[j][4 * q + 0]);
-                                acc[j][4 * q + 1] = __fmaf_rn(f.y, g[j], acc[j][4 * q + 1]);
-                                acc[j][4 * q + 2] = __fmaf_rn(f.z, g[j], acc[j][4 * q + 2]);
-                                acc[j][4 * q + 3] = __fmaf_rn(f.w, g[j], acc[j][4 * q + 3]);
+                                if constexpr (PK) {
+                                    const float2 g2 = make_float2(g[j], g[j]);
+                                    acc2[j][2 * q] = __ffma2_rn(make_float2(f.x, f.y), g2, acc2[j][2 * q]);
+                                    acc2[j][2 * q + 1] = __ffma2_rn(make_float2(f.z, f.w), g2, acc2[j][2 * q + 1]);
+                                } else {
+                                    acc(j, 4 * q + 0) = __fmaf_rn(f.x, g[j], acc(j, 4 * q + 0));
+                                    acc(j, 4 * q + 1) = __fmaf_rn(f.y, g[j], acc(j, 4 * q + 1));
+                                    acc(j, 4 * q + 2) = __fmaf_rn(f.z, g[j], acc(j, 4 * q + 2));
+                                    acc(j, 4 * q + 3) = __fmaf_rn(f.w, g[j], acc(j, 4 * q + 3));
+                                }
                             }
                         }
                     }
@@ -1408,12 +1426,12 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
                             for (int y = 0; y < x0; ++y) cw = __fadd_rn(cw, s_pc[R1 + y]);
 #pragma unroll
                             for (int x = 0; x < XW; ++x) {
-                                acc[j][x] = __fmaf_rn(cw, gR, sum);
+                                acc(j, x) = __fmaf_rn(cw, gR, sum);
                                 cw = __fadd_rn(cw, s_pc[R1 + x0 + x]);
                             }
                         } else {
 #pragma unroll
-                            for (int x = 0; x < XW; ++x) acc[j][x] = sum;
+                            for (int x = 0; x < XW; ++x) acc(j, x) = sum;
                         }
                     }
                 }
@@ -1431,7 +1449,7 @@ twop_sweep_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg
 #pragma unroll
                         for (int x = 0; x < XW; ++x) {
                             const int T1 = x0 + x + R1;   // mixture rows exist for T1 <= min(dmax1, m1 Q1)
-                            const float ax = (T1 < (int)nt) ? __fadd_rn(acc[j][x], mixr[T1]) : acc[j][x];
+                            const float ax = (T1 < (int)nt) ? __fadd_rn(acc(j, x), mixr[T1]) : acc(j, x);
                             const float k = __fmaf_rn(gam, ax, base);
                             const bool up = k > key[x];
                             key[x] = up ? k : key[x];
