@@ -50,6 +50,9 @@ CASES = [
     (2, 3, 2, 5, 3, w.LIFO, 0.9, 0.5),
     (2, 2, 3, 3, 3, w.FIFO, 0.97, 0.7),
     (2, 2, 3, 3, 2, w.LIFO, 1.0, 0.5),
+    # 64 rests of product 1 at one lane each: half a block per product-2 state
+    (3, 2, 2, 7, 3, w.FIFO, 0.95, 0.5),
+    (3, 2, 2, 7, 3, w.LIFO, 0.9, 0.5),
 ]
 
 
@@ -110,6 +113,29 @@ def test_pipeline_kernel_matches_generic_and_sampled_oracle(name):
     P = oracle.Problem(inst)
     rng = np.random.default_rng(11)
     states = np.unique(np.concatenate([[0, n - 1], rng.choice(n, 48, replace=False)]))
+    v_o, _ = P.backup_states(vin, states)
+    assert np.abs(vp[states] - v_o).max() <= V_RTOL * np.abs(v_o).max()
+    assert not policy_mismatches(P, vin, pp[states], states)
+
+
+def test_pipeline_sweep_sampled_oracle_paper_size():
+    """The paper's m = 3 experiment 1 (16.8M states): one backup from V_0 plus
+    three sweeps, at sampled states, against the FP64 oracle."""
+    inst = w.scenario_b("m3_exp1")
+    n = inst.n_states
+    with Handle(inst) as Hp:
+        assert vi.vi_problem_kernel(Hp.h)[0] == vi.VI_KERNEL_GROUP
+        V0 = _expected_revenue_start(Hp)
+        V, _, _ = Hp.solve(0.0, 3, flags=vi.VI_FLAG_WARM_START, V=V0.clone())
+        Vo = _zeros_pair(n)
+        po = torch.empty(n, dtype=torch.uint8, device="cuda")
+        vi.vi_backup(Hp.h, V, Vo, po)
+        torch.cuda.synchronize()
+        vp, pp = Hp.v_abs(Vo, {"offset": 0.0}), po.cpu().numpy()
+        vin = Hp.v_abs(V, {"offset": 0.0})
+    P = oracle.Problem(inst)
+    rng = np.random.default_rng(12)
+    states = np.unique(np.concatenate([[0, n - 1], rng.choice(n, 24, replace=False)]))
     v_o, _ = P.backup_states(vin, states)
     assert np.abs(vp[states] - v_o).max() <= V_RTOL * np.abs(v_o).max()
     assert not policy_mismatches(P, vin, pp[states], states)
