@@ -34,7 +34,7 @@
  *    belongs to the handle and is released by vi_problem_destroy.  Released
  *    device blocks (up to 8 GiB), pinned host blocks (up to 256 MiB) and
  *    streams are kept by the library for the next handle of a similar size;
- *    vi_release_cached_memory returns them to the driver.
+ *    vi_release_cached_memory frees them.
  *  - A handle is not thread-safe; use one handle per host thread.  The solve
  *    server is thread-safe.
  *  - vi_last_error() describes the most recent failure on the calling thread.

@@ -8,7 +8,7 @@
 // tenth of a 4M-state solve when an application creates a handle per problem.
 // Released blocks are therefore kept, up to a cap, and handed to the next
 // request of a close size on the same device.  vi_release_cached_memory()
-// returns all of them to the driver.
+// frees all of them.
 //
 // The caller of a release guarantees that no queued work still uses the block
 // (vi_problem_destroy synchronises the device first, as cudaFree would).

@@ -256,7 +256,7 @@ static void retire_loop(vi_server_s *srv, int k) {
         Request &rq = *job.req;
         vi_status st = VI_OK;
         // device -> pinned staging (a pageable destination would make the copy
-        // synchronous in the driver and hold up the worker's launches), then, for
+        // synchronous and hold up the worker's launches), then, for
         // vi_server_submit_to, a host copy into the caller's buffers on this thread
         rq.V = (double *)pinned_get(srv, (size_t)job.n * 8, &rq.V_cap);
         rq.policy = (uint8_t *)pinned_get(srv, job.n, &rq.policy_cap);
