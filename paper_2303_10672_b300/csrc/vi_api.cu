@@ -1030,8 +1030,12 @@ static vi_status build_graph(vi_problem *h) {
 
     void *sweep_args[] = {&h->args_kp, &h->args_mode_sweep, &h->args_null_v, &h->args_null_v, &h->args_null_p,
                           &h->args_lpr};
-    cudaGraphNode_t n_sweep;
+    // two sweeps per pass of the loop body: the loop's per-pass cost is paid once per
+    // two sweeps; a sweep that finds the stop flag set returns at once
+    cudaGraphNode_t n_sweep, n_sweep2;
     vi_status vs = add_sweep_nodes(body, ld_sweep, sweep_args, nullptr, &n_sweep);
+    if (vs != VI_OK) return vs;
+    vs = add_sweep_nodes(body, ld_sweep, sweep_args, n_sweep, &n_sweep2);
     if (vs != VI_OK) return vs;
 
     void *extract_args[] = {&h->args_kp, &h->args_mode_extract, &h->args_null_v, &h->args_null_v,
