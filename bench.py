@@ -254,6 +254,21 @@ def two_product_fmas(inst) -> int:
     return sweep + S1 * terms2 + nt * terms2
 
 
+def solve_launches(iters, no_graph: bool, max_iters: int, per_sweep: int) -> int:
+    """Kernel launches of the timed solves: per solve the init kernel, the sweeps
+    (the graph's loop body holds two, the host loop launches four between status
+    reads; a sweep after the stop returns at once but is launched) with their
+    pre-kernels, and the extraction sweep."""
+    group = 4 if no_graph else 2
+    total = 0
+    for it in iters:
+        sweeps = -(-it // group) * group if it > 0 else 0
+        if no_graph:
+            sweeps = min(sweeps, max_iters)   # the host loop stops launching at max_iters
+        total += 1 + (sweeps + 1) * per_sweep
+    return int(total)
+
+
 def algorithmic_work(inst) -> dict:
     """Algorithmic work of one Bellman sweep and the compulsory HBM bytes (old and
     new value of every state, 8 B float pair each).  One product: one
@@ -471,7 +486,8 @@ def run_native(args):
                        "converged": bool(info["status"] == vi.VI_OK), "precision": args.precision or inst.precision,
                        "stop_rule": "span", "l2": "flushed between steps (2x L2 write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "gpu_launches": int(sum(iters) + 2 * args.steps),
+            "gpu_launches": solve_launches(iters, args.no_graph, args.max_iters,
+                                           3 if (len(inst.products) == 2 and kch == vi.VI_KERNEL_GROUP) else 1),
             "clocks": clocks,
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
