@@ -549,7 +549,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
     if (PAIR && mode != MODE_EXTRACT) {
         // the previous values of WB states are loaded together, so that one load
         // latency serves WB states instead of one
-        constexpr int WB = LIFO ? 4 : 1;
+        constexpr int WB = 4;
         const float2 *vin2 = (const float2 *)B.vin;
         float2 *vout2 = (float2 *)B.vout;
         for (uint32_t i0 = threadIdx.x; i0 < nblk; i0 += WB * kGroupThreads) {
