@@ -255,9 +255,8 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                 const uint32_t atop = (uint32_t)a * P.w_top;
                 // L >= 2 with the shared path: the tail value's index is known now, so its
                 // load is issued before the chunks and is consumed after them (measured on
-                // B300: 2% faster at 11 x per lane, 0.6% slower at 21, which has no
-                // registers to spare)
-                constexpr bool early_tail = PAIR && LPIPE && XW <= 12;
+                // B300: 2% faster at 11 x per lane, 0.5% at 21)
+                constexpr bool early_tail = PAIR && LPIPE;
                 float2 rawR = make_float2(0.f, 0.f);
                 if constexpr (early_tail) {
                     if (shared_fifo && R >= 1 && x0 + R <= dmax) rawR = __ldg(V2 + tail_rel + atop);
