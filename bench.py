@@ -256,10 +256,10 @@ def two_product_fmas(inst) -> int:
 
 def solve_launches(iters, no_graph: bool, max_iters: int, per_sweep: int) -> int:
     """Kernel launches of the timed solves: per solve the init kernel, the sweeps
-    (the graph's loop body holds two, the host loop launches four between status
+    (the graph's loop body holds four, the host loop launches four between status
     reads; a sweep after the stop returns at once but is launched) with their
     pre-kernels, and the extraction sweep."""
-    group = 4 if no_graph else 2
+    group = 4
     total = 0
     for it in iters:
         sweeps = -(-it // group) * group if it > 0 else 0

@@ -976,6 +976,8 @@ static vi_status add_sweep_nodes(cudaGraph_t g, const LaunchDesc &ld, void **arg
     return VI_OK;
 }
 
+constexpr int kSweepsPerPass = 4;
+
 static vi_status build_graph(vi_problem *h) {
     if (h->graph_exec && h->graph_xw == h->sweep_xw) return VI_OK;
     if (h->graph_exec) {
@@ -1030,13 +1032,16 @@ static vi_status build_graph(vi_problem *h) {
 
     void *sweep_args[] = {&h->args_kp, &h->args_mode_sweep, &h->args_null_v, &h->args_null_v, &h->args_null_p,
                           &h->args_lpr};
-    // two sweeps per pass of the loop body: the loop's per-pass cost is paid once per
-    // two sweeps; a sweep that finds the stop flag set returns at once
-    cudaGraphNode_t n_sweep, n_sweep2;
-    vi_status vs = add_sweep_nodes(body, ld_sweep, sweep_args, nullptr, &n_sweep);
-    if (vs != VI_OK) return vs;
-    vs = add_sweep_nodes(body, ld_sweep, sweep_args, n_sweep, &n_sweep2);
-    if (vs != VI_OK) return vs;
+    // kSweepsPerPass sweeps per pass of the loop body: the loop's per-pass cost is
+    // paid once per pass; a sweep that finds the stop flag set returns at once
+    cudaGraphNode_t n_sweep = nullptr;
+    vi_status vs = VI_OK;
+    for (int k = 0; k < kSweepsPerPass; ++k) {
+        cudaGraphNode_t n_next;
+        vs = add_sweep_nodes(body, ld_sweep, sweep_args, n_sweep, &n_next);
+        if (vs != VI_OK) return vs;
+        n_sweep = n_next;
+    }
 
     void *extract_args[] = {&h->args_kp, &h->args_mode_extract, &h->args_null_v, &h->args_null_v,
                             &h->args_null_p, &h->args_lpr};

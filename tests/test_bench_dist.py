@@ -55,16 +55,16 @@ def test_single_rank_needs_no_process_group():
 
 
 def test_solve_launch_count():
-    """gpu_launches: per solve the init kernel, the sweeps as launched (two per graph
+    """gpu_launches: per solve the init kernel, the sweeps as launched (four per graph
     pass, four per host-loop batch, capped at max_iters by the host loop only), with
     their pre-kernels, and the extraction sweep."""
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.solve_launches([22] * 10, False, 5000, 1) == 10 * (1 + 22 + 1)
-    assert bench.solve_launches([19], False, 5000, 1) == 1 + 20 + 1          # the 20th sweep is empty
-    assert bench.solve_launches([19], True, 5000, 1) == 1 + 20 + 1           # host loop: batches of 4
+    assert bench.solve_launches([22] * 10, False, 5000, 1) == 10 * (1 + 24 + 1)   # sweeps 23, 24 empty
+    assert bench.solve_launches([19], False, 5000, 1) == 1 + 20 + 1
+    assert bench.solve_launches([19], True, 5000, 1) == 1 + 20 + 1
     assert bench.solve_launches([22], True, 5000, 1) == 1 + 24 + 1
     assert bench.solve_launches([5], True, 5, 1) == 1 + 5 + 1                 # capped at max_iters
-    assert bench.solve_launches([5], False, 5, 1) == 1 + 6 + 1                # the graph body runs whole
+    assert bench.solve_launches([5], False, 5, 1) == 1 + 8 + 1                # the graph body runs whole
     assert bench.solve_launches([15], False, 5000, 3) == 1 + (16 + 1) * 3     # two pre-kernels per sweep
     assert bench.solve_launches([0], False, 0, 1) == 1 + 0 + 1               # extraction only
