@@ -289,8 +289,8 @@ def algorithmic_work(inst) -> dict:
 # DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu captures
 # summarised in profiles/sweep_group_*.md; an entry is dropped when that kernel changes
 NCU_TRAFFIC = {
-    ("cfg2_m5L2Q20_nb_fifo", "sweep_group_kernel (lane width 21)"): 34_048_512,
-    ("cfg4_m8L1Q10_lifo", "sweep_group_kernel (lane width 11)"): 393_087_488,
+    ("cfg2_m5L2Q20_nb_fifo", "sweep_group_kernel (lane width 21)"): 34_112_768,
+    ("cfg4_m8L1Q10_lifo", "sweep_group_kernel (lane width 11)"): 393_176_064,
     ("cfg2_m5L2Q20_nb_fifo", "sweep_tc_kernel"): 34_158_336,
 }
 
