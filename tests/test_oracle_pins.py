@@ -279,6 +279,71 @@ def test_bruteforce_two_products():
 
 
 # ---------------------------------------------------------------------------
+# FP64 policy evaluation (the paper's double-precision evaluation of a fixed
+# policy): the oracle's fixed-policy sweeps against the unit-by-unit model's
+# dense linear solve (I - gamma P_pi) V = r_pi, and its iterates and stopping
+# sweep against the fixed-point recursion V_k = r_pi + gamma P_pi V_{k-1} formed
+# from the same dense matrices
+# ---------------------------------------------------------------------------
+
+def _pe_instances():
+    for case in BRUTE:
+        rng = np.random.default_rng(case["m"] * 7 + case["L"] + case["issuing"])
+        cost = tuple(rng.uniform(0.5, 8.0, 4)) + (float(rng.uniform(0, 3)),)
+        yield workloads.single_product(case["m"], case["L"], case["Q"], cost,
+                                       workloads.poisson_pmf(case["mu"], case["dmax"]), 0.9, case["issuing"])
+    yield workloads.single_product(3, 2, 3, (2.0, 0.5, 4.0, 3.0, 0.0), workloads.poisson_pmf(2.5, 8), 0.95, LIFO)
+    c1 = (0.5, 0.2, 1.0, 0.7, 1.0)
+    c2 = (0.4, 0.1, 0.5, 0.9, 1.2)
+    yield workloads.Instance("b2", [workloads.Product(2, 1, 1, c1, workloads.poisson_pmf(0.8, 3)),
+                                    workloads.Product(2, 1, 1, c2, workloads.poisson_pmf(1.1, 3))],
+                             gamma=0.85, issuing=FIFO, subst_rate=0.5)
+
+
+def _dense_pi(Pm, R, pol):
+    idx = np.arange(len(pol))
+    return Pm[pol, idx, :], R[pol, idx]
+
+
+@pytest.mark.parametrize("k", range(7))
+def test_policy_eval_matches_dense_solve(k):
+    inst = list(_pe_instances())[k]
+    S, A = inst.n_states, inst.n_actions
+    Pm, R = unit_model.dense_model(inst)
+    P = oracle.Problem(inst)
+    rng = np.random.default_rng(100 + k)
+    opt = P.vi_solve(tol=1e-12, max_iters=5000, stop_rule=1)["policy"].astype(np.int64)
+    for pol in (rng.integers(0, A, S), opt, np.full(S, A - 1)):
+        want = unit_model.policy_values(Pm, R, inst.gamma, pol[None])[0]
+        V, iters, ok = P.policy_eval(pol.astype(np.uint8), tol=1e-12, max_iters=20000)
+        assert ok
+        np.testing.assert_allclose(V, want, rtol=1e-10, atol=1e-9)
+
+        # the iterates and the stopping sweep: first k with sup |V_k - V_{k-1}| < tol
+        Ppi, rpi = _dense_pi(Pm, R, pol)
+        V0 = rng.uniform(-5.0, 5.0, S)
+        tol = 1e-3
+        Vd, kstop = V0.copy(), None
+        dense_iterates = []
+        for it in range(1, 2000):
+            Vn = rpi + inst.gamma * (Ppi @ Vd)
+            dense_iterates.append(Vn)
+            if np.abs(Vn - Vd).max() < tol:
+                kstop = it
+                Vd = Vn
+                break
+            Vd = Vn
+        V, iters, ok = P.policy_eval(pol.astype(np.uint8), tol=tol, max_iters=5000, V0=V0)
+        assert ok and iters == kstop
+        np.testing.assert_allclose(V, Vd, rtol=1e-12, atol=1e-10)
+        # a sweep cap returns the capped iterate, not converged
+        for cap in (1, 2, max(1, kstop // 2)):
+            V, iters, ok = P.policy_eval(pol.astype(np.uint8), tol=tol, max_iters=cap, V0=V0)
+            assert iters == cap and ok == (cap >= kstop)
+            np.testing.assert_allclose(V, dense_iterates[cap - 1], rtol=1e-12, atol=1e-10)
+
+
+# ---------------------------------------------------------------------------
 # P3: invariants
 # ---------------------------------------------------------------------------
 
