@@ -316,7 +316,7 @@ def run_native(args):
     prods = [dict(m=q.m, L=q.L, Q=q.Q, cost=q.cost, pmf=q.pmf) for q in inst.products]
     desc, keep = vi.make_desc(prods, inst.gamma, inst.issuing, prec, vi.VI_STOP_SPAN, inst.subst_rate)
     kernel = {"auto": vi.VI_KERNEL_AUTO, "group": vi.VI_KERNEL_GROUP, "tensor": vi.VI_KERNEL_TENSOR,
-              "generic": vi.VI_KERNEL_GENERIC}[args.kernel]
+              "generic": vi.VI_KERNEL_GENERIC, "lifo1": vi.VI_KERNEL_LIFO_L1}[args.kernel]
 
     def configure(hh):
         if kernel != vi.VI_KERNEL_AUTO:
@@ -378,7 +378,8 @@ def run_native(args):
     k1.synchronize()
     k_ms = k0.elapsed_time(k1) / reps
     kch, kw = vi.vi_problem_kernel(h)
-    kernel_name = {vi.VI_KERNEL_GENERIC: "sweep_generic_kernel", vi.VI_KERNEL_TENSOR: "sweep_tc_kernel"}.get(
+    kernel_name = {vi.VI_KERNEL_GENERIC: "sweep_generic_kernel", vi.VI_KERNEL_TENSOR: "sweep_tc_kernel",
+                   vi.VI_KERNEL_LIFO_L1: "sweep_lifo1_kernel"}.get(
         kch, f"sweep_group_kernel (lane width {kw})")
     if len(inst.products) == 2 and kch == vi.VI_KERNEL_GROUP:
         kernel_name = ("twop_e2_kernel + twop_mix_kernel + twop_sweep_kernel" if inst.products[0].L >= 2
@@ -800,7 +801,7 @@ def main():
     ap.add_argument("--paper", default="abc", help="which of the paper's Scenario A/B/C results to run ('' or 0 = none)")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven sweep loop instead of the CUDA graph (same kernels; lets a profiler see each launch)")
-    ap.add_argument("--kernel", choices=["auto", "group", "tensor", "generic"], default="auto",
+    ap.add_argument("--kernel", choices=["auto", "group", "tensor", "generic", "lifo1"], default="auto",
                     help="sweep kernel (auto: the autotuner picks among the factorised variants)")
     ap.add_argument("--group-width", type=int, default=0,
                     help="lane width of the factorised kernel (0 = autotuned)")

@@ -204,8 +204,8 @@ vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
 
 /* Per-handle options (no counterpart in the paper; tuning and test hooks).
  * VI_OPT_KERNEL: which sweep kernel runs -- VI_KERNEL_AUTO (factorised kernel
- * whenever the instance allows it; the tensor-core variant is one of the
- * autotuned candidates; two products in VI_PREC_FP32 run the factorised
+ * whenever the instance allows it; for LIFO with L = 1 the VI_KERNEL_LIFO_L1
+ * sweep is one of the autotuned candidates; two products in VI_PREC_FP32 run the factorised
  * two-product sweep -- with lead times >= 2 on both products its pipeline form
  * (m >= 2, Q+1 <= 32) -- which vi_problem_kernel reports as VI_KERNEL_GROUP with
  * width 0),
@@ -215,7 +215,13 @@ vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
  * at least one state digit) or VI_KERNEL_TENSOR (factorised, with the FIFO
  * expectation of a tile of rests and orders computed as one product on the
  * tensor cores; VI_EINVAL unless one product, FIFO, VI_PREC_FP32, L >= 2,
- * 2 <= Q+1 <= 32 and Dmax <= 127).
+ * 2 <= Q+1 <= 32 and Dmax <= 127; only run when asked for) or
+ * VI_KERNEL_LIFO_L1 (factorised LIFO sweep for lead time one: every order's
+ * next states lie on two sequences of the rest -- the order partly used, the
+ * order used up and the rest issued freshest first -- gathered once per rest,
+ * so each order's expectation is a short convolution of them with the pmf;
+ * persistent blocks; VI_EINVAL unless one product, LIFO, VI_PREC_FP32, L = 1,
+ * m >= 2, 2 <= Q+1 <= 16 and Dmax <= 31).
  * VI_OPT_PE_MAX_ITERS: sweep cap of the FP64 policy evaluation in vi_solve.
  * VI_OPT_GROUP_WIDTH: run the factorised kernel with this many expiring-slot
  * values per lane (1..12, 16, 21 or 24; Q+1 is split over ceil((Q+1)/width)
@@ -227,12 +233,12 @@ vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
  * sweep then reports VI_ECUDA ("bounded wait ... gave up") and the CUDA
  * context stays usable.  0 restores normal operation. */
 enum { VI_OPT_KERNEL = 1, VI_OPT_PE_MAX_ITERS = 2, VI_OPT_GROUP_WIDTH = 3, VI_OPT_TEST_STALL = 4 };
-enum { VI_KERNEL_AUTO = 0, VI_KERNEL_GENERIC = 1, VI_KERNEL_GROUP = 2, VI_KERNEL_TENSOR = 3 };
+enum { VI_KERNEL_AUTO = 0, VI_KERNEL_GENERIC = 1, VI_KERNEL_GROUP = 2, VI_KERNEL_TENSOR = 3, VI_KERNEL_LIFO_L1 = 4 };
 vi_status vi_problem_set_option(vi_handle h, int option, int value);
 
 /* Which sweep kernel the handle runs (no counterpart in the paper): *kernel =
- * VI_KERNEL_GENERIC, VI_KERNEL_GROUP or VI_KERNEL_TENSOR, *width = the lane
- * width of VI_KERNEL_GROUP (0 otherwise).  Resolves the choice (and runs the
+ * VI_KERNEL_GENERIC, VI_KERNEL_GROUP, VI_KERNEL_TENSOR or VI_KERNEL_LIFO_L1,
+ * *width = the lane width of VI_KERNEL_GROUP (0 otherwise).  Resolves the choice (and runs the
  * autotuner, on the handle's default stream) if no solve has done so yet.
  * Either pointer may be NULL.  Errors: VI_EINVAL (null handle), VI_ECUDA. */
 vi_status vi_problem_kernel(vi_handle h, int *kernel, int *width);

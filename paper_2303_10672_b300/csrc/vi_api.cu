@@ -702,10 +702,16 @@ extern "C" vi_status vi_problem_set_option(vi_handle h, int option, int value) {
                                "the tensor-core kernel needs one product, FIFO, FP32 precision, L >= 2, "
                                "2 <= Q+1 <= 32 and Dmax <= 127");
             h->kernel_choice = VI_KERNEL_TENSOR;
+        } else if (value == VI_KERNEL_LIFO_L1) {
+            if (!h->group_ok || !lifo1_supported(h->kp, h->vk, h->kahan))
+                return vi_fail(VI_EINVAL,
+                               "the lead-time-one LIFO kernel needs one product, LIFO, FP32 precision, L = 1, "
+                               "m >= 2, 2 <= Q+1 <= 16 and Dmax <= 31");
+            h->kernel_choice = VI_KERNEL_LIFO_L1;
         } else {
             return vi_fail(VI_EINVAL, "bad kernel choice %d", value);
         }
-        h->group_xw = (value == VI_KERNEL_TENSOR) ? kTcWidth : 0;
+        h->group_xw = (value == VI_KERNEL_TENSOR) ? kTcWidth : (value == VI_KERNEL_LIFO_L1) ? kLifo1Width : 0;
         if (h->graph_exec) {
             cudaGraphExecDestroy(h->graph_exec);
             h->graph_exec = nullptr;
@@ -756,9 +762,9 @@ extern "C" vi_status vi_problem_set_option(vi_handle h, int option, int value) {
 // kernel choice and autotuning of the factorised kernel's lane width
 // ---------------------------------------------------------------------------
 struct TuneKey {
-    int vk, issuing, m, L, Q, dmax, tc;
+    int vk, issuing, m, L, Q, dmax, l1;
     bool operator<(const TuneKey &o) const {
-        return std::tie(vk, issuing, m, L, Q, dmax, tc) < std::tie(o.vk, o.issuing, o.m, o.L, o.Q, o.dmax, o.tc);
+        return std::tie(vk, issuing, m, L, Q, dmax, l1) < std::tie(o.vk, o.issuing, o.m, o.L, o.Q, o.dmax, o.l1);
     }
 };
 static std::mutex g_tune_mu;
@@ -778,9 +784,11 @@ static vi_status launch_desc(const LaunchDesc &ld, void **args, cudaStream_t s);
 // time one plain sweep per candidate width on scratch buffers, keep the fastest
 static vi_status autotune(vi_problem *h, cudaStream_t s) {
     const ProdParams &P = h->kp.p[0];
-    // the tensor-core kernel competes only when the caller left the choice open
-    const int tc = (h->kernel_choice == VI_KERNEL_AUTO && tc_supported(h->kp, h->vk, h->kahan)) ? 1 : 0;
-    const TuneKey key{h->vk, h->kp.issuing, P.m, P.L, P.Q, P.dmax, tc};
+    // the lead-time-one LIFO kernel competes when the caller left the choice open; the
+    // tensor-core FIFO kernel (slower than the CUDA-core sweep as measured on B300)
+    // runs only when asked for
+    const int l1 = (h->kernel_choice == VI_KERNEL_AUTO && lifo1_supported(h->kp, h->vk, h->kahan)) ? 1 : 0;
+    const TuneKey key{h->vk, h->kp.issuing, P.m, P.L, P.Q, P.dmax, l1};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -796,7 +804,7 @@ static vi_status autotune(vi_problem *h, cudaStream_t s) {
     }
     int cand[17];
     int nc = group_width_candidates(P.G, cand, 16);
-    if (tc) cand[nc++] = kTcWidth;
+    if (l1) cand[nc++] = kLifo1Width;
     const size_t nb = (size_t)h->kp.nS * h->value_bytes;
     void *a = nullptr, *b = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -923,7 +931,7 @@ static vi_status choose_kernel(vi_problem *h, cudaStream_t s) {
     }
     h->sweep_xw = h->group_xw;
     // measured on B300: 2.4% faster for the FIFO 4.08M-state sweep, none for LIFO
-    if (h->sweep_xw == kTcWidth || h->kp.issuing != VI_FIFO) {
+    if (h->sweep_xw == kTcWidth || h->sweep_xw == kLifo1Width || h->kp.issuing != VI_FIFO) {
         h->kp.grp_order = nullptr;
         return VI_OK;
     }
@@ -935,8 +943,11 @@ extern "C" vi_status vi_problem_kernel(vi_handle h, int *kernel, int *width) {
     vi_status st = choose_kernel(h, nullptr);
     if (st != VI_OK) return st;
     const int xw = h->sweep_xw;
-    if (kernel) *kernel = (xw == 0) ? VI_KERNEL_GENERIC : (xw == kTcWidth) ? VI_KERNEL_TENSOR : VI_KERNEL_GROUP;
-    if (width) *width = (xw == 0 || xw == kTcWidth || xw == kTwoWidth) ? 0 : xw;
+    if (kernel)
+        *kernel = (xw == 0) ? VI_KERNEL_GENERIC
+                  : (xw == kTcWidth) ? VI_KERNEL_TENSOR
+                  : (xw == kLifo1Width) ? VI_KERNEL_LIFO_L1 : VI_KERNEL_GROUP;
+    if (width) *width = (xw == 0 || xw == kTcWidth || xw == kTwoWidth || xw == kLifo1Width) ? 0 : xw;
     return VI_OK;
 }
 

@@ -70,6 +70,10 @@ bool group_width_supported(int xw);
 constexpr int kTcWidth = 100;
 // lane-width token of the factorised two-product sweep
 constexpr int kTwoWidth = 200;
+// lane-width token of the persistent LIFO sweep for lead time one (vi_lifo1.cuh)
+constexpr int kLifo1Width = 300;
+bool lifo1_supported(const KernelParams &kp, int vk, int kahan);
+cudaError_t describe_lifo1(const KernelParams &kp, LaunchDesc &d);
 bool two_supported(const KernelParams &kp, int vk);
 size_t two_table_floats(const KernelParams &kp, size_t *mix_floats);
 // rows of the substitution mixture table: product-1 stock T1 = 0..min(dmax1, m1 Q1)

@@ -5,6 +5,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
+import oracle
 import paper_2303_10672_b300 as vi
 
 PREC = {"fp32": vi.VI_PREC_FP32, "fp32_kahan": vi.VI_PREC_FP32_KAHAN, "fp64": vi.VI_PREC_FP64,
@@ -92,3 +93,55 @@ def policy_mismatches(P_oracle, V_ref: np.ndarray, pol_gpu: np.ndarray, states=N
         if gap > TIE_RTOL * abs(q[i, ao]):
             bad.append((int(s), ao, ag, float(gap)))
     return bad
+
+
+# full solves vs the oracle at the oracle's stopping iteration
+def solve_parity(inst, precision, kernel=vi.VI_KERNEL_AUTO, tol=1e-4, stop_rule=0):
+    P = oracle.Problem(inst)
+    ref = P.vi_solve(tol=tol, max_iters=5000, stop_rule=stop_rule)
+    i_o = ref["iters"]
+    with Handle(inst, precision=precision, stop_rule=stop_rule, kernel=kernel) as H:
+        # same iteration count as the oracle, stop test disabled (tol = 0)
+        V, pol, info = H.solve(0.0, i_o)
+        assert info["iters"] == i_o
+        v = H.v_abs(V, info)
+        err = compare_values(v, ref["V"])
+        assert err <= V_RTOL, f"value error {err:.3e}"
+        bad = policy_mismatches(P, ref["V"], pol.cpu().numpy())
+        assert not bad, bad[:5]
+        # the device stopping test: same rule, own iteration count
+        V2, pol2, info2 = H.solve(tol, 5000)
+        assert info2["status"] == vi.VI_OK
+        assert abs(info2["iters"] - i_o) <= 2, (info2["iters"], i_o)
+    return err
+
+
+# full-size instances: one backup in the benchmark's launch configuration, compared on
+# sampled states computed one by one by the oracle
+def sampled_backup_parity(inst, k_sweeps, n_samples, seed, precision="fp32", kernel=vi.VI_KERNEL_AUTO):
+    P = oracle.Problem(inst)
+    with Handle(inst, precision=precision, kernel=kernel) as H:
+        V, pol, info = H.solve(0.0, k_sweeps)           # V_k (+ offset for the single layout)
+        n = H.sizes["n_states"]
+        V_next = torch.empty_like(V)
+        pol_next = torch.empty(n, dtype=torch.uint8, device="cuda")
+        dmx, dmn = vi.vi_backup(H.h, V, V_next, pol_next)
+        torch.cuda.synchronize()
+        b = info["offset"]
+        v_k = H.v_abs(V, info)
+        # single layout: V_next holds V_abs' - gamma b; pair / double: absolute
+        v_next = values_abs(V_next, inst.gamma * b, H.layout)
+        rng = np.random.default_rng(seed)
+        states = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, n_samples)]))
+        want, _ = P.backup_states(v_k, states)
+        err = np.abs(v_next[states] - want).max() / np.abs(want).max()
+        assert err <= V_RTOL, err
+        bad = policy_mismatches(P, v_k, pol_next.cpu().numpy()[states], states)
+        assert not bad, bad[:5]
+        # the policy written by the extraction sweep of the solve is the argmax from V_k
+        bad = policy_mismatches(P, v_k, pol.cpu().numpy()[states], states)
+        assert not bad, bad[:5]
+        # change statistics: max / min of V_next - V_k in the kernel's own value units
+        dv = values_abs(V_next, 0.0, H.layout) - values_abs(V, 0.0, H.layout)
+        scale = max(1.0, np.abs(v_k).max())
+        assert abs(dmx - dv.max()) <= 1e-6 * scale and abs(dmn - dv.min()) <= 1e-6 * scale
