@@ -311,6 +311,7 @@ vi_status build_single_product(const vi_problem_desc &d, KernelParams &kp, std::
     std::vector<double> blob;
     fill_prod_params(kp.p[0], d.m[0], d.L[0], d.Q[0], d.dmax[0], d.cost[0][0]);
     fill_product_tables(kp.p[0], pm, d.issuing, d.cost[0], true, blob);
+    for (int i = 0; i < 32; ++i) kp.pmf32[i] = (i <= d.dmax[0]) ? (float)pm[i] : 0.f;
     kp.nS = kp.p[0].nS;
     kp.nA = kp.p[0].G;
     kp.n_tables = (int)blob.size();
@@ -362,6 +363,7 @@ extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_hand
         fill_prod_params(kp.p[k], d.m[k], d.L[k], d.Q[k], d.dmax[k], d.cost[k][0]);
         fill_product_tables(kp.p[k], h->pmf[k], d.issuing, d.cost[k], d.n_products == 1, blob);
     }
+    for (int i = 0; i < 32; ++i) kp.pmf32[i] = (i <= d.dmax[0]) ? (float)h->pmf[0][i] : 0.f;
     if (d.n_products == 1) {
         kp.nS = kp.p[0].nS;
         kp.nA = kp.p[0].G;
@@ -799,7 +801,7 @@ static vi_status autotune(vi_problem *h, cudaStream_t s) {
     }
     const char *env = getenv("VI_AUTOTUNE");
     if (env && env[0] == '0') {
-        h->group_xw = heuristic_width(P.G, h->kp.issuing);
+        h->group_xw = l1 ? kLifo1Width : heuristic_width(P.G, h->kp.issuing);
         return VI_OK;
     }
     int cand[17];
@@ -1111,6 +1113,8 @@ static vi_status solve_impl(vi_problem *h, double tol, int max_iters, void *V, u
                             int flags, vi_solve_info *info, void *vhost) {
     if (!h) return vi_fail(VI_EINVAL, "null handle");
     if (!V) return vi_fail(VI_EINVAL, "null V");
+    if (((uintptr_t)V) % (uintptr_t)h->value_bytes != 0)
+        return vi_fail(VI_EINVAL, "V must be aligned to its %d-byte values", h->value_bytes);
     if (!(tol >= 0.0) || max_iters < 0) return vi_fail(VI_EINVAL, "need tol >= 0 and max_iters >= 0");
     if ((flags & VI_FLAG_WARM_START) && !info) return vi_fail(VI_EINVAL, "warm start needs info->offset");
     if (h->periodic && (flags & VI_FLAG_POLICY_EVAL))
@@ -1223,7 +1227,8 @@ extern "C" vi_status vi_solve_host(vi_handle h, double tol, int max_iters, void 
     // them, so the transfer overlaps the sweep instead of following it (not with the
     // FP64 policy evaluation, which reads both on the device afterwards)
     void *dv = nullptr, *dp = nullptr;
-    const bool direct = !(flags & VI_FLAG_POLICY_EVAL) && pinned_view(V_host, &dv) &&
+    const bool direct = !(flags & VI_FLAG_POLICY_EVAL) && ((uintptr_t)V_host) % (uintptr_t)h->value_bytes == 0 &&
+                        pinned_view(V_host, &dv) &&
                         (!policy_host || pinned_view(policy_host, &dp));
     vi_status st;
     if (direct) {
@@ -1245,6 +1250,8 @@ extern "C" vi_status vi_backup(vi_handle h, const void *V_in, void *V_out, uint8
                                double *dstats) {
     if (!h) return vi_fail(VI_EINVAL, "null handle");
     if (!V_in || !V_out || V_in == V_out) return vi_fail(VI_EINVAL, "V_in and V_out must be distinct buffers");
+    if ((((uintptr_t)V_in) | ((uintptr_t)V_out)) % (uintptr_t)h->value_bytes != 0)
+        return vi_fail(VI_EINVAL, "V_in and V_out must be aligned to their %d-byte values", h->value_bytes);
     cudaStream_t s = (cudaStream_t)stream;
     vi_status cs = choose_kernel(h, s);
     if (cs != VI_OK) return cs;
@@ -1323,6 +1330,7 @@ extern "C" vi_status vi_policy_eval(vi_handle h, const uint8_t *policy, double *
     if (h && h->periodic) return vi_fail(VI_EINVAL, "vi_policy_eval is not available for periodic problems");
     if (!h) return vi_fail(VI_EINVAL, "null handle");
     if (!policy || !V || !(tol >= 0.0) || max_iters < 0) return vi_fail(VI_EINVAL, "bad policy-eval arguments");
+    if (((uintptr_t)V) % sizeof(double) != 0) return vi_fail(VI_EINVAL, "V must be 8-byte aligned");
     return policy_eval_impl(h, policy, V, tol, max_iters, (cudaStream_t)stream, iters, delta);
 }
 

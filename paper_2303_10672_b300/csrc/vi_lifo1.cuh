@@ -36,15 +36,33 @@ constexpr int kL1Threads = 128;
 // bits per packed slot count for a radix G (ceil(log2 G))
 __host__ __device__ constexpr int l1_bits(int G) { return G <= 2 ? 1 : (G <= 4 ? 2 : (G <= 8 ? 3 : (G <= 16 ? 4 : 5))); }
 
-// shared memory of one block, in bytes
+// asynchronous global -> shared copies (cp.async): the gathers of the next tile
+// and the previous values of the current one land in shared memory while the
+// block computes, without holding registers
+__device__ __forceinline__ uint32_t l1_smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void l1_cp8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(l1_smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void l1_cp16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(l1_smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void l1_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void l1_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// shared memory of one block, in bytes: gathered columns (G + DP - 1 float pairs per
+// rest), the tile's previous / new values, the padded RT table and its low half,
+// the gamma C_a columns and the tile's policy bytes
 __host__ __device__ inline size_t lifo1_smem(int G, int DP, int rt_rows) {
     const int GP = (G + 3) & ~3;
-    return (size_t)4 * (2 * rt_rows * GP + DP + G * kL1Threads) + (size_t)8 * G * kL1Threads +
-           (size_t)G * kL1Threads + 16;
+    return (size_t)8 * (G + DP - 1) * kL1Threads + (size_t)8 * G * kL1Threads + (size_t)4 * 2 * rt_rows * GP +
+           (size_t)4 * G * kL1Threads + (size_t)G * kL1Threads + 16;
 }
 
 // resident blocks per SM the register allocation aims for: four (128 registers)
-// with a 16-entry pmf, two with a 32-entry one (its gathered columns double)
+// with a 16-entry pmf, two with a 32-entry one
 __host__ __device__ constexpr int lifo1_min_blocks(int DP) { return DP <= 16 ? 4 : 2; }
 
 template <int G, int DP>
@@ -53,19 +71,20 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
     constexpr int GP = (G + 3) & ~3;   // RT rows padded to whole float4s
     constexpr int CB = l1_bits(G);
     constexpr int NT = kL1Threads;
-    static_assert(G >= 2 && G <= 16 && DP >= G && DP % 4 == 0, "lifo1 geometry");
+    constexpr int NTH = G + DP - 1;    // gathered per rest: T[0..G-1], H[1..DP-1]
+    static_assert(G >= 2 && G <= 16 && DP >= G && DP % 4 == 0 && DP <= 32, "lifo1 geometry");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SolveState *st = kp.st;
     Bufs B;
     if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
     const ProdParams &P = kp.p[0];
     const int rows = P.rt_rows;
-    float *s_RTh = (float *)smem_raw;               // RT(R, x), row R padded to GP
-    float *s_RTl = s_RTh + rows * GP;               // its low half
-    float *s_p = s_RTl + rows * GP;                 // pmf, zero past dmax (DP entries)
-    float *s_kc = s_p + DP;                         // per-thread columns: gamma C_a
-    float2 *s_out = (float2 *)(s_kc + G * NT);      // new values of the tile's states
-    uint8_t *s_pol = (uint8_t *)(s_out + G * NT);   // and their first argmax
+    float2 *s_TH = (float2 *)smem_raw;               // column j of thread t at [j * NT + t]
+    float2 *s_VO = s_TH + NTH * NT;                  // the tile's previous values, then its new ones
+    float *s_RTh = (float *)(s_VO + G * NT);         // RT(R, x), row R padded to GP
+    float *s_RTl = s_RTh + rows * GP;                // its low half
+    float *s_kc = s_RTl + rows * GP;                 // per-thread columns: gamma C_a
+    uint8_t *s_pol = (uint8_t *)(s_kc + G * NT);     // the tile's first argmax
     {
         const float *tab = (const float *)kp.tables;
         for (int i = threadIdx.x; i < rows * GP; i += NT) {
@@ -73,14 +92,10 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
             s_RTh[i] = (x < G) ? tab[P.off_RT + R * G + x] : 0.f;
             s_RTl[i] = (x < G) ? tab[P.off_RTlo + R * G + x] : 0.f;
         }
-        for (int i = threadIdx.x; i < DP; i += NT) s_p[i] = (i <= P.dmax) ? tab[P.off_p + i] : 0.f;
-    }
-    __syncthreads();
-    float p[DP];
-#pragma unroll
-    for (int d = 0; d < DP; ++d) p[d] = s_p[d];
+    }   // the first barrier of the tile loop publishes the table
 
-    const uint32_t nR = P.nS / (uint32_t)G;
+    const uint32_t nS = P.nS;
+    const uint32_t nR = nS / (uint32_t)G;
     const uint32_t ntiles = (nR + NT - 1) / NT;
     const int nrs = P.n_rest_slots;                  // m - 2 rest slots: X_2 .. X_{m-1}
     const uint32_t w_top = P.w_top;                  // G^(m-2): weight of the order's next-state slot
@@ -88,180 +103,208 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
     const float gam = (float)kp.gamma;
     const float c_o = (float)P.c_o;
     const float2 *V2 = (const float2 *)B.vin;
-    float mx = -INFINITY, mn = INFINITY;
+    // 16-byte pieces need 16-byte aligned value buffers (the state offsets of a tile are even)
+    const bool al16 = ((((uintptr_t)B.vin) | ((uintptr_t)B.vout)) & 15u) == 0;
     const int tid = threadIdx.x;
     float *kc_col = s_kc + tid;
+    float mx = -INFINITY, mn = INFINITY;
 
-    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // the gathers of tile t into this thread's column: T[j] = V[r + j G^(m-2)], then
+    // H[k] = V[r after k units issued freshest first] for k <= min(R, dmax); returns R
+    auto prefetch_gathers = [&](uint32_t t) -> int {
+        const uint32_t r = t * NT + (uint32_t)tid;
+        if (r >= nR) return 0;
+        unsigned long long packed = 0ull;
+        int Rr = 0;
+        uint32_t rem = r;
+        for (int j = 0; j < nrs; ++j) {
+            const uint32_t q = rem / (uint32_t)G;
+            const int dg = (int)(rem - q * (uint32_t)G);
+            rem = q;
+            packed |= (unsigned long long)dg << (CB * j);
+            Rr += dg;
+        }
+#pragma unroll
+        for (int j = 0; j < G; ++j) l1_cp8(s_TH + j * NT + tid, V2 + r + (uint32_t)j * w_top);
+        // slot by slot from X_{m-1} down: each unit issued subtracts the slot's weight
+        const int hcount = min(Rr, dmax);
+        uint32_t w = (nrs > 0) ? w_top / (uint32_t)G : 0u;
+        uint32_t idx = r;
+        float2 *col = s_TH + G * NT + tid;   // H[1] of this thread
+        int k = 0;
+        for (int slot = nrs - 1; slot >= 0 && k < hcount; --slot) {
+            const int units = min((int)((packed >> (CB * slot)) & ((1ull << CB) - 1ull)), hcount - k);
+            for (int u = 0; u < units; ++u) {
+                idx -= w;
+                l1_cp8(col + k * NT, V2 + idx);
+                ++k;
+            }
+            w /= (uint32_t)G;
+        }
+        return Rr;
+    };
+    // the previous values of tile t's states, in 16-byte pieces where aligned
+    auto prefetch_old = [&](uint32_t t) {
+        const uint32_t s0 = t * (uint32_t)(NT * G);
+        const uint32_t nblk = min((uint32_t)(NT * G), nS - s0);
+        const float2 *src = V2 + s0;
+        if (al16) {
+            for (uint32_t i = tid; i < (nblk >> 1); i += NT) l1_cp16(s_VO + 2 * i, src + 2 * i);
+            if ((nblk & 1u) && tid == 0) l1_cp8(s_VO + nblk - 1, src + nblk - 1);
+        } else {
+            for (uint32_t i = tid; i < nblk; i += NT) l1_cp8(s_VO + i, src + i);
+        }
+    };
+
+    uint32_t tile = blockIdx.x;
+    int Rnext = 0;
+    if (tile < ntiles) Rnext = prefetch_gathers(tile);
+    l1_commit();
+    if (tile < ntiles) prefetch_old(tile);
+    l1_commit();
+    for (; tile < ntiles; tile += gridDim.x) {
+        const uint32_t next = tile + gridDim.x;
         const uint32_t r = tile * NT + (uint32_t)tid;
-        if (r < nR) {
-            // -- decode the rest: digit j of r is X_{j+2}
-            unsigned long long packed = 0ull;
-            int Rrest = 0;
-            {
-                uint32_t rem = r;
-                for (int j = 0; j < nrs; ++j) {
-                    const uint32_t q = rem / (uint32_t)G;
-                    const int dg = (int)(rem - q * (uint32_t)G);
-                    rem = q;
-                    packed |= (unsigned long long)dg << (CB * j);
-                    Rrest += dg;
-                }
-            }
-            // -- next-state indices of the used-up-order sequence: LIFO from X_{m-1} down
+        const bool active = r < nR;
+        const int Rrest = Rnext;
+        l1_wait<1>();   // this thread's gathers of the tile have landed (its previous values may not)
+        __syncthreads();
+        float2 R0 = make_float2(0.f, 0.f);
+        float T[G], H[DP];
+        if (active) {
             const int hcount = min(Rrest, dmax);
-            uint32_t hidx[DP];
-            {
-                int slot = nrs - 1;
-                uint32_t w = (nrs > 0) ? w_top / (uint32_t)G : 0u;
-                int left = (nrs > 0) ? (int)((packed >> (CB * slot)) & ((1ull << CB) - 1ull)) : 0;
-                uint32_t idx = r;
-                hidx[0] = r;
-#pragma unroll
-                for (int k = 1; k < DP; ++k) {
-                    if (k <= hcount) {
-                        // k <= R: a non-empty slot remains below; the bound only guards the loop
-                        while (left == 0 && slot > 0) {
-                            --slot;
-                            w /= (uint32_t)G;
-                            left = (int)((packed >> (CB * slot)) & ((1ull << CB) - 1ull));
-                        }
-                        idx -= w;
-                        --left;
-                    }
-                    hidx[k] = idx;
-                }
-            }
-            // -- gathers: every load of the rest is issued before any is used
-            const float2 R0 = __ldg(V2 + r);
-            float2 traw[G];
-            traw[0] = R0;
-#pragma unroll
-            for (int j = 1; j < G; ++j) traw[j] = __ldg(V2 + r + (uint32_t)j * w_top);
-            float2 hraw[DP];
-            hraw[0] = R0;
-#pragma unroll
-            for (int k = 1; k < DP; ++k) hraw[k] = (k <= hcount) ? __ldg(V2 + hidx[k]) : make_float2(0.f, 0.f);
-            float T[G], H[DP];
+            R0 = s_TH[tid];
             T[0] = 0.f;
             H[0] = 0.f;
 #pragma unroll
-            for (int j = 1; j < G; ++j) T[j] = pair_diff(traw[j], R0);
+            for (int j = 1; j < G; ++j) T[j] = pair_diff(s_TH[j * NT + tid], R0);
 #pragma unroll
-            for (int k = 1; k < DP; ++k) H[k] = (k <= hcount) ? pair_diff(hraw[k], R0) : H[k - 1];
+            for (int k = 1; k < DP; ++k)
+                H[k] = (k <= hcount) ? pair_diff(s_TH[(G - 1 + k) * NT + tid], R0) : H[k - 1];
+        }
+        __syncthreads();   // every column is read: the next tile's gathers may land
+        if (next < ntiles) Rnext = prefetch_gathers(next);
+        l1_commit();
 
+        float best[G];
+        int arg[G];
+        if (active) {
             // -- expectations of every order: C_a = sum_{d<a} p_d T[a-d] + sum_{k>=1} p_{a+k} H~[k]
             float C[G];
 #pragma unroll
             for (int a = 0; a < G; ++a) {
                 float c = 0.f;
 #pragma unroll
-                for (int d = 0; d < a; ++d) c = fmaf(p[d], T[a - d], c);
+                for (int d = 0; d < a; ++d) c = fmaf(kp.pmf32[d], T[a - d], c);
 #pragma unroll
-                for (int k = 1; a + k < DP; ++k) c = fmaf(p[a + k], H[k], c);
+                for (int k = 1; a + k < DP; ++k) c = fmaf(kp.pmf32[a + k], H[k], c);
                 C[a] = c;
             }
             // -- first argmax over orders per x on the float key -c_o a + gamma C_a + RT(R + a, x)
-            float best[G];
-            int arg[G];
+            // the RT row of the next order is loaded while this one is compared
+            const float4 *rows4 = (const float4 *)(s_RTh + Rrest * GP);
+            float4 rw[GP / 4];
+#pragma unroll
+            for (int q = 0; q < GP / 4; ++q) rw[q] = rows4[q];
 #pragma unroll
             for (int a = 0; a < G; ++a) {
+                float4 rn[GP / 4];
+                if (a + 1 < G) {
+#pragma unroll
+                    for (int q = 0; q < GP / 4; ++q) rn[q] = rows4[(a + 1) * (GP / 4) + q];
+                }
                 const float bl = __fmul_rn(gam, C[a]);
                 kc_col[a * NT] = bl;
                 const float ks = __fadd_rn(__fmul_rn(-c_o, (float)a), bl);
-                const float4 *row = (const float4 *)(s_RTh + (Rrest + a) * GP);
-                float rt[GP];
+                const float2 ks2 = make_float2(ks, ks);
+                float key[GP];
 #pragma unroll
                 for (int q = 0; q < GP / 4; ++q) {
-                    const float4 v = row[q];
-                    rt[4 * q] = v.x;
-                    rt[4 * q + 1] = v.y;
-                    rt[4 * q + 2] = v.z;
-                    rt[4 * q + 3] = v.w;
+                    const float4 v = rw[q];
+                    const float2 k01 = __fadd2_rn(ks2, make_float2(v.x, v.y));   // lane-wise __fadd_rn
+                    const float2 k23 = __fadd2_rn(ks2, make_float2(v.z, v.w));
+                    key[4 * q] = k01.x;
+                    key[4 * q + 1] = k01.y;
+                    key[4 * q + 2] = k23.x;
+                    key[4 * q + 3] = k23.y;
                 }
 #pragma unroll
                 for (int x = 0; x < G; ++x) {
-                    const float key = __fadd_rn(ks, rt[x]);
                     if (a == 0) {
-                        best[x] = key;
+                        best[x] = key[x];
                         arg[x] = 0;
                     } else {
-                        const bool up = key > best[x];
-                        best[x] = up ? key : best[x];
+                        const bool up = key[x] > best[x];
+                        best[x] = up ? key[x] : best[x];
                         arg[x] = up ? a : arg[x];
                     }
                 }
+                if (a + 1 < G) {
+#pragma unroll
+                    for (int q = 0; q < GP / 4; ++q) rw[q] = rn[q];
+                }
             }
-            // -- the exact pair of each x's chosen order: gamma R0 + (-c_o a) + gamma C_a + RT
+        }
+        l1_wait<1>();   // this thread's pieces of the previous values have landed
+        __syncthreads();
+        if (active) {
+            // -- the exact pair of each x's chosen order: gamma R0 + (-c_o a) + gamma C_a + RT,
+            // its change from the previous value, and the new value in place of the old
             float ph, pe;
             two_prod(gam, R0.x, ph, pe);
             const float pl = __fmaf_rn(gam, R0.y, pe);
-            float2 *o = s_out + tid * G;
+            float2 *o = s_VO + tid * G;
             uint8_t *op = s_pol + tid * G;
+            // every shared-memory operand of the rebuild is loaded before its arithmetic
+            float kq[G], rh[G], rl[G];
 #pragma unroll
             for (int x = 0; x < G; ++x) {
                 const int a = arg[x];
                 const int R = Rrest + a;
-                float qh = __fmul_rn(-c_o, (float)a), ql = kc_col[a * NT];
-                pair_add(qh, ql, s_RTh[R * GP + x], s_RTl[R * GP + x]);
+                kq[x] = kc_col[a * NT];
+                rh[x] = s_RTh[R * GP + x];
+                rl[x] = s_RTl[R * GP + x];
+            }
+#pragma unroll
+            for (int x = 0; x < G; ++x) {
+                const int a = arg[x];
+                float qh = __fmul_rn(-c_o, (float)a), ql = kq[x];
+                pair_add(qh, ql, rh[x], rl[x]);
                 float sh, se;
                 two_sum(ph, qh, sh, se);
                 const float lo = __fadd_rn(se, __fadd_rn(pl, ql));
                 float vh, vl;
                 fast_two_sum(sh, lo, vh, vl);
-                o[x] = make_float2(vh, vl);
+                if (mode != MODE_EXTRACT) {
+                    const float dl = pair_diff(make_float2(vh, vl), o[x]);
+                    mx = fmaxf(mx, dl);
+                    mn = fminf(mn, dl);
+                    o[x] = make_float2(vh, vl);
+                }
                 op[x] = (uint8_t)a;
             }
         }
         __syncthreads();
-        // -- the tile's states leave in 16-byte pieces (two states), with the change statistics
+        // -- the tile's states leave in 16-byte pieces (two states) where aligned; an
+        // extraction moves the previous values unchanged (only when a buffer is given)
         const uint32_t s0 = tile * (uint32_t)(NT * G);
-        const uint32_t nblk = min((uint32_t)(NT * G), P.nS - s0);
-        const float4 *vin4 = (const float4 *)((const float2 *)B.vin + s0);   // s0 is even: 16-byte aligned
-        const float4 *out4 = (const float4 *)s_out;
-        const uint32_t n2 = nblk >> 1;
-        if (mode != MODE_EXTRACT) {
-            float4 *vout4 = (float4 *)((float2 *)B.vout + s0);
-            constexpr int WB = 3;   // loads of the previous values in flight per thread
-            for (uint32_t i0 = tid; i0 < n2; i0 += WB * NT) {
-                float4 vold[WB];
-#pragma unroll
-                for (int u = 0; u < WB; ++u) {
-                    const uint32_t i = i0 + (uint32_t)u * NT;
-                    vold[u] = (i < n2) ? vin4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-#pragma unroll
-                for (int u = 0; u < WB; ++u) {
-                    const uint32_t i = i0 + (uint32_t)u * NT;
-                    if (i < n2) {
-                        const float4 vn = out4[i];
-                        vout4[i] = vn;
-                        const float d0 = pair_diff(make_float2(vn.x, vn.y), make_float2(vold[u].x, vold[u].y));
-                        const float d1 = pair_diff(make_float2(vn.z, vn.w), make_float2(vold[u].z, vold[u].w));
-                        mx = fmaxf(mx, fmaxf(d0, d1));
-                        mn = fminf(mn, fminf(d0, d1));
-                    }
-                }
+        const uint32_t nblk = min((uint32_t)(NT * G), nS - s0);
+        if (B.vout) {
+            float2 *dst = (float2 *)B.vout + s0;
+            if (al16) {
+                for (uint32_t i = tid; i < (nblk >> 1); i += NT) ((float4 *)dst)[i] = ((const float4 *)s_VO)[i];
+                if ((nblk & 1u) && tid == 0) dst[nblk - 1] = s_VO[nblk - 1];
+            } else {
+                for (uint32_t i = tid; i < nblk; i += NT) dst[i] = s_VO[i];
             }
-            if ((nblk & 1u) && tid == 0) {
-                const uint32_t i = nblk - 1;
-                const float2 vn = s_out[i];
-                const float2 vo = ((const float2 *)B.vin)[s0 + i];
-                ((float2 *)B.vout)[s0 + i] = vn;
-                const float dl = pair_diff(vn, vo);
-                mx = fmaxf(mx, dl);
-                mn = fminf(mn, dl);
-            }
-        } else if (B.vout) {
-            // extraction: the values of V_iters move to the caller's buffer unchanged
-            float4 *vout4 = (float4 *)((float2 *)B.vout + s0);
-            for (uint32_t i = tid; i < n2; i += NT) vout4[i] = vin4[i];
-            if ((nblk & 1u) && tid == 0) ((float2 *)B.vout)[s0 + nblk - 1] = ((const float2 *)B.vin)[s0 + nblk - 1];
         }
         if (B.pol)
             for (uint32_t i = tid; i < nblk; i += NT) B.pol[s0 + i] = s_pol[i];
-        __syncthreads();   // s_out and s_pol are rewritten by the next tile
+        __syncthreads();   // the value staging is free for the next tile's previous values
+        if (next < ntiles) prefetch_old(next);
+        l1_commit();
     }
+    l1_wait<0>();
     if (mode != MODE_EXTRACT) block_reduce_and_finalize<float>(mx, mn, st, mode, gridDim.x);
 }
 

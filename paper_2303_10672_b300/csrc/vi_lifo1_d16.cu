@@ -25,7 +25,6 @@ bool lifo1_supported(const KernelParams &kp, int vk, int kahan) {
 }
 
 cudaError_t describe_lifo1(const KernelParams &kp, LaunchDesc &d) {
-    d.lpr = 1;
     d.n_pre = 0;
     return kp.p[0].dmax < 16 ? describe_lifo1_d16(kp, d) : describe_lifo1_d32(kp, d);
 }

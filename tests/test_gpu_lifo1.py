@@ -99,3 +99,19 @@ def test_lifo1_host_loop_matches_graph():
         Vh, ph, ih = H.solve(1e-4, 5000, flags=vi.VI_FLAG_NO_GRAPH)
         assert ig["iters"] == ih["iters"]
         assert torch.equal(Vg, Vh) and torch.equal(pg, ph)
+
+
+def test_misaligned_value_buffers_rejected():
+    # value buffers must sit on their element size; nothing is launched otherwise
+    inst = _inst(5, 6, 3.0, 12, 0.9)
+    with Handle(inst, precision="fp32", kernel=K) as H:
+        n = H.sizes["n_states"]
+        raw = torch.zeros(2 * n + 1, dtype=torch.float32, device="cuda")
+        bad = raw[1:]                                  # 4 bytes past an 8-byte boundary
+        good = torch.zeros(n, dtype=torch.float64, device="cuda")
+        with pytest.raises(vi.ViError):
+            vi.vi_backup(H.h, bad, good, None)
+        with pytest.raises(vi.ViError):
+            vi.vi_backup(H.h, good, bad, None)
+        with pytest.raises(vi.ViError):
+            vi.vi_solve(H.h, 1e-4, 10, bad)
