@@ -131,6 +131,15 @@ static void fill_product_tables(ProdParams &P, const std::vector<double> &pmf, i
     blob.insert(blob.end(), rt.begin(), rt.end());
     P.off_RTlo = (int)blob.size();
     for (double v : rt) blob.push_back(v - (double)(float)v);
+    P.off_LF = P.off_LH = 0;
+    if (issuing == VI_LIFO) {
+        // the same expected reward split as LF(T) + LH(R), T = y1 + R:
+        //   LF(T) = (c_s + c_r) T - c_s E[D] - (c_s + c_r + c_w) E[(T-D)^+],  LH(R) = (c_w - c_h) E[(R-D)^+]
+        P.off_LF = (int)blob.size();
+        for (int T = 0; T <= P.tmax; ++T) blob.push_back((c_s + c_r) * T - c_s * mu - (c_s + c_r + c_w) * G[T]);
+        P.off_LH = (int)blob.size();
+        for (int R = 0; R < P.rt_rows; ++R) blob.push_back((c_w - c_h) * G[R]);
+    }
 }
 
 static double binom(int n, int k, double rho) {

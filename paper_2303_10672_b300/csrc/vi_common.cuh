@@ -42,6 +42,9 @@ struct ProdParams {
                           // y1 units in the expiring slot and R in the others (FP64-built)
     int off_RTlo;         // FP32 blobs: RT - fl32(RT), the low half of the pair (zero in FP64 blobs)
     int rt_rows;          // R ranges over 0..rt_rows-1 = (m-1)Q
+    int off_LF, off_LH;   // LIFO: RT(R, y1) = LF[y1 + R] + LH[R] (LF over 0..tmax, LH over 0..rt_rows-1;
+                          // 0 when absent), with y1 issued last the period's sums depend on y1 + R only
+                          // except for the units of the other slots left unsold
     int pn;               // length of p / F / tail
     double c_o;           // order cost per unit
 };

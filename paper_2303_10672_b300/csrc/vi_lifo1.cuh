@@ -15,14 +15,20 @@
 // R = units of the rest.  (The d = a term is p_a T[0] = 0; p is zero past dmax.)
 // Then Q(s, a) = gamma R0 + (-c_o a + gamma C_a + RT(R + a, x)) (Eq.
 // valueiterationdetupdate with the expected-reward table RT), and the first
-// argmax over orders is taken per x.
+// argmax over orders is taken per x.  Under LIFO the table splits as
+// RT(R, x) = LF(x + R) + LH(R), so the float key of (x, a) is
+// (-c_o a + gamma C_a + LH(R + a)) + LF(x + R + a): one window of 2G - 1 LF
+// values per rest serves all G^2 keys; the exact value of the chosen order is
+// rebuilt from the (hi, lo) pair of RT.
 //
-// G = Q+1 and the pmf capacity DP (> dmax) are compile-time, so the gathers, the
-// convolution and the max over (x, a) are fully unrolled without per-thread
-// bounds.  One thread owns one rest (its G states); a block holds kL1Threads
-// rests and walks the grid's tiles (persistent blocks, one expected-reward table
-// staged per block).  The block's G kL1Threads new values go out through
-// shared memory in 16-byte pieces, together with the change statistics.
+// G = Q+1 and the pmf capacity DP (> dmax) are compile-time, so the convolution
+// and the max over (x, a) are fully unrolled without per-thread bounds.  One
+// thread owns one rest (its G states); a block holds kL1Threads rests and walks
+// the grid's tiles (persistent blocks, tables staged once per block).  The
+// gathers of the next tile and the previous values of the current one are copied
+// into shared memory by cp.async while the block computes; the new values
+// replace the previous ones there (their change feeds the stopping test) and
+// leave in 16-byte pieces.
 #pragma once
 
 #include <algorithm>
@@ -53,22 +59,23 @@ __device__ __forceinline__ void l1_wait() {
 }
 
 // shared memory of one block, in bytes: gathered columns (G + DP - 1 float pairs per
-// rest), the tile's previous / new values, the padded RT table and its low half,
-// the gamma C_a columns and the tile's policy bytes
-__host__ __device__ inline size_t lifo1_smem(int G, int DP, int rt_rows) {
-    const int GP = (G + 3) & ~3;
-    return (size_t)8 * (G + DP - 1) * kL1Threads + (size_t)8 * G * kL1Threads + (size_t)4 * 2 * rt_rows * GP +
-           (size_t)4 * G * kL1Threads + (size_t)G * kL1Threads + 16;
+// rest), the tile's previous / new values, the (hi, lo) pairs of RT at an odd row
+// stride, the LIFO split LF / LH of RT, the gamma C_a columns and the policy bytes
+__host__ __device__ inline size_t lifo1_smem(int G, int DP, int rt_rows, int tmax) {
+    return (size_t)8 * (G + DP - 1) * kL1Threads + (size_t)8 * G * kL1Threads + (size_t)8 * rt_rows * (G | 1) +
+           (size_t)4 * (tmax + 1 + rt_rows) + (size_t)4 * G * kL1Threads + (size_t)G * kL1Threads + 32;
 }
 
 // resident blocks per SM the register allocation aims for: four (128 registers)
-// with a 16-entry pmf, two with a 32-entry one
+// with a 16-entry pmf, two with a 32-entry one (five, with the table reads moved to
+// L1 to make room, measured no faster on B300: their address arithmetic cost what
+// the extra warps gained)
 __host__ __device__ constexpr int lifo1_min_blocks(int DP) { return DP <= 16 ? 4 : 2; }
 
 template <int G, int DP>
 __global__ void __launch_bounds__(kL1Threads, lifo1_min_blocks(DP))
 sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int lpr) {
-    constexpr int GP = (G + 3) & ~3;   // RT rows padded to whole float4s
+    constexpr int GO = G | 1;          // odd row stride of the RT pairs: rows of different lanes hit other banks
     constexpr int CB = l1_bits(G);
     constexpr int NT = kL1Threads;
     constexpr int NTH = G + DP - 1;    // gathered per rest: T[0..G-1], H[1..DP-1]
@@ -79,20 +86,24 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
     if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
     const ProdParams &P = kp.p[0];
     const int rows = P.rt_rows;
+    const int nF = P.tmax + 1;
     float2 *s_TH = (float2 *)smem_raw;               // column j of thread t at [j * NT + t]
     float2 *s_VO = s_TH + NTH * NT;                  // the tile's previous values, then its new ones
-    float *s_RTh = (float *)(s_VO + G * NT);         // RT(R, x), row R padded to GP
-    float *s_RTl = s_RTh + rows * GP;                // its low half
-    float *s_kc = s_RTl + rows * GP;                 // per-thread columns: gamma C_a
+    float2 *s_RTp = s_VO + G * NT;                   // (hi, lo) of RT(R, x) at [R * GO + x]
+    float *s_LF = (float *)(s_RTp + rows * GO);      // LF(T), T = 0..tmax
+    float *s_LH = s_LF + nF;                         // LH(R), R = 0..rows-1
+    float *s_kc = s_LH + rows;                       // per-thread columns: gamma C_a
     uint8_t *s_pol = (uint8_t *)(s_kc + G * NT);     // the tile's first argmax
     {
         const float *tab = (const float *)kp.tables;
-        for (int i = threadIdx.x; i < rows * GP; i += NT) {
-            const int R = i / GP, x = i - R * GP;
-            s_RTh[i] = (x < G) ? tab[P.off_RT + R * G + x] : 0.f;
-            s_RTl[i] = (x < G) ? tab[P.off_RTlo + R * G + x] : 0.f;
+        for (int i = threadIdx.x; i < rows * GO; i += NT) {
+            const int R = i / GO, x = i - R * GO;
+            s_RTp[i] = (x < G) ? make_float2(tab[P.off_RT + R * G + x], tab[P.off_RTlo + R * G + x])
+                               : make_float2(0.f, 0.f);
         }
-    }   // the first barrier of the tile loop publishes the table
+        for (int i = threadIdx.x; i < nF; i += NT) s_LF[i] = tab[P.off_LF + i];
+        for (int i = threadIdx.x; i < rows; i += NT) s_LH[i] = tab[P.off_LH + i];
+    }   // the first barrier of the tile loop publishes the tables
 
     const uint32_t nS = P.nS;
     const uint32_t nR = nS / (uint32_t)G;
@@ -200,33 +211,27 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
                 for (int k = 1; a + k < DP; ++k) c = fmaf(kp.pmf32[a + k], H[k], c);
                 C[a] = c;
             }
-            // -- first argmax over orders per x on the float key -c_o a + gamma C_a + RT(R + a, x)
-            // the RT row of the next order is loaded while this one is compared
-            const float4 *rows4 = (const float4 *)(s_RTh + Rrest * GP);
-            float4 rw[GP / 4];
+            // -- first argmax over orders per x on the float key (-c_o a + gamma C_a + LH(R + a)) +
+            // LF(x + R + a): the rest's LF window covers every key
+            float Fw[2 * G];
 #pragma unroll
-            for (int q = 0; q < GP / 4; ++q) rw[q] = rows4[q];
+            for (int i = 0; i < 2 * G - 1; ++i) Fw[i] = s_LF[Rrest + i];
+            Fw[2 * G - 1] = 0.f;
 #pragma unroll
             for (int a = 0; a < G; ++a) {
-                float4 rn[GP / 4];
-                if (a + 1 < G) {
-#pragma unroll
-                    for (int q = 0; q < GP / 4; ++q) rn[q] = rows4[(a + 1) * (GP / 4) + q];
-                }
                 const float bl = __fmul_rn(gam, C[a]);
                 kc_col[a * NT] = bl;
-                const float ks = __fadd_rn(__fmul_rn(-c_o, (float)a), bl);
+                const float ks = __fadd_rn(__fadd_rn(__fmul_rn(-c_o, (float)a), bl), s_LH[Rrest + a]);
                 const float2 ks2 = make_float2(ks, ks);
-                float key[GP];
+                float key[G + 1];
+                // pairs (x, x+1) start where x + a is even, so that each pair of LF values is
+                // an aligned register pair (lane-wise __fadd_rn)
+                if (a & 1) key[0] = __fadd_rn(ks, Fw[a]);
 #pragma unroll
-                for (int q = 0; q < GP / 4; ++q) {
-                    const float4 v = rw[q];
-                    const float2 k01 = __fadd2_rn(ks2, make_float2(v.x, v.y));   // lane-wise __fadd_rn
-                    const float2 k23 = __fadd2_rn(ks2, make_float2(v.z, v.w));
-                    key[4 * q] = k01.x;
-                    key[4 * q + 1] = k01.y;
-                    key[4 * q + 2] = k23.x;
-                    key[4 * q + 3] = k23.y;
+                for (int x = a & 1; x < G; x += 2) {
+                    const float2 k2 = __fadd2_rn(ks2, make_float2(Fw[x + a], Fw[x + a + 1]));
+                    key[x] = k2.x;
+                    key[x + 1] = k2.y;
                 }
 #pragma unroll
                 for (int x = 0; x < G; ++x) {
@@ -238,10 +243,6 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
                         best[x] = up ? key[x] : best[x];
                         arg[x] = up ? a : arg[x];
                     }
-                }
-                if (a + 1 < G) {
-#pragma unroll
-                    for (int q = 0; q < GP / 4; ++q) rw[q] = rn[q];
                 }
             }
         }
@@ -256,20 +257,19 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
             float2 *o = s_VO + tid * G;
             uint8_t *op = s_pol + tid * G;
             // every shared-memory operand of the rebuild is loaded before its arithmetic
-            float kq[G], rh[G], rl[G];
+            float kq[G];
+            float2 rp[G];
 #pragma unroll
             for (int x = 0; x < G; ++x) {
                 const int a = arg[x];
-                const int R = Rrest + a;
                 kq[x] = kc_col[a * NT];
-                rh[x] = s_RTh[R * GP + x];
-                rl[x] = s_RTl[R * GP + x];
+                rp[x] = s_RTp[(Rrest + a) * GO + x];
             }
 #pragma unroll
             for (int x = 0; x < G; ++x) {
                 const int a = arg[x];
                 float qh = __fmul_rn(-c_o, (float)a), ql = kq[x];
-                pair_add(qh, ql, rh[x], rl[x]);
+                pair_add(qh, ql, rp[x].x, rp[x].y);
                 float sh, se;
                 two_sum(ph, qh, sh, se);
                 const float lo = __fadd_rn(se, __fadd_rn(pl, ql));
@@ -281,7 +281,7 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
                     mn = fminf(mn, dl);
                     o[x] = make_float2(vh, vl);
                 }
-                op[x] = (uint8_t)a;
+                if (B.pol) op[x] = (uint8_t)a;
             }
         }
         __syncthreads();
@@ -311,7 +311,7 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
 template <int G, int DP>
 cudaError_t describe_lifo1_t(const KernelParams &kp, LaunchDesc &d) {
     const ProdParams &P = kp.p[0];
-    const size_t smem = lifo1_smem(G, DP, P.rt_rows);
+    const size_t smem = lifo1_smem(G, DP, P.rt_rows, P.tmax);
     cudaError_t e = cudaFuncSetAttribute(sweep_lifo1_kernel<G, DP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

@@ -21,7 +21,7 @@ cudaError_t describe_lifo1_d16(const KernelParams &kp, LaunchDesc &d) {
 bool lifo1_supported(const KernelParams &kp, int vk, int kahan) {
     const ProdParams &P = kp.p[0];
     return kp.n_products == 1 && vk == VK_PAIR && !kahan && kp.issuing == 1 && P.L == 1 && P.m >= 2 &&
-           P.G >= 2 && P.G <= 16 && P.dmax < 32 && !kp.pc;
+           P.G >= 2 && P.G <= 16 && P.dmax < 32 && !kp.pc && P.off_LF > 0;
 }
 
 cudaError_t describe_lifo1(const KernelParams &kp, LaunchDesc &d) {
