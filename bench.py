@@ -1,15 +1,17 @@
 """Benchmark of the value-iteration hot path on B300.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload cfg2|cfg4|cfg1|cfg3] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload cfg4|cfg2|cfg1|cfg3] [--impl reference]
 
 A step is one complete solve of the workload through the C ABI: synchronous
 FP32 Bellman sweeps (decode, FIFO/LIFO issue, gathers, max/argmax, FP64 span
 reduction and device-side stopping test inside a CUDA-graph while loop) until
 the span of V_i - V_{i-1} is below 1e-4, then the extraction sweep writing the
 policy.  The metric is nominal Bellman state-action-demand updates per second:
-|S| |A| |Omega| x sweeps / solve time.  Default workload: m=5, L=2, Q=20
-(21^5 = 4,084,101 states), negative-binomial demand (mean 8, var 20) folded at
-40, FIFO, costs U[1,10] seeded, gamma 0.99.
+|S| |A| |Omega| x sweeps / solve time.  Default workload: the largest
+single-product configuration, m=8, L=1, Q=10 (11^7 = 19,487,171 states), 11
+orders, Poisson(4) demand folded at 15, LIFO issuing, costs (3, 1, 5, 7),
+gamma 0.95; the 4,084,101-state FIFO configuration (m=5, L=2, Q=20) is
+reported beside it under "cfg2".
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (one Bellman update of a sample of states per
@@ -271,11 +273,12 @@ def solve_launches(iters, no_graph: bool, max_iters: int, per_sweep: int) -> int
 
 def algorithmic_work(inst) -> dict:
     """Algorithmic work of one Bellman sweep and the compulsory HBM bytes (old and
-    new value of every state, 8 B float pair each).  One product: one
+    new value of every state, 8 B float pair each).  One product: the method's one
     multiply-add of p(d) and the next-state value per (state, order, demand
-    outcome), which the factorised kernel performs exactly.  Two products: the
-    multiply-adds of the factorised method (two_product_fmas); `updates` stays the
-    nominal |S| |A| |Omega|."""
+    outcome); the factorised FIFO sweep performs exactly these, the LIFO sweeps
+    fewer (the next states of a rest do not depend on its expiring units).  Two
+    products: the multiply-adds of the factorised method (two_product_fmas);
+    `updates` stays the nominal |S| |A| |Omega|."""
     updates = inst.updates_per_sweep
     if len(inst.products) == 2:
         fmas = two_product_fmas(inst)
@@ -283,15 +286,24 @@ def algorithmic_work(inst) -> dict:
                 "work": "2 flop per multiply-add of the factorised two-product method (E2 table, "
                         "substitution mixture, sum over d1 below stock)"}
     return {"updates": updates, "flops": 2 * updates, "bytes": inst.n_states * 16,
-            "work": "2 flop (one multiply-add) per state x order x demand outcome"}
+            "work": "2 flop (one multiply-add) per state x order x demand outcome, the method's arithmetic"}
+
+
+def lifo1_executed_fmas(inst) -> int:
+    """Multiply-adds the lead-time-one LIFO sweep executes per launch: per rest and
+    order a, a terms on the partly used order and DP - 1 - a on the rest (DP = 16 or
+    32 pmf slots, zero past dmax), i.e. G (DP - 1) per rest."""
+    p = inst.products[0]
+    G = p.Q + 1
+    DP = 16 if p.dmax < 16 else 32
+    return (p.n_states // G) * G * (DP - 1)
 
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu captures
-# summarised in profiles/sweep_group_*.md; an entry is dropped when that kernel changes
+# summarised in profiles/; an entry is dropped when that kernel changes
 NCU_TRAFFIC = {
     ("cfg2_m5L2Q20_nb_fifo", "sweep_group_kernel (lane width 21)"): 34_112_768,
-    ("cfg4_m8L1Q10_lifo", "sweep_group_kernel (lane width 11)"): 393_176_064,
-    ("cfg2_m5L2Q20_nb_fifo", "sweep_tc_kernel"): 34_158_336,
+    ("cfg4_m8L1Q10_lifo", "sweep_lifo1_kernel"): 392_813_312,
 }
 
 
@@ -302,6 +314,101 @@ def l2_read_peak_gbs(vi, torch) -> float:
     reps = 64
     best = min(vi.vi_probe_l2_read(buf, nbytes, reps) for _ in range(3))
     return nbytes * reps / (best * 1e-3) / 1e9
+
+
+def kernel_name_of(vi, inst, kch, kw) -> str:
+    if len(inst.products) == 2 and kch == vi.VI_KERNEL_GROUP:
+        return ("twop_e2_kernel + twop_mix_kernel + twop_sweep_kernel" if inst.products[0].L >= 2
+                else "two_e2_kernel + two_mix_kernel + sweep_two_kernel")
+    return {vi.VI_KERNEL_GENERIC: "sweep_generic_kernel", vi.VI_KERNEL_TENSOR: "sweep_tc_kernel",
+            vi.VI_KERNEL_LIFO_L1: "sweep_lifo1_kernel"}.get(kch, f"sweep_group_kernel (lane width {kw})")
+
+
+def time_sweep_kernel(vi, torch, h, V, stream, flush, reps: int = 20) -> float:
+    """Average duration of the dominant kernel: back-to-back single sweeps (vi_backup,
+    the same kernel and grid as the solve) between CUDA events on the launching stream."""
+    V2 = torch.empty_like(V)
+    vi.vi_backup(h, V, V2, None, stream=stream, stats=False)
+    flush.fill_(1.0)
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for i in range(reps):
+        if i % 2 == 0:
+            vi.vi_backup(h, V, V2, None, stream=stream, stats=False)
+        else:
+            vi.vi_backup(h, V2, V, None, stream=stream, stats=False)
+    k1.record(stream)
+    k1.synchronize()
+    return k0.elapsed_time(k1) / reps
+
+
+def roofline_of(vi, torch, inst, kernel_name: str, k_ms: float, sm_mhz: float, l2_gbs) -> dict:
+    """FP32 ALU roofline of the dominant kernel: the method's multiply-adds per launch
+    against SMs x 128 FP32 lanes x 2 flop x the median SM clock sampled in the run,
+    with the HBM fraction of the compulsory traffic and the gather ratio beside it."""
+    work = algorithmic_work(inst)
+    pk = peaks()
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = work["flops"] / (k_ms * 1e-3) / 1e12
+    hbm_gbs = work["bytes"] / (k_ms * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC.get((inst.name, kernel_name))
+    out = {
+        "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+        "traffic": traffic, "kernel": kernel_name, "kernel_ms": k_ms, "work": work["work"],
+        "peak_basis": f"{n_sm} SMs (device property) x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz "
+                      f"(median SM clock sampled during the timed solves)",
+        "hbm": {"compulsory_bytes": work["bytes"], "achieved_GBs": hbm_gbs, "peak_GBs": pk["hbm_gbs"],
+                "frac": hbm_gbs / pk["hbm_gbs"], "peak_source": pk["source"],
+                "basis": "16 B per state per sweep: the previous value read and the new one written "
+                         "(float pairs)",
+                "measured_dram_GBs": None if traffic is None else traffic / (k_ms * 1e-3) / 1e9},
+    }
+    if kernel_name == "sweep_lifo1_kernel":
+        fm = lifo1_executed_fmas(inst)
+        out["executed_fmas_per_launch"] = fm
+        out["executed_fp32_frac"] = 2 * fm / (k_ms * 1e-3) / 1e12 / fp32_peak
+    if len(inst.products) == 1 and l2_gbs:
+        g = work["updates"] * 4 / (k_ms * 1e-3) / 1e9
+        out["gather"] = {"logical_GBs": g, "l2_read_peak_GBs": l2_gbs, "ratio": g / l2_gbs,
+                         "note": "not a bound: the factorised sweeps gather each next-state value once per "
+                                 "rest and order (FIFO) or once per rest (LIFO), not once per update"}
+    return out
+
+
+def solve_summary(vi, torch, inst, args, stream, flush, steps: int, warmup: int) -> dict:
+    """A secondary workload: timed solves (L2 flushed between them) and its dominant
+    kernel, with the same metric and roofline as the headline."""
+    prods = [dict(m=q.m, L=q.L, Q=q.Q, cost=q.cost, pmf=q.pmf) for q in inst.products]
+    desc, keep = vi.make_desc(prods, inst.gamma, inst.issuing, vi.VI_PREC_FP32, vi.VI_STOP_SPAN, inst.subst_rate)
+    h = vi.vi_problem_create_desc(desc)
+    try:
+        sizes = vi.vi_problem_sizes(h)
+        n = sizes["n_states"]
+        V = torch.empty(n, dtype=torch.float64, device="cuda")
+        pol = torch.empty(n, dtype=torch.uint8, device="cuda")
+        nominal = float(n) * sizes["n_actions"] * sizes["n_outcomes"]
+        for _ in range(warmup):
+            vi.vi_solve(h, TOL, args.max_iters, V, pol, stream=stream)
+        ms, iters = [], []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = vi.vi_solve(h, TOL, args.max_iters, V, pol, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            iters.append(info["iters"])
+        k_ms = time_sweep_kernel(vi, torch, h, V, stream, flush)
+        kch, kw = vi.vi_problem_kernel(h)
+        return {"workload": inst.name, "states": n, "value": nominal * sum(iters) / (sum(ms) * 1e-3),
+                "unit": UNIT, "ms_per_solve": sum(ms) / len(ms), "sweeps_per_solve": iters[-1],
+                "kernel": kernel_name_of(vi, inst, kch, kw), "kernel_ms": k_ms}
+    finally:
+        vi.vi_problem_destroy(h)
 
 
 def run_native(args):
@@ -361,50 +468,14 @@ def run_native(args):
     updates = nominal * sum(iters)
     value = replica_value(updates, dev_s_max, world)
 
-    # dominant kernel: one sweep launch (same kernel, same grid) timed with events
-    V2 = torch.empty_like(V)
-    reps = 20
-    vi.vi_backup(h, V, V2, None, stream=stream, stats=False)
-    flush.fill_(1.0)
-    k0 = torch.cuda.Event(enable_timing=True)
-    k1 = torch.cuda.Event(enable_timing=True)
-    k0.record(stream)
-    for i in range(reps):
-        if i % 2 == 0:
-            vi.vi_backup(h, V, V2, None, stream=stream, stats=False)
-        else:
-            vi.vi_backup(h, V2, V, None, stream=stream, stats=False)
-    k1.record(stream)
-    k1.synchronize()
-    k_ms = k0.elapsed_time(k1) / reps
+    # dominant kernel: single sweep launches (same kernel, same grid) timed with events
+    k_ms = time_sweep_kernel(vi, torch, h, V, stream, flush)
     kch, kw = vi.vi_problem_kernel(h)
-    kernel_name = {vi.VI_KERNEL_GENERIC: "sweep_generic_kernel", vi.VI_KERNEL_TENSOR: "sweep_tc_kernel",
-                   vi.VI_KERNEL_LIFO_L1: "sweep_lifo1_kernel"}.get(
-        kch, f"sweep_group_kernel (lane width {kw})")
-    if len(inst.products) == 2 and kch == vi.VI_KERNEL_GROUP:
-        kernel_name = ("twop_e2_kernel + twop_mix_kernel + twop_sweep_kernel" if inst.products[0].L >= 2
-                       else "two_e2_kernel + two_mix_kernel + sweep_two_kernel")
-    work = algorithmic_work(inst)
+    kernel_name = kernel_name_of(vi, inst, kch, kw)
     pk = peaks()
     sm_mhz = clocks.get("sm_mhz") or pk["sm_max_mhz"]
-    fp32_peak_tflops = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    achieved_tflops = work["flops"] / (k_ms * 1e-3) / 1e12
     l2_gbs = l2_read_peak_gbs(vi, torch)
-    gather_gbs = work["updates"] * 4 / (k_ms * 1e-3) / 1e9
-    roofline = {
-        "bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-        "frac": achieved_tflops / fp32_peak_tflops, "traffic": NCU_TRAFFIC.get((inst.name, kernel_name)),
-        "kernel": kernel_name, "kernel_ms": k_ms,
-        "work": work["work"],
-        "peak_basis": f"148 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock sampled)",
-        # one product: every nominal update gathers one next-state value; the
-        # two-product method does not expand the joint outcomes, so no such model
-        "gather": None if len(inst.products) == 2 else {
-            "logical_GBs": gather_gbs, "l2_read_peak_GBs": l2_gbs, "frac": gather_gbs / l2_gbs,
-            "basis": "4 B of next-state value per update vs an L1-bypassing read of a 32 MiB "
-                     "L2-resident buffer (measured here)"},
-        "hbm_compulsory_GBs": work["bytes"] / (k_ms * 1e-3) / 1e9, "hbm_peak_GBs": pk["hbm_gbs"],
-    }
+    roofline = roofline_of(vi, torch, inst, kernel_name, k_ms, sm_mhz, l2_gbs)
 
     # policy rollouts (row a12): 4096 rollouts x 365 periods of the extracted policy
     rollouts = None
@@ -476,6 +547,12 @@ def run_native(args):
     paper_b = run_paper_scenario_b(vi, torch, stream) if (rank == 0 and "b" in args.paper) else None
     paper_c = run_paper_scenario_c(vi, torch, stream, args.no_graph) if (rank == 0 and "c" in args.paper) else None
     serving = run_serving(args.serving) if (args.serving > 0 and rank == 0) else None
+    # the other large single-product configuration (4,084,101 states, FIFO, lead time 2)
+    extra = None
+    if rank == 0 and args.extra and args.workload != "cfg2":
+        x = solve_summary(vi, torch, workloads.config2(), args, stream, flush, steps=5, warmup=2)
+        x["roofline"] = roofline_of(vi, torch, workloads.config2(), x["kernel"], x["kernel_ms"], sm_mhz, l2_gbs)
+        extra = x
     if rank == 0:
         cpu = oracle_sample_rate(inst, args.cpu_seconds) if args.cpu_seconds > 0 else None
         out = {
@@ -495,13 +572,15 @@ def run_native(args):
                     "steps": e2e_steps, "includes": "vi_problem_create + vi_solve_host + vi_problem_destroy"},
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind",
                                                                            "sample")},
-            "serving": serving,
             "rollouts": rollouts,
             "policy_search": policy_search,
             "paper_scenario_a": paper_a,
             "paper_scenario_b": paper_b,
             "paper_scenario_c": paper_c,
             "wall_s": wall,
+            # last, so that they stay in the tail of the line
+            "cfg2": extra,
+            "serving": serving,
         }
         print(json.dumps(out))
     vi.vi_problem_destroy(h)
@@ -793,7 +872,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="cfg4", choices=sorted(WORKLOADS))
+    ap.add_argument("--extra", type=int, default=1, help="also measure the 4.08M-state config 2 (0 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle sample length (0 = skip)")
     ap.add_argument("--precision", default=None, choices=["fp32", "fp32_kahan", "fp64", "fp32_single"])
     ap.add_argument("--max-iters", type=int, default=MAX_ITERS)
