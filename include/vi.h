@@ -362,14 +362,17 @@ vi_status vi_basestock_search(vi_handle h, int s_lo, int s_hi, int n_rollouts, i
  * instances with 2 <= Q+1 <= 24 and at least one state digit, solved in
  * VI_PREC_FP32 with the span stopping test -- wait in arrival order and are
  * admitted while a slot is free and their device memory (about 17 bytes per
- * state) fits mem_budget_bytes.  A host worker thread with its own stream runs
- * one batched sweep launch over all admitted instances per iteration, so
- * instances of different sizes advance together; an instance whose stopping
- * test passed gets its extraction sweep in the next launch and is then
- * retired, freeing memory for queued requests.  Value buffers come from a
- * memory pool of the server's own that keeps freed memory reserved up to the
- * budget (min(budget, 1 GiB) is reserved at creation).  `stream` is unused (the
- * worker owns a stream); max_slots in 1..1024. */
+ * state) fits mem_budget_bytes.  A host worker thread with its own stream keeps
+ * one persistent kernel launch running over all admitted instances: its blocks
+ * claim blocks of the instances' current sweeps (largest instances first), and
+ * each instance's next sweep -- or its extraction sweep once its stopping test
+ * has passed -- starts as soon as its previous one has finished, so instances of
+ * different sizes advance together, each at its own pace.  A finished instance
+ * is retired between launches, freeing memory for queued requests; its values
+ * and policy are copied to host memory by retirement threads.  Value buffers
+ * come from a memory pool of the server's own that keeps freed memory reserved
+ * up to the budget (min(budget, 1 GiB) is reserved at creation).  `stream` is
+ * unused (the worker owns a stream); max_slots in 1..1024. */
 vi_status vi_server_create(size_t mem_budget_bytes, int max_slots, void *stream, vi_server *out);
 /* Queue a request; returns at once with its id.  The description is copied.
  * VI_EINVAL for a bad description, VI_EBUSY if it can never fit the budget. */

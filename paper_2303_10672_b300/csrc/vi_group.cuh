@@ -20,7 +20,19 @@ namespace vib {
 // gathered values; each chunk first walks the next-state indices, then issues
 // all of its loads, then consumes them, so the loads overlap.
 // ===========================================================================
-template <int XW, int LIFO, int VK, int LPIPE>
+// Value loads of the body.  A sweep launch reads values that no block of the same
+// launch writes, through the read-only path (COH = 0).  The server's persistent
+// launch runs many sweeps: a block reads values that other blocks of the same
+// launch wrote in the previous sweep, after an acquire fence, so it uses ordinary
+// (ld.global.ca, coherent after the fence) loads (COH = 1), written as the load
+// intrinsic so that the gathers of a batch are still issued together.
+template <int COH, typename T>
+__device__ __forceinline__ T vload(const T *p) {
+    if constexpr (COH) return __ldca(p);
+    else return __ldg(p);
+}
+
+template <int XW, int LIFO, int VK, int LPIPE, int COH = 0>
 __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid, unsigned n_blocks, int mode,
                                            const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int lpr,
                                            unsigned char *smem_raw) {
@@ -103,7 +115,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
         Rrest = ri.R;
         const float *V1 = (const float *)B.vin;
         const float2 *V2 = (const float2 *)B.vin;
-        if (PAIR) R0 = __ldg(V2 + r);   // s'_0 of action 0
+        if (PAIR) R0 = vload<COH>(V2 + r);   // s'_0 of action 0
         if (shared_fifo) {
             // FIFO: the demand reaching the rest slots empties them oldest first; that path
             // (relative to the rest index r) is the same for every order
@@ -131,8 +143,8 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
             // left) and H[k] = V[state r after k units issued LIFO from X_{m-1}..X_2]
             const int nH = min(ri.R, dmax) + 1;
             auto value = [&](uint32_t i) -> float {
-                if (PAIR) return pair_diff(__ldg(V2 + i), R0);
-                return __ldg(V1 + i);
+                if (PAIR) return pair_diff(vload<COH>(V2 + i), R0);
+                return vload<COH>(V1 + i);
             };
             for (int j0 = 0; j0 < G; j0 += LCS) {
                 float v[LCS];
@@ -218,9 +230,9 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
             if (shared_lifo)
                 ref = R0;   // all shared values are measured from R0
             else if (PAIR)
-                ref = __ldg(V2 + idx0);
+                ref = vload<COH>(V2 + idx0);
             else
-                g0 = __ldg(V1 + idx0);
+                g0 = vload<COH>(V1 + idx0);
             // accumulators in pairs of x, so that the widest FIFO correlations run on
             // packed two-lane FMAs (each lane rounds exactly as fmaf)
             float2 acc2[(XW + 1) / 2];
@@ -262,7 +274,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                 constexpr bool early_tail = PAIR && LPIPE;
                 float2 rawR = make_float2(0.f, 0.f);
                 if constexpr (early_tail) {
-                    if (shared_fifo && R >= 1 && x0 + R <= dmax) rawR = __ldg(V2 + tail_rel + atop);
+                    if (shared_fifo && R >= 1 && x0 + R <= dmax) rawR = vload<COH>(V2 + tail_rel + atop);
                 }
                 int ecur = 0;
                 // index of g(e); e never decreases between calls (the walker moves forward)
@@ -276,8 +288,8 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                     return wk.idx;
                 };
                 auto value_of = [&](uint32_t i) -> float {
-                    if (PAIR) return pair_diff(__ldg(V2 + i), ref);
-                    return __ldg(V1 + i);
+                    if (PAIR) return pair_diff(vload<COH>(V2 + i), ref);
+                    return vload<COH>(V1 + i);
                 };
                 const int kend = min(R - 1, dmax - x0);   // last k carrying mass for some x of this lane
                 // window of chunk k0 (k0 = 1 mod 4): p[x0 + k0 + i] = copy_o[x0 + k0 - o + i]
@@ -299,7 +311,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                     if (PAIR) {
                         float2 raw[KW];
 #pragma unroll
-                        for (int j = 0; j < KW; ++j) raw[j] = __ldg(V2 + idx[j]);
+                        for (int j = 0; j < KW; ++j) raw[j] = vload<COH>(V2 + idx[j]);
                         if (PACKED && preclamped && shared_fifo) {
                             // (raw - ref) per half as one packed fma(ref, -1, raw), then the
                             // halves added: the same rounding as pair_diff
@@ -318,7 +330,7 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                         }
                     } else {
 #pragma unroll
-                        for (int j = 0; j < KW; ++j) g[j] = (k0 + j <= kend) ? __ldg(V1 + idx[j]) : 0.f;
+                        for (int j = 0; j < KW; ++j) g[j] = (k0 + j <= kend) ? vload<COH>(V1 + idx[j]) : 0.f;
                     }
                     if constexpr (PACKED) {
 #pragma unroll
@@ -414,12 +426,12 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
                     if (PAIR) {
                         float2 raw[LCH];
 #pragma unroll
-                        for (int j = 0; j < LCH; ++j) raw[j] = __ldg(V2 + idx[j]);
+                        for (int j = 0; j < LCH; ++j) raw[j] = vload<COH>(V2 + idx[j]);
 #pragma unroll
                         for (int j = 0; j < LCH; ++j) gv[j] = pair_diff(raw[j], ref);
                     } else {
 #pragma unroll
-                        for (int j = 0; j < LCH; ++j) gv[j] = __ldg(V1 + idx[j]);
+                        for (int j = 0; j < LCH; ++j) gv[j] = vload<COH>(V1 + idx[j]);
                     }
 #pragma unroll
                     for (int j = 0; j < LCH; ++j) c = fmaf(s_p[d0 + j], gv[j], c);   // zero mass beyond dmax

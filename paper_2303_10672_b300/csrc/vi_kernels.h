@@ -82,15 +82,35 @@ bool tc_supported(const KernelParams &kp, int vk, int kahan);
 cudaError_t describe_tc(const KernelParams &kp, LaunchDesc &d);
 int batch_width(int G);
 void batch_geometry(const KernelParams &kp, int *lpr, uint32_t *blocks, size_t *smem);
-// loads every batched variant and sets its shared-memory limit (before the first launch)
+// loads the persistent server kernel and sets its shared-memory limit (before the first launch)
 cudaError_t prepare_sweep_batch();
 // loads the server's helper kernels (status gather, FP64 conversion, solve init)
 cudaError_t prepare_server_helpers();
-// variant of the batched kernel: 2 * LIFO + (L >= 2); one launch per (lane width, variant)
+// variant of the factorised body an instance runs in the server: 2 * LIFO + (L >= 2)
 int batch_variant(const KernelParams &kp);
-cudaError_t launch_sweep_batch(int xw, int variant, const KernelParams *kps, const int *modes, const int *lprs,
-                               const uint32_t *block_start, int n_slots, uint32_t total_blocks, size_t smem,
-                               cudaStream_t stream);
+
+// One admitted instance of the solve server, as the persistent server kernel sees it.
+// Blocks of the kernel claim the blocks of an instance's current sweep from `ticket`
+// (next block index in the low 32 bits); the block that completes a sweep's last
+// block publishes the next sweep (or the extraction, once the stopping test passed)
+// by resetting the ticket, so every instance advances at its own pace.
+constexpr unsigned kSrvClosed = 0xFFFFFFFFu;   // low ticket word of an instance with nothing to claim
+struct SrvSlot {
+    unsigned long long ticket;   // (sweeps published << 32) | next unclaimed block of the current sweep
+    unsigned done;               // blocks of the current sweep that have finished
+    int mode;                    // MODE_SWEEP or MODE_EXTRACT for the current sweep
+    int phase;                   // 0 sweeping, 1 extracting, 2 finished (extraction written)
+    unsigned nblocks;            // blocks per sweep
+    int xw, variant, lpr;        // body of the instance: lane width, variant, lanes per rest
+    int pad;
+};
+// the persistent server kernel: blocks claim work over the instances listed in act[0..n_act)
+// until every one has finished, budget_ns of device time have passed, or (finish_exit_ns
+// > 0) one has finished after the launch ran finish_exit_ns (a bounded number of polls in
+// any case)
+cudaError_t launch_serve(const KernelParams *kps, SrvSlot *slots, const int *act, int n_act, size_t smem,
+                         unsigned long long budget_ns, unsigned long long finish_exit_ns, unsigned *finished,
+                         cudaStream_t stream);
 struct SlotStatus {
     int iter, keep_going, converged, pad;
     double crit;

@@ -2,17 +2,21 @@
 //
 // A host worker thread owns one CUDA stream.  Requests wait in a FIFO queue and
 // are admitted, in order, while a slot is free and their device memory (value
-// ping-pong and policy) fits the budget.  Each iteration of the worker runs a few
-// batched sweeps over all admitted instances -- one launch per lane-width class
-// and sweep, each block finding its instance from a prefix sum of block counts --
-// so instances of different sizes advance together, then reads every slot's
-// status once.  An instance whose stopping test passed gets an extraction sweep
-// in the next iteration; its values are converted to FP64 on the device and a
-// retirement thread copies them (and the policy) to pinned host memory on a
-// second stream and releases the buffers, while the worker carries on.  The
-// pinned result buffers come from a free list of the server's (power-of-two
-// sizes) and go back to it when the caller polls the result: fresh pageable
-// memory would cost a zero-fill and a page fault per page of every result.
+// ping-pong and policy) fits the budget.  Each pass of the worker is one launch
+// of the persistent server kernel (vi_batch.cu) over every admitted instance:
+// its blocks claim blocks of the instances' current sweeps, largest instances
+// first, and each instance's next sweep -- or its extraction sweep, once its
+// stopping test has passed -- opens as soon as its previous one has finished, so
+// instances of every size and lane width advance together, each at its own
+// pace, with no host round trip between sweeps.  A launch runs until its budget
+// of device time is spent, every instance has finished, or -- while requests
+// wait for a slot -- one has finished.  The worker enqueues the next pass before
+// it reads the outcome of the previous one, so the device does not wait for the
+// host.  A finished instance's values are converted to FP64 on the device and a
+// retirement thread copies them and the policy to host memory, through two
+// pinned staging chunks of its own, on a stream of its own, and releases the
+// device buffers.  No host buffer is pinned per request: pinning (and the driver
+// lock it holds) had stalled the worker's own calls.
 //
 // Slots own their expectation tables, solve state and pinned upload staging for
 // the server's lifetime; value and policy buffers come from the stream-ordered
@@ -44,13 +48,16 @@ using namespace vib;
 namespace {
 
 constexpr int kSlotTabFloats = 16384;   // expectation-table capacity of a slot (64 KiB)
-constexpr int kSweepsPerCheck = 4;      // batched sweeps between two status reads (small batches)
-// Above this many active states a batched sweep outlasts the status round trip,
-// and further sweeps would only delay the extraction of instances that stopped.
-constexpr double kOneSweepStates = 1 << 20;
-// retirement threads: results written straight into the callers' (pageable) buffers
-// are mostly page faults and copies on the host, which several threads overlap
-constexpr int kRetireThreads = 2;
+// device time one launch of the server kernel may run before the worker looks at
+// the queue again; while requests wait for a slot, a launch also ends once an
+// instance has finished and it has run kPassMinNs (ending at every finish would
+// leave the device mostly waiting for the launches' slowest blocks)
+constexpr unsigned long long kPassBudgetNs = 1000000ull;
+constexpr unsigned long long kPassMinNs = 200000ull;
+// retirement threads: results written into the callers' (pageable) buffers are
+// mostly page faults and copies on the host, which several threads overlap
+constexpr int kRetireThreads = 4;
+constexpr size_t kRetireStageBytes = (size_t)4 << 20;   // one of a thread's two pinned staging chunks
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -72,9 +79,8 @@ struct Request {
     vi_status status = VI_OK;
     int iters = 0;
     double crit = 0.0;
-    double *V = nullptr;           // pinned result buffers (from the server's free list)
+    double *V = nullptr;           // host result buffers (malloc) held until the poll, unless delivered
     uint8_t *policy = nullptr;
-    size_t V_cap = 0, policy_cap = 0;
     double *dst_V = nullptr;       // vi_server_submit_to: the caller's host buffers, written at retirement
     uint8_t *dst_policy = nullptr;
 };
@@ -86,6 +92,7 @@ struct Slot {
     void *scratch = nullptr;       // ping-pong partner, then the FP64 result
     uint8_t *policy = nullptr;
     int mode = MODE_SWEEP;
+    uint64_t gen = 0;              // occupant count: a pass's status names the occupant it was read for
     int xw = 0, variant = 0, lpr = 0;
     uint32_t blocks = 0;
     size_t smem = 0;
@@ -123,47 +130,27 @@ struct vi_server_s {
     std::condition_variable retire_cv;
     bool stop = false, retire_stop = false;
     uint64_t next_id = 1;
-    std::multimap<size_t, void *> pinned_free;   // pinned result buffers by capacity (guarded by mu)
+    void *rstage[kRetireThreads] = {};           // pinned staging of each retirement thread: two chunks
+    cudaEvent_t rstage_ev[kRetireThreads][2] = {};
     std::deque<uint64_t> completed;               // finished, not yet reported by vi_server_wait
     std::condition_variable done_cv;
     vi_status fatal = VI_OK;
     char fatal_msg[256] = "";
-    // batch descriptors (device) and their pinned host mirrors
+    // per slot: kernel parameters and the server kernel's descriptor (device), with
+    // pinned staging written at admission; the pass lists (active slots, their
+    // state pointers, status, descriptors read back) have two pinned halves of
+    // n_desc entries, one per pass in flight
+    int n_desc = 0;
     KernelParams *d_kps = nullptr, *h_kps = nullptr;
-    int *d_modes = nullptr, *h_modes = nullptr;
-    int *d_modes_sweep = nullptr;     // MODE_SWEEP for every slot: the later sweeps of an iteration
-    int *d_lprs = nullptr, *h_lprs = nullptr;
-    uint32_t *d_bstart = nullptr, *h_bstart = nullptr;
+    SrvSlot *d_srv = nullptr, *h_srv = nullptr;
+    SrvSlot *h_srv_back = nullptr;    // descriptors read back after a pass (two halves)
+    int *d_act = nullptr, *h_act = nullptr;
+    unsigned *d_finished = nullptr;   // instances finished during the current launch
     SolveState **d_sts = nullptr, **h_sts = nullptr;
     SlotStatus *d_status = nullptr, *h_status = nullptr;
 };
 
 static size_t request_bytes(uint64_t n) { return (size_t)n * (8 + 8 + 1) + (1 << 16); }
-
-// a pinned host buffer of at least `bytes` (power-of-two capacity, 64 KiB or more)
-static void *pinned_get(vi_server_s *srv, size_t bytes, size_t *cap) {
-    size_t c = (size_t)1 << 16;
-    while (c < bytes) c <<= 1;
-    {
-        std::lock_guard<std::mutex> lk(srv->mu);
-        auto it = srv->pinned_free.find(c);
-        if (it != srv->pinned_free.end()) {
-            void *p = it->second;
-            srv->pinned_free.erase(it);
-            *cap = c;
-            return p;
-        }
-    }
-    void *p = nullptr;
-    if (cudaMallocHost(&p, c) != cudaSuccess) return nullptr;
-    *cap = c;
-    return p;
-}
-
-// caller holds srv->mu
-static void pinned_put_locked(vi_server_s *srv, void *p, size_t cap) {
-    if (p) srv->pinned_free.emplace(cap, p);
-}
 
 static bool server_shape_ok(const vi_problem_desc &d) {
     if (d.n_products != 1) return false;
@@ -184,6 +171,7 @@ static void set_fatal(vi_server_s *srv, const char *what, cudaError_t e) {
 // admit a request into a free slot (worker thread; nothing here waits for the device)
 static vi_status slot_open(vi_server_s *srv, Slot &sl, std::shared_ptr<Request> req) {
     sl.req = req;
+    sl.gen += 1;
     sl.kp = req->kp;
     const uint32_t n = sl.kp.nS;
     memcpy(sl.h_tab, req->ftab.data(), req->ftab.size() * sizeof(float));
@@ -215,6 +203,24 @@ static vi_status slot_open(vi_server_s *srv, Slot &sl, std::shared_ptr<Request> 
     sl.xw = batch_width(sl.kp.p[0].G);
     sl.variant = batch_variant(sl.kp);
     batch_geometry(sl.kp, &sl.lpr, &sl.blocks, &sl.smem);
+    // the instance's parameters and its descriptor for the server kernel
+    const int idx = (int)(&sl - srv->slots.data());
+    srv->h_kps[idx] = sl.kp;
+    SrvSlot &d = srv->h_srv[idx];
+    memset(&d, 0, sizeof(d));
+    d.ticket = 0ull;
+    d.done = 0u;
+    d.mode = sl.mode;
+    d.phase = (sl.mode == MODE_EXTRACT) ? 1 : 0;
+    d.nblocks = sl.blocks;
+    d.xw = sl.xw;
+    d.variant = sl.variant;
+    d.lpr = sl.lpr;
+    if ((e = cudaMemcpyAsync(srv->d_kps + idx, srv->h_kps + idx, sizeof(KernelParams), cudaMemcpyHostToDevice,
+                             srv->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(srv->d_srv + idx, &d, sizeof(SrvSlot), cudaMemcpyHostToDevice, srv->stream)) !=
+            cudaSuccess)
+        return vi_fail(VI_ECUDA, "server slot init: %s", cudaGetErrorString(e));
     return VI_OK;
 }
 
@@ -239,9 +245,35 @@ static void finish(vi_server_s *srv, Request &rq, vi_status st) {
     srv->done_cv.notify_all();
 }
 
-// retirement thread: wait for a finished instance's FP64 conversion, copy the
-// values and the policy to host memory (the caller's buffers given at submission,
-// else pinned buffers of the server's), release the device buffers
+// device -> host copy of n bytes through the thread's two pinned staging chunks: the
+// copy of one chunk runs while the previous one is copied on into dst on the host
+// (a direct copy into pageable memory would be synchronous in the driver)
+static cudaError_t copy_out(vi_server_s *srv, int k, void *dst, const void *src, size_t n) {
+    cudaStream_t rs = srv->rstream[k];
+    char *stage[2] = {(char *)srv->rstage[k], (char *)srv->rstage[k] + kRetireStageBytes};
+    const size_t nc = (n + kRetireStageBytes - 1) / kRetireStageBytes;
+    cudaError_t e = cudaSuccess;
+    auto issue = [&](size_t c) {
+        const size_t off = c * kRetireStageBytes, len = std::min(kRetireStageBytes, n - off);
+        cudaError_t r = cudaMemcpyAsync(stage[c & 1], (const char *)src + off, len, cudaMemcpyDeviceToHost, rs);
+        if (r == cudaSuccess) r = cudaEventRecord(srv->rstage_ev[k][c & 1], rs);
+        return r;
+    };
+    if (nc > 0) e = issue(0);
+    for (size_t c = 0; c < nc && e == cudaSuccess; ++c) {
+        if (c + 1 < nc) e = issue(c + 1);
+        if (e == cudaSuccess) e = cudaEventSynchronize(srv->rstage_ev[k][c & 1]);
+        if (e == cudaSuccess) {
+            const size_t off = c * kRetireStageBytes, len = std::min(kRetireStageBytes, n - off);
+            memcpy((char *)dst + off, stage[c & 1], len);
+        }
+    }
+    return e;
+}
+
+// retirement thread: copy a finished instance's FP64 values and policy to host
+// memory -- the caller's buffers given at submission, else host buffers the server
+// keeps until the poll -- and release its device buffers
 static void retire_loop(vi_server_s *srv, int k) {
     cudaStream_t rs = srv->rstream[k];
     while (true) {
@@ -255,37 +287,21 @@ static void retire_loop(vi_server_s *srv, int k) {
         }
         Request &rq = *job.req;
         vi_status st = VI_OK;
-        // device -> pinned staging (a pageable destination would make the copy
-        // synchronous and hold up the worker's launches), then, for
-        // vi_server_submit_to, a host copy into the caller's buffers on this thread
-        rq.V = (double *)pinned_get(srv, (size_t)job.n * 8, &rq.V_cap);
-        rq.policy = (uint8_t *)pinned_get(srv, job.n, &rq.policy_cap);
-        cudaError_t e;
-        if (!rq.V || !rq.policy) {
-            st = vi_fail(VI_ENOMEM, "server retire: no pinned host memory for the result");
+        double *dV = rq.dst_V;
+        uint8_t *dP = rq.dst_policy;
+        if (!dV) dV = rq.V = (double *)malloc((size_t)job.n * 8);
+        if (!dP) dP = rq.policy = (uint8_t *)malloc(job.n);
+        cudaError_t e = cudaSuccess;
+        if (!dV || !dP) {
+            st = vi_fail(VI_ENOMEM, "server retire: no host memory for the result");
         } else if ((e = cudaStreamWaitEvent(rs, job.ready, 0)) != cudaSuccess ||
-                   (e = cudaMemcpyAsync(rq.V, job.scratch, (size_t)job.n * 8, cudaMemcpyDeviceToHost, rs)) !=
-                       cudaSuccess ||
-                   (e = cudaMemcpyAsync(rq.policy, job.policy, job.n, cudaMemcpyDeviceToHost, rs)) != cudaSuccess ||
-                   (e = cudaStreamSynchronize(rs)) != cudaSuccess) {
+                   (e = copy_out(srv, k, dV, job.scratch, (size_t)job.n * 8)) != cudaSuccess ||
+                   (e = copy_out(srv, k, dP, job.policy, job.n)) != cudaSuccess) {
             st = vi_fail(VI_ECUDA, "server retire: %s", cudaGetErrorString(e));
         }
         cudaFreeAsync(job.V, rs);
         cudaFreeAsync(job.scratch, rs);
         cudaFreeAsync(job.policy, rs);
-        if (st == VI_OK && (rq.dst_V || rq.dst_policy)) {
-            if (rq.dst_V) memcpy(rq.dst_V, rq.V, (size_t)job.n * 8);
-            if (rq.dst_policy) memcpy(rq.dst_policy, rq.policy, job.n);
-            std::lock_guard<std::mutex> lk(srv->mu);
-            if (rq.dst_V) {
-                pinned_put_locked(srv, rq.V, rq.V_cap);
-                rq.V = nullptr;
-            }
-            if (rq.dst_policy) {
-                pinned_put_locked(srv, rq.policy, rq.policy_cap);
-                rq.policy = nullptr;
-            }
-        }
         cudaEventDestroy(job.ready);
         rq.iters = job.ss.iter;
         rq.crit = job.ss.crit;
@@ -294,55 +310,48 @@ static void retire_loop(vi_server_s *srv, int k) {
     }
 }
 
-// one launch per (lane width, variant) class over the active slots; modes from the
-// slots (first sweep of an iteration) or MODE_SWEEP for all (the later ones)
-static cudaError_t launch_round(vi_server_s *srv, const std::vector<int> &act, bool first) {
-    int koff = 0, boff = 0;
-    for (int cls = 0; cls < 5 * 4; ++cls) {
-        static const int widths[5] = {8, 12, 16, 21, 24};
-        const int xw = widths[cls / 4], variant = cls % 4;
-        const int kbase = koff, bbase = boff;
-        uint32_t total = 0;
-        size_t smem = 0;
-        for (int i : act) {
-            Slot &sl = srv->slots[i];
-            if (sl.xw != xw || sl.variant != variant) continue;
-            if (first) {
-                srv->h_kps[koff] = sl.kp;
-                srv->h_modes[koff] = sl.mode;
-                srv->h_lprs[koff] = sl.lpr;
-                srv->h_bstart[boff] = total;
-            }
-            ++boff;
-            total += sl.blocks;
-            smem = std::max(smem, sl.smem);
-            ++koff;
-        }
-        const int n_cls = koff - kbase;
-        if (n_cls == 0) continue;
-        if (first) srv->h_bstart[boff] = total;
-        ++boff;
-        cudaError_t e;
-        if (first) {
-            if ((e = cudaMemcpyAsync(srv->d_kps + kbase, srv->h_kps + kbase, sizeof(KernelParams) * n_cls,
-                                     cudaMemcpyHostToDevice, srv->stream)) != cudaSuccess ||
-                (e = cudaMemcpyAsync(srv->d_modes + kbase, srv->h_modes + kbase, sizeof(int) * n_cls,
-                                     cudaMemcpyHostToDevice, srv->stream)) != cudaSuccess ||
-                (e = cudaMemcpyAsync(srv->d_lprs + kbase, srv->h_lprs + kbase, sizeof(int) * n_cls,
-                                     cudaMemcpyHostToDevice, srv->stream)) != cudaSuccess ||
-                (e = cudaMemcpyAsync(srv->d_bstart + bbase, srv->h_bstart + bbase, sizeof(uint32_t) * (n_cls + 1),
-                                     cudaMemcpyHostToDevice, srv->stream)) != cudaSuccess)
-                return e;
-        }
-        e = launch_sweep_batch(xw, variant, srv->d_kps + kbase, (first ? srv->d_modes : srv->d_modes_sweep) + kbase,
-                               srv->d_lprs + kbase, srv->d_bstart + bbase, n_cls, total, smem, srv->stream);
-        if (e != cudaSuccess) return e;
-    }
+// a pass of batched sweeps whose status has not been read yet
+struct Pass {
+    bool valid = false;
+    int buf = 0;                   // half of the pinned staging it used
+    std::vector<int> slot;         // active slots, in the order of the status array
+    std::vector<uint64_t> gen;     // their occupants when the pass was enqueued
+};
+
+// hand a slot whose extraction has run to a retirement thread
+static cudaError_t retire_slot(vi_server_s *srv, Slot &sl, const SlotStatus &ss) {
+    RetireJob job;
+    job.req = sl.req;
+    job.V = sl.V;
+    job.scratch = sl.scratch;
+    job.policy = sl.policy;
+    job.n = sl.kp.nS;
+    job.ss = ss;
+    cudaError_t e;
+    // FP64 values into the scratch buffer, after every sweep enqueued so far
+    if ((e = launch_to_fp64(sl.V, VK_PAIR, 0.0, (double *)sl.scratch, job.n, srv->stream)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&job.ready, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventRecord(job.ready, srv->stream)) != cudaSuccess)
+        return e;
+    sl.V = sl.scratch = nullptr;
+    sl.policy = nullptr;
+    sl.req.reset();
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->retire_q.push_back(job);
+    srv->retire_cv.notify_one();
     return cudaSuccess;
 }
 
 static void worker_loop(vi_server_s *srv) {
     const int cap = srv->max_slots;
+    cudaEvent_t pass_done[2] = {nullptr, nullptr};
+    for (auto &ev : pass_done)
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            set_fatal(srv, "server events", cudaGetLastError());
+            return;
+        }
+    Pass prev;
+    int buf = 0;
     while (true) {
         std::vector<std::shared_ptr<Request>> admit;
         {
@@ -358,7 +367,7 @@ static void worker_loop(vi_server_s *srv) {
                 admit.push_back(q);
                 srv->queue.pop_front();
             }
-            if (active == 0 && admit.empty()) {
+            if (active == 0 && admit.empty() && !prev.valid) {
                 srv->cv.wait_for(lk, std::chrono::milliseconds(2));
                 continue;
             }
@@ -371,73 +380,90 @@ static void worker_loop(vi_server_s *srv) {
                 finish(srv, *rq, st);
             }
         }
-        std::vector<int> act;
-        bool sweeping = false;
-        double states = 0.0;
+        // -- enqueue this pass: one launch of the server kernel over every admitted
+        // instance, then the status and the descriptors read back
+        Pass cur;
+        size_t smem = 0;
         for (int i = 0; i < cap; ++i)
             if (srv->slots[i].req) {
-                act.push_back(i);
-                sweeping |= (srv->slots[i].mode == MODE_SWEEP);
-                states += (double)srv->slots[i].kp.nS;
+                cur.slot.push_back(i);
+                smem = std::max(smem, srv->slots[i].smem);
             }
-        if (act.empty()) continue;
-        // a few sweeps back to back while the batch is small: an instance that stopped
-        // turns the later ones into no-ops
-        const int rounds = (sweeping && states < kOneSweepStates) ? kSweepsPerCheck : 1;
+        // largest instances first: the kernel claims work in this order, so the device
+        // works through one large sweep at a time and the small instances advance in the
+        // gaps while a large sweep's last blocks finish
+        std::stable_sort(cur.slot.begin(), cur.slot.end(),
+                         [srv](int a, int b) { return srv->slots[a].kp.nS > srv->slots[b].kp.nS; });
+        for (int i : cur.slot) cur.gen.push_back(srv->slots[i].gen);
         cudaError_t e = cudaSuccess;
-        for (int rd = 0; rd < rounds && e == cudaSuccess; ++rd) e = launch_round(srv, act, rd == 0);
-        if (e != cudaSuccess) {
-            set_fatal(srv, "batched sweep", e);
-            break;
-        }
-        for (size_t j = 0; j < act.size(); ++j) srv->h_sts[j] = srv->slots[act[j]].d_state;
-        if ((e = cudaMemcpyAsync(srv->d_sts, srv->h_sts, sizeof(SolveState *) * act.size(), cudaMemcpyHostToDevice,
-                                 srv->stream)) != cudaSuccess ||
-            (e = launch_gather_status(srv->d_sts, (int)act.size(), srv->d_status, srv->stream)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(srv->h_status, srv->d_status, sizeof(SlotStatus) * act.size(),
-                                 cudaMemcpyDeviceToHost, srv->stream)) != cudaSuccess ||
-            (e = cudaStreamSynchronize(srv->stream)) != cudaSuccess) {
-            set_fatal(srv, "server stream", e);
-            break;
-        }
-        for (size_t j = 0; j < act.size(); ++j) {
-            Slot &sl = srv->slots[act[j]];
-            const SlotStatus ss = srv->h_status[j];
-            if (sl.mode == MODE_EXTRACT) {
-                // extraction done: FP64 values into the scratch buffer, then hand over
-                RetireJob job;
-                job.req = sl.req;
-                job.V = sl.V;
-                job.scratch = sl.scratch;
-                job.policy = sl.policy;
-                job.n = sl.kp.nS;
-                job.ss = ss;
-                if ((e = launch_to_fp64(sl.V, VK_PAIR, 0.0, (double *)sl.scratch, job.n, srv->stream)) !=
-                        cudaSuccess ||
-                    (e = cudaEventCreateWithFlags(&job.ready, cudaEventDisableTiming)) != cudaSuccess ||
-                    (e = cudaEventRecord(job.ready, srv->stream)) != cudaSuccess) {
-                    set_fatal(srv, "server retire", e);
-                    break;
-                }
-                sl.V = sl.scratch = nullptr;
-                sl.policy = nullptr;
-                sl.req.reset();
+        if (!cur.slot.empty()) {
+            cur.valid = true;
+            cur.buf = buf;
+            const int na = (int)cur.slot.size();
+            int *h_act = srv->h_act + buf * srv->n_desc;
+            SolveState **h_sts = srv->h_sts + buf * srv->n_desc;
+            for (int j = 0; j < na; ++j) {
+                h_act[j] = cur.slot[j];
+                h_sts[j] = srv->slots[cur.slot[j]].d_state;
+            }
+            bool queued;
+            {
                 std::lock_guard<std::mutex> lk(srv->mu);
-                srv->retire_q.push_back(job);
-                srv->retire_cv.notify_one();
-            } else if (!ss.keep_going) {
-                sl.mode = MODE_EXTRACT;
+                queued = !srv->queue.empty();
+            }
+            if ((e = cudaMemcpyAsync(srv->d_act, h_act, sizeof(int) * na, cudaMemcpyHostToDevice, srv->stream)) !=
+                    cudaSuccess ||
+                (e = cudaMemsetAsync(srv->d_finished, 0, sizeof(unsigned), srv->stream)) != cudaSuccess ||
+                (e = launch_serve(srv->d_kps, srv->d_srv, srv->d_act, na, smem, kPassBudgetNs,
+                                  queued ? kPassMinNs : 0ull, srv->d_finished, srv->stream)) != cudaSuccess) {
+                set_fatal(srv, "server kernel", e);
+                break;
+            }
+            if ((e = cudaMemcpyAsync(srv->d_sts, h_sts, sizeof(SolveState *) * na, cudaMemcpyHostToDevice,
+                                     srv->stream)) != cudaSuccess ||
+                (e = launch_gather_status(srv->d_sts, na, srv->d_status, srv->stream)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(srv->h_status + buf * srv->n_desc, srv->d_status, sizeof(SlotStatus) * na,
+                                     cudaMemcpyDeviceToHost, srv->stream)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(srv->h_srv_back + buf * srv->n_desc, srv->d_srv, sizeof(SrvSlot) * cap,
+                                     cudaMemcpyDeviceToHost, srv->stream)) != cudaSuccess ||
+                (e = cudaEventRecord(pass_done[buf], srv->stream)) != cudaSuccess) {
+                set_fatal(srv, "server stream", e);
+                break;
             }
         }
-        if (e != cudaSuccess) break;
+        // -- the previous pass's outcome, read while this pass runs: an instance whose
+        // extraction has been written is handed to a retirement thread
+        if (prev.valid) {
+            if ((e = cudaEventSynchronize(pass_done[prev.buf])) != cudaSuccess) {
+                set_fatal(srv, "server stream", e);
+                break;
+            }
+            const SlotStatus *hs = srv->h_status + prev.buf * srv->n_desc;
+            const SrvSlot *hb = srv->h_srv_back + prev.buf * srv->n_desc;
+            for (size_t j = 0; j < prev.slot.size() && e == cudaSuccess; ++j) {
+                const int i = prev.slot[j];
+                Slot &sl = srv->slots[i];
+                if (!sl.req || sl.gen != prev.gen[j]) continue;   // retired since
+                if (hb[i].phase == 2) {
+                    e = retire_slot(srv, sl, hs[j]);
+                    if (e != cudaSuccess) set_fatal(srv, "server retire", e);
+                }
+            }
+            if (e != cudaSuccess) break;
+        }
+        prev = std::move(cur);
+        buf ^= 1;
     }
-    // cancel whatever is left
+    // cancel whatever is left once the last pass has finished
+    if (srv->stream) cudaStreamSynchronize(srv->stream);
     for (auto &sl : srv->slots)
         if (sl.req) {
             auto rq = sl.req;
             slot_release(srv, sl);
             finish(srv, *rq, VI_ECANCELLED);
         }
+    for (auto &ev : pass_done)
+        if (ev) cudaEventDestroy(ev);
     std::lock_guard<std::mutex> lk(srv->mu);
     for (auto &rq : srv->queue) {
         rq->status = VI_ECANCELLED;
@@ -458,7 +484,8 @@ extern "C" vi_status vi_server_create(size_t mem_budget_bytes, int max_slots, vo
     srv->budget = mem_budget_bytes;
     srv->max_slots = max_slots;
     srv->slots.resize(max_slots);
-    const int n = max_slots + 24;   // one extra block_start entry per (width, variant) class
+    const int n = max_slots;
+    srv->n_desc = n;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaError_t e;
@@ -488,22 +515,28 @@ extern "C" vi_status vi_server_create(size_t mem_budget_bytes, int max_slots, vo
             cudaGetLastError();   // not enough free memory to reserve now: grow on demand instead
         }
     }
+    for (int k = 0; k < kRetireThreads; ++k)
+        if ((e = cudaStreamCreateWithFlags(&srv->rstream[k], cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaMallocHost(&srv->rstage[k], 2 * kRetireStageBytes)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&srv->rstage_ev[k][0], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&srv->rstage_ev[k][1], cudaEventDisableTiming)) != cudaSuccess) {
+            vi_server_destroy(srv);
+            return vi_fail(e == cudaErrorMemoryAllocation ? VI_ENOMEM : VI_ECUDA, "server retirement set-up: %s",
+                           cudaGetErrorString(e));
+        }
     if ((e = cudaStreamCreateWithFlags(&srv->stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&srv->rstream[0], cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&srv->rstream[1], cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaMalloc(&srv->d_kps, sizeof(KernelParams) * n)) != cudaSuccess ||
-        (e = cudaMallocHost(&srv->h_kps, sizeof(KernelParams) * n)) != cudaSuccess ||
-        (e = cudaMalloc(&srv->d_modes, sizeof(int) * n)) != cudaSuccess ||
-        (e = cudaMalloc(&srv->d_modes_sweep, sizeof(int) * n)) != cudaSuccess ||
-        (e = cudaMallocHost(&srv->h_modes, sizeof(int) * n)) != cudaSuccess ||
-        (e = cudaMalloc(&srv->d_lprs, sizeof(int) * n)) != cudaSuccess ||
-        (e = cudaMallocHost(&srv->h_lprs, sizeof(int) * n)) != cudaSuccess ||
-        (e = cudaMalloc(&srv->d_bstart, sizeof(uint32_t) * n)) != cudaSuccess ||
-        (e = cudaMallocHost(&srv->h_bstart, sizeof(uint32_t) * n)) != cudaSuccess ||
+        (e = cudaMalloc(&srv->d_kps, sizeof(KernelParams) * max_slots)) != cudaSuccess ||
+        (e = cudaMallocHost(&srv->h_kps, sizeof(KernelParams) * max_slots)) != cudaSuccess ||
+        (e = cudaMalloc(&srv->d_srv, sizeof(SrvSlot) * max_slots)) != cudaSuccess ||
+        (e = cudaMallocHost(&srv->h_srv, sizeof(SrvSlot) * max_slots)) != cudaSuccess ||
+        (e = cudaMallocHost(&srv->h_srv_back, sizeof(SrvSlot) * 2 * n)) != cudaSuccess ||
+        (e = cudaMalloc(&srv->d_act, sizeof(int) * n)) != cudaSuccess ||
+        (e = cudaMallocHost(&srv->h_act, sizeof(int) * 2 * n)) != cudaSuccess ||
+        (e = cudaMalloc(&srv->d_finished, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMalloc(&srv->d_sts, sizeof(SolveState *) * n)) != cudaSuccess ||
-        (e = cudaMallocHost(&srv->h_sts, sizeof(SolveState *) * n)) != cudaSuccess ||
+        (e = cudaMallocHost(&srv->h_sts, sizeof(SolveState *) * 2 * n)) != cudaSuccess ||
         (e = cudaMalloc(&srv->d_status, sizeof(SlotStatus) * n)) != cudaSuccess ||
-        (e = cudaMallocHost(&srv->h_status, sizeof(SlotStatus) * n)) != cudaSuccess) {
+        (e = cudaMallocHost(&srv->h_status, sizeof(SlotStatus) * 2 * n)) != cudaSuccess) {
         vi_server_destroy(srv);
         return vi_fail(e == cudaErrorMemoryAllocation ? VI_ENOMEM : VI_ECUDA, "server setup: %s",
                        cudaGetErrorString(e));
@@ -520,14 +553,6 @@ extern "C" vi_status vi_server_create(size_t mem_budget_bytes, int max_slots, vo
     if ((e = prepare_sweep_batch()) != cudaSuccess || (e = prepare_server_helpers()) != cudaSuccess) {
         vi_server_destroy(srv);
         return vi_fail(VI_ECUDA, "server kernels: %s", cudaGetErrorString(e));
-    }
-    {
-        std::vector<int> sweep(n, MODE_SWEEP);
-        if ((e = cudaMemcpy(srv->d_modes_sweep, sweep.data(), sizeof(int) * n, cudaMemcpyHostToDevice)) !=
-            cudaSuccess) {
-            vi_server_destroy(srv);
-            return vi_fail(VI_ECUDA, "server setup: %s", cudaGetErrorString(e));
-        }
     }
     (void)stream;   // the server keeps its own streams so that its host loops never block the caller's
     srv->worker = std::thread([srv, dev]() {
@@ -598,13 +623,10 @@ extern "C" vi_status vi_server_poll(vi_server srv, uint64_t request_id, int *don
     }
     if (V_host && rq->V) memcpy(V_host, rq->V, (size_t)rq->n_states * sizeof(double));
     if (policy_host && rq->policy) memcpy(policy_host, rq->policy, (size_t)rq->n_states);
-    {
-        std::lock_guard<std::mutex> lk(srv->mu);
-        pinned_put_locked(srv, rq->V, rq->V_cap);
-        pinned_put_locked(srv, rq->policy, rq->policy_cap);
-        rq->V = nullptr;
-        rq->policy = nullptr;
-    }
+    free(rq->V);
+    free(rq->policy);
+    rq->V = nullptr;
+    rq->policy = nullptr;
     if (info) {
         memset(info, 0, sizeof(*info));
         info->iters = rq->iters;
@@ -660,22 +682,25 @@ extern "C" vi_status vi_server_destroy(vi_server srv) {
     }
     cudaFree(srv->d_kps);
     cudaFreeHost(srv->h_kps);
-    cudaFree(srv->d_modes);
-    cudaFree(srv->d_modes_sweep);
-    cudaFreeHost(srv->h_modes);
-    cudaFree(srv->d_lprs);
-    cudaFreeHost(srv->h_lprs);
-    cudaFree(srv->d_bstart);
-    cudaFreeHost(srv->h_bstart);
+    cudaFree(srv->d_srv);
+    cudaFreeHost(srv->h_srv);
+    cudaFreeHost(srv->h_srv_back);
+    cudaFree(srv->d_act);
+    cudaFreeHost(srv->h_act);
+    cudaFree(srv->d_finished);
     cudaFree(srv->d_sts);
     cudaFreeHost(srv->h_sts);
     cudaFree(srv->d_status);
     cudaFreeHost(srv->h_status);
     for (auto &kv : srv->all) {   // results that were never polled
-        if (kv.second->V) cudaFreeHost(kv.second->V);
-        if (kv.second->policy) cudaFreeHost(kv.second->policy);
+        free(kv.second->V);
+        free(kv.second->policy);
     }
-    for (auto &kv : srv->pinned_free) cudaFreeHost(kv.second);
+    for (int k = 0; k < kRetireThreads; ++k) {
+        if (srv->rstage[k]) cudaFreeHost(srv->rstage[k]);
+        for (auto ev : srv->rstage_ev[k])
+            if (ev) cudaEventDestroy(ev);
+    }
     if (srv->stream) cudaStreamDestroy(srv->stream);
     for (auto rs : srv->rstream)
         if (rs) cudaStreamDestroy(rs);
