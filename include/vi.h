@@ -74,13 +74,15 @@ enum { VI_STOP_SPAN = 0, VI_STOP_SUPNORM = 1, VI_STOP_PERIODIC = 2 };
  *                      differences between values; the absolute value is
  *                      rebuilt with error-free float transformations, so the
  *                      stopping test sees no FP32 rounding noise.
- *  VI_PREC_FP32_KAHAN  as VI_PREC_FP32 with compensated (Kahan) sums over outcomes
- *                      in the one-thread-per-state kernel (VI_KERNEL_GENERIC).
- *                      Two-product instances otherwise run the factorised
- *                      two-product sweep, whose sums are short (at most Dmax1+1
- *                      terms of product-2 expectations, each over at most
- *                      Dmax2+1 outcomes, all measured from nearby values) and
- *                      uncompensated in both FP32 modes.
+ *  VI_PREC_FP32_KAHAN  as VI_PREC_FP32 with compensated (Kahan) sums over
+ *                      outcomes: in the one-thread-per-state kernel
+ *                      (VI_KERNEL_GENERIC), which single-product instances run in
+ *                      this mode, and in the factorised two-product sweep for lead
+ *                      time one on both products (its product-2 expectation and
+ *                      substitution-mixture sums and its sum over product-1
+ *                      demand).  Two products with longer lead times run the
+ *                      generic kernel in this mode (their factorised pipeline
+ *                      form is not compensated).
  *  VI_PREC_FP64        FP64 arithmetic and storage, double[|S|].
  *  VI_PREC_FP32_SINGLE one float per state relative to an FP64 offset
  *                      (V = info.offset + v), float[|S|].  Fastest; its stopping
@@ -121,7 +123,7 @@ typedef struct {
     double offset;           /* FP64 offset b: V_abs(s) = offset + V[s] (VI_PREC_FP32_SINGLE; else 0) */
     double wall_ms;          /* device time of the solve (CUDA events), sweeps + extraction */
     double updates_per_s;    /* nominal |S||A||Omega| x iters / wall time */
-    int pe_iters;            /* FP64 policy-evaluation sweeps (VI_FLAG_POLICY_EVAL) */
+    int pe_iters;            /* FP64 policy-evaluation sweeps (VI_FLAG_POLICY_EVAL; a multiple of 8) */
     double pe_delta;         /* last sup-norm change of the policy evaluation */
     double pe_gap;           /* max_s |V_pe(s) - V_abs(s)| after evaluation */
 } vi_solve_info;
@@ -280,9 +282,12 @@ vi_status vi_backup(vi_handle h, const void *V_in, void *V_out, uint8_t *policy,
 
 /* Evaluate a fixed policy in FP64 (the paper's double-precision arithmetic,
  * Methods "Value iteration"): V <- r_pi + gamma P_pi V until the sup-norm
- * change is < tol or max_iters sweeps.  V: device double[|S|], in (start) /
- * out.  policy: device uint8[|S|].  iters / delta: host out (may be NULL).
- * Returns VI_OK or VI_ENOTCONVERGED. */
+ * change is < tol or max_iters sweeps.  The change is read back after every
+ * 8th sweep (and after sweep max_iters), so iters is the first multiple of 8
+ * at or past the sweep whose change fell below tol, and delta is the change of
+ * that sweep.  V: device double[|S|], in (start) / out.  policy: device
+ * uint8[|S|].  iters / delta: host out (may be NULL).  Returns VI_OK or
+ * VI_ENOTCONVERGED. */
 vi_status vi_policy_eval(vi_handle h, const uint8_t *policy, double *V, double tol,
                          int max_iters, void *stream, int *iters, double *delta);
 
@@ -426,7 +431,9 @@ vi_status vi_server_destroy(vi_server srv);
  * the GPU -- on different streams, or from several host threads without
  * ordering -- race.  The first call on a device looks up the array's device
  * address (a one-time set-up for that device); make that first call before
- * any stream capture.  No cudaMalloc, cudaFree or other allocator is called.
+ * any stream capture.  The address is kept for the life of the process, so
+ * the device's primary context must not be reset (cudaDeviceReset) between
+ * calls.  No cudaMalloc, cudaFree or other allocator is called.
  * Errors: VI_EINVAL (bad instance or buffers, tables too large), VI_ECUDA. */
 #define VI_NOALLOC_MAX_TABLE_FLOATS 16384
 vi_status vi_backup_noalloc(int m, int L, int Q, const double cost[5], const double *pmf, int dmax,

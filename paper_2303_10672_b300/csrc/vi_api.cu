@@ -122,11 +122,7 @@ static void fill_product_tables(ProdParams &P, const std::vector<double> &pmf, i
     std::vector<double> G = expected_leftover(pmf, P.tmax);
     std::vector<double> rt((size_t)P.rt_rows * P.G);
     for (int R = 0; R < P.rt_rows; ++R)
-        for (int y1 = 0; y1 < P.G; ++y1) {
-            const int T = y1 + R;
-            const double ew = (issuing == VI_LIFO) ? G[T] - G[R] : G[y1];
-            rt[(size_t)R * P.G + y1] = (c_s + c_r) * T - c_s * mu - (c_h + c_s + c_r) * G[T] + (c_h - c_w) * ew;
-        }
+        for (int y1 = 0; y1 < P.G; ++y1) rt[(size_t)R * P.G + y1] = expected_period_reward(y1, R, G.data(), mu, cost, issuing);
     P.off_RT = (int)blob.size();
     blob.insert(blob.end(), rt.begin(), rt.end());
     P.off_RTlo = (int)blob.size();
@@ -391,7 +387,7 @@ extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_hand
     h->kahan = (d.precision == VI_PREC_FP32_KAHAN) ? 1 : 0;
     h->value_bytes = (h->vk == VK_SINGLE) ? 4 : 8;
     h->group_ok = group_supported(kp, h->vk, h->kahan);
-    h->two_ok = two_supported(kp, h->vk);
+    h->two_ok = two_supported(kp, h->vk, h->kahan);
     h->group_xw = 0;   // chosen by the autotuner on the first solve (or set explicitly)
     std::vector<float> fblob(blob.size());
     for (size_t i = 0; i < blob.size(); ++i) fblob[i] = (float)blob[i];

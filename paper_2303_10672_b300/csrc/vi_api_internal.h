@@ -61,6 +61,16 @@ struct vi_problem {
 };
 
 vi_status vi_fail(vi_status s, const char *fmt, ...);
+// Expected one-period reward without the order cost, given y1 units in the
+// expiring slot and R in the others (T = y1 + R available), with G[n] = E[(n-D)^+]
+// and mu = E[D]:  (c_s + c_r) T - c_s mu - (c_h + c_s + c_r) G[T] + (c_h - c_w) E[W],
+// E[W] = G[y1] (FIFO: the expiring units go first) or G[T] - G[R] (LIFO: last).
+inline double expected_period_reward(int y1, int R, const double *G, double mu, const double *cost, int issuing) {
+    const double c_h = cost[1], c_s = cost[2], c_w = cost[3], c_r = cost[4];
+    const int T = y1 + R;
+    const double ew = (issuing == VI_LIFO) ? G[T] - G[R] : G[y1];
+    return (c_s + c_r) * T - c_s * mu - (c_h + c_s + c_r) * G[T] + (c_h - c_w) * ew;
+}
 // shared with the allocation-free entry point (vi_noalloc.cu)
 void fill_prod_params(vib::ProdParams &P, int m, int L, int Q, int dmax, double c_o);
 int heuristic_width(int G, int lifo);

@@ -990,6 +990,7 @@ int group_width_candidates(int G, int *out, int max_out) {
 // with E2 and Mix product-2 expectations measured from V(i1, i2_0), built once
 // per sweep by two small kernels ahead of the sweep.
 // ===========================================================================
+template <int KAHAN>
 __global__ void __launch_bounds__(kGenericThreads)
 two_e2_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int) {
     SolveState *st = kp.st;
@@ -1009,14 +1010,15 @@ two_e2_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, ui
     const ProdState p2s = prod_state(P2, s2);
     const ProdAction A2 = prod_action(P2, p2s, a2, kp.issuing);
     const float2 *V2 = (const float2 *)B.vin;
-    Acc<float, 0> acc;
+    Acc<float, KAHAN> acc;
     acc.init();
     GetRel get{V2, V2[i1 + S1 * A2.wk.idx]};
-    expect_rest<float, 0>(acc, get, i1, S1, A2.wk, P2.cb, kp.issuing, (uint32_t)P2.G, A2.y1, A2.R,
-                          tab + P2.off_p, tab + P2.off_F, tab + P2.off_tail, P2.dmax + 1, 1.f);
+    expect_rest<float, KAHAN>(acc, get, i1, S1, A2.wk, P2.cb, kp.issuing, (uint32_t)P2.G, A2.y1, A2.R,
+                              tab + P2.off_p, tab + P2.off_F, tab + P2.off_tail, P2.dmax + 1, 1.f);
     kp.two_e2[t] = acc.s;
 }
 
+template <int KAHAN>
 __global__ void __launch_bounds__(kGenericThreads)
 two_mix_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int) {
     SolveState *st = kp.st;
@@ -1037,15 +1039,17 @@ two_mix_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, u
     const ProdState p2s = prod_state(P2, s2);
     const ProdAction A2 = prod_action(P2, p2s, a2, kp.issuing);
     const float2 *V2 = (const float2 *)B.vin;
-    Acc<float, 0> acc;
+    Acc<float, KAHAN> acc;
     acc.init();
     GetRel get{V2, V2[S1 * A2.wk.idx]};
     const int row = T1 * kp.zlen;
-    expect_rest<float, 0>(acc, get, 0u, S1, A2.wk, P2.cb, kp.issuing, (uint32_t)P2.G, A2.y1, A2.R,
-                          tab + kp.off_M + row, tab + kp.off_Mc + row, tab + kp.off_Mt + row, kp.zlen, 1.f);
+    expect_rest<float, KAHAN>(acc, get, 0u, S1, A2.wk, P2.cb, kp.issuing, (uint32_t)P2.G, A2.y1, A2.R,
+                              tab + kp.off_M + row, tab + kp.off_Mc + row, tab + kp.off_Mt + row, kp.zlen, 1.f);
     kp.two_mix[t] = acc.s;
 }
 
+// KAHAN = 1: the sum over d1 is compensated like the E2 and mixture sums
+template <int KAHAN>
 __global__ void __launch_bounds__(kGenericThreads)
 sweep_two_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int) {
     SolveState *st = kp.st;
@@ -1076,18 +1080,27 @@ sweep_two_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg,
                 const float2 ref = V2[A1.wk.idx + i20];
                 const float *e2 = kp.two_e2 + ((uint64_t)s2 * P2.G + a2) * S1;
                 float acc = 0.f;
+                Acc<float, 1> kacc;   // KAHAN = 1 only
+                kacc.init();
                 Walker w1 = A1.wk;
                 int e1c = 0;
                 for (int d1 = 0; d1 < top1; ++d1) {
                     const int e1 = lifo ? min(d1, A1.R) : max(d1 - A1.y1, 0);
                     for (; e1c < e1; ++e1c) walker_step(w1, P1.cb, lifo, (uint32_t)P1.G);
                     const float t = e2[w1.idx] + pair_diff(V2[w1.idx + i20], ref);
-                    acc = fmaf(tab[P1.off_p + d1], t, acc);
+                    if (KAHAN) kacc.add(tab[P1.off_p + d1], t);
+                    else acc = fmaf(tab[P1.off_p + d1], t, acc);
                 }
                 if (A1.T <= P1.dmax) {
                     const float t = kp.two_mix[((uint32_t)s2 * P2.G + a2) * kp.two_nt1 + A1.T];
-                    acc += t + tab[P1.off_tail + A1.T] * pair_diff(V2[i20], ref);
+                    if (KAHAN) {
+                        kacc.add(1.f, t);
+                        kacc.add(tab[P1.off_tail + A1.T], pair_diff(V2[i20], ref));
+                    } else {
+                        acc += t + tab[P1.off_tail + A1.T] * pair_diff(V2[i20], ref);
+                    }
                 }
+                if (KAHAN) acc = kacc.s;
                 float qh, ql;
                 const float ca =
                     __fadd_rn(__fmul_rn(-(float)P1.c_o, (float)a1), __fmul_rn(-(float)P2.c_o, (float)a2));
@@ -1568,7 +1581,7 @@ static size_t two_npipe1(const ProdParams &P1) {
     return n;
 }
 
-bool two_supported(const KernelParams &kp, int vk) {
+bool two_supported(const KernelParams &kp, int vk, int kahan) {
     if (kp.n_products != 2 || vk != VK_PAIR) return false;
     const ProdParams &P1 = kp.p[0];
     const ProdParams &P2 = kp.p[1];
@@ -1576,8 +1589,9 @@ bool two_supported(const KernelParams &kp, int vk) {
     const size_t e2 = two_table_floats(kp, &mix);
     if (P1.L == 1 && P2.L == 1) return e2 <= ((size_t)1 << 27) && mix <= ((size_t)1 << 27);
     // lead times >= 2 on both products: the pipeline form; the correlation keeps
-    // up to 32 expiring-slot values per thread and the rest path in shared memory
-    if (P1.L < 2 || P2.L < 2 || P1.m < 2 || P2.m < 2) return false;
+    // up to 32 expiring-slot values per thread and the rest path in shared memory.
+    // Its sums are not compensated: VI_PREC_FP32_KAHAN runs the generic kernel instead.
+    if (kahan || P1.L < 2 || P2.L < 2 || P1.m < 2 || P2.m < 2) return false;
     if (P1.G > 32 || P2.G > 32) return false;
     if (twop_smem(P1, kGenericThreads) > 48 * 1024) return false;
     return e2 <= ((size_t)1 << 30) && mix <= ((size_t)1 << 30);
@@ -1592,19 +1606,19 @@ size_t two_table_floats(const KernelParams &kp, size_t *mix_floats) {
     return (size_t)P1.nS * P2.nS * (size_t)P2.G;
 }
 
-static cudaError_t describe_two(const KernelParams &kp, LaunchDesc &d) {
+static cudaError_t describe_two(const KernelParams &kp, int kahan, LaunchDesc &d) {
     const uint64_t n_e2 = (uint64_t)kp.p[0].nS * kp.p[1].nS * (uint32_t)kp.p[1].G;
     const uint64_t n_mix = (uint64_t)kp.p[1].nS * (uint32_t)kp.p[1].G * (uint32_t)kp.two_nt1;
-    d.fn = (const void *)sweep_two_kernel;
+    d.fn = kahan ? (const void *)sweep_two_kernel<1> : (const void *)sweep_two_kernel<0>;
     d.grid = dim3((kp.nS + kGenericThreads - 1) / kGenericThreads);
     d.block = dim3(kGenericThreads);
     d.smem = 0;
     d.lpr = 0;
     d.n_pre = 2;
-    d.pre_fn[0] = (const void *)two_e2_kernel;
+    d.pre_fn[0] = kahan ? (const void *)two_e2_kernel<1> : (const void *)two_e2_kernel<0>;
     d.pre_grid[0] = dim3((unsigned)((n_e2 + kGenericThreads - 1) / kGenericThreads));
     d.pre_block[0] = dim3(kGenericThreads);
-    d.pre_fn[1] = (const void *)two_mix_kernel;
+    d.pre_fn[1] = kahan ? (const void *)two_mix_kernel<1> : (const void *)two_mix_kernel<0>;
     d.pre_grid[1] = dim3((unsigned)((n_mix + kGenericThreads - 1) / kGenericThreads));
     d.pre_block[1] = dim3(kGenericThreads);
     return cudaSuccess;
@@ -1616,7 +1630,7 @@ cudaError_t describe_sweep(const KernelParams &kp, int vk, int kahan, int use_gr
     if (kp.pc) return describe_pc(kp, d);
     if (use_group == kTcWidth) return describe_tc(kp, d);
     if (use_group == kLifo1Width) return describe_lifo1(kp, d);
-    if (use_group == kTwoWidth) return (kp.p[0].L >= 2) ? describe_twop(kp, d) : describe_two(kp, d);
+    if (use_group == kTwoWidth) return (kp.p[0].L >= 2) ? describe_twop(kp, d) : describe_two(kp, kahan, d);
     if (use_group) {
         const int xw = use_group;   // lane width of the factorised kernel
         const bool pipe = kp.p[0].L >= 2;

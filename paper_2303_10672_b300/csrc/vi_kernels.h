@@ -74,7 +74,7 @@ constexpr int kTwoWidth = 200;
 constexpr int kLifo1Width = 300;
 bool lifo1_supported(const KernelParams &kp, int vk, int kahan);
 cudaError_t describe_lifo1(const KernelParams &kp, LaunchDesc &d);
-bool two_supported(const KernelParams &kp, int vk);
+bool two_supported(const KernelParams &kp, int vk, int kahan);
 size_t two_table_floats(const KernelParams &kp, size_t *mix_floats);
 // rows of the substitution mixture table: product-1 stock T1 = 0..min(dmax1, m1 Q1)
 int two_mix_rows(const ProdParams &P1);

@@ -63,7 +63,6 @@ static int build_tables_static(ProdParams &P, const double *pmf, int issuing, co
         g_tab_d[n + k] = t;
     }
     n += P.pn;
-    const double c_h = cost[1], c_s = cost[2], c_w = cost[3], c_r = cost[4];
     double mu = 0.0;
     for (int d = 0; d <= dmax; ++d) mu += (double)d * pmf[d];
     for (int y = 0; y <= P.tmax; ++y) {
@@ -74,11 +73,7 @@ static int build_tables_static(ProdParams &P, const double *pmf, int issuing, co
     const double *G = g_leftover;
     P.off_RT = n;
     for (int R = 0; R < P.rt_rows; ++R)
-        for (int y1 = 0; y1 < P.G; ++y1) {
-            const int T = y1 + R;
-            const double ew = (issuing == VI_LIFO) ? G[T] - G[R] : G[y1];
-            g_tab_d[n++] = (c_s + c_r) * T - c_s * mu - (c_h + c_s + c_r) * G[T] + (c_h - c_w) * ew;
-        }
+        for (int y1 = 0; y1 < P.G; ++y1) g_tab_d[n++] = expected_period_reward(y1, R, G, mu, cost, issuing);
     P.off_RTlo = n;
     for (int i = 0; i < P.G * P.rt_rows; ++i) {
         const double v = g_tab_d[P.off_RT + i];
