@@ -328,9 +328,28 @@ def vi_backup(h: int, V_in, V_out, policy=None, stream=None, stats: bool = True)
     return (ds[0], ds[1]) if stats else None
 
 
+def _noalloc_buffer(x, nbytes: int, what: str, dtypes) -> None:
+    """The allocation-free sweep has no handle to check sizes against: refuse a buffer
+    that is not a contiguous CUDA tensor of a listed dtype holding nbytes."""
+    if x is None:
+        return
+    if hasattr(x, "is_cuda"):
+        if not x.is_cuda or not x.is_contiguous() or str(x.dtype) not in dtypes:
+            raise ViError(VI_EINVAL, "vi_backup_noalloc", f"{what} must be a contiguous CUDA tensor of {dtypes}")
+    nb = _nbytes(x)
+    if nb is not None and nb < nbytes:
+        raise ViError(VI_EINVAL, "vi_backup_noalloc", f"{what} buffer of {nb} bytes, the instance needs {nbytes}")
+
+
 def vi_backup_noalloc(m: int, L: int, Q: int, cost: Sequence[float], pmf: np.ndarray, gamma: float, issuing: int,
                       V_in, V_out, policy=None, stream=None, stats: bool = True):
     """One sweep without any allocation (see vi.h); V_in / V_out in the float-pair layout."""
+    if len(cost) != 5:
+        raise ViError(VI_EINVAL, "vi_backup_noalloc", "cost needs 5 entries (c_o, c_h, c_s, c_w, c_r)")
+    n_states = (Q + 1) ** ((m - 1) + (L - 1)) if m >= 1 and L >= 1 and Q >= 0 else 0
+    _noalloc_buffer(V_in, 8 * n_states, "V_in", ("torch.float32", "torch.float64"))
+    _noalloc_buffer(V_out, 8 * n_states, "V_out", ("torch.float32", "torch.float64"))
+    _noalloc_buffer(policy, n_states, "policy", ("torch.uint8",))
     c = np.ascontiguousarray(cost, np.float64)
     p = np.ascontiguousarray(pmf, np.float64)
     ds = (C.c_double * 2)()
