@@ -411,6 +411,63 @@ def solve_summary(vi, torch, inst, args, stream, flush, steps: int, warmup: int)
         vi.vi_problem_destroy(h)
 
 
+CFG3_ORACLE = os.path.join(ROOT, "tests", "golden", "cfg3_oracle_sample.json")
+
+
+def run_cfg3_accuracy(vi, torch, stream) -> dict:
+    """The two-product configuration (50,625 states) in FP32 with compensated sums,
+    its error against the FP64 oracle reported per result: the GPU runs the oracle's
+    sweep count (tol 0), and its values and first-argmax policy are compared with
+    the oracle's stored solve at 2,004 sampled states; a second solve with the
+    span test (tol 1e-4) gives the GPU's own stop sweep and, with
+    VI_FLAG_POLICY_EVAL, the FP64 evaluation of its policy (pe_gap =
+    max_s |V_pe(s) - V(s)|, and pe_span = max - min of V_pe - V, the gap up to the
+    constant that a span-test stop leaves)."""
+    with open(CFG3_ORACLE) as f:
+        ref = json.load(f)
+    inst = workloads.config3()
+    prods = [dict(m=q.m, L=q.L, Q=q.Q, cost=q.cost, pmf=q.pmf) for q in inst.products]
+    desc, keep = vi.make_desc(prods, inst.gamma, inst.issuing, vi.VI_PREC_FP32_KAHAN, vi.VI_STOP_SPAN,
+                              inst.subst_rate)
+    h = vi.vi_problem_create_desc(desc)
+    try:
+        n = vi.vi_problem_sizes(h)["n_states"]
+        assert n == ref["n_states"]
+        states = np.asarray(ref["states"], np.int64)
+        V = torch.empty(n, dtype=torch.float64, device="cuda")
+        pol = torch.empty(n, dtype=torch.uint8, device="cuda")
+        # the oracle's sweep count, no early stop
+        vi.vi_solve(h, 0.0, ref["iters"], V, pol, stream=stream)
+        torch.cuda.synchronize()
+        pair = V.view(torch.float32).reshape(-1, 2).double()
+        v = (pair[:, 0] + pair[:, 1]).cpu().numpy()[states]
+        want = np.asarray(ref["V"])
+        err = float(np.abs(v - want).max() / np.abs(want).max())
+        mism = int((pol.cpu().numpy()[states] != np.asarray(ref["policy"], np.uint8)).sum())
+        # the GPU's own stopping test, then FP64 evaluation of its policy
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        own = vi.vi_solve(h, ref["tol"], MAX_ITERS, V, pol, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        pe = vi.vi_solve(h, ref["tol"], MAX_ITERS, V, pol, stream=stream, flags=vi.VI_FLAG_POLICY_EVAL)
+        kch, kw = vi.vi_problem_kernel(h)
+        return {"workload": inst.name, "states": n, "precision": "fp32_kahan",
+                "kernel": kernel_name_of(vi, inst, kch, kw),
+                "vs_oracle": {"sweeps": ref["iters"], "sampled_states": int(len(states)),
+                              "max_abs_dV_over_max_abs_V": err,
+                              "policy_differences": mism, "policy_note": "exact compare, ties not separated"},
+                "own_stop_sweep": own["iters"], "oracle_stop_sweep": ref["iters"], "ms_per_solve": ms,
+                "pe_gap": pe["pe_gap"], "pe_span": pe["pe_span"],
+                "pe_span_over_max_abs_V": pe["pe_span"] / ref["max_abs_V"], "pe_sweeps": pe["pe_iters"],
+                "pe_note": "span-test solve: V is right up to a constant, so pe_span (max - min of V_pe - V) "
+                           "is the error and pe_gap holds that constant"}
+    finally:
+        vi.vi_problem_destroy(h)
+
+
 def run_native(args):
     import torch
     import paper_2303_10672_b300 as vi
@@ -553,6 +610,7 @@ def run_native(args):
         x = solve_summary(vi, torch, workloads.config2(), args, stream, flush, steps=5, warmup=2)
         x["roofline"] = roofline_of(vi, torch, workloads.config2(), x["kernel"], x["kernel_ms"], sm_mhz, l2_gbs)
         extra = x
+    cfg3 = run_cfg3_accuracy(vi, torch, stream) if (rank == 0 and args.extra) else None
     if rank == 0:
         cpu = oracle_sample_rate(inst, args.cpu_seconds) if args.cpu_seconds > 0 else None
         out = {
@@ -572,15 +630,16 @@ def run_native(args):
                     "steps": e2e_steps, "includes": "vi_problem_create + vi_solve_host + vi_problem_destroy"},
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind",
                                                                            "sample")},
+            "serving": serving_summary(serving),
+            "cfg3": cfg3,
             "rollouts": rollouts,
             "policy_search": policy_search,
             "paper_scenario_a": paper_a,
             "paper_scenario_b": paper_b,
             "paper_scenario_c": paper_c,
             "wall_s": wall,
-            # last, so that they stay in the tail of the line
             "cfg2": extra,
-            "serving": serving,
+            "serving_detail": serving,
         }
         print(json.dumps(out))
     vi.vi_problem_destroy(h)
@@ -761,6 +820,20 @@ def run_paper_scenario_c(vi, torch, stream, no_graph: bool = False) -> dict:
     return out
 
 
+def serving_summary(d):
+    """The serving comparison in a few numbers: server over sequential throughput
+    (Poisson stream and burst) and both p99 latencies."""
+    if d is None:
+        return None
+    srv, seq, b = d["server"], d["sequential"], d["burst"]
+    return {"requests": d["requests"],
+            "burst_speedup": b["server_updates_per_s"] / b["sequential_updates_per_s"],
+            "stream_speedup": srv["updates_per_s"] / seq["updates_per_s"],
+            "p99_ms": {"server": srv["p99_ms"], "sequential": seq["p99_ms"]},
+            "p50_ms": {"server": srv["p50_ms"], "sequential": seq["p50_ms"]},
+            "results_match": d["results_match"]}
+
+
 def run_serving(n_requests: int = 512, seed: int = 5, slots: int = 64, budget_gb: float = 64.0) -> dict:
     """Serving mix: requests arriving as a Poisson stream, served by the
     continuous-batching server vs sequential plain solves of the same mix (each:
@@ -854,8 +927,24 @@ def run_serving(n_requests: int = 512, seed: int = 5, slots: int = 64, budget_gb
         vi.vi_problem_destroy(h)
         upd_bs += nominal[k] * info["iters"]
     span_bs = time.perf_counter() - t0
+    # equal accuracy (untimed): the burst's results against sequential solves of the
+    # same requests; the two run different kernels, so values agree to rounding
+    worst, pol_diff = 0.0, 0
+    for k, d in enumerate(descs):
+        h = vi.vi_problem_create_desc(d[0])
+        w, q = host_bufs(k)
+        vi.vi_solve_host(h, TOL, MAX_ITERS, w, q)
+        vi.vi_problem_destroy(h)
+        a = w.view(np.float32).reshape(-1, 2).astype(np.float64).sum(axis=1)   # float pairs
+        b = bufs[k][0]                                                          # absolute FP64 values
+        worst = max(worst, float(np.abs(a - b).max() / max(np.abs(a).max(), 1e-300)))
+        pol_diff += int((q != bufs[k][1]).sum())
+    del bufs
     return {
         "workload": f"{n_requests} single-product requests, Poisson arrivals 200/s, m 2..6, L 1..3, Q 8..20, seed {seed}",
+        "requests": n_requests,
+        "results_match": {"max_rel_dV_vs_sequential": worst, "policy_differences": pol_diff,
+                          "states": int(sum(n_states))},
         "server": {"updates_per_s": upd / span_srv, "p50_ms": float(np.percentile(lat_srv, 50)),
                    "p99_ms": float(np.percentile(lat_srv, 99)), "makespan_s": span_srv, "slots": slots},
         "sequential": {"updates_per_s": upd_seq / span_seq, "p50_ms": float(np.percentile(lat_seq, 50)),

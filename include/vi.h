@@ -126,6 +126,8 @@ typedef struct {
     int pe_iters;            /* FP64 policy-evaluation sweeps (VI_FLAG_POLICY_EVAL; a multiple of 8) */
     double pe_delta;         /* last sup-norm change of the policy evaluation */
     double pe_gap;           /* max_s |V_pe(s) - V_abs(s)| after evaluation */
+    double pe_span;          /* max_s - min_s of V_pe(s) - V_abs(s): the gap up to a constant,
+                                the relevant one after a span-test stop */
 } vi_solve_info;
 
 /* Create a single-product problem (VI_PREC_FP32, span stopping test).

@@ -67,6 +67,7 @@ class vi_solve_info(C.Structure):
         ("dmax", C.c_double), ("dmin", C.c_double), ("offset", C.c_double),
         ("wall_ms", C.c_double), ("updates_per_s", C.c_double),
         ("pe_iters", C.c_int), ("pe_delta", C.c_double), ("pe_gap", C.c_double),
+        ("pe_span", C.c_double),
     ]
 
     def as_dict(self) -> dict:

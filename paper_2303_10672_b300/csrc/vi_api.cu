@@ -1195,12 +1195,13 @@ static vi_status solve_impl(vi_problem *h, double tol, int max_iters, void *V, u
         double scale = std::max(fabs(info->offset), 1.0);
         vi_status ps = policy_eval_impl(h, policy, h->d_pe[0], 1e-9 * scale, h->pe_max_iters, s, &it, &delta);
         if (ps != VI_OK && ps != VI_ENOTCONVERGED) return ps;
-        CUDA_TRY(launch_absdiff(h->d_pe[0], h->d_pe[1], n, h->d_state, s));
+        CUDA_TRY(launch_diff_range(h->d_pe[0], h->d_pe[1], n, h->d_state, s));
         CUDA_TRY(cudaMemcpyAsync(hs, h->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
         info->pe_iters = it;
         info->pe_delta = delta;
-        info->pe_gap = hs->dmax_abs;
+        info->pe_gap = std::max(fabs(hs->dmax_abs), fabs(hs->dmin_abs));
+        info->pe_span = hs->dmax_abs - hs->dmin_abs;
     }
     return result;
 }

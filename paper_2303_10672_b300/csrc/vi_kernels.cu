@@ -453,11 +453,12 @@ __global__ void to_fp64_kernel(const void *v, int vk, double offset, double *out
 }
 
 // max_s |a(s) - b(s)| into the state's plain accumulators
-__global__ void absdiff_kernel(const double *a, const double *b, uint32_t n, SolveState *st) {
+// max and min of a - b over the n entries, into st->dmax_abs / st->dmin_abs
+__global__ void diff_range_kernel(const double *a, const double *b, uint32_t n, SolveState *st) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    double d = 0.0;
-    if (i < n) d = fabs(a[i] - b[i]);
-    block_reduce_and_finalize<double>(d, d, st, MODE_PLAIN, gridDim.x);
+    double mx = -INFINITY, mn = INFINITY;
+    if (i < n) mx = mn = a[i] - b[i];
+    block_reduce_and_finalize<double>(mx, mn, st, MODE_PLAIN, gridDim.x);
 }
 
 // ===========================================================================
@@ -1708,8 +1709,8 @@ cudaError_t launch_to_fp64(const void *v, int vk, double offset, double *out, ui
     return cudaGetLastError();
 }
 
-cudaError_t launch_absdiff(const double *a, const double *b, uint32_t n, SolveState *st, cudaStream_t stream) {
-    absdiff_kernel<<<(n + 255) / 256, 256, 0, stream>>>(a, b, n, st);
+cudaError_t launch_diff_range(const double *a, const double *b, uint32_t n, SolveState *st, cudaStream_t stream) {
+    diff_range_kernel<<<(n + 255) / 256, 256, 0, stream>>>(a, b, n, st);
     return cudaGetLastError();
 }
 

@@ -47,8 +47,9 @@ cudaError_t launch_next_states(const KernelParams &kp, const uint32_t *states, i
 cudaError_t launch_policy_eval(const KernelParams &kp, const uint8_t *policy, const double *vin,
                                double *vout, cudaStream_t stream);
 cudaError_t launch_to_fp64(const void *v, int vk, double offset, double *out, uint32_t n, cudaStream_t stream);
-cudaError_t launch_absdiff(const double *a, const double *b, uint32_t n, SolveState *st,
-                           cudaStream_t stream);
+// max and min of a - b into st->dmax_abs / st->dmin_abs
+cudaError_t launch_diff_range(const double *a, const double *b, uint32_t n, SolveState *st,
+                              cudaStream_t stream);
 cudaError_t launch_solve_init(SolveState *st, uint32_t n, cudaStream_t stream);
 
 // what a graph kernel node needs (the dynamic shared-memory attribute is set)

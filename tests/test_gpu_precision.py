@@ -5,7 +5,7 @@ VI_FLAG_POLICY_EVAL evaluates the extracted policy in FP64 from the solve's
 values until the sup-norm change is below 1e-9, and reports the gap
 max_s |V_pe(s) - V(s)|.  The oracle's fixed-policy evaluation (pinned to the dense
 solve (I - gamma P_pi) V = r_pi) of the same GPU policy from the same start gives
-the reference gap and sweep count.
+the reference gap (and its span, max - min of V_pe - V) and sweep count.
 """
 import numpy as np
 import pytest
@@ -43,7 +43,9 @@ def test_policy_eval_flag_matches_oracle(name):
     V_pe, it, ok = oracle.Problem(inst).policy_eval(policy, tol=1e-9 * scale, max_iters=100000, V0=v)
     assert ok
     gap_ref = float(np.abs(V_pe - v).max())
+    span_ref = float((V_pe - v).max() - (V_pe - v).min())
     assert abs(info["pe_gap"] - gap_ref) <= 1e-8 * np.abs(V_pe).max(), (info["pe_gap"], gap_ref)
+    assert abs(info["pe_span"] - span_ref) <= 1e-8 * np.abs(V_pe).max(), (info["pe_span"], span_ref)
     # the GPU reads the change back after every 8th sweep: it stops at the first
     # multiple of 8 at or past the oracle's stop sweep (that sweep itself may move by
     # one under summation-order rounding when its change is that close to the tolerance)
