@@ -136,7 +136,7 @@ typedef struct {
  * cost: host double[5]; pmf: host double[dmax+1].  Copies everything it needs
  * to the current CUDA device.  Errors: VI_EINVAL for m < 1, L < 1, Q < 0,
  * Q+1 > 256 (policy is uint8), |S| >= 2^32, dmax < 0 or > 4095, pmf entries
- * < 0 or not summing to 1 within 1e-9, gamma outside (0, 1], a negative cost
+ * < 0 or not summing to 1 within 1e-12, gamma outside (0, 1], a negative cost
  * or issuing not FIFO/LIFO; VI_ENOMEM / VI_ECUDA on allocation failure. */
 vi_status vi_problem_create(int m, int L, int Q, const double cost[5], const double *pmf,
                             int dmax, double gamma, int issuing, vi_handle *out);
@@ -182,7 +182,7 @@ typedef struct {
 
 /* Create a Scenario C problem.  Copies everything it needs to the current
  * device.  Errors: VI_EINVAL for m outside 2..8, Q outside 0..63, a pmf row not
- * summing to 1 within 1e-9, gamma outside (0, 1), a negative cost, a bad stop
+ * summing to 1 within 1e-12, gamma outside (0, 1), a negative cost, a bad stop
  * rule or 7 (Q+1)^m >= 2^31; VI_ENOMEM / VI_ECUDA. */
 vi_status vi_problem_create_periodic(const vi_periodic_desc *desc, vi_handle *out);
 

@@ -272,7 +272,7 @@ static vi_status validate_product(int m, int L, int Q, const double *cost, const
         if (!(pmf[d] >= 0.0) || !isfinite(pmf[d])) return vi_fail(VI_EINVAL, "pmf[%d] must be >= 0", d);
         s += pmf[d];
     }
-    if (fabs(s - 1.0) > 1e-9) return vi_fail(VI_EINVAL, "pmf sums to %.17g, not 1", s);
+    if (fabs(s - 1.0) > 1e-12) return vi_fail(VI_EINVAL, "pmf sums to %.17g, not 1", s);
     int K = (m - 1) + (L - 1);
     double ns = pow((double)(Q + 1), (double)K);
     if (ns >= 4294967296.0 || K > kMaxDigits) return vi_fail(VI_EINVAL, "|S| = (Q+1)^%d does not fit 32 bits", K);
@@ -504,7 +504,7 @@ extern "C" vi_status vi_problem_create_periodic(const vi_periodic_desc *desc, vi
             if (!(v >= 0.0)) return vi_fail(VI_EINVAL, "negative demand probability");
             sum += v;
         }
-        if (fabs(sum - 1.0) > 1e-9) return vi_fail(VI_EINVAL, "weekday %d pmf sums to %.12g", t, sum);
+        if (fabs(sum - 1.0) > 1e-12) return vi_fail(VI_EINVAL, "weekday %d pmf sums to %.17g", t, sum);
     }
     const int G = d.Q + 1;
     double n_post = 7.0;

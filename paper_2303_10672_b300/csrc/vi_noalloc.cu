@@ -98,7 +98,7 @@ extern "C" vi_status vi_backup_noalloc(int m, int L, int Q, const double cost[5]
         if (!(pmf[d] >= 0.0)) return vi_fail(VI_EINVAL, "pmf entries must be >= 0");
         sum += pmf[d];
     }
-    if (fabs(sum - 1.0) > 1e-9) return vi_fail(VI_EINVAL, "pmf does not sum to 1");
+    if (fabs(sum - 1.0) > 1e-12) return vi_fail(VI_EINVAL, "pmf does not sum to 1");
     const int K = (m - 1) + (L - 1);
     double ns = 1.0;
     for (int k = 0; k < K; ++k) ns *= (double)(Q + 1);
