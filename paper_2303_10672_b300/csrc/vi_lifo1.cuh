@@ -23,12 +23,14 @@
 //
 // G = Q+1 and the pmf capacity DP (> dmax) are compile-time, so the convolution
 // and the max over (x, a) are fully unrolled without per-thread bounds.  One
-// thread owns one rest (its G states); a block holds kL1Threads rests and walks
-// the grid's tiles (persistent blocks, tables staged once per block).  The
-// gathers of the next tile and the previous values of the current one are copied
-// into shared memory by cp.async while the block computes; the new values
-// replace the previous ones there (their change feeds the stopping test) and
-// leave in 16-byte pieces.
+// thread owns one rest (its G states); each warp walks tiles of 32 rests on its
+// own (persistent blocks, tables staged once per block, no block-wide barrier in
+// the tile loop), so the warps of an SM drift apart and overlap each other's
+// phases.  The gathers of the warp's next tile and the previous values of its
+// current one are copied into shared memory by cp.async while it computes; the
+// new values replace the previous ones there (their change feeds the stopping
+// test) and leave in 16-byte pieces.  The exact rebuild of the chosen orders runs
+// on pairs of x in packed FP32 arithmetic, lane-wise the scalar operations.
 #pragma once
 
 #include <algorithm>
@@ -38,6 +40,12 @@
 namespace vib {
 
 constexpr int kL1Threads = 128;
+
+// two independent lanes of FP32 arithmetic in one instruction, each lane rounded as
+// the scalar operation (a - b is a + (-b) exactly), so packed and scalar code agree
+// bit for bit
+__device__ __forceinline__ float2 l1_add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 l1_sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 
 // bits per packed slot count for a radix G (ceil(log2 G))
 __host__ __device__ constexpr int l1_bits(int G) { return G <= 2 ? 1 : (G <= 4 ? 2 : (G <= 8 ? 3 : (G <= 16 ? 4 : 5))); }
@@ -59,8 +67,9 @@ __device__ __forceinline__ void l1_wait() {
 }
 
 // shared memory of one block, in bytes: gathered columns (G + DP - 1 float pairs per
-// rest), the tile's previous / new values, the (hi, lo) pairs of RT at an odd row
+// rest), the tiles' previous / new values, the (hi, lo) pairs of RT at an odd row
 // stride, the LIFO split LF / LH of RT, the gamma C_a columns and the policy bytes
+// (the per-rest parts split into one region per warp)
 __host__ __device__ inline size_t lifo1_smem(int G, int DP, int rt_rows, int tmax) {
     return (size_t)8 * (G + DP - 1) * kL1Threads + (size_t)8 * G * kL1Threads + (size_t)8 * rt_rows * (G | 1) +
            (size_t)4 * (tmax + 1 + rt_rows) + (size_t)4 * G * kL1Threads + (size_t)G * kL1Threads + 32;
@@ -87,13 +96,16 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
     const ProdParams &P = kp.p[0];
     const int rows = P.rt_rows;
     const int nF = P.tmax + 1;
-    float2 *s_TH = (float2 *)smem_raw;               // column j of thread t at [j * NT + t]
-    float2 *s_VO = s_TH + NTH * NT;                  // the tile's previous values, then its new ones
-    float2 *s_RTp = s_VO + G * NT;                   // (hi, lo) of RT(R, x) at [R * GO + x]
+    constexpr int WPB = NT / 32;       // warps per block; each warp walks tiles of 32 rests on its own
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // per-warp regions: gathered columns, the tile's states, gamma C_a columns, policy bytes
+    float2 *s_TH = (float2 *)smem_raw + warp * (NTH * 32);                   // column j of a lane at [j * 32 + lane]
+    float2 *s_VO = (float2 *)smem_raw + WPB * (NTH * 32) + warp * (G * 32);  // previous values, then new ones
+    float2 *s_RTp = (float2 *)smem_raw + WPB * (NTH + G) * 32;               // (hi, lo) of RT(R, x) at [R * GO + x]
     float *s_LF = (float *)(s_RTp + rows * GO);      // LF(T), T = 0..tmax
     float *s_LH = s_LF + nF;                         // LH(R), R = 0..rows-1
-    float *s_kc = s_LH + rows;                       // per-thread columns: gamma C_a
-    uint8_t *s_pol = (uint8_t *)(s_kc + G * NT);     // the tile's first argmax
+    float *s_kc = s_LH + rows + warp * (G * 32);     // gamma C_a of a lane at [a * 32 + lane]
+    uint8_t *s_pol = (uint8_t *)(s_LH + rows + WPB * (G * 32)) + warp * (G * 32);   // the tile's first argmax
     {
         const float *tab = (const float *)kp.tables;
         for (int i = threadIdx.x; i < rows * GO; i += NT) {
@@ -103,11 +115,12 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
         }
         for (int i = threadIdx.x; i < nF; i += NT) s_LF[i] = tab[P.off_LF + i];
         for (int i = threadIdx.x; i < rows; i += NT) s_LH[i] = tab[P.off_LH + i];
-    }   // the first barrier of the tile loop publishes the tables
+    }
+    __syncthreads();   // the tables are shared by the block's warps; nothing else is
 
     const uint32_t nS = P.nS;
     const uint32_t nR = nS / (uint32_t)G;
-    const uint32_t ntiles = (nR + NT - 1) / NT;
+    const uint32_t ntiles = (nR + 31u) / 32u;       // tiles of 32 rests, one warp each
     const int nrs = P.n_rest_slots;                  // m - 2 rest slots: X_2 .. X_{m-1}
     const uint32_t w_top = P.w_top;                  // G^(m-2): weight of the order's next-state slot
     const int dmax = P.dmax;
@@ -116,14 +129,13 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
     const float2 *V2 = (const float2 *)B.vin;
     // 16-byte pieces need 16-byte aligned value buffers (the state offsets of a tile are even)
     const bool al16 = ((((uintptr_t)B.vin) | ((uintptr_t)B.vout)) & 15u) == 0;
-    const int tid = threadIdx.x;
-    float *kc_col = s_kc + tid;
+    float *kc_col = s_kc + lane;
     float mx = -INFINITY, mn = INFINITY;
 
-    // the gathers of tile t into this thread's column: T[j] = V[r + j G^(m-2)], then
+    // the gathers of tile t into this lane's column: T[j] = V[r + j G^(m-2)], then
     // H[k] = V[r after k units issued freshest first] for k <= min(R, dmax); returns R
     auto prefetch_gathers = [&](uint32_t t) -> int {
-        const uint32_t r = t * NT + (uint32_t)tid;
+        const uint32_t r = t * 32u + (uint32_t)lane;
         if (r >= nR) return 0;
         unsigned long long packed = 0ull;
         int Rr = 0;
@@ -136,18 +148,18 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
             Rr += dg;
         }
 #pragma unroll
-        for (int j = 0; j < G; ++j) l1_cp8(s_TH + j * NT + tid, V2 + r + (uint32_t)j * w_top);
+        for (int j = 0; j < G; ++j) l1_cp8(s_TH + j * 32 + lane, V2 + r + (uint32_t)j * w_top);
         // slot by slot from X_{m-1} down: each unit issued subtracts the slot's weight
         const int hcount = min(Rr, dmax);
         uint32_t w = (nrs > 0) ? w_top / (uint32_t)G : 0u;
         uint32_t idx = r;
-        float2 *col = s_TH + G * NT + tid;   // H[1] of this thread
+        float2 *col = s_TH + G * 32 + lane;   // H[1] of this lane
         int k = 0;
         for (int slot = nrs - 1; slot >= 0 && k < hcount; --slot) {
             const int units = min((int)((packed >> (CB * slot)) & ((1ull << CB) - 1ull)), hcount - k);
             for (int u = 0; u < units; ++u) {
                 idx -= w;
-                l1_cp8(col + k * NT, V2 + idx);
+                l1_cp8(col + k * 32, V2 + idx);
                 ++k;
             }
             w /= (uint32_t)G;
@@ -156,44 +168,51 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
     };
     // the previous values of tile t's states, in 16-byte pieces where aligned
     auto prefetch_old = [&](uint32_t t) {
-        const uint32_t s0 = t * (uint32_t)(NT * G);
-        const uint32_t nblk = min((uint32_t)(NT * G), nS - s0);
+        const uint32_t s0 = t * (uint32_t)(32 * G);
+        const uint32_t nblk = min((uint32_t)(32 * G), nS - s0);
         const float2 *src = V2 + s0;
         if (al16) {
-            for (uint32_t i = tid; i < (nblk >> 1); i += NT) l1_cp16(s_VO + 2 * i, src + 2 * i);
-            if ((nblk & 1u) && tid == 0) l1_cp8(s_VO + nblk - 1, src + nblk - 1);
+            for (uint32_t i = lane; i < (nblk >> 1); i += 32) l1_cp16(s_VO + 2 * i, src + 2 * i);
+            if ((nblk & 1u) && lane == 0) l1_cp8(s_VO + nblk - 1, src + nblk - 1);
         } else {
-            for (uint32_t i = tid; i < nblk; i += NT) l1_cp8(s_VO + i, src + i);
+            for (uint32_t i = lane; i < nblk; i += 32) l1_cp8(s_VO + i, src + i);
         }
     };
 
-    uint32_t tile = blockIdx.x;
+    const uint32_t wstride = gridDim.x * (uint32_t)WPB;
+    uint32_t tile = blockIdx.x * (uint32_t)WPB + (uint32_t)warp;
     int Rnext = 0;
     if (tile < ntiles) Rnext = prefetch_gathers(tile);
     l1_commit();
     if (tile < ntiles) prefetch_old(tile);
     l1_commit();
-    for (; tile < ntiles; tile += gridDim.x) {
-        const uint32_t next = tile + gridDim.x;
-        const uint32_t r = tile * NT + (uint32_t)tid;
+    for (; tile < ntiles; tile += wstride) {
+        const uint32_t next = tile + wstride;
+        const uint32_t r = tile * 32u + (uint32_t)lane;
         const bool active = r < nR;
         const int Rrest = Rnext;
-        l1_wait<1>();   // this thread's gathers of the tile have landed (its previous values may not)
-        __syncthreads();
+        l1_wait<1>();   // this lane's gathers of the tile have landed (its previous values may not)
         float2 R0 = make_float2(0.f, 0.f);
         float T[G], H[DP];
         if (active) {
             const int hcount = min(Rrest, dmax);
-            R0 = s_TH[tid];
+            R0 = s_TH[lane];
+            // pair_diff(g, R0) = (g.hi - R0.hi) + (g.lo - R0.lo), both differences in one packed add
+            const float2 nR0 = make_float2(-R0.x, -R0.y);
             T[0] = 0.f;
             H[0] = 0.f;
 #pragma unroll
-            for (int j = 1; j < G; ++j) T[j] = pair_diff(s_TH[j * NT + tid], R0);
+            for (int j = 1; j < G; ++j) {
+                const float2 d = l1_add2(s_TH[j * 32 + lane], nR0);
+                T[j] = __fadd_rn(d.x, d.y);
+            }
 #pragma unroll
-            for (int k = 1; k < DP; ++k)
-                H[k] = (k <= hcount) ? pair_diff(s_TH[(G - 1 + k) * NT + tid], R0) : H[k - 1];
+            for (int k = 1; k < DP; ++k) {
+                const float2 d = l1_add2(s_TH[(G - 1 + k) * 32 + lane], nR0);
+                H[k] = (k <= hcount) ? __fadd_rn(d.x, d.y) : H[k - 1];
+            }
         }
-        __syncthreads();   // every column is read: the next tile's gathers may land
+        __syncwarp();   // the column is read (each lane reads and refills only its own)
         if (next < ntiles) Rnext = prefetch_gathers(next);
         l1_commit();
 
@@ -220,7 +239,7 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
 #pragma unroll
             for (int a = 0; a < G; ++a) {
                 const float bl = __fmul_rn(gam, C[a]);
-                kc_col[a * NT] = bl;
+                kc_col[a * 32] = bl;
                 const float ks = __fadd_rn(__fadd_rn(__fmul_rn(-c_o, (float)a), bl), s_LH[Rrest + a]);
                 const float2 ks2 = make_float2(ks, ks);
                 float key[G + 1];
@@ -246,61 +265,103 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
                 }
             }
         }
-        l1_wait<1>();   // this thread's pieces of the previous values have landed
-        __syncthreads();
+        l1_wait<1>();   // this lane's pieces of the previous values have landed
+        __syncwarp();   // ... and every lane's: a lane's states were copied by other lanes
         if (active) {
             // -- the exact pair of each x's chosen order: gamma R0 + (-c_o a) + gamma C_a + RT,
             // its change from the previous value, and the new value in place of the old
             float ph, pe;
             two_prod(gam, R0.x, ph, pe);
             const float pl = __fmaf_rn(gam, R0.y, pe);
-            float2 *o = s_VO + tid * G;
-            uint8_t *op = s_pol + tid * G;
-            // every shared-memory operand of the rebuild is loaded before its arithmetic
-            float kq[G];
-            float2 rp[G];
+            float2 *o = s_VO + lane * G;
+            uint8_t *op = s_pol + lane * G;
+            // every shared-memory operand of the rebuild is loaded before its arithmetic; the
+            // rebuild runs on pairs of x (x, x+1) in packed arithmetic, lane by lane the same
+            // operations as pair_add, two_sum, fast_two_sum and pair_diff
+            float kq[G], rh[G], rl[G], oh[G], ol[G];
 #pragma unroll
             for (int x = 0; x < G; ++x) {
                 const int a = arg[x];
-                kq[x] = kc_col[a * NT];
-                rp[x] = s_RTp[(Rrest + a) * GO + x];
-            }
-#pragma unroll
-            for (int x = 0; x < G; ++x) {
-                const int a = arg[x];
-                float qh = __fmul_rn(-c_o, (float)a), ql = kq[x];
-                pair_add(qh, ql, rp[x].x, rp[x].y);
-                float sh, se;
-                two_sum(ph, qh, sh, se);
-                const float lo = __fadd_rn(se, __fadd_rn(pl, ql));
-                float vh, vl;
-                fast_two_sum(sh, lo, vh, vl);
+                kq[x] = kc_col[a * 32];
+                const float *rpx = (const float *)(s_RTp + (Rrest + a) * GO + x);
+                rh[x] = rpx[0];
+                rl[x] = rpx[1];
                 if (mode != MODE_EXTRACT) {
-                    const float dl = pair_diff(make_float2(vh, vl), o[x]);
-                    mx = fmaxf(mx, dl);
-                    mn = fminf(mn, dl);
-                    o[x] = make_float2(vh, vl);
+                    oh[x] = ((const float *)(o + x))[0];
+                    ol[x] = ((const float *)(o + x))[1];
                 }
-                if (B.pol) op[x] = (uint8_t)a;
+            }
+            const float2 ph2 = make_float2(ph, ph), pl2 = make_float2(pl, pl), nco2 = make_float2(-c_o, -c_o);
+#pragma unroll
+            for (int x = 0; x < G; x += 2) {
+                if (x + 1 < G) {
+                    const int a0 = arg[x], a1 = arg[x + 1];
+                    float2 qh = __fmul2_rn(nco2, make_float2((float)a0, (float)a1));
+                    float2 ql = make_float2(kq[x], kq[x + 1]);
+                    const float2 r_h = make_float2(rh[x], rh[x + 1]), r_l = make_float2(rl[x], rl[x + 1]);
+                    // pair_add(qh, ql, r_h, r_l)
+                    {
+                        const float2 sm = l1_add2(qh, r_h);
+                        const float2 bb = l1_sub2(sm, qh);
+                        const float2 e = l1_add2(l1_sub2(qh, l1_sub2(sm, bb)), l1_sub2(r_h, bb));
+                        qh = sm;
+                        ql = l1_add2(e, l1_add2(ql, r_l));
+                    }
+                    // two_sum(ph, qh), then fast_two_sum(sh, se + (pl + ql))
+                    const float2 sh = l1_add2(ph2, qh);
+                    const float2 bb = l1_sub2(sh, ph2);
+                    const float2 se = l1_add2(l1_sub2(ph2, l1_sub2(sh, bb)), l1_sub2(qh, bb));
+                    const float2 lo = l1_add2(se, l1_add2(pl2, ql));
+                    const float2 vh = l1_add2(sh, lo);
+                    const float2 vl = l1_sub2(lo, l1_sub2(vh, sh));
+                    if (mode != MODE_EXTRACT) {
+                        const float2 dl = l1_add2(l1_sub2(vh, make_float2(oh[x], oh[x + 1])),
+                                                  l1_sub2(vl, make_float2(ol[x], ol[x + 1])));
+                        mx = fmaxf(mx, fmaxf(dl.x, dl.y));
+                        mn = fminf(mn, fminf(dl.x, dl.y));
+                        o[x] = make_float2(vh.x, vl.x);
+                        o[x + 1] = make_float2(vh.y, vl.y);
+                    }
+                    if (B.pol) {
+                        op[x] = (uint8_t)a0;
+                        op[x + 1] = (uint8_t)a1;
+                    }
+                } else {
+                    const int a = arg[x];
+                    float qh = __fmul_rn(-c_o, (float)a), ql = kq[x];
+                    pair_add(qh, ql, rh[x], rl[x]);
+                    float sh, se;
+                    two_sum(ph, qh, sh, se);
+                    const float lo = __fadd_rn(se, __fadd_rn(pl, ql));
+                    float vh, vl;
+                    fast_two_sum(sh, lo, vh, vl);
+                    if (mode != MODE_EXTRACT) {
+                        const float dl = pair_diff(make_float2(vh, vl), make_float2(oh[x], ol[x]));
+                        mx = fmaxf(mx, dl);
+                        mn = fminf(mn, dl);
+                        o[x] = make_float2(vh, vl);
+                    }
+                    if (B.pol) op[x] = (uint8_t)a;
+                }
             }
         }
-        __syncthreads();
+        __syncwarp();   // the tile's new values and policy bytes are in place
         // -- the tile's states leave in 16-byte pieces (two states) where aligned; an
         // extraction moves the previous values unchanged (only when a buffer is given)
-        const uint32_t s0 = tile * (uint32_t)(NT * G);
-        const uint32_t nblk = min((uint32_t)(NT * G), nS - s0);
+        const uint32_t s0 = tile * (uint32_t)(32 * G);
+        const uint32_t nblk = min((uint32_t)(32 * G), nS - s0);
         if (B.vout) {
             float2 *dst = (float2 *)B.vout + s0;
             if (al16) {
-                for (uint32_t i = tid; i < (nblk >> 1); i += NT) ((float4 *)dst)[i] = ((const float4 *)s_VO)[i];
-                if ((nblk & 1u) && tid == 0) dst[nblk - 1] = s_VO[nblk - 1];
+                for (uint32_t i = lane; i < (nblk >> 1); i += 32) ((float4 *)dst)[i] = ((const float4 *)s_VO)[i];
+                if ((nblk & 1u) && lane == 0) dst[nblk - 1] = s_VO[nblk - 1];
             } else {
-                for (uint32_t i = tid; i < nblk; i += NT) dst[i] = s_VO[i];
+                for (uint32_t i = lane; i < nblk; i += 32) dst[i] = s_VO[i];
             }
         }
         if (B.pol)
-            for (uint32_t i = tid; i < nblk; i += NT) B.pol[s0 + i] = s_pol[i];
-        __syncthreads();   // the value staging is free for the next tile's previous values
+            for (uint32_t i = lane; i < nblk; i += 32) B.pol[s0 + i] = s_pol[i];
+        __syncwarp();   // the value staging is free for the next tile's previous values
         if (next < ntiles) prefetch_old(next);
         l1_commit();
     }
