@@ -80,7 +80,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (FileNotFoundError, OSError):
@@ -89,6 +89,13 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def wait_ready(self, timeout_s: float = 5.0):
+        """Wait for the first sample, so that the timed region is sampled from its start."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout_s:
+            time.sleep(0.01)
+        self.lines.clear()
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -303,7 +310,7 @@ def lifo1_executed_fmas(inst) -> int:
 # summarised in profiles/; an entry is dropped when that kernel changes
 NCU_TRAFFIC = {
     ("cfg2_m5L2Q20_nb_fifo", "sweep_group_kernel (lane width 21)"): 34_112_768,
-    ("cfg4_m8L1Q10_lifo", "sweep_lifo1_kernel"): 394_354_688,
+    ("cfg4_m8L1Q10_lifo", "sweep_lifo1_kernel"): 394_590_208,
 }
 
 
@@ -324,23 +331,27 @@ def kernel_name_of(vi, inst, kch, kw) -> str:
             vi.VI_KERNEL_LIFO_L1: "sweep_lifo1_kernel"}.get(kch, f"sweep_group_kernel (lane width {kw})")
 
 
-def time_sweep_kernel(vi, torch, h, V, stream, flush, reps: int = 20) -> float:
-    """Average duration of the dominant kernel: back-to-back single sweeps (vi_backup,
-    the same kernel and grid as the solve) between CUDA events on the launching stream."""
+def time_sweep_kernel(vi, torch, h, V, stream, flush, reps: int = 20, rounds: int = 5) -> float:
+    """Duration of the dominant kernel: the median over `rounds` of the average of `reps`
+    back-to-back single sweeps (vi_backup, the same kernel and grid as the solve) between
+    CUDA events on the launching stream, L2 flushed before each round."""
     V2 = torch.empty_like(V)
     vi.vi_backup(h, V, V2, None, stream=stream, stats=False)
-    flush.fill_(1.0)
-    k0 = torch.cuda.Event(enable_timing=True)
-    k1 = torch.cuda.Event(enable_timing=True)
-    k0.record(stream)
-    for i in range(reps):
-        if i % 2 == 0:
-            vi.vi_backup(h, V, V2, None, stream=stream, stats=False)
-        else:
-            vi.vi_backup(h, V2, V, None, stream=stream, stats=False)
-    k1.record(stream)
-    k1.synchronize()
-    return k0.elapsed_time(k1) / reps
+    avg = []
+    for _ in range(rounds):
+        flush.fill_(1.0)
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        for i in range(reps):
+            if i % 2 == 0:
+                vi.vi_backup(h, V, V2, None, stream=stream, stats=False)
+            else:
+                vi.vi_backup(h, V2, V, None, stream=stream, stats=False)
+        k1.record(stream)
+        k1.synchronize()
+        avg.append(k0.elapsed_time(k1) / reps)
+    return float(np.median(avg))
 
 
 def roofline_of(vi, torch, inst, kernel_name: str, k_ms: float, sm_mhz: float, l2_gbs) -> dict:
@@ -500,10 +511,11 @@ def run_native(args):
     nominal = float(n) * sizes["n_actions"] * sizes["n_outcomes"]
 
     sflags = vi.VI_FLAG_NO_GRAPH if args.no_graph else 0
-    for _ in range(args.warmup):
-        vi.vi_solve(h, TOL, args.max_iters, V, pol, flags=sflags)
     sampler = ClockSampler(local)
     sampler.start()
+    for _ in range(args.warmup):
+        vi.vi_solve(h, TOL, args.max_iters, V, pol, flags=sflags)
+    sampler.wait_ready()
     barrier_sync(world)
     step_ms, iters = [], []
     t_wall0 = time.perf_counter()
@@ -519,14 +531,15 @@ def run_native(args):
         iters.append(info["iters"])
     barrier_sync(world)
     wall = time.perf_counter() - t_wall0
-    clocks = sampler.stop()
     dev_s = sum(step_ms) / 1000.0
     dev_s_max = max_over_ranks(dev_s, world)
     updates = nominal * sum(iters)
     value = replica_value(updates, dev_s_max, world)
 
-    # dominant kernel: single sweep launches (same kernel, same grid) timed with events
+    # dominant kernel: single sweep launches (same kernel, same grid) timed with events,
+    # still inside the clock-sampling window
     k_ms = time_sweep_kernel(vi, torch, h, V, stream, flush)
+    clocks = sampler.stop()
     kch, kw = vi.vi_problem_kernel(h)
     kernel_name = kernel_name_of(vi, inst, kch, kw)
     pk = peaks()
@@ -958,7 +971,7 @@ def run_serving(n_requests: int = 512, seed: int = 5, slots: int = 64, budget_gb
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="cfg4", choices=sorted(WORKLOADS))
