@@ -191,6 +191,13 @@ def oracle_sample_rate(inst, seconds_target: float, seed: int = 0):
                 seconds=dt)
 
 
+def workload_config(inst, l2: str, parallelism: str) -> dict:
+    """The workload both arms report: the instance, its sizes and the stopping test,
+    then how the arm ran it."""
+    return {"workload": inst.name, "states": inst.n_states, "actions": inst.n_actions,
+            "outcomes": inst.n_outcomes, "tol": TOL, "stop_rule": "span", "l2": l2, "parallelism": parallelism}
+
+
 def run_reference(args):
     import torch  # noqa: F401  (rank/world plumbing only)
     rank = int(os.environ.get("RANK", 0))
@@ -210,8 +217,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * float(np.mean(secs)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": inst.name, "states": inst.n_states, "actions": inst.n_actions,
-                   "outcomes": inst.n_outcomes, "parallelism": "host OpenMP"},
+        "config": workload_config(inst, "not applicable (host cores)", "host OpenMP"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                          "sample": r["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -630,11 +636,11 @@ def run_native(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * dev_s_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision or inst.precision], "data": "synthetic",
-            "config": {"workload": inst.name, "states": n, "actions": sizes["n_actions"],
-                       "outcomes": sizes["n_outcomes"], "sweeps_per_solve": iters[-1], "tol": TOL,
-                       "converged": bool(info["status"] == vi.VI_OK), "precision": args.precision or inst.precision,
-                       "stop_rule": "span", "l2": "flushed between steps (2x L2 write)",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "config": workload_config(inst, "flushed between steps (2x L2 write); 2 x 156 MB of values exceed L2"
+                                      if inst.n_states * 16 > L2_BYTES else "flushed between steps (2x L2 write)",
+                                      f"replicas x{world}" if world > 1 else "single GPU"),
+            "solve": {"sweeps": iters[-1], "converged": bool(info["status"] == vi.VI_OK),
+                      "precision": args.precision or inst.precision},
             "gpu_launches": solve_launches(iters, args.no_graph, args.max_iters,
                                            3 if (len(inst.products) == 2 and kch == vi.VI_KERNEL_GROUP) else 1),
             "clocks": clocks,
