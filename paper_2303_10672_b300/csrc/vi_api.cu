@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -969,13 +970,32 @@ static vi_status ensure_scratch(vi_problem *h) {
 
 static vi_status launch_desc(const LaunchDesc &ld, void **args, cudaStream_t s) {
     for (int i = 0; i < ld.n_pre; ++i) CUDA_TRY(cudaLaunchKernel(ld.pre_fn[i], ld.pre_grid[i], ld.pre_block[i], args, 0, s));
-    CUDA_TRY(cudaLaunchKernel(ld.fn, ld.grid, ld.block, args, ld.smem, s));
+    if (!ld.pdl || ld.n_pre) {
+        CUDA_TRY(cudaLaunchKernel(ld.fn, ld.grid, ld.block, args, ld.smem, s));
+        return VI_OK;
+    }
+    // the kernel waits for the grids before it in the stream itself (griddepcontrol),
+    // so it may start while the previous kernel's last blocks run
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = ld.grid;
+    cfg.blockDim = ld.block;
+    cfg.dynamicSmemBytes = ld.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CUDA_TRY(cudaLaunchKernelExC(&cfg, ld.fn, args));
     return VI_OK;
 }
 
-// kernel nodes of one sweep (pre-kernels, then the sweep) after `dep`; returns the last node
+// kernel nodes of one sweep (pre-kernels, then the sweep) after `dep`; returns the last
+// node.  programmatic: `dep` is the previous sweep of the same kernel, which lets this
+// one start its set-up early (LaunchDesc::pdl)
 static vi_status add_sweep_nodes(cudaGraph_t g, const LaunchDesc &ld, void **args, cudaGraphNode_t dep,
-                                 cudaGraphNode_t *last) {
+                                 cudaGraphNode_t *last, bool programmatic = false) {
     cudaKernelNodeParams kn;
     cudaGraphNode_t prev = dep;
     for (int i = 0; i <= ld.n_pre; ++i) {
@@ -987,7 +1007,17 @@ static vi_status add_sweep_nodes(cudaGraph_t g, const LaunchDesc &ld, void **arg
         kn.sharedMemBytes = pre ? 0u : (unsigned)ld.smem;
         kn.kernelParams = args;
         cudaGraphNode_t node;
-        CUDA_TRY(cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kn));
+        if (programmatic && ld.pdl && !ld.n_pre && prev) {
+            CUDA_TRY(cudaGraphAddKernelNode(&node, g, nullptr, 0, &kn));
+            cudaGraphEdgeData ed;
+            memset(&ed, 0, sizeof(ed));
+            ed.from_port = cudaGraphKernelNodePortProgrammatic;
+            ed.to_port = 0;
+            ed.type = cudaGraphDependencyTypeProgrammatic;
+            CUDA_TRY(cudaGraphAddDependencies(g, &prev, &node, &ed, 1));
+        } else {
+            CUDA_TRY(cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kn));
+        }
         prev = node;
     }
     *last = prev;
@@ -996,7 +1026,24 @@ static vi_status add_sweep_nodes(cudaGraph_t g, const LaunchDesc &ld, void **arg
 
 constexpr int kSweepsPerPass = 4;
 
+// programmatic edges between the sweeps of a loop pass; cleared (for the process) if a
+// graph with them cannot be built or instantiated, and the graph is built without
+static std::atomic<bool> g_graph_pdl{true};
+
+static vi_status build_graph_once(vi_problem *h, bool pdl);
+
 static vi_status build_graph(vi_problem *h) {
+    if (h->graph_exec && h->graph_xw == h->sweep_xw) return VI_OK;
+    if (g_graph_pdl.load()) {
+        const vi_status st = build_graph_once(h, true);
+        if (st == VI_OK) return VI_OK;
+        cudaGetLastError();
+        g_graph_pdl.store(false);
+    }
+    return build_graph_once(h, false);
+}
+
+static vi_status build_graph_once(vi_problem *h, bool pdl) {
     if (h->graph_exec && h->graph_xw == h->sweep_xw) return VI_OK;
     if (h->graph_exec) {
         cudaGraphExecDestroy(h->graph_exec);
@@ -1056,7 +1103,7 @@ static vi_status build_graph(vi_problem *h) {
     vi_status vs = VI_OK;
     for (int k = 0; k < kSweepsPerPass; ++k) {
         cudaGraphNode_t n_next;
-        vs = add_sweep_nodes(body, ld_sweep, sweep_args, n_sweep, &n_next);
+        vs = add_sweep_nodes(body, ld_sweep, sweep_args, n_sweep, &n_next, pdl && k > 0);
         if (vs != VI_OK) return vs;
         n_sweep = n_next;
     }

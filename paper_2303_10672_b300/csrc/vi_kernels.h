@@ -62,6 +62,11 @@ struct LaunchDesc {
     int n_pre = 0;
     const void *pre_fn[2] = {nullptr, nullptr};
     dim3 pre_grid[2], pre_block[2];
+    // 1: fn lets its dependents launch early and waits for the grids it depends on
+    // (griddepcontrol) before it reads any value or solve state, so it may be launched
+    // as a programmatic dependent of the previous sweep (its set-up overlaps that
+    // sweep's last blocks)
+    int pdl = 0;
 };
 // use_group = 0: generic kernel; kTcWidth: tensor-core FIFO kernel; otherwise the
 // factorised kernel with that lane width XW

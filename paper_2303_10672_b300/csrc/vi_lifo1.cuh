@@ -90,9 +90,12 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
     constexpr int NTH = G + DP - 1;    // gathered per rest: T[0..G-1], H[1..DP-1]
     static_assert(G >= 2 && G <= 16 && DP >= G && DP % 4 == 0 && DP <= 32, "lifo1 geometry");
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // a sweep launched as a programmatic dependent of this one may start its set-up
+    // (the tables below) while this one's last blocks run; values and the solve state
+    // are read only after the wait, which returns once the grids this launch depends
+    // on have completed (at once for an ordinary launch)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     SolveState *st = kp.st;
-    Bufs B;
-    if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
     const ProdParams &P = kp.p[0];
     const int rows = P.rt_rows;
     const int nF = P.tmax + 1;
@@ -117,6 +120,9 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
         for (int i = threadIdx.x; i < rows; i += NT) s_LH[i] = tab[P.off_LH + i];
     }
     __syncthreads();   // the tables are shared by the block's warps; nothing else is
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    Bufs B;
+    if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
 
     const uint32_t nS = P.nS;
     const uint32_t nR = nS / (uint32_t)G;
@@ -390,6 +396,7 @@ cudaError_t describe_lifo1_t(const KernelParams &kp, LaunchDesc &d) {
     d.block = dim3(kL1Threads);
     d.smem = smem;
     d.lpr = 1;
+    d.pdl = 1;
     return cudaSuccess;
 }
 
