@@ -40,8 +40,11 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
     constexpr int LCH = 8;   // LIFO load batch
     constexpr int LCS = 8;   // load batch of the shared LIFO sequences
     SolveState *st = kp.st;
-    Bufs B;
-    if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
+    // a standalone sweep lets the next sweep launch at its start and stages its tables
+    // before it waits for the grids it depends on (a programmatic dependent launch:
+    // the set-up overlaps the previous sweep's last blocks; the wait returns at once
+    // for an ordinary launch).  Values and the solve state are read after the wait.
+    if constexpr (COH == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const ProdParams &P = kp.p[0];
     const int G = P.G;
     const int RB = kGroupThreads / lpr;                    // rests per block
@@ -64,6 +67,9 @@ __device__ __forceinline__ void group_body(const KernelParams &kp, uint32_t bid,
         }
         __syncthreads();
     }
+    if constexpr (COH == 0) asm volatile("griddepcontrol.wait;" ::: "memory");
+    Bufs B;
+    if (!resolve_bufs(st, mode, vin_arg, vout_arg, pol_arg, B)) return;
     const float *s_RT = s_tab + P.off_RT;
     const float *s_RTlo = s_tab + P.off_RTlo;
 
@@ -657,6 +663,7 @@ cudaError_t describe_group_t(const KernelParams &kp, LaunchDesc &d) {
     d.block = dim3(kGroupThreads);
     d.smem = group_smem(kp, rb, VK);
     d.lpr = lpr;
+    d.pdl = 1;
     return cudaFuncSetAttribute(sweep_group_kernel<XW, LIFO, VK, LPIPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)d.smem);
 }
