@@ -353,16 +353,18 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
         }
         __syncwarp();   // the tile's new values and policy bytes are in place
         // -- the tile's states leave in 16-byte pieces (two states) where aligned; an
-        // extraction moves the previous values unchanged (only when a buffer is given)
+        // extraction moves the previous values unchanged (only when a buffer is given).
+        // The stores are marked streaming (evict first): this sweep never reads them, so
+        // L2 keeps the values it still gathers instead
         const uint32_t s0 = tile * (uint32_t)(32 * G);
         const uint32_t nblk = min((uint32_t)(32 * G), nS - s0);
         if (B.vout) {
             float2 *dst = (float2 *)B.vout + s0;
             if (al16) {
-                for (uint32_t i = lane; i < (nblk >> 1); i += 32) ((float4 *)dst)[i] = ((const float4 *)s_VO)[i];
-                if ((nblk & 1u) && lane == 0) dst[nblk - 1] = s_VO[nblk - 1];
+                for (uint32_t i = lane; i < (nblk >> 1); i += 32) __stcs((float4 *)dst + i, ((const float4 *)s_VO)[i]);
+                if ((nblk & 1u) && lane == 0) __stcs(dst + nblk - 1, s_VO[nblk - 1]);
             } else {
-                for (uint32_t i = lane; i < nblk; i += 32) dst[i] = s_VO[i];
+                for (uint32_t i = lane; i < nblk; i += 32) __stcs(dst + i, s_VO[i]);
             }
         }
         if (B.pol)
