@@ -315,8 +315,14 @@ def lifo1_executed_fmas(inst) -> int:
 # DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu captures
 # summarised in profiles/; an entry is dropped when that kernel changes
 NCU_TRAFFIC = {
-    ("cfg2_m5L2Q20_nb_fifo", "sweep_group_kernel (lane width 21)"): 34_112_768,
-    ("cfg4_m8L1Q10_lifo", "sweep_lifo1_kernel"): 394_590_208,
+    ("cfg2_m5L2Q20_nb_fifo", "sweep_group_kernel (lane width 21)"): 34_362_112,
+    ("cfg4_m8L1Q10_lifo", "sweep_lifo1_kernel"): 381_214_720,
+}
+# thread instructions of one launch of the dominant kernel (warp instructions x active
+# threads per warp instruction), from the same captures
+NCU_THREAD_INSTR = {
+    ("cfg2_m5L2Q20_nb_fifo", "sweep_group_kernel (lane width 21)"): 187_319_919 * 29.41,
+    ("cfg4_m8L1Q10_lifo", "sweep_lifo1_kernel"): 93_897_724 * 31.47,
 }
 
 
@@ -382,6 +388,14 @@ def roofline_of(vi, torch, inst, kernel_name: str, k_ms: float, sm_mhz: float, l
                          "(float pairs)",
                 "measured_dram_GBs": None if traffic is None else traffic / (k_ms * 1e-3) / 1e9},
     }
+    ti = NCU_THREAD_INSTR.get((inst.name, kernel_name))
+    if ti is not None:
+        # the issue ceiling: every SM issues at most 128 thread instructions per clock
+        per_update = ti / work["updates"]
+        ceiling = n_sm * 128 * sm_mhz * 1e6 / per_update
+        rate = work["updates"] / (k_ms * 1e-3)
+        out["issue"] = {"thread_instructions_per_update": per_update, "ceiling_updates_per_s": ceiling,
+                        "achieved_updates_per_s": rate, "frac": rate / ceiling}
     if kernel_name == "sweep_lifo1_kernel":
         fm = lifo1_executed_fmas(inst)
         out["executed_fmas_per_launch"] = fm
