@@ -222,53 +222,55 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
         if (next < ntiles) Rnext = prefetch_gathers(next);
         l1_commit();
 
-        float best[G];
         int arg[G];
-        if (active) {
+        {
             // -- expectations of every order: C_a = sum_{d<a} p_d T[a-d] + sum_{k>=1} p_{a+k} H~[k]
+            // (a lane past the last rest takes zeros: it only joins the warp's bounds below)
             float C[G];
 #pragma unroll
             for (int a = 0; a < G; ++a) {
                 float c = 0.f;
+                if (active) {
 #pragma unroll
-                for (int d = 0; d < a; ++d) c = fmaf(kp.pmf32[d], T[a - d], c);
+                    for (int d = 0; d < a; ++d) c = fmaf(kp.pmf32[d], T[a - d], c);
 #pragma unroll
-                for (int k = 1; a + k < DP; ++k) c = fmaf(kp.pmf32[a + k], H[k], c);
+                    for (int k = 1; a + k < DP; ++k) c = fmaf(kp.pmf32[a + k], H[k], c);
+                }
                 C[a] = c;
             }
-            // -- first argmax over orders per x on the float key (-c_o a + gamma C_a + LH(R + a)) +
-            // LF(x + R + a): the rest's LF window covers every key
+            // -- first argmax over orders per x on the float key ks_a + LF(x + R + a), with
+            // ks_a = -c_o a + gamma C_a + LH(R + a): the rest's LF window covers every key
             float Fw[2 * G];
 #pragma unroll
             for (int i = 0; i < 2 * G - 1; ++i) Fw[i] = s_LF[Rrest + i];
             Fw[2 * G - 1] = 0.f;
+            float ks[G];
 #pragma unroll
             for (int a = 0; a < G; ++a) {
                 const float bl = __fmul_rn(gam, C[a]);
                 kc_col[a * 32] = bl;
-                const float ks = __fadd_rn(__fadd_rn(__fmul_rn(-c_o, (float)a), bl), s_LH[Rrest + a]);
-                const float2 ks2 = make_float2(ks, ks);
-                float key[G + 1];
-                // pairs (x, x+1) start where x + a is even, so that each pair of LF values is
-                // an aligned register pair (lane-wise __fadd_rn)
-                if (a & 1) key[0] = __fadd_rn(ks, Fw[a]);
+                ks[a] = __fadd_rn(__fadd_rn(__fmul_rn(-c_o, (float)a), bl), s_LH[Rrest + a]);
+            }
+            // LF is concave (its -E[(T - D)^+] term is), so the key has decreasing
+            // differences in (x, a) and the first argmax does not increase with x: the orders
+            // past the largest one the warp chose for x - 1 are not searched for x.  (Where
+            // rounding of the float keys breaks the monotonicity, the orders it would have
+            // preferred tie within that rounding.)
+            int lim = G - 1;
 #pragma unroll
-                for (int x = a & 1; x < G; x += 2) {
-                    const float2 k2 = __fadd2_rn(ks2, make_float2(Fw[x + a], Fw[x + a + 1]));
-                    key[x] = k2.x;
-                    key[x + 1] = k2.y;
-                }
+            for (int x = 0; x < G; ++x) {
+                float b = __fadd_rn(ks[0], Fw[x]);
+                int ab = 0;
 #pragma unroll
-                for (int x = 0; x < G; ++x) {
-                    if (a == 0) {
-                        best[x] = key[x];
-                        arg[x] = 0;
-                    } else {
-                        const bool up = key[x] > best[x];
-                        best[x] = up ? key[x] : best[x];
-                        arg[x] = up ? a : arg[x];
-                    }
+                for (int a = 1; a < G; ++a) {
+                    if (a > lim) break;   // uniform across the warp
+                    const float key = __fadd_rn(ks[a], Fw[x + a]);
+                    const bool up = key > b;
+                    b = up ? key : b;
+                    ab = up ? a : ab;
                 }
+                arg[x] = ab;
+                lim = __reduce_max_sync(0xffffffffu, active ? ab : 0);
             }
         }
         l1_wait<1>();   // this lane's pieces of the previous values have landed
