@@ -1049,7 +1049,13 @@ two_mix_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, u
     kp.two_mix[t] = acc.s;
 }
 
-// KAHAN = 1: the sum over d1 is compensated like the E2 and mixture sums
+// KAHAN = 1: the sum over d1 is compensated like the E2 and mixture sums.  Sixteen
+// lanes share a state, lane j taking the product-1 orders a1 = j, j + 16, ..: each
+// keeps the first argmax of its orders, and the lanes' bests are combined pairwise
+// (the better one wins, an exact tie goes to the smaller joint order), so the first
+// argmax over all orders comes out.  (Lanes over the product-2 orders instead, which
+// run equal d1 loops, measured 6% slower.)
+constexpr int kTwoLanes = 16;
 template <int KAHAN>
 __global__ void __launch_bounds__(kGenericThreads)
 sweep_two_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg, uint8_t *pol_arg, int) {
@@ -1064,15 +1070,17 @@ sweep_two_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg,
     const float gam = (float)kp.gamma;
     const int lifo = kp.issuing;
     float mx = -INFINITY, mn = INFINITY;
-    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t s = blockIdx.x * (uint32_t)(kGenericThreads / kTwoLanes) + (threadIdx.x / kTwoLanes);
+    const int j = (int)(threadIdx.x % kTwoLanes);
+    float bh = -INFINITY, bl = 0.f;
+    int arg = 0;
+    float2 R0 = make_float2(0.f, 0.f);
     if (s < kp.nS) {
         const uint32_t s2 = s / S1;
         const ProdState p1s = prod_state(P1, s - s2 * S1);
         const ProdState p2s = prod_state(P2, s2);
-        const float2 R0 = V2[two_base_state(kp, p1s, p2s, 0)];
-        float bh = -INFINITY, bl = 0.f;
-        int arg = 0;
-        for (int a1 = 0; a1 < P1.G; ++a1) {
+        R0 = V2[two_base_state(kp, p1s, p2s, 0)];
+        for (int a1 = j; a1 < P1.G; a1 += kTwoLanes) {
             const ProdAction A1 = prod_action(P1, p1s, a1, lifo);
             const int top1 = min(A1.T, P1.dmax + 1);   // d1 in [0, top1)
             for (int a2 = 0; a2 < P2.G; ++a2) {
@@ -1117,6 +1125,23 @@ sweep_two_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_arg,
                 arg = up ? a1 * P2.G + a2 : arg;
             }
         }
+    }
+    // the state's lanes: lower lanes hold the lower product-1 orders
+#pragma unroll
+    for (int off = 1; off < kTwoLanes; off <<= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, bh, off);
+        const float ol = __shfl_xor_sync(0xffffffffu, bl, off);
+        const int oa = __shfl_xor_sync(0xffffffffu, arg, off);
+        const bool lower = (j & off) == 0;
+        const float Lh = lower ? bh : oh, Ll = lower ? bl : ol, Uh = lower ? oh : bh, Ul = lower ? ol : bl;
+        const int La = lower ? arg : oa, Ua = lower ? oa : arg;
+        const float diff = __fadd_rn(__fsub_rn(Uh, Lh), __fsub_rn(Ul, Ll));
+        const bool up = diff > 0.f || (diff == 0.f && Ua < La);
+        bh = up ? Uh : Lh;
+        bl = up ? Ul : Ll;
+        arg = up ? Ua : La;
+    }
+    if (s < kp.nS && j == 0) {
         const float2 vold = V2[s];
         if (mode == MODE_EXTRACT) {
             if (B.vout) ((float2 *)B.vout)[s] = vold;
@@ -1611,7 +1636,8 @@ static cudaError_t describe_two(const KernelParams &kp, int kahan, LaunchDesc &d
     const uint64_t n_e2 = (uint64_t)kp.p[0].nS * kp.p[1].nS * (uint32_t)kp.p[1].G;
     const uint64_t n_mix = (uint64_t)kp.p[1].nS * (uint32_t)kp.p[1].G * (uint32_t)kp.two_nt1;
     d.fn = kahan ? (const void *)sweep_two_kernel<1> : (const void *)sweep_two_kernel<0>;
-    d.grid = dim3((kp.nS + kGenericThreads - 1) / kGenericThreads);
+    constexpr uint32_t per_block = kGenericThreads / kTwoLanes;   // states per block
+    d.grid = dim3((unsigned)(((uint64_t)kp.nS + per_block - 1) / per_block));
     d.block = dim3(kGenericThreads);
     d.smem = 0;
     d.lpr = 0;
