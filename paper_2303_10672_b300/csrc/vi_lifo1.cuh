@@ -88,6 +88,7 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
     constexpr int CB = l1_bits(G);
     constexpr int NT = kL1Threads;
     constexpr int NTH = G + DP - 1;    // gathered per rest: T[0..G-1], H[1..DP-1]
+    constexpr int XB = 2;              // x searched together in the first argmax
     static_assert(G >= 2 && G <= 16 && DP >= G && DP % 4 == 0 && DP <= 32, "lifo1 geometry");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // a sweep launched as a programmatic dependent of this one may start its set-up
@@ -240,10 +241,11 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
             }
             // -- first argmax over orders per x on the float key ks_a + LF(x + R + a), with
             // ks_a = -c_o a + gamma C_a + LH(R + a): the rest's LF window covers every key
-            float Fw[2 * G];
+            float Fw[2 * G + XB];
 #pragma unroll
             for (int i = 0; i < 2 * G - 1; ++i) Fw[i] = s_LF[Rrest + i];
-            Fw[2 * G - 1] = 0.f;
+#pragma unroll
+            for (int i = 2 * G - 1; i < 2 * G + XB; ++i) Fw[i] = 0.f;
             float ks[G];
 #pragma unroll
             for (int a = 0; a < G; ++a) {
@@ -253,24 +255,46 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
             }
             // LF is concave (its -E[(T - D)^+] term is), so the key has decreasing
             // differences in (x, a) and the first argmax does not increase with x: the orders
-            // past the largest one the warp chose for x - 1 are not searched for x.  (Where
+            // past the largest one the warp chose for the x before are not searched.  (Where
             // rounding of the float keys breaks the monotonicity, the orders it would have
-            // preferred tie within that rounding.)
+            // preferred tie within that rounding.)  The x go in pairs under the bound of the
+            // pair before, two independent compare-select chains in flight; once the bound is
+            // order 0, every later x takes order 0 with no search.
             int lim = G - 1;
 #pragma unroll
-            for (int x = 0; x < G; ++x) {
-                float b = __fadd_rn(ks[0], Fw[x]);
-                int ab = 0;
+            for (int x = 0; x < G; x += XB) {
+                if (x > 0 && lim == 0) {   // uniform across the warp
+#pragma unroll
+                    for (int i = 0; i < XB; ++i)
+                        if (x + i < G) arg[x + i] = 0;
+                    continue;
+                }
+                float b[XB];
+                int ab[XB];
+#pragma unroll
+                for (int i = 0; i < XB; ++i) {
+                    b[i] = __fadd_rn(ks[0], Fw[x + i]);   // x + i >= G reads the zero pad: unused
+                    ab[i] = 0;
+                }
 #pragma unroll
                 for (int a = 1; a < G; ++a) {
                     if (a > lim) break;   // uniform across the warp
-                    const float key = __fadd_rn(ks[a], Fw[x + a]);
-                    const bool up = key > b;
-                    b = up ? key : b;
-                    ab = up ? a : ab;
+#pragma unroll
+                    for (int i = 0; i < XB; ++i) {
+                        const float key = __fadd_rn(ks[a], Fw[x + i + a]);
+                        const bool up = key > b[i];
+                        b[i] = up ? key : b[i];
+                        ab[i] = up ? a : ab[i];
+                    }
                 }
-                arg[x] = ab;
-                lim = __reduce_max_sync(0xffffffffu, active ? ab : 0);
+                int last = ab[0];
+#pragma unroll
+                for (int i = 0; i < XB; ++i)
+                    if (x + i < G) {
+                        arg[x + i] = ab[i];
+                        last = ab[i];
+                    }
+                lim = __reduce_max_sync(0xffffffffu, active ? last : 0);
             }
         }
         l1_wait<1>();   // this lane's pieces of the previous values have landed
