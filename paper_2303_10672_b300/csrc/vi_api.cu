@@ -301,6 +301,11 @@ void fill_prod_params(ProdParams &P, int m, int L, int Q, int dmax, double c_o) 
     for (int k = 0; k + 2 <= m - 1; ++k) wz *= (uint64_t)P.G;   // G^(m-2)
     P.w_zt = (uint32_t)wz;
     P.c_o = c_o;
+    // exact division by G (Granlund and Montgomery's round-up constants, see DivG)
+    const int l = ceil_log2(P.G);
+    P.g_mag = (uint32_t)((((uint64_t)1 << 32) * (((uint64_t)1 << l) - (uint64_t)P.G)) / (uint64_t)P.G + 1u);
+    P.g_sh1 = l < 1 ? l : 1;
+    P.g_sh2 = l > 1 ? l - 1 : 0;
 }
 
 vi_status build_single_product(const vi_problem_desc &d, KernelParams &kp, std::vector<float> &ftab,

@@ -47,6 +47,8 @@ struct ProdParams {
                           // except for the units of the other slots left unsold
     int pn;               // length of p / F / tail
     double c_o;           // order cost per unit
+    uint32_t g_mag;       // x / G as a multiply-high and two shifts (DivG below)
+    int g_sh1, g_sh2;
 };
 
 struct SolveState;  // device-resident solve bookkeeping (below)
@@ -162,6 +164,21 @@ __device__ __forceinline__ double dkey_inv(unsigned long long k) {
     return __longlong_as_double((long long)b);
 }
 
+// Division of a 32-bit index by the radix G: the quotient operator (PlainDiv), or an
+// exact multiply-high with the constants of Granlund and Montgomery, "Division by
+// invariant integers using multiplication" (PLDI 1994; the round-up method for
+// every 32-bit dividend), which the host sets per product: l = ceil(log2 G),
+// g_mag = floor(2^32 (2^l - G) / G) + 1, g_sh1 = min(l, 1), g_sh2 = max(l - 1, 0).
+struct PlainDiv {
+    __device__ __forceinline__ static uint32_t q(uint32_t x, uint32_t G, const ProdParams *) { return x / G; }
+};
+struct DivG {
+    __device__ __forceinline__ static uint32_t q(uint32_t x, uint32_t, const ProdParams *P) {
+        const uint32_t t = __umulhi(x, P->g_mag);
+        return (t + ((x - t) >> P->g_sh1)) >> P->g_sh2;
+    }
+};
+
 // ---------------------------------------------------------------------------
 // The next-state walker: index of s'(e) after e units of demand reached the rest
 // slots.  Slot counts are packed `cb` bits each in consumption order.
@@ -193,7 +210,10 @@ __device__ __forceinline__ void walker_init(Walker &wk, uint32_t idx0, unsigned 
 
 // consume one unit; callers only step while units remain in the slots (e <= R).
 // The slot search is bounded so that a violated precondition cannot spin.
-__device__ __forceinline__ void walker_step(Walker &wk, int cb, int lifo, uint32_t G) {
+// (LIFO moves down a slot by dividing the slot weight by G: Div chooses how, with P
+// holding DivG's constants.)
+template <class Div = PlainDiv>
+__device__ __forceinline__ void walker_step(Walker &wk, int cb, int lifo, uint32_t G, const ProdParams *P = nullptr) {
     unsigned long long mask = (1ull << cb) - 1ull;
     for (int guard = 0; wk.left == 0; ++guard) {
         if (guard >= kMaxDigits) return;
@@ -202,7 +222,7 @@ __device__ __forceinline__ void walker_step(Walker &wk, int cb, int lifo, uint32
             wk.w *= G;
         } else {
             wk.slot -= 1;
-            wk.w /= G;
+            wk.w = Div::q(wk.w, G, P);
         }
         wk.left = (int)((wk.packed >> (cb * wk.slot)) & mask);
     }
@@ -218,13 +238,14 @@ struct RestInfo {
     int R;                       // their sum
 };
 
+template <class Div = PlainDiv>
 __device__ __forceinline__ RestInfo decode_rest(uint32_t r, const ProdParams &P) {
     RestInfo ri;
     ri.packed = 0ull;
     ri.R = 0;
     uint32_t rem = r;
     for (int j = 0; j < P.n_rest_slots; ++j) {
-        uint32_t q = rem / (uint32_t)P.G;
+        uint32_t q = Div::q(rem, (uint32_t)P.G, &P);
         int dgt = (int)(rem - q * (uint32_t)P.G);
         rem = q;
         ri.packed |= (unsigned long long)dgt << (P.cb * j);

@@ -107,16 +107,17 @@ struct ProdState {
     RestInfo ri;
 };
 
+template <class Div = PlainDiv>
 __device__ __forceinline__ ProdState prod_state(const ProdParams &P, uint32_t sk) {
     ProdState ps;
     if (P.K >= 1) {
-        ps.r = sk / (uint32_t)P.G;
+        ps.r = Div::q(sk, (uint32_t)P.G, &P);
         ps.x = (int)(sk - ps.r * (uint32_t)P.G);
     } else {
         ps.r = 0;
         ps.x = 0;
     }
-    ps.ri = decode_rest(ps.r, P);
+    ps.ri = decode_rest<Div>(ps.r, P);
     return ps;
 }
 
@@ -495,7 +496,7 @@ __global__ void solve_init_kernel(SolveState *st, uint32_t n) {
 }
 
 // ===========================================================================
-// rollouts: thread = rollout
+// rollouts: one period of one product, the KPI sums, the cost table
 // ===========================================================================
 struct RollOut {
     uint32_t s_next;
@@ -503,13 +504,15 @@ struct RollOut {
 };
 
 // one product, one period, with the sweep kernels' walker for the next state
+// (Div: how indices are divided by G, see DivG)
+template <class Div = PlainDiv>
 __device__ __forceinline__ RollOut roll_product(const ProdParams &P, int lifo, uint32_t sk, int a, int z) {
-    const ProdState ps = prod_state(P, sk);
+    const ProdState ps = prod_state<Div>(P, sk);
     const ProdAction pa = prod_action(P, ps, a, lifo);
     RollOut o;
     const int e = lifo ? min(z, pa.R) : min(max(z - pa.y1, 0), pa.R);
     Walker wk = pa.wk;
-    for (int k = 0; k < e; ++k) walker_step(wk, P.cb, lifo, (uint32_t)P.G);
+    for (int k = 0; k < e; ++k) walker_step<Div>(wk, P.cb, lifo, (uint32_t)P.G, &P);
     o.s_next = wk.idx;
     o.total = pa.T;
     o.issued = min(z, pa.T);
@@ -523,7 +526,7 @@ __device__ __forceinline__ RollOut roll_product(const ProdParams &P, int lifo, u
             o.arrived = ps.x;
         } else {
             uint32_t q = ps.r;
-            for (int j = 0; j < P.m - 2; ++j) q /= (uint32_t)P.G;
+            for (int j = 0; j < P.m - 2; ++j) q = Div::q(q, (uint32_t)P.G, &P);
             o.arrived = (int)(q % (uint32_t)P.G);
         }
     } else {
@@ -570,9 +573,10 @@ __device__ __forceinline__ void fill_cost_tab(double *t, const RollParams &rp, i
 }
 
 // one period of a single product: reward (FP64, unfused, in the oracle's order) and outcome
+template <class Div = PlainDiv>
 __device__ __forceinline__ double single_period(const ProdParams &P1, int lifo, const CostTab &ct, uint32_t s, int a,
                                                 int d1, RollOut &o) {
-    o = roll_product(P1, lifo, s, a, d1);
+    o = roll_product<Div>(P1, lifo, s, a, d1);
     double rew = 0.0;
     rew = __dsub_rn(rew, ct(0, 0, a));
     rew = __dsub_rn(rew, ct(0, 1, o.carried));
@@ -601,8 +605,54 @@ struct KpiSums {
     }
 };
 
-__global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *policy, double *returns, double *kpis,
-                               double *kpis_prod, int32_t *traj) {
+// ---------------------------------------------------------------------------
+// Rollouts: a group of LPR = 32 / RPW lanes per rollout, RPW rollouts per warp.  The
+// state is all that one period hands to the next, so a group takes LPR periods at a
+// time in three steps:
+//   A. lane j of the group draws the random words and the demands of period t0 + j
+//      (Philox counters (t, r): they do not depend on the state);
+//   B. the group walks the state chain s_t -> a_t = pi(s_t) -> s_{t+1} through the LPR
+//      periods, its lanes in step, each lane keeping (s_t, a_t) of its own period;
+//   C. lane j evaluates its period: outcome, reward and counts.
+// The return is folded in period order with the FP64 operations of a serial loop and
+// the KPI counts are integer sums, so the results are those of one thread walking
+// the whole rollout, bit for bit.  Only step B is serial, and its indices are
+// divided by G with DivG's multiply-high.  The fold is the same in every lane of a
+// group, so RPW rollouts share each FP64 instruction of it.
+// ---------------------------------------------------------------------------
+constexpr int kRollWarps = 4;   // warps per block
+// rollouts per warp: measured on B300 (config 4, 4096 x 365): 1 0.51 ms, 2 0.41, 4 0.41, 8 0.45
+constexpr int kRollRPW = 4;
+constexpr int kRollLPR = 32 / kRollRPW;    // lanes (and periods per step) per rollout
+using RollDiv = DivG;
+
+// two products, one period: both outcomes, the substitution u from the words (w2, w3)
+struct TwoOut {
+    RollOut o1, o2;
+    int own2, short1, short2;
+    uint32_t s_next;
+};
+template <class Div>
+__device__ __forceinline__ TwoOut two_period(const KernelParams &kp, int lifo, uint32_t s, int a, int d1, int d2,
+                                             uint32_t w2, uint32_t w3) {
+    const ProdParams &P1 = kp.p[0], &P2 = kp.p[1];
+    const uint32_t S1 = P1.nS;
+    const uint32_t s2 = s / S1, s1 = s - s2 * S1;
+    const int a1 = a / P2.G, a2 = a - a1 * P2.G;
+    TwoOut t;
+    t.o1 = roll_product<Div>(P1, lifo, s1, a1, d1);
+    const int u = substitutes(w2, w3, t.o1.shortage);
+    t.o2 = roll_product<Div>(P2, lifo, s2, a2, d2 + u);
+    t.own2 = min(d2, t.o2.total);
+    t.short1 = t.o1.shortage - (t.o2.issued - t.own2);
+    t.short2 = max(d2 - t.o2.total, 0);
+    t.s_next = t.o1.s_next + S1 * t.o2.s_next;
+    return t;
+}
+
+__global__ void __launch_bounds__(32 * kRollWarps)
+rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *policy, double *returns, double *kpis,
+               double *kpis_prod, int32_t *traj) {
     __shared__ unsigned long long s_thr[2][kMaxRollDmax + 1];
     __shared__ double s_ct[2 * 5 * kCostTab];
     for (int i = threadIdx.x; i <= kMaxRollDmax; i += blockDim.x) {
@@ -612,100 +662,144 @@ __global__ void rollout_kernel(KernelParams kp, RollParams rp, const uint8_t *po
     fill_cost_tab(s_ct, rp, kp.n_products);
     __syncthreads();
     const CostTab ct{s_ct, &rp, kCostTab};
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rp.n_rollouts) return;
+    constexpr int LPR = kRollLPR;
+    const int lane = threadIdx.x & 31;
+    const int sl = lane % LPR;   // lane within the rollout's group
+    const int r = (blockIdx.x * kRollWarps + (int)(threadIdx.x >> 5)) * kRollRPW + lane / LPR;
+    // a group past the last rollout runs along (its lanes take part in the shuffles) but
+    // writes nothing; a warp with no rollout leaves at once
+    if ((blockIdx.x * kRollWarps + (int)(threadIdx.x >> 5)) * kRollRPW >= rp.n_rollouts) return;
+    const bool real = r < rp.n_rollouts;
     const int lifo = kp.issuing;
+    const bool two = kp.n_products == 2;
     const uint32_t k0 = (uint32_t)(rp.seed & 0xffffffffull), k1 = (uint32_t)(rp.seed >> 32);
+    const int T = rp.warmup + rp.horizon;
+    const ProdParams &P1 = kp.p[0];
     uint32_t s = 0;
     double ret = 0.0, disc = 1.0;
     long long dem = 0, iss = 0, was = 0, arr = 0, car = 0;
     KpiSums ks;
     ks.init();
-    const ProdParams &P1 = kp.p[0];
-    for (int t = 0; t < rp.warmup + rp.horizon; ++t) {
-        // the policy load is issued first: the random numbers do not depend on it
-        const int a = __ldg(policy + s);
-        uint32_t w[4];
-        philox4x32_10((uint32_t)t, (uint32_t)r, 0u, 0u, k0, k1, w);
-        double rew = 0.0;
-        int t_dem, t_iss, t_was, t_arr, t_car;
-        int p_dem[2] = {0, 0}, p_srv[2] = {0, 0}, p_was[2] = {0, 0}, p_arr[2] = {0, 0}, p_car[2] = {0, 0};
-        uint32_t s_next;
-        if (kp.n_products == 1) {
-            const int d1 = draw_demand(w[0], s_thr[0], P1.dmax);
-            RollOut o;
-            rew = single_period(P1, lifo, ct, s, a, d1, o);
-            s_next = o.s_next;
-            t_dem = d1;
-            t_iss = o.issued;
-            t_was = o.wasted;
-            t_arr = o.arrived;
-            t_car = o.carried;
-            p_dem[0] = d1;
-            p_srv[0] = o.issued;
-            p_was[0] = o.wasted;
-            p_arr[0] = o.arrived;
-            p_car[0] = o.carried;
-        } else {
-            const ProdParams &P2 = kp.p[1];
-            const int d1 = draw_demand(w[0], s_thr[0], P1.dmax);
-            const int d2 = draw_demand(w[1], s_thr[1], P2.dmax);
-            const uint32_t S1 = P1.nS;
-            const uint32_t s2 = s / S1, s1 = s - s2 * S1;
-            const int a1 = a / P2.G, a2 = a - a1 * P2.G;
-            const RollOut o1 = roll_product(P1, lifo, s1, a1, d1);
-            const int u = substitutes(w[2], w[3], o1.shortage);
-            const RollOut o2 = roll_product(P2, lifo, s2, a2, d2 + u);
-            const int own2 = min(d2, o2.total);
-            const int short1 = o1.shortage - (o2.issued - own2);
-            const int short2 = max(d2 - o2.total, 0);
-            rew = __dsub_rn(rew, ct(0, 0, a1));
-            rew = __dsub_rn(rew, ct(0, 1, o1.carried));
-            rew = __dsub_rn(rew, ct(0, 2, short1));
-            rew = __dsub_rn(rew, ct(0, 3, o1.wasted));
-            rew = __dadd_rn(rew, ct(0, 4, o1.issued));
-            rew = __dsub_rn(rew, ct(1, 0, a2));
-            rew = __dsub_rn(rew, ct(1, 1, o2.carried));
-            rew = __dsub_rn(rew, ct(1, 2, short2));
-            rew = __dsub_rn(rew, ct(1, 3, o2.wasted));
-            rew = __dadd_rn(rew, ct(1, 4, o2.issued));
-            s_next = o1.s_next + S1 * o2.s_next;
-            t_dem = d1 + d2;
-            t_iss = o1.issued + o2.issued;
-            t_was = o1.wasted + o2.wasted;
-            t_arr = o1.arrived + o2.arrived;
-            t_car = o1.carried + o2.carried;
-            const int sub = o2.issued - own2;
-            p_dem[0] = d1;
-            p_dem[1] = d2;
-            p_srv[0] = o1.issued + sub;
-            p_srv[1] = own2;
-            p_was[0] = o1.wasted;
-            p_was[1] = o2.wasted;
-            p_arr[0] = o1.arrived;
-            p_arr[1] = o2.arrived;
-            p_car[0] = o1.carried;
-            p_car[1] = o2.carried;
+    for (int t0 = 0; t0 < T; t0 += LPR) {
+        const int t = t0 + sl;
+        const int nj = min(LPR, T - t0);   // the same for the whole warp
+        // A. this lane's period: random words and demands
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        int d1 = 0, d2 = 0;
+        if (t < T) {
+            philox4x32_10((uint32_t)t, (uint32_t)r, 0u, 0u, k0, k1, w);
+            d1 = draw_demand(w[0], s_thr[0], P1.dmax);
+            if (two) d2 = draw_demand(w[1], s_thr[1], kp.p[1].dmax);
         }
-        if (t >= rp.warmup) {
-            if (traj) traj[(size_t)r * rp.horizon + (t - rp.warmup)] = (int32_t)s;
-            ret = __dadd_rn(ret, __dmul_rn(disc, rew));
-            disc = __dmul_rn(disc, kp.gamma);
-            dem += t_dem;
-            iss += t_iss;
-            was += t_was;
-            arr += t_arr;
-            car += t_car;
-            for (int j = 0; j < 2; ++j) {
-                ks.dem[j] += p_dem[j];
-                ks.served[j] += p_srv[j];
-                ks.was[j] += p_was[j];
-                ks.arr[j] += p_arr[j];
-                ks.car[j] += p_car[j];
+        // B. the state chain of the group's periods
+        uint32_t my_s = 0u;
+        int my_a = 0;
+        for (int j = 0; j < nj; ++j) {
+            const int a = __ldg(policy + s);
+            const int dj = __shfl_sync(0xffffffffu, d1, j, LPR);
+            if (sl == j) {
+                my_s = s;
+                my_a = a;
+            }
+            if (!two) {
+                s = roll_product<RollDiv>(P1, lifo, s, a, dj).s_next;
+            } else {
+                const int dj2 = __shfl_sync(0xffffffffu, d2, j, LPR);
+                const uint32_t wj2 = __shfl_sync(0xffffffffu, w[2], j, LPR);
+                const uint32_t wj3 = __shfl_sync(0xffffffffu, w[3], j, LPR);
+                s = two_period<RollDiv>(kp, lifo, s, a, dj, dj2, wj2, wj3).s_next;
             }
         }
-        s = s_next;
+        // C. this lane's period: outcome, reward (FP64, unfused, in the oracle's order), counts
+        double rew = 0.0;
+        if (t < T) {
+            int t_dem, t_iss, t_was, t_arr, t_car;
+            int p_dem[2] = {0, 0}, p_srv[2] = {0, 0}, p_was[2] = {0, 0}, p_arr[2] = {0, 0}, p_car[2] = {0, 0};
+            if (!two) {
+                RollOut o;
+                rew = single_period<RollDiv>(P1, lifo, ct, my_s, my_a, d1, o);
+                t_dem = d1;
+                t_iss = o.issued;
+                t_was = o.wasted;
+                t_arr = o.arrived;
+                t_car = o.carried;
+                p_dem[0] = d1;
+                p_srv[0] = o.issued;
+                p_was[0] = o.wasted;
+                p_arr[0] = o.arrived;
+                p_car[0] = o.carried;
+            } else {
+                const TwoOut q = two_period<RollDiv>(kp, lifo, my_s, my_a, d1, d2, w[2], w[3]);
+                const int a1 = my_a / kp.p[1].G, a2 = my_a - a1 * kp.p[1].G;
+                rew = __dsub_rn(rew, ct(0, 0, a1));
+                rew = __dsub_rn(rew, ct(0, 1, q.o1.carried));
+                rew = __dsub_rn(rew, ct(0, 2, q.short1));
+                rew = __dsub_rn(rew, ct(0, 3, q.o1.wasted));
+                rew = __dadd_rn(rew, ct(0, 4, q.o1.issued));
+                rew = __dsub_rn(rew, ct(1, 0, a2));
+                rew = __dsub_rn(rew, ct(1, 1, q.o2.carried));
+                rew = __dsub_rn(rew, ct(1, 2, q.short2));
+                rew = __dsub_rn(rew, ct(1, 3, q.o2.wasted));
+                rew = __dadd_rn(rew, ct(1, 4, q.o2.issued));
+                t_dem = d1 + d2;
+                t_iss = q.o1.issued + q.o2.issued;
+                t_was = q.o1.wasted + q.o2.wasted;
+                t_arr = q.o1.arrived + q.o2.arrived;
+                t_car = q.o1.carried + q.o2.carried;
+                const int sub = q.o2.issued - q.own2;
+                p_dem[0] = d1;
+                p_dem[1] = d2;
+                p_srv[0] = q.o1.issued + sub;
+                p_srv[1] = q.own2;
+                p_was[0] = q.o1.wasted;
+                p_was[1] = q.o2.wasted;
+                p_arr[0] = q.o1.arrived;
+                p_arr[1] = q.o2.arrived;
+                p_car[0] = q.o1.carried;
+                p_car[1] = q.o2.carried;
+            }
+            if (t >= rp.warmup && real) {
+                if (traj) traj[(size_t)r * rp.horizon + (t - rp.warmup)] = (int32_t)my_s;
+                dem += t_dem;
+                iss += t_iss;
+                was += t_was;
+                arr += t_arr;
+                car += t_car;
+                for (int j = 0; j < 2; ++j) {
+                    ks.dem[j] += p_dem[j];
+                    ks.served[j] += p_srv[j];
+                    ks.was[j] += p_was[j];
+                    ks.arr[j] += p_arr[j];
+                    ks.car[j] += p_car[j];
+                }
+            }
+        }
+        // the discounted return, period by period
+        for (int j = 0; j < nj; ++j) {
+            const double rj = __shfl_sync(0xffffffffu, rew, j, LPR);
+            if (t0 + j >= rp.warmup) {
+                ret = __dadd_rn(ret, __dmul_rn(disc, rj));
+                disc = __dmul_rn(disc, kp.gamma);
+            }
+        }
     }
+    // the group's sums of the counts (integers: any order gives the same sums)
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) {
+        dem += __shfl_xor_sync(0xffffffffu, dem, o);
+        iss += __shfl_xor_sync(0xffffffffu, iss, o);
+        was += __shfl_xor_sync(0xffffffffu, was, o);
+        arr += __shfl_xor_sync(0xffffffffu, arr, o);
+        car += __shfl_xor_sync(0xffffffffu, car, o);
+        for (int j = 0; j < 2; ++j) {
+            ks.dem[j] += __shfl_xor_sync(0xffffffffu, ks.dem[j], o);
+            ks.served[j] += __shfl_xor_sync(0xffffffffu, ks.served[j], o);
+            ks.was[j] += __shfl_xor_sync(0xffffffffu, ks.was[j], o);
+            ks.arr[j] += __shfl_xor_sync(0xffffffffu, ks.arr[j], o);
+            ks.car[j] += __shfl_xor_sync(0xffffffffu, ks.car[j], o);
+        }
+    }
+    if (sl != 0 || !real) return;
     returns[r] = ret;
     if (kpis) {
         const double fd = (double)dem, fi = (double)iss, fw = (double)was, fa = (double)arr;
@@ -743,14 +837,14 @@ __global__ void basestock_kernel(KernelParams kp, RollParams rp, int s_lo, int n
         int stock = 0;
         uint32_t rem = s;
         for (int k = 0; k < P1.K; ++k) {
-            const uint32_t q = rem / (uint32_t)P1.G;
+            const uint32_t q = DivG::q(rem, (uint32_t)P1.G, &P1);
             stock += (int)(rem - q * (uint32_t)P1.G);
             rem = q;
         }
         const int a = min(max(S - stock, 0), P1.Q);
         const int d1 = draw_demand(w[0], s_thr, P1.dmax);
         RollOut o;
-        const double rew = single_period(P1, lifo, ct, s, a, d1, o);
+        const double rew = single_period<DivG>(P1, lifo, ct, s, a, d1, o);
         if (t >= rp.warmup) {
             ret = __dadd_rn(ret, __dmul_rn(disc, rew));
             disc = __dmul_rn(disc, kp.gamma);
@@ -1742,9 +1836,9 @@ cudaError_t launch_diff_range(const double *a, const double *b, uint32_t n, Solv
 
 cudaError_t launch_rollouts(const KernelParams &kp, const RollParams &rp, const uint8_t *policy, double *returns,
                             double *kpis, double *kpis_prod, int32_t *traj, cudaStream_t stream) {
-    const int threads = 128;
-    const int blocks = (rp.n_rollouts + threads - 1) / threads;
-    rollout_kernel<<<blocks, threads, 0, stream>>>(kp, rp, policy, returns, kpis, kpis_prod, traj);
+    const int per_block = kRollWarps * kRollRPW;
+    const int blocks = (rp.n_rollouts + per_block - 1) / per_block;
+    rollout_kernel<<<blocks, 32 * kRollWarps, 0, stream>>>(kp, rp, policy, returns, kpis, kpis_prod, traj);
     return cudaGetLastError();
 }
 
