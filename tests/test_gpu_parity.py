@@ -217,6 +217,21 @@ def test_rollouts_bit_exact(inst):
     rollout_parity(inst, pol, 64, 50, seed=0xDEADBEEF12345, warmup=3)
 
 
+@pytest.mark.parametrize("n, horizon, warmup", [(37, 29, 5), (1, 7, 0), (17, 9, 8), (5, 1, 0)])
+def test_rollouts_ragged_counts_bit_exact(n, horizon, warmup):
+    # rollout counts that leave part of the last warp's lane groups empty, and
+    # horizons that end inside a group's block of periods
+    inst = SMALL[7]
+    pol = oracle.Problem(inst).vi_solve(tol=1e-4, max_iters=3000)["policy"]
+    rollout_parity(inst, pol, n, horizon, seed=1234567, warmup=warmup)
+
+
+def test_rollouts_ragged_two_products_bit_exact():
+    inst = workloads.config3(Q=2)
+    pol = oracle.Problem(inst).vi_solve(tol=1e-4, max_iters=3000)["policy"]
+    rollout_parity(inst, pol, 13, 11, seed=99, warmup=2)
+
+
 def test_rollouts_two_products_bit_exact():
     inst = workloads.config3(Q=3)
     pol = oracle.Problem(inst).vi_solve(tol=1e-4, max_iters=3000)["policy"]
