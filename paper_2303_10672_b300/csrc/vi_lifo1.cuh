@@ -89,9 +89,6 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
     constexpr int NT = kL1Threads;
     constexpr int NTH = G + DP - 1;    // gathered per rest: T[0..G-1], H[1..DP-1]
     constexpr int XB = 2;              // x searched together in the first argmax
-#ifndef VI_LIFO1_HUNROLL
-#define VI_LIFO1_HUNROLL 0
-#endif
     static_assert(G >= 2 && G <= 16 && DP >= G && DP % 4 == 0 && DP <= 32, "lifo1 geometry");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // a sweep launched as a programmatic dependent of this one may start its set-up
@@ -164,25 +161,6 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
         uint32_t w = (nrs > 0) ? w_top / (uint32_t)G : 0u;
         uint32_t idx = r;
         float2 *col = s_TH + G * 32 + lane;   // H[1] of this lane
-#if VI_LIFO1_HUNROLL
-        // unit by unit, unrolled over k: a slot with no units left passes to the next one
-        // down (hcount <= the units held, so one always remains; the search is bounded)
-        int slot = nrs - 1;
-        int left = (nrs > 0) ? (int)((packed >> (CB * slot)) & ((1ull << CB) - 1ull)) : 0;
-#pragma unroll
-        for (int k = 0; k < DP - 1; ++k) {
-            if (k < hcount) {
-                for (int guard = 0; left == 0 && guard < nrs; ++guard) {
-                    --slot;
-                    w /= (uint32_t)G;
-                    left = (int)((packed >> (CB * slot)) & ((1ull << CB) - 1ull));
-                }
-                idx -= w;
-                --left;
-                l1_cp8(col + k * 32, V2 + idx);
-            }
-        }
-#else
         int k = 0;
         for (int slot = nrs - 1; slot >= 0 && k < hcount; --slot) {
             const int units = min((int)((packed >> (CB * slot)) & ((1ull << CB) - 1ull)), hcount - k);
@@ -193,7 +171,6 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
             }
             w /= (uint32_t)G;
         }
-#endif
         return Rr;
     };
     // the previous values of tile t's states, in 16-byte pieces where aligned
