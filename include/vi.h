@@ -433,10 +433,13 @@ vi_status vi_server_destroy(vi_server srv);
  * the GPU -- on different streams, or from several host threads without
  * ordering -- race.  The first call on a device looks up the array's device
  * address (a one-time set-up for that device); make that first call before
- * any stream capture.  The address is kept for the life of the process, so
+ * any stream capture.  A call on a stream that is being captured is refused
+ * with VI_EINVAL: the tables go up from a host staging buffer that the next
+ * call overwrites.  The address is kept for the life of the process, so
  * the device's primary context must not be reset (cudaDeviceReset) between
  * calls.  No cudaMalloc, cudaFree or other allocator is called.
- * Errors: VI_EINVAL (bad instance or buffers, tables too large), VI_ECUDA. */
+ * Errors: VI_EINVAL (bad instance or buffers, tables too large, stream being
+ * captured), VI_ECUDA. */
 #define VI_NOALLOC_MAX_TABLE_FLOATS 16384
 vi_status vi_backup_noalloc(int m, int L, int Q, const double cost[5], const double *pmf, int dmax,
                             double gamma, int issuing, const void *V_in, void *V_out, uint8_t *policy,

@@ -105,6 +105,13 @@ extern "C" vi_status vi_backup_noalloc(int m, int L, int Q, const double cost[5]
     if (ns >= 4294967296.0 || K > kMaxDigits) return vi_fail(VI_EINVAL, "|S| does not fit 32 bits");
 
     cudaStream_t s = (cudaStream_t)stream;
+    // the table upload reads a host staging buffer that the next call overwrites, and the
+    // statistics read-back synchronises the stream: neither belongs in a captured graph
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &cs);
+    if (ce != cudaSuccess) return vi_fail(VI_ECUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(ce));
+    if (cs != cudaStreamCaptureStatusNone)
+        return vi_fail(VI_EINVAL, "vi_backup_noalloc is refused on a stream that is being captured");
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     KernelParams kp;
     memset(&kp, 0, sizeof(kp));

@@ -86,3 +86,33 @@ def test_noalloc_refuses_short_buffers():
         assert e.value.status == vi.VI_EINVAL
     with pytest.raises(vi.ViError):
         vi.vi_backup_noalloc(p.m, p.L, p.Q, p.cost[:4], p.pmf, inst.gamma, inst.issuing, V, torch.empty_like(V))
+
+
+def test_noalloc_refused_while_capturing():
+    # the tables go up from a host staging buffer that the next call overwrites, so a
+    # captured call would replay another call's tables: a capturing stream is refused
+    inst = workloads.config1()
+    p = inst.products[0]
+    n = inst.n_states
+    V = torch.zeros(2 * n, dtype=torch.float32, device="cuda")
+    W = torch.zeros_like(V)
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    vi.lib()                     # the library is loaded before the capture starts
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        g.capture_begin()
+        try:
+            W.add_(1.0)          # the capture holds one node of its own
+            with pytest.raises(vi.ViError) as e:
+                vi.vi_backup_noalloc(p.m, p.L, p.Q, p.cost, p.pmf, inst.gamma, inst.issuing, V, W,
+                                     stream=side)
+            assert e.value.status == vi.VI_EINVAL
+        finally:
+            g.capture_end()
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(W[0]) == 1.0                    # the capture itself was left intact
+    # outside the capture the same call runs
+    vi.vi_backup_noalloc(p.m, p.L, p.Q, p.cost, p.pmf, inst.gamma, inst.issuing, V, W, stream=side)
+    torch.cuda.synchronize()
