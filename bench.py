@@ -312,6 +312,18 @@ def lifo1_executed_fmas(inst) -> int:
     return (p.n_states // G) * G * (DP - 1)
 
 
+def fifo_col_executed_fmas(inst) -> int:
+    """Multiply-adds of the expectations in the FIFO column sweep per launch: per column
+    of Q+1 rests and per order, dmax (dmax + 1) / 2 for the first rest's sum over the
+    demand (x' + k <= dmax) and, for each further rest z = 1..Q, one per x' still needed
+    (x' < min(dmax, 2Q - z + 1))."""
+    p = inst.products[0]
+    G = p.Q + 1
+    cols = p.n_states // (G * G)
+    per_order = p.dmax * (p.dmax + 1) // 2 + sum(min(p.dmax, 2 * p.Q - z + 1) for z in range(1, G))
+    return cols * G * per_order
+
+
 # DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu captures
 # summarised in profiles/; an entry is dropped when that kernel changes
 NCU_TRAFFIC = {
@@ -340,7 +352,8 @@ def kernel_name_of(vi, inst, kch, kw) -> str:
         return ("twop_e2_kernel + twop_mix_kernel + twop_sweep_kernel" if inst.products[0].L >= 2
                 else "two_e2_kernel + two_mix_kernel + sweep_two_kernel")
     return {vi.VI_KERNEL_GENERIC: "sweep_generic_kernel", vi.VI_KERNEL_TENSOR: "sweep_tc_kernel",
-            vi.VI_KERNEL_LIFO_L1: "sweep_lifo1_kernel"}.get(kch, f"sweep_group_kernel (lane width {kw})")
+            vi.VI_KERNEL_LIFO_L1: "sweep_lifo1_kernel",
+            vi.VI_KERNEL_FIFO_COL: "sweep_fifo_col_kernel"}.get(kch, f"sweep_group_kernel (lane width {kw})")
 
 
 def time_sweep_kernel(vi, torch, h, V, stream, flush, reps: int = 20, rounds: int = 5) -> float:
@@ -396,8 +409,8 @@ def roofline_of(vi, torch, inst, kernel_name: str, k_ms: float, sm_mhz: float, l
         rate = work["updates"] / (k_ms * 1e-3)
         out["issue"] = {"thread_instructions_per_update": per_update, "ceiling_updates_per_s": ceiling,
                         "achieved_updates_per_s": rate, "frac": rate / ceiling}
-    if kernel_name == "sweep_lifo1_kernel":
-        fm = lifo1_executed_fmas(inst)
+    if kernel_name in ("sweep_lifo1_kernel", "sweep_fifo_col_kernel"):
+        fm = lifo1_executed_fmas(inst) if kernel_name == "sweep_lifo1_kernel" else fifo_col_executed_fmas(inst)
         out["executed_fmas_per_launch"] = fm
         out["executed_fp32_frac"] = 2 * fm / (k_ms * 1e-3) / 1e12 / fp32_peak
     if len(inst.products) == 1 and l2_gbs:
@@ -511,7 +524,8 @@ def run_native(args):
     prods = [dict(m=q.m, L=q.L, Q=q.Q, cost=q.cost, pmf=q.pmf) for q in inst.products]
     desc, keep = vi.make_desc(prods, inst.gamma, inst.issuing, prec, vi.VI_STOP_SPAN, inst.subst_rate)
     kernel = {"auto": vi.VI_KERNEL_AUTO, "group": vi.VI_KERNEL_GROUP, "tensor": vi.VI_KERNEL_TENSOR,
-              "generic": vi.VI_KERNEL_GENERIC, "lifo1": vi.VI_KERNEL_LIFO_L1}[args.kernel]
+              "generic": vi.VI_KERNEL_GENERIC, "lifo1": vi.VI_KERNEL_LIFO_L1,
+              "fifocol": vi.VI_KERNEL_FIFO_COL}[args.kernel]
 
     def configure(hh):
         if kernel != vi.VI_KERNEL_AUTO:
@@ -1003,7 +1017,7 @@ def main():
     ap.add_argument("--paper", default="abc", help="which of the paper's Scenario A/B/C results to run ('' or 0 = none)")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven sweep loop instead of the CUDA graph (same kernels; lets a profiler see each launch)")
-    ap.add_argument("--kernel", choices=["auto", "group", "tensor", "generic", "lifo1"], default="auto",
+    ap.add_argument("--kernel", choices=["auto", "group", "tensor", "generic", "lifo1", "fifocol"], default="auto",
                     help="sweep kernel (auto: the autotuner picks among the factorised variants)")
     ap.add_argument("--group-width", type=int, default=0,
                     help="lane width of the factorised kernel (0 = autotuned)")

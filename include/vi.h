@@ -209,7 +209,8 @@ vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
 /* Per-handle options (no counterpart in the paper; tuning and test hooks).
  * VI_OPT_KERNEL: which sweep kernel runs -- VI_KERNEL_AUTO (factorised kernel
  * whenever the instance allows it; for LIFO with L = 1 the VI_KERNEL_LIFO_L1
- * sweep is one of the autotuned candidates; two products in VI_PREC_FP32 run the factorised
+ * sweep and for FIFO with L >= 2 the VI_KERNEL_FIFO_COL sweep is one of the
+ * autotuned candidates; two products in VI_PREC_FP32 run the factorised
  * two-product sweep -- with lead times >= 2 on both products its pipeline form
  * (m >= 2, Q+1 <= 32) -- which vi_problem_kernel reports as VI_KERNEL_GROUP with
  * width 0),
@@ -225,7 +226,14 @@ vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
  * order used up and the rest issued freshest first -- gathered once per rest,
  * so each order's expectation is a short convolution of them with the pmf;
  * persistent blocks; VI_EINVAL unless one product, LIFO, VI_PREC_FP32, L = 1,
- * m >= 2, 2 <= Q+1 <= 16 and Dmax <= 31).
+ * m >= 2, 2 <= Q+1 <= 16 and Dmax <= 31) or
+ * VI_KERNEL_FIFO_COL (FIFO sweep for lead times >= 2 by columns of rests: the
+ * Q+1 rests that differ only in the oldest rest slot Z_1 share one
+ * expectation over the demand, from which each rest's follows by one
+ * multiply-add per (expiring-slot value, order), since one unit more in Z_1
+ * is the first to be issued after the expiring slot; one of the autotuned
+ * candidates; VI_EINVAL unless one product, FIFO, VI_PREC_FP32, L >= 2,
+ * m >= 2, 2 <= Q+1 <= 32 and Dmax <= 62).
  * VI_OPT_PE_MAX_ITERS: sweep cap of the FP64 policy evaluation in vi_solve.
  * VI_OPT_GROUP_WIDTH: run the factorised kernel with this many expiring-slot
  * values per lane (1..12, 16, 21 or 24; Q+1 is split over ceil((Q+1)/width)
@@ -237,11 +245,19 @@ vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
  * sweep then reports VI_ECUDA ("bounded wait ... gave up") and the CUDA
  * context stays usable.  0 restores normal operation. */
 enum { VI_OPT_KERNEL = 1, VI_OPT_PE_MAX_ITERS = 2, VI_OPT_GROUP_WIDTH = 3, VI_OPT_TEST_STALL = 4 };
-enum { VI_KERNEL_AUTO = 0, VI_KERNEL_GENERIC = 1, VI_KERNEL_GROUP = 2, VI_KERNEL_TENSOR = 3, VI_KERNEL_LIFO_L1 = 4 };
+enum {
+    VI_KERNEL_AUTO = 0,
+    VI_KERNEL_GENERIC = 1,
+    VI_KERNEL_GROUP = 2,
+    VI_KERNEL_TENSOR = 3,
+    VI_KERNEL_LIFO_L1 = 4,
+    VI_KERNEL_FIFO_COL = 5
+};
 vi_status vi_problem_set_option(vi_handle h, int option, int value);
 
 /* Which sweep kernel the handle runs (no counterpart in the paper): *kernel =
- * VI_KERNEL_GENERIC, VI_KERNEL_GROUP, VI_KERNEL_TENSOR or VI_KERNEL_LIFO_L1,
+ * VI_KERNEL_GENERIC, VI_KERNEL_GROUP, VI_KERNEL_TENSOR, VI_KERNEL_LIFO_L1 or
+ * VI_KERNEL_FIFO_COL,
  * *width = the lane width of VI_KERNEL_GROUP (0 otherwise).  Resolves the choice (and runs the
  * autotuner, on the handle's default stream) if no solve has done so yet.
  * Either pointer may be NULL.  Errors: VI_EINVAL (null handle), VI_ECUDA. */

@@ -23,7 +23,8 @@ VI_STOP_SPAN, VI_STOP_SUPNORM, VI_STOP_PERIODIC = 0, 1, 2
 VI_PREC_FP32, VI_PREC_FP32_KAHAN, VI_PREC_FP64, VI_PREC_FP32_SINGLE = 0, 1, 2, 3
 VI_FLAG_WARM_START, VI_FLAG_NO_GRAPH, VI_FLAG_POLICY_EVAL = 1, 2, 4
 VI_OPT_KERNEL, VI_OPT_PE_MAX_ITERS, VI_OPT_GROUP_WIDTH, VI_OPT_TEST_STALL = 1, 2, 3, 4
-VI_KERNEL_AUTO, VI_KERNEL_GENERIC, VI_KERNEL_GROUP, VI_KERNEL_TENSOR, VI_KERNEL_LIFO_L1 = 0, 1, 2, 3, 4
+VI_KERNEL_AUTO, VI_KERNEL_GENERIC, VI_KERNEL_GROUP, VI_KERNEL_TENSOR, VI_KERNEL_LIFO_L1, VI_KERNEL_FIFO_COL = \
+    0, 1, 2, 3, 4, 5
 
 PRECISIONS = {"fp32": VI_PREC_FP32, "fp32_kahan": VI_PREC_FP32_KAHAN, "fp64": VI_PREC_FP64,
               "fp32_single": VI_PREC_FP32_SINGLE}

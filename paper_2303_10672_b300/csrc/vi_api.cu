@@ -280,6 +280,19 @@ static vi_status validate_product(int m, int L, int Q, const double *cost, const
     return VI_OK;
 }
 
+// product 0's pmf and -P(D > x) in FP32 for the sweeps that read them from the
+// parameter constant bank (zero past dmax; P(D > x) summed from the top in FP64)
+static void fill_pmf_consts(KernelParams &kp, const double *pmf, int dmax) {
+    constexpr int n = (int)(sizeof(kp.pmf32) / sizeof(kp.pmf32[0]));
+    for (int i = 0; i < n; ++i) kp.pmf32[i] = (i <= dmax) ? (float)pmf[i] : 0.f;
+    for (int x = 0; x < n; ++x) kp.nsurv32[x] = 0.f;
+    double t = 0.0;
+    for (int x = dmax - 1; x >= 0; --x) {
+        t += pmf[x + 1];
+        if (x < n) kp.nsurv32[x] = -(float)t;
+    }
+}
+
 void fill_prod_params(ProdParams &P, int m, int L, int Q, int dmax, double c_o) {
     memset(&P, 0, sizeof(P));
     P.m = m;
@@ -322,7 +335,7 @@ vi_status build_single_product(const vi_problem_desc &d, KernelParams &kp, std::
     std::vector<double> blob;
     fill_prod_params(kp.p[0], d.m[0], d.L[0], d.Q[0], d.dmax[0], d.cost[0][0]);
     fill_product_tables(kp.p[0], pm, d.issuing, d.cost[0], true, blob);
-    for (int i = 0; i < 32; ++i) kp.pmf32[i] = (i <= d.dmax[0]) ? (float)pm[i] : 0.f;
+    fill_pmf_consts(kp, pm.data(), d.dmax[0]);
     kp.nS = kp.p[0].nS;
     kp.nA = kp.p[0].G;
     kp.n_tables = (int)blob.size();
@@ -374,7 +387,7 @@ extern "C" vi_status vi_problem_create_desc(const vi_problem_desc *desc, vi_hand
         fill_prod_params(kp.p[k], d.m[k], d.L[k], d.Q[k], d.dmax[k], d.cost[k][0]);
         fill_product_tables(kp.p[k], h->pmf[k], d.issuing, d.cost[k], d.n_products == 1, blob);
     }
-    for (int i = 0; i < 32; ++i) kp.pmf32[i] = (i <= d.dmax[0]) ? (float)h->pmf[0][i] : 0.f;
+    fill_pmf_consts(kp, h->pmf[0].data(), d.dmax[0]);
     if (d.n_products == 1) {
         kp.nS = kp.p[0].nS;
         kp.nA = kp.p[0].G;
@@ -721,10 +734,19 @@ extern "C" vi_status vi_problem_set_option(vi_handle h, int option, int value) {
                                "the lead-time-one LIFO kernel needs one product, LIFO, FP32 precision, L = 1, "
                                "m >= 2, 2 <= Q+1 <= 16 and Dmax <= 31");
             h->kernel_choice = VI_KERNEL_LIFO_L1;
+        } else if (value == VI_KERNEL_FIFO_COL) {
+            if (!h->group_ok || !fifo_col_supported(h->kp, h->vk, h->kahan))
+                return vi_fail(VI_EINVAL,
+                               "the FIFO column kernel needs one product, FIFO, FP32 precision, L >= 2, "
+                               "m >= 2, 2 <= Q+1 <= 32 and Dmax <= 62");
+            h->kernel_choice = VI_KERNEL_FIFO_COL;
         } else {
             return vi_fail(VI_EINVAL, "bad kernel choice %d", value);
         }
-        h->group_xw = (value == VI_KERNEL_TENSOR) ? kTcWidth : (value == VI_KERNEL_LIFO_L1) ? kLifo1Width : 0;
+        h->group_xw = (value == VI_KERNEL_TENSOR)     ? kTcWidth
+                      : (value == VI_KERNEL_LIFO_L1)  ? kLifo1Width
+                      : (value == VI_KERNEL_FIFO_COL) ? kFifoColWidth
+                                                      : 0;
         if (h->graph_exec) {
             cudaGraphExecDestroy(h->graph_exec);
             h->graph_exec = nullptr;
@@ -775,9 +797,9 @@ extern "C" vi_status vi_problem_set_option(vi_handle h, int option, int value) {
 // kernel choice and autotuning of the factorised kernel's lane width
 // ---------------------------------------------------------------------------
 struct TuneKey {
-    int vk, issuing, m, L, Q, dmax, l1;
+    int vk, issuing, m, L, Q, dmax, extra;   // extra: which dedicated kernels competed (bit 0 LIFO L=1, bit 1 FIFO column)
     bool operator<(const TuneKey &o) const {
-        return std::tie(vk, issuing, m, L, Q, dmax, l1) < std::tie(o.vk, o.issuing, o.m, o.L, o.Q, o.dmax, o.l1);
+        return std::tie(vk, issuing, m, L, Q, dmax, extra) < std::tie(o.vk, o.issuing, o.m, o.L, o.Q, o.dmax, o.extra);
     }
 };
 static std::mutex g_tune_mu;
@@ -801,7 +823,8 @@ static vi_status autotune(vi_problem *h, cudaStream_t s) {
     // tensor-core FIFO kernel (slower than the CUDA-core sweep as measured on B300)
     // runs only when asked for
     const int l1 = (h->kernel_choice == VI_KERNEL_AUTO && lifo1_supported(h->kp, h->vk, h->kahan)) ? 1 : 0;
-    const TuneKey key{h->vk, h->kp.issuing, P.m, P.L, P.Q, P.dmax, l1};
+    const int fc = (h->kernel_choice == VI_KERNEL_AUTO && fifo_col_supported(h->kp, h->vk, h->kahan)) ? 1 : 0;
+    const TuneKey key{h->vk, h->kp.issuing, P.m, P.L, P.Q, P.dmax, l1 | (fc << 1)};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -812,12 +835,13 @@ static vi_status autotune(vi_problem *h, cudaStream_t s) {
     }
     const char *env = getenv("VI_AUTOTUNE");
     if (env && env[0] == '0') {
-        h->group_xw = l1 ? kLifo1Width : heuristic_width(P.G, h->kp.issuing);
+        h->group_xw = l1 ? kLifo1Width : fc ? kFifoColWidth : heuristic_width(P.G, h->kp.issuing);
         return VI_OK;
     }
-    int cand[17];
+    int cand[18];
     int nc = group_width_candidates(P.G, cand, 16);
     if (l1) cand[nc++] = kLifo1Width;
+    if (fc) cand[nc++] = kFifoColWidth;
     const size_t nb = (size_t)h->kp.nS * h->value_bytes;
     void *a = nullptr, *b = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -944,7 +968,8 @@ static vi_status choose_kernel(vi_problem *h, cudaStream_t s) {
     }
     h->sweep_xw = h->group_xw;
     // measured on B300: 2.4% faster for the FIFO 4.08M-state sweep, none for LIFO
-    if (h->sweep_xw == kTcWidth || h->sweep_xw == kLifo1Width || h->kp.issuing != VI_FIFO) {
+    if (h->sweep_xw == kTcWidth || h->sweep_xw == kLifo1Width || h->sweep_xw == kFifoColWidth ||
+        h->kp.issuing != VI_FIFO) {
         h->kp.grp_order = nullptr;
         return VI_OK;
     }
@@ -959,8 +984,10 @@ extern "C" vi_status vi_problem_kernel(vi_handle h, int *kernel, int *width) {
     if (kernel)
         *kernel = (xw == 0) ? VI_KERNEL_GENERIC
                   : (xw == kTcWidth) ? VI_KERNEL_TENSOR
-                  : (xw == kLifo1Width) ? VI_KERNEL_LIFO_L1 : VI_KERNEL_GROUP;
-    if (width) *width = (xw == 0 || xw == kTcWidth || xw == kTwoWidth || xw == kLifo1Width) ? 0 : xw;
+                  : (xw == kLifo1Width) ? VI_KERNEL_LIFO_L1
+                  : (xw == kFifoColWidth) ? VI_KERNEL_FIFO_COL : VI_KERNEL_GROUP;
+    if (width)
+        *width = (xw == 0 || xw == kTcWidth || xw == kTwoWidth || xw == kLifo1Width || xw == kFifoColWidth) ? 0 : xw;
     return VI_OK;
 }
 

@@ -81,8 +81,9 @@ struct KernelParams {
     int two_npipe1;       // product-1 pipeline classes of an emptied next state: G1^(L1-1)
     const uint32_t *two_rperm;   // lead times >= 2: product-1 rests ordered by their unit total
     const uint32_t *grp_order;   // factorised sweep: block order, heaviest rests first (null: natural order)
-    float pmf32[32];             // product 0's pmf in FP32, zero past dmax (kept here so that sweeps with
+    float pmf32[64];             // product 0's pmf in FP32, zero past dmax (kept here so that sweeps with
                                  // compile-time demand loops read it from the parameter constant bank)
+    float nsurv32[64];           // -P(D > x) of product 0 in FP32, zero from dmax on (the FIFO column sweep)
     // Scenario C (periodic demand, life on arrival; vi_pc.cu): p[0] holds m, Q = A_max,
     // G, dmax, nS = G^(m-1) states per weekday
     int pc;                      // 1 for a periodic problem

@@ -1751,6 +1751,7 @@ cudaError_t describe_sweep(const KernelParams &kp, int vk, int kahan, int use_gr
     if (kp.pc) return describe_pc(kp, d);
     if (use_group == kTcWidth) return describe_tc(kp, d);
     if (use_group == kLifo1Width) return describe_lifo1(kp, d);
+    if (use_group == kFifoColWidth) return describe_fifo_col(kp, d);
     if (use_group == kTwoWidth) return (kp.p[0].L >= 2) ? describe_twop(kp, d) : describe_two(kp, kahan, d);
     if (use_group) {
         const int xw = use_group;   // lane width of the factorised kernel

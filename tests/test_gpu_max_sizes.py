@@ -3,8 +3,9 @@ against the FP64 oracle at sampled states, through the C ABI.
 
 2,562,890,625 states (LIFO, L = 1, Q+1 = 15, past 2^31: every state index, tile
 offset and gather address is above the signed 32-bit range somewhere) on the
-persistent LIFO kernel, and 1,801,088,541 states (FIFO, two pipeline slots) on
-the factorised kernel.  The oracle needs V only at the next states of the sampled
+persistent LIFO kernel, 1,801,088,541 states (FIFO, two pipeline slots) on
+the factorised kernel and 2,494,357,888 states (FIFO, lead time 2) on the FIFO
+column kernel.  The oracle needs V only at the next states of the sampled
 states: those values are gathered on the device (vi_next_states gives their
 indices) into a zero-filled host array whose other pages are never touched.
 Checked: one backup's values (max relative error <= 1e-5), its first argmax up to
@@ -96,3 +97,13 @@ def test_fifo_pipeline_1_8e9_states():
     assert inst.n_states == 21 ** 7
     k = _max_size_backup(inst, vi.VI_KERNEL_GROUP, 2, 300, 62)
     assert k[0] == vi.VI_KERNEL_GROUP
+
+
+def test_fifo_column_past_2_31_states():
+    # 22^7 = 2,494,357,888 states on the FIFO column kernel: column starts, state
+    # indices and order offsets above the signed 32-bit range
+    inst = workloads.single_product(7, 2, 21, (2.0, 1.0, 6.0, 3.0, 1.0), workloads.poisson_pmf(6.0, 20), 0.95,
+                                    FIFO)
+    assert inst.n_states == 22 ** 7 > (1 << 31)
+    k = _max_size_backup(inst, vi.VI_KERNEL_FIFO_COL, 2, 300, 63)
+    assert k == (vi.VI_KERNEL_FIFO_COL, 0)
