@@ -1,5 +1,6 @@
 // vi_batch.cu -- the solve server's persistent sweep kernel: one launch advances
 // every admitted instance, each at its own pace.
+#include "vi_fifo_col.cuh"
 #include "vi_group.cuh"
 
 namespace vib {
@@ -132,11 +133,22 @@ serve_kernel(const KernelParams *kps, SrvSlot *slots, const int *act, int n_act,
         }
         __syncthreads();
         const SrvSlot &S = slots[i];
-        switch (S.xw) {
-            case 8: serve_variant<8>(S.variant, s_kp, s_b, s_nb, s_mode, S.lpr, smem_raw); break;
-            case 12: serve_variant<12>(S.variant, s_kp, s_b, s_nb, s_mode, S.lpr, smem_raw); break;
-            case 16: serve_variant<16>(S.variant, s_kp, s_b, s_nb, s_mode, S.lpr, smem_raw); break;
-            default: serve_variant<21>(S.variant, s_kp, s_b, s_nb, s_mode, S.lpr, smem_raw); break;
+        if (S.variant == kSrvColVariant) {
+            // FIFO with lead time >= 2 and dmax <= 46: the column body (the same arithmetic as the
+            // standalone sweep)
+            ColSmem &sm = *(ColSmem *)smem_raw;
+            switch (fifo_col_dp(s_kp.p[0].dmax)) {
+                case 16: fifo_col_body<16, 1>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
+                case 32: fifo_col_body<32, 1>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
+                default: fifo_col_body<48, 1>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
+            }
+        } else {
+            switch (S.xw) {
+                case 8: serve_variant<8>(S.variant, s_kp, s_b, s_nb, s_mode, S.lpr, smem_raw); break;
+                case 12: serve_variant<12>(S.variant, s_kp, s_b, s_nb, s_mode, S.lpr, smem_raw); break;
+                case 16: serve_variant<16>(S.variant, s_kp, s_b, s_nb, s_mode, S.lpr, smem_raw); break;
+                default: serve_variant<21>(S.variant, s_kp, s_b, s_nb, s_mode, S.lpr, smem_raw); break;
+            }
         }
         __syncthreads();   // every thread's stores of this block are issued
         if (threadIdx.x == 0) {
@@ -175,6 +187,13 @@ int batch_width(int G) {
 // blocks per sweep and shared memory of one instance in the server kernel
 void batch_geometry(const KernelParams &kp, int *lpr, uint32_t *blocks, size_t *smem) {
     const int G = kp.p[0].G;
+    if (batch_variant(kp) == kSrvColVariant) {
+        const uint32_t ncol = kp.p[0].nS / (uint32_t)G / (uint32_t)G;
+        *lpr = 1;
+        *blocks = (ncol + kColWarps - 1) / kColWarps;
+        *smem = sizeof(ColSmem);
+        return;
+    }
     const int xw = batch_width(G);
     const int l = (G + xw - 1) / xw;
     const int rb = kGroupThreads / l;
@@ -183,7 +202,12 @@ void batch_geometry(const KernelParams &kp, int *lpr, uint32_t *blocks, size_t *
     *smem = group_smem(kp, rb, VK_PAIR);
 }
 
-int batch_variant(const KernelParams &kp) { return (kp.issuing ? 2 : 0) + (kp.p[0].L >= 2 ? 1 : 0); }
+int batch_variant(const KernelParams &kp) {
+    // the server carries the column body up to the 48-entry pmf capacity (dmax <= 46), so that
+    // the largest instantiation's registers do not weigh on the persistent kernel
+    if (fifo_col_supported(kp, VK_PAIR, 0) && fifo_col_dp(kp.p[0].dmax) <= 48) return kSrvColVariant;
+    return (kp.issuing ? 2 : 0) + (kp.p[0].L >= 2 ? 1 : 0);
+}
 
 // loads the kernel and lets it use up to 200 KiB of dynamic shared memory, so that no
 // first launch pays for loading its code (the server calls it at creation)

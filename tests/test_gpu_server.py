@@ -57,11 +57,18 @@ def test_results_equal_alone_and_in_the_mix():
         res = wait_all(srv, ids, sizes)
     finally:
         vi.vi_server_destroy(srv)
+    # the mix holds instances of both bodies
+    assert any(i.products[0].L >= 2 for i in insts) and any(i.products[0].L == 1 for i in insts)
     for inst, rid in zip(insts, ids):
         V, pol, info = res[rid]
         assert info["status"] == vi.VI_OK
-        # the server runs the factorised CUDA-core kernel (bit-identical across lane widths)
-        with Handle(inst, precision="fp32", kernel=vi.VI_KERNEL_GROUP) as H:
+        # the server runs the FIFO column body for lead times >= 2 (pmf of at most 47
+        # entries) and the factorised CUDA-core body otherwise (bit-identical across lane
+        # widths); the standalone sweep with that body gives the same arithmetic
+        p = inst.products[0]
+        col = inst.issuing == workloads.FIFO and p.L >= 2 and p.m >= 2 and p.Q + 1 <= 32 and p.dmax <= 46
+        kernel = vi.VI_KERNEL_FIFO_COL if col else vi.VI_KERNEL_GROUP
+        with Handle(inst, precision="fp32", kernel=kernel) as H:
             Va, pola, ia = H.solve(1e-4, 5000)
             va = H.v_abs(Va, ia)
         assert info["iters"] == ia["iters"]
