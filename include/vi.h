@@ -209,8 +209,8 @@ vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
 /* Per-handle options (no counterpart in the paper; tuning and test hooks).
  * VI_OPT_KERNEL: which sweep kernel runs -- VI_KERNEL_AUTO (factorised kernel
  * whenever the instance allows it; for LIFO with L = 1 the VI_KERNEL_LIFO_L1
- * sweep and for FIFO with L >= 2 the VI_KERNEL_FIFO_COL sweep is one of the
- * autotuned candidates; two products in VI_PREC_FP32 run the factorised
+ * sweep and for FIFO the VI_KERNEL_FIFO_COL sweep is one of the autotuned
+ * candidates; two products in VI_PREC_FP32 run the factorised
  * two-product sweep -- with lead times >= 2 on both products its pipeline form
  * (m >= 2, Q+1 <= 32) -- which vi_problem_kernel reports as VI_KERNEL_GROUP with
  * width 0),
@@ -227,13 +227,13 @@ vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
  * so each order's expectation is a short convolution of them with the pmf;
  * persistent blocks; VI_EINVAL unless one product, LIFO, VI_PREC_FP32, L = 1,
  * m >= 2, 2 <= Q+1 <= 16 and Dmax <= 31) or
- * VI_KERNEL_FIFO_COL (FIFO sweep for lead times >= 2 by columns of rests: the
- * Q+1 rests that differ only in the oldest rest slot Z_1 share one
- * expectation over the demand, from which each rest's follows by one
- * multiply-add per (expiring-slot value, order), since one unit more in Z_1
- * is the first to be issued after the expiring slot; one of the autotuned
- * candidates; VI_EINVAL unless one product, FIFO, VI_PREC_FP32, L >= 2,
- * m >= 2, 2 <= Q+1 <= 32 and Dmax <= 62).
+ * VI_KERNEL_FIFO_COL (FIFO sweep by columns of rests: the Q+1 rests that
+ * differ only in the oldest rest slot Z_1 share one expectation over the
+ * demand, from which each rest's follows by one multiply-add per
+ * (expiring-slot value, order), since one unit more in Z_1 is the first to be
+ * issued after the expiring slot; one of the autotuned candidates; VI_EINVAL
+ * unless one product, FIFO, VI_PREC_FP32, m >= 2 (m >= 3 with L = 1),
+ * 2 <= Q+1 <= 32 and Dmax <= 62).
  * VI_OPT_PE_MAX_ITERS: sweep cap of the FP64 policy evaluation in vi_solve.
  * VI_OPT_GROUP_WIDTH: run the factorised kernel with this many expiring-slot
  * values per lane (1..12, 16, 21 or 24; Q+1 is split over ceil((Q+1)/width)

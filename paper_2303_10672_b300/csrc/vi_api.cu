@@ -737,8 +737,8 @@ extern "C" vi_status vi_problem_set_option(vi_handle h, int option, int value) {
         } else if (value == VI_KERNEL_FIFO_COL) {
             if (!h->group_ok || !fifo_col_supported(h->kp, h->vk, h->kahan))
                 return vi_fail(VI_EINVAL,
-                               "the FIFO column kernel needs one product, FIFO, FP32 precision, L >= 2, "
-                               "m >= 2, 2 <= Q+1 <= 32 and Dmax <= 62");
+                               "the FIFO column kernel needs one product, FIFO, FP32 precision, m >= 2 "
+                               "(m >= 3 if L = 1), 2 <= Q+1 <= 32 and Dmax <= 62");
             h->kernel_choice = VI_KERNEL_FIFO_COL;
         } else {
             return vi_fail(VI_EINVAL, "bad kernel choice %d", value);

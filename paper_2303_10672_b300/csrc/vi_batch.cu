@@ -138,9 +138,9 @@ serve_kernel(const KernelParams *kps, SrvSlot *slots, const int *act, int n_act,
             // standalone sweep)
             ColSmem &sm = *(ColSmem *)smem_raw;
             switch (fifo_col_dp(s_kp.p[0].dmax)) {
-                case 16: fifo_col_body<16, 1>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
-                case 32: fifo_col_body<32, 1>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
-                default: fifo_col_body<48, 1>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
+                case 16: fifo_col_body<16, 1, 0>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
+                case 32: fifo_col_body<32, 1, 0>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
+                default: fifo_col_body<48, 1, 0>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
             }
         } else {
             switch (S.xw) {
@@ -203,9 +203,11 @@ void batch_geometry(const KernelParams &kp, int *lpr, uint32_t *blocks, size_t *
 }
 
 int batch_variant(const KernelParams &kp) {
-    // the server carries the column body up to the 48-entry pmf capacity (dmax <= 46), so that
-    // the largest instantiation's registers do not weigh on the persistent kernel
-    if (fifo_col_supported(kp, VK_PAIR, 0) && fifo_col_dp(kp.p[0].dmax) <= 48) return kSrvColVariant;
+    // the server carries the column body for lead times >= 2 up to the 48-entry pmf capacity
+    // (dmax <= 46), so that further instantiations' registers do not weigh on the
+    // persistent kernel
+    if (fifo_col_supported(kp, VK_PAIR, 0) && kp.p[0].L >= 2 && fifo_col_dp(kp.p[0].dmax) <= 48)
+        return kSrvColVariant;
     return (kp.issuing ? 2 : 0) + (kp.p[0].L >= 2 ? 1 : 0);
 }
 

@@ -1,5 +1,5 @@
-// vi_fifo_col.cuh -- FIFO sweep for lead times of two or more, one column of rests
-// at a time (the body, included by vi_fifo_col.cu and by the server kernel in
+// vi_fifo_col.cuh -- FIFO sweep, one column of rests at a time (the body, included
+// by vi_fifo_col.cu and, for lead times of two or more, by the server kernel in
 // vi_batch.cu).
 //
 // Under FIFO (Eq. demoor:fifo) the expiring slot x is issued first and the oldest
@@ -18,6 +18,10 @@
 //   C(x', r0, a) = sum_{k >= 1} p[x' + k] g(min(k, R0)),
 // g(k) the value after k units measured from ref(r0, a) (the tail mass beyond the
 // rest is the pmf's own terms past R0), and C vanishes from x' = dmax on.
+// With lead time one the order a arrives as the freshest stock slot, the last one
+// issued: its digit of weight G^(K-1) holds what is left of it, the path runs on
+// through those a units (R0 + a in place of R0), and the recurrence is unchanged
+// because Z_1 is still the first slot after x; the reward-table row is R + a.
 //
 // One warp per column.  Lane a holds order a's C(., z, a) in registers (x'
 // unrolled; the pmf and -P(D > x) come from the parameter constant bank), forms
@@ -25,7 +29,8 @@
 // the keys and C to shared memory.  Lane x then takes the first argmax over the
 // orders of its x and rebuilds the chosen order's value exactly in float pairs:
 // the base pair gamma (ref - R0) - c_o a, plus gamma C, plus the reward-table pair
-// RT(R, x), plus gamma R0 (the operations of the factorised sweep).
+// RT(R, x), plus gamma R0 (the operations of the factorised sweep).  With lead time
+// one the key also holds RT(R + a, x), which then differs between orders.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -62,7 +67,11 @@ __device__ __forceinline__ float2 col_load(const float2 *p) {
 
 // Block `bid` of a sweep of n_blocks blocks (kColWarps columns, one per warp; all
 // threads of the block call it).  kp may live in shared memory (the server).
-template <int DP, int COH>
+// LT1 = 1: lead time one.  The order then arrives as the freshest stock slot, issued
+// after the rest's units (its next-state digit, of weight G^(K-1), counts the units
+// left of it), so each order's path continues past the rest's units into its own, and
+// the reward table's R counts the order: RT(R + a, x) enters each order's key.
+template <int DP, int COH, int LT1>
 __device__ __forceinline__ void fifo_col_body(const KernelParams &kp, uint32_t bid, unsigned n_blocks, int mode,
                                               const void *vin_arg, void *vout_arg, uint8_t *pol_arg, ColSmem &sm) {
     constexpr int XE = DP - 1;   // C(x') kept for x' = 0..DP-2; zero from dmax on
@@ -83,8 +92,8 @@ __device__ __forceinline__ void fifo_col_body(const KernelParams &kp, uint32_t b
         const float2 *V2 = (const float2 *)B.vin;
         const float *tab = (const float *)kp.tables;
         const uint32_t r0 = col * (uint32_t)G;   // the column's rest with Z_1 = 0
-        const int nz = P.n_rest_slots;            // stock slots of the rest: Z_1 .. Z_{m-1}
-        // units of the column in Z_2 .. Z_{m-1}
+        const int nz = P.n_rest_slots;            // stock slots of the rest: Z_1 .. Z_{m-1} (m-2 if LT1)
+        // units of the column in Z_2 .. Z_{nz}
         int Rc = 0;
         {
             uint32_t q = col;
@@ -114,6 +123,9 @@ __device__ __forceinline__ void fifo_col_body(const KernelParams &kp, uint32_t b
         const int a = lane < G ? lane : 0;   // lanes past the last order repeat order 0 (never read)
         const float2 *Va = V2 + (size_t)a * P.w_top;
         const float2 ref0 = col_load<COH>(Va + r0);
+        // units of the order left after k units reached the rest: all of them with a
+        // pipeline (the order is not stock yet), else what the rest's Rc units left over
+        auto order_left = [&](int k) -> uint32_t { return LT1 ? (uint32_t)max(a - max(k - Rc, 0), 0) : (uint32_t)a; };
 
         // -- C(x', r0, a) for x' = 0..DP-2, terms in increasing k (zero mass past dmax)
         float C[XE];
@@ -129,7 +141,7 @@ __device__ __forceinline__ void fifo_col_body(const KernelParams &kp, uint32_t b
                     if (k < DP) {
                         const uint32_t idx =
                             (k < 32) ? __shfl_sync(0xffffffffu, pa, k) : __shfl_sync(0xffffffffu, pb, k - 32);
-                        raw[j] = col_load<COH>(Va + idx);
+                        raw[j] = col_load<COH>(V2 + (idx + order_left(k) * P.w_top));
                     }
                 }
 #pragma unroll
@@ -165,10 +177,12 @@ __device__ __forceinline__ void fifo_col_body(const KernelParams &kp, uint32_t b
             float2 vold = make_float2(0.f, 0.f);
             float rth = 0.f, rtl = 0.f;
             if (x < G) {
-                const int ti = (Rc + z) * G + x;
                 vold = col_load<COH>(V2 + s);
-                rth = __ldg(tab + P.off_RT + ti);
-                rtl = __ldg(tab + P.off_RTlo + ti);
+                if (!LT1) {   // with a pipeline the reward row does not depend on the order
+                    const int ti = (Rc + z) * G + x;
+                    rth = __ldg(tab + P.off_RT + ti);
+                    rtl = __ldg(tab + P.off_RTlo + ti);
+                }
             }
             if (z > 0) {
                 // C(x, r0 + z) = C(x + 1, r0 + z - 1) - P(D > x) (ref(r0 + z) - ref(r0 + z - 1)),
@@ -183,6 +197,7 @@ __device__ __forceinline__ void fifo_col_body(const KernelParams &kp, uint32_t b
             float Bh, Bl;
             action_base(gam, refz, R0z, __fmul_rn(-c_o, (float)a), Bh, Bl);
             const float kb = __fadd_rn(Bh, Bl);
+            const float *rtk = tab + P.off_RT + (Rc + z + a) * G;   // LT1: this order's reward row
 #pragma unroll
             for (int x4 = 0; x4 < 32; x4 += 4) {
                 if (x4 < G) {   // uniform
@@ -191,6 +206,7 @@ __device__ __forceinline__ void fifo_col_body(const KernelParams &kp, uint32_t b
                     for (int i = 0; i < 4; ++i) {
                         cv[i] = (x4 + i < XE) ? C[x4 + i] : 0.f;
                         kv[i] = __fmaf_rn(gam, cv[i], kb);
+                        if (LT1) kv[i] = __fadd_rn(kv[i], (x4 + i < G) ? __ldg(rtk + x4 + i) : 0.f);
                     }
                     *(float4 *)(krow + x4) = make_float4(kv[0], kv[1], kv[2], kv[3]);
                     *(float4 *)(crow + x4) = make_float4(cv[0], cv[1], cv[2], cv[3]);
@@ -213,6 +229,11 @@ __device__ __forceinline__ void fifo_col_body(const KernelParams &kp, uint32_t b
                 // the chosen order's exact pair
                 const float cbest = sm.cv[warp][ab * kColRow + x];
                 const float2 bb = sm.base[warp][ab];
+                if (LT1) {
+                    const int ti = (Rc + z + ab) * G + x;
+                    rth = __ldg(tab + P.off_RT + ti);
+                    rtl = __ldg(tab + P.off_RTlo + ti);
+                }
                 float bh = bb.x, bl = __fmaf_rn(gam, cbest, bb.y);
                 pair_add(bh, bl, rth, rtl);
                 const float2 vnew = pair_finish(gam, R0z, bh, bl);

@@ -80,7 +80,7 @@ constexpr int kTwoWidth = 200;
 constexpr int kLifo1Width = 300;
 bool lifo1_supported(const KernelParams &kp, int vk, int kahan);
 cudaError_t describe_lifo1(const KernelParams &kp, LaunchDesc &d);
-// lane-width token of the FIFO sweep for lead times >= 2 by columns of rests (vi_fifo_col.cu)
+// lane-width token of the FIFO sweep by columns of rests (vi_fifo_col.cu)
 constexpr int kFifoColWidth = 400;
 bool fifo_col_supported(const KernelParams &kp, int vk, int kahan);
 cudaError_t describe_fifo_col(const KernelParams &kp, LaunchDesc &d);

@@ -1,5 +1,5 @@
-"""The FIFO sweep for lead times >= 2 by columns of rests (VI_KERNEL_FIFO_COL)
-against the FP64 oracle, through the C ABI.
+"""The FIFO sweep by columns of rests (VI_KERNEL_FIFO_COL) against the FP64
+oracle, through the C ABI.
 
 The kernel computes the expectation of the column's first rest over the demand
 and those of the column's other rests from the recurrence
@@ -11,8 +11,10 @@ device stopping test within two sweeps of the oracle's.  The shapes cover every
 pmf capacity (dmax up to 14, 30, 46 and 62), the smallest and largest radix
 (Q+1 = 2 and 32), m = 2 (the arrival is the only stock slot of the rest), lead
 times 2 to 4, a column count that leaves the last block of four columns ragged,
-demand below the order cap (dmax < Q), zero demand, and the 4.08M-state
-instance in the launch configuration the benchmark times.
+demand below the order cap (dmax < Q), zero demand, lead time one (the order
+is the freshest stock slot and its own reward row enters each order's key:
+m = 3..6, Q+1 up to 32, config 1's shape), and the 4.08M-state instance in the
+launch configuration the benchmark times.
 """
 import numpy as np
 import pytest
@@ -41,6 +43,11 @@ SHAPES = [
     (3, 2, 12, 1.0, 4, 0.95),     # dmax < Q: the expectations vanish early
     (4, 2, 3, 2.0, 0, 0.9),       # deterministic zero demand
     (5, 2, 1, 0.7, 5, 0.9),       # Q+1 = 2, four stock slots
+    (3, 1, 20, 5.0, 25, 0.99),    # lead time one: config 1's shape (one column)
+    (4, 1, 6, 3.0, 14, 0.9),      # lead time one, 7 columns
+    (5, 1, 4, 2.0, 30, 0.95),     # lead time one, 25 columns, dmax 30
+    (3, 1, 31, 8.0, 46, 0.9),     # lead time one, Q+1 = 32
+    (6, 1, 3, 1.5, 10, 0.9),      # lead time one, four rest slots
 ]
 
 
@@ -70,9 +77,10 @@ def test_fifo_col_config2_full_size_sampled():
     sampled_backup_parity(workloads.config2(), 3, 400, 45, "fp32", kernel=K)
 
 
-def test_fifo_col_matches_factorised_group_kernel():
+@pytest.mark.parametrize("L", [2, 1])
+def test_fifo_col_matches_factorised_group_kernel(L):
     # the column recurrence and the direct sums over the demand agree after many sweeps
-    inst = _inst(4, 2, 9, 4.0, 20, 0.95, seed=3)
+    inst = _inst(4 if L == 2 else 5, L, 9, 4.0, 20, 0.95, seed=3)
     with Handle(inst, precision="fp32", kernel=K) as A, Handle(inst, precision="fp32", kernel=vi.VI_KERNEL_GROUP) as B:
         Va, pa, ia = A.solve(0.0, 25)
         Vb, pb, ib = B.solve(0.0, 25)
@@ -95,7 +103,7 @@ def test_fifo_col_rejected_where_unsupported():
     pmf = workloads.poisson_pmf(3, 12)
     bad = [workloads.single_product(3, 2, 32, (3, 1, 5, 7, 0), pmf, 0.9, FIFO),                        # Q+1 = 33
            workloads.single_product(3, 2, 6, (3, 1, 5, 7, 0), workloads.poisson_pmf(20, 63), 0.9, FIFO),  # dmax 63
-           workloads.single_product(4, 1, 6, (3, 1, 5, 7, 0), pmf, 0.9, FIFO),                        # L = 1
+           workloads.single_product(2, 1, 6, (3, 1, 5, 7, 0), pmf, 0.9, FIFO),                        # L = 1, m = 2
            workloads.single_product(4, 2, 6, (3, 1, 5, 7, 0), pmf, 0.9, LIFO),                        # LIFO
            workloads.single_product(1, 3, 6, (3, 1, 5, 7, 0), pmf, 0.9, FIFO)]                        # m = 1
     for inst in bad:
