@@ -980,8 +980,8 @@ def run_serving(n_requests: int = 512, seed: int = 5, slots: int = 64, budget_gb
         upd_bs += nominal[k] * info["iters"]
     span_bs = time.perf_counter() - t0
     # equal accuracy (untimed): the burst's results against sequential solves of the same
-    # requests, (1) with the body the server ran for the request (the FIFO column sweep for
-    # lead times >= 2 and dmax <= 46, else the factorised sweep): the same arithmetic, so
+    # requests, (1) with the body the server ran for the request (the FIFO column sweep where
+    # it applies and dmax <= 46, else the factorised sweep): the same arithmetic, so
     # equal values; (2) with the autotuned kernel the timed sequential solves ran: other
     # rounding, so the span test may stop a sweep earlier or later, and values that stop at
     # different sweeps differ by a near-constant shift (the span test fixes V only up to a
@@ -999,7 +999,8 @@ def run_serving(n_requests: int = 512, seed: int = 5, slots: int = 64, budget_gb
     worst_auto, worst_centred, pol_auto, stop_diff = 0.0, 0.0, 0, 0
     for k, r in enumerate(reqs):
         p = r.instance.products[0]
-        col = r.instance.issuing == workloads.FIFO and p.L >= 2 and p.m >= 2 and p.Q + 1 <= 32 and p.dmax <= 46
+        col = (r.instance.issuing == workloads.FIFO and ((p.L >= 2 and p.m >= 2) or (p.L == 1 and p.m >= 3))
+               and p.Q + 1 <= 32 and p.dmax <= 46)
         b = bufs[k][0]                                                          # absolute FP64 values
         a, q, _ = seq_solve(k, vi.VI_KERNEL_FIFO_COL if col else vi.VI_KERNEL_GROUP)
         scale = max(np.abs(a).max(), 1e-300)

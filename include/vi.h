@@ -390,8 +390,8 @@ vi_status vi_basestock_search(vi_handle h, int s_lo, int s_hi, int n_rollouts, i
  * claim blocks of the instances' current sweeps (largest instances first), and
  * each instance's next sweep -- or its extraction sweep once its stopping test
  * has passed -- starts as soon as its previous one has finished, so instances of
- * different sizes advance together, each at its own pace.  FIFO instances with
- * lead times >= 2 and Dmax <= 46 run the body of VI_KERNEL_FIFO_COL, the others
+ * different sizes advance together, each at its own pace.  FIFO instances that
+ * VI_KERNEL_FIFO_COL accepts, with Dmax <= 46, run its body, the others
  * that of VI_KERNEL_GROUP, so a result equals, bit for bit, the instance solved
  * alone with that kernel.  A finished instance
  * is retired between launches, freeing memory for queued requests; its values

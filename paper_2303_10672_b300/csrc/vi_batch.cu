@@ -134,13 +134,22 @@ serve_kernel(const KernelParams *kps, SrvSlot *slots, const int *act, int n_act,
         __syncthreads();
         const SrvSlot &S = slots[i];
         if (S.variant == kSrvColVariant) {
-            // FIFO with lead time >= 2 and dmax <= 46: the column body (the same arithmetic as the
-            // standalone sweep)
+            // FIFO with dmax <= 46 where the column sweep applies: its body (the same arithmetic
+            // as the standalone sweep)
             ColSmem &sm = *(ColSmem *)smem_raw;
-            switch (fifo_col_dp(s_kp.p[0].dmax)) {
-                case 16: fifo_col_body<16, 1, 0>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
-                case 32: fifo_col_body<32, 1, 0>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
-                default: fifo_col_body<48, 1, 0>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
+            const int dp = fifo_col_dp(s_kp.p[0].dmax);
+            if (s_kp.p[0].L == 1) {
+                switch (dp) {
+                    case 16: fifo_col_body<16, 1, 1>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
+                    case 32: fifo_col_body<32, 1, 1>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
+                    default: fifo_col_body<48, 1, 1>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
+                }
+            } else {
+                switch (dp) {
+                    case 16: fifo_col_body<16, 1, 0>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
+                    case 32: fifo_col_body<32, 1, 0>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
+                    default: fifo_col_body<48, 1, 0>(s_kp, s_b, s_nb, s_mode, nullptr, nullptr, nullptr, sm); break;
+                }
             }
         } else {
             switch (S.xw) {
@@ -203,11 +212,9 @@ void batch_geometry(const KernelParams &kp, int *lpr, uint32_t *blocks, size_t *
 }
 
 int batch_variant(const KernelParams &kp) {
-    // the server carries the column body for lead times >= 2 up to the 48-entry pmf capacity
-    // (dmax <= 46), so that further instantiations' registers do not weigh on the
-    // persistent kernel
-    if (fifo_col_supported(kp, VK_PAIR, 0) && kp.p[0].L >= 2 && fifo_col_dp(kp.p[0].dmax) <= 48)
-        return kSrvColVariant;
+    // the server carries the column body up to the 48-entry pmf capacity (dmax <= 46), so
+    // that the largest instantiations' registers do not weigh on the persistent kernel
+    if (fifo_col_supported(kp, VK_PAIR, 0) && fifo_col_dp(kp.p[0].dmax) <= 48) return kSrvColVariant;
     return (kp.issuing ? 2 : 0) + (kp.p[0].L >= 2 ? 1 : 0);
 }
 

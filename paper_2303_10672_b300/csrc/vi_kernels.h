@@ -97,7 +97,7 @@ cudaError_t prepare_sweep_batch();
 // loads the server's helper kernels (status gather, FP64 conversion, solve init)
 cudaError_t prepare_server_helpers();
 // body an instance runs in the server: the factorised body's variant 2 * LIFO + (L >= 2),
-// or kSrvColVariant for the FIFO column body (FIFO, L >= 2, where fifo_col_supported, dmax <= 46)
+// or kSrvColVariant for the FIFO column body (where fifo_col_supported, dmax <= 46)
 constexpr int kSrvColVariant = 4;
 int batch_variant(const KernelParams &kp);
 

@@ -43,6 +43,13 @@ def mix(n, seed, max_states=60_000):
     return [r.instance for r in reqs]
 
 
+def _column_body(inst):
+    """Whether the server runs the FIFO column body for this instance."""
+    p = inst.products[0]
+    return (inst.issuing == workloads.FIFO and ((p.L >= 2 and p.m >= 2) or (p.L == 1 and p.m >= 3))
+            and p.Q + 1 <= 32 and p.dmax <= 46)
+
+
 def test_results_equal_alone_and_in_the_mix():
     insts = mix(24, seed=11)
     srv = vi.vi_server_create(4 << 30, 16)
@@ -57,16 +64,16 @@ def test_results_equal_alone_and_in_the_mix():
         res = wait_all(srv, ids, sizes)
     finally:
         vi.vi_server_destroy(srv)
-    # the mix holds instances of both bodies
-    assert any(i.products[0].L >= 2 for i in insts) and any(i.products[0].L == 1 for i in insts)
+    # the mix holds instances of both bodies, and lead time one on the column body
+    assert any(map(_column_body, insts)) and not all(map(_column_body, insts))
+    assert any(_column_body(i) and i.products[0].L == 1 for i in insts)
     for inst, rid in zip(insts, ids):
         V, pol, info = res[rid]
         assert info["status"] == vi.VI_OK
-        # the server runs the FIFO column body for lead times >= 2 (pmf of at most 47
+        # the server runs the FIFO column body where it applies (pmf of at most 47
         # entries) and the factorised CUDA-core body otherwise (bit-identical across lane
         # widths); the standalone sweep with that body gives the same arithmetic
-        p = inst.products[0]
-        col = inst.issuing == workloads.FIFO and p.L >= 2 and p.m >= 2 and p.Q + 1 <= 32 and p.dmax <= 46
+        col = _column_body(inst)
         kernel = vi.VI_KERNEL_FIFO_COL if col else vi.VI_KERNEL_GROUP
         with Handle(inst, precision="fp32", kernel=kernel) as H:
             Va, pola, ia = H.solve(1e-4, 5000)
