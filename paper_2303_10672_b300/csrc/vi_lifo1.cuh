@@ -127,23 +127,35 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
 
     const uint32_t nS = P.nS;
     const uint32_t nR = nS / (uint32_t)G;
-    const uint32_t ntiles = (nR + 31u) / 32u;       // tiles of 32 rests, one warp each
     const int nrs = P.n_rest_slots;                  // m - 2 rest slots: X_2 .. X_{m-1}
+    // columns: the G rests that differ only in X_{m-1}, the first rest slot issued after
+    // the order (weight w7 in the rest index); a column tile is 32 columns side by side
+    const uint32_t colLen = (nrs >= 2) ? (uint32_t)G : 1u;
+    const uint32_t w7 = (nrs >= 2) ? P.w_top / (uint32_t)G : 0u;   // G^(m-3)
+    const uint32_t nbase = nR / colLen;              // rests with X_{m-1} = 0 (every rest without columns)
+    const uint32_t ncolt = (nbase + 31u) / 32u;      // column tiles
     const uint32_t w_top = P.w_top;                  // G^(m-2): weight of the order's next-state slot
     const int dmax = P.dmax;
     const float gam = (float)kp.gamma;
     const float c_o = (float)P.c_o;
     const float2 *V2 = (const float2 *)B.vin;
-    // 16-byte pieces need 16-byte aligned value buffers (the state offsets of a tile are even)
+    // 16-byte pieces need 16-byte aligned value buffers and a tile that starts on an even state
     const bool al16 = ((((uintptr_t)B.vin) | ((uintptr_t)B.vout)) & 15u) == 0;
     float *kc_col = s_kc + lane;
     float mx = -INFINITY, mn = INFINITY;
 
-    // the gathers of tile t into this lane's column: T[j] = V[r + j G^(m-2)], then
-    // H[k] = V[r after k units issued freshest first] for k <= min(R, dmax); returns R
-    auto prefetch_gathers = [&](uint32_t t) -> int {
-        const uint32_t r = t * 32u + (uint32_t)lane;
-        if (r >= nR) return 0;
+    // the gathers of rest z of column tile c into this lane's column: T[j] = V[r + j G^(m-2)],
+    // then (a fresh rest only) H[k] = V[r after k units issued freshest first] for
+    // k <= min(R, dmax); returns R (Rprev + 1 for the next rest of the same column)
+    auto prefetch_gathers = [&](uint32_t c, uint32_t z, bool fresh, int Rprev) -> int {
+        const uint32_t rb = c * 32u + (uint32_t)lane;
+        if (rb >= nbase) return 0;
+        const uint32_t r = rb + z * w7;
+        if (!fresh) {
+#pragma unroll
+            for (int j = 0; j < G; ++j) l1_cp8(s_TH + j * 32 + lane, V2 + r + (uint32_t)j * w_top);
+            return Rprev + 1;
+        }
         unsigned long long packed = 0ull;
         int Rr = 0;
         uint32_t rem = r;
@@ -173,12 +185,15 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
         }
         return Rr;
     };
-    // the previous values of tile t's states, in 16-byte pieces where aligned
-    auto prefetch_old = [&](uint32_t t) {
-        const uint32_t s0 = t * (uint32_t)(32 * G);
-        const uint32_t nblk = min((uint32_t)(32 * G), nS - s0);
+    // the previous values of a tile's states, in 16-byte pieces where aligned (a tile of
+    // rests z w7 .. z w7 + 31 starts on an odd state when z w7 G is odd)
+    auto tile_s0 = [&](uint32_t c, uint32_t z) -> uint32_t { return (c * 32u + z * w7) * (uint32_t)G; };
+    auto tile_nblk = [&](uint32_t c) -> uint32_t { return min(32u, nbase - c * 32u) * (uint32_t)G; };
+    auto prefetch_old = [&](uint32_t c, uint32_t z) {
+        const uint32_t s0 = tile_s0(c, z);
+        const uint32_t nblk = tile_nblk(c);
         const float2 *src = V2 + s0;
-        if (al16) {
+        if (al16 && !(s0 & 1u)) {
             for (uint32_t i = lane; i < (nblk >> 1); i += 32) l1_cp16(s_VO + 2 * i, src + 2 * i);
             if ((nblk & 1u) && lane == 0) l1_cp8(s_VO + nblk - 1, src + nblk - 1);
         } else {
@@ -186,41 +201,114 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
         }
     };
 
-    const uint32_t wstride = gridDim.x * (uint32_t)WPB;
-    uint32_t tile = blockIdx.x * (uint32_t)WPB + (uint32_t)warp;
+    // The warp's items (column tile, rest z of the column): first F whole columns
+    // wid + k W rest by rest, the H part of each rest after the first following from the
+    // previous one; then the leftover columns' rests dealt out one at a time over all
+    // warps, each computed afresh, so that every warp gets nearly the same number of rests
+    const uint32_t W = gridDim.x * (uint32_t)WPB;
+    const uint32_t wid = blockIdx.x * (uint32_t)WPB + (uint32_t)warp;
+    const uint32_t F = ncolt / W;
+    const uint32_t NL = (ncolt - F * W) * colLen;
+    auto item_at = [&](int ph, uint32_t k, uint32_t z, uint32_t j, uint32_t &ct, uint32_t &zt, bool &fr) -> bool {
+        if (ph == 0) {
+            ct = wid + k * W;
+            zt = z;
+            fr = (z == 0);
+            return true;
+        }
+        const uint32_t jj = wid + j * W;
+        if (jj >= NL) return false;
+        const uint32_t q = jj / colLen;
+        ct = F * W + q;
+        zt = jj - q * colLen;
+        fr = true;
+        return true;
+    };
+    auto advance = [&](int &ph, uint32_t &k, uint32_t &z, uint32_t &j) {
+        if (ph == 0) {
+            if (z + 1 < colLen) {
+                ++z;
+                return;
+            }
+            z = 0;
+            if (++k < F) return;
+            ph = 1;
+            j = 0;
+            return;
+        }
+        ++j;
+    };
+    int ph = (F > 0) ? 0 : 1;
+    uint32_t ik = 0, iz = 0, ij = 0;
+    uint32_t ct = 0, zt = 0;
+    bool fresh = true;
+    bool have = item_at(ph, ik, iz, ij, ct, zt, fresh);
     int Rnext = 0;
-    if (tile < ntiles) Rnext = prefetch_gathers(tile);
+    if (have) Rnext = prefetch_gathers(ct, zt, fresh, 0);
     l1_commit();
-    if (tile < ntiles) prefetch_old(tile);
+    if (have) prefetch_old(ct, zt);
     l1_commit();
-    for (; tile < ntiles; tile += wstride) {
-        const uint32_t next = tile + wstride;
-        const uint32_t r = tile * 32u + (uint32_t)lane;
-        const bool active = r < nR;
+    float2 R0prev = make_float2(0.f, 0.f);
+    // H part of each order's expectation, sum_{k>=1} p_{a+k} H~[k], for a = 0..DP-2 (zero
+    // from dmax on; HP[DP-1] stays zero): carried from rest to rest along a column
+    float HP[DP];
+#pragma unroll
+    for (int a = 0; a < DP; ++a) HP[a] = 0.f;
+    while (have) {
+        int ph2 = ph;
+        uint32_t k2 = ik, z2 = iz, j2 = ij, cn = 0, zn = 0;
+        bool fn = true;
+        advance(ph2, k2, z2, j2);
+        const bool have_next = item_at(ph2, k2, z2, j2, cn, zn, fn);
+        const bool active = ct * 32u + (uint32_t)lane < nbase;
         const int Rrest = Rnext;
         l1_wait<1>();   // this lane's gathers of the tile have landed (its previous values may not)
         float2 R0 = make_float2(0.f, 0.f);
-        float T[G], H[DP];
-        if (active) {
-            const int hcount = min(Rrest, dmax);
-            R0 = s_TH[lane];
-            // pair_diff(g, R0) = (g.hi - R0.hi) + (g.lo - R0.lo), both differences in one packed add
-            const float2 nR0 = make_float2(-R0.x, -R0.y);
-            T[0] = 0.f;
+        if (active) R0 = s_TH[lane];
+        // pair_diff(g, R0) = (g.hi - R0.hi) + (g.lo - R0.lo), both differences in one packed add
+        const float2 nR0 = make_float2(-R0.x, -R0.y);
+        if (fresh) {
+            // the H part from the rest's own sequence, read and summed before T is read (fewer
+            // registers live at once)
+            float H[DP];
             H[0] = 0.f;
+            if (active) {
+                const int hcount = min(Rrest, dmax);
+#pragma unroll
+                for (int k = 1; k < DP; ++k) {
+                    const float2 d = l1_add2(s_TH[(G - 1 + k) * 32 + lane], nR0);
+                    H[k] = (k <= hcount) ? __fadd_rn(d.x, d.y) : H[k - 1];
+                }
+            }
+#pragma unroll
+            for (int a = 0; a + 1 < DP; ++a) {
+                float h = 0.f;
+                if (active) {
+#pragma unroll
+                    for (int k = 1; a + k < DP; ++k) h = fmaf(kp.pmf32[a + k], H[k], h);
+                }
+                HP[a] = h;
+            }
+        } else {
+            // one unit more in X_{m-1}, the first rest unit issued after the order, shifts H by
+            // one: H'[k] = H[k-1], so measured from R0' = V[r'],
+            //   HP'(a) = HP(a + 1) - P(D > a) (V[r'] - V[r])
+            const float dl = active ? pair_diff(R0, R0prev) : 0.f;
+#pragma unroll
+            for (int a = 0; a + 1 < DP; ++a) HP[a] = __fmaf_rn(kp.nsurv32[a], dl, HP[a + 1]);
+        }
+        R0prev = R0;
+        float T[G];
+        T[0] = 0.f;
+        if (active) {
 #pragma unroll
             for (int j = 1; j < G; ++j) {
                 const float2 d = l1_add2(s_TH[j * 32 + lane], nR0);
                 T[j] = __fadd_rn(d.x, d.y);
             }
-#pragma unroll
-            for (int k = 1; k < DP; ++k) {
-                const float2 d = l1_add2(s_TH[(G - 1 + k) * 32 + lane], nR0);
-                H[k] = (k <= hcount) ? __fadd_rn(d.x, d.y) : H[k - 1];
-            }
         }
         __syncwarp();   // the column is read (each lane reads and refills only its own)
-        if (next < ntiles) Rnext = prefetch_gathers(next);
+        if (have_next) Rnext = prefetch_gathers(cn, zn, fn, Rrest);
         l1_commit();
 
         int arg[G];
@@ -234,10 +322,8 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
                 if (active) {
 #pragma unroll
                     for (int d = 0; d < a; ++d) c = fmaf(kp.pmf32[d], T[a - d], c);
-#pragma unroll
-                    for (int k = 1; a + k < DP; ++k) c = fmaf(kp.pmf32[a + k], H[k], c);
                 }
-                C[a] = c;
+                C[a] = __fadd_rn(c, HP[a]);
             }
             // -- first argmax over orders per x on the float key ks_a + LF(x + R + a), with
             // ks_a = -c_o a + gamma C_a + LH(R + a): the rest's LF window covers every key
@@ -382,11 +468,11 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
         // extraction moves the previous values unchanged (only when a buffer is given).
         // The stores are marked streaming (evict first): this sweep never reads them, so
         // L2 keeps the values it still gathers instead
-        const uint32_t s0 = tile * (uint32_t)(32 * G);
-        const uint32_t nblk = min((uint32_t)(32 * G), nS - s0);
+        const uint32_t s0 = tile_s0(ct, zt);
+        const uint32_t nblk = tile_nblk(ct);
         if (B.vout) {
             float2 *dst = (float2 *)B.vout + s0;
-            if (al16) {
+            if (al16 && !(s0 & 1u)) {
                 for (uint32_t i = lane; i < (nblk >> 1); i += 32) __stcs((float4 *)dst + i, ((const float4 *)s_VO)[i]);
                 if ((nblk & 1u) && lane == 0) __stcs(dst + nblk - 1, s_VO[nblk - 1]);
             } else {
@@ -396,8 +482,16 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
         if (B.pol)
             for (uint32_t i = lane; i < nblk; i += 32) B.pol[s0 + i] = s_pol[i];
         __syncwarp();   // the value staging is free for the next tile's previous values
-        if (next < ntiles) prefetch_old(next);
+        if (have_next) prefetch_old(cn, zn);
         l1_commit();
+        ph = ph2;
+        ik = k2;
+        iz = z2;
+        ij = j2;
+        ct = cn;
+        zt = zn;
+        fresh = fn;
+        have = have_next;
     }
     l1_wait<0>();
     if (mode != MODE_EXTRACT) block_reduce_and_finalize<float>(mx, mn, st, mode, gridDim.x);

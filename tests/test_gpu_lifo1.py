@@ -6,8 +6,10 @@ iteration; policies equal except ties whose FP64 Q-gap is <= 1e-6 relative; the
 device stopping test within two sweeps of the oracle's.  The shapes span several
 128-rest tiles with a ragged last tile, both pmf capacities (dmax < 16 and
 16..31), the smallest and largest radix (Q+1 = 2 and 16), a single rest (m = 2),
-demand that stops inside the rest (dmax < units held) and the 19.5M-state
-instance in the launch configuration the benchmark times.
+demand that stops inside the rest (dmax < units held) and, at full size (the
+19.5M-state instance in the launch configuration the benchmark times and a
+62.7M-state one of another radix), the columns of rests along X_{m-1} whose H
+part follows from rest to rest.
 """
 import numpy as np
 import pytest
@@ -63,6 +65,15 @@ def test_lifo1_config4_rescaled_costs():
 def test_lifo1_config4_full_size_sampled():
     # 19,487,171 states, the benchmark's workload and launch configuration
     sampled_backup_parity(workloads.config4(), 3, 400, 44, "fp32", kernel=K)
+
+
+def test_lifo1_columns_other_radix_sampled():
+    # 13^7 = 62,748,517 states: enough column tiles (13^5 / 32) for every warp to walk whole
+    # columns of rests along X_{m-1} (the H part carried from rest to rest) before the
+    # leftover rests are dealt out one at a time; smaller instances compute every rest afresh
+    inst = _inst(8, 12, 5.0, 15, 0.95, seed=8)
+    assert inst.n_states == 13 ** 7
+    sampled_backup_parity(inst, 3, 400, 46, "fp32", kernel=K)
 
 
 def test_lifo1_matches_factorised_group_kernel():
