@@ -249,11 +249,14 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
     if (have) prefetch_old(ct, zt);
     l1_commit();
     float2 R0prev = make_float2(0.f, 0.f);
-    // H part of each order's expectation, sum_{k>=1} p_{a+k} H~[k], for a = 0..DP-2 (zero
-    // from dmax on; HP[DP-1] stays zero): carried from rest to rest along a column
-    float HP[DP];
-#pragma unroll
-    for (int a = 0; a < DP; ++a) HP[a] = 0.f;
+    // H part of each order's expectation, HP(a) = sum_{k>=1} p_{a+k} H~[k] for a = 0..DP-2
+    // (zero from dmax on).  It is carried from rest to rest along a column in the lane's
+    // own H rows of the staging, two values per row: a rest that continues a column gathers
+    // no H, and a fresh rest's H gathers land there only after the previous rest has taken
+    // its values into registers
+    constexpr int NHP = DP - 1;
+    constexpr int NHR = (NHP + 1) / 2;
+    float2 *hpcol = s_TH + G * 32 + lane;
     while (have) {
         int ph2 = ph;
         uint32_t k2 = ik, z2 = iz, j2 = ij, cn = 0, zn = 0;
@@ -267,6 +270,7 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
         if (active) R0 = s_TH[lane];
         // pair_diff(g, R0) = (g.hi - R0.hi) + (g.lo - R0.lo), both differences in one packed add
         const float2 nR0 = make_float2(-R0.x, -R0.y);
+        float hp[NHP];
         if (fresh) {
             // the H part from the rest's own sequence, read and summed before T is read (fewer
             // registers live at once)
@@ -281,21 +285,33 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
                 }
             }
 #pragma unroll
-            for (int a = 0; a + 1 < DP; ++a) {
+            for (int a = 0; a < NHP; ++a) {
                 float h = 0.f;
                 if (active) {
 #pragma unroll
                     for (int k = 1; a + k < DP; ++k) h = fmaf(kp.pmf32[a + k], H[k], h);
                 }
-                HP[a] = h;
+                hp[a] = h;
             }
         } else {
             // one unit more in X_{m-1}, the first rest unit issued after the order, shifts H by
             // one: H'[k] = H[k-1], so measured from R0' = V[r'],
             //   HP'(a) = HP(a + 1) - P(D > a) (V[r'] - V[r])
             const float dl = active ? pair_diff(R0, R0prev) : 0.f;
+            float old[2 * NHR];
 #pragma unroll
-            for (int a = 0; a + 1 < DP; ++a) HP[a] = __fmaf_rn(kp.nsurv32[a], dl, HP[a + 1]);
+            for (int i = 0; i < NHR; ++i) {
+                const float2 v = hpcol[i * 32];
+                old[2 * i] = v.x;
+                old[2 * i + 1] = v.y;
+            }
+#pragma unroll
+            for (int a = 0; a < NHP; ++a) hp[a] = __fmaf_rn(kp.nsurv32[a], dl, (a + 1 < NHP) ? old[a + 1] : 0.f);
+        }
+        if (have_next && !fn) {
+            // the next rest continues this column: keep the H part for it
+#pragma unroll
+            for (int i = 0; i < NHR; ++i) hpcol[i * 32] = make_float2(hp[2 * i], (2 * i + 1 < NHP) ? hp[2 * i + 1] : 0.f);
         }
         R0prev = R0;
         float T[G];
@@ -323,7 +339,7 @@ sweep_lifo1_kernel(KernelParams kp, int mode, const void *vin_arg, void *vout_ar
 #pragma unroll
                     for (int d = 0; d < a; ++d) c = fmaf(kp.pmf32[d], T[a - d], c);
                 }
-                C[a] = __fadd_rn(c, HP[a]);
+                C[a] = __fadd_rn(c, (a < NHP) ? hp[a] : 0.f);
             }
             // -- first argmax over orders per x on the float key ks_a + LF(x + R + a), with
             // ks_a = -c_o a + gamma C_a + LH(R + a): the rest's LF window covers every key
