@@ -328,14 +328,14 @@ def fifo_col_executed_fmas(inst) -> int:
 # summarised in profiles/; an entry is dropped when that kernel changes
 NCU_TRAFFIC = {
     ("cfg2_m5L2Q20_nb_fifo", "sweep_group_kernel (lane width 21)"): 34_362_112,
-    ("cfg4_m8L1Q10_lifo", "sweep_lifo1_kernel"): 235_734_528 + 117_213_696,
+    ("cfg4_m8L1Q10_lifo", "sweep_lifo1_kernel"): 236_745_984 + 114_699_264,
     ("cfg2_m5L2Q20_nb_fifo", "sweep_fifo_col_kernel"): 32_748_288 + 749_568,
 }
 # thread instructions of one launch of the dominant kernel (warp instructions x active
 # threads per warp instruction), from the same captures
 NCU_THREAD_INSTR = {
     ("cfg2_m5L2Q20_nb_fifo", "sweep_group_kernel (lane width 21)"): 187_319_919 * 29.41,
-    ("cfg4_m8L1Q10_lifo", "sweep_lifo1_kernel"): 64_768_184 * 31.62,
+    ("cfg4_m8L1Q10_lifo", "sweep_lifo1_kernel"): 63_584_026 * 31.62,
     ("cfg2_m5L2Q20_nb_fifo", "sweep_fifo_col_kernel"): 96_298_900 * 27.59,
 }
 
