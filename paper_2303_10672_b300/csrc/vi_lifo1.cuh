@@ -21,16 +21,29 @@
 // values per rest serves all G^2 keys; the exact value of the chosen order is
 // rebuilt from the (hi, lo) pair of RT.
 //
+// Columns of rests.  X_{m-1}, the freshest rest slot, is the first one issued
+// after the order, so a rest r' with one unit more there has H_{r'}[k] = H_r[k-1]
+// (k >= 1), and the H part of each order's expectation,
+// HP(a) = sum_{k>=1} p_{a+k} H~[k] measured from R0, follows from the previous
+// rest's:  HP'(a) = HP(a + 1) - P(D > a) (V[r'] - V[r]).  The G rests that differ
+// only in X_{m-1} form a column; its first rest gathers H and sums HP, each
+// further rest gathers only T and takes HP by that recurrence.
+//
 // G = Q+1 and the pmf capacity DP (> dmax) are compile-time, so the convolution
 // and the max over (x, a) are fully unrolled without per-thread bounds.  One
-// thread owns one rest (its G states); each warp walks tiles of 32 rests on its
-// own (persistent blocks, tables staged once per block, no block-wide barrier in
-// the tile loop), so the warps of an SM drift apart and overlap each other's
-// phases.  The gathers of the warp's next tile and the previous values of its
-// current one are copied into shared memory by cp.async while it computes; the
-// new values replace the previous ones there (their change feeds the stopping
-// test) and leave in 16-byte pieces.  The exact rebuild of the chosen orders runs
-// on pairs of x in packed FP32 arithmetic, lane-wise the scalar operations.
+// thread owns one rest (its G states); each warp walks column tiles of 32 side by
+// side on its own, rest by rest (persistent blocks, tables staged once per block,
+// no block-wide barrier in the loop), so the warps of an SM drift apart and
+// overlap each other's phases.  A warp takes floor(column tiles / warps) whole
+// columns; the leftover columns' rests are then dealt out one at a time over all
+// warps and computed afresh, so that the warps get nearly equal work.  The gathers
+// of the warp's next tile and the previous values of its current one are copied
+// into shared memory by cp.async while it computes; the new values replace the
+// previous ones there (their change feeds the stopping test) and leave in 16-byte
+// pieces where the tile starts on an even state.  HP waits for the next rest of a
+// column in the lane's own H rows of that staging, which such a rest does not
+// gather into.  The exact rebuild of the chosen orders runs on pairs of x in packed
+// FP32 arithmetic, lane-wise the scalar operations.
 #pragma once
 
 #include <algorithm>
