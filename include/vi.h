@@ -224,8 +224,10 @@ vi_status vi_problem_sizes(vi_handle h, uint64_t *n_states, int *n_actions,
  * VI_KERNEL_LIFO_L1 (factorised LIFO sweep for lead time one: every order's
  * next states lie on two sequences of the rest -- the order partly used, the
  * order used up and the rest issued freshest first -- gathered once per rest,
- * so each order's expectation is a short convolution of them with the pmf;
- * persistent blocks; VI_EINVAL unless one product, LIFO, VI_PREC_FP32, L = 1,
+ * so each order's expectation is a short convolution of them with the pmf; the
+ * used-up part carried from rest to rest along the rests that differ only in
+ * the freshest rest slot (the first one issued after the order); persistent
+ * blocks; VI_EINVAL unless one product, LIFO, VI_PREC_FP32, L = 1,
  * m >= 2, 2 <= Q+1 <= 16 and Dmax <= 31) or
  * VI_KERNEL_FIFO_COL (FIFO sweep by columns of rests: the Q+1 rests that
  * differ only in the oldest rest slot Z_1 share one expectation over the
