@@ -302,14 +302,28 @@ def algorithmic_work(inst) -> dict:
             "work": "2 flop (one multiply-add) per state x order x demand outcome, the method's arithmetic"}
 
 
-def lifo1_executed_fmas(inst) -> int:
-    """Multiply-adds the lead-time-one LIFO sweep executes per launch: per rest and
-    order a, a terms on the partly used order and DP - 1 - a on the rest (DP = 16 or
-    32 pmf slots, zero past dmax), i.e. G (DP - 1) per rest."""
+def lifo1_executed_fmas(inst, n_sm: int = 148) -> int:
+    """Multiply-adds the lead-time-one LIFO sweep executes per launch.  Per rest, the part
+    on the partly used order, a terms for order a (G (G - 1) / 2); the part on the used-up
+    sequence, sum_{a < DP-1} (DP - 1 - a) at a rest computed afresh and DP - 1 (one step of
+    the recurrence per entry) at a further rest of a column.  Columns are the G rests that
+    differ in X_{m-1}; each of the kernel's warps (4 per block, one wave of resident blocks:
+    4 per SM with a 16-slot pmf, 2 with 32) walks floor(column tiles / warps) whole columns,
+    and the leftover columns' rests are computed afresh."""
     p = inst.products[0]
     G = p.Q + 1
     DP = 16 if p.dmax < 16 else 32
-    return (p.n_states // G) * G * (DP - 1)
+    nrs = p.m - 2
+    n_rests = p.n_states // G
+    col = G if nrs >= 2 else 1
+    nbase = n_rests // col
+    tiles = (nbase + 31) // 32
+    warps = min((n_rests + 127) // 128, n_sm * (4 if DP == 16 else 2)) * 4
+    whole = (tiles // warps) * warps                      # column tiles walked whole
+    whole_rests = min(whole * 32, nbase) * col
+    fresh = min(whole * 32, nbase) + (n_rests - whole_rests)
+    per_fresh = (DP - 1) * DP // 2
+    return n_rests * G * (G - 1) // 2 + fresh * per_fresh + (n_rests - fresh) * (DP - 1)
 
 
 def fifo_col_executed_fmas(inst) -> int:
@@ -412,7 +426,8 @@ def roofline_of(vi, torch, inst, kernel_name: str, k_ms: float, sm_mhz: float, l
         out["issue"] = {"thread_instructions_per_update": per_update, "ceiling_updates_per_s": ceiling,
                         "achieved_updates_per_s": rate, "frac": rate / ceiling}
     if kernel_name in ("sweep_lifo1_kernel", "sweep_fifo_col_kernel"):
-        fm = lifo1_executed_fmas(inst) if kernel_name == "sweep_lifo1_kernel" else fifo_col_executed_fmas(inst)
+        fm = (lifo1_executed_fmas(inst, n_sm) if kernel_name == "sweep_lifo1_kernel"
+              else fifo_col_executed_fmas(inst))
         out["executed_fmas_per_launch"] = fm
         out["executed_fp32_frac"] = 2 * fm / (k_ms * 1e-3) / 1e12 / fp32_peak
     if len(inst.products) == 1 and l2_gbs:
